@@ -1,0 +1,529 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+None of these compares the oracle with itself: each check uses an
+independent route (numerical quadrature of the heat kernel, a library
+B-spline routine, Kronecker products of 1-D matrices, textbook closed forms,
+conservation identities, convergence rates, values printed in the paper).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.sparse as sp
+from scipy.interpolate import BSpline
+
+import workloads as W
+from oracle import assembly, bspline, pointsource, sources
+from oracle.geometry import PatchGeom
+from oracle.solver import Model, ThetaSolver
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MAT = W.MAT_DEFAULT
+ALPHA = MAT.k / (MAT.rho * MAT.cp)
+
+
+def _gh(n):
+    return np.polynomial.hermite.hermgauss(n)
+
+
+# ---------------------------------------------------------------------------
+# P1: the tau-shifted point source is a Gaussian spot (1/e^2 radius r,
+#     variance r^2/4 per axis) carried forward by the heat kernel
+#     (Section 2.1, Eq. semi-temperature and the definition of tau).
+# ---------------------------------------------------------------------------
+def _conv_1d(xd, s, sigma0, n=80):
+    """int G1(xd - y, s) phi1(y) dy by Gauss-Hermite with the narrower of the
+    two Gaussians as weight.  G1 = heat kernel of diffusivity ALPHA, phi1 the
+    spot profile of variance sigma0^2."""
+    u, w = _gh(n)
+    var_g = 2.0 * ALPHA * s
+    if s == 0.0:
+        return np.exp(-xd ** 2 / (2 * sigma0 ** 2)) / np.sqrt(2 * np.pi * sigma0 ** 2)
+    if var_g < sigma0 ** 2:
+        y = xd + np.sqrt(2 * var_g) * u              # weight: heat kernel around xd
+        f = np.exp(-y ** 2 / (2 * sigma0 ** 2)) / np.sqrt(2 * np.pi * sigma0 ** 2)
+    else:
+        y = np.sqrt(2 * sigma0 ** 2) * u             # weight: spot profile
+        f = np.exp(-(xd - y) ** 2 / (4 * ALPHA * s)) / np.sqrt(4 * np.pi * ALPHA * s)
+    return np.dot(w, f) / np.sqrt(np.pi)
+
+
+@pytest.mark.parametrize("t_since", [0.0, 2e-6, 3e-5, 4e-4])
+def test_P1_point_source_equals_heat_kernel_convolution(t_since):
+    r = 20e-6
+    E = 1e-3
+    age = np.array([t_since + r * r / (8 * ALPHA)])
+    xs = np.zeros((1, 3))
+    pts = np.array([[0, 0, 0], [15e-6, -10e-6, -5e-6], [40e-6, 20e-6, -30e-6],
+                    [-70e-6, 5e-6, -60e-6]])
+    got = pointsource.T_point(pts, xs, age, E, MAT, s_img=1.0)[:, 0]
+    sigma0 = r / 2.0
+    for q, x in enumerate(pts):
+        ref = E / (MAT.rho * MAT.cp)
+        for d in range(3):
+            ref *= _conv_1d(x[d], t_since, sigma0)
+        assert abs(got[q] - ref) <= 1e-11 * abs(ref) + 1e-300, (q, got[q], ref)
+
+
+# ---------------------------------------------------------------------------
+# P2: T~ solves the heat equation; the gradient is its derivative; the normal
+#     derivative vanishes on the top plane (Section 2.1).
+# ---------------------------------------------------------------------------
+def test_P2_heat_equation_and_gradient_by_finite_differences():
+    E = 5e-4
+    xs = np.array([[0.1e-3, -0.05e-3, 0.0]])
+    x0 = np.array([[0.13e-3, -0.02e-3, -0.04e-3]])
+    age = np.array([3e-5])
+    T = lambda x, a: pointsource.T_point(x, xs, np.array([a]), E, MAT)[0, 0]
+    g = pointsource.gradT_point(x0, xs, age, E, MAT)[0, 0]
+    h = 1e-8
+    lap = 0.0
+    for d in range(3):
+        e = np.zeros((1, 3))
+        e[0, d] = h
+        fd = (T(x0 + e, age[0]) - T(x0 - e, age[0])) / (2 * h)
+        assert abs(fd - g[d]) < 1e-6 * np.abs(g).max()
+        lap += (T(x0 + e, age[0]) - 2 * T(x0, age[0]) + T(x0 - e, age[0])) / h ** 2
+    ht = 1e-9
+    dTdt = (T(x0, age[0] + ht) - T(x0, age[0] - ht)) / (2 * ht)
+    assert abs(dTdt - ALPHA * lap) < 1e-4 * abs(dTdt)
+    # normal derivative on the top plane z = z_source vanishes
+    xt = np.array([[0.3e-3, 0.1e-3, 0.0]])
+    gt = pointsource.gradT_point(xt, xs, age, E, MAT)[0, 0]
+    assert gt[2] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# P3: E = A P dt printed in Section 3.1; the half-space integral carries E
+#     for s_img = 2 (reading R2) and E/2 for the printed s_img = 1.
+# ---------------------------------------------------------------------------
+def _golden_kv(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split()[:2]
+        out[k] = float(v)
+    return out
+
+
+def test_P3_energy_per_source_matches_paper():
+    g = _golden_kv("paper_energy.txt")
+    scan = W.straight_track((0, 0, 0), (1e-3, 0, 0), power=g["power_W"],
+                            absorptivity=g["absorptivity"], speed=0.5)
+    E = sources.energy(scan, g["dt_s"])
+    assert round(E, 7) == pytest.approx(g["E_J"], abs=0.005e-4)
+
+
+@pytest.mark.parametrize("s_img", [1.0, 2.0])
+def test_P3_half_space_energy(s_img):
+    E = 6.35e-4
+    age = np.array([4e-5])
+    xs = np.zeros((1, 3))
+    u, w = _gh(60)
+    sig = np.sqrt(4 * ALPHA * age[0])
+    X, Y = np.meshgrid(sig * u, sig * u, indexing="ij")
+    WW = np.outer(w, w) * sig * sig * np.exp(np.outer(u * u, np.ones_like(u)) +
+                                             np.outer(np.ones_like(u), u * u))
+
+    def fz(z):
+        pts = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+        return np.dot(WW.ravel(), pointsource.T_point(pts, xs, age, E, MAT, s_img)[:, 0])
+
+    val, _ = si.quad(fz, -12.0 * sig, 0.0, epsabs=0, epsrel=1e-12, limit=200)
+    energy = MAT.rho * MAT.cp * val
+    assert energy == pytest.approx(s_img * E / 2.0, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# P4: a long straight track of s_img = 2 sources converges to Rosenthal's
+#     quasi-steady moving point-source solution (textbook closed form).
+# ---------------------------------------------------------------------------
+def test_P4_sum_converges_to_rosenthal():
+    """Every tau-shifted source is a point source released r^2/(8 alpha)
+    before its activation, so the equivalent continuous laser sits v r^2/(8
+    alpha) ahead of the last source.  With that position the sum of equally
+    spaced sources reproduces Rosenthal's solution to rounding (the rectangle
+    rule is spectrally accurate for this smooth, decaying integrand)."""
+    P, A, v, dt = 200.0, 0.4, 1.0, 2e-6
+    n_src = 15000                      # 30 mm of track, 30 ms
+    L = (n_src - 1) * v * dt
+    scan = W.straight_track((0, 0, 0), (L, 0, 0), P, A, v)
+    xs = sources.discretize(scan, dt)
+    assert len(xs) == n_src
+    E = sources.energy(scan, dt)
+    age = pointsource.ages(n_src, n_src, dt, MAT, scan.spot_radius)
+    x_laser = xs[-1, 0] + v * scan.spot_radius ** 2 / (8 * ALPHA)
+    rel = np.array([[-300e-6, 120e-6, -50e-6], [0.0, 250e-6, 0.0], [150e-6, 200e-6, -100e-6],
+                    [-600e-6, 0.0, -200e-6], [-250e-6, -250e-6, 0.0], [-100e-6, 60e-6, -60e-6]])
+    pts = rel + np.array([xs[-1, 0], 0, 0])
+    got = pointsource.T_tilde(pts, xs, age, E, MAT, s_img=2.0)
+    d = pts - np.array([x_laser, 0, 0])
+    R = np.linalg.norm(d, axis=1)
+    ros = A * P / (2 * np.pi * MAT.k * R) * np.exp(-v * (R + d[:, 0]) / (2 * ALPHA))
+    np.testing.assert_allclose(got, ros, rtol=1e-10)
+    # the printed full-space kernel (s_img = 1) carries half of it
+    got1 = pointsource.T_tilde(pts, xs, age, E, MAT, s_img=1.0)
+    np.testing.assert_allclose(got1, 0.5 * ros, rtol=1e-10)
+
+
+def test_R1_source_discretisation_counts_and_spacing():
+    wl = W.block_meander(n_tracks=3)
+    xs = sources.discretize(wl.scan, wl.dt)
+    assert len(xs) == 3 * 584                         # 3.5 mm / 6 um -> 584 per track
+    d = np.linalg.norm(np.diff(xs[:584], axis=0), axis=1)
+    np.testing.assert_allclose(d, 1.2 * 5e-6, rtol=1e-9)
+    # second track runs back, starting at its own start point
+    np.testing.assert_allclose(xs[584], [3.75e-3, 1.15e-3, 1e-3], atol=1e-15)
+    # contour: arc length continues across vertices of one track
+    sc = W.Scan(path=np.array([[0, 0, 0], [1e-4, 0, 0], [1e-4, 1e-4, 0]]),
+                seg_on=np.array([1, 1], np.uint8), power=1, absorptivity=1, speed=1.0)
+    xc = sources.discretize(sc, 3e-5)
+    np.testing.assert_allclose(xc[4], [1e-4, 2e-5, 0], atol=1e-15)
+    assert len(xc) == 7
+
+
+# ---------------------------------------------------------------------------
+# P5: basis functions.
+# ---------------------------------------------------------------------------
+def test_P5_partition_of_unity_and_library_bspline():
+    U = np.array([0, 0, 0, 0.2, 0.2, 0.5, 0.7, 1, 1, 1], float)
+    p = 2
+    n = len(U) - p - 1
+    for u in np.linspace(0, 1, 57):
+        N, dN = bspline.basis_all_ders(U, p, u)
+        assert abs(N.sum() - 1) < 1e-15
+        assert abs(dN.sum()) < 1e-12
+        for i in range(n):
+            c = np.zeros(n)
+            c[i] = 1
+            spl = BSpline(U, c, p, extrapolate=False)
+            ref = spl(u) if u < 1 else BSpline(U, c, p)(u)
+            dref = spl.derivative()(u) if u < 1 else BSpline(U, c, p).derivative()(u)
+            if u in (0.2,):  # C0 knot: derivative one-sided (right limit) in both
+                continue
+            assert abs(N[i] - ref) < 1e-14
+            assert abs(dN[i] - dref) < 1e-11
+
+
+def test_P5_bernstein_on_one_element():
+    U = np.array([0, 0, 0, 0, 1, 1, 1, 1], float)
+    for u in np.linspace(0, 1, 11):
+        N, dN = bspline.basis_all_ders(U, 3, u)
+        B = [(1 - u) ** 3, 3 * u * (1 - u) ** 2, 3 * u ** 2 * (1 - u), u ** 3]
+        dB = [-3 * (1 - u) ** 2, 3 * (1 - u) ** 2 - 6 * u * (1 - u), 6 * u * (1 - u) - 3 * u ** 2,
+              3 * u ** 2]
+        np.testing.assert_allclose(N, B, atol=1e-15)
+        np.testing.assert_allclose(dN, dB, atol=1e-13)
+
+
+def _table2_patch():
+    """Quarter-cylinder part of Table 2 extruded from z = 0 to the printed
+    top surface z = 2 mm (unit: m)."""
+    rows = []
+    kn = {}
+    for line in open(os.path.join(GOLDEN, "table2_control_net.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = line.split()
+        if f[0].startswith("knots"):
+            kn[f[0]] = np.array([float(v) for v in f[1:]])
+            continue
+        ev = lambda s: float(eval(s, {"sqrt": np.sqrt}))
+        rows.append(([ev(v) for v in f[1:4]], [ev(v) for v in f[4:7]]))
+    n0 = len(rows)
+    ctrl = np.zeros((2, 2, n0, 3))
+    for i, (b1, b2) in enumerate(rows):
+        for k, z in enumerate((0.0, 2.0)):
+            ctrl[k, 0, i] = [b1[0], b1[1], z]
+            ctrl[k, 1, i] = [b2[0], b2[1], z]
+    wmid = np.cos(np.pi / 8)
+    w1 = np.array([1, wmid, 1, wmid, 1.0])
+    weights = np.broadcast_to(w1, (2, 2, n0)).copy()
+    patch = W.Patch(degree=(2, 1, 1), knots=[kn["knots_xi"], kn["knots_eta"], kn["knots_zeta"]],
+                    ctrl=ctrl * 1e-3, weights=weights)
+    return patch
+
+
+def test_P5_table2_arc_is_exact_circle():
+    g = PatchGeom(_table2_patch())
+    for u in np.linspace(0, 1, 41):
+        x = g.point([u, 0.0, 1.0])
+        assert abs(np.hypot(x[0] - 2e-3, x[1]) - 1e-3) < 1e-17
+        assert abs(x[2] - 2e-3) < 1e-18
+        # the ruled surface stays inside the square [0, 2] x [0, 2] mm
+        y = g.point([u, 0.5, 0.5])
+        assert -1e-15 <= y[0] <= 2e-3 + 1e-15 and -1e-15 <= y[1] <= 2e-3 + 1e-15
+    # without the weights the arc is not a circle (the pin can fail)
+    p = _table2_patch()
+    p.weights = None
+    g2 = PatchGeom(p)
+    x = g2.point([0.25, 0.0, 1.0])
+    assert abs(np.hypot(x[0] - 2e-3, x[1]) - 1e-3) > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# P6: assembly.
+# ---------------------------------------------------------------------------
+def _bspline_1d_matrices(U, p, L, nq=12):
+    """1-D mass and stiffness of B-splines via scipy's BSpline (independent
+    of the oracle's Cox-de Boor) and a high-order Gauss rule on each span."""
+    n = len(U) - p - 1
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    Mx = np.zeros((n, n))
+    Sx = np.zeros((n, n))
+    spl = []
+    for i in range(n):
+        c = np.zeros(n)
+        c[i] = 1
+        b = BSpline(U, c, p)
+        spl.append((b, b.derivative()))
+    for a, bnd in zip(U[:-1], U[1:]):
+        if bnd <= a:
+            continue
+        u = a + (bnd - a) * (xg + 1) / 2
+        w = wg * (bnd - a) / 2
+        V = np.array([s[0](u) for s in spl])
+        D = np.array([s[1](u) for s in spl])
+        Mx += (V * w) @ V.T
+        Sx += (D * w) @ D.T
+    return Mx * L, Sx / L
+
+
+def test_P6_cuboid_matrices_are_kronecker_products():
+    size = (0.9e-3, 0.7e-3, 0.4e-3)
+    n_el = (4, 3, 2)
+    patch = W.cuboid_patch(size, n_el, 2)
+    g = PatchGeom(patch)
+    rho_cp = MAT.rho * MAT.cp
+    M, K = assembly.assemble_MK(g, rho_cp, MAT.k)
+    m1 = [_bspline_1d_matrices(patch.knots[d], 2, size[d]) for d in range(3)]
+    Mk = rho_cp * np.kron(m1[2][0], np.kron(m1[1][0], m1[0][0]))
+    Kk = MAT.k * (np.kron(m1[2][1], np.kron(m1[1][0], m1[0][0])) +
+                  np.kron(m1[2][0], np.kron(m1[1][1], m1[0][0])) +
+                  np.kron(m1[2][0], np.kron(m1[1][0], m1[0][1])))
+    np.testing.assert_allclose(M.toarray(), Mk, rtol=0, atol=1e-12 * np.abs(Mk).max())
+    np.testing.assert_allclose(K.toarray(), Kk, rtol=0, atol=1e-12 * np.abs(Kk).max())
+    assert M.sum() == pytest.approx(rho_cp * np.prod(size), rel=1e-13)
+
+
+def _distorted_patch(weights=False, seed=3):
+    rng = np.random.default_rng(seed)
+    patch = W.cuboid_patch((1e-3, 0.8e-3, 0.5e-3), (3, 3, 2), 2)
+    c = patch.ctrl.copy()
+    inner = c[1:-1, 1:-1, 1:-1]
+    inner += rng.uniform(-0.04e-3, 0.04e-3, inner.shape)
+    # bend the side faces too (keep the top plane flat)
+    c[:-1, :, 0, 0] += rng.uniform(-0.03e-3, 0.03e-3, c[:-1, :, 0, 0].shape)
+    c[:-1, 0, :, 1] += rng.uniform(-0.03e-3, 0.03e-3, c[:-1, 0, :, 1].shape)
+    patch.ctrl = c
+    if weights:
+        patch.weights = rng.uniform(0.8, 1.2, c.shape[:3])
+    return patch
+
+
+def test_P6_symmetry_constants_and_volume_on_curved_nurbs():
+    patch = _distorted_patch(weights=True)
+    g = PatchGeom(patch)
+    M, K = assembly.assemble_MK(g, 1.0, 1.0)
+    assert abs(M - M.T).max() < 1e-14 * abs(M).max()
+    assert abs(K - K.T).max() < 1e-14 * abs(K).max()
+    assert np.abs(K @ np.ones(g.n_dof)).max() < 1e-12 * abs(K).max()
+    # volume by the divergence theorem on the faces: V = (1/3) int x . n dS
+    V = 0.0
+    for f in range(6):
+        fp = g.face_points(f)
+        V += np.sum(fp["wdS"] * np.einsum("qc,qc->q", fp["x"], fp["n"])) / 3.0
+    assert M.sum() == pytest.approx(V, rel=1e-6)
+
+
+def test_P6_patch_test_linear_field_is_reproduced():
+    """Steady conduction with flux data of a linear field on every face but
+    the Dirichlet bottom: the Galerkin solution is the linear field itself
+    (isoparametric; 3-point Gauss is exact for this B-spline patch)."""
+    patch = _distorted_patch(weights=False)
+    patch.faces = (1, 1, 1, 1, 2, 1)
+    g = PatchGeom(patch)
+    M, K = assembly.assemble_MK(g, 1.0, MAT.k)
+    a, b = 300.0, np.array([2.0e4, -1.5e4, 3.0e4])
+    ctrl = patch.ctrl.reshape(-1, 3)
+    T_exact = a + ctrl @ b
+    pts = assembly.boundary_points(g, 1)
+    F = assembly.weight_matrix(g, pts) @ (MAT.k * pts["n"] @ b)
+    d = g.dirichlet_dofs()
+    f = ~d
+    Kff = K[f][:, f].toarray()
+    rhs = F[f] - K[f][:, d] @ T_exact[d]
+    T_f = np.linalg.solve(Kff, rhs)
+    np.testing.assert_allclose(T_f, T_exact[f], rtol=0, atol=1e-9 * a)
+
+
+# ---------------------------------------------------------------------------
+# P7: space and time convergence on a manufactured heat solution.
+# ---------------------------------------------------------------------------
+def _manufactured(n_el, dt, n_steps, theta, p=2):
+    Lx, Ly, Lz = 1e-3, 1e-3, 0.5e-3
+    kap = np.array([np.pi / Lx, 0.7 * np.pi / Ly, 0.5 * np.pi / Lz])
+    phi = 0.3
+    amp = 5.0
+    lam = ALPHA * kap @ kap
+
+    def T_ex(x, t):
+        return MAT.T_c + amp * np.exp(-lam * t) * np.cos(x @ kap + phi)
+
+    def grad_ex(x, t):
+        return -amp * np.exp(-lam * t) * np.sin(x @ kap + phi)[:, None] * kap[None, :]
+
+    patch = W.cuboid_patch((Lx, Ly, Lz), (n_el, n_el, max(1, n_el // 2)), p)
+    patch.faces = (1, 1, 1, 1, 2, 1)
+    g = PatchGeom(patch)
+    rho_cp = MAT.rho * MAT.cp
+    M, K = assembly.assemble_MK(g, rho_cp, MAT.k)
+    nb = assembly.boundary_points(g, 1)
+    Wn = assembly.weight_matrix(g, nb)
+    bot = assembly.boundary_points(g, 2)
+    Wb = assembly.weight_matrix(g, bot)
+    d = g.dirichlet_dofs()
+    Mb = assembly.boundary_mass(g, bot)[d][:, d].toarray()
+
+    def F_at(t):
+        return Wn @ (MAT.k * np.einsum("qc,qc->q", grad_ex(nb["x"], t), nb["n"]))
+
+    def g_at(t):
+        return np.linalg.solve(Mb, (Wb @ T_ex(bot["x"], t))[d])
+
+    # initial coefficients: L2 projection of T_ex(., 0)
+    elems = g.element_list()
+    rows = []
+    for e in elems:
+        for xi, wt in g.element_quadrature(e):
+            dofs, R, dR, x, J = g.local_eval(xi, [e[k][2] for k in range(3)])
+            rows.append((dofs, R, x, wt * np.linalg.det(J)))
+    n = g.n_dof
+    Mp = np.zeros((n, n))
+    bp = np.zeros(n)
+    for dofs, R, x, w in rows:
+        Mp[np.ix_(dofs, dofs)] += w * np.outer(R, R)
+        bp[dofs] += w * R * T_ex(x[None, :], 0.0)[0]
+    T = np.linalg.solve(Mp, bp)
+    solver = ThetaSolver(M, K, d, dt, theta)
+    F0 = F_at(0.0)
+    for s in range(n_steps):
+        t1 = (s + 1) * dt
+        F1 = F_at(t1)
+        T = solver.step(T, F0, F1, g_at(t1))
+        F0 = F1
+    err2 = 0.0
+    for dofs, R, x, w in rows:
+        err2 += w * (R @ T[dofs] - T_ex(x[None, :], n_steps * dt)[0]) ** 2
+    return np.sqrt(err2), T
+
+
+def test_P7_spatial_convergence_rate():
+    dt, nst = 2e-4, 10
+    errs = [_manufactured(n, dt, nst, 0.5)[0] for n in (2, 4, 8)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > 2.6, (errs, rates)          # O(h^{p+1}) = O(h^3) for p = 2
+
+
+def _ramped_run(dt, n_steps, theta):
+    """Start at T_c (exact in the space, compatible with the data at t = 0)
+    and drive the lateral/top flux and the bottom temperature by a smooth
+    ramp s(t) = sin^2(pi t / (2 T)) that starts with zero slope, so that the
+    semi-discrete solution is smooth in time and the step order shows."""
+    patch = W.cuboid_patch((1e-3, 1e-3, 0.5e-3), (3, 3, 2), 2)
+    patch.faces = (1, 1, 1, 1, 2, 1)
+    g = PatchGeom(patch)
+    M, K = assembly.assemble_MK(g, MAT.rho * MAT.cp, MAT.k)
+    nb = assembly.boundary_points(g, 1)
+    q_prof = assembly.weight_matrix(g, nb) @ (2e5 * np.cos(3e3 * nb["x"][:, 0]) * nb["n"][:, 1])
+    d = g.dirichlet_dofs()
+    g_prof = 4.0 * np.sin(2e3 * patch.ctrl.reshape(-1, 3)[d, 0])
+    T_tot = 4e-3
+    ramp = lambda t: np.sin(0.5 * np.pi * t / T_tot) ** 2
+    solver = ThetaSolver(M, K, d, dt, theta)
+    T = np.full(g.n_dof, MAT.T_c)
+    F0 = ramp(0.0) * q_prof
+    for s_ in range(n_steps):
+        t1 = (s_ + 1) * dt
+        F1 = ramp(t1) * q_prof
+        T = solver.step(T, F0, F1, MAT.T_c + ramp(t1) * g_prof)
+        F0 = F1
+    return T
+
+
+@pytest.mark.parametrize("theta,order", [(0.5, 2), (1.0, 1)])
+def test_P7_temporal_convergence_rate(theta, order):
+    T_end = 4e-3
+    sols = [_ramped_run(T_end / nst, nst, theta) for nst in (8, 16, 32, 512)]
+    ref = sols[-1]
+    e = [np.abs(s - ref).max() for s in sols[:-1]]
+    rates = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert np.all(np.abs(rates - order) < 0.25), (e, rates)
+
+
+# ---------------------------------------------------------------------------
+# P9: conservation.  All faces but the top carry the T~ flux (no Dirichlet):
+#     (a) algebraic: 1^T M (T^{n+1} - T^n) = dt 1^T (theta F^{n+1} + (1-theta) F^n);
+#     (b) physical: box integral of rho c (T~ + T^ - T_c) equals the absorbed
+#         energy n E, with the box integral of T~ in closed form (erf).
+# ---------------------------------------------------------------------------
+def _box_T_tilde_integral(lo, hi, xs, age, E, s_img=2.0):
+    from scipy.special import erf
+    sig = np.sqrt(2 * ALPHA * age)
+    tot = np.full(len(age), s_img * E / (MAT.rho * MAT.cp))
+    for d in range(3):
+        a = (lo[d] - xs[:, d]) / (np.sqrt(2) * sig)
+        b = (hi[d] - xs[:, d]) / (np.sqrt(2) * sig)
+        tot *= 0.5 * (erf(b) - erf(a))
+    return MAT.rho * MAT.cp * tot.sum()
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0])
+def test_P9_energy_balance_all_neumann(theta):
+    size = (0.8e-3, 0.5e-3, 0.3e-3)
+    patch = W.cuboid_patch(size, (16, 10, 6), 2, faces=(1, 1, 1, 1, 1, 0))
+    scan = W.straight_track((0.1e-3, 0.08e-3, 0.3e-3), (0.7e-3, 0.08e-3, 0.3e-3),
+                            power=100.0, absorptivity=0.5, speed=1.0)
+    wl = W.Workload("p9", patch, MAT, scan, dt=10e-6, theta=theta, n_steps=60)
+    m = Model(wl)
+    ones = np.ones(m.geom.n_dof)
+    roundoff = 1e-13 * (ones @ (m.M @ ones)) * MAT.T_c      # rounding of 1^T M T
+    leak = 0.0
+    for _ in range(wl.n_steps):
+        T0, F0 = m.T_hat.copy(), m.F.copy()
+        m.step()
+        lhs = ones @ (m.M @ (m.T_hat - T0))
+        rhs = wl.dt * ones @ (theta * m.last["F"] + (1 - theta) * F0)
+        assert abs(lhs - rhs) <= 1e-9 * abs(rhs) + roundoff
+        leak += rhs
+    n = m.n
+    age = m.source_ages(n)
+    inside = _box_T_tilde_integral((0, 0, 0), size, m.xs[:n], age, m.E)
+    total = inside + ones @ (m.M @ (m.T_hat - MAT.T_c))
+    assert (n * m.E - inside) > 0.05 * n * m.E       # a real share leaves through the walls
+    assert total == pytest.approx(n * m.E, rel=0.02)
+
+
+def test_P10_far_field_correction_vanishes():
+    patch = W.cuboid_patch((2e-3, 2e-3, 1e-3), (8, 8, 4), 2)
+    scan = W.straight_track((1e-3, 1e-3, 1e-3), (1.02e-3, 1e-3, 1e-3), 100.0, 0.5, 1.0)
+    wl = W.Workload("p10", patch, MAT, scan, dt=5e-6, theta=0.5, n_steps=5)
+    m = Model(wl)
+    m.run(5)
+    assert np.abs(m.T_hat - MAT.T_c).max() < 1e-9
+
+
+def test_R5_dirichlet_projection_reproduces_face_space_functions():
+    """The L2 projection returns the coefficients of any function of the
+    bottom-face spline space; linear fields are in it (x = sum R_i P_i)."""
+    wl = W.small_block(n_el=(4, 3, 2))
+    m = Model(wl, build_solver=False)
+    ctrl = wl.patch.ctrl.reshape(-1, 3)
+    f = lambda x: 2.0 + 3e3 * x[:, 0] - 5e3 * x[:, 1]
+    # T~ chosen so that T_c - T~ = f on the bottom face
+    g = m.dirichlet_g(wl.material.T_c - f(m.bot["x"]))
+    np.testing.assert_allclose(g, f(ctrl[m.dir]), rtol=0, atol=1e-12)
