@@ -1,0 +1,207 @@
+/*
+ * sa.h - C ABI of the GB300 semi-analytical isogeometric thermal library.
+ *
+ * The method (Sections 2-2.4 of the paper): the temperature of a part under
+ * a scanning laser is split into T = T~ + T^ (Eq. temperature-decomposition).
+ * T~ is a closed-form sum of point-source solutions over every past laser
+ * position (Eqs. sum-of-point-temp, semi-temperature); T^ solves the
+ * source-free heat equation on a NURBS patch (Eq. that-heat) with Neumann
+ * data k dT~/dn on the lateral faces (Eq. that-bc-n) and Dirichlet data
+ * T_c - T~ on the bottom face (Eq. that-bc-d), discretised by IGA
+ * (Section 2.3) and advanced by the theta-scheme (Eq. theta-method).
+ *
+ * Conventions for every call:
+ *  - Units are SI (m, s, W, J, K).
+ *  - Every call returns an sa_status; nothing throws across the ABI.
+ *  - Input buffers passed by the caller are copied during the call; the
+ *    caller keeps ownership.  Output buffers are caller-allocated.
+ *  - The library owns all device memory of a context and frees it in
+ *    sa_destroy.  Device buffers are allocated during set-up
+ *    (sa_create_patch, sa_set_scan, the first sa_step), never per step.
+ *  - Work runs asynchronously on the stream given in sa_options (NULL = the
+ *    legacy default stream) unless a call says otherwise.
+ *  - After SA_ERR_CUDA the context is poisoned: every later call returns
+ *    SA_ERR_STATE except sa_destroy and sa_last_error.
+ *  - Calls out of order (a step before patch, material and scan) return
+ *    SA_ERR_STATE.
+ *  - sa_last_error(ctx) gives a one-line message for the last failure.
+ */
+#ifndef SA_H
+#define SA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sa_ctx sa_ctx;
+
+typedef enum sa_status {
+    SA_OK = 0,
+    SA_ERR_ARG = 1,            /* invalid argument (NULL, size, range, NaN) */
+    SA_ERR_GEOMETRY = 2,       /* invalid knots / weights / degenerate Jacobian */
+    SA_ERR_STATE = 3,          /* call out of order, or context poisoned */
+    SA_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    SA_ERR_OOM = 5,            /* device allocation failed */
+    SA_ERR_NOT_CONVERGED = 6,  /* PCG hit pcg_max_iter before pcg_tol */
+    SA_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    SA_ERR_NAN = 8             /* a non-finite value appeared in the state */
+} sa_status;
+
+/* Precision of the history sum (the only stage whose precision changes). */
+enum { SA_FP64 = 0,   /* every stage in FP64                                       */
+       SA_MIXED = 1   /* history sum in FP32 with ages relative to the current
+                         step, chunked Kahan-compensated accumulation and an FP64
+                         total; assembly, boundary integrals, PCG stay FP64        */ };
+
+/* Face ids: 0 xi=0, 1 xi=1, 2 eta=0, 3 eta=1, 4 zeta=0, 5 zeta=1. */
+enum { SA_FACE_NONE = 0,       /* no boundary term (top face, Section 2.1)      */
+       SA_FACE_NEUMANN = 1,    /* lateral face: F_i = int (-q_N) N_i dS          */
+       SA_FACE_DIRICHLET = 2   /* bottom face: T^ = T_c - T~ (L2 projection)     */ };
+
+typedef struct sa_options {
+    int precision;             /* SA_FP64 (default) or SA_MIXED                   */
+    double pcg_tol;            /* stop when ||r||_2 <= pcg_tol ||b||_2; 1e-10     */
+    int pcg_max_iter;          /* per solve; default 2000                         */
+    double half_space_factor;  /* s_img multiplying every point source; default 2
+                                  (image across the adiabatic top plane); 1 gives
+                                  the printed full-space kernel                   */
+    void* cuda_stream;         /* cudaStream_t to run on, NULL = default stream   */
+    int use_graph;             /* 1: each sa_step replays one captured CUDA graph */
+    int device;                /* CUDA device ordinal; -1 = the current device   */
+    int hist_points_per_lane;  /* history-sum tile: points per lane (1,2,4); 0=auto*/
+    int hist_warps;            /* history-sum tile: warps splitting the sources (4,8); 0=auto */
+} sa_options;
+
+/* Fill o with the defaults listed above. */
+void sa_options_default(sa_options* o);
+
+/* Create an empty context on the chosen device.  o may be NULL (defaults). */
+sa_status sa_create(const sa_options* o, sa_ctx** out);
+
+/*
+ * Geometry: one trivariate NURBS patch (Section 2.3, the map Phi and the
+ * basis of degree p on the knot vectors).
+ *   degree[d]   polynomial degree in parametric direction d (1..4)
+ *   n_ctrl[d]   control points in direction d
+ *   ctrl_xyz    n_ctrl[0]*n_ctrl[1]*n_ctrl[2]*3 doubles (host), index
+ *               ((k*n1 + j)*n0 + i)*3 + c, xi index i fastest
+ *   weights     same count without the *3, > 0; NULL = B-spline (all 1)
+ *   knots[d]    n_knots[d] = n_ctrl[d] + degree[d] + 1 nondecreasing values,
+ *               open (first and last value repeated degree+1 times)
+ * The top face (zeta = 1) must be the plane z = const: the point sources
+ * lie on it.  Set-up (on the device): element and face Gauss points
+ * ((p+1) per direction), the assembly of M and K in CSR form and the
+ * boundary weight matrices.  Errors: SA_ERR_ARG, SA_ERR_GEOMETRY
+ * (non-open or decreasing knots, weights <= 0, non-planar top, det J <= 0 at
+ * a Gauss point), SA_ERR_OOM, SA_ERR_CUDA.
+ */
+sa_status sa_create_patch(sa_ctx* ctx, const int degree[3], const int n_ctrl[3],
+                          const double* ctrl_xyz, const double* weights,
+                          const double* const knots[3], const int n_knots[3]);
+
+/* Face kinds (SA_FACE_*), face ids as above.  Default: faces 0-3 NEUMANN,
+ * face 4 DIRICHLET, face 5 NONE.  Must be called before sa_create_patch to
+ * take effect on set-up; SA_ERR_STATE afterwards. */
+sa_status sa_set_boundary(sa_ctx* ctx, const int face_kind[6]);
+
+/* Material (Section 2, Eq. linear-heat: alpha = k/(rho c_p)) and the
+ * platform / initial temperature T_c (Section 2: T(x,0) = T_c).  All > 0
+ * except T_c (any finite value). */
+sa_status sa_set_material(sa_ctx* ctx, double k, double rho, double cp, double T_c);
+
+/*
+ * Scan (Section 2): the laser moves along a polyline on the top plane.
+ *   path_xyz  nv*3 doubles (host), vertex coordinates; z is ignored (the
+ *             sources are put on the top plane)
+ *   seg_on    nv-1 flags: 1 laser on, 0 a jump that takes no time and adds
+ *             no source; NULL = all on
+ * A maximal run of laser-on segments is a track.  Along each track, sources
+ * sit at arc lengths 0, v*dt, 2 v*dt, ... (dt of the first sa_step); source
+ * I (1-based, in scan order) carries E = A P dt and is active from step I on
+ * (Section 2 and 3.1).  spot_radius r enters through tau = t - r^2/(8 alpha)
+ * (Eq. semi-temperature).  Errors: SA_ERR_ARG.
+ */
+sa_status sa_set_scan(sa_ctx* ctx, const double* path_xyz, int nv,
+                      const unsigned char* seg_on, double power, double absorptivity,
+                      double speed, double spot_radius);
+
+typedef struct sa_step_stats {
+    int steps_done;            /* steps completed in this call                     */
+    int pcg_iters_last;        /* PCG iterations of the last step                  */
+    int pcg_iters_total;       /* summed over the steps of this call               */
+    int pcg_iters_max;
+    int bot_iters_total;       /* iterations of the bottom (Dirichlet) projection  */
+    double rel_res_last;       /* ||r||/||b|| at exit of the last step's PCG       */
+    int n_active_sources;      /* sources in the sum at the last step              */
+    long long step_index;      /* n after the call                                 */
+} sa_step_stats;
+
+/*
+ * Advance the correction field n_steps theta-steps of size dt (Eq.
+ * theta-method, theta in [0, 1]).  Per step n -> n+1: point-source history
+ * sums at the boundary quadrature points, F^{n+1} and the bottom projection,
+ * the theta right-hand side, PCG (Jacobi) from x0 = T^^n.  dt must stay the
+ * same for the life of a scan (the source spacing is v*dt); a change returns
+ * SA_ERR_ARG.  theta may change between calls (the operator is rebuilt).
+ * stats may be NULL: the call then returns after enqueueing the work (errors
+ * of the device-side solves are reported by the next call that synchronises).
+ * With stats != NULL the call synchronises the stream and returns
+ * SA_ERR_NOT_CONVERGED / SA_ERR_TIMEOUT / SA_ERR_NAN when a step failed.
+ */
+sa_status sa_step(sa_ctx* ctx, double theta, double dt, int n_steps, sa_step_stats* stats);
+
+/*
+ * Reconstruction T = T~ + T^ (Section 2.4) at n physical points at the
+ * current step t_n = n dt: point inversion x -> xi by Newton's method on the
+ * NURBS map, sum_i R_i(xi) T^_i, plus the history sum at t_n (FP64).
+ *   pts    n*3 doubles, host (on_device = 0) or device (on_device = 1)
+ *   T_out  n doubles, same memory space; a point outside the patch gets NaN
+ * Synchronous.  Errors: SA_ERR_ARG, SA_ERR_STATE, SA_ERR_CUDA.
+ */
+sa_status sa_eval_T(sa_ctx* ctx, const double* pts, int n, double* T_out, int on_device);
+
+/* Sizes of a context after set-up. */
+typedef struct sa_sizes {
+    int n_dof, n_free, n_dir;      /* control variables; free / Dirichlet             */
+    int q_lat, q_bot;              /* lateral / bottom quadrature points              */
+    int n_src;                     /* discretised sources (0 before the first step)   */
+    long long nnz_mk;              /* nonzeros of the M, K rows of free control vars. */
+    long long nnz_a;               /* nonzeros of the free-free operator              */
+    long long step_index;          /* current n                                       */
+    int n_elem;                    /* volume elements                                 */
+} sa_sizes;
+sa_status sa_get_sizes(sa_ctx* ctx, sa_sizes* out);
+
+/* Fields that can be read back (synchronous copy to host or device memory).
+ * Indices are NATURAL control-point order ((k*n1 + j)*n0 + i) for dof vectors
+ * and the canonical quadrature order for point vectors: faces in increasing
+ * id, face elements with the lower tangential direction fastest, then the
+ * Gauss points of each face element with the lower tangential direction
+ * fastest. */
+enum { SA_FIELD_THAT = 0,      /* T^ at control variables (n_dof)                    */
+       SA_FIELD_F = 1,         /* F^n at control variables (n_dof)                   */
+       SA_FIELD_DTDN_LAT = 2,  /* dT~/dn at lateral points, last step (q_lat)        */
+       SA_FIELD_TT_BOT = 3,    /* T~ at bottom points, last step (q_bot)             */
+       SA_FIELD_LAT_X = 4,     /* lateral points: x,y,z,nx,ny,nz,wdS (q_lat*7)       */
+       SA_FIELD_BOT_X = 5      /* bottom points: x,y,z,wdS (q_bot*4)                 */ };
+sa_status sa_get_field(sa_ctx* ctx, int field, double* out, long long count, int on_device);
+
+/* Assembled matrices in natural order, CSR over ALL control variables:
+ * which = 0 mass M, 1 conductivity K.  rowptr: n_dof+1, colind and vals:
+ * nnz (from sa_get_matrix_nnz).  Host buffers. */
+sa_status sa_get_matrix_nnz(sa_ctx* ctx, long long* nnz);
+sa_status sa_get_matrix(sa_ctx* ctx, int which, long long* rowptr, int* colind, double* vals);
+
+/* Checkpoint: the state is (n, T^ (n_dof, natural order), F^n (n_dof)).  The
+ * sources are recomputed from the scan.  Host buffers; synchronous. */
+sa_status sa_get_state(sa_ctx* ctx, long long* n, double* T_hat, double* F);
+sa_status sa_set_state(sa_ctx* ctx, long long n, const double* T_hat, const double* F);
+
+void sa_destroy(sa_ctx* ctx);
+const char* sa_status_str(sa_status s);
+const char* sa_last_error(const sa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SA_H */

@@ -1,0 +1,232 @@
+"""ctypes binding of libsa (include/sa.h): argument marshalling only.
+
+Functions keep the C names.  Host arrays are numpy float64/int32/uint8;
+device arrays are anything with ``data_ptr()`` (torch tensors) and are
+passed with ``on_device=1``.  A non-zero status raises ``SAError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsa.so")
+
+SA_OK, SA_ERR_ARG, SA_ERR_GEOMETRY, SA_ERR_STATE, SA_ERR_CUDA, SA_ERR_OOM, \
+    SA_ERR_NOT_CONVERGED, SA_ERR_TIMEOUT, SA_ERR_NAN = range(9)
+SA_FP64, SA_MIXED = 0, 1
+SA_FACE_NONE, SA_FACE_NEUMANN, SA_FACE_DIRICHLET = 0, 1, 2
+SA_FIELD_THAT, SA_FIELD_F, SA_FIELD_DTDN_LAT, SA_FIELD_TT_BOT, SA_FIELD_LAT_X, SA_FIELD_BOT_X = range(6)
+
+
+class sa_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("pcg_tol", C.c_double), ("pcg_max_iter", C.c_int),
+                ("half_space_factor", C.c_double), ("cuda_stream", C.c_void_p),
+                ("use_graph", C.c_int), ("device", C.c_int),
+                ("hist_points_per_lane", C.c_int), ("hist_warps", C.c_int)]
+
+
+class sa_step_stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int), ("pcg_iters_last", C.c_int),
+                ("pcg_iters_total", C.c_int), ("pcg_iters_max", C.c_int),
+                ("bot_iters_total", C.c_int), ("rel_res_last", C.c_double),
+                ("n_active_sources", C.c_int), ("step_index", C.c_longlong)]
+
+
+class sa_sizes(C.Structure):
+    _fields_ = [("n_dof", C.c_int), ("n_free", C.c_int), ("n_dir", C.c_int),
+                ("q_lat", C.c_int), ("q_bot", C.c_int), ("n_src", C.c_int),
+                ("nnz_mk", C.c_longlong), ("nnz_a", C.c_longlong),
+                ("step_index", C.c_longlong), ("n_elem", C.c_int)]
+
+
+class SAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsa.so not built ({LIB_PATH}); run "
+                          "`python -m paper_2511_20432_gb300.build` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, LL, V = C.c_void_p, C.c_int, C.c_double, C.c_longlong, None
+    sig = {
+        "sa_options_default": (V, [C.POINTER(sa_options)]),
+        "sa_create": (I, [C.POINTER(sa_options), C.POINTER(P)]),
+        "sa_create_patch": (I, [P, P, P, P, P, P, P]),
+        "sa_set_boundary": (I, [P, P]),
+        "sa_set_material": (I, [P, D, D, D, D]),
+        "sa_set_scan": (I, [P, P, I, P, D, D, D, D]),
+        "sa_step": (I, [P, D, D, I, C.POINTER(sa_step_stats)]),
+        "sa_eval_T": (I, [P, P, I, P, I]),
+        "sa_get_sizes": (I, [P, C.POINTER(sa_sizes)]),
+        "sa_get_field": (I, [P, I, P, LL, I]),
+        "sa_get_matrix_nnz": (I, [P, C.POINTER(LL)]),
+        "sa_get_matrix": (I, [P, I, P, P, P]),
+        "sa_get_state": (I, [P, C.POINTER(LL), P, P]),
+        "sa_set_state": (I, [P, LL, P, P]),
+        "sa_destroy": (V, [P]),
+        "sa_status_str": (C.c_char_p, [I]),
+        "sa_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_name(s):
+    return lib.sa_status_str(int(s)).decode()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, status):
+    if status != SA_OK:
+        msg = lib.sa_last_error(ctx).decode() if ctx else ""
+        raise SAError(status, msg)
+
+
+def options(**kw) -> sa_options:
+    o = sa_options()
+    lib.sa_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = int(v.cuda_stream)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owns one sa_ctx.  Every method is one C call."""
+
+    def __init__(self, opts: sa_options | None = None, **kw):
+        self.ptr = C.c_void_p()
+        o = opts if opts is not None else options(**kw)
+        self._opts = o
+        _check(None, lib.sa_create(C.byref(o), C.byref(self.ptr)))
+
+    def close(self):
+        if self.ptr:
+            lib.sa_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- set-up -------------------------------------------------------------
+    def set_boundary(self, face_kind):
+        fk = np.ascontiguousarray(face_kind, dtype=np.int32)
+        _check(self.ptr, lib.sa_set_boundary(self.ptr, _ptr(fk)))
+
+    def create_patch(self, degree, n_ctrl, ctrl_xyz, weights, knots):
+        deg = np.ascontiguousarray(degree, dtype=np.int32)
+        nc = np.ascontiguousarray(n_ctrl, dtype=np.int32)
+        ctrl = np.ascontiguousarray(ctrl_xyz, dtype=np.float64)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+        ks = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        kp = (C.c_void_p * 3)(*[k.ctypes.data for k in ks])
+        nk = np.array([len(k) for k in ks], dtype=np.int32)
+        _check(self.ptr, lib.sa_create_patch(self.ptr, _ptr(deg), _ptr(nc), _ptr(ctrl), _ptr(w),
+                                             C.cast(kp, C.c_void_p), _ptr(nk)))
+
+    def set_material(self, k, rho, cp, T_c):
+        _check(self.ptr, lib.sa_set_material(self.ptr, k, rho, cp, T_c))
+
+    def set_scan(self, path_xyz, seg_on, power, absorptivity, speed, spot_radius):
+        path = np.ascontiguousarray(path_xyz, dtype=np.float64)
+        on = None if seg_on is None else np.ascontiguousarray(seg_on, dtype=np.uint8)
+        _check(self.ptr, lib.sa_set_scan(self.ptr, _ptr(path), int(path.shape[0]), _ptr(on),
+                                         power, absorptivity, speed, spot_radius))
+
+    # ---- stepping ---------------------------------------------------------------
+    def step(self, theta, dt, n_steps=1, stats=True):
+        st = sa_step_stats() if stats else None
+        _check(self.ptr, lib.sa_step(self.ptr, theta, dt, int(n_steps),
+                                     C.byref(st) if st is not None else None))
+        return st
+
+    def eval_T(self, pts, out=None, on_device=False):
+        if on_device:
+            n = pts.shape[0]
+            _check(self.ptr, lib.sa_eval_T(self.ptr, _ptr(pts), int(n), _ptr(out), 1))
+            return out
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        o = np.empty(p.shape[0])
+        _check(self.ptr, lib.sa_eval_T(self.ptr, _ptr(p), int(p.shape[0]), _ptr(o), 0))
+        return o
+
+    # ---- read-back --------------------------------------------------------------
+    def sizes(self) -> sa_sizes:
+        s = sa_sizes()
+        _check(self.ptr, lib.sa_get_sizes(self.ptr, C.byref(s)))
+        return s
+
+    def field(self, which, count=None):
+        s = self.sizes()
+        n = {SA_FIELD_THAT: s.n_dof, SA_FIELD_F: s.n_dof, SA_FIELD_DTDN_LAT: s.q_lat,
+             SA_FIELD_TT_BOT: s.q_bot, SA_FIELD_LAT_X: 7 * s.q_lat,
+             SA_FIELD_BOT_X: 4 * s.q_bot}[which] if count is None else count
+        o = np.empty(max(n, 1))
+        _check(self.ptr, lib.sa_get_field(self.ptr, int(which), _ptr(o), int(n), 0))
+        return o[:n]
+
+    def matrix(self, which):
+        nnz = C.c_longlong()
+        _check(self.ptr, lib.sa_get_matrix_nnz(self.ptr, C.byref(nnz)))
+        n = self.sizes().n_dof
+        ptr = np.empty(n + 1, dtype=np.int64)
+        col = np.empty(nnz.value, dtype=np.int32)
+        val = np.empty(nnz.value)
+        _check(self.ptr, lib.sa_get_matrix(self.ptr, int(which), _ptr(ptr), _ptr(col), _ptr(val)))
+        return ptr, col, val
+
+    def get_state(self):
+        n = self.sizes().n_dof
+        T = np.empty(n)
+        F = np.empty(n)
+        k = C.c_longlong()
+        _check(self.ptr, lib.sa_get_state(self.ptr, C.byref(k), _ptr(T), _ptr(F)))
+        return k.value, T, F
+
+    def set_state(self, n, T, F):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        _check(self.ptr, lib.sa_set_state(self.ptr, int(n), _ptr(T), _ptr(F)))
+
+
+def context_from_workload(wl, precision=SA_FP64, s_img=2.0, **opts):
+    """Build a Context from a workloads.Workload description (marshalling)."""
+    ctx = Context(precision=precision, half_space_factor=s_img, **opts)
+    p = wl.patch
+    ctx.set_boundary(p.faces)
+    ctx.create_patch(p.degree, p.n_ctrl, p.ctrl.reshape(-1, 3), None if p.weights is None
+                     else p.weights.ravel(), p.knots)
+    m = wl.material
+    ctx.set_material(m.k, m.rho, m.cp, m.T_c)
+    s = wl.scan
+    ctx.set_scan(s.path, s.seg_on, s.power, s.absorptivity, s.speed, s.spot_radius)
+    return ctx

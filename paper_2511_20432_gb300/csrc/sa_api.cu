@@ -1,0 +1,1058 @@
+// C ABI of libsa: host-side validation, set-up (element lists, CSR
+// patterns, Dirichlet elimination order, scan discretisation) and the
+// per-step launch sequence.  See include/sa.h for the contract of each call.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "sa_internal.h"
+
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+sa_status sa_fail(sa_ctx* c, sa_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+sa_status sa_cuda_fail(sa_ctx* c, cudaError_t e, const char* where) {
+    if (c) {
+        c->poisoned = true;
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return SA_ERR_CUDA;
+}
+
+namespace {
+
+// Gauss-Legendre nodes and weights on [-1, 1] for 1..4 points (closed forms).
+void gauss_legendre(int n, double* x, double* w) {
+    switch (n) {
+        case 1:
+            x[0] = 0.0;
+            w[0] = 2.0;
+            break;
+        case 2:
+            x[0] = -1.0 / std::sqrt(3.0);
+            x[1] = -x[0];
+            w[0] = w[1] = 1.0;
+            break;
+        case 3:
+            x[0] = -std::sqrt(0.6);
+            x[1] = 0.0;
+            x[2] = std::sqrt(0.6);
+            w[0] = w[2] = 5.0 / 9.0;
+            w[1] = 8.0 / 9.0;
+            break;
+        default: {
+            const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+            const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+            const double wa = (18.0 + std::sqrt(30.0)) / 36.0;
+            const double wb = (18.0 - std::sqrt(30.0)) / 36.0;
+            x[0] = -b;
+            x[1] = -a;
+            x[2] = a;
+            x[3] = b;
+            w[0] = wb;
+            w[1] = wa;
+            w[2] = wa;
+            w[3] = wb;
+        }
+    }
+}
+
+bool is_fin(double v) { return std::isfinite(v); }
+
+sa_status check_usable(sa_ctx* c) {
+    if (!c) return SA_ERR_ARG;
+    if (c->poisoned) return sa_fail(c, SA_ERR_STATE, "context poisoned by an earlier CUDA error: %s", c->err.c_str());
+    return SA_OK;
+}
+
+int nat(const sa_ctx* c, int i, int j, int k) { return (k * c->n[1] + j) * c->n[0] + i; }
+
+// Build one CSR (rows given as internal/bottom-local indices) from entries
+// (row, q) listed in point-major order; returns slot of every entry.
+void build_w_csr(int n_rows, const std::vector<int>& erow, const std::vector<int>& ecol,
+                 std::vector<int>& ptr, std::vector<int>& col, std::vector<int>& slot) {
+    ptr.assign(n_rows + 1, 0);
+    for (int r : erow) ptr[r + 1]++;
+    for (int r = 0; r < n_rows; ++r) ptr[r + 1] += ptr[r];
+    col.assign(erow.size(), 0);
+    slot.assign(erow.size(), 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t e = 0; e < erow.size(); ++e) {
+        const int s = fill[erow[e]]++;
+        col[s] = ecol[e];
+        slot[e] = s;
+    }
+}
+
+template <class T>
+cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
+    cudaError_t e = b.alloc(v.size());
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+#define SA_UPLOAD(ctx, buf, vec)                                                              \
+    do {                                                                                      \
+        cudaError_t e__ = upload(buf, vec);                                                   \
+        if (e__ != cudaSuccess) {                                                             \
+            cudaGetLastError();                                                               \
+            return e__ == cudaErrorMemoryAllocation                                           \
+                       ? sa_fail(ctx, SA_ERR_OOM, "allocation of %s failed", #buf)            \
+                       : sa_cuda_fail(ctx, e__, "upload " #buf);                              \
+        }                                                                                     \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+void sa_options_default(sa_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = SA_FP64;
+    o->pcg_tol = 1e-10;
+    o->pcg_max_iter = 2000;
+    o->half_space_factor = 2.0;
+    o->cuda_stream = nullptr;
+    o->use_graph = 0;
+    o->device = -1;
+    o->hist_points_per_lane = 0;
+    o->hist_warps = 0;
+}
+
+const char* sa_status_str(sa_status s) {
+    switch (s) {
+        case SA_OK: return "SA_OK";
+        case SA_ERR_ARG: return "SA_ERR_ARG";
+        case SA_ERR_GEOMETRY: return "SA_ERR_GEOMETRY";
+        case SA_ERR_STATE: return "SA_ERR_STATE";
+        case SA_ERR_CUDA: return "SA_ERR_CUDA";
+        case SA_ERR_OOM: return "SA_ERR_OOM";
+        case SA_ERR_NOT_CONVERGED: return "SA_ERR_NOT_CONVERGED";
+        case SA_ERR_TIMEOUT: return "SA_ERR_TIMEOUT";
+        case SA_ERR_NAN: return "SA_ERR_NAN";
+    }
+    return "SA_ERR_UNKNOWN";
+}
+
+const char* sa_last_error(const sa_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sa_status sa_create(const sa_options* o, sa_ctx** out) {
+    if (!out) return SA_ERR_ARG;
+    *out = nullptr;
+    sa_options opt;
+    if (o)
+        opt = *o;
+    else
+        sa_options_default(&opt);
+    if (opt.precision != SA_FP64 && opt.precision != SA_MIXED) return SA_ERR_ARG;
+    if (!(opt.pcg_tol > 0.0) || opt.pcg_max_iter <= 0) return SA_ERR_ARG;
+    if (!(opt.half_space_factor > 0.0) || !is_fin(opt.half_space_factor)) return SA_ERR_ARG;
+    if (opt.hist_points_per_lane != 0 && opt.hist_points_per_lane != 1 &&
+        opt.hist_points_per_lane != 2 && opt.hist_points_per_lane != 4)
+        return SA_ERR_ARG;
+    if (opt.hist_warps != 0 && opt.hist_warps != 4 && opt.hist_warps != 8) return SA_ERR_ARG;
+    sa_ctx* c = new sa_ctx();
+    c->opt = opt;
+    if (opt.device >= 0) {
+        cudaError_t e = cudaSetDevice(opt.device);
+        if (e != cudaSuccess) {
+            delete c;
+            return SA_ERR_CUDA;
+        }
+    }
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return SA_ERR_CUDA;
+    }
+    c->stream = (cudaStream_t)opt.cuda_stream;
+    if (c->st.alloc(1) != cudaSuccess) {
+        delete c;
+        return SA_ERR_OOM;
+    }
+    if (cudaMemset(c->st.p, 0, sizeof(DevStatus)) != cudaSuccess) {
+        delete c;
+        return SA_ERR_CUDA;
+    }
+    c->hist_P = opt.hist_points_per_lane ? opt.hist_points_per_lane : 4;
+    c->hist_W = opt.hist_warps ? opt.hist_warps : 8;
+    *out = c;
+    return SA_OK;
+}
+
+void sa_destroy(sa_ctx* c) {
+    if (!c) return;
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    delete c;
+}
+
+sa_status sa_set_boundary(sa_ctx* c, const int face_kind[6]) {
+    sa_status s = check_usable(c);
+    if (s) return s;
+    if (!face_kind) return sa_fail(c, SA_ERR_ARG, "face_kind is NULL");
+    if (c->has_patch) return sa_fail(c, SA_ERR_STATE, "sa_set_boundary after sa_create_patch");
+    for (int f = 0; f < 6; ++f)
+        if (face_kind[f] < SA_FACE_NONE || face_kind[f] > SA_FACE_DIRICHLET)
+            return sa_fail(c, SA_ERR_ARG, "face_kind[%d] = %d", f, face_kind[f]);
+    std::memcpy(c->face_kind, face_kind, sizeof(c->face_kind));
+    return SA_OK;
+}
+
+sa_status sa_set_material(sa_ctx* c, double k, double rho, double cp, double T_c) {
+    sa_status s = check_usable(c);
+    if (s) return s;
+    if (!(k > 0) || !(rho > 0) || !(cp > 0) || !is_fin(k) || !is_fin(rho) || !is_fin(cp) ||
+        !is_fin(T_c))
+        return sa_fail(c, SA_ERR_ARG, "material k=%g rho=%g cp=%g T_c=%g", k, rho, cp, T_c);
+    if (c->has_material && c->n_step > 0 && (k != c->k || rho != c->rho || cp != c->cp))
+        return sa_fail(c, SA_ERR_STATE, "material changed after stepping");
+    c->k = k;
+    c->rho = rho;
+    c->cp = cp;
+    c->Tc = T_c;
+    c->has_material = true;
+    c->op_theta = -1;   // operator depends on rho c_p and k
+    return SA_OK;
+}
+
+sa_status sa_set_scan(sa_ctx* c, const double* path_xyz, int nv, const unsigned char* seg_on,
+                      double power, double absorptivity, double speed, double spot_radius) {
+    sa_status s = check_usable(c);
+    if (s) return s;
+    if (!path_xyz || nv < 2) return sa_fail(c, SA_ERR_ARG, "scan needs at least 2 vertices");
+    if (!(power >= 0) || !(absorptivity >= 0) || !(speed > 0) || !(spot_radius > 0) ||
+        !is_fin(power) || !is_fin(absorptivity) || !is_fin(speed) || !is_fin(spot_radius))
+        return sa_fail(c, SA_ERR_ARG, "scan parameters P=%g A=%g v=%g r=%g", power, absorptivity,
+                       speed, spot_radius);
+    for (int i = 0; i < 3 * nv; ++i)
+        if (!is_fin(path_xyz[i])) return sa_fail(c, SA_ERR_ARG, "non-finite path vertex");
+    if (c->n_step > 0) return sa_fail(c, SA_ERR_STATE, "sa_set_scan after stepping");
+    c->path.assign(path_xyz, path_xyz + 3 * nv);
+    c->seg_on.assign(nv - 1, 1);
+    if (seg_on)
+        for (int i = 0; i < nv - 1; ++i) c->seg_on[i] = seg_on[i] ? 1 : 0;
+    c->power = power;
+    c->absorptivity = absorptivity;
+    c->speed = speed;
+    c->spot_radius = spot_radius;
+    c->has_scan = true;
+    c->src_dt = 0;
+    c->n_src = 0;
+    return SA_OK;
+}
+
+sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
+                          const double* ctrl_xyz, const double* weights,
+                          const double* const knots[3], const int n_knots[3]) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (c->has_patch) return sa_fail(c, SA_ERR_STATE, "patch already created");
+    if (!degree || !n_ctrl || !ctrl_xyz || !knots || !n_knots)
+        return sa_fail(c, SA_ERR_ARG, "NULL argument");
+    // ---- validation ------------------------------------------------------
+    for (int d = 0; d < 3; ++d) {
+        if (degree[d] < 1 || degree[d] > SA_MAX_DEGREE)
+            return sa_fail(c, SA_ERR_ARG, "degree[%d] = %d (supported 1..%d)", d, degree[d], SA_MAX_DEGREE);
+        if (n_ctrl[d] < degree[d] + 1)
+            return sa_fail(c, SA_ERR_ARG, "n_ctrl[%d] = %d < degree+1", d, n_ctrl[d]);
+        if (n_knots[d] != n_ctrl[d] + degree[d] + 1)
+            return sa_fail(c, SA_ERR_ARG, "n_knots[%d] = %d != n_ctrl + degree + 1", d, n_knots[d]);
+        if (!knots[d]) return sa_fail(c, SA_ERR_ARG, "knots[%d] is NULL", d);
+        const double* U = knots[d];
+        for (int i = 0; i < n_knots[d]; ++i)
+            if (!is_fin(U[i])) return sa_fail(c, SA_ERR_GEOMETRY, "non-finite knot");
+        for (int i = 0; i + 1 < n_knots[d]; ++i)
+            if (U[i + 1] < U[i]) return sa_fail(c, SA_ERR_GEOMETRY, "knots[%d] decreasing at %d", d, i);
+        for (int i = 1; i <= degree[d]; ++i)
+            if (U[i] != U[0] || U[n_knots[d] - 1 - i] != U[n_knots[d] - 1])
+                return sa_fail(c, SA_ERR_GEOMETRY, "knots[%d] not open", d);
+        if (!(U[n_knots[d] - 1] > U[0])) return sa_fail(c, SA_ERR_GEOMETRY, "knots[%d] empty", d);
+        for (int i = 0; i + degree[d] + 1 < n_knots[d]; ++i)
+            if (U[i + degree[d] + 1] == U[i])
+                return sa_fail(c, SA_ERR_GEOMETRY, "knot multiplicity > degree in direction %d", d);
+    }
+    const long long ndof_ll = (long long)n_ctrl[0] * n_ctrl[1] * n_ctrl[2];
+    if (ndof_ll > (1ll << 28)) return sa_fail(c, SA_ERR_ARG, "patch too large");
+    const int ndof = (int)ndof_ll;
+    for (long long i = 0; i < 3 * ndof_ll; ++i)
+        if (!is_fin(ctrl_xyz[i])) return sa_fail(c, SA_ERR_GEOMETRY, "non-finite control point");
+    if (weights)
+        for (int i = 0; i < ndof; ++i)
+            if (!(weights[i] > 0.0) || !is_fin(weights[i]))
+                return sa_fail(c, SA_ERR_GEOMETRY, "weight %d = %g must be > 0", i, weights[i]);
+    // bounding box, top plane
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < ndof; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], ctrl_xyz[3 * i + d]);
+            hi[d] = std::max(hi[d], ctrl_xyz[3 * i + d]);
+        }
+    const double scale = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                   (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    if (!(scale > 0)) return sa_fail(c, SA_ERR_GEOMETRY, "degenerate control net");
+    const int n0 = n_ctrl[0], n1 = n_ctrl[1], n2 = n_ctrl[2];
+    const double zt = ctrl_xyz[3 * ((n2 - 1) * n1 * n0) + 2];
+    for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n0; ++i)
+            if (std::fabs(ctrl_xyz[3 * (((n2 - 1) * n1 + j) * n0 + i) + 2] - zt) > 1e-12 * scale)
+                return sa_fail(c, SA_ERR_GEOMETRY, "top face (zeta = 1) is not a plane z = const");
+
+    // ---- host copy and element lists -----------------------------------------
+    for (int d = 0; d < 3; ++d) {
+        c->p[d] = degree[d];
+        c->n[d] = n_ctrl[d];
+        c->U[d].assign(knots[d], knots[d] + n_knots[d]);
+        c->espan[d].clear();
+        for (int s = degree[d]; s < n_ctrl[d]; ++s)
+            if (c->U[d][s + 1] > c->U[d][s]) c->espan[d].push_back(s);
+        c->ne[d] = (int)c->espan[d].size();
+        // elements touching basis i: spans s with s - p <= i <= s
+        c->elo[d].assign(n_ctrl[d], 0);
+        c->ehi[d].assign(n_ctrl[d], -1);
+        for (int i = 0; i < n_ctrl[d]; ++i) {
+            int first = -1, last = -2;
+            for (int e = 0; e < c->ne[d]; ++e) {
+                const int s = c->espan[d][e];
+                if (s - degree[d] <= i && i <= s) {
+                    if (first < 0) first = e;
+                    last = e;
+                }
+            }
+            c->elo[d][i] = first;
+            c->ehi[d][i] = last;
+        }
+    }
+    c->n_elem = c->ne[0] * c->ne[1] * c->ne[2];
+    c->ctrl.assign(ctrl_xyz, ctrl_xyz + 3 * ndof_ll);
+    c->w.assign(ndof, 1.0);
+    if (weights) c->w.assign(weights, weights + ndof);
+    c->n_dof = ndof;
+    c->z_top = zt;
+    c->x_ref = 0.5 * (lo[0] + hi[0]);
+    c->y_ref = 0.5 * (lo[1] + hi[1]);
+    c->length_scale = scale;
+
+    // ---- Dirichlet control variables and the internal order -----------------
+    std::vector<char> isdir(ndof, 0);
+    for (int f = 0; f < 6; ++f) {
+        if (c->face_kind[f] != SA_FACE_DIRICHLET) continue;
+        const int d = f / 2, side = f % 2;
+        const int layer = side == 0 ? 0 : c->n[d] - 1;   // open knots
+        for (int k = 0; k < n2; ++k)
+            for (int j = 0; j < n1; ++j)
+                for (int i = 0; i < n0; ++i) {
+                    const int idx[3] = {i, j, k};
+                    if (idx[d] == layer) isdir[nat(c, i, j, k)] = 1;
+                }
+    }
+    c->perm.assign(ndof, 0);
+    c->iperm.assign(ndof, 0);
+    int nf = 0;
+    for (int i = 0; i < ndof; ++i)
+        if (!isdir[i]) c->iperm[nf++] = i;
+    c->n_free = nf;
+    int nd = nf;
+    for (int i = 0; i < ndof; ++i)
+        if (isdir[i]) c->iperm[nd++] = i;
+    c->n_dir = ndof - nf;
+    for (int i = 0; i < ndof; ++i) c->perm[c->iperm[i]] = i;
+
+    // ---- upload geometry --------------------------------------------------
+    std::vector<double4> cw(ndof);
+    for (int i = 0; i < ndof; ++i)
+        cw[i] = make_double4(ctrl_xyz[3 * i], ctrl_xyz[3 * i + 1], ctrl_xyz[3 * i + 2], c->w[i]);
+    SA_UPLOAD(c, c->dcw, cw);
+    for (int d = 0; d < 3; ++d) {
+        SA_UPLOAD(c, c->dU[d], c->U[d]);
+        SA_UPLOAD(c, c->despan[d], c->espan[d]);
+    }
+    SA_UPLOAD(c, c->dperm, c->perm);
+    DevPatch& dp = c->dp;
+    for (int d = 0; d < 3; ++d) {
+        dp.p[d] = c->p[d];
+        dp.n[d] = c->n[d];
+        dp.ne[d] = c->ne[d];
+        dp.U[d] = c->dU[d].p;
+        dp.espan[d] = c->despan[d].p;
+    }
+    dp.cw = c->dcw.p;
+    cudaStream_t s = c->stream;
+
+    // ---- boundary quadrature points and weight matrices ------------------------
+    double gx[3][SA_MAX_DEGREE + 1], gw[3][SA_MAX_DEGREE + 1];
+    for (int d = 0; d < 3; ++d) gauss_legendre(c->p[d] + 1, gx[d], gw[d]);
+    for (int kind = SA_FACE_NEUMANN; kind <= SA_FACE_DIRICHLET; ++kind) {
+        const bool lat = kind == SA_FACE_NEUMANN;
+        // enumerate entries (point-major) to build the CSR pattern on the host
+        std::vector<int> erow, ecol;
+        std::vector<int> face_q0, face_e0;
+        int Q = 0;
+        for (int f = 0; f < 6; ++f) {
+            face_q0.push_back(Q);
+            face_e0.push_back((int)erow.size());
+            if (c->face_kind[f] != kind) continue;
+            const int d = f / 2, side = f % 2;
+            const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+            const int nea = c->ne[ta], neb = c->ne[tb];
+            const int nga = c->p[ta] + 1, ngb = c->p[tb] + 1;
+            const int layer = side == 0 ? 0 : c->n[d] - 1;
+            for (int eb = 0; eb < neb; ++eb)
+                for (int ea = 0; ea < nea; ++ea)
+                    for (int g = 0; g < nga * ngb; ++g) {
+                        const int q = Q++;
+                        for (int lb = 0; lb <= c->p[tb]; ++lb)
+                            for (int la = 0; la <= c->p[ta]; ++la) {
+                                int idx[3];
+                                idx[d] = layer;
+                                idx[ta] = c->espan[ta][ea] - c->p[ta] + la;
+                                idx[tb] = c->espan[tb][eb] - c->p[tb] + lb;
+                                const int in = c->perm[nat(c, idx[0], idx[1], idx[2])];
+                                erow.push_back(in);
+                                ecol.push_back(q);
+                            }
+                    }
+        }
+        face_q0.push_back(Q);
+        face_e0.push_back((int)erow.size());
+        std::vector<int> ptr, col, slot;
+        if (lat) {
+            // compact rows: the distinct internal dofs, ascending
+            std::vector<int> rows(erow.begin(), erow.end());
+            std::sort(rows.begin(), rows.end());
+            rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+            std::vector<int> rmap(ndof, -1);
+            for (size_t r = 0; r < rows.size(); ++r) rmap[rows[r]] = (int)r;
+            std::vector<int> er(erow.size());
+            for (size_t e = 0; e < erow.size(); ++e) er[e] = rmap[erow[e]];
+            build_w_csr((int)rows.size(), er, ecol, ptr, col, slot);
+            c->wlat_rows = (int)rows.size();
+            c->q_lat = Q;
+            SA_UPLOAD(c, c->wlat_rowdof, rows);
+            SA_UPLOAD(c, c->wlat_ptr, ptr);
+            SA_UPLOAD(c, c->wlat_col, col);
+            SA_ALLOC(c, c->wlat_val, col.size());
+            SA_ALLOC(c, c->lat64, (size_t)7 * Q);
+        } else {
+            std::vector<int> er(erow.size());
+            for (size_t e = 0; e < erow.size(); ++e) {
+                er[e] = erow[e] - c->n_free;
+                if (er[e] < 0) return sa_fail(c, SA_ERR_GEOMETRY, "Dirichlet face function is not a Dirichlet dof");
+            }
+            build_w_csr(c->n_dir, er, ecol, ptr, col, slot);
+            for (int r = 0; r < c->n_dir; ++r)
+                if (ptr[r + 1] == ptr[r])
+                    return sa_fail(c, SA_ERR_GEOMETRY, "Dirichlet dof without support on a Dirichlet face");
+            c->q_bot = Q;
+            SA_UPLOAD(c, c->wbot_ptr, ptr);
+            SA_UPLOAD(c, c->wbot_col, col);
+            SA_ALLOC(c, c->wbot_val, col.size());
+            SA_ALLOC(c, c->bot64, (size_t)4 * Q);
+        }
+        DBuf<int> dslot;
+        SA_UPLOAD(c, dslot, slot);
+        DBuf<double> cooR;
+        DBuf<int> cooD;
+        if (!lat && Q > 0) {
+            SA_ALLOC(c, cooR, erow.size());
+            SA_ALLOC(c, cooD, erow.size());
+        }
+        for (int f = 0; f < 6; ++f) {
+            if (c->face_kind[f] != kind) continue;
+            const int d = f / 2;
+            const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+            cudaError_t e = launch_face_points(
+                dp, f, 0, 0, c->ne[ta], c->ne[tb], nullptr, gx[ta], gw[ta], gx[tb], gw[tb],
+                face_q0[f], lat ? c->lat64.p : c->bot64.p, Q, lat ? 1 : 0, dslot.p + face_e0[f],
+                lat ? c->wlat_val.p : c->wbot_val.p, lat ? nullptr : cooR.p + face_e0[f],
+                lat ? nullptr : cooD.p + face_e0[f], c->dperm.p, s);
+            if (e != cudaSuccess) return sa_cuda_fail(c, e, "face points");
+        }
+        if (!lat && c->n_dir > 0) {
+            // M_bot pattern: bottom-local dofs sharing a face element
+            std::vector<std::vector<int>> nb(c->n_dir);
+            for (int f = 0; f < 6; ++f) {
+                if (c->face_kind[f] != kind) continue;
+                const int d = f / 2;
+                const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+                const int nfb = (c->p[ta] + 1) * (c->p[tb] + 1);
+                const int npt = (c->p[ta] + 1) * (c->p[tb] + 1);
+                const int nel = c->ne[ta] * c->ne[tb];
+                for (int el = 0; el < nel; ++el) {
+                    const int e0 = face_e0[f] + el * npt * nfb;   // first Gauss point
+                    for (int a = 0; a < nfb; ++a)
+                        for (int b = 0; b < nfb; ++b)
+                            nb[erow[e0 + a] - c->n_free].push_back(erow[e0 + b] - c->n_free);
+                }
+            }
+            std::vector<int> mptr(c->n_dir + 1, 0), mcol;
+            for (int r = 0; r < c->n_dir; ++r) {
+                std::sort(nb[r].begin(), nb[r].end());
+                nb[r].erase(std::unique(nb[r].begin(), nb[r].end()), nb[r].end());
+                mptr[r + 1] = mptr[r] + (int)nb[r].size();
+                mcol.insert(mcol.end(), nb[r].begin(), nb[r].end());
+            }
+            c->nnz_mbot = (long long)mcol.size();
+            SA_UPLOAD(c, c->mbot_ptr, mptr);
+            SA_UPLOAD(c, c->mbot_col, mcol);
+            SA_ALLOC(c, c->mbot_val, mcol.size());
+            SA_ALLOC(c, c->mbot_dinv, c->n_dir);
+            // face functions per point: same count on every Dirichlet face
+            int nfb = -1;
+            for (int f = 0; f < 6; ++f)
+                if (c->face_kind[f] == kind) {
+                    const int d = f / 2;
+                    const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+                    const int v = (c->p[ta] + 1) * (c->p[tb] + 1);
+                    if (nfb >= 0 && v != nfb)
+                        return sa_fail(c, SA_ERR_ARG, "Dirichlet faces with different tangential degrees");
+                    nfb = v;
+                }
+            cudaError_t e = launch_mbot_fill(c->n_dir, c->mbot_ptr.p, c->mbot_col.p, c->wbot_ptr.p,
+                                             c->wbot_col.p, c->wbot_val.p, cooD.p, cooR.p, nfb,
+                                             c->n_free, c->mbot_val.p, c->mbot_dinv.p, s);
+            if (e != cudaSuccess) return sa_cuda_fail(c, e, "M_bot");
+            SA_CUDA(c, cudaStreamSynchronize(s));   // cooR/cooD freed on return
+        }
+        SA_CUDA(c, cudaStreamSynchronize(s));
+    }
+    SA_ALLOC(c, c->lat32, (size_t)6 * c->q_lat);
+    SA_ALLOC(c, c->bot32, (size_t)3 * c->q_bot);
+    {
+        cudaError_t e = launch_points32(c->q_lat, c->q_bot, c->lat64.p, c->bot64.p, c->x_ref,
+                                        c->y_ref, c->z_top, c->lat32.p, c->bot32.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "points32");
+    }
+
+    // ---- CSR pattern of M and K (natural order) ---------------------------------
+    std::vector<std::vector<int>> nbr1[3];
+    for (int d = 0; d < 3; ++d) {
+        nbr1[d].assign(c->n[d], {});
+        for (int i = 0; i < c->n[d]; ++i)
+            for (int j = 0; j < c->n[d]; ++j)
+                if (std::max(c->elo[d][i], c->elo[d][j]) <= std::min(c->ehi[d][i], c->ehi[d][j]))
+                    nbr1[d][i].push_back(j);
+    }
+    std::vector<long long> mk_ptr(ndof + 1, 0);
+    for (int k = 0; k < n2; ++k)
+        for (int j = 0; j < n1; ++j)
+            for (int i = 0; i < n0; ++i)
+                mk_ptr[nat(c, i, j, k) + 1] =
+                    (long long)nbr1[0][i].size() * nbr1[1][j].size() * nbr1[2][k].size();
+    for (int r = 0; r < ndof; ++r) mk_ptr[r + 1] += mk_ptr[r];
+    c->nnz = mk_ptr[ndof];
+    std::vector<int> mk_col(c->nnz);
+    for (int k = 0; k < n2; ++k)
+        for (int j = 0; j < n1; ++j)
+            for (int i = 0; i < n0; ++i) {
+                long long s0 = mk_ptr[nat(c, i, j, k)];
+                for (int kk : nbr1[2][k])
+                    for (int jj : nbr1[1][j])
+                        for (int ii : nbr1[0][i]) mk_col[s0++] = nat(c, ii, jj, kk);
+            }
+    SA_UPLOAD(c, c->mk_ptr, mk_ptr);
+    SA_UPLOAD(c, c->mk_col, mk_col);
+    SA_ALLOC(c, c->M, c->nnz);
+    SA_ALLOC(c, c->K, c->nnz);
+
+    // ---- element matrices (unit rho c_p and k) and their gather -------------------
+    {
+        for (int d = 0; d < 3; ++d) {
+            SA_UPLOAD(c, c->d_elo[d], c->elo[d]);
+            SA_UPLOAD(c, c->d_ehi[d], c->ehi[d]);
+        }
+        const int nloc = (c->p[0] + 1) * (c->p[1] + 1) * (c->p[2] + 1);
+        DBuf<double> Mloc, Kloc;
+        DBuf<int> bad;
+        SA_ALLOC(c, Mloc, (size_t)c->n_elem * nloc * nloc);
+        SA_ALLOC(c, Kloc, (size_t)c->n_elem * nloc * nloc);
+        SA_ALLOC(c, bad, 1);
+        SA_CUDA(c, cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+        double xg[3 * (SA_MAX_DEGREE + 1)], wg[3 * (SA_MAX_DEGREE + 1)];
+        for (int d = 0; d < 3; ++d)
+            for (int g = 0; g <= c->p[d]; ++g) {
+                xg[d * (SA_MAX_DEGREE + 1) + g] = gx[d][g];
+                wg[d * (SA_MAX_DEGREE + 1) + g] = gw[d][g];
+            }
+        cudaError_t e = launch_element_local(dp, 1.0, 1.0, xg, wg, Mloc.p, Kloc.p, bad.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "element matrices");
+        const int* elo[3] = {c->d_elo[0].p, c->d_elo[1].p, c->d_elo[2].p};
+        const int* ehi[3] = {c->d_ehi[0].p, c->d_ehi[1].p, c->d_ehi[2].p};
+        e = launch_mk_gather(dp, c->mk_ptr.p, c->mk_col.p, elo, ehi, Mloc.p, Kloc.p, c->M.p,
+                             c->K.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather M, K");
+        int hbad = 0;
+        SA_CUDA(c, cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SA_CUDA(c, cudaStreamSynchronize(s));
+        if (hbad) return sa_fail(c, SA_ERR_GEOMETRY, "det J <= 0 at a Gauss point (inverted or degenerate patch)");
+    }
+
+    // ---- free-free operator pattern -------------------------------------------------
+    {
+        std::vector<int> a_ptr(c->n_free + 1, 0), a_col, a_src;
+        a_col.reserve((size_t)c->nnz);
+        a_src.reserve((size_t)c->nnz);
+        for (int i = 0; i < c->n_free; ++i) {
+            const int r = c->iperm[i];
+            for (long long t = mk_ptr[r]; t < mk_ptr[r + 1]; ++t) {
+                const int j = c->perm[mk_col[t]];
+                if (j < c->n_free) {
+                    a_col.push_back(j);
+                    a_src.push_back((int)t);
+                }
+            }
+            a_ptr[i + 1] = (int)a_col.size();
+        }
+        if (c->nnz > (long long)INT32_MAX)
+            return sa_fail(c, SA_ERR_ARG, "operator too large for 32-bit slots");
+        c->nnz_a = (long long)a_col.size();
+        SA_UPLOAD(c, c->a_ptr, a_ptr);
+        SA_UPLOAD(c, c->a_col, a_col);
+        SA_UPLOAD(c, c->a_src, a_src);
+        SA_ALLOC(c, c->a_val, c->nnz_a);
+        SA_ALLOC(c, c->a_dinv, c->n_free);
+    }
+
+    // ---- state and work vectors ---------------------------------------------------
+    const int nwork = std::max(std::max(c->n_free, c->n_dir), 1);
+    SA_ALLOC(c, c->That, ndof);
+    SA_ALLOC(c, c->F0, ndof);
+    SA_ALLOC(c, c->F1, ndof);
+    SA_ALLOC(c, c->gnew, std::max(c->n_dir, 1));
+    SA_ALLOC(c, c->bbot, std::max(c->n_dir, 1));
+    SA_ALLOC(c, c->rhs, nwork);
+    SA_ALLOC(c, c->r0, nwork);
+    SA_ALLOC(c, c->wr, nwork);
+    SA_ALLOC(c, c->wz, nwork);
+    SA_ALLOC(c, c->wp0, nwork);
+    SA_ALLOC(c, c->wp1, nwork);
+    SA_ALLOC(c, c->wq, nwork);
+    SA_ALLOC(c, c->s_lat, std::max(c->q_lat, 1));
+    SA_ALLOC(c, c->tt_bot, std::max(c->q_bot, 1));
+    SA_CUDA(c, cudaMemsetAsync(c->F0.p, 0, sizeof(double) * ndof, s));
+    SA_CUDA(c, cudaMemsetAsync(c->F1.p, 0, sizeof(double) * ndof, s));
+    SA_CUDA(c, cudaMemsetAsync(c->s_lat.p, 0, sizeof(double) * std::max(c->q_lat, 1), s));
+    SA_CUDA(c, cudaMemsetAsync(c->tt_bot.p, 0, sizeof(double) * std::max(c->q_bot, 1), s));
+    SA_CUDA(c, cudaMemsetAsync(c->wp0.p, 0, sizeof(double) * nwork, s));
+    SA_CUDA(c, cudaMemsetAsync(c->wp1.p, 0, sizeof(double) * nwork, s));
+    // PCG launch shape: co-resident blocks (cooperative launch)
+    {
+        int occ = 0;
+        SA_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel_ptr(),
+                                                                 pcg_block_size(), 0));
+        if (occ < 1) return sa_fail(c, SA_ERR_CUDA, "PCG kernel cannot be resident");
+        c->pcg_block = pcg_block_size();
+        c->pcg_grid = c->num_sms * std::min(occ, 2);
+        SA_ALLOC(c, c->partials, (size_t)6 * c->pcg_grid);
+    }
+    SA_CUDA(c, cudaStreamSynchronize(s));
+    c->has_patch = true;
+    c->n_step = 0;
+    return SA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// stepping
+// ---------------------------------------------------------------------------
+namespace {
+
+// Scan -> source positions (see sa_set_scan): tracks are maximal runs of
+// laser-on segments; sources at arc lengths 0, v dt, 2 v dt, ... on each.
+void discretize_scan(const sa_ctx* c, double dt, std::vector<double>& xy) {
+    xy.clear();
+    const int nv = (int)c->path.size() / 3;
+    const double step = c->speed * dt;
+    int s = 0;
+    const int nseg = nv - 1;
+    while (s < nseg) {
+        if (!c->seg_on[s]) {
+            ++s;
+            continue;
+        }
+        int e = s;
+        while (e < nseg && c->seg_on[e]) ++e;
+        std::vector<double> cum(1, 0.0), len;
+        for (int k = s; k < e; ++k) {
+            const double* a = &c->path[3 * k];
+            const double* b = &c->path[3 * (k + 1)];
+            const double l = std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) +
+                                       (b[2] - a[2]) * (b[2] - a[2]));
+            len.push_back(l);
+            cum.push_back(cum.back() + l);
+        }
+        const double L = cum.back();
+        const long long count = (long long)std::floor(L / step + 1e-9) + 1;
+        for (long long jj = 0; jj < count; ++jj) {
+            const double arc = std::min(jj * step, L);
+            int k = (int)(std::upper_bound(cum.begin(), cum.end(), arc) - cum.begin()) - 1;
+            k = std::min(std::max(k, 0), (int)len.size() - 1);
+            const double t = len[k] > 0 ? (arc - cum[k]) / len[k] : 0.0;
+            const double* a = &c->path[3 * (s + k)];
+            const double* b = &c->path[3 * (s + k + 1)];
+            xy.push_back(a[0] + t * (b[0] - a[0]));
+            xy.push_back(a[1] + t * (b[1] - a[1]));
+        }
+        s = e;
+    }
+}
+
+sa_status ensure_sources(sa_ctx* c, double dt) {
+    if (c->src_dt != 0.0) {
+        if (dt != c->src_dt)
+            return sa_fail(c, SA_ERR_ARG, "dt %g differs from the dt %g the scan was discretised with", dt, c->src_dt);
+        return SA_OK;
+    }
+    std::vector<double> xy;
+    discretize_scan(c, dt, xy);
+    const int n = (int)(xy.size() / 2);
+    std::vector<double2> pos(std::max(n, 1));
+    for (int i = 0; i < n; ++i) pos[i] = make_double2(xy[2 * i] - c->x_ref, xy[2 * i + 1] - c->y_ref);
+    SA_UPLOAD(c, c->src_pos, pos);
+    const size_t m = std::max(n, 1);
+    SA_ALLOC(c, c->src64T, m);
+    SA_ALLOC(c, c->src64F, m);
+    SA_ALLOC(c, c->src32T, m);
+    SA_ALLOC(c, c->src32F, m);
+    SA_ALLOC(c, c->evT, m);
+    SA_ALLOC(c, c->evF, m);
+    c->n_src = n;
+    c->src_dt = dt;
+    c->E = c->absorptivity * c->power * dt;
+    return SA_OK;
+}
+
+sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
+    if (c->op_dt == dt && c->op_theta == theta) return SA_OK;
+    cudaError_t e = launch_build_A(c->nnz_a, c->a_src.p, c->M.p, c->K.p,
+                                   c->rho * c->cp / dt, theta * c->k, c->a_val.p, c->n_free,
+                                   c->a_ptr.p, c->a_col.p, c->a_dinv.p, c->stream);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "build A");
+    c->op_dt = dt;
+    c->op_theta = theta;
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    return SA_OK;
+}
+
+sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
+    cudaStream_t s = c->stream;
+    const double alpha = c->k / (c->rho * c->cp);
+    cudaError_t e;
+    e = launch_prologue(c->st.p, 0, c->st.p, c->n_src, c->src_pos.p, dt, alpha,
+                        c->spot_radius * c->spot_radius / (8.0 * alpha),
+                        c->opt.half_space_factor * c->E / (c->rho * c->cp), c->opt.precision,
+                        c->opt.precision == SA_FP64 ? c->src64T.p : nullptr,
+                        c->opt.precision == SA_FP64 ? c->src64F.p : nullptr,
+                        c->opt.precision == SA_MIXED ? c->src32T.p : nullptr,
+                        c->opt.precision == SA_MIXED ? c->src32F.p : nullptr, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "prologue");
+    e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat, c->q_bot,
+                       c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p, c->x_ref, c->y_ref,
+                       c->z_top, c->src32F.p, c->src32T.p, c->src64F.p, c->src64T.p,
+                       c->s_lat.p, c->tt_bot.p, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "history");
+    e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
+                      c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
+                      c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
+    if (c->n_dir > 0) {
+        // x0 = g^n (the Dirichlet part of the state)
+        e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
+                            cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
+        const int grid_bot = std::max(1, std::min(c->pcg_grid, (c->n_dir + 255) / 256));
+        e = launch_pcg(1, c->n_dir, c->mbot_ptr.p, c->mbot_col.p, c->mbot_val.p, c->mbot_dinv.p,
+                       c->bbot.p, nullptr, c->gnew.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p,
+                       c->wq.p, c->partials.p, c->st.p, c->opt.pcg_tol,
+                       c->opt.pcg_max_iter, grid_bot, c->pcg_block, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
+    }
+    e = launch_theta_rhs(c->n_free, c->mk_ptr.p, c->mk_col.p, c->M.p, c->K.p, c->dperm.p,
+                         c->d_iperm_free.p, c->That.p, c->gnew.p, c->F0.p, c->F1.p,
+                         c->rho * c->cp / dt, c->k, theta, c->rhs.p, c->r0.p, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
+    e = launch_pcg(0, c->n_free, c->a_ptr.p, c->a_col.p, c->a_val.p, c->a_dinv.p, c->rhs.p,
+                   c->r0.p, c->That.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p, c->wq.p,
+                   c->partials.p, c->st.p, c->opt.pcg_tol, c->opt.pcg_max_iter, c->pcg_grid,
+                   c->pcg_block, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
+    e = launch_finalize(c->n_dir, c->n_free, c->n_dof, c->gnew.p, c->That.p, c->F1.p, c->F0.p,
+                        c->st.p, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "finalize");
+    return SA_OK;
+}
+
+sa_status init_state_if_needed(sa_ctx* c) {
+    if (c->state_init) return SA_OK;
+    std::vector<int> ipf(c->iperm.begin(), c->iperm.begin() + c->n_free);
+    if (ipf.empty()) ipf.assign(1, 0);
+    SA_UPLOAD(c, c->d_iperm_free, ipf);
+    // T^(x, 0) = T_c (Section 2.1): constants are exact in the spline space
+    std::vector<double> T0(c->n_dof, c->Tc);
+    SA_CUDA(c, cudaMemcpy(c->That.p, T0.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
+    c->state_init = true;
+    return SA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats* stats) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!c->has_patch || !c->has_material || !c->has_scan)
+        return sa_fail(c, SA_ERR_STATE, "sa_step needs patch, material and scan");
+    if (!(theta >= 0.0 && theta <= 1.0)) return sa_fail(c, SA_ERR_ARG, "theta %g not in [0, 1]", theta);
+    if (!(dt > 0.0) || !is_fin(dt)) return sa_fail(c, SA_ERR_ARG, "dt %g must be > 0", dt);
+    if (n_steps < 0) return sa_fail(c, SA_ERR_ARG, "n_steps < 0");
+    if ((st = ensure_sources(c, dt))) return st;
+    if ((st = init_state_if_needed(c))) return st;
+    if ((st = ensure_operator(c, theta, dt))) return st;
+    cudaStream_t s = c->stream;
+    if (stats) {
+        // reset the accumulated counters (not n, not the barrier words)
+        DevStatus z;
+        std::memset(&z, 0, sizeof(z));
+        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->err, &z.err, offsetof(DevStatus, n), cudaMemcpyHostToDevice, s));
+        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->iters_total, &z.iters_total,
+                                   offsetof(DevStatus, pad) - offsetof(DevStatus, iters_total),
+                                   cudaMemcpyHostToDevice, s));
+        SA_CUDA(c, cudaStreamSynchronize(s));
+    }
+    const bool graph = c->opt.use_graph && s != nullptr;
+    for (int i = 0; i < n_steps; ++i) {
+        if (graph) {
+            if (!c->graph_exec) {
+                cudaGraph_t g;
+                SA_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                sa_status es = enqueue_step(c, theta, dt);
+                cudaError_t ee = cudaStreamEndCapture(s, &g);
+                if (es) return es;
+                if (ee != cudaSuccess) return sa_cuda_fail(c, ee, "end capture");
+                ee = cudaGraphInstantiate(&c->graph_exec, g, 0);
+                cudaGraphDestroy(g);
+                if (ee != cudaSuccess) return sa_cuda_fail(c, ee, "graph instantiate");
+            }
+            SA_CUDA(c, cudaGraphLaunch(c->graph_exec, s));
+        } else {
+            if ((st = enqueue_step(c, theta, dt))) return st;
+        }
+    }
+    c->n_step += n_steps;
+    if (stats) {
+        DevStatus h;
+        SA_CUDA(c, cudaMemcpyAsync(&h, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        SA_CUDA(c, cudaStreamSynchronize(s));
+        stats->steps_done = n_steps;
+        stats->pcg_iters_last = h.pcg_iters;
+        stats->pcg_iters_total = (int)h.iters_total;
+        stats->pcg_iters_max = h.iters_max;
+        stats->bot_iters_total = (int)h.bot_total;
+        stats->rel_res_last = h.rel_res;
+        stats->n_active_sources = h.n_active;
+        stats->step_index = h.n;
+        if (h.err & SA_DEV_TIMEOUT) return sa_fail(c, SA_ERR_TIMEOUT, "a device-side wait timed out");
+        if (h.err & SA_DEV_NAN) return sa_fail(c, SA_ERR_NAN, "non-finite value in the solve");
+        if (h.err & (SA_DEV_NOT_CONVERGED | SA_DEV_BOT_NOT_CONVERGED))
+            return sa_fail(c, SA_ERR_NOT_CONVERGED, "PCG did not converge (flags %d, rel res %g)", h.err, h.rel_res);
+    }
+    return SA_OK;
+}
+
+sa_status sa_get_sizes(sa_ctx* c, sa_sizes* out) {
+    if (!c || !out) return SA_ERR_ARG;
+    if (!c->has_patch) return sa_fail(c, SA_ERR_STATE, "no patch");
+    out->n_dof = c->n_dof;
+    out->n_free = c->n_free;
+    out->n_dir = c->n_dir;
+    out->q_lat = c->q_lat;
+    out->q_bot = c->q_bot;
+    out->n_src = c->n_src;
+    out->nnz_mk = c->nnz;
+    out->nnz_a = c->nnz_a;
+    out->step_index = c->n_step;
+    out->n_elem = c->n_elem;
+    return SA_OK;
+}
+
+sa_status sa_get_field(sa_ctx* c, int field, double* out, long long count, int on_device) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!out) return sa_fail(c, SA_ERR_ARG, "out is NULL");
+    if (!c->has_patch) return sa_fail(c, SA_ERR_STATE, "no patch");
+    if (c->has_material) {
+        if ((st = init_state_if_needed(c))) return st;
+    }
+    cudaStream_t s = c->stream;
+    std::vector<double> h;
+    long long need = 0;
+    switch (field) {
+        case SA_FIELD_THAT:
+        case SA_FIELD_F: {
+            need = c->n_dof;
+            if (count < need) return sa_fail(c, SA_ERR_ARG, "count %lld < %lld", count, need);
+            std::vector<double> in(c->n_dof);
+            SA_CUDA(c, cudaMemcpyAsync(in.data(), field == SA_FIELD_THAT ? c->That.p : c->F0.p,
+                                       sizeof(double) * c->n_dof, cudaMemcpyDeviceToHost, s));
+            SA_CUDA(c, cudaStreamSynchronize(s));
+            h.resize(c->n_dof);
+            for (int i = 0; i < c->n_dof; ++i) h[i] = in[c->perm[i]];
+            break;
+        }
+        case SA_FIELD_DTDN_LAT:
+        case SA_FIELD_TT_BOT: {
+            need = field == SA_FIELD_DTDN_LAT ? c->q_lat : c->q_bot;
+            if (count < need) return sa_fail(c, SA_ERR_ARG, "count %lld < %lld", count, need);
+            h.resize(need);
+            if (need)
+                SA_CUDA(c, cudaMemcpyAsync(h.data(), field == SA_FIELD_DTDN_LAT ? c->s_lat.p : c->tt_bot.p,
+                                           sizeof(double) * need, cudaMemcpyDeviceToHost, s));
+            SA_CUDA(c, cudaStreamSynchronize(s));
+            break;
+        }
+        case SA_FIELD_LAT_X:
+        case SA_FIELD_BOT_X: {
+            const bool lat = field == SA_FIELD_LAT_X;
+            const int Q = lat ? c->q_lat : c->q_bot;
+            const int nc = lat ? 7 : 4;
+            need = (long long)Q * nc;
+            if (count < need) return sa_fail(c, SA_ERR_ARG, "count %lld < %lld", count, need);
+            std::vector<double> soa(need);
+            if (need)
+                SA_CUDA(c, cudaMemcpyAsync(soa.data(), lat ? c->lat64.p : c->bot64.p,
+                                           sizeof(double) * need, cudaMemcpyDeviceToHost, s));
+            SA_CUDA(c, cudaStreamSynchronize(s));
+            h.resize(need);
+            for (int q = 0; q < Q; ++q)
+                for (int k = 0; k < nc; ++k) h[(size_t)q * nc + k] = soa[(size_t)k * Q + q];
+            break;
+        }
+        default:
+            return sa_fail(c, SA_ERR_ARG, "unknown field %d", field);
+    }
+    if (on_device) {
+        if (need) SA_CUDA(c, cudaMemcpy(out, h.data(), sizeof(double) * need, cudaMemcpyHostToDevice));
+    } else {
+        std::copy(h.begin(), h.end(), out);
+    }
+    return SA_OK;
+}
+
+sa_status sa_get_matrix_nnz(sa_ctx* c, long long* nnz) {
+    if (!c || !nnz) return SA_ERR_ARG;
+    if (!c->has_patch) return sa_fail(c, SA_ERR_STATE, "no patch");
+    *nnz = c->nnz;
+    return SA_OK;
+}
+
+sa_status sa_get_matrix(sa_ctx* c, int which, long long* rowptr, int* colind, double* vals) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!rowptr || !colind || !vals || (which != 0 && which != 1)) return sa_fail(c, SA_ERR_ARG, "bad argument");
+    if (!c->has_patch || !c->has_material) return sa_fail(c, SA_ERR_STATE, "needs patch and material");
+    SA_CUDA(c, cudaStreamSynchronize(c->stream));
+    SA_CUDA(c, cudaMemcpy(rowptr, c->mk_ptr.p, sizeof(long long) * (c->n_dof + 1), cudaMemcpyDeviceToHost));
+    SA_CUDA(c, cudaMemcpy(colind, c->mk_col.p, sizeof(int) * c->nnz, cudaMemcpyDeviceToHost));
+    SA_CUDA(c, cudaMemcpy(vals, which == 0 ? c->M.p : c->K.p, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost));
+    const double f = which == 0 ? c->rho * c->cp : c->k;
+    for (long long i = 0; i < c->nnz; ++i) vals[i] *= f;
+    return SA_OK;
+}
+
+sa_status sa_get_state(sa_ctx* c, long long* n, double* T_hat, double* F) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!n || !T_hat || !F) return sa_fail(c, SA_ERR_ARG, "NULL argument");
+    if (!c->has_patch || !c->has_material) return sa_fail(c, SA_ERR_STATE, "needs patch and material");
+    if ((st = sa_get_field(c, SA_FIELD_THAT, T_hat, c->n_dof, 0))) return st;
+    if ((st = sa_get_field(c, SA_FIELD_F, F, c->n_dof, 0))) return st;
+    *n = c->n_step;
+    return SA_OK;
+}
+
+sa_status sa_set_state(sa_ctx* c, long long n, const double* T_hat, const double* F) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!T_hat || !F || n < 0) return sa_fail(c, SA_ERR_ARG, "bad argument");
+    if (!c->has_patch || !c->has_material) return sa_fail(c, SA_ERR_STATE, "needs patch and material");
+    for (int i = 0; i < c->n_dof; ++i)
+        if (!is_fin(T_hat[i]) || !is_fin(F[i])) return sa_fail(c, SA_ERR_NAN, "non-finite state");
+    if ((st = init_state_if_needed(c))) return st;
+    std::vector<double> Ti(c->n_dof), Fi(c->n_dof);
+    for (int i = 0; i < c->n_dof; ++i) {
+        Ti[c->perm[i]] = T_hat[i];
+        Fi[c->perm[i]] = F[i];
+    }
+    cudaStream_t s = c->stream;
+    SA_CUDA(c, cudaStreamSynchronize(s));
+    SA_CUDA(c, cudaMemcpy(c->That.p, Ti.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
+    SA_CUDA(c, cudaMemcpy(c->F0.p, Fi.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
+    SA_CUDA(c, cudaMemcpy(&c->st.p->n, &n, sizeof(long long), cudaMemcpyHostToDevice));
+    c->n_step = n;
+    return SA_OK;
+}
+
+sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_device) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (n < 0 || (n > 0 && (!pts || !T_out))) return sa_fail(c, SA_ERR_ARG, "bad argument");
+    if (!c->has_patch || !c->has_material) return sa_fail(c, SA_ERR_STATE, "needs patch and material");
+    if (n == 0) return SA_OK;
+    if ((st = init_state_if_needed(c))) return st;
+    cudaStream_t s = c->stream;
+    if (!c->ecent.p) {
+        SA_ALLOC(c, c->ecent, (size_t)3 * c->n_elem);
+        cudaError_t e = launch_elem_centers(c->dp, c->ecent.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "element centres");
+    }
+    int n_active = 0;
+    if (c->has_scan && c->src_dt > 0.0 && c->n_step > 0 && c->n_src > 0) {
+        const double alpha = c->k / (c->rho * c->cp);
+        cudaError_t e = launch_prologue(nullptr, c->n_step, nullptr, c->n_src, c->src_pos.p, c->src_dt,
+                                        alpha, c->spot_radius * c->spot_radius / (8.0 * alpha),
+                                        c->opt.half_space_factor * c->E / (c->rho * c->cp), SA_FP64,
+                                        c->evT.p, c->evF.p, nullptr, nullptr, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "eval prologue");
+        n_active = (int)std::min<long long>(c->n_step, c->n_src);
+    }
+    const double* dpts = pts;
+    double* dout = T_out;
+    if (!on_device) {
+        SA_ALLOC(c, c->eval_pts, (size_t)3 * n);
+        SA_ALLOC(c, c->eval_out, (size_t)n);
+        SA_CUDA(c, cudaMemcpyAsync(c->eval_pts.p, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        dpts = c->eval_pts.p;
+        dout = c->eval_out.p;
+    }
+    cudaError_t e = launch_eval_points(c->dp, dpts, n, c->ecent.p, c->dperm.p, c->That.p,
+                                       c->evT.p, n_active, c->x_ref, c->y_ref, c->z_top,
+                                       c->length_scale, dout, s);
+    if (e != cudaSuccess) return sa_cuda_fail(c, e, "eval");
+    if (!on_device)
+        SA_CUDA(c, cudaMemcpyAsync(T_out, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    SA_CUDA(c, cudaStreamSynchronize(s));
+    return SA_OK;
+}
+
+}  // extern "C"

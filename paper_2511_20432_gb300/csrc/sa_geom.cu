@@ -1,0 +1,673 @@
+// One-time set-up kernels: NURBS basis by Cox-de Boor, boundary quadrature
+// points with normals and weights, element matrices and their deterministic
+// gather into CSR (Section 2.3: the map Phi, grad_x N = J^{-T} grad_xi N,
+// dV = det J dxi, and the integrals M_ij, K_ij, F_i).
+#include "sa_internal.h"
+
+namespace {
+
+// Non-zero B-spline values N[0..p] = N_{s-p..s, p}(u) and their first
+// derivatives on the knot span s (U[s] <= u < U[s+1], or u = U[s+1] at the
+// right end), by the triangular Cox-de Boor recursion: degree q is built
+// from degree q-1, N_{i,q} = (u-U_i)/(U_{i+q}-U_i) N_{i,q-1}
+// + (U_{i+q+1}-u)/(U_{i+q+1}-U_{i+1}) N_{i+1,q-1}; the derivative of degree
+// p uses the degree p-1 values.  No denominator vanishes on a non-empty span.
+__device__ void bspline_1d(const double* U, int p, int s, double u, double* N, double* dN) {
+    double cur[SA_MAX_DEGREE + 1], prev[SA_MAX_DEGREE + 1];
+    cur[0] = 1.0;
+    for (int q = 1; q <= p; ++q) {
+        for (int r = 0; r < q; ++r) prev[r] = cur[r];
+        for (int r = 0; r <= q; ++r) {
+            const int i = s - q + r;
+            double v = 0.0;
+            if (r > 0) v += (u - U[i]) / (U[i + q] - U[i]) * prev[r - 1];
+            if (r < q) v += (U[i + q + 1] - u) / (U[i + q + 1] - U[i + 1]) * prev[r];
+            cur[r] = v;
+        }
+    }
+    // here prev holds degree p-1 (if p >= 1)
+    for (int r = 0; r <= p; ++r) {
+        N[r] = cur[r];
+        if (p == 0) {
+            dN[r] = 0.0;
+            continue;
+        }
+        const int i = s - p + r;
+        double d = 0.0;
+        if (r > 0) d += p / (U[i + p] - U[i]) * prev[r - 1];
+        if (r < p) d -= p / (U[i + p + 1] - U[i + 1]) * prev[r];
+        dN[r] = d;
+    }
+}
+
+struct Basis1D {
+    double N[3][SA_MAX_DEGREE + 1];
+    double dN[3][SA_MAX_DEGREE + 1];
+    int s[3];
+};
+
+__device__ inline int nat_index(const DevPatch& dp, int i, int j, int k) {
+    return (k * dp.n[1] + j) * dp.n[0] + i;
+}
+
+// NURBS geometry at one parametric point: first pass (weights W, dW and the
+// Jacobian J[c][d] = d x_c / d xi_d through the quotient rule).
+__device__ void nurbs_point(const DevPatch& dp, const Basis1D& b, double x[3], double J[3][3],
+                            double& Wsum, double dW[3]) {
+    Wsum = 0.0;
+    dW[0] = dW[1] = dW[2] = 0.0;
+    double xw[3] = {0, 0, 0};
+    double dxw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+        for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+            for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                const int gi = b.s[0] - dp.p[0] + a0, gj = b.s[1] - dp.p[1] + a1,
+                          gk = b.s[2] - dp.p[2] + a2;
+                const double4 c = dp.cw[nat_index(dp, gi, gj, gk)];
+                const double Nv = b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
+                const double d0 = b.dN[0][a0] * b.N[1][a1] * b.N[2][a2];
+                const double d1 = b.N[0][a0] * b.dN[1][a1] * b.N[2][a2];
+                const double d2 = b.N[0][a0] * b.N[1][a1] * b.dN[2][a2];
+                const double wN = c.w * Nv;
+                Wsum += wN;
+                dW[0] += c.w * d0;
+                dW[1] += c.w * d1;
+                dW[2] += c.w * d2;
+                const double P[3] = {c.x, c.y, c.z};
+                for (int cc = 0; cc < 3; ++cc) {
+                    xw[cc] += wN * P[cc];
+                    dxw[cc][0] += c.w * d0 * P[cc];
+                    dxw[cc][1] += c.w * d1 * P[cc];
+                    dxw[cc][2] += c.w * d2 * P[cc];
+                }
+            }
+    // x = xw / W ;  dx/dxi = (dxw W - xw dW) / W^2
+    for (int cc = 0; cc < 3; ++cc) {
+        x[cc] = xw[cc] / Wsum;
+        for (int d = 0; d < 3; ++d) J[cc][d] = (dxw[cc][d] - x[cc] * dW[d]) / Wsum;
+    }
+}
+
+__device__ inline double det3(const double J[3][3]) {
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// ---------------------------------------------------------------------------
+// boundary quadrature points of one face
+// ---------------------------------------------------------------------------
+struct FaceArgs {
+    DevPatch dp;
+    int d, side, ta, tb;       // fixed direction, side, tangential directions
+    int nea, neb, nga, ngb;
+    double xg_a[SA_MAX_DEGREE + 1], wg_a[SA_MAX_DEGREE + 1];
+    double xg_b[SA_MAX_DEGREE + 1], wg_b[SA_MAX_DEGREE + 1];
+    int q_offset, q_stride, with_normal;
+    double* pts64;             // SoA with stride q_stride
+    const int* slot;           // (face point, face function) -> CSR slot of W
+    double* w_val;
+    double* coo_R;             // optional: per point, face-function values
+    int* coo_dof;              // optional: per point, internal dof of face functions
+    const int* perm;
+};
+
+__global__ void k_face_points(FaceArgs a) {
+    const int nq = a.nea * a.neb * a.nga * a.ngb;
+    const int qf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qf >= nq) return;
+    const DevPatch& dp = a.dp;
+    int t = qf;
+    const int ga = t % a.nga; t /= a.nga;
+    const int gb = t % a.ngb; t /= a.ngb;
+    const int ea = t % a.nea; t /= a.nea;
+    const int eb = t;
+    Basis1D b;
+    double xi[3];
+    const int sa = dp.espan[a.ta][ea], sb = dp.espan[a.tb][eb];
+    {
+        const double lo = dp.U[a.ta][sa], hi = dp.U[a.ta][sa + 1];
+        xi[a.ta] = lo + 0.5 * (hi - lo) * (a.xg_a[ga] + 1.0);
+    }
+    {
+        const double lo = dp.U[a.tb][sb], hi = dp.U[a.tb][sb + 1];
+        xi[a.tb] = lo + 0.5 * (hi - lo) * (a.xg_b[gb] + 1.0);
+    }
+    const int nd = dp.n[a.d], pd = dp.p[a.d];
+    const int sd = a.side == 0 ? pd : nd - 1;
+    xi[a.d] = a.side == 0 ? dp.U[a.d][pd] : dp.U[a.d][nd];
+    b.s[a.ta] = sa;
+    b.s[a.tb] = sb;
+    b.s[a.d] = sd;
+    for (int d = 0; d < 3; ++d) bspline_1d(dp.U[d], dp.p[d], b.s[d], xi[d], b.N[d], b.dN[d]);
+    double x[3], J[3][3], W, dW[3];
+    nurbs_point(dp, b, x, J, W, dW);
+    const double ha = dp.U[a.ta][sa + 1] - dp.U[a.ta][sa];
+    const double hb = dp.U[a.tb][sb + 1] - dp.U[a.tb][sb];
+    const double wt = 0.25 * ha * hb * a.wg_a[ga] * a.wg_b[gb];
+    // x_u x x_v, oriented outward: on the side-0 face the normal points to
+    // decreasing xi_d, i.e. n . (dx/dxi_d) < 0, and > 0 on the side-1 face.
+    const double xu[3] = {J[0][a.ta], J[1][a.ta], J[2][a.ta]};
+    const double xv[3] = {J[0][a.tb], J[1][a.tb], J[2][a.tb]};
+    double c[3] = {xu[1] * xv[2] - xu[2] * xv[1], xu[2] * xv[0] - xu[0] * xv[2],
+                   xu[0] * xv[1] - xu[1] * xv[0]};
+    const double area = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double dotd = c[0] * J[0][a.d] + c[1] * J[1][a.d] + c[2] * J[2][a.d];
+    const double want = a.side == 0 ? -1.0 : 1.0;
+    const double sgn = (dotd * want >= 0.0) ? 1.0 : -1.0;
+    const double wdS = wt * area;
+    const int q = a.q_offset + qf;
+    double* P = a.pts64;
+    P[0 * a.q_stride + q] = x[0];
+    P[1 * a.q_stride + q] = x[1];
+    P[2 * a.q_stride + q] = x[2];
+    if (a.with_normal) {
+        P[3 * a.q_stride + q] = sgn * c[0] / area;
+        P[4 * a.q_stride + q] = sgn * c[1] / area;
+        P[5 * a.q_stride + q] = sgn * c[2] / area;
+        P[6 * a.q_stride + q] = wdS;
+    } else {
+        P[3 * a.q_stride + q] = wdS;
+    }
+    // face functions: the layer of the fixed direction that is non-zero on
+    // the face (open knots: the first or last), tangential local indices
+    const int ld = a.side == 0 ? 0 : pd;
+    const int pa = dp.p[a.ta], pb = dp.p[a.tb];
+    const int nfb = (pa + 1) * (pb + 1);
+    for (int lb = 0; lb <= pb; ++lb)
+        for (int la = 0; la <= pa; ++la) {
+            int loc[3];
+            loc[a.d] = ld;
+            loc[a.ta] = la;
+            loc[a.tb] = lb;
+            int g3[3];
+            for (int d = 0; d < 3; ++d) g3[d] = b.s[d] - dp.p[d] + loc[d];
+            const int nat = nat_index(dp, g3[0], g3[1], g3[2]);
+            const double Nv = b.N[0][loc[0]] * b.N[1][loc[1]] * b.N[2][loc[2]];
+            const double R = dp.cw[nat].w * Nv / W;
+            const int e = qf * nfb + lb * (pa + 1) + la;
+            a.w_val[a.slot[e]] = wdS * R;
+            if (a.coo_R) {
+                a.coo_R[e] = R;
+                a.coo_dof[e] = a.perm[nat];
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// element matrices: one block per element
+// ---------------------------------------------------------------------------
+struct ElemArgs {
+    DevPatch dp;
+    double rho_cp, k;
+    double xg[3][SA_MAX_DEGREE + 1], wg[3][SA_MAX_DEGREE + 1];
+    double* Mloc;
+    double* Kloc;
+    int* bad_jac;
+};
+
+__global__ void k_element_local(ElemArgs a) {
+    extern __shared__ double sm[];
+    const DevPatch& dp = a.dp;
+    const int nl0 = dp.p[0] + 1, nl1 = dp.p[1] + 1, nl2 = dp.p[2] + 1;
+    const int nloc = nl0 * nl1 * nl2;
+    const int nqp = nloc;                       // (p+1) Gauss points per direction
+    double* sR = sm;                            // [nqp][nloc]
+    double* sG = sR + nqp * nloc;               // [nqp][nloc][3]
+    double* sw = sG + 3 * nqp * nloc;           // [nqp]
+    const int e = blockIdx.x;
+    const int e0 = e % dp.ne[0], e1 = (e / dp.ne[0]) % dp.ne[1], e2 = e / (dp.ne[0] * dp.ne[1]);
+    const int es[3] = {e0, e1, e2};
+    for (int qp = threadIdx.x; qp < nqp; qp += blockDim.x) {
+        const int g0 = qp % nl0, g1 = (qp / nl0) % nl1, g2 = qp / (nl0 * nl1);
+        const int gs[3] = {g0, g1, g2};
+        Basis1D b;
+        double wt = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            const int s = dp.espan[d][es[d]];
+            const double lo = dp.U[d][s], hi = dp.U[d][s + 1];
+            const double u = lo + 0.5 * (hi - lo) * (a.xg[d][gs[d]] + 1.0);
+            wt *= 0.5 * (hi - lo) * a.wg[d][gs[d]];
+            b.s[d] = s;
+            bspline_1d(dp.U[d], dp.p[d], s, u, b.N[d], b.dN[d]);
+        }
+        double x[3], J[3][3], W, dW[3];
+        nurbs_point(dp, b, x, J, W, dW);
+        const double det = det3(J);
+        if (!(det > 0.0)) atomicOr(a.bad_jac, 1);
+        // inverse transpose: grad_x R = J^{-T} grad_xi R
+        double inv[3][3];
+        inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+        inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+        inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+        inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        sw[qp] = wt * det;
+        for (int a2 = 0; a2 < nl2; ++a2)
+            for (int a1 = 0; a1 < nl1; ++a1)
+                for (int a0 = 0; a0 < nl0; ++a0) {
+                    const int la = (a2 * nl1 + a1) * nl0 + a0;
+                    const int gi = b.s[0] - dp.p[0] + a0, gj = b.s[1] - dp.p[1] + a1,
+                              gk = b.s[2] - dp.p[2] + a2;
+                    const double w = dp.cw[nat_index(dp, gi, gj, gk)].w;
+                    const double Nv = b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
+                    const double dNv[3] = {b.dN[0][a0] * b.N[1][a1] * b.N[2][a2],
+                                           b.N[0][a0] * b.dN[1][a1] * b.N[2][a2],
+                                           b.N[0][a0] * b.N[1][a1] * b.dN[2][a2]};
+                    const double R = w * Nv / W;
+                    double dR[3];
+                    for (int d = 0; d < 3; ++d) dR[d] = (w * dNv[d] - R * dW[d]) / W;
+                    sR[qp * nloc + la] = R;
+                    for (int c = 0; c < 3; ++c)
+                        sG[(qp * nloc + la) * 3 + c] =
+                            inv[0][c] * dR[0] + inv[1][c] * dR[1] + inv[2][c] * dR[2];
+                }
+    }
+    __syncthreads();
+    const size_t base = (size_t)e * nloc * nloc;
+    for (int pr = threadIdx.x; pr < nloc * nloc; pr += blockDim.x) {
+        const int ia = pr / nloc, ib = pr % nloc;
+        double m = 0.0, kk = 0.0;
+        for (int qp = 0; qp < nqp; ++qp) {
+            const double w = sw[qp];
+            m += w * sR[qp * nloc + ia] * sR[qp * nloc + ib];
+            const double* ga = &sG[(qp * nloc + ia) * 3];
+            const double* gb = &sG[(qp * nloc + ib) * 3];
+            kk += w * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
+        }
+        a.Mloc[base + pr] = a.rho_cp * m;
+        a.Kloc[base + pr] = a.k * kk;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CSR gather: M_ij = sum over the elements supporting both i and j of the
+// local entries, in a fixed element order (e2, e1, e0 ascending): one warp
+// per row, deterministic, no atomics.
+// ---------------------------------------------------------------------------
+struct GatherArgs {
+    DevPatch dp;
+    const long long* ptr;
+    const int* col;
+    const int* elo[3];
+    const int* ehi[3];
+    const double* Mloc;
+    const double* Kloc;
+    double* M;
+    double* K;
+};
+
+__global__ void k_mk_gather(GatherArgs a) {
+    const DevPatch& dp = a.dp;
+    const int n_dof = dp.n[0] * dp.n[1] * dp.n[2];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_dof) return;
+    const int i = warp;
+    const int ii[3] = {i % dp.n[0], (i / dp.n[0]) % dp.n[1], i / (dp.n[0] * dp.n[1])};
+    const int nl0 = dp.p[0] + 1, nl1 = dp.p[1] + 1, nl2 = dp.p[2] + 1;
+    const int nloc = nl0 * nl1 * nl2;
+    for (long long s = a.ptr[i] + lane; s < a.ptr[i + 1]; s += 32) {
+        const int j = a.col[s];
+        const int jj[3] = {j % dp.n[0], (j / dp.n[0]) % dp.n[1], j / (dp.n[0] * dp.n[1])};
+        int lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = max(a.elo[d][ii[d]], a.elo[d][jj[d]]);
+            hi[d] = min(a.ehi[d][ii[d]], a.ehi[d][jj[d]]);
+        }
+        double m = 0.0, kk = 0.0;
+        for (int e2 = lo[2]; e2 <= hi[2]; ++e2)
+            for (int e1 = lo[1]; e1 <= hi[1]; ++e1)
+                for (int e0 = lo[0]; e0 <= hi[0]; ++e0) {
+                    const int es[3] = {e0, e1, e2};
+                    int la[3], lb[3];
+                    for (int d = 0; d < 3; ++d) {
+                        const int first = dp.espan[d][es[d]] - dp.p[d];
+                        la[d] = ii[d] - first;
+                        lb[d] = jj[d] - first;
+                    }
+                    const int ia = (la[2] * nl1 + la[1]) * nl0 + la[0];
+                    const int ib = (lb[2] * nl1 + lb[1]) * nl0 + lb[0];
+                    const size_t e = ((size_t)e2 * dp.ne[1] + e1) * dp.ne[0] + e0;
+                    const size_t off = e * nloc * nloc + (size_t)ia * nloc + ib;
+                    m += a.Mloc[off];
+                    kk += a.Kloc[off];
+                }
+        a.M[s] = m;
+        a.K[s] = kk;
+    }
+}
+
+// M_bot[r][c] = sum_q wdS_q R_r(x_q) R_c(x_q): thread per CSR entry, the
+// points of row r from W_bot (value wdS R_r), R_c from the point's list.
+__global__ void k_mbot_fill(int n_rows, const int* mptr, const int* mcol, const int* wptr,
+                            const int* wcol, const double* wval, const int* coo_dof,
+                            const double* coo_R, int nfb, int n_free, double* mval,
+                            double* dinv) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    for (int s = mptr[r]; s < mptr[r + 1]; ++s) {
+        const int c = mcol[s];
+        double acc = 0.0;
+        for (int t = wptr[r]; t < wptr[r + 1]; ++t) {
+            const int q = wcol[t];
+            for (int f = 0; f < nfb; ++f)
+                if (coo_dof[q * nfb + f] - n_free == c) acc += wval[t] * coo_R[q * nfb + f];
+        }
+        mval[s] = acc;
+        if (c == r) dinv[r] = 1.0 / acc;
+    }
+}
+
+__global__ void k_build_A(long long nnz_a, const int* a_src, const double* M, const double* K,
+                          double inv_dt, double theta, double* a_val) {
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= nnz_a) return;
+    const int src = a_src[s];
+    a_val[s] = M[src] * inv_dt + theta * K[src];
+}
+
+__global__ void k_diag_inv(int n, const int* ptr, const int* col, const double* val,
+                           double* dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int s = ptr[i]; s < ptr[i + 1]; ++s)
+        if (col[s] == i) dinv[i] = 1.0 / val[s];
+}
+
+__global__ void k_points32(int q_lat, int q_bot, const double* lat64, const double* bot64,
+                           double x_ref, double y_ref, double z_top, float* lat32,
+                           float* bot32) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < q_lat) {
+        const double dz = lat64[2 * q_lat + q] - z_top;
+        lat32[0 * q_lat + q] = (float)(lat64[0 * q_lat + q] - x_ref);
+        lat32[1 * q_lat + q] = (float)(lat64[1 * q_lat + q] - y_ref);
+        lat32[2 * q_lat + q] = (float)(dz * dz);
+        lat32[3 * q_lat + q] = (float)(lat64[5 * q_lat + q] * dz);
+        lat32[4 * q_lat + q] = (float)lat64[3 * q_lat + q];
+        lat32[5 * q_lat + q] = (float)lat64[4 * q_lat + q];
+    }
+    if (q < q_bot) {
+        const double dz = bot64[2 * q_bot + q] - z_top;
+        bot32[0 * q_bot + q] = (float)(bot64[0 * q_bot + q] - x_ref);
+        bot32[1 * q_bot + q] = (float)(bot64[1 * q_bot + q] - y_ref);
+        bot32[2 * q_bot + q] = (float)(dz * dz);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// reconstruction T = T~ + T^ at physical points (Section 2.4)
+// ---------------------------------------------------------------------------
+__device__ int find_span(const double* U, int p, int n, double u) {
+    if (u >= U[n]) {
+        int s = n - 1;
+        while (s > p && U[s] == U[s + 1]) --s;
+        return s;
+    }
+    if (u <= U[p]) return p;
+    int lo = p, hi = n;                 // U[lo] <= u < U[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (U[mid] <= u)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ void eval_at(const DevPatch& dp, const double xi[3], Basis1D& b, double x[3],
+                        double J[3][3], double& W) {
+    for (int d = 0; d < 3; ++d) {
+        b.s[d] = find_span(dp.U[d], dp.p[d], dp.n[d], xi[d]);
+        bspline_1d(dp.U[d], dp.p[d], b.s[d], xi[d], b.N[d], b.dN[d]);
+    }
+    double dW[3];
+    nurbs_point(dp, b, x, J, W, dW);
+}
+
+__global__ void k_elem_centers(DevPatch dp, double* ecent) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
+    if (e >= nel) return;
+    const int es[3] = {e % dp.ne[0], (e / dp.ne[0]) % dp.ne[1], e / (dp.ne[0] * dp.ne[1])};
+    double xi[3];
+    for (int d = 0; d < 3; ++d) {
+        const int s = dp.espan[d][es[d]];
+        xi[d] = 0.5 * (dp.U[d][s] + dp.U[d][s + 1]);
+    }
+    Basis1D b;
+    double x[3], J[3][3], W;
+    eval_at(dp, xi, b, x, J, W);
+    ecent[3 * e + 0] = x[0];
+    ecent[3 * e + 1] = x[1];
+    ecent[3 * e + 2] = x[2];
+}
+
+struct EvalArgs {
+    DevPatch dp;
+    const double* pts;
+    int n;
+    const double* ecent;
+    const int* perm;
+    const double* That;
+    const double4* s64T;
+    int n_active;
+    double x_ref, y_ref, z_top, scale;
+    double* T_out;
+};
+
+__global__ void k_eval(EvalArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n) return;
+    const DevPatch& dp = a.dp;
+    const double xs[3] = {a.pts[3 * t], a.pts[3 * t + 1], a.pts[3 * t + 2]};
+    // initial guess: parametric centre of the element with the nearest
+    // physical centre
+    const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
+    int best = 0;
+    double bd = 1e300;
+    for (int e = 0; e < nel; ++e) {
+        const double dx = a.ecent[3 * e] - xs[0], dy = a.ecent[3 * e + 1] - xs[1],
+                     dz = a.ecent[3 * e + 2] - xs[2];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 < bd) {
+            bd = d2;
+            best = e;
+        }
+    }
+    const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1], best / (dp.ne[0] * dp.ne[1])};
+    double xi[3], lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        const int s = dp.espan[d][es[d]];
+        xi[d] = 0.5 * (dp.U[d][s] + dp.U[d][s + 1]);
+        lo[d] = dp.U[d][dp.p[d]];
+        hi[d] = dp.U[d][dp.n[d]];
+    }
+    // Newton on x(xi) = x*, clamped to the parametric box
+    Basis1D b;
+    double x[3], J[3][3], W;
+    double res = 1e300;
+    for (int it = 0; it < 60; ++it) {
+        eval_at(dp, xi, b, x, J, W);
+        const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
+        res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (res <= 1e-13 * a.scale) break;
+        const double det = det3(J);
+        if (!(fabs(det) > 0.0)) break;
+        double dxi[3];
+        for (int c = 0; c < 3; ++c) {
+            double Jc[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J[r][k];
+            dxi[c] = det3(Jc) / det;
+        }
+        for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
+    }
+    if (!(res <= 1e-9 * a.scale)) {
+        a.T_out[t] = nan("");
+        return;
+    }
+    double That = 0.0;
+    for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+        for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+            for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0, b.s[1] - dp.p[1] + a1,
+                                          b.s[2] - dp.p[2] + a2);
+                const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
+                That += R * a.That[a.perm[nat]];
+            }
+    const double px = xs[0] - a.x_ref, py = xs[1] - a.y_ref, dz = xs[2] - a.z_top;
+    double Tt = 0.0;
+    for (int j = 0; j < a.n_active; ++j) {
+        const double4 sv = a.s64T[j];
+        const double dx = px - sv.x, dy = py - sv.y;
+        Tt += sv.w * exp(-sv.z * (dx * dx + dy * dy + dz * dz));
+    }
+    a.T_out[t] = Tt + That;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_face_points(const DevPatch& dp, int face, int pa_unused, int pb_unused, int nea,
+                               int neb, const int*, const double* xg_a, const double* wg_a,
+                               const double* xg_b, const double* wg_b, int q_offset,
+                               double* pts64, int q_stride, int with_normal,
+                               const int* slot_of_entry, double* w_val, double* coo_R,
+                               int* coo_dof, const int* perm, cudaStream_t s) {
+    (void)pa_unused;
+    (void)pb_unused;
+    FaceArgs a;
+    a.dp = dp;
+    a.d = face / 2;
+    a.side = face % 2;
+    a.ta = a.d == 0 ? 1 : 0;
+    a.tb = a.d == 2 ? 1 : 2;
+    a.nea = nea;
+    a.neb = neb;
+    a.nga = dp.p[a.ta] + 1;
+    a.ngb = dp.p[a.tb] + 1;
+    for (int g = 0; g < a.nga; ++g) {
+        a.xg_a[g] = xg_a[g];
+        a.wg_a[g] = wg_a[g];
+    }
+    for (int g = 0; g < a.ngb; ++g) {
+        a.xg_b[g] = xg_b[g];
+        a.wg_b[g] = wg_b[g];
+    }
+    a.q_offset = q_offset;
+    a.q_stride = q_stride;
+    a.with_normal = with_normal;
+    a.pts64 = pts64;
+    a.slot = slot_of_entry;
+    a.w_val = w_val;
+    a.coo_R = coo_R;
+    a.coo_dof = coo_dof;
+    a.perm = perm;
+    const int nq = nea * neb * a.nga * a.ngb;
+    if (nq == 0) return cudaSuccess;
+    k_face_points<<<(nq + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_element_local(const DevPatch& dp, double rho_cp, double k, const double* xg,
+                                 const double* wg, double* Mloc, double* Kloc, int* bad_jac,
+                                 cudaStream_t s) {
+    ElemArgs a;
+    a.dp = dp;
+    a.rho_cp = rho_cp;
+    a.k = k;
+    for (int d = 0; d < 3; ++d)
+        for (int g = 0; g <= dp.p[d]; ++g) {
+            a.xg[d][g] = xg[d * (SA_MAX_DEGREE + 1) + g];
+            a.wg[d][g] = wg[d * (SA_MAX_DEGREE + 1) + g];
+        }
+    a.Mloc = Mloc;
+    a.Kloc = Kloc;
+    a.bad_jac = bad_jac;
+    const int nloc = (dp.p[0] + 1) * (dp.p[1] + 1) * (dp.p[2] + 1);
+    const size_t smem = (size_t)nloc * nloc * 4 * sizeof(double) + nloc * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_element_local,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
+    k_element_local<<<nel, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mk_gather(const DevPatch& dp, const long long* ptr, const int* col,
+                             const int* const* elo, const int* const* ehi, const double* Mloc,
+                             const double* Kloc, double* M, double* K, cudaStream_t s) {
+    GatherArgs a;
+    a.dp = dp;
+    a.ptr = ptr;
+    a.col = col;
+    for (int d = 0; d < 3; ++d) {
+        a.elo[d] = elo[d];
+        a.ehi[d] = ehi[d];
+    }
+    a.Mloc = Mloc;
+    a.Kloc = Kloc;
+    a.M = M;
+    a.K = K;
+    const int n_dof = dp.n[0] * dp.n[1] * dp.n[2];
+    const long long threads = (long long)n_dof * 32;
+    k_mk_gather<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mbot_fill(int n_rows, const int* mptr, const int* mcol, const int* wptr,
+                             const int* wcol, const double* wval, const int* coo_dof,
+                             const double* coo_R, int nfb, int n_free, double* mval,
+                             double* dinv, cudaStream_t s) {
+    if (n_rows == 0) return cudaSuccess;
+    k_mbot_fill<<<(n_rows + 127) / 128, 128, 0, s>>>(n_rows, mptr, mcol, wptr, wcol, wval,
+                                                     coo_dof, coo_R, nfb, n_free, mval, dinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_A(long long nnz_a, const int* a_src, const double* M, const double* K,
+                           double inv_dt, double theta, double* a_val, int n_free,
+                           const int* a_ptr, const int* a_col, double* dinv, cudaStream_t s) {
+    if (nnz_a > 0)
+        k_build_A<<<(unsigned)((nnz_a + 255) / 256), 256, 0, s>>>(nnz_a, a_src, M, K, inv_dt,
+                                                                  theta, a_val);
+    if (n_free > 0)
+        k_diag_inv<<<(n_free + 255) / 256, 256, 0, s>>>(n_free, a_ptr, a_col, a_val, dinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points32(int q_lat, int q_bot, const double* lat64, const double* bot64,
+                            double x_ref, double y_ref, double z_top, float* lat32,
+                            float* bot32, cudaStream_t s) {
+    const int q = q_lat > q_bot ? q_lat : q_bot;
+    if (q == 0) return cudaSuccess;
+    k_points32<<<(q + 255) / 256, 256, 0, s>>>(q_lat, q_bot, lat64, bot64, x_ref, y_ref, z_top,
+                                               lat32, bot32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_elem_centers(const DevPatch& dp, double* ecent, cudaStream_t s) {
+    const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
+    k_elem_centers<<<(nel + 127) / 128, 128, 0, s>>>(dp, ecent);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
+                               const int* perm, const double* That, const double4* s64T,
+                               int n_active, double x_ref, double y_ref, double z_top,
+                               double scale, double* T_out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    EvalArgs a{dp, pts, n, ecent, perm, That, s64T, n_active, x_ref, y_ref, z_top, scale, T_out};
+    k_eval<<<(n + 63) / 64, 64, 0, s>>>(a);
+    return cudaGetLastError();
+}

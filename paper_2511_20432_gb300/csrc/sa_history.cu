@@ -1,0 +1,325 @@
+// Per-step history sums of the analytical point-source field (Section 2.1,
+// Eqs. sum-of-point-temp and semi-temperature) at the boundary quadrature
+// points:
+//   lateral points:  dT~/dn(x_q) = sum_I -g_I exp(-a_I R^2) (n_q . (x_q - x_I))
+//   bottom points:   T~(x_q)     = sum_I  c_I exp(-a_I R^2)
+// with, for source I at step n, age = (n - I) dt + r^2/(8 alpha),
+// a_I = 1/(4 alpha age), c_I = s_img E / (rho c_p (4 pi alpha age)^{3/2}),
+// g_I = 2 a_I c_I (the gradient of the Gaussian brings down
+// -(x - x_I)/(2 alpha age) = -2 a_I (x - x_I)).
+//
+// The per-step prologue forms these coefficients once per source in FP64
+// from the integer step difference.  The sum kernel is ALU-bound (FP32 FMA
+// pipe + MUFU ex2 in the mixed path, the FP64 pipe in the plain path); it is
+// not a contraction, so it does not use tensor cores.
+//
+// Work layout: one CTA owns a tile of 32*P points (P per lane, held in
+// registers) and all of its NW warps split the active sources round-robin;
+// the sources are read as warp-uniform 16-byte loads (one transaction per
+// warp, served by L1/L2: the whole source table of a step is at most a few
+// hundred KB).  Each lane accumulates FP32 partial sums over 32 of its
+// sources, then adds them into a Neumaier-compensated FP32 pair; the NW warp
+// results are added in FP64 in fixed order through shared memory.  Every
+// output point is written by exactly one thread: deterministic, no atomics,
+// no scratch memory.
+#include "sa_internal.h"
+
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------
+// prologue: source coefficients for step n1
+// ---------------------------------------------------------------------------
+struct PrologueArgs {
+    const DevStatus* st_in;   // when non-null, n1 = st_in->n + 1; else n_explicit
+    long long n_explicit;
+    DevStatus* st_out;        // n_active written here when non-null
+    int n_src;
+    const double2* pos;
+    double dt, alpha, r2_8a, coefE;
+    int precision;
+    double4* s64T;
+    double4* s64F;
+    float4* s32T;
+    float4* s32F;
+};
+
+__global__ void k_prologue(PrologueArgs a) {
+    const long long n1 = a.st_in ? a.st_in->n + 1 : a.n_explicit;
+    const int K = (int)(n1 < (long long)a.n_src ? n1 : (long long)a.n_src);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.st_out) a.st_out->n_active = K;
+    const double kPi = 3.141592653589793;
+    const double kLog2e = 1.4426950408889634;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
+        const long long I = i + 1;
+        const double age = (double)(n1 - I) * a.dt + a.r2_8a;
+        const double aI = 1.0 / (4.0 * a.alpha * age);
+        const double base = 4.0 * kPi * a.alpha * age;
+        const double cI = a.coefE / (base * sqrt(base));
+        const double gI = 2.0 * aI * cI;
+        const double2 p = a.pos[i];
+        if (a.s64T) {
+            a.s64T[i] = make_double4(p.x, p.y, aI, cI);
+            a.s64F[i] = make_double4(p.x, p.y, aI, gI);
+        }
+        if (a.s32T) {
+            const float sx = (float)p.x, sy = (float)p.y;
+            const float na = (float)(-aI * kLog2e);
+            a.s32T[i] = make_float4(sx, sy, na, (float)log2(cI));
+            a.s32F[i] = make_float4(sx, sy, na, (float)log2(gI));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// history sum
+// ---------------------------------------------------------------------------
+struct HistArgs {
+    const DevStatus* st;
+    int q_lat, q_bot;
+    int b_lat;                 // CTAs on lateral tiles; the rest on bottom tiles
+    const float* lat32;
+    const float* bot32;
+    const double* lat64;
+    const double* bot64;
+    double x_ref, y_ref, z_top;
+    const float4* s32F;
+    const float4* s32T;
+    const double4* s64F;
+    const double4* s64T;
+    double* s_lat;
+    double* tt_bot;
+};
+
+// Neumaier compensated addition of x into (s, c).
+__device__ __forceinline__ void neumaier(float& s, float& c, float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+}
+
+template <bool FLUX, int P, int NW>
+__device__ void tile_mixed(const HistArgs& a, int tile, double* red) {
+    const int Q = FLUX ? a.q_lat : a.q_bot;
+    const float* pts = FLUX ? a.lat32 : a.bot32;
+    const float4* src = FLUX ? a.s32F : a.s32T;
+    const int K = a.st->n_active;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q0 = tile * 32 * P;
+    float px[P], py[P], dz2[P], nzdz[P], nx[P], ny[P];
+    float s[P], c[P], acc[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int q = q0 + lane + 32 * p;
+        const bool ok = q < Q;
+        px[p] = ok ? pts[0 * Q + q] : 0.f;
+        py[p] = ok ? pts[1 * Q + q] : 0.f;
+        dz2[p] = ok ? pts[2 * Q + q] : 0.f;
+        if (FLUX) {
+            nzdz[p] = ok ? pts[3 * Q + q] : 0.f;
+            nx[p] = ok ? pts[4 * Q + q] : 0.f;
+            ny[p] = ok ? pts[5 * Q + q] : 0.f;
+        }
+        s[p] = 0.f;
+        c[p] = 0.f;
+        acc[p] = 0.f;
+    }
+    int cnt = 0;
+    int j = w;
+    // software pipeline: the next warp-uniform source is loaded one ahead
+    float4 nxt = j < K ? __ldg(&src[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (; j < K; j += NW) {
+        const float4 sv = nxt;
+        if (j + NW < K) nxt = __ldg(&src[j + NW]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float dx = px[p] - sv.x;
+            const float dy = py[p] - sv.y;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz2[p]));
+            const float e = ex2_approx(fmaf(sv.z, r2, sv.w));
+            if (FLUX) {
+                const float nd = fmaf(nx[p], dx, fmaf(ny[p], dy, nzdz[p]));
+                acc[p] = fmaf(e, nd, acc[p]);
+            } else {
+                acc[p] += e;
+            }
+        }
+        if (++cnt == 32) {
+            cnt = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                neumaier(s[p], c[p], acc[p]);
+                acc[p] = 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        neumaier(s[p], c[p], acc[p]);
+        red[w * 32 * P + lane + 32 * p] = (double)s[p] + (double)c[p];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * P; t += 32 * NW) {
+        double tot = 0.0;
+        for (int ww = 0; ww < NW; ++ww) tot += red[ww * 32 * P + t];
+        const int q = q0 + t;
+        if (q < Q) {
+            if (FLUX)
+                a.s_lat[q] = -tot;
+            else
+                a.tt_bot[q] = tot;
+        }
+    }
+}
+
+template <bool FLUX, int P, int NW>
+__device__ void tile_fp64(const HistArgs& a, int tile, double* red) {
+    const int Q = FLUX ? a.q_lat : a.q_bot;
+    const double* pts = FLUX ? a.lat64 : a.bot64;
+    const double4* src = FLUX ? a.s64F : a.s64T;
+    const int K = a.st->n_active;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q0 = tile * 32 * P;
+    double px[P], py[P], dz[P], nx[P], ny[P], nz[P], acc[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int q = q0 + lane + 32 * p;
+        const bool ok = q < Q;
+        px[p] = ok ? pts[0 * Q + q] - a.x_ref : 0.0;
+        py[p] = ok ? pts[1 * Q + q] - a.y_ref : 0.0;
+        dz[p] = ok ? pts[2 * Q + q] - a.z_top : 0.0;
+        if (FLUX) {
+            nx[p] = ok ? pts[3 * Q + q] : 0.0;
+            ny[p] = ok ? pts[4 * Q + q] : 0.0;
+            nz[p] = ok ? pts[5 * Q + q] : 0.0;
+        }
+        acc[p] = 0.0;
+    }
+    for (int j = w; j < K; j += NW) {
+        const double4 sv = src[j];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const double dx = px[p] - sv.x;
+            const double dy = py[p] - sv.y;
+            const double r2 = dx * dx + dy * dy + dz[p] * dz[p];
+            const double e = sv.w * exp(-sv.z * r2);
+            if (FLUX)
+                acc[p] += e * (nx[p] * dx + ny[p] * dy + nz[p] * dz[p]);
+            else
+                acc[p] += e;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) red[w * 32 * P + lane + 32 * p] = acc[p];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * P; t += 32 * NW) {
+        double tot = 0.0;
+        for (int ww = 0; ww < NW; ++ww) tot += red[ww * 32 * P + t];
+        const int q = q0 + t;
+        if (q < Q) {
+            if (FLUX)
+                a.s_lat[q] = -tot;
+            else
+                a.tt_bot[q] = tot;
+        }
+    }
+}
+
+template <int P, int NW>
+__global__ void __launch_bounds__(32 * NW) k_history_mixed(HistArgs a) {
+    __shared__ double red[NW * 32 * P];
+    if ((int)blockIdx.x < a.b_lat)
+        tile_mixed<true, P, NW>(a, blockIdx.x, red);
+    else
+        tile_mixed<false, P, NW>(a, blockIdx.x - a.b_lat, red);
+}
+
+template <int P, int NW>
+__global__ void __launch_bounds__(32 * NW) k_history_fp64(HistArgs a) {
+    __shared__ double red[NW * 32 * P];
+    if ((int)blockIdx.x < a.b_lat)
+        tile_fp64<true, P, NW>(a, blockIdx.x, red);
+    else
+        tile_fp64<false, P, NW>(a, blockIdx.x - a.b_lat, red);
+}
+
+template <int P, int NW>
+cudaError_t launch_hist_t(int precision, const HistArgs& a0, cudaStream_t s) {
+    HistArgs a = a0;
+    const int tile = 32 * P;
+    a.b_lat = (a.q_lat + tile - 1) / tile;
+    const int b_bot = (a.q_bot + tile - 1) / tile;
+    const int grid = a.b_lat + b_bot;
+    if (grid == 0) return cudaSuccess;
+    if (precision == SA_MIXED)
+        k_history_mixed<P, NW><<<grid, 32 * NW, 0, s>>>(a);
+    else
+        k_history_fp64<P, NW><<<grid, 32 * NW, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_prologue(const DevStatus* st_in, long long n_explicit, DevStatus* st_out,
+                            int n_src, const double2* pos, double dt, double alpha,
+                            double r2_8a, double coefE, int precision, double4* s64T,
+                            double4* s64F, float4* s32T, float4* s32F, cudaStream_t s) {
+    PrologueArgs a;
+    a.st_in = st_in;
+    a.n_explicit = n_explicit;
+    a.st_out = st_out;
+    a.n_src = n_src;
+    a.pos = pos;
+    a.dt = dt;
+    a.alpha = alpha;
+    a.r2_8a = r2_8a;
+    a.coefE = coefE;
+    a.precision = precision;
+    a.s64T = s64T;
+    a.s64F = s64F;
+    a.s32T = s32T;
+    a.s32F = s32F;
+    int blocks = (n_src + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    k_prologue<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_history(int precision, int P, int warps, const DevStatus* st, int q_lat,
+                           int q_bot, const float* lat32, const float* bot32,
+                           const double* lat64, const double* bot64, double x_ref,
+                           double y_ref, double z_top, const float4* s32F,
+                           const float4* s32T, const double4* s64F, const double4* s64T,
+                           double* s_lat, double* tt_bot, cudaStream_t s) {
+    HistArgs a;
+    a.st = st;
+    a.q_lat = q_lat;
+    a.q_bot = q_bot;
+    a.b_lat = 0;
+    a.lat32 = lat32;
+    a.bot32 = bot32;
+    a.lat64 = lat64;
+    a.bot64 = bot64;
+    a.x_ref = x_ref;
+    a.y_ref = y_ref;
+    a.z_top = z_top;
+    a.s32F = s32F;
+    a.s32T = s32T;
+    a.s64F = s64F;
+    a.s64T = s64T;
+    a.s_lat = s_lat;
+    a.tt_bot = tt_bot;
+    if (warps == 4) {
+        if (P == 1) return launch_hist_t<1, 4>(precision, a, s);
+        if (P == 2) return launch_hist_t<2, 4>(precision, a, s);
+        return launch_hist_t<4, 4>(precision, a, s);
+    }
+    if (P == 1) return launch_hist_t<1, 8>(precision, a, s);
+    if (P == 2) return launch_hist_t<2, 8>(precision, a, s);
+    return launch_hist_t<4, 8>(precision, a, s);
+}

@@ -1,0 +1,278 @@
+// Internal declarations shared by the translation units of libsa.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/sa.h"
+
+// ---------------------------------------------------------------------------
+// limits
+// ---------------------------------------------------------------------------
+#define SA_MAX_DEGREE 3
+#define SA_MAX_NLOC ((SA_MAX_DEGREE + 1) * (SA_MAX_DEGREE + 1) * (SA_MAX_DEGREE + 1))
+#define SA_MAX_NFACE ((SA_MAX_DEGREE + 1) * (SA_MAX_DEGREE + 1))
+
+// device error flags (DevStatus::err)
+enum {
+    SA_DEV_NOT_CONVERGED = 1,
+    SA_DEV_BOT_NOT_CONVERGED = 2,
+    SA_DEV_TIMEOUT = 4,
+    SA_DEV_NAN = 8,
+    SA_DEV_BAD_INDEX = 16
+};
+
+// Written by kernels, read by the host after a stream synchronisation.
+struct DevStatus {
+    int err;
+    int pcg_iters;            // last main solve
+    int bot_iters;            // last bottom solve
+    int n_active;             // sources in the sum at the last step
+    double rel_res;           // last main solve
+    double bot_rel_res;
+    long long n;              // step index (device copy)
+    long long iters_total;    // accumulated since the last reset by the host
+    long long bot_total;
+    int iters_max;
+    int pad;
+    unsigned bar_count[4];    // grid barrier counters (one pair per cooperative kernel slot)
+    unsigned bar_gen[4];
+};
+
+// Geometry description handed to device kernels by value.
+struct DevPatch {
+    int p[3];
+    int n[3];
+    int ne[3];
+    const double* U[3];       // knot vectors
+    const int* espan[3];      // span index of each element, per direction
+    const double4* cw;        // control points (x, y, z, w), natural order
+};
+
+// ---------------------------------------------------------------------------
+// RAII device buffer
+// ---------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = count;
+        return cudaSuccess;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// the context
+// ---------------------------------------------------------------------------
+struct sa_ctx {
+    sa_options opt;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool poisoned = false;
+    int num_sms = 0;
+
+    // patch (host copy)
+    bool has_patch = false;
+    int p[3] = {0, 0, 0}, n[3] = {0, 0, 0}, ne[3] = {0, 0, 0};
+    std::vector<double> U[3];
+    std::vector<int> espan[3];
+    std::vector<int> elo[3], ehi[3];   // element range touching each 1-D basis function
+    std::vector<double> ctrl, w;
+    int face_kind[6] = {SA_FACE_NEUMANN, SA_FACE_NEUMANN, SA_FACE_NEUMANN, SA_FACE_NEUMANN,
+                        SA_FACE_DIRICHLET, SA_FACE_NONE};
+    int n_dof = 0, n_free = 0, n_dir = 0, n_elem = 0;
+    std::vector<int> perm;    // natural -> internal (free first, then Dirichlet)
+    std::vector<int> iperm;   // internal -> natural
+    double z_top = 0, x_ref = 0, y_ref = 0, length_scale = 1;
+
+    // material
+    bool has_material = false;
+    double k = 0, rho = 0, cp = 0, Tc = 0;
+
+    // scan
+    bool has_scan = false;
+    std::vector<double> path;
+    std::vector<unsigned char> seg_on;
+    double power = 0, absorptivity = 0, speed = 0, spot_radius = 0;
+    double src_dt = 0;        // dt the sources were discretised with (0: not yet)
+    int n_src = 0;
+    double E = 0;
+
+    // stepping
+    long long n_step = 0;     // host mirror of the step index
+    double op_dt = 0, op_theta = -1;   // operator currently built
+    bool state_dirty_graph = true;
+    cudaGraphExec_t graph_exec = nullptr;
+
+    // ---- device: geometry -------------------------------------------------
+    DBuf<double> dU[3];
+    DBuf<int> despan[3];
+    DBuf<double4> dcw;
+    DBuf<int> dperm;          // natural -> internal
+    DevPatch dp;
+
+    // quadrature points (canonical order)
+    int q_lat = 0, q_bot = 0;
+    DBuf<double> lat64;       // SoA: x, y, z, nx, ny, nz, wdS   (7 * q_lat)
+    DBuf<double> bot64;       // SoA: x, y, z, wdS               (4 * q_bot)
+    DBuf<float> lat32;        // SoA: px, py, dz2, nzdz, nx, ny  (6 * q_lat)
+    DBuf<float> bot32;        // SoA: px, py, dz2                (3 * q_bot)
+
+    // W_lat: rows = control variables touched by lateral points
+    int wlat_rows = 0;
+    DBuf<int> wlat_rowdof, wlat_ptr, wlat_col;
+    DBuf<double> wlat_val;
+    // W_bot: rows = Dirichlet control variables (bottom-local index)
+    DBuf<int> wbot_ptr, wbot_col;
+    DBuf<double> wbot_val;
+    // M_bot (Dirichlet x Dirichlet, bottom-local indices) and its Jacobi inverse
+    long long nnz_mbot = 0;
+    DBuf<int> mbot_ptr, mbot_col;
+    DBuf<double> mbot_val, mbot_dinv;
+
+    // M, K: CSR over all control variables, natural order
+    long long nnz = 0;
+    DBuf<long long> mk_ptr;
+    DBuf<int> mk_col;
+    DBuf<double> M, K;
+    // free-free operator A = M/dt + theta K, internal indices
+    long long nnz_a = 0;
+    DBuf<int> a_ptr, a_col, a_src;   // a_src: slot in the natural CSR
+    DBuf<double> a_val, a_dinv;
+
+    // ---- device: scan and history ------------------------------------------
+    DBuf<double2> src_pos;    // relative (x - x_ref, y - y_ref)
+    DBuf<double4> src64T, src64F;   // (sx, sy, a, c) / (sx, sy, a, g)
+    DBuf<float4> src32T, src32F;    // (sx, sy, -a log2 e, log2 c / log2 g)
+    DBuf<double> s_lat;       // dT~/dn at lateral points
+    DBuf<double> tt_bot;      // T~ at bottom points
+
+    // ---- device: state and solver work ---------------------------------------
+    DBuf<double> That;        // internal order (n_dof)
+    DBuf<double> F0, F1;      // internal order (n_dof)
+    DBuf<double> gnew, bbot;  // n_dir
+    DBuf<double> rhs, r0;     // n_free
+    DBuf<double> wr, wz, wp0, wp1, wq;   // PCG work, max(n_free, n_dir)
+    DBuf<double> partials;    // 4 * max grid
+    DBuf<DevStatus> st;
+    int pcg_grid = 0, pcg_block = 0;
+    int hist_P = 0, hist_W = 0;
+
+    // ---- device: set-up and evaluation helpers ---------------------------------
+    DBuf<int> d_elo[3], d_ehi[3];   // element range touching each 1-D basis function
+    DBuf<int> d_iperm_free;         // internal free index -> natural index
+    bool state_init = false;
+    DBuf<double> ecent;             // physical element centres (eval initial guess)
+    DBuf<double4> evT, evF;         // FP64 source coefficients at the current step
+    DBuf<double> eval_pts, eval_out;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+sa_status sa_fail(sa_ctx* c, sa_status s, const char* fmt, ...);
+sa_status sa_cuda_fail(sa_ctx* c, cudaError_t e, const char* where);
+
+#define SA_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e__ = (call);                                    \
+        if (e__ != cudaSuccess) return sa_cuda_fail(ctx, e__, #call); \
+    } while (0)
+
+#define SA_ALLOC(ctx, buf, count)                                                      \
+    do {                                                                               \
+        cudaError_t e__ = (buf).alloc(count);                                          \
+        if (e__ != cudaSuccess) {                                                      \
+            cudaGetLastError();                                                        \
+            return sa_fail(ctx, e__ == cudaErrorMemoryAllocation ? SA_ERR_OOM : SA_ERR_CUDA, \
+                           "allocation of %s (%zu elements): %s", #buf, (size_t)(count), \
+                           cudaGetErrorString(e__));                                   \
+        }                                                                              \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// entry points of the kernel translation units
+// ---------------------------------------------------------------------------
+// sa_geom.cu
+cudaError_t launch_face_points(const DevPatch& dp, int face, int pa, int pb, int nea, int neb,
+                               const int* dof_of_local,  // unused placeholder (nullptr)
+                               const double* xg_a, const double* wg_a, const double* xg_b,
+                               const double* wg_b, int q_offset, double* pts64, int q_stride,
+                               int with_normal, const int* slot_of_entry, double* w_val,
+                               double* coo_R, int* coo_dof, const int* perm, cudaStream_t s);
+cudaError_t launch_element_local(const DevPatch& dp, double rho_cp, double k, const double* xg,
+                                 const double* wg, double* Mloc, double* Kloc, int* bad_jac,
+                                 cudaStream_t s);
+cudaError_t launch_mk_gather(const DevPatch& dp, const long long* ptr, const int* col,
+                             const int* const* elo, const int* const* ehi, const double* Mloc,
+                             const double* Kloc, double* M, double* K, cudaStream_t s);
+cudaError_t launch_elem_centers(const DevPatch& dp, double* ecent, cudaStream_t s);
+cudaError_t launch_mbot_fill(int n_rows, const int* mptr, const int* mcol, const int* wptr,
+                             const int* wcol, const double* wval, const int* coo_dof,
+                             const double* coo_R, int nfb, int n_free, double* mval,
+                             double* dinv, cudaStream_t s);
+cudaError_t launch_build_A(long long nnz_a, const int* a_src, const double* M, const double* K,
+                           double inv_dt, double theta, double* a_val, int n_free,
+                           const int* a_ptr, const int* a_col, double* dinv, cudaStream_t s);
+cudaError_t launch_points32(int q_lat, int q_bot, const double* lat64, const double* bot64,
+                            double x_ref, double y_ref, double z_top, float* lat32,
+                            float* bot32, cudaStream_t s);
+
+// sa_history.cu
+cudaError_t launch_prologue(const DevStatus* st_in, long long n_explicit, DevStatus* st_out,
+                            int n_src, const double2* pos, double dt, double alpha,
+                            double r2_8a, double coefE, int precision, double4* s64T,
+                            double4* s64F, float4* s32T, float4* s32F, cudaStream_t s);
+cudaError_t launch_history(int precision, int P, int warps, const DevStatus* st, int q_lat,
+                           int q_bot, const float* lat32, const float* bot32,
+                           const double* lat64, const double* bot64, double x_ref,
+                           double y_ref, double z_top, const float4* s32F,
+                           const float4* s32T, const double4* s64F, const double4* s64T,
+                           double* s_lat, double* tt_bot, cudaStream_t s);
+cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
+                               const int* perm, const double* That, const double4* s64T,
+                               int n_active, double x_ref, double y_ref, double z_top,
+                               double scale, double* T_out, cudaStream_t s);
+
+// sa_solve.cu
+cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat_ptr,
+                          const int* wlat_col, const double* wlat_val, const double* s_lat,
+                          double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
+                          const double* wbot_val, const double* tt_bot, double Tc, double* F1,
+                          double* bbot, cudaStream_t s);
+cudaError_t launch_theta_rhs(int n_free, const long long* mk_ptr, const int* mk_col,
+                             const double* M, const double* K, const int* perm,
+                             const int* iperm_free, const double* That, const double* gnew,
+                             const double* F0, const double* F1, double inv_dt, double kscale,
+                             double theta, double* rhs, double* r0, cudaStream_t s);
+cudaError_t launch_pcg(int which, int n, const int* ptr, const int* col, const double* val,
+                       const double* dinv, const double* b, const double* r0_or_null, double* x,
+                       double* r, double* z, double* p0, double* p1, double* q,
+                       double* partials, DevStatus* st, double tol, int max_iter, int grid,
+                       int block, cudaStream_t s);
+cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
+                            const double* F1, double* F0, DevStatus* st, cudaStream_t s);
+int pcg_block_size();
+const void* pcg_kernel_ptr();

@@ -1,0 +1,299 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 GPU path 1e-10 relative L-infinity (1e-12 for set-up
+quantities and single history sums); mixed path 1e-4 relative and 0.05 K.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._common import (TOL_FP64, TOL_MIXED_ABS, TOL_MIXED_REL, gpu_context, lateral_xi,
+                           rel_linf)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_20432_gb300 import build
+    build.build()
+    import paper_2511_20432_gb300 as sa_mod
+    return sa_mod
+
+
+def _oracle(wl, **kw):
+    from oracle.solver import Model
+    return Model(wl, **kw)
+
+
+def _patch_cases():
+    return {
+        "cuboid": W.cuboid_patch((0.9e-3, 0.7e-3, 0.4e-3), (5, 4, 3), 2),
+        "nurbs_distorted": W.distorted_block(weights=True),
+        "bspline_p3": W.distorted_block(weights=False, degree=3, n_el=(3, 2, 2), seed=5),
+        "quarter_cylinder": W.quarter_cylinder_part(),
+        "mixed_degree": W.cuboid_patch((0.6e-3, 0.5e-3, 0.3e-3), (4, 3, 2), (3, 2, 1)),
+    }
+
+
+def _wl_for(patch, n_steps=4, dt=5e-6, theta=0.5):
+    ctrl = patch.ctrl.reshape(-1, 3)
+    lo, hi = ctrl.min(0), ctrl.max(0)
+    z = float(patch.ctrl[-1, 0, 0, 2])
+    x0 = lo + 0.3 * (hi - lo)
+    x1 = lo + 0.6 * (hi - lo)
+    scan = W.straight_track((x0[0], x0[1], z), (x1[0], x0[1], z), 150.0, 0.4, 1.0)
+    return W.Workload("case", patch, W.MAT_DEFAULT, scan, dt=dt, theta=theta, n_steps=n_steps)
+
+
+@pytest.mark.parametrize("case", list(_patch_cases()))
+def test_boundary_points_match_oracle(sa, case):
+    patch = _patch_cases()[case]
+    wl = _wl_for(patch)
+    m = _oracle(wl, build_solver=False)
+    ctx = gpu_context(wl, sa.SA_FP64)
+    lat = ctx.field(sa.SA_FIELD_LAT_X).reshape(-1, 7)
+    bot = ctx.field(sa.SA_FIELD_BOT_X).reshape(-1, 4)
+    scale = np.abs(patch.ctrl).max()
+    assert lat.shape[0] == len(m.lat["x"]) and bot.shape[0] == len(m.bot["x"])
+    assert np.abs(lat[:, :3] - m.lat["x"]).max() <= 1e-13 * scale
+    assert np.abs(lat[:, 3:6] - m.lat["n"]).max() <= 1e-12
+    assert rel_linf(lat[:, 6], m.lat["wdS"]) <= 1e-12
+    assert np.abs(bot[:, :3] - m.bot["x"]).max() <= 1e-13 * scale
+    assert rel_linf(bot[:, 3], m.bot["wdS"]) <= 1e-12
+
+
+@pytest.mark.parametrize("case", list(_patch_cases()))
+def test_assembly_matches_oracle(sa, case):
+    patch = _patch_cases()[case]
+    wl = _wl_for(patch)
+    m = _oracle(wl, build_solver=False)
+    ctx = gpu_context(wl, sa.SA_FP64)
+    import scipy.sparse as sp
+    n = patch.n_dof
+    for which, ref in ((0, m.M), (1, m.K)):
+        ptr, col, val = ctx.matrix(which)
+        G = sp.csr_matrix((val, col, ptr), shape=(n, n))
+        D = (G - ref).toarray()
+        assert np.abs(D).max() <= 1e-12 * np.abs(ref).max(), (case, which)
+
+
+def _lockstep(sa, wl, precision, n_check, every=1, **opts):
+    """Step oracle and GPU together; return max relative errors of the
+    history sums, F and T^ over the checked steps."""
+    m = _oracle(wl)
+    ctx = gpu_context(wl, precision, pcg_tol=1e-13 if precision == sa.SA_FP64 else 1e-10,
+                      **opts)
+    err = dict(s_lat=0.0, tt_bot=0.0, F=0.0, That=0.0, That_abs=0.0)
+    for step in range(n_check):
+        ctx.step(wl.theta, wl.dt, 1)
+        m.step()
+        if (step + 1) % every and step + 1 != n_check:
+            continue
+        err["s_lat"] = max(err["s_lat"], rel_linf(ctx.field(sa.SA_FIELD_DTDN_LAT), m.last["s_lat"]))
+        err["tt_bot"] = max(err["tt_bot"], rel_linf(ctx.field(sa.SA_FIELD_TT_BOT), m.last["Tt_bot"]))
+        err["F"] = max(err["F"], rel_linf(ctx.field(sa.SA_FIELD_F), m.F))
+        T = ctx.field(sa.SA_FIELD_THAT)
+        err["That"] = max(err["That"], rel_linf(T, m.T_hat))
+        err["That_abs"] = max(err["That_abs"], np.abs(T - m.T_hat).max())
+    return err, ctx, m
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_cuboid_single_track_fp64(sa, theta):
+    wl = W.cuboid_single_track(theta=theta, n_steps=150)
+    err, ctx, m = _lockstep(sa, wl, sa.SA_FP64, 150, every=25)
+    assert err["s_lat"] <= 1e-12 and err["tt_bot"] <= 1e-12, err
+    assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+    # reconstruction T = T~ + T^ at interior and boundary points
+    rng = np.random.default_rng(7)
+    xi = rng.uniform(0, 1, (40, 3))
+    xi[:8, 2] = 1.0
+    x, T_ref = m.eval_T(xi)
+    T = ctx.eval_T(x)
+    assert rel_linf(T, T_ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_cuboid_single_track_mixed(sa, theta):
+    wl = W.cuboid_single_track(theta=theta, n_steps=150)
+    err, ctx, m = _lockstep(sa, wl, sa.SA_MIXED, 150, every=15)
+    assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
+    assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+
+
+@pytest.mark.parametrize("P,NW", [(1, 4), (2, 8), (4, 8), (4, 4)])
+def test_multichunk_ragged_tiles(sa, P, NW):
+    """Several tracks (hundreds of sources over many warps), tiles with a
+    ragged tail, a distorted NURBS block; every tile shape of the kernel."""
+    patch = W.distorted_block(weights=True, n_el=(7, 5, 3), size=(1.4e-3, 1.0e-3, 0.5e-3), seed=11)
+    z = float(patch.ctrl[-1, 0, 0, 2])
+    scan = W.meander(0.2e-3, 1.2e-3, 0.25e-3, 0.15e-3, 4, z, 180.0, 0.4, 1.5)
+    wl = W.Workload("mc", patch, W.MAT_DEFAULT, scan, dt=4e-6, theta=0.5, n_steps=420)
+    for prec in (sa.SA_FP64, sa.SA_MIXED):
+        err, ctx, m = _lockstep(sa, wl, prec, 420, every=70, hist_points_per_lane=P,
+                                hist_warps=NW)
+        if prec == sa.SA_FP64:
+            assert err["s_lat"] <= 1e-12 and err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+        else:
+            assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
+            assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+
+
+def test_degenerate_cases(sa):
+    """No sources before the first step; a scan whose laser is off: T^ stays
+    T_c exactly; the empty eval call; one element, degree 1."""
+    patch = W.cuboid_patch((0.3e-3, 0.3e-3, 0.2e-3), (1, 1, 1), 1)
+    scan = W.Scan(path=np.array([[0, 0, 0.2e-3], [0.3e-3, 0.3e-3, 0.2e-3]]),
+                  seg_on=np.zeros(1, np.uint8), power=100.0, absorptivity=0.5, speed=1.0)
+    wl = W.Workload("off", patch, W.MAT_DEFAULT, scan, dt=1e-5, theta=0.5, n_steps=3)
+    ctx = gpu_context(wl, sa.SA_FP64)
+    T0 = ctx.field(sa.SA_FIELD_THAT)
+    assert np.all(T0 == W.MAT_DEFAULT.T_c)
+    st = ctx.step(0.5, 1e-5, 3)
+    assert st.n_active_sources == 0
+    assert np.all(ctx.field(sa.SA_FIELD_THAT) == W.MAT_DEFAULT.T_c)
+    assert ctx.eval_T(np.zeros((0, 3))).shape == (0,)
+    # one element, degree 1, a short track: parity holds
+    scan2 = W.straight_track((0.1e-3, 0.1e-3, 0.2e-3), (0.2e-3, 0.15e-3, 0.2e-3), 80.0, 0.5, 1.0)
+    wl2 = W.Workload("one", patch, W.MAT_DEFAULT, scan2, dt=1e-5, theta=1.0, n_steps=12)
+    err, _, _ = _lockstep(sa, wl2, sa.SA_FP64, 12)
+    assert err["That"] <= TOL_FP64 and err["F"] <= TOL_FP64, err
+
+
+def test_checkpoint_resume_is_bit_exact(sa):
+    wl = W.small_block(n_el=(6, 5, 3), n_tracks=2)
+    a = gpu_context(wl, sa.SA_MIXED)
+    a.step(wl.theta, wl.dt, 30)
+    n, T, F = a.get_state()
+    assert n == 30
+    a.step(wl.theta, wl.dt, 25)
+    Ta = a.field(sa.SA_FIELD_THAT)
+    b = gpu_context(wl, sa.SA_MIXED)
+    b.step(wl.theta, wl.dt, 0)          # fixes dt (source spacing) without stepping
+    b.set_state(n, T, F)
+    b.step(wl.theta, wl.dt, 25)
+    assert np.array_equal(b.field(sa.SA_FIELD_THAT), Ta)
+
+
+def test_graph_replay_equals_direct_launches(sa):
+    import torch
+    wl = W.small_block(n_el=(6, 5, 3), n_tracks=2)
+    s = torch.cuda.Stream()
+    a = gpu_context(wl, sa.SA_MIXED, cuda_stream=s, use_graph=1)
+    b = gpu_context(wl, sa.SA_MIXED, cuda_stream=s, use_graph=0)
+    a.step(wl.theta, wl.dt, 40)
+    b.step(wl.theta, wl.dt, 40)
+    assert np.array_equal(a.field(sa.SA_FIELD_THAT), b.field(sa.SA_FIELD_THAT))
+
+
+def test_errors_are_reported(sa):
+    wl = W.small_block()
+    p = wl.patch
+    ctx = sa.Context()
+    bad = [k.copy() for k in p.knots]
+    bad[0][3], bad[0][4] = bad[0][4], bad[0][3] + 0.01
+    with pytest.raises(sa.SAError) as e:
+        ctx.create_patch(p.degree, p.n_ctrl, p.ctrl.reshape(-1, 3), None, bad)
+    assert e.value.status in (sa.SA_ERR_GEOMETRY,)
+    with pytest.raises(sa.SAError) as e:
+        ctx.create_patch(p.degree, p.n_ctrl, p.ctrl.reshape(-1, 3),
+                         -np.ones(p.n_dof), p.knots)
+    assert e.value.status == sa.SA_ERR_GEOMETRY
+    c2 = p.ctrl.copy()
+    c2[-1, 0, 0, 2] += 1e-5
+    with pytest.raises(sa.SAError) as e:
+        ctx.create_patch(p.degree, p.n_ctrl, c2.reshape(-1, 3), None, p.knots)
+    assert e.value.status == sa.SA_ERR_GEOMETRY
+    ctx.create_patch(p.degree, p.n_ctrl, p.ctrl.reshape(-1, 3), None, p.knots)
+    with pytest.raises(sa.SAError) as e:
+        ctx.step(0.5, 1e-5, 1)
+    assert e.value.status == sa.SA_ERR_STATE
+    m = wl.material
+    ctx.set_material(m.k, m.rho, m.cp, m.T_c)
+    s = wl.scan
+    ctx.set_scan(s.path, s.seg_on, s.power, s.absorptivity, s.speed, s.spot_radius)
+    with pytest.raises(sa.SAError) as e:
+        ctx.step(1.5, 1e-5, 1)
+    assert e.value.status == sa.SA_ERR_ARG
+    ctx.step(0.5, 1e-5, 2)
+    with pytest.raises(sa.SAError) as e:
+        ctx.step(0.5, 2e-5, 1)
+    assert e.value.status == sa.SA_ERR_ARG
+    # a capped PCG reports non-convergence and the context stays usable
+    c3 = gpu_context(wl, sa.SA_FP64, pcg_max_iter=1, pcg_tol=1e-15)
+    with pytest.raises(sa.SAError) as e:
+        c3.step(0.5, wl.dt, 3)
+    assert e.value.status == sa.SA_ERR_NOT_CONVERGED
+    assert np.isfinite(c3.field(sa.SA_FIELD_THAT)).all()
+
+
+def test_full_size_block_sampled(sa):
+    """64x64x16 elements (78,408 control points), degree 2, in the launch
+    configuration of the benchmark (mixed history sum, graph replay): the
+    history sums at sampled lateral points against the oracle evaluated point
+    by point; sampled rows of M and K against the oracle's element sums; and
+    the theta-system residual of the computed step."""
+    import torch
+    from oracle import assembly, pointsource
+    from oracle.geometry import PatchGeom
+    wl = W.block_meander(n_tracks=20, theta=0.5)
+    s = torch.cuda.Stream()
+    ctx = gpu_context(wl, sa.SA_MIXED, cuda_stream=s, use_graph=1)
+    n_steps = 700
+    T_prev = None
+    F_prev = None
+    ctx.step(wl.theta, wl.dt, n_steps - 1)
+    T_prev = ctx.field(sa.SA_FIELD_THAT)
+    F_prev = ctx.field(sa.SA_FIELD_F)
+    st = ctx.step(wl.theta, wl.dt, 1)
+    assert st.n_active_sources == n_steps
+    geom = PatchGeom(wl.patch)
+    from oracle import sources as osrc
+    xs = osrc.discretize(wl.scan, wl.dt)
+    E = osrc.energy(wl.scan, wl.dt)
+    age = pointsource.ages(n_steps, n_steps, wl.dt, wl.material, wl.scan.spot_radius)
+    s_gpu = ctx.field(sa.SA_FIELD_DTDN_LAT)
+    rng = np.random.default_rng(1)
+    sizes = ctx.sizes()
+    # include the points nearest to the laser (largest flux) and random ones
+    idx = np.unique(np.concatenate([np.argsort(-np.abs(s_gpu))[:32],
+                                    rng.integers(0, sizes.q_lat, 96)]))
+    ref = np.empty(len(idx))
+    for t, q in enumerate(idx):
+        f, xi, spans = lateral_xi(geom, int(q))
+        dofs, R, dR, x, J = geom.local_eval(xi, spans)
+        nvec = {0: -1, 1: 1, 2: -1, 3: 1}[f] * np.eye(3)[{0: 0, 1: 0, 2: 1, 3: 1}[f]]
+        ref[t] = pointsource.dTdn_tilde(x[None], nvec[None], xs[:n_steps], age, E,
+                                        wl.material)[0]
+    scale = np.abs(s_gpu).max()
+    assert np.abs(s_gpu[idx] - ref).max() <= TOL_MIXED_REL * scale
+    # sampled rows of M and K
+    ptr, col, Mv = ctx.matrix(0)
+    _, _, Kv = ctx.matrix(1)
+    rows = rng.integers(0, sizes.n_dof, 6)
+    rho_cp = wl.material.rho * wl.material.cp
+    for r in rows:
+        els = assembly.elements_touching_dof(geom, int(r))
+        Mo, Ko = assembly.assemble_MK(geom, rho_cp, wl.material.k, elements=els)
+        sl = slice(ptr[r], ptr[r + 1])
+        mo = Mo[int(r)].toarray().ravel()[col[sl]]
+        ko = Ko[int(r)].toarray().ravel()[col[sl]]
+        assert np.abs(Mv[sl] - mo).max() <= 1e-12 * np.abs(mo).max()
+        assert np.abs(Kv[sl] - ko).max() <= 1e-12 * np.abs(ko).max()
+    # theta-system residual of the last step (property at any size)
+    import scipy.sparse as sp
+    n = sizes.n_dof
+    M = sp.csr_matrix((Mv, col, ptr), shape=(n, n))
+    K = sp.csr_matrix((Kv, col, ptr), shape=(n, n))
+    T1 = ctx.field(sa.SA_FIELD_THAT)
+    F1 = ctx.field(sa.SA_FIELD_F)
+    th, dt = wl.theta, wl.dt
+    dirm = geom.dirichlet_dofs()
+    lhs = (M / dt + th * K) @ T1
+    rhs = (M / dt - (1 - th) * K) @ T_prev + th * F1 + (1 - th) * F_prev
+    res = np.linalg.norm((lhs - rhs)[~dirm]) / np.linalg.norm(rhs[~dirm])
+    assert res <= 1e-9, res

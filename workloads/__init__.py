@@ -243,3 +243,41 @@ def batched_instance(instance_id: int, n_steps=2000) -> Workload:
     return Workload(f"batched_{instance_id}", patch, MAT_DEFAULT, scan, dt=5e-6,
                     theta=0.5, n_steps=n_steps,
                     meta=dict(instance_id=instance_id, seed=SEED_BASE + instance_id))
+
+
+def distorted_block(weights=False, seed=3, n_el=(3, 3, 2), size=(1e-3, 0.8e-3, 0.5e-3),
+                    degree=2, jitter=0.04e-3, faces=DEFAULT_FACES) -> Patch:
+    """A cuboid patch whose interior and side control points are moved by a
+    seeded jitter (top plane kept flat); optional random weights in
+    [0.8, 1.2] make it a genuine NURBS patch."""
+    rng = np.random.default_rng(seed)
+    patch = cuboid_patch(size, n_el, degree, faces=faces)
+    c = patch.ctrl.copy()
+    inner = c[1:-1, 1:-1, 1:-1]
+    inner += rng.uniform(-jitter, jitter, inner.shape)
+    c[:-1, :, 0, 0] += rng.uniform(-0.75 * jitter, 0.75 * jitter, c[:-1, :, 0, 0].shape)
+    c[:-1, 0, :, 1] += rng.uniform(-0.75 * jitter, 0.75 * jitter, c[:-1, 0, :, 1].shape)
+    patch.ctrl = c
+    if weights:
+        patch.weights = rng.uniform(0.8, 1.2, c.shape[:3])
+    return patch
+
+
+def quarter_cylinder_part(n_refine=1) -> Patch:
+    """The quarter-cylinder part of Section 3.1 (Table 2 control net, knot
+    vectors printed with it, middle arc weights cos(pi/8)), extruded from
+    z = 0 to the printed top z = 2 mm; degree (2, 1, 1).  ``n_refine`` > 1 is
+    not offered here (the printed net is used as is)."""
+    r2 = np.sqrt(2.0)
+    b1 = [(1, 0), (1, r2 - 1), (2 - r2 / 2, r2 / 2), (3 - r2, 1), (2, 1)]
+    b2 = [(0, 0), (0, 1), (0, 2), (1, 2), (2, 2)]
+    ctrl = np.zeros((2, 2, 5, 3))
+    for i in range(5):
+        for k, z in enumerate((0.0, 2.0)):
+            ctrl[k, 0, i] = [b1[i][0], b1[i][1], z]
+            ctrl[k, 1, i] = [b2[i][0], b2[i][1], z]
+    wm = np.cos(np.pi / 8)
+    w = np.broadcast_to(np.array([1, wm, 1, wm, 1.0]), (2, 2, 5)).copy()
+    knots = [np.array([0, 0, 0, 0.5, 0.5, 1, 1, 1.0]), np.array([0, 0, 1, 1.0]),
+             np.array([0, 0, 1, 1.0])]
+    return Patch(degree=(2, 1, 1), knots=knots, ctrl=ctrl * 1e-3, weights=w)
