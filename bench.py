@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of the per-step hot path on one GB300.
+
+Workload: the 4 x 4 x 1 mm block as one degree-2 B-spline patch with
+64 x 64 x 16 elements (78,408 control points, 36,864 lateral and 36,864
+bottom quadrature points), a 20-track meander (3.5 mm tracks, 0.1 mm hatch,
+P = 250 W, v = 1.2 m/s, dt = 5 us, theta = 0.5), full history kept.  The
+timed steps start mid-scan (step 5,840: the 10-track point, where a step
+costs the average step of the whole scan, since the active source count
+grows by one per step).
+
+A "step" is one theta-step of the whole hot path: source coefficients,
+history sums at every boundary quadrature point, boundary integrals, bottom
+projection, theta right-hand side, PCG.  ``value`` is theta-steps/s of the
+mixed path (FP32 history sum, FP64 elsewhere) replayed as CUDA graphs with
+the inputs resident in HBM; the plain FP64 path is timed beside it.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
+bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point-source evals/s and θ-steps/s, mixed+learned vs plain FP64, one GB300"
+UNIT = "theta-steps/s"
+START_STEP = 5840
+N_MONITOR = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--start-step", type=int, default=START_STEP)
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(dev):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                              "-lms", "200", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(h):
+    p, path = h
+    if p is not None:
+        p.terminate()
+        try:
+            p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            p.kill()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(path)
+    except OSError:
+        pass
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of one step
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import numpy as np
+    import workloads as W
+    from oracle import pointsource, sources
+    from oracle.geometry import PatchGeom
+    wl = W.block_meander(20, theta=0.5)
+    geom = PatchGeom(wl.patch)
+    xs = sources.discretize(wl.scan, wl.dt)
+    E = sources.energy(wl.scan, wl.dt)
+    n = args.start_step
+    age = pointsource.ages(n, n, wl.dt, wl.material, wl.scan.spot_radius)
+    rng = np.random.default_rng(0)
+    lat = geom.face_points(0)
+    bot = geom.face_points(4)
+    q_lat_full = 4 * len(lat["x"])
+    q_bot_full = len(bot["x"])
+    n_pts = 128
+    il = rng.integers(0, len(lat["x"]), n_pts)
+    ib = rng.integers(0, len(bot["x"]), n_pts)
+
+    def one():
+        t0 = time.perf_counter()
+        pointsource.dTdn_tilde(lat["x"][il], lat["n"][il], xs[:n], age, E, wl.material)
+        pointsource.T_tilde(bot["x"][ib], xs[:n], age, E, wl.material)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    t = float(np.mean(ts))
+    pairs_sample = 2 * n_pts * n
+    evals = pairs_sample / t
+    pairs_step = (q_lat_full + q_bot_full) * n
+    steps_per_s = evals / pairs_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": steps_per_s, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / steps_per_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name + f" mid-scan step {n}", "start_step": n},
+        "point_source_evals_per_s": evals,
+        "cpu_baseline": {"value": steps_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle history sums on {n_pts} lateral + {n_pts} bottom "
+                                   f"points x {n} sources per step, scaled to the "
+                                   f"{q_lat_full + q_bot_full} points of one step; the oracle's "
+                                   "linear solve is not included"},
+        "e2e": {"value": steps_per_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline_block(wl, n, seconds_target=10.0):
+    import numpy as np
+    from oracle import pointsource, sources
+    from oracle.geometry import PatchGeom
+    geom = PatchGeom(wl.patch)
+    xs = sources.discretize(wl.scan, wl.dt)
+    E = sources.energy(wl.scan, wl.dt)
+    age = pointsource.ages(n, n, wl.dt, wl.material, wl.scan.spot_radius)
+    lat = geom.face_points(0)
+    bot = geom.face_points(4)
+    q_full = 4 * len(lat["x"]) + len(bot["x"])
+    rng = np.random.default_rng(0)
+    n_pts, spent, pairs = 256, 0.0, 0
+    while spent < seconds_target:
+        il = rng.integers(0, len(lat["x"]), n_pts)
+        ib = rng.integers(0, len(bot["x"]), n_pts)
+        t0 = time.perf_counter()
+        pointsource.dTdn_tilde(lat["x"][il], lat["n"][il], xs[:n], age, E, wl.material)
+        pointsource.T_tilde(bot["x"][ib], xs[:n], age, E, wl.material)
+        spent += time.perf_counter() - t0
+        pairs += 2 * n_pts * n
+    evals = pairs / spent
+    return {"value": evals / (q_full * n), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle history sums on {pairs // n} sampled boundary points x {n} "
+                      f"sources ({spent:.1f} s), scaled to the {q_full} points of one step; "
+                      "the oracle's linear solve is not included",
+            "point_source_evals_per_s": evals}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2511_20432_gb300 as sa
+    import workloads as W
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = W.block_meander(20, theta=0.5)
+    th, dt = wl.theta, wl.dt
+    stream = torch.cuda.Stream()
+    ctx = sa.context_from_workload(wl, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
+    sz = ctx.sizes()
+    q_pts = sz.q_lat + sz.q_bot
+    n0 = args.start_step
+    ctx.step(th, dt, n0)                       # untimed fast-forward to mid-scan
+    ctx.step(th, dt, args.warmup)              # warm-up (graph instantiated, caches warm)
+    state = ctx.get_state()
+    K = args.steps
+    n_first = n0 + args.warmup + 1
+    pairs = q_pts * sum(min(n_first + i, sz.n_src) for i in range(K))
+
+    # ---- timed region: K graph replays of the mixed path ------------------
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(local)
+    e0.record(stream)
+    ctx.step(th, dt, K, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stats = ctx.step(th, dt, 0)                # counters accumulated over the timed steps
+    iters_avg = stats.pcg_iters_total / K
+    value = world * K / (ms / 1e3)
+    evals = world * pairs / (ms / 1e3)
+
+    # ---- stage breakdown (CUDA events on the launching stream) --------------
+    K_t = min(K, 40)
+    ctx_t = sa.context_from_workload(wl, precision=sa.SA_MIXED, cuda_stream=stream, stage_timing=1)
+    ctx_t.step(th, dt, 0)
+    ctx_t.set_state(*state)
+    ctx_t.step(th, dt, 2)
+    ctx_t.stage_times()
+    st_t = ctx_t.step(th, dt, K_t)
+    stage_ms, k_timed = ctx_t.stage_times()
+    stage_avg = {k: v / k_timed for k, v in stage_ms.items()}
+    iters_t = st_t.pcg_iters_total / K_t
+    pairs_t = q_pts * (min(state[0] + 3 + K_t // 2, sz.n_src))
+    ctx_t.close()
+
+    # ---- plain FP64 path at the same point of the scan ------------------------
+    K64 = min(K, 12)
+    ctx64 = sa.context_from_workload(wl, precision=sa.SA_FP64, cuda_stream=stream, use_graph=1)
+    ctx64.step(th, dt, 0)
+    ctx64.set_state(*state)
+    ctx64.step(th, dt, 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx64.step(th, dt, K64, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    fp64_steps = K64 / (ms64 / 1e3)
+    ctx64.close()
+
+    # ---- end to end through the public API with host buffers -------------------
+    rng = np.random.default_rng(3)
+    mon = np.column_stack([rng.uniform(0.2e-3, 3.8e-3, N_MONITOR), rng.uniform(0.2e-3, 3.8e-3, N_MONITOR),
+                           rng.uniform(0.5e-3, 1.0e-3, N_MONITOR)])
+    mon = np.ascontiguousarray(mon)
+    K_e = min(K, 100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K_e):
+        ctx.step(th, dt, 1)                     # synchronous: status read back
+        T_mon = ctx.eval_T(mon)                 # host points in, host temperatures out
+    t_e2e = time.perf_counter() - t0
+    e2e = world * K_e / t_e2e
+    assert np.isfinite(T_mon).all()
+
+    # ---- roofline of the dominant stage ---------------------------------------------
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    total = sum(stage_avg.values())
+    shares = {k: v / total for k, v in stage_avg.items()}
+    dom = max(stage_avg, key=stage_avg.get)
+    n_free, nnz_a = sz.n_free, sz.nnz_a
+    pcg_bytes = iters_t * (12 * nnz_a + 100 * n_free) + 40 * n_free
+    kernels = {
+        "pcg": {"bound": "hbm", "bytes_per_launch": pcg_bytes, "ms": stage_avg["pcg"],
+                "achieved_gbs": pcg_bytes / (stage_avg["pcg"] * 1e-3) / 1e9,
+                "iters_per_step": iters_t},
+        "history": {"bound": "alu", "pairs_per_launch": pairs_t, "ms": stage_avg["history"],
+                    "achieved_gpairs": pairs_t / (stage_avg["history"] * 1e-3) / 1e9,
+                    "peak_gpairs": n_sm * sm_max * 1e6 * 16 / 1e9},
+    }
+    if dom == "history":
+        k = kernels["history"]
+        roof = {"bound": "alu", "achieved": k["achieved_gpairs"], "peak": k["peak_gpairs"],
+                "unit": "Gpairs/s", "frac": k["achieved_gpairs"] / k["peak_gpairs"],
+                "traffic": None, "kernel": "k_history_mixed",
+                "peak_basis": f"{n_sm} SMs x {sm_max:.0f} MHz x 16 pairs/clk/SM (MUFU ex2 16/clk)"}
+    else:
+        k = kernels["pcg"]
+        roof = {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": k["achieved_gbs"] / hbm if hbm else None, "traffic": None,
+                "kernel": "k_pcg (free block)", "peak_basis": "hbm_gbs of measured"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": wl.name + f" mid-scan from step {n0}", "n_dof": sz.n_dof,
+                   "q_lat": sz.q_lat, "q_bot": sz.q_bot, "nnz_a": nnz_a,
+                   "active_sources_first": n_first, "theta": th, "dt": dt,
+                   "precision": "mixed: FP32 history sum, FP64 boundary integrals and PCG",
+                   "l2": "per-step inputs larger than L2 (M, K and A in CSR, ~370 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "point_source_evals_per_s": evals,
+        "fp64_steps_per_s": world * fp64_steps,
+        "mixed_over_fp64": value / (world * fp64_steps),
+        "pcg_iters_per_step": iters_avg,
+        "stage_ms": stage_avg, "stage_share": shares, "kernels": kernels,
+        "roofline": roof,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
+                "d2h_bytes_per_step": N_MONITOR * 8 + 96},
+        "gpu_launches": 7 * K,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline_block(wl, n0)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

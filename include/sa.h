@@ -70,6 +70,9 @@ typedef struct sa_options {
     int device;                /* CUDA device ordinal; -1 = the current device   */
     int hist_points_per_lane;  /* history-sum tile: points per lane (1,2,4); 0=auto*/
     int hist_warps;            /* history-sum tile: warps splitting the sources (4,8); 0=auto */
+    int stage_timing;          /* 1: CUDA events around every stage of each step (direct
+                                  launches, the graph path is off while set); the step then
+                                  synchronises; read the times with sa_get_stage_times   */
 } sa_options;
 
 /* Fill o with the defaults listed above. */
@@ -81,7 +84,7 @@ sa_status sa_create(const sa_options* o, sa_ctx** out);
 /*
  * Geometry: one trivariate NURBS patch (Section 2.3, the map Phi and the
  * basis of degree p on the knot vectors).
- *   degree[d]   polynomial degree in parametric direction d (1..4)
+ *   degree[d]   polynomial degree in parametric direction d (1..3)
  *   n_ctrl[d]   control points in direction d
  *   ctrl_xyz    n_ctrl[0]*n_ctrl[1]*n_ctrl[2]*3 doubles (host), index
  *               ((k*n1 + j)*n0 + i)*3 + c, xi index i fastest
@@ -125,10 +128,12 @@ sa_status sa_set_scan(sa_ctx* ctx, const double* path_xyz, int nv,
                       const unsigned char* seg_on, double power, double absorptivity,
                       double speed, double spot_radius);
 
+/* Counters cover every step since the previous call that returned stats
+ * (steps enqueued with stats == NULL included). */
 typedef struct sa_step_stats {
-    int steps_done;            /* steps completed in this call                     */
+    int steps_done;            /* steps enqueued by this call                      */
     int pcg_iters_last;        /* PCG iterations of the last step                  */
-    int pcg_iters_total;       /* summed over the steps of this call               */
+    int pcg_iters_total;       /* summed over the covered steps                    */
     int pcg_iters_max;
     int bot_iters_total;       /* iterations of the bottom (Dirichlet) projection  */
     double rel_res_last;       /* ||r||/||b|| at exit of the last step's PCG       */
@@ -196,6 +201,20 @@ sa_status sa_get_matrix(sa_ctx* ctx, int which, long long* rowptr, int* colind, 
  * sources are recomputed from the scan.  Host buffers; synchronous. */
 sa_status sa_get_state(sa_ctx* ctx, long long* n, double* T_hat, double* F);
 sa_status sa_set_state(sa_ctx* ctx, long long n, const double* T_hat, const double* F);
+
+/* Stages of one step, in launch order. */
+enum { SA_STAGE_PROLOGUE = 0,  /* source coefficients of the step                       */
+       SA_STAGE_HISTORY = 1,   /* history sums at the lateral and bottom points          */
+       SA_STAGE_GATHER = 2,    /* F^{n+1} and the bottom right-hand side                 */
+       SA_STAGE_BOTTOM = 3,    /* bottom L2 projection (PCG)                             */
+       SA_STAGE_RHS = 4,       /* theta right-hand side and initial residual             */
+       SA_STAGE_PCG = 5,       /* free-block PCG                                         */
+       SA_STAGE_FINALIZE = 6,  /* Dirichlet values, F^n <- F^{n+1}, n <- n+1            */
+       SA_N_STAGES = 7 };
+/* Milliseconds per stage accumulated over the steps run with stage_timing
+ * since the previous call (which resets them); *steps = number of steps.
+ * ms: SA_N_STAGES doubles (host). */
+sa_status sa_get_stage_times(sa_ctx* ctx, double* ms, long long* steps);
 
 void sa_destroy(sa_ctx* ctx);
 const char* sa_status_str(sa_status s);

@@ -19,13 +19,15 @@ SA_OK, SA_ERR_ARG, SA_ERR_GEOMETRY, SA_ERR_STATE, SA_ERR_CUDA, SA_ERR_OOM, \
 SA_FP64, SA_MIXED = 0, 1
 SA_FACE_NONE, SA_FACE_NEUMANN, SA_FACE_DIRICHLET = 0, 1, 2
 SA_FIELD_THAT, SA_FIELD_F, SA_FIELD_DTDN_LAT, SA_FIELD_TT_BOT, SA_FIELD_LAT_X, SA_FIELD_BOT_X = range(6)
+STAGES = ("prologue", "history", "gather", "bottom", "rhs", "pcg", "finalize")
 
 
 class sa_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("pcg_tol", C.c_double), ("pcg_max_iter", C.c_int),
                 ("half_space_factor", C.c_double), ("cuda_stream", C.c_void_p),
                 ("use_graph", C.c_int), ("device", C.c_int),
-                ("hist_points_per_lane", C.c_int), ("hist_warps", C.c_int)]
+                ("hist_points_per_lane", C.c_int), ("hist_warps", C.c_int),
+                ("stage_timing", C.c_int)]
 
 
 class sa_step_stats(C.Structure):
@@ -69,6 +71,7 @@ def _load():
         "sa_get_matrix": (I, [P, I, P, P, P]),
         "sa_get_state": (I, [P, C.POINTER(LL), P, P]),
         "sa_set_state": (I, [P, LL, P, P]),
+        "sa_get_stage_times": (I, [P, P, C.POINTER(LL)]),
         "sa_destroy": (V, [P]),
         "sa_status_str": (C.c_char_p, [I]),
         "sa_last_error": (C.c_char_p, [P]),
@@ -203,6 +206,12 @@ class Context:
         val = np.empty(nnz.value)
         _check(self.ptr, lib.sa_get_matrix(self.ptr, int(which), _ptr(ptr), _ptr(col), _ptr(val)))
         return ptr, col, val
+
+    def stage_times(self):
+        ms = np.zeros(len(STAGES))
+        k = C.c_longlong()
+        _check(self.ptr, lib.sa_get_stage_times(self.ptr, _ptr(ms), C.byref(k)))
+        return dict(zip(STAGES, ms)), k.value
 
     def get_state(self):
         n = self.sizes().n_dof

@@ -191,6 +191,12 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
         delete c;
         return SA_ERR_CUDA;
     }
+    if (opt.stage_timing)
+        for (int i = 0; i <= SA_N_STAGES; ++i)
+            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+                delete c;
+                return SA_ERR_CUDA;
+            }
     c->hist_P = opt.hist_points_per_lane ? opt.hist_points_per_lane : 4;
     c->hist_W = opt.hist_warps ? opt.hist_warps : 8;
     *out = c;
@@ -200,6 +206,8 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
 void sa_destroy(sa_ctx* c) {
     if (!c) return;
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (int i = 0; i <= SA_N_STAGES; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;
 }
 
@@ -757,7 +765,13 @@ sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
 sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     cudaStream_t s = c->stream;
     const double alpha = c->k / (c->rho * c->cp);
+    const bool timing = c->opt.stage_timing != 0;
+#define SA_MARK(i)                                                        \
+    do {                                                                  \
+        if (timing) SA_CUDA(c, cudaEventRecord(c->ev[i], s));             \
+    } while (0)
     cudaError_t e;
+    SA_MARK(SA_STAGE_PROLOGUE);
     e = launch_prologue(c->st.p, 0, c->st.p, c->n_src, c->src_pos.p, dt, alpha,
                         c->spot_radius * c->spot_radius / (8.0 * alpha),
                         c->opt.half_space_factor * c->E / (c->rho * c->cp), c->opt.precision,
@@ -766,15 +780,18 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                         c->opt.precision == SA_MIXED ? c->src32T.p : nullptr,
                         c->opt.precision == SA_MIXED ? c->src32F.p : nullptr, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "prologue");
+    SA_MARK(SA_STAGE_HISTORY);
     e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat, c->q_bot,
                        c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p, c->x_ref, c->y_ref,
                        c->z_top, c->src32F.p, c->src32T.p, c->src64F.p, c->src64T.p,
                        c->s_lat.p, c->tt_bot.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "history");
+    SA_MARK(SA_STAGE_GATHER);
     e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
                       c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
                       c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
+    SA_MARK(SA_STAGE_BOTTOM);
     if (c->n_dir > 0) {
         // x0 = g^n (the Dirichlet part of the state)
         e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
@@ -787,18 +804,32 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                        c->opt.pcg_max_iter, grid_bot, c->pcg_block, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
+    SA_MARK(SA_STAGE_RHS);
     e = launch_theta_rhs(c->n_free, c->mk_ptr.p, c->mk_col.p, c->M.p, c->K.p, c->dperm.p,
                          c->d_iperm_free.p, c->That.p, c->gnew.p, c->F0.p, c->F1.p,
                          c->rho * c->cp / dt, c->k, theta, c->rhs.p, c->r0.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
+    SA_MARK(SA_STAGE_PCG);
     e = launch_pcg(0, c->n_free, c->a_ptr.p, c->a_col.p, c->a_val.p, c->a_dinv.p, c->rhs.p,
                    c->r0.p, c->That.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p, c->wq.p,
                    c->partials.p, c->st.p, c->opt.pcg_tol, c->opt.pcg_max_iter, c->pcg_grid,
                    c->pcg_block, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
+    SA_MARK(SA_STAGE_FINALIZE);
     e = launch_finalize(c->n_dir, c->n_free, c->n_dof, c->gnew.p, c->That.p, c->F1.p, c->F0.p,
                         c->st.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "finalize");
+    SA_MARK(SA_N_STAGES);
+#undef SA_MARK
+    if (timing) {
+        SA_CUDA(c, cudaEventSynchronize(c->ev[SA_N_STAGES]));
+        for (int i = 0; i < SA_N_STAGES; ++i) {
+            float ms = 0.f;
+            SA_CUDA(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+            c->stage_ms[i] += ms;
+        }
+        c->stage_steps += 1;
+    }
     return SA_OK;
 }
 
@@ -830,17 +861,7 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
     if ((st = init_state_if_needed(c))) return st;
     if ((st = ensure_operator(c, theta, dt))) return st;
     cudaStream_t s = c->stream;
-    if (stats) {
-        // reset the accumulated counters (not n, not the barrier words)
-        DevStatus z;
-        std::memset(&z, 0, sizeof(z));
-        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->err, &z.err, offsetof(DevStatus, n), cudaMemcpyHostToDevice, s));
-        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->iters_total, &z.iters_total,
-                                   offsetof(DevStatus, pad) - offsetof(DevStatus, iters_total),
-                                   cudaMemcpyHostToDevice, s));
-        SA_CUDA(c, cudaStreamSynchronize(s));
-    }
-    const bool graph = c->opt.use_graph && s != nullptr;
+    const bool graph = c->opt.use_graph && s != nullptr && !c->opt.stage_timing;
     for (int i = 0; i < n_steps; ++i) {
         if (graph) {
             if (!c->graph_exec) {
@@ -872,11 +893,31 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
         stats->rel_res_last = h.rel_res;
         stats->n_active_sources = h.n_active;
         stats->step_index = h.n;
+        // reset the counters read above (not n, not the barrier words): the
+        // next stats report covers the steps since this call
+        DevStatus z;
+        std::memset(&z, 0, sizeof(z));
+        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->err, &z.err, offsetof(DevStatus, n), cudaMemcpyHostToDevice, s));
+        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->iters_total, &z.iters_total,
+                                   offsetof(DevStatus, pad) - offsetof(DevStatus, iters_total),
+                                   cudaMemcpyHostToDevice, s));
+        SA_CUDA(c, cudaStreamSynchronize(s));
         if (h.err & SA_DEV_TIMEOUT) return sa_fail(c, SA_ERR_TIMEOUT, "a device-side wait timed out");
         if (h.err & SA_DEV_NAN) return sa_fail(c, SA_ERR_NAN, "non-finite value in the solve");
         if (h.err & (SA_DEV_NOT_CONVERGED | SA_DEV_BOT_NOT_CONVERGED))
             return sa_fail(c, SA_ERR_NOT_CONVERGED, "PCG did not converge (flags %d, rel res %g)", h.err, h.rel_res);
     }
+    return SA_OK;
+}
+
+sa_status sa_get_stage_times(sa_ctx* c, double* ms, long long* steps) {
+    if (!c || !ms || !steps) return SA_ERR_ARG;
+    for (int i = 0; i < SA_N_STAGES; ++i) {
+        ms[i] = c->stage_ms[i];
+        c->stage_ms[i] = 0.0;
+    }
+    *steps = c->stage_steps;
+    c->stage_steps = 0;
     return SA_OK;
 }
 

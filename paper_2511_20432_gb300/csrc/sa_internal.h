@@ -187,6 +187,11 @@ struct sa_ctx {
     DBuf<double> ecent;             // physical element centres (eval initial guess)
     DBuf<double4> evT, evF;         // FP64 source coefficients at the current step
     DBuf<double> eval_pts, eval_out;
+
+    // stage timing (sa_options::stage_timing)
+    cudaEvent_t ev[SA_N_STAGES + 1] = {};
+    double stage_ms[SA_N_STAGES] = {};
+    long long stage_steps = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -85,7 +85,7 @@ def _lockstep(sa, wl, precision, n_check, every=1, **opts):
     """Step oracle and GPU together; return max relative errors of the
     history sums, F and T^ over the checked steps."""
     m = _oracle(wl)
-    ctx = gpu_context(wl, precision, pcg_tol=1e-13 if precision == sa.SA_FP64 else 1e-10,
+    ctx = gpu_context(wl, precision, pcg_tol=1e-15 if precision == sa.SA_FP64 else 1e-10,
                       **opts)
     err = dict(s_lat=0.0, tt_bot=0.0, F=0.0, That=0.0, That_abs=0.0)
     for step in range(n_check):
