@@ -98,6 +98,52 @@ void build_w_csr(int n_rows, const std::vector<int>& erow, const std::vector<int
     }
 }
 
+// SELL-32 layout of a row list: rows r = 0..n-1 with entries
+// (col, src) in [ptr[r], ptr[r+1]); diag = storage index of col == diag_col[r]
+// (diag_col may be empty: no diagonal needed).
+struct SellHost {
+    int n = 0, n_slices = 0;
+    std::vector<long long> sptr;
+    std::vector<int> col, src, diag;
+};
+
+void build_sell(int n, const std::vector<long long>& ptr, const std::vector<int>& col,
+                const std::vector<int>& src, const std::vector<int>& diag_col, SellHost& out) {
+    out.n = n;
+    out.n_slices = (n + 31) / 32;
+    out.sptr.assign(out.n_slices + 1, 0);
+    for (int s = 0; s < out.n_slices; ++s) {
+        long long w = 0;
+        for (int l = 0; l < 32; ++l) {
+            const int r = s * 32 + l;
+            if (r < n) w = std::max(w, ptr[r + 1] - ptr[r]);
+        }
+        out.sptr[s + 1] = out.sptr[s] + 32 * w;
+    }
+    const long long tot = out.sptr[out.n_slices];
+    out.col.assign(tot, 0);
+    out.src.assign(tot, -1);
+    out.diag.assign(std::max(n, 1), 0);
+    for (int s = 0; s < out.n_slices; ++s) {
+        const long long w = (out.sptr[s + 1] - out.sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const int r = s * 32 + l;
+            for (long long k = 0; k < w; ++k) {
+                const long long e = out.sptr[s] + 32 * k + l;
+                if (r < n && ptr[r] + k < ptr[r + 1]) {
+                    const long long t = ptr[r] + k;
+                    out.col[e] = col[t];
+                    out.src[e] = src[t];
+                    if (!diag_col.empty() && col[t] == diag_col[r]) out.diag[r] = (int)e;
+                } else {
+                    out.col[e] = r < n ? (diag_col.empty() ? 0 : diag_col[r]) : 0;
+                    out.src[e] = -1;
+                }
+            }
+        }
+    }
+}
+
 template <class T>
 cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
     cudaError_t e = b.alloc(v.size());
@@ -105,6 +151,17 @@ cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
     if (v.empty()) return cudaSuccess;
     return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
+
+#define SA_UPLOAD_SELL(ctx, dev, host)          \
+    do {                                          \
+        (dev).n = (host).n;                       \
+        (dev).n_slices = (host).n_slices;         \
+        (dev).n_stored = (long long)(host).col.size(); \
+        SA_UPLOAD(ctx, (dev).sptr, (host).sptr);  \
+        SA_UPLOAD(ctx, (dev).col, (host).col);    \
+        SA_UPLOAD(ctx, (dev).src, (host).src);    \
+        SA_UPLOAD(ctx, (dev).diag, (host).diag);  \
+    } while (0)
 
 #define SA_UPLOAD(ctx, buf, vec)                                                              \
     do {                                                                                      \
@@ -536,6 +593,19 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                                              c->wbot_col.p, c->wbot_val.p, cooD.p, cooR.p, nfb,
                                              c->n_free, c->mbot_val.p, c->mbot_dinv.p, s);
             if (e != cudaSuccess) return sa_cuda_fail(c, e, "M_bot");
+            {
+                std::vector<long long> p64(mptr.begin(), mptr.end());
+                std::vector<int> srcs(mcol.size()), dcol(c->n_dir);
+                std::iota(srcs.begin(), srcs.end(), 0);
+                std::iota(dcol.begin(), dcol.end(), 0);
+                SellHost sh;
+                build_sell(c->n_dir, p64, mcol, srcs, dcol, sh);
+                SA_UPLOAD_SELL(c, c->mbot_s, sh);
+                SA_ALLOC(c, c->mbot_sval, sh.col.size());
+                e = launch_sell_fill(c->mbot_s.n_stored, c->mbot_s.src.p, c->mbot_val.p, 1.0,
+                                     nullptr, 0.0, c->mbot_sval.p, s);
+                if (e != cudaSuccess) return sa_cuda_fail(c, e, "M_bot SELL");
+            }
             SA_CUDA(c, cudaStreamSynchronize(s));   // cooR/cooD freed on return
         }
         SA_CUDA(c, cudaStreamSynchronize(s));
@@ -611,30 +681,46 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         if (hbad) return sa_fail(c, SA_ERR_GEOMETRY, "det J <= 0 at a Gauss point (inverted or degenerate patch)");
     }
 
-    // ---- free-free operator pattern -------------------------------------------------
+    // ---- free-free operator A and the free rows of M, K (SELL) ---------------
     {
-        std::vector<int> a_ptr(c->n_free + 1, 0), a_col, a_src;
+        if (c->nnz > (long long)INT32_MAX)
+            return sa_fail(c, SA_ERR_ARG, "operator too large for 32-bit slots");
+        std::vector<long long> a_ptr(c->n_free + 1, 0), r_ptr(c->n_free + 1, 0);
+        std::vector<int> a_col, a_src, r_col, r_src, dcol(c->n_free);
         a_col.reserve((size_t)c->nnz);
         a_src.reserve((size_t)c->nnz);
+        r_col.reserve((size_t)c->nnz);
+        r_src.reserve((size_t)c->nnz);
         for (int i = 0; i < c->n_free; ++i) {
             const int r = c->iperm[i];
+            dcol[i] = i;
             for (long long t = mk_ptr[r]; t < mk_ptr[r + 1]; ++t) {
                 const int j = c->perm[mk_col[t]];
+                r_col.push_back(j);
+                r_src.push_back((int)t);
                 if (j < c->n_free) {
                     a_col.push_back(j);
                     a_src.push_back((int)t);
                 }
             }
-            a_ptr[i + 1] = (int)a_col.size();
+            a_ptr[i + 1] = (long long)a_col.size();
+            r_ptr[i + 1] = (long long)r_col.size();
         }
-        if (c->nnz > (long long)INT32_MAX)
-            return sa_fail(c, SA_ERR_ARG, "operator too large for 32-bit slots");
         c->nnz_a = (long long)a_col.size();
-        SA_UPLOAD(c, c->a_ptr, a_ptr);
-        SA_UPLOAD(c, c->a_col, a_col);
-        SA_UPLOAD(c, c->a_src, a_src);
-        SA_ALLOC(c, c->a_val, c->nnz_a);
-        SA_ALLOC(c, c->a_dinv, c->n_free);
+        SellHost sa_h, sr_h;
+        build_sell(c->n_free, a_ptr, a_col, a_src, dcol, sa_h);
+        SA_UPLOAD_SELL(c, c->a_s, sa_h);
+        SA_ALLOC(c, c->a_val, sa_h.col.size());
+        SA_ALLOC(c, c->a_dinv, std::max(c->n_free, 1));
+        build_sell(c->n_free, r_ptr, r_col, r_src, dcol, sr_h);
+        SA_UPLOAD_SELL(c, c->r_s, sr_h);
+        SA_ALLOC(c, c->r_M, sr_h.col.size());
+        SA_ALLOC(c, c->r_K, sr_h.col.size());
+        cudaError_t e = launch_sell_fill(c->r_s.n_stored, c->r_s.src.p, c->M.p, 1.0, nullptr, 0.0,
+                                         c->r_M.p, s);
+        if (e == cudaSuccess)
+            e = launch_sell_fill(c->r_s.n_stored, c->r_s.src.p, c->K.p, 1.0, nullptr, 0.0, c->r_K.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "free-row SELL");
     }
 
     // ---- state and work vectors ---------------------------------------------------
@@ -666,7 +752,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                                                                  pcg_block_size(), 0));
         if (occ < 1) return sa_fail(c, SA_ERR_CUDA, "PCG kernel cannot be resident");
         c->pcg_block = pcg_block_size();
-        c->pcg_grid = c->num_sms * std::min(occ, 2);
+        c->pcg_grid = c->num_sms;   // one co-resident block of 512 threads per SM
         SA_ALLOC(c, c->partials, (size_t)6 * c->pcg_grid);
     }
     SA_CUDA(c, cudaStreamSynchronize(s));
@@ -749,9 +835,9 @@ sa_status ensure_sources(sa_ctx* c, double dt) {
 
 sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
     if (c->op_dt == dt && c->op_theta == theta) return SA_OK;
-    cudaError_t e = launch_build_A(c->nnz_a, c->a_src.p, c->M.p, c->K.p,
-                                   c->rho * c->cp / dt, theta * c->k, c->a_val.p, c->n_free,
-                                   c->a_ptr.p, c->a_col.p, c->a_dinv.p, c->stream);
+    cudaError_t e = launch_sell_fill(c->a_s.n_stored, c->a_s.src.p, c->M.p, c->rho * c->cp / dt,
+                                     c->K.p, theta * c->k, c->a_val.p, c->stream);
+    if (e == cudaSuccess) e = launch_sell_dinv(c->n_free, c->a_s.diag.p, c->a_val.p, c->a_dinv.p, c->stream);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "build A");
     c->op_dt = dt;
     c->op_theta = theta;
@@ -798,19 +884,21 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                             cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
         const int grid_bot = std::max(1, std::min(c->pcg_grid, (c->n_dir + 255) / 256));
-        e = launch_pcg(1, c->n_dir, c->mbot_ptr.p, c->mbot_col.p, c->mbot_val.p, c->mbot_dinv.p,
+        e = launch_pcg(1, c->n_dir, c->mbot_s.n_slices, c->mbot_s.sptr.p, c->mbot_s.col.p,
+                       c->mbot_sval.p, c->mbot_dinv.p,
                        c->bbot.p, nullptr, c->gnew.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p,
                        c->wq.p, c->partials.p, c->st.p, c->opt.pcg_tol,
                        c->opt.pcg_max_iter, grid_bot, c->pcg_block, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
     SA_MARK(SA_STAGE_RHS);
-    e = launch_theta_rhs(c->n_free, c->mk_ptr.p, c->mk_col.p, c->M.p, c->K.p, c->dperm.p,
-                         c->d_iperm_free.p, c->That.p, c->gnew.p, c->F0.p, c->F1.p,
-                         c->rho * c->cp / dt, c->k, theta, c->rhs.p, c->r0.p, s);
+    e = launch_theta_rhs(c->n_free, c->r_s.n_slices, c->r_s.sptr.p, c->r_s.col.p, c->r_M.p,
+                         c->r_K.p, c->That.p, c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt,
+                         c->k, theta, c->rhs.p, c->r0.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     SA_MARK(SA_STAGE_PCG);
-    e = launch_pcg(0, c->n_free, c->a_ptr.p, c->a_col.p, c->a_val.p, c->a_dinv.p, c->rhs.p,
+    e = launch_pcg(0, c->n_free, c->a_s.n_slices, c->a_s.sptr.p, c->a_s.col.p, c->a_val.p,
+                   c->a_dinv.p, c->rhs.p,
                    c->r0.p, c->That.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p, c->wq.p,
                    c->partials.p, c->st.p, c->opt.pcg_tol, c->opt.pcg_max_iter, c->pcg_grid,
                    c->pcg_block, s);

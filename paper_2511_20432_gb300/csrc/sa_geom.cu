@@ -363,20 +363,24 @@ __global__ void k_mbot_fill(int n_rows, const int* mptr, const int* mcol, const 
     }
 }
 
-__global__ void k_build_A(long long nnz_a, const int* a_src, const double* M, const double* K,
-                          double inv_dt, double theta, double* a_val) {
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= nnz_a) return;
-    const int src = a_src[s];
-    a_val[s] = M[src] * inv_dt + theta * K[src];
+// SELL values from a CSR source: out[e] = s1 in1[src[e]] + s2 in2[src[e]]
+// (0 on padding).
+__global__ void k_sell_fill(long long n_stored, const int* src, const double* in1, double s1,
+                            const double* in2, double s2, double* out) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n_stored) return;
+    const int t = src[e];
+    double v = 0.0;
+    if (t >= 0) {
+        v = s1 * in1[t];
+        if (in2) v += s2 * in2[t];
+    }
+    out[e] = v;
 }
 
-__global__ void k_diag_inv(int n, const int* ptr, const int* col, const double* val,
-                           double* dinv) {
+__global__ void k_sell_dinv(int n, const int* diag, const double* val, double* dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int s = ptr[i]; s < ptr[i + 1]; ++s)
-        if (col[s] == i) dinv[i] = 1.0 / val[s];
+    if (i < n) dinv[i] = 1.0 / val[diag[i]];
 }
 
 __global__ void k_points32(int q_lat, int q_bot, const double* lat64, const double* bot64,
@@ -635,14 +639,18 @@ cudaError_t launch_mbot_fill(int n_rows, const int* mptr, const int* mcol, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_A(long long nnz_a, const int* a_src, const double* M, const double* K,
-                           double inv_dt, double theta, double* a_val, int n_free,
-                           const int* a_ptr, const int* a_col, double* dinv, cudaStream_t s) {
-    if (nnz_a > 0)
-        k_build_A<<<(unsigned)((nnz_a + 255) / 256), 256, 0, s>>>(nnz_a, a_src, M, K, inv_dt,
-                                                                  theta, a_val);
-    if (n_free > 0)
-        k_diag_inv<<<(n_free + 255) / 256, 256, 0, s>>>(n_free, a_ptr, a_col, a_val, dinv);
+cudaError_t launch_sell_fill(long long n_stored, const int* src, const double* in1, double s1,
+                            const double* in2, double s2, double* out, cudaStream_t s) {
+    if (n_stored == 0) return cudaSuccess;
+    k_sell_fill<<<(unsigned)((n_stored + 255) / 256), 256, 0, s>>>(n_stored, src, in1, s1, in2, s2,
+                                                                  out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_dinv(int n, const int* diag, const double* val, double* dinv,
+                             cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_sell_dinv<<<(n + 255) / 256, 256, 0, s>>>(n, diag, val, dinv);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,20 @@ struct DBuf {
     }
 };
 
+// Sliced ELLPACK, slice height 32, column-major inside a slice: entry k of
+// row r = 32 s + l lives at sptr[s] + 32 k + l.  Padding entries have value
+// 0 and column = the row itself (in range).  One warp per slice, lane = row:
+// every value/column load is a coalesced 32-wide access and the lanes'
+// gathers x[col] are contiguous for banded (tensor-product) matrices.
+struct SellDev {
+    int n = 0, n_slices = 0;
+    long long n_stored = 0;
+    DBuf<long long> sptr;     // n_slices + 1
+    DBuf<int> col;            // n_stored
+    DBuf<int> src;            // n_stored: slot in the source CSR, -1 for padding
+    DBuf<int> diag;           // n: storage index of the diagonal entry
+};
+
 // ---------------------------------------------------------------------------
 // the context
 // ---------------------------------------------------------------------------
@@ -151,16 +165,22 @@ struct sa_ctx {
     long long nnz_mbot = 0;
     DBuf<int> mbot_ptr, mbot_col;
     DBuf<double> mbot_val, mbot_dinv;
+    SellDev mbot_s;
+    DBuf<double> mbot_sval;
 
     // M, K: CSR over all control variables, natural order
     long long nnz = 0;
     DBuf<long long> mk_ptr;
     DBuf<int> mk_col;
     DBuf<double> M, K;
-    // free-free operator A = M/dt + theta K, internal indices
+    // free-free operator A = M/dt + theta K, internal indices (SELL)
     long long nnz_a = 0;
-    DBuf<int> a_ptr, a_col, a_src;   // a_src: slot in the natural CSR
+    SellDev a_s;
     DBuf<double> a_val, a_dinv;
+    // free rows of M and K over all columns (internal indices), for the
+    // theta right-hand side (SELL, unit rho c_p and k)
+    SellDev r_s;
+    DBuf<double> r_M, r_K;
 
     // ---- device: scan and history ------------------------------------------
     DBuf<double2> src_pos;    // relative (x - x_ref, y - y_ref)
@@ -238,9 +258,10 @@ cudaError_t launch_mbot_fill(int n_rows, const int* mptr, const int* mcol, const
                              const int* wcol, const double* wval, const int* coo_dof,
                              const double* coo_R, int nfb, int n_free, double* mval,
                              double* dinv, cudaStream_t s);
-cudaError_t launch_build_A(long long nnz_a, const int* a_src, const double* M, const double* K,
-                           double inv_dt, double theta, double* a_val, int n_free,
-                           const int* a_ptr, const int* a_col, double* dinv, cudaStream_t s);
+cudaError_t launch_sell_fill(long long n_stored, const int* src, const double* in1, double s1,
+                            const double* in2, double s2, double* out, cudaStream_t s);
+cudaError_t launch_sell_dinv(int n, const int* diag, const double* val, double* dinv,
+                             cudaStream_t s);
 cudaError_t launch_points32(int q_lat, int q_bot, const double* lat64, const double* bot64,
                             double x_ref, double y_ref, double z_top, float* lat32,
                             float* bot32, cudaStream_t s);
@@ -267,16 +288,16 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, cudaStream_t s);
-cudaError_t launch_theta_rhs(int n_free, const long long* mk_ptr, const int* mk_col,
-                             const double* M, const double* K, const int* perm,
-                             const int* iperm_free, const double* That, const double* gnew,
-                             const double* F0, const double* F1, double inv_dt, double kscale,
-                             double theta, double* rhs, double* r0, cudaStream_t s);
-cudaError_t launch_pcg(int which, int n, const int* ptr, const int* col, const double* val,
-                       const double* dinv, const double* b, const double* r0_or_null, double* x,
-                       double* r, double* z, double* p0, double* p1, double* q,
-                       double* partials, DevStatus* st, double tol, int max_iter, int grid,
-                       int block, cudaStream_t s);
+cudaError_t launch_theta_rhs(int n_free, int n_slices, const long long* sptr, const int* col,
+                             const double* M, const double* K, const double* That,
+                             const double* gnew, const double* F0, const double* F1,
+                             double inv_dt, double kscale, double theta, double* rhs,
+                             double* r0, cudaStream_t s);
+cudaError_t launch_pcg(int which, int n, int n_slices, const long long* sptr, const int* col,
+                       const double* val, const double* dinv, const double* b,
+                       const double* r0_or_null, double* x, double* r, double* z, double* p0,
+                       double* p1, double* q, double* partials, DevStatus* st, double tol,
+                       int max_iter, int grid, int block, cudaStream_t s);
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
                             const double* F1, double* F0, DevStatus* st, cudaStream_t s);
 int pcg_block_size();

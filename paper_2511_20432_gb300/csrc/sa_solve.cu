@@ -65,12 +65,11 @@ __global__ void k_gather(GatherArgs a) {
 // ---------------------------------------------------------------------------
 struct RhsArgs {
     int n_free;
-    const long long* ptr;
-    const int* col;
-    const double* M;
-    const double* K;
-    const int* perm;
-    const int* iperm;
+    int n_slices;
+    const long long* sptr;
+    const int* col;            // internal column indices
+    const double* M;           // unit rho c_p
+    const double* K;           // unit k
     const double* That;
     const double* gnew;
     const double* F0;
@@ -80,16 +79,21 @@ struct RhsArgs {
     double* r0;
 };
 
+// One warp per 32-row slice, lane = free row (SELL storage).
 __global__ void k_theta_rhs(RhsArgs a) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= a.n_free) return;
-    const int nr = a.iperm[i];
+    if (sl >= a.n_slices) return;
+    const int i = sl * 32 + lane;
+    const long long base = a.sptr[sl];
+    const int w = (int)((a.sptr[sl + 1] - base) >> 5);
     double accb = 0.0, acca = 0.0;
-    for (long long s = a.ptr[nr] + lane; s < a.ptr[nr + 1]; s += 32) {
-        const int j = a.perm[a.col[s]];
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+        const long long e = base + 32ll * k + lane;
+        const int j = __ldg(a.col + e);
+        const double m = __ldg(a.M + e) * a.inv_dt, kk = __ldg(a.K + e) * a.kscale;
         const double T = a.That[j];
-        const double m = a.M[s] * a.inv_dt, kk = a.K[s] * a.kscale;
         if (j < a.n_free) {
             accb += m * T - kk * ((1.0 - a.theta) * T);
             acca += (m + a.theta * kk) * T;
@@ -98,9 +102,7 @@ __global__ void k_theta_rhs(RhsArgs a) {
             accb += m * (T - G) - kk * ((1.0 - a.theta) * T + a.theta * G);
         }
     }
-    accb = warp_sum(accb);
-    acca = warp_sum(acca);
-    if (lane == 0) {
+    if (i < a.n_free) {
         const double b = accb + a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i];
         a.rhs[i] = b;
         a.r0[i] = b - acca;
@@ -194,7 +196,8 @@ __device__ double grid_total(const double* part) {
 
 struct PcgArgs {
     int n;
-    const int* ptr;
+    int n_slices;
+    const long long* sptr;     // SELL operator
     const int* col;
     const double* val;
     const double* dinv;
@@ -218,7 +221,9 @@ struct PcgArgs {
 // buffered), so one iteration is two grid phases:
 //   B: p' = z + beta p ; q = A p' ; (p', q)
 //   C: x += alpha p' ; r -= alpha q ; z = D^{-1} r ; (r, r), (r, z)
-// SpMV: one warp per row over a contiguous block of rows per warp.
+// SpMV: SELL-32, one warp per slice (lane = row), slices grid-strided over
+// the warps; the k loop is unrolled so each lane keeps several independent
+// coalesced loads in flight.
 __global__ void __launch_bounds__(512) k_pcg(PcgArgs a) {
     const int n = a.n;
     const int G = gridDim.x;
@@ -226,9 +231,6 @@ __global__ void __launch_bounds__(512) k_pcg(PcgArgs a) {
     const int nwb = blockDim.x >> 5;
     const int gw = blockIdx.x * nwb + (threadIdx.x >> 5);
     const int nw = G * nwb;
-    const int rows_per_warp = (n + nw - 1) / nw;
-    const int row0 = gw * rows_per_warp;
-    const int row1 = min(n, row0 + rows_per_warp);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = G * blockDim.x;
     unsigned* bc = &a.st->bar_count[a.which];
@@ -240,12 +242,17 @@ __global__ void __launch_bounds__(512) k_pcg(PcgArgs a) {
     {
         double v[3] = {0.0, 0.0, 0.0};
         if (a.r0 == nullptr) {
-            for (int i = row0; i < row1; ++i) {
+            for (int sl = gw; sl < a.n_slices; sl += nw) {
+                const long long base = a.sptr[sl];
+                const int w = (int)((a.sptr[sl + 1] - base) >> 5);
                 double acc = 0.0;
-                for (int s = a.ptr[i] + lane; s < a.ptr[i + 1]; s += 32)
-                    acc += a.val[s] * a.x[a.col[s]];
-                acc = warp_sum(acc);
-                if (lane == 0) {
+#pragma unroll 8
+                for (int k = 0; k < w; ++k) {
+                    const long long e = base + 32ll * k + lane;
+                    acc = fma(__ldg(a.val + e), a.x[__ldg(a.col + e)], acc);
+                }
+                const int i = sl * 32 + lane;
+                if (i < n) {
                     const double ri = a.b[i] - acc;
                     const double zi = a.dinv[i] * ri;
                     a.r[i] = ri;
@@ -289,16 +296,27 @@ __global__ void __launch_bounds__(512) k_pcg(PcgArgs a) {
         {
             double v[1] = {0.0};
             const bool first = (it == 0);
-            for (int i = row0; i < row1; ++i) {
+            for (int sl = gw; sl < a.n_slices; sl += nw) {
+                const long long base = a.sptr[sl];
+                const int w = (int)((a.sptr[sl + 1] - base) >> 5);
                 double acc = 0.0;
-                for (int s = a.ptr[i] + lane; s < a.ptr[i + 1]; s += 32) {
-                    const int j = a.col[s];
-                    const double pj = first ? a.z[j] : a.z[j] + beta * pc[j];
-                    acc += a.val[s] * pj;
+                if (first) {
+#pragma unroll 8
+                    for (int k = 0; k < w; ++k) {
+                        const long long e = base + 32ll * k + lane;
+                        acc = fma(__ldg(a.val + e), a.z[__ldg(a.col + e)], acc);
+                    }
+                } else {
+#pragma unroll 8
+                    for (int k = 0; k < w; ++k) {
+                        const long long e = base + 32ll * k + lane;
+                        const int j = __ldg(a.col + e);
+                        acc = fma(__ldg(a.val + e), fma(beta, pc[j], a.z[j]), acc);
+                    }
                 }
-                acc = warp_sum(acc);
-                if (lane == 0) {
-                    const double pi = first ? a.z[i] : a.z[i] + beta * pc[i];
+                const int i = sl * 32 + lane;
+                if (i < n) {
+                    const double pi = first ? a.z[i] : fma(beta, pc[i], a.z[i]);
                     pn[i] = pi;
                     a.q[i] = acc;
                     v[0] += pi * acc;
@@ -383,29 +401,29 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
     return cudaGetLastError();
 }
 
-cudaError_t launch_theta_rhs(int n_free, const long long* mk_ptr, const int* mk_col,
-                             const double* M, const double* K, const int* perm,
-                             const int* iperm_free, const double* That, const double* gnew,
-                             const double* F0, const double* F1, double inv_dt, double kscale,
-                             double theta, double* rhs, double* r0, cudaStream_t s) {
-    RhsArgs a{n_free, mk_ptr, mk_col, M, K, perm, iperm_free, That, gnew, F0, F1, inv_dt, kscale,
-              theta, rhs, r0};
+cudaError_t launch_theta_rhs(int n_free, int n_slices, const long long* sptr, const int* col,
+                             const double* M, const double* K, const double* That,
+                             const double* gnew, const double* F0, const double* F1,
+                             double inv_dt, double kscale, double theta, double* rhs,
+                             double* r0, cudaStream_t s) {
+    RhsArgs a{n_free, n_slices, sptr, col, M, K, That, gnew, F0, F1, inv_dt, kscale, theta, rhs,
+              r0};
     if (n_free == 0) return cudaSuccess;
-    k_theta_rhs<<<(unsigned)(((long long)n_free * 32 + 255) / 256), 256, 0, s>>>(a);
+    k_theta_rhs<<<(unsigned)(((long long)n_slices * 32 + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 int pcg_block_size() { return 512; }
 const void* pcg_kernel_ptr() { return (const void*)k_pcg; }
 
-cudaError_t launch_pcg(int which, int n, const int* ptr, const int* col, const double* val,
-                       const double* dinv, const double* b, const double* r0_or_null, double* x,
-                       double* r, double* z, double* p0, double* p1, double* q,
-                       double* partials, DevStatus* st, double tol, int max_iter, int grid,
-                       int block, cudaStream_t s) {
+cudaError_t launch_pcg(int which, int n, int n_slices, const long long* sptr, const int* col,
+                       const double* val, const double* dinv, const double* b,
+                       const double* r0_or_null, double* x, double* r, double* z, double* p0,
+                       double* p1, double* q, double* partials, DevStatus* st, double tol,
+                       int max_iter, int grid, int block, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    PcgArgs a{n, ptr, col, val, dinv, b, r0_or_null, x, r, z, p0, p1, q, partials, st, which,
-              tol, max_iter};
+    PcgArgs a{n, n_slices, sptr, col, val, dinv, b, r0_or_null, x, r, z, p0, p1, q, partials, st,
+              which, tol, max_iter};
     cudaError_t e = cudaMemsetAsync(&st->bar_count[which], 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
