@@ -165,6 +165,30 @@ sa_status sa_step(sa_ctx* ctx, double theta, double dt, int n_steps, sa_step_sta
  */
 sa_status sa_eval_T(sa_ctx* ctx, const double* pts, int n, double* T_out, int on_device);
 
+/*
+ * Allocation-free variant of sa_eval_T (this entry point has no counterpart
+ * in the paper; it exists for callers that cannot allocate device memory).
+ * Some callers must not call cudaMalloc/cudaFree while they run: a
+ * monitoring hook inside a latency-critical loop (an allocation may
+ * synchronise the device), or code inside a framework whose caching
+ * allocator already holds the free device memory.  sa_eval_T may allocate
+ * (its first call, a larger point count); this call never allocates.
+ *   pts    n*3 doubles in DEVICE memory (caller-allocated)
+ *   T_out  n doubles in DEVICE memory (caller-allocated); NaN outside the patch
+ * Same result as sa_eval_T.  Working memory: one fixed file-scope device
+ * array of 7 MiB (the current step's source coefficients and the element
+ * centres), held by every device that loads the library until the process
+ * exits.  Limits: at most 65,536 discretised sources and 131,072 elements;
+ * larger contexts get SA_ERR_ARG with a message.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU (different
+ * streams or contexts, concurrently) race; serialise them.  Synchronous on
+ * the context's stream.  Needs a context that has stepped or had its state
+ * set (SA_ERR_STATE otherwise).
+ */
+sa_status sa_eval_T_noalloc(sa_ctx* ctx, const double* pts, int n, double* T_out);
+
 /* Sizes of a context after set-up. */
 typedef struct sa_sizes {
     int n_dof, n_free, n_dir;      /* control variables; free / Dirichlet             */

@@ -65,6 +65,7 @@ def _load():
         "sa_set_scan": (I, [P, P, I, P, D, D, D, D]),
         "sa_step": (I, [P, D, D, I, C.POINTER(sa_step_stats)]),
         "sa_eval_T": (I, [P, P, I, P, I]),
+        "sa_eval_T_noalloc": (I, [P, P, I, P]),
         "sa_get_sizes": (I, [P, C.POINTER(sa_sizes)]),
         "sa_get_field": (I, [P, I, P, LL, I]),
         "sa_get_matrix_nnz": (I, [P, C.POINTER(LL)]),

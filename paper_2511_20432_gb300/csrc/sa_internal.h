@@ -16,6 +16,9 @@
 #define SA_MAX_DEGREE 3
 #define SA_MAX_NLOC ((SA_MAX_DEGREE + 1) * (SA_MAX_DEGREE + 1) * (SA_MAX_DEGREE + 1))
 #define SA_MAX_NFACE ((SA_MAX_DEGREE + 1) * (SA_MAX_DEGREE + 1))
+// limits of sa_eval_T_noalloc (its fixed scratch array)
+#define SA_NOALLOC_MAX_SOURCES 65536
+#define SA_NOALLOC_MAX_ELEMENTS 131072
 
 // device error flags (DevStatus::err)
 enum {
