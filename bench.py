@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--start-step", type=int, default=START_STEP)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="path timed in the main region")
+    ap.add_argument("--quick", action="store_true",
+                    help="main timed region only (no stage, FP64, e2e or CPU legs): "
+                         "the form used under ncu")
     return ap.parse_args()
 
 
@@ -215,7 +220,8 @@ def run_ours(args):
     wl = W.block_meander(20, theta=0.5)
     th, dt = wl.theta, wl.dt
     stream = torch.cuda.Stream()
-    ctx = sa.context_from_workload(wl, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
+    prec = sa.SA_MIXED if args.precision == "mixed" else sa.SA_FP64
+    ctx = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1)
     n0 = args.start_step
     ctx.step(th, dt, n0)                       # untimed fast-forward to mid-scan
     ctx.step(th, dt, args.warmup)              # warm-up (graph instantiated, caches warm)
@@ -245,8 +251,19 @@ def run_ours(args):
         ms = float(t.item())
     stats = ctx.step(th, dt, 0)                # counters accumulated over the timed steps
     iters_avg = stats.pcg_iters_total / K
+    bot_avg = stats.bot_iters_total / K
     value = world * K / (ms / 1e3)
     evals = world * pairs / (ms / 1e3)
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
+                              "precision": args.precision, "start_step": n0,
+                              "point_source_evals_per_s": evals, "pcg_iters_per_step": iters_avg,
+                              "bot_iters_per_step": bot_avg, "clocks": clocks}))
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # ---- stage breakdown (CUDA events on the launching stream) --------------
     K_t = min(K, 40)
@@ -334,7 +351,7 @@ def run_ours(args):
         "point_source_evals_per_s": evals,
         "fp64_steps_per_s": world * fp64_steps,
         "mixed_over_fp64": value / (world * fp64_steps),
-        "pcg_iters_per_step": iters_avg,
+        "pcg_iters_per_step": iters_avg, "bot_iters_per_step": bot_avg,
         "stage_ms": stage_avg, "stage_share": shares, "kernels": kernels,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,

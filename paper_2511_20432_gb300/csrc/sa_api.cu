@@ -105,6 +105,7 @@ struct SellHost {
     int n = 0, n_slices = 0;
     std::vector<long long> sptr;
     std::vector<int> col, src, diag;
+    std::vector<short> col16;   // column - row, filled when every offset fits
 };
 
 void build_sell(int n, const std::vector<long long>& ptr, const std::vector<int>& col,
@@ -142,6 +143,25 @@ void build_sell(int n, const std::vector<long long>& ptr, const std::vector<int>
             }
         }
     }
+    // 16-bit offsets from the row (padding lanes past n use row n-1)
+    bool fits = n > 0;
+    out.col16.assign(tot, 0);
+    for (int s = 0; s < out.n_slices && fits; ++s) {
+        const long long w = (out.sptr[s + 1] - out.sptr[s]) / 32;
+        for (int l = 0; l < 32 && fits; ++l) {
+            const int r = std::min(s * 32 + l, n - 1);
+            for (long long k = 0; k < w; ++k) {
+                const long long e = out.sptr[s] + 32 * k + l;
+                const long long d = (s * 32 + l < n) ? (long long)out.col[e] - r : 0;
+                if (d < -32768 || d > 32767) {
+                    fits = false;
+                    break;
+                }
+                out.col16[e] = (short)d;
+            }
+        }
+    }
+    if (!fits) out.col16.clear();
 }
 
 template <class T>
@@ -158,7 +178,10 @@ cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
         (dev).n_slices = (host).n_slices;         \
         (dev).n_stored = (long long)(host).col.size(); \
         SA_UPLOAD(ctx, (dev).sptr, (host).sptr);  \
-        SA_UPLOAD(ctx, (dev).col, (host).col);    \
+        if ((host).col16.empty())                 \
+            SA_UPLOAD(ctx, (dev).col, (host).col);    \
+        else                                      \
+            SA_UPLOAD(ctx, (dev).col16, (host).col16); \
         SA_UPLOAD(ctx, (dev).src, (host).src);    \
         SA_UPLOAD(ctx, (dev).diag, (host).diag);  \
     } while (0)
@@ -604,6 +627,11 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                 SA_ALLOC(c, c->mbot_sval, sh.col.size());
                 e = launch_sell_fill(c->mbot_s.n_stored, c->mbot_s.src.p, c->mbot_val.p, 1.0,
                                      nullptr, 0.0, c->mbot_sval.p, s);
+                if (e == cudaSuccess && c->opt.precision == SA_MIXED) {
+                    cudaError_t ea = c->mbot_sval32.alloc(sh.col.size());
+                    if (ea != cudaSuccess) return sa_fail(c, SA_ERR_OOM, "allocation of M_bot FP32");
+                    e = launch_to_f32(c->mbot_s.n_stored, c->mbot_sval.p, c->mbot_sval32.p, s);
+                }
                 if (e != cudaSuccess) return sa_cuda_fail(c, e, "M_bot SELL");
             }
             SA_CUDA(c, cudaStreamSynchronize(s));   // cooR/cooD freed on return
@@ -720,6 +748,13 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                                          c->r_M.p, s);
         if (e == cudaSuccess)
             e = launch_sell_fill(c->r_s.n_stored, c->r_s.src.p, c->K.p, 1.0, nullptr, 0.0, c->r_K.p, s);
+        if (e == cudaSuccess && c->opt.precision == SA_MIXED) {
+            SA_ALLOC(c, c->r_M32, sr_h.col.size());
+            SA_ALLOC(c, c->r_K32, sr_h.col.size());
+            SA_ALLOC(c, c->a_val32, sa_h.col.size());
+            e = launch_to_f32(c->r_s.n_stored, c->r_M.p, c->r_M32.p, s);
+            if (e == cudaSuccess) e = launch_to_f32(c->r_s.n_stored, c->r_K.p, c->r_K32.p, s);
+        }
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "free-row SELL");
     }
 
@@ -737,6 +772,13 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_ALLOC(c, c->wp0, nwork);
     SA_ALLOC(c, c->wp1, nwork);
     SA_ALLOC(c, c->wq, nwork);
+    SA_ALLOC(c, c->dev64, ndof);
+    SA_ALLOC(c, c->dev32, ndof);
+    if (c->opt.precision == SA_MIXED) {
+        SA_ALLOC(c, c->wzl, nwork);
+        SA_ALLOC(c, c->wpl0, nwork);
+        SA_ALLOC(c, c->wpl1, nwork);
+    }
     SA_ALLOC(c, c->s_lat, std::max(c->q_lat, 1));
     SA_ALLOC(c, c->tt_bot, std::max(c->q_bot, 1));
     SA_CUDA(c, cudaMemsetAsync(c->F0.p, 0, sizeof(double) * ndof, s));
@@ -748,8 +790,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     // PCG launch shape: co-resident blocks (cooperative launch)
     {
         int occ = 0;
-        SA_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel_ptr(),
-                                                                 pcg_block_size(), 0));
+        SA_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       &occ, pcg_kernel_ptr(c->opt.precision), pcg_block_size(), 0));
         if (occ < 1) return sa_fail(c, SA_ERR_CUDA, "PCG kernel cannot be resident");
         c->pcg_block = pcg_block_size();
         c->pcg_grid = c->num_sms;   // one co-resident block of 512 threads per SM
@@ -838,6 +880,8 @@ sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
     cudaError_t e = launch_sell_fill(c->a_s.n_stored, c->a_s.src.p, c->M.p, c->rho * c->cp / dt,
                                      c->K.p, theta * c->k, c->a_val.p, c->stream);
     if (e == cudaSuccess) e = launch_sell_dinv(c->n_free, c->a_s.diag.p, c->a_val.p, c->a_dinv.p, c->stream);
+    if (e == cudaSuccess && c->opt.precision == SA_MIXED)
+        e = launch_to_f32(c->a_s.n_stored, c->a_val.p, c->a_val32.p, c->stream);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "build A");
     c->op_dt = dt;
     c->op_theta = theta;
@@ -875,34 +919,75 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     SA_MARK(SA_STAGE_GATHER);
     e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
                       c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
-                      c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, s);
+                      c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, c->n_dof, c->That.p,
+                      c->dev64.p, c->dev32.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
+    const bool mixed = c->opt.precision == SA_MIXED;
     SA_MARK(SA_STAGE_BOTTOM);
     if (c->n_dir > 0) {
         // x0 = g^n (the Dirichlet part of the state)
         e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
                             cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
-        const int grid_bot = std::max(1, std::min(c->pcg_grid, (c->n_dir + 255) / 256));
-        e = launch_pcg(1, c->n_dir, c->mbot_s.n_slices, c->mbot_s.sptr.p, c->mbot_s.col.p,
-                       c->mbot_sval.p, c->mbot_dinv.p,
-                       c->bbot.p, nullptr, c->gnew.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p,
-                       c->wq.p, c->partials.p, c->st.p, c->opt.pcg_tol,
-                       c->opt.pcg_max_iter, grid_bot, c->pcg_block, s);
+        PcgLaunch L;
+        L.op = sell_view(c->mbot_s);
+        L.val = mixed ? (const void*)c->mbot_sval32.p : (const void*)c->mbot_sval.p;
+        L.val_hi = c->mbot_sval.p;
+        L.dinv = c->mbot_dinv.p;
+        L.b = c->bbot.p;
+        L.r0 = nullptr;
+        L.x = c->gnew.p;
+        L.r = c->wr.p;
+        L.z = c->wz.p;
+        L.p0 = c->wp0.p;
+        L.p1 = c->wp1.p;
+        L.q = c->wq.p;
+        L.zl = c->wzl.p;
+        L.pl0 = c->wpl0.p;
+        L.pl1 = c->wpl1.p;
+        L.partials = c->partials.p;
+        L.st = c->st.p;
+        L.which = 1;
+        L.tol = c->opt.pcg_tol;
+        L.max_iter = c->opt.pcg_max_iter;
+        L.grid = c->n_dir <= 32768 ? 1 : c->pcg_grid;
+        e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
     SA_MARK(SA_STAGE_RHS);
-    e = launch_theta_rhs(c->n_free, c->r_s.n_slices, c->r_s.sptr.p, c->r_s.col.p, c->r_M.p,
-                         c->r_K.p, c->That.p, c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt,
-                         c->k, theta, c->rhs.p, c->r0.p, s);
+    e = launch_theta_rhs(c->opt.precision, sell_view(c->r_s),
+                         mixed ? (const void*)c->r_K32.p : (const void*)c->r_K.p,
+                         mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
+                         mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
+                         c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->r0.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     SA_MARK(SA_STAGE_PCG);
-    e = launch_pcg(0, c->n_free, c->a_s.n_slices, c->a_s.sptr.p, c->a_s.col.p, c->a_val.p,
-                   c->a_dinv.p, c->rhs.p,
-                   c->r0.p, c->That.p, c->wr.p, c->wz.p, c->wp0.p, c->wp1.p, c->wq.p,
-                   c->partials.p, c->st.p, c->opt.pcg_tol, c->opt.pcg_max_iter, c->pcg_grid,
-                   c->pcg_block, s);
-    if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
+    {
+        PcgLaunch L;
+        L.op = sell_view(c->a_s);
+        L.val = mixed ? (const void*)c->a_val32.p : (const void*)c->a_val.p;
+        L.val_hi = c->a_val.p;
+        L.dinv = c->a_dinv.p;
+        L.b = nullptr;
+        L.r0 = c->r0.p;
+        L.x = c->That.p;
+        L.r = c->wr.p;
+        L.z = c->wz.p;
+        L.p0 = c->wp0.p;
+        L.p1 = c->wp1.p;
+        L.q = c->wq.p;
+        L.zl = c->wzl.p;
+        L.pl0 = c->wpl0.p;
+        L.pl1 = c->wpl1.p;
+        L.partials = c->partials.p;
+        L.st = c->st.p;
+        L.which = 0;
+        L.tol = c->opt.pcg_tol;
+        L.max_iter = c->opt.pcg_max_iter;
+        L.grid = c->pcg_grid;
+        e = launch_pcg(c->opt.precision, L, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
+    }
     SA_MARK(SA_STAGE_FINALIZE);
     e = launch_finalize(c->n_dir, c->n_free, c->n_dof, c->gnew.p, c->That.p, c->F1.p, c->F0.p,
                         c->st.p, s);
@@ -1168,8 +1253,10 @@ sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_d
     const double* dpts = pts;
     double* dout = T_out;
     if (!on_device) {
-        SA_ALLOC(c, c->eval_pts, (size_t)3 * n);
-        SA_ALLOC(c, c->eval_out, (size_t)n);
+        if (c->eval_out.n < (size_t)n) {   // grown on demand, kept between calls
+            SA_ALLOC(c, c->eval_pts, (size_t)3 * n);
+            SA_ALLOC(c, c->eval_out, (size_t)n);
+        }
         SA_CUDA(c, cudaMemcpyAsync(c->eval_pts.p, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
         dpts = c->eval_pts.p;
         dout = c->eval_out.p;

@@ -378,6 +378,11 @@ __global__ void k_sell_fill(long long n_stored, const int* src, const double* in
     out[e] = v;
 }
 
+__global__ void k_to_f32(long long n, const double* in, float* out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
 __global__ void k_sell_dinv(int n, const int* diag, const double* val, double* dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dinv[i] = 1.0 / val[diag[i]];
@@ -467,17 +472,21 @@ struct EvalArgs {
     double* T_out;
 };
 
+// One warp per query point: the lanes search the element centres and sum
+// the sources; lane 0 runs the Newton iteration.  Reductions use a fixed
+// xor tree (deterministic).
 __global__ void k_eval(EvalArgs a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (t >= a.n) return;
     const DevPatch& dp = a.dp;
     const double xs[3] = {a.pts[3 * t], a.pts[3 * t + 1], a.pts[3 * t + 2]};
     // initial guess: parametric centre of the element with the nearest
-    // physical centre
+    // physical centre (ties: lowest element index)
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
-    int best = 0;
+    int best = 0x7fffffff;
     double bd = 1e300;
-    for (int e = 0; e < nel; ++e) {
+    for (int e = lane; e < nel; e += 32) {
         const double dx = a.ecent[3 * e] - xs[0], dy = a.ecent[3 * e + 1] - xs[1],
                      dz = a.ecent[3 * e + 2] - xs[2];
         const double d2 = dx * dx + dy * dy + dz * dz;
@@ -486,57 +495,70 @@ __global__ void k_eval(EvalArgs a) {
             best = e;
         }
     }
-    const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1], best / (dp.ne[0] * dp.ne[1])};
-    double xi[3], lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-        const int s = dp.espan[d][es[d]];
-        xi[d] = 0.5 * (dp.U[d][s] + dp.U[d][s + 1]);
-        lo[d] = dp.U[d][dp.p[d]];
-        hi[d] = dp.U[d][dp.n[d]];
-    }
-    // Newton on x(xi) = x*, clamped to the parametric box
-    Basis1D b;
-    double x[3], J[3][3], W;
-    double res = 1e300;
-    for (int it = 0; it < 60; ++it) {
-        eval_at(dp, xi, b, x, J, W);
-        const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
-        res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-        if (res <= 1e-13 * a.scale) break;
-        const double det = det3(J);
-        if (!(fabs(det) > 0.0)) break;
-        double dxi[3];
-        for (int c = 0; c < 3; ++c) {
-            double Jc[3][3];
-            for (int r = 0; r < 3; ++r)
-                for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J[r][k];
-            dxi[c] = det3(Jc) / det;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (od < bd || (od == bd && ob < best)) {
+            bd = od;
+            best = ob;
         }
-        for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
-    }
-    if (!(res <= 1e-9 * a.scale)) {
-        a.T_out[t] = nan("");
-        return;
     }
     double That = 0.0;
-    for (int a2 = 0; a2 <= dp.p[2]; ++a2)
-        for (int a1 = 0; a1 <= dp.p[1]; ++a1)
-            for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
-                const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0, b.s[1] - dp.p[1] + a1,
-                                          b.s[2] - dp.p[2] + a2);
-                const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
-                That += R * a.That[a.perm[nat]];
+    int ok = 0;
+    if (lane == 0) {
+        const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1],
+                           best / (dp.ne[0] * dp.ne[1])};
+        double xi[3], lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            const int s = dp.espan[d][es[d]];
+            xi[d] = 0.5 * (dp.U[d][s] + dp.U[d][s + 1]);
+            lo[d] = dp.U[d][dp.p[d]];
+            hi[d] = dp.U[d][dp.n[d]];
+        }
+        // Newton on x(xi) = x*, clamped to the parametric box
+        Basis1D b;
+        double x[3], J[3][3], W;
+        double res = 1e300;
+        for (int it = 0; it < 60; ++it) {
+            eval_at(dp, xi, b, x, J, W);
+            const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
+            res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            if (res <= 1e-13 * a.scale) break;
+            const double det = det3(J);
+            if (!(fabs(det) > 0.0)) break;
+            double dxi[3];
+            for (int c = 0; c < 3; ++c) {
+                double Jc[3][3];
+                for (int r = 0; r < 3; ++r)
+                    for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J[r][k];
+                dxi[c] = det3(Jc) / det;
             }
+            for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
+        }
+        ok = res <= 1e-9 * a.scale;
+        if (ok)
+            for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                    for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                        const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                  b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
+                        const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
+                        That += R * a.That[a.perm[nat]];
+                    }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
     const double px = xs[0] - a.x_ref, py = xs[1] - a.y_ref, dz = xs[2] - a.z_top;
     double Tt = 0.0;
-    for (int j = 0; j < a.n_active; ++j) {
+    for (int j = lane; j < a.n_active; j += 32) {
         const double4 sv = a.s64T[j];
         const double dx = px - sv.x, dy = py - sv.y;
         Tt += sv.w * exp(-sv.z * (dx * dx + dy * dy + dz * dz));
     }
-    a.T_out[t] = Tt + That;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Tt += __shfl_xor_sync(0xffffffffu, Tt, o);
+    if (lane == 0) a.T_out[t] = ok ? Tt + That : nan("");
 }
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -647,6 +669,12 @@ cudaError_t launch_sell_fill(long long n_stored, const int* src, const double* i
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_f32(long long n, const double* in, float* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sell_dinv(int n, const int* diag, const double* val, double* dinv,
                              cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -676,6 +704,6 @@ cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, con
                                double scale, double* T_out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     EvalArgs a{dp, pts, n, ecent, perm, That, s64T, n_active, x_ref, y_ref, z_top, scale, T_out};
-    k_eval<<<(n + 63) / 64, 64, 0, s>>>(a);
+    k_eval<<<(unsigned)(((long long)n * 32 + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }

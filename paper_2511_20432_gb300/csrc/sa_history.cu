@@ -14,14 +14,17 @@
 // not a contraction, so it does not use tensor cores.
 //
 // Work layout: one CTA owns a tile of 32*P points (P per lane, held in
-// registers) and all of its NW warps split the active sources round-robin;
-// the sources are read as warp-uniform 16-byte loads (one transaction per
-// warp, served by L1/L2: the whole source table of a step is at most a few
-// hundred KB).  Each lane accumulates FP32 partial sums over 32 of its
-// sources, then adds them into a Neumaier-compensated FP32 pair; the NW warp
-// results are added in FP64 in fixed order through shared memory.  Every
-// output point is written by exactly one thread: deterministic, no atomics,
-// no scratch memory.
+// registers) and all of its NW warps split the active sources round-robin.
+// Mixed path: the source table streams through shared memory in chunks of
+// 512 (8 KB), double-buffered: one thread issues the bulk asynchronous copy
+// (cp.async.bulk, TMA engine) of the next chunk, completion tracked by an
+// mbarrier, while the CTA works on the current one; every source is then a
+// broadcast shared-memory read.  Each lane accumulates an FP32 partial sum
+// per chunk and adds it into a Neumaier-compensated FP32 pair; the NW warp
+// results are added in FP64 in fixed order through shared memory.  FP64
+// path: warp-uniform global loads (L1/L2-resident table).  Every output point
+// is written by exactly one thread: deterministic, no atomics, no scratch
+// memory.
 #include "sa_internal.h"
 
 namespace {
@@ -80,7 +83,7 @@ __global__ void k_prologue(PrologueArgs a) {
 // history sum
 // ---------------------------------------------------------------------------
 struct HistArgs {
-    const DevStatus* st;
+    DevStatus* st;
     int q_lat, q_bot;
     int b_lat;                 // CTAs on lateral tiles; the rest on bottom tiles
     const float* lat32;
@@ -103,8 +106,77 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
     s = t;
 }
 
+// ---------------------------------------------------------------------------
+// shared-memory staging of the source table: one thread issues a bulk
+// asynchronous copy (TMA engine) of the next chunk while the CTA computes on
+// the current one; completion is tracked by an mbarrier.  Waits are bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for a chunk: false after ~1 s (the caller flags the error).
+__device__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < (1ll << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+
+constexpr int kChunk = 512;   // sources per staged chunk (8 KB)
+
+struct Stage {
+    float4 buf[2][kChunk];
+    unsigned long long mbar[2];
+    int abort_flag;
+};
+
 template <bool FLUX, int P, int NW>
-__device__ void tile_mixed(const HistArgs& a, int tile, double* red) {
+__device__ void tile_mixed(const HistArgs& a, int tile, double* red, Stage& sg) {
+    float4 (*sbuf)[kChunk] = sg.buf;
+    unsigned long long* mbar = sg.mbar;
+    int& abort_flag = sg.abort_flag;
     const int Q = FLUX ? a.q_lat : a.q_bot;
     const float* pts = FLUX ? a.lat32 : a.bot32;
     const float4* src = FLUX ? a.s32F : a.s32T;
@@ -112,7 +184,7 @@ __device__ void tile_mixed(const HistArgs& a, int tile, double* red) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q0 = tile * 32 * P;
     float px[P], py[P], dz2[P], nzdz[P], nx[P], ny[P];
-    float s[P], c[P], acc[P];
+    float s[P], c[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int q = q0 + lane + 32 * p;
@@ -127,42 +199,64 @@ __device__ void tile_mixed(const HistArgs& a, int tile, double* red) {
         }
         s[p] = 0.f;
         c[p] = 0.f;
-        acc[p] = 0.f;
     }
-    int cnt = 0;
-    int j = w;
-    // software pipeline: the next warp-uniform source is loaded one ahead
-    float4 nxt = j < K ? __ldg(&src[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (; j < K; j += NW) {
-        const float4 sv = nxt;
-        if (j + NW < K) nxt = __ldg(&src[j + NW]);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const float dx = px[p] - sv.x;
-            const float dy = py[p] - sv.y;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz2[p]));
-            const float e = ex2_approx(fmaf(sv.z, r2, sv.w));
-            if (FLUX) {
-                const float nd = fmaf(nx[p], dx, fmaf(ny[p], dy, nzdz[p]));
-                acc[p] = fmaf(e, nd, acc[p]);
-            } else {
-                acc[p] += e;
-            }
+    const int n_chunks = (K + kChunk - 1) / kChunk;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+        if (n_chunks > 0) bulk_load(sbuf[0], src, (unsigned)(min(K, kChunk) * sizeof(float4)), &mbar[0]);
+    }
+    __syncthreads();
+    for (int ch = 0; ch < n_chunks; ++ch) {
+        const int b = ch & 1;
+        if (threadIdx.x == 0 && ch + 1 < n_chunks) {
+            const int off = (ch + 1) * kChunk;
+            bulk_load(sbuf[b ^ 1], src + off, (unsigned)(min(K - off, kChunk) * sizeof(float4)),
+                      &mbar[b ^ 1]);
         }
-        if (++cnt == 32) {
-            cnt = 0;
+        if (!mbar_wait_bounded(&mbar[b], (ch >> 1) & 1)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        const int len = min(K - ch * kChunk, kChunk);
+        float acc[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[p] = 0.f;
+#pragma unroll 4
+        for (int j = w; j < len; j += NW) {
+            const float4 sv = sbuf[b][j];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                neumaier(s[p], c[p], acc[p]);
-                acc[p] = 0.f;
+                const float dx = px[p] - sv.x;
+                const float dy = py[p] - sv.y;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz2[p]));
+                const float e = ex2_approx(fmaf(sv.z, r2, sv.w));
+                if (FLUX) {
+                    const float nd = fmaf(nx[p], dx, fmaf(ny[p], dy, nzdz[p]));
+                    acc[p] = fmaf(e, nd, acc[p]);
+                } else {
+                    acc[p] += e;
+                }
             }
         }
+#pragma unroll
+        for (int p = 0; p < P; ++p) neumaier(s[p], c[p], acc[p]);
+        __syncthreads();   // every warp is done with buffer b before it is refilled
+    }
+    if (abort_flag) {
+        // a chunk never arrived: flag it, let the copies in flight land
+        // (bounded), write nothing
+        if (threadIdx.x == 0) {
+            atomicOr((int*)&a.st->err, SA_DEV_TIMEOUT);
+            mbar_wait_bounded(&mbar[0], 0);
+            mbar_wait_bounded(&mbar[1], 0);
+        }
+        __syncthreads();
+        return;
     }
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        neumaier(s[p], c[p], acc[p]);
-        red[w * 32 * P + lane + 32 * p] = (double)s[p] + (double)c[p];
-    }
+    for (int p = 0; p < P; ++p) red[w * 32 * P + lane + 32 * p] = (double)s[p] + (double)c[p];
     __syncthreads();
     for (int t = threadIdx.x; t < 32 * P; t += 32 * NW) {
         double tot = 0.0;
@@ -233,10 +327,11 @@ __device__ void tile_fp64(const HistArgs& a, int tile, double* red) {
 template <int P, int NW>
 __global__ void __launch_bounds__(32 * NW) k_history_mixed(HistArgs a) {
     __shared__ double red[NW * 32 * P];
+    __shared__ __align__(128) Stage sg;
     if ((int)blockIdx.x < a.b_lat)
-        tile_mixed<true, P, NW>(a, blockIdx.x, red);
+        tile_mixed<true, P, NW>(a, blockIdx.x, red, sg);
     else
-        tile_mixed<false, P, NW>(a, blockIdx.x - a.b_lat, red);
+        tile_mixed<false, P, NW>(a, blockIdx.x - a.b_lat, red, sg);
 }
 
 template <int P, int NW>
@@ -290,7 +385,7 @@ cudaError_t launch_prologue(const DevStatus* st_in, long long n_explicit, DevSta
     return cudaGetLastError();
 }
 
-cudaError_t launch_history(int precision, int P, int warps, const DevStatus* st, int q_lat,
+cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q_lat,
                            int q_bot, const float* lat32, const float* bot32,
                            const double* lat64, const double* bot64, double x_ref,
                            double y_ref, double z_top, const float4* s32F,

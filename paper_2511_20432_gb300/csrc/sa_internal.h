@@ -94,9 +94,53 @@ struct SellDev {
     int n = 0, n_slices = 0;
     long long n_stored = 0;
     DBuf<long long> sptr;     // n_slices + 1
-    DBuf<int> col;            // n_stored
+    DBuf<int> col;            // n_stored (absolute columns)
+    DBuf<short> col16;        // n_stored (column - row), when every offset fits
     DBuf<int> src;            // n_stored: slot in the source CSR, -1 for padding
     DBuf<int> diag;           // n: storage index of the diagonal entry
+};
+
+// What the kernels need of a SELL operator (no ownership).
+struct SellView {
+    int n, n_slices;
+    const long long* sptr;
+    const int* col32;         // null when col16 is used
+    const short* col16;
+};
+
+inline SellView sell_view(const SellDev& s) {
+    SellView v;
+    v.n = s.n;
+    v.n_slices = s.n_slices;
+    v.sptr = s.sptr.p;
+    v.col16 = s.col16.p;
+    v.col32 = s.col16.p ? nullptr : s.col.p;
+    return v;
+}
+
+// Arguments of one PCG solve.
+struct PcgLaunch {
+    SellView op;
+    const void* val;          // operator values in the path's precision
+    const double* val_hi;     // FP64 values (initial residual when r0 == null)
+    const double* dinv;
+    const double* b;
+    const double* r0;         // given initial residual (x0 = x), or null
+    double* x;
+    double* r;
+    double* z;
+    double* p0;
+    double* p1;
+    double* q;
+    void* zl;                 // FP32 copies (mixed path)
+    void* pl0;
+    void* pl1;
+    double* partials;
+    DevStatus* st;
+    int which;
+    double tol;
+    int max_iter;
+    int grid;                 // 1: one block, no grid barrier
 };
 
 // ---------------------------------------------------------------------------
@@ -170,6 +214,7 @@ struct sa_ctx {
     DBuf<double> mbot_val, mbot_dinv;
     SellDev mbot_s;
     DBuf<double> mbot_sval;
+    DBuf<float> mbot_sval32;
 
     // M, K: CSR over all control variables, natural order
     long long nnz = 0;
@@ -180,10 +225,12 @@ struct sa_ctx {
     long long nnz_a = 0;
     SellDev a_s;
     DBuf<double> a_val, a_dinv;
+    DBuf<float> a_val32;
     // free rows of M and K over all columns (internal indices), for the
     // theta right-hand side (SELL, unit rho c_p and k)
     SellDev r_s;
     DBuf<double> r_M, r_K;
+    DBuf<float> r_M32, r_K32;
 
     // ---- device: scan and history ------------------------------------------
     DBuf<double2> src_pos;    // relative (x - x_ref, y - y_ref)
@@ -198,6 +245,9 @@ struct sa_ctx {
     DBuf<double> gnew, bbot;  // n_dir
     DBuf<double> rhs, r0;     // n_free
     DBuf<double> wr, wz, wp0, wp1, wq;   // PCG work, max(n_free, n_dir)
+    DBuf<float> wzl, wpl0, wpl1;         // FP32 copies (mixed path)
+    DBuf<double> dev64;                  // T^n - T_c (n_dof)
+    DBuf<float> dev32;
     DBuf<double> partials;    // 4 * max grid
     DBuf<DevStatus> st;
     int pcg_grid = 0, pcg_block = 0;
@@ -263,6 +313,7 @@ cudaError_t launch_mbot_fill(int n_rows, const int* mptr, const int* mcol, const
                              double* dinv, cudaStream_t s);
 cudaError_t launch_sell_fill(long long n_stored, const int* src, const double* in1, double s1,
                             const double* in2, double s2, double* out, cudaStream_t s);
+cudaError_t launch_to_f32(long long n, const double* in, float* out, cudaStream_t s);
 cudaError_t launch_sell_dinv(int n, const int* diag, const double* val, double* dinv,
                              cudaStream_t s);
 cudaError_t launch_points32(int q_lat, int q_bot, const double* lat64, const double* bot64,
@@ -274,7 +325,7 @@ cudaError_t launch_prologue(const DevStatus* st_in, long long n_explicit, DevSta
                             int n_src, const double2* pos, double dt, double alpha,
                             double r2_8a, double coefE, int precision, double4* s64T,
                             double4* s64F, float4* s32T, float4* s32F, cudaStream_t s);
-cudaError_t launch_history(int precision, int P, int warps, const DevStatus* st, int q_lat,
+cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q_lat,
                            int q_bot, const float* lat32, const float* bot32,
                            const double* lat64, const double* bot64, double x_ref,
                            double y_ref, double z_top, const float4* s32F,
@@ -290,18 +341,15 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           const int* wlat_col, const double* wlat_val, const double* s_lat,
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
-                          double* bbot, cudaStream_t s);
-cudaError_t launch_theta_rhs(int n_free, int n_slices, const long long* sptr, const int* col,
-                             const double* M, const double* K, const double* That,
+                          double* bbot, int n_dof, const double* That, double* dev64,
+                          float* dev32, cudaStream_t s);
+cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
+                             const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
-                             double inv_dt, double kscale, double theta, double* rhs,
-                             double* r0, cudaStream_t s);
-cudaError_t launch_pcg(int which, int n, int n_slices, const long long* sptr, const int* col,
-                       const double* val, const double* dinv, const double* b,
-                       const double* r0_or_null, double* x, double* r, double* z, double* p0,
-                       double* p1, double* q, double* partials, DevStatus* st, double tol,
-                       int max_iter, int grid, int block, cudaStream_t s);
+                             double inv_dt_rhocp, double k, double theta, double* r0,
+                             cudaStream_t s);
+cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
                             const double* F1, double* F0, DevStatus* st, cudaStream_t s);
 int pcg_block_size();
-const void* pcg_kernel_ptr();
+const void* pcg_kernel_ptr(int precision);

@@ -1,16 +1,30 @@
 // Per-step solver kernels: boundary integrals of the point-source data
 // (Section 2.3, F_i = int_lat (-q_N) N_i dS; the bottom projection), the
-// theta-scheme right-hand side (Eq. theta-method) and a persistent
-// cooperative Jacobi-PCG in FP64.
-#include <cooperative_groups.h>
+// theta-scheme right-hand side (Eq. theta-method) and Jacobi-PCG.
+//
+// Precision: the plain path runs every stage in FP64.  The mixed path keeps
+// FP64 for the state, the residuals, the dot products and the initial
+// residual of each solve, and applies the operator in FP32 (FP32 values and
+// FP32 copies of the gathered Krylov vectors).  Each solve works on the
+// increment from its FP64 initial guess, so the FP32 operator perturbs the
+// increment only (relative ~1e-7), far below the residual tolerance measured
+// against the full right-hand side.
+#include <type_traits>
 
 #include "sa_internal.h"
 
 namespace {
 
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // F^{n+1} = W_lat (-k dT~/dn)  and  b_bot = W_bot (T_c - T~): one warp per
-// row of the constant weight matrices, fixed order, no atomics.
+// row of the constant weight matrices, fixed order, no atomics.  The same
+// launch writes dev = T^n - T_c (FP64 and FP32) for the right-hand side.
 // ---------------------------------------------------------------------------
 struct GatherArgs {
     int wlat_rows;
@@ -28,16 +42,25 @@ struct GatherArgs {
     double Tc;
     double* F1;
     double* bbot;
+    int n_dof;
+    const double* That;
+    double* dev64;
+    float* dev32;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __global__ void k_gather(GatherArgs a) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long row_threads = 32ll * (a.wlat_rows + a.n_dir);
+    if (gt >= row_threads) {
+        const long long i = gt - row_threads;
+        if (i < a.n_dof) {
+            const double d = a.That[i] - a.Tc;
+            a.dev64[i] = d;
+            a.dev32[i] = (float)d;
+        }
+        return;
+    }
+    const int row = (int)(gt >> 5);
     const int lane = threadIdx.x & 31;
     if (row < a.wlat_rows) {
         double acc = 0.0;
@@ -45,7 +68,7 @@ __global__ void k_gather(GatherArgs a) {
             acc += a.lval[s] * a.s_lat[a.lcol[s]];
         acc = warp_sum(acc);
         if (lane == 0) a.F1[a.rowdof[row]] = -a.k * acc;
-    } else if (row < a.wlat_rows + a.n_dir) {
+    } else {
         const int r = row - a.wlat_rows;
         double acc = 0.0;
         for (int s = a.bptr[r] + lane; s < a.bptr[r + 1]; s += 32)
@@ -56,63 +79,72 @@ __global__ void k_gather(GatherArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// theta right-hand side on the free rows, with the Dirichlet values lifted:
-//   b = (M/dt)(T^n - G) - K((1-theta) T^n + theta G) + theta F^{n+1}
-//       + (1-theta) F^n,    G = g^{n+1} on Dirichlet columns, 0 elsewhere,
-// which equals (M/dt - (1-theta)K) T^n + theta F^{n+1} + (1-theta) F^n
-// - (M/dt + theta K)_{fd} g^{n+1}; and in the same pass the initial PCG
-// residual r0 = b - A_ff T^n_f.  One warp per free row.
+// SELL operator access (slice height 32, lane = row)
 // ---------------------------------------------------------------------------
-struct RhsArgs {
-    int n_free;
-    int n_slices;
+template <typename VT>
+struct Op {
+    int n, n_slices;
     const long long* sptr;
-    const int* col;            // internal column indices
-    const double* M;           // unit rho c_p
-    const double* K;           // unit k
+    const int* col32;      // absolute column, or
+    const short* col16;    // column - row (when every offset fits in 16 bits)
+    const VT* val;
+    __device__ __forceinline__ int col(long long e, int row) const {
+        return col16 ? row + (int)__ldg(col16 + e) : __ldg(col32 + e);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// theta right-hand side on the free rows, as the initial residual of the
+// increment system (x0 = T^n):
+//   r0 = b - A_ff T^n_f = theta F^{n+1} + (1-theta) F^n - [K (T^n - T_c)]_f
+//        - A_fd (g^{n+1} - g^n)
+// (B - A = -K and K 1 = 0).  No large terms cancel, so the FP32 operator of
+// the mixed path keeps r0 accurate relative to the increment.  The M values
+// are read only for Dirichlet columns.
+// ---------------------------------------------------------------------------
+template <typename VT>
+struct RhsArgs {
+    Op<VT> K;              // free rows of K (unit k), all columns (internal)
+    const VT* Mval;        // free rows of M (unit rho c_p), same storage as K
+    const VT* dev;         // T^n - T_c
     const double* That;
     const double* gnew;
     const double* F0;
     const double* F1;
-    double inv_dt, kscale, theta;
-    double* rhs;
+    int n_free;
+    double inv_dt_rhocp, k, theta;
     double* r0;
 };
 
-// One warp per 32-row slice, lane = free row (SELL storage).
-__global__ void k_theta_rhs(RhsArgs a) {
+template <typename VT>
+__global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (sl >= a.n_slices) return;
+    if (sl >= a.K.n_slices) return;
     const int i = sl * 32 + lane;
-    const long long base = a.sptr[sl];
-    const int w = (int)((a.sptr[sl + 1] - base) >> 5);
-    double accb = 0.0, acca = 0.0;
-#pragma unroll 4
+    const int ir = min(i, a.n_free - 1);
+    const long long base = a.K.sptr[sl];
+    const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
+    VT acc = 0;
+    double accd = 0.0;
+#pragma unroll 8
     for (int k = 0; k < w; ++k) {
         const long long e = base + 32ll * k + lane;
-        const int j = __ldg(a.col + e);
-        const double m = __ldg(a.M + e) * a.inv_dt, kk = __ldg(a.K + e) * a.kscale;
-        const double T = a.That[j];
-        if (j < a.n_free) {
-            accb += m * T - kk * ((1.0 - a.theta) * T);
-            acca += (m + a.theta * kk) * T;
-        } else {
-            const double G = a.gnew[j - a.n_free];
-            accb += m * (T - G) - kk * ((1.0 - a.theta) * T + a.theta * G);
+        const int j = a.K.col(e, ir);
+        const VT kv = __ldg(a.K.val + e);
+        acc = fma(kv, a.dev[j], acc);
+        if (j >= a.n_free) {   // Dirichlet column: - A_ij (g^{n+1}_j - g^n_j)
+            const double Aij =
+                (double)__ldg(a.Mval + e) * a.inv_dt_rhocp + a.theta * a.k * (double)kv;
+            accd += Aij * (a.gnew[j - a.n_free] - a.That[j]);
         }
     }
-    if (i < a.n_free) {
-        const double b = accb + a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i];
-        a.rhs[i] = b;
-        a.r0[i] = b - acca;
-    }
+    if (i < a.n_free)
+        a.r0[i] = a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i] - a.k * (double)acc - accd;
 }
 
 // ---------------------------------------------------------------------------
-// grid barrier with a bounded wait (co-residency is guaranteed by the
-// cooperative launch; a wait that exceeds the limit flags SA_DEV_TIMEOUT and
-// the kernel returns instead of hanging)
+// synchronisation policies for the PCG body
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -120,44 +152,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned* vgen = gen;
-        const unsigned my = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            long long spins = 0;
-            while (*vgen == my) {
-                if ((++spins & 255) == 0) {
-                    if (global_ns() - t0 > 2000000000ull || spins > (1ll << 30)) {
-                        atomicOr(err, SA_DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
-                if (*((volatile int*)err) & SA_DEV_TIMEOUT) {
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// Deterministic block reduction of NV values per thread; thread 0 gets the
-// sums in out[] (fixed xor-tree within warps, fixed warp order).
+// Deterministic block reduction of NV values per thread into out[] (visible
+// to every thread on return): fixed xor tree in the warps, fixed warp order.
 template <int NV>
 __device__ void block_reduce(double (&v)[NV], double* out) {
     __shared__ double sred[NV][32];
@@ -168,198 +164,263 @@ __device__ void block_reduce(double (&v)[NV], double* out) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) sred[k][w] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double t = 0.0;
-            for (int ww = 0; ww < nw; ++ww) t += sred[k][ww];
-            out[k] = t;
-        }
-    __syncthreads();
-}
-
-// Sum of part[0..G) identical in every block (fixed order), broadcast to
-// all threads of the block.
-__device__ double grid_total(const double* part) {
-    __shared__ double res;
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < NV) {
         double t = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) t += ((volatile const double*)part)[i];
-        t = warp_sum(t);
-        if (threadIdx.x == 0) res = t;
+        for (int ww = 0; ww < nw; ++ww) t += sred[threadIdx.x][ww];
+        out[threadIdx.x] = t;
     }
     __syncthreads();
-    const double r = res;
-    __syncthreads();
-    return r;
 }
 
+// Grid-wide: per-block partials, a bounded-wait barrier (co-residency from
+// the cooperative launch; a wait over the limit flags SA_DEV_TIMEOUT and the
+// kernel returns), then every block sums all partials in the same order.
+struct GridSync {
+    unsigned* count;
+    unsigned* gen;
+    int* err;
+    double* part;
+    __device__ bool barrier() const {
+        __shared__ int ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ok = 1;
+            volatile unsigned* vgen = gen;
+            const unsigned my = *vgen;
+            __threadfence();
+            const unsigned arrived = atomicAdd(count, 1u) + 1u;
+            if (arrived == gridDim.x) {
+                atomicExch(count, 0u);
+                __threadfence();
+                atomicAdd(gen, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                long long spins = 0;
+                while (*vgen == my) {
+                    if ((++spins & 255) == 0) {
+                        if (global_ns() - t0 > 2000000000ull || spins > (1ll << 30)) {
+                            atomicOr(err, SA_DEV_TIMEOUT);
+                            ok = 0;
+                            break;
+                        }
+                        if (*((volatile int*)err) & SA_DEV_TIMEOUT) {
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        return ok != 0;
+    }
+    // slot: first of NV consecutive partial rows of length gridDim.x
+    template <int NV>
+    __device__ bool reduce(double (&v)[NV], int slot, double (&out)[NV]) const {
+        __shared__ double bl[NV];
+        __shared__ double res[NV];
+        block_reduce<NV>(v, bl);
+        const int G = gridDim.x;
+        if (threadIdx.x < NV) part[(slot + threadIdx.x) * G + blockIdx.x] = bl[threadIdx.x];
+        if (!barrier()) return false;
+        if (threadIdx.x < 32) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const volatile double* pk = part + (slot + k) * G;
+                double t = 0.0;
+                for (int i = threadIdx.x; i < G; i += 32) t += pk[i];
+                t = warp_sum(t);
+                if (threadIdx.x == 0) res[k] = t;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = res[k];
+        __syncthreads();
+        return true;
+    }
+};
+
+// One block: __syncthreads only.
+struct BlockSync {
+    template <int NV>
+    __device__ bool reduce(double (&v)[NV], int, double (&out)[NV]) const {
+        __shared__ double res[NV];
+        block_reduce<NV>(v, res);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = res[k];
+        __syncthreads();
+        return true;
+    }
+};
+
+template <typename VT>
 struct PcgArgs {
-    int n;
-    int n_slices;
-    const long long* sptr;     // SELL operator
-    const int* col;
-    const double* val;
+    Op<VT> A;
+    const double* val_hi;  // FP64 values of A (mode 0 initial residual); may equal A.val
     const double* dinv;
-    const double* b;
-    const double* r0;      // optional initial residual (x0 = x)
+    const double* b;       // mode 0: right-hand side
+    const double* r0;      // mode 1: initial residual (x0 = x); b = r0 + A x for the norm
     double* x;
     double* r;
     double* z;
     double* p0;
     double* p1;
     double* q;
-    double* part;          // 6 * gridDim.x
+    VT* zl;                // low-precision copies (mixed path; unused in FP64)
+    VT* pl0;
+    VT* pl1;
+    double* part;
     DevStatus* st;
     int which;             // 0 main solve, 1 bottom projection
     double tol;
     int max_iter;
 };
 
-// Jacobi-preconditioned CG (Hestenes-Stiefel) in FP64.  The update of the
-// search direction p = z + beta p is fused into the next SpMV (p double
-// buffered), so one iteration is two grid phases:
+// Jacobi-preconditioned CG (Hestenes-Stiefel).  The update p = z + beta p
+// is fused into the next SpMV (p double buffered), so one iteration is two
+// phases with one reduction each:
 //   B: p' = z + beta p ; q = A p' ; (p', q)
 //   C: x += alpha p' ; r -= alpha q ; z = D^{-1} r ; (r, r), (r, z)
-// SpMV: SELL-32, one warp per slice (lane = row), slices grid-strided over
-// the warps; the k loop is unrolled so each lane keeps several independent
-// coalesced loads in flight.
-__global__ void __launch_bounds__(512) k_pcg(PcgArgs a) {
-    const int n = a.n;
-    const int G = gridDim.x;
+// SpMV: SELL-32, one warp per slice (lane = row), slices strided over the
+// warps (gw, nw); vectors strided over the threads (tid, nth).
+template <typename VT, class Sync>
+__device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw, int tid,
+                         int nth) {
+    constexpr bool LO = std::is_same<VT, float>::value;
+    const int n = a.A.n;
     const int lane = threadIdx.x & 31;
-    const int nwb = blockDim.x >> 5;
-    const int gw = blockIdx.x * nwb + (threadIdx.x >> 5);
-    const int nw = G * nwb;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nth = G * blockDim.x;
-    unsigned* bc = &a.st->bar_count[a.which];
-    unsigned* bg = &a.st->bar_gen[a.which];
-    int* err = &a.st->err;
-    __shared__ double red[3];
-
-    // ---- phase A: r = b - A x (or given), z = D^{-1} r, (r,z), (r,r), (b,b)
+    double red[3];
+    // ---- phase A
     {
         double v[3] = {0.0, 0.0, 0.0};
-        if (a.r0 == nullptr) {
-            for (int sl = gw; sl < a.n_slices; sl += nw) {
-                const long long base = a.sptr[sl];
-                const int w = (int)((a.sptr[sl + 1] - base) >> 5);
-                double acc = 0.0;
+        for (int sl = gw; sl < a.A.n_slices; sl += nw) {
+            const long long base = a.A.sptr[sl];
+            const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
+            const int i = sl * 32 + lane;
+            const int ir = min(i, n - 1);
+            double acc = 0.0;
+            if (a.r0 == nullptr) {   // r = b - A x with the FP64 values
+#pragma unroll 4
+                for (int k = 0; k < w; ++k) {
+                    const long long e = base + 32ll * k + lane;
+                    acc = fma(__ldg(a.val_hi + e), a.x[a.A.col(e, ir)], acc);
+                }
+            } else {                 // A x for the norm of b only
+                VT s = 0;
 #pragma unroll 8
                 for (int k = 0; k < w; ++k) {
                     const long long e = base + 32ll * k + lane;
-                    acc = fma(__ldg(a.val + e), a.x[__ldg(a.col + e)], acc);
+                    s = fma(__ldg(a.A.val + e), (VT)a.x[a.A.col(e, ir)], s);
                 }
-                const int i = sl * 32 + lane;
-                if (i < n) {
-                    const double ri = a.b[i] - acc;
-                    const double zi = a.dinv[i] * ri;
-                    a.r[i] = ri;
-                    a.z[i] = zi;
-                    v[0] += ri * zi;
-                    v[1] += ri * ri;
-                    v[2] += a.b[i] * a.b[i];
-                }
+                acc = (double)s;
             }
-        } else {
-            for (int i = tid; i < n; i += nth) {
-                const double ri = a.r0[i];
+            if (i < n) {
+                double ri, bi;
+                if (a.r0 == nullptr) {
+                    bi = a.b[i];
+                    ri = bi - acc;
+                } else {
+                    ri = a.r0[i];
+                    bi = ri + acc;
+                }
                 const double zi = a.dinv[i] * ri;
                 a.r[i] = ri;
                 a.z[i] = zi;
+                if (LO) a.zl[i] = (VT)zi;
                 v[0] += ri * zi;
                 v[1] += ri * ri;
-                v[2] += a.b[i] * a.b[i];
+                v[2] += bi * bi;
             }
         }
-        block_reduce<3>(v, red);
-        if (threadIdx.x == 0) {
-            a.part[0 * G + blockIdx.x] = red[0];
-            a.part[1 * G + blockIdx.x] = red[1];
-            a.part[2 * G + blockIdx.x] = red[2];
-        }
+        if (!sync.template reduce<3>(v, 0, red)) return;
     }
-    if (!grid_barrier(bc, bg, err)) return;
-    double rz = grid_total(a.part + 0 * G);
-    double rr = grid_total(a.part + 1 * G);
-    const double bb = grid_total(a.part + 2 * G);
+    double rz = red[0], rr = red[1];
+    const double bb = red[2];
     const double stop2 = a.tol * a.tol * bb;
     int it = 0;
     double beta = 0.0;
     bool conv = rr <= stop2;
+    bool nan = !(rr == rr);
     double* pc = a.p0;
     double* pn = a.p1;
-    bool nan = !(rr == rr);
+    VT* plc = LO ? a.pl0 : (VT*)a.p0;
+    VT* pln = LO ? a.pl1 : (VT*)a.p1;
+    const VT* zl = LO ? a.zl : (const VT*)a.z;
     while (!conv && !nan && it < a.max_iter) {
         // ---- phase B
+        double pq;
         {
             double v[1] = {0.0};
             const bool first = (it == 0);
-            for (int sl = gw; sl < a.n_slices; sl += nw) {
-                const long long base = a.sptr[sl];
-                const int w = (int)((a.sptr[sl + 1] - base) >> 5);
-                double acc = 0.0;
+            const VT bl = (VT)beta;
+            for (int sl = gw; sl < a.A.n_slices; sl += nw) {
+                const long long base = a.A.sptr[sl];
+                const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
+                const int i = sl * 32 + lane;
+                const int ir = min(i, n - 1);
+                VT acc = 0;
                 if (first) {
 #pragma unroll 8
                     for (int k = 0; k < w; ++k) {
                         const long long e = base + 32ll * k + lane;
-                        acc = fma(__ldg(a.val + e), a.z[__ldg(a.col + e)], acc);
+                        acc = fma(__ldg(a.A.val + e), zl[a.A.col(e, ir)], acc);
                     }
                 } else {
 #pragma unroll 8
                     for (int k = 0; k < w; ++k) {
                         const long long e = base + 32ll * k + lane;
-                        const int j = __ldg(a.col + e);
-                        acc = fma(__ldg(a.val + e), fma(beta, pc[j], a.z[j]), acc);
+                        const int j = a.A.col(e, ir);
+                        acc = fma(__ldg(a.A.val + e), fma(bl, plc[j], zl[j]), acc);
                     }
                 }
-                const int i = sl * 32 + lane;
                 if (i < n) {
                     const double pi = first ? a.z[i] : fma(beta, pc[i], a.z[i]);
                     pn[i] = pi;
-                    a.q[i] = acc;
-                    v[0] += pi * acc;
+                    if (LO) pln[i] = (VT)pi;
+                    a.q[i] = (double)acc;
+                    v[0] += pi * (double)acc;
                 }
             }
-            block_reduce<1>(v, red);
-            if (threadIdx.x == 0) a.part[3 * G + blockIdx.x] = red[0];
+            double o[1];
+            if (!sync.template reduce<1>(v, 3, o)) return;
+            pq = o[0];
         }
-        if (!grid_barrier(bc, bg, err)) return;
-        const double pq = grid_total(a.part + 3 * G);
         const double alpha = rz / pq;
         // ---- phase C
         {
             double v[2] = {0.0, 0.0};
             for (int i = tid; i < n; i += nth) {
-                a.x[i] += alpha * pn[i];
-                const double ri = a.r[i] - alpha * a.q[i];
+                a.x[i] = fma(alpha, pn[i], a.x[i]);
+                const double ri = fma(-alpha, a.q[i], a.r[i]);
                 const double zi = a.dinv[i] * ri;
                 a.r[i] = ri;
                 a.z[i] = zi;
+                if (LO) a.zl[i] = (VT)zi;
                 v[0] += ri * ri;
                 v[1] += ri * zi;
             }
-            block_reduce<2>(v, red);
-            if (threadIdx.x == 0) {
-                a.part[4 * G + blockIdx.x] = red[0];
-                a.part[5 * G + blockIdx.x] = red[1];
-            }
+            double o[2];
+            if (!sync.template reduce<2>(v, 4, o)) return;
+            rr = o[0];
+            const double rzn = o[1];
+            ++it;
+            nan = !(rr == rr) || !(pq == pq);
+            conv = rr <= stop2;
+            beta = rzn / rz;
+            rz = rzn;
         }
-        if (!grid_barrier(bc, bg, err)) return;
-        rr = grid_total(a.part + 4 * G);
-        const double rzn = grid_total(a.part + 5 * G);
-        ++it;
-        nan = !(rr == rr) || !(pq == pq);
-        conv = rr <= stop2;
-        beta = rzn / rz;
-        rz = rzn;
         double* t = pc;
         pc = pn;
         pn = t;
+        VT* tl = plc;
+        plc = pln;
+        pln = tl;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+        int* err = &a.st->err;
         if (a.which == 0) {
             a.st->pcg_iters = it;
             a.st->rel_res = rel;
@@ -371,6 +432,22 @@ __global__ void __launch_bounds__(512) k_pcg(PcgArgs a) {
         }
         if (nan) atomicOr(err, SA_DEV_NAN);
     }
+}
+
+constexpr int kPcgBlock = 1024;
+
+template <typename VT>
+__global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_grid(PcgArgs<VT> a) {
+    GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
+    const int nwb = blockDim.x >> 5;
+    pcg_body<VT, GridSync>(a, sync, blockIdx.x * nwb + (threadIdx.x >> 5), gridDim.x * nwb,
+                           blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_block(PcgArgs<VT> a) {
+    BlockSync sync;
+    pcg_body<VT, BlockSync>(a, sync, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x);
 }
 
 __global__ void k_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
@@ -386,49 +463,49 @@ __global__ void k_finalize(int n_dir, int n_free, int n_dof, const double* gnew,
     }
 }
 
-}  // namespace
-
-cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat_ptr,
-                          const int* wlat_col, const double* wlat_val, const double* s_lat,
-                          double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
-                          const double* wbot_val, const double* tt_bot, double Tc, double* F1,
-                          double* bbot, cudaStream_t s) {
-    GatherArgs a{wlat_rows, wlat_rowdof, wlat_ptr, wlat_col, wlat_val, s_lat, k, n_dir,
-                 wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot};
-    const long long rows = (long long)wlat_rows + n_dir;
-    if (rows == 0) return cudaSuccess;
-    k_gather<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
+template <typename VT>
+Op<VT> make_op(const SellView& s, const void* val) {
+    Op<VT> o;
+    o.n = s.n;
+    o.n_slices = s.n_slices;
+    o.sptr = s.sptr;
+    o.col32 = s.col32;
+    o.col16 = s.col16;
+    o.val = (const VT*)val;
+    return o;
 }
 
-cudaError_t launch_theta_rhs(int n_free, int n_slices, const long long* sptr, const int* col,
-                             const double* M, const double* K, const double* That,
-                             const double* gnew, const double* F0, const double* F1,
-                             double inv_dt, double kscale, double theta, double* rhs,
-                             double* r0, cudaStream_t s) {
-    RhsArgs a{n_free, n_slices, sptr, col, M, K, That, gnew, F0, F1, inv_dt, kscale, theta, rhs,
-              r0};
-    if (n_free == 0) return cudaSuccess;
-    k_theta_rhs<<<(unsigned)(((long long)n_slices * 32 + 255) / 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-int pcg_block_size() { return 512; }
-const void* pcg_kernel_ptr() { return (const void*)k_pcg; }
-
-cudaError_t launch_pcg(int which, int n, int n_slices, const long long* sptr, const int* col,
-                       const double* val, const double* dinv, const double* b,
-                       const double* r0_or_null, double* x, double* r, double* z, double* p0,
-                       double* p1, double* q, double* partials, DevStatus* st, double tol,
-                       int max_iter, int grid, int block, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    PcgArgs a{n, n_slices, sptr, col, val, dinv, b, r0_or_null, x, r, z, p0, p1, q, partials, st,
-              which, tol, max_iter};
-    cudaError_t e = cudaMemsetAsync(&st->bar_count[which], 0, sizeof(unsigned), s);
+template <typename VT>
+cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
+    PcgArgs<VT> a;
+    a.A = make_op<VT>(L.op, L.val);
+    a.val_hi = L.val_hi;
+    a.dinv = L.dinv;
+    a.b = L.b;
+    a.r0 = L.r0;
+    a.x = L.x;
+    a.r = L.r;
+    a.z = L.z;
+    a.p0 = L.p0;
+    a.p1 = L.p1;
+    a.q = L.q;
+    a.zl = (VT*)L.zl;
+    a.pl0 = (VT*)L.pl0;
+    a.pl1 = (VT*)L.pl1;
+    a.part = L.partials;
+    a.st = L.st;
+    a.which = L.which;
+    a.tol = L.tol;
+    a.max_iter = L.max_iter;
+    if (L.grid <= 1) {
+        k_pcg_block<VT><<<1, kPcgBlock, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
+    cfg.gridDim = dim3(L.grid);
+    cfg.blockDim = dim3(kPcgBlock);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -436,7 +513,52 @@ cudaError_t launch_pcg(int which, int n, int n_slices, const long long* sptr, co
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pcg, a);
+    return cudaLaunchKernelEx(&cfg, k_pcg_grid<VT>, a);
+}
+
+}  // namespace
+
+cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat_ptr,
+                          const int* wlat_col, const double* wlat_val, const double* s_lat,
+                          double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
+                          const double* wbot_val, const double* tt_bot, double Tc, double* F1,
+                          double* bbot, int n_dof, const double* That, double* dev64,
+                          float* dev32, cudaStream_t s) {
+    GatherArgs a{wlat_rows, wlat_rowdof, wlat_ptr, wlat_col, wlat_val, s_lat, k, n_dir,
+                 wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot, n_dof, That, dev64, dev32};
+    const long long threads = 32ll * ((long long)wlat_rows + n_dir) + n_dof;
+    if (threads == 0) return cudaSuccess;
+    k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
+                             const void* Mval, const void* dev, const double* That,
+                             const double* gnew, const double* F0, const double* F1,
+                             double inv_dt_rhocp, double k, double theta, double* r0,
+                             cudaStream_t s) {
+    if (op.n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(((long long)op.n_slices * 32 + 255) / 256);
+    if (precision == SA_MIXED) {
+        RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, That,
+                         gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, r0};
+        k_theta_rhs<float><<<blocks, 256, 0, s>>>(a);
+    } else {
+        RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev,
+                          That, gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, r0};
+        k_theta_rhs<double><<<blocks, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int pcg_block_size() { return kPcgBlock; }
+const void* pcg_kernel_ptr(int precision) {
+    return precision == SA_MIXED ? (const void*)k_pcg_grid<float> : (const void*)k_pcg_grid<double>;
+}
+
+cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s) {
+    if (L.op.n == 0) return cudaSuccess;
+    return precision == SA_MIXED ? launch_pcg_t<float>(L, s) : launch_pcg_t<double>(L, s);
 }
 
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
