@@ -794,7 +794,12 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                        &occ, pcg_kernel_ptr(c->opt.precision), pcg_block_size(), 0));
         if (occ < 1) return sa_fail(c, SA_ERR_CUDA, "PCG kernel cannot be resident");
         c->pcg_block = pcg_block_size();
-        c->pcg_grid = c->num_sms;   // one co-resident block of 512 threads per SM
+        c->pcg_grid = c->num_sms;   // one co-resident block of 1024 threads per SM
+        // split each slice over enough warps to fill the grid (at most 8)
+        const int warps = c->pcg_grid * (pcg_block_size() / 32);
+        int ks = 1;
+        while (ks < 8 && c->a_s.n_slices * ks * 2 <= warps) ks *= 2;
+        c->pcg_ksplit = ks;
         SA_ALLOC(c, c->partials, (size_t)6 * c->pcg_grid);
     }
     SA_CUDA(c, cudaStreamSynchronize(s));
@@ -950,7 +955,9 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
-        L.grid = c->n_dir <= 32768 ? 1 : c->pcg_grid;
+        // small system: a few blocks (cheap barriers), slices split 4 ways
+        L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices * 4 + 31) / 32));
+        L.ksplit = 4;
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
@@ -985,6 +992,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
         L.grid = c->pcg_grid;
+        L.ksplit = c->pcg_ksplit;
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
     }

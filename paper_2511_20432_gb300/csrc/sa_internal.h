@@ -141,6 +141,7 @@ struct PcgLaunch {
     double tol;
     int max_iter;
     int grid;                 // 1: one block, no grid barrier
+    int ksplit;               // warps per SELL slice in the SpMV (1, 2, 4, 8)
 };
 
 // ---------------------------------------------------------------------------
@@ -250,7 +251,7 @@ struct sa_ctx {
     DBuf<float> dev32;
     DBuf<double> partials;    // 4 * max grid
     DBuf<DevStatus> st;
-    int pcg_grid = 0, pcg_block = 0;
+    int pcg_grid = 0, pcg_block = 0, pcg_ksplit = 1;
     int hist_P = 0, hist_W = 0;
 
     // ---- device: set-up and evaluation helpers ---------------------------------

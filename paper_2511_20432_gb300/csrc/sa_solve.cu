@@ -276,6 +276,8 @@ struct PcgArgs {
     int which;             // 0 main solve, 1 bottom projection
     double tol;
     int max_iter;
+    int ksplit;            // warps per slice in the SpMV (divides the warps of a block)
+    VT* sq;                // shared scratch for the split partial sums (set in-kernel)
 };
 
 // Jacobi-preconditioned CG (Hestenes-Stiefel).  The update p = z + beta p
@@ -349,39 +351,60 @@ __device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw,
     VT* pln = LO ? a.pl1 : (VT*)a.p1;
     const VT* zl = LO ? a.zl : (const VT*)a.z;
     while (!conv && !nan && it < a.max_iter) {
-        // ---- phase B
+        // ---- phase B (each slice split over KS consecutive warps of a block)
         double pq;
         {
             double v[1] = {0.0};
             const bool first = (it == 0);
             const VT bl = (VT)beta;
-            for (int sl = gw; sl < a.A.n_slices; sl += nw) {
-                const long long base = a.A.sptr[sl];
-                const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
-                const int i = sl * 32 + lane;
-                const int ir = min(i, n - 1);
+            const int nwb = blockDim.x >> 5;
+            const int wib = threadIdx.x >> 5;
+            const int KS = a.ksplit;
+            const int units = a.A.n_slices * KS;
+            const int rounds = (units + nw - 1) / nw;
+            for (int rd = 0; rd < rounds; ++rd) {
+                const int u = rd * nw + gw;
+                const int sl = u / KS, h = u % KS;
                 VT acc = 0;
-                if (first) {
+                if (sl < a.A.n_slices) {
+                    const long long base = a.A.sptr[sl];
+                    const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
+                    const int chunk = (w + KS - 1) / KS;
+                    const int k0 = h * chunk, k1 = min(w, k0 + chunk);
+                    const int ir = min(sl * 32 + lane, n - 1);
+                    if (first) {
 #pragma unroll 8
-                    for (int k = 0; k < w; ++k) {
-                        const long long e = base + 32ll * k + lane;
-                        acc = fma(__ldg(a.A.val + e), zl[a.A.col(e, ir)], acc);
-                    }
-                } else {
+                        for (int k = k0; k < k1; ++k) {
+                            const long long e = base + 32ll * k + lane;
+                            acc = fma(__ldg(a.A.val + e), zl[a.A.col(e, ir)], acc);
+                        }
+                    } else {
 #pragma unroll 8
-                    for (int k = 0; k < w; ++k) {
-                        const long long e = base + 32ll * k + lane;
-                        const int j = a.A.col(e, ir);
-                        acc = fma(__ldg(a.A.val + e), fma(bl, plc[j], zl[j]), acc);
+                        for (int k = k0; k < k1; ++k) {
+                            const long long e = base + 32ll * k + lane;
+                            const int j = a.A.col(e, ir);
+                            acc = fma(__ldg(a.A.val + e), fma(bl, plc[j], zl[j]), acc);
+                        }
                     }
                 }
-                if (i < n) {
-                    const double pi = first ? a.z[i] : fma(beta, pc[i], a.z[i]);
-                    pn[i] = pi;
-                    if (LO) pln[i] = (VT)pi;
-                    a.q[i] = (double)acc;
-                    v[0] += pi * (double)acc;
+                if (KS > 1) {
+                    a.sq[wib * 32 + lane] = acc;
+                    __syncthreads();
                 }
+                if (h == 0 && sl < a.A.n_slices) {
+                    VT tot = acc;
+                    for (int hh = 1; hh < KS; ++hh) tot += a.sq[(wib + hh) * 32 + lane];
+                    const int i = sl * 32 + lane;
+                    if (i < n) {
+                        const double pi = first ? a.z[i] : fma(beta, pc[i], a.z[i]);
+                        pn[i] = pi;
+                        if (LO) pln[i] = (VT)pi;
+                        a.q[i] = (double)tot;
+                        v[0] += pi * (double)tot;
+                    }
+                }
+                if (KS > 1) __syncthreads();
+                (void)nwb;
             }
             double o[1];
             if (!sync.template reduce<1>(v, 3, o)) return;
@@ -438,6 +461,8 @@ constexpr int kPcgBlock = 1024;
 
 template <typename VT>
 __global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_grid(PcgArgs<VT> a) {
+    __shared__ VT sq[kPcgBlock];
+    a.sq = sq;
     GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
     const int nwb = blockDim.x >> 5;
     pcg_body<VT, GridSync>(a, sync, blockIdx.x * nwb + (threadIdx.x >> 5), gridDim.x * nwb,
@@ -446,6 +471,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_grid(PcgArgs<VT> a) {
 
 template <typename VT>
 __global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_block(PcgArgs<VT> a) {
+    __shared__ VT sq[kPcgBlock];
+    a.sq = sq;
     BlockSync sync;
     pcg_body<VT, BlockSync>(a, sync, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x);
 }
@@ -497,6 +524,8 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     a.which = L.which;
     a.tol = L.tol;
     a.max_iter = L.max_iter;
+    a.ksplit = L.ksplit > 0 ? L.ksplit : 1;
+    a.sq = nullptr;
     if (L.grid <= 1) {
         k_pcg_block<VT><<<1, kPcgBlock, 0, s>>>(a);
         return cudaGetLastError();
