@@ -240,6 +240,35 @@ enum { SA_STAGE_PROLOGUE = 0,  /* source coefficients of the step               
  * ms: SA_N_STAGES doubles (host). */
 sa_status sa_get_stage_times(sa_ctx* ctx, double* ms, long long* steps);
 
+/*
+ * Batches: many independent instances (uneven patches, different scans and
+ * powers; one material, one theta and dt) stepped together with one launch
+ * per stage, replayed as one CUDA graph per step when use_graph is set and a
+ * stream is given.  The instances' operators, boundary weights, points and
+ * sources are concatenated (block-diagonal operators, every instance padded
+ * to whole 32-row slices and 128-point tiles); the PCG keeps per-instance
+ * dot products, step lengths and convergence tests (Sections 2.3-2.4 for
+ * each instance, unchanged).  sa_batch_create takes contexts that have a
+ * patch, material and scan and are at the same step; the batch copies their
+ * state at its first step and owns it from then on (read it back with
+ * sa_batch_get_field); the contexts must outlive the batch.
+ */
+typedef struct sa_batch sa_batch;
+sa_status sa_batch_create(sa_ctx* const* insts, int n_inst, const sa_options* o, sa_batch** out);
+sa_status sa_batch_step(sa_batch* b, double theta, double dt, int n_steps, sa_step_stats* stats);
+/* fields SA_FIELD_THAT, SA_FIELD_F (natural order of instance inst),
+ * SA_FIELD_DTDN_LAT, SA_FIELD_TT_BOT; host buffer */
+sa_status sa_batch_get_field(sa_batch* b, int inst, int field, double* out, long long count);
+/* PCG iterations of the last step per instance (main, bottom projection) */
+sa_status sa_batch_get_iters(sa_batch* b, int* main_iters, int* bottom_iters);
+/* Autotuner of the history-sum tile (points per lane x warps): times every
+ * shape on the batch's data (CUDA events), keeps the fastest and appends the
+ * choice to the JSON-lines file cache_path (NULL: no cache), keyed by the
+ * batch sizes; a cached choice is reused without timing (*best_ms = -1). */
+sa_status sa_batch_autotune(sa_batch* b, const char* cache_path, int* P, int* NW, double* best_ms);
+const char* sa_batch_last_error(const sa_batch* b);
+void sa_batch_destroy(sa_batch* b);
+
 void sa_destroy(sa_ctx* ctx);
 const char* sa_status_str(sa_status s);
 const char* sa_last_error(const sa_ctx* ctx);

@@ -73,6 +73,13 @@ def _load():
         "sa_get_state": (I, [P, C.POINTER(LL), P, P]),
         "sa_set_state": (I, [P, LL, P, P]),
         "sa_get_stage_times": (I, [P, P, C.POINTER(LL)]),
+        "sa_batch_create": (I, [P, I, C.POINTER(sa_options), C.POINTER(P)]),
+        "sa_batch_step": (I, [P, D, D, I, C.POINTER(sa_step_stats)]),
+        "sa_batch_get_field": (I, [P, I, I, P, LL]),
+        "sa_batch_get_iters": (I, [P, P, P]),
+        "sa_batch_autotune": (I, [P, C.c_char_p, C.POINTER(I), C.POINTER(I), C.POINTER(D)]),
+        "sa_batch_last_error": (C.c_char_p, [P]),
+        "sa_batch_destroy": (V, [P]),
         "sa_destroy": (V, [P]),
         "sa_status_str": (C.c_char_p, [I]),
         "sa_last_error": (C.c_char_p, [P]),
@@ -226,6 +233,62 @@ class Context:
         T = np.ascontiguousarray(T, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.float64)
         _check(self.ptr, lib.sa_set_state(self.ptr, int(n), _ptr(T), _ptr(F)))
+
+
+class Batch:
+    """Owns one sa_batch over existing Contexts (kept alive here)."""
+
+    def __init__(self, contexts, opts: sa_options | None = None, **kw):
+        self.contexts = list(contexts)
+        self.ptr = C.c_void_p()
+        o = opts if opts is not None else options(**kw)
+        self._opts = o
+        arr = (C.c_void_p * len(self.contexts))(*[c.ptr.value for c in self.contexts])
+        st = lib.sa_batch_create(C.cast(arr, C.c_void_p), len(self.contexts), C.byref(o),
+                                 C.byref(self.ptr))
+        if st != SA_OK:
+            raise SAError(st, "sa_batch_create")
+
+    def _check(self, st):
+        if st != SA_OK:
+            raise SAError(st, lib.sa_batch_last_error(self.ptr).decode())
+
+    def close(self):
+        if self.ptr:
+            lib.sa_batch_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, theta, dt, n_steps=1, stats=True):
+        st = sa_step_stats() if stats else None
+        self._check(lib.sa_batch_step(self.ptr, theta, dt, int(n_steps),
+                                      C.byref(st) if st is not None else None))
+        return st
+
+    def field(self, inst, which):
+        s = self.contexts[inst].sizes()
+        n = {SA_FIELD_THAT: s.n_dof, SA_FIELD_F: s.n_dof, SA_FIELD_DTDN_LAT: s.q_lat,
+             SA_FIELD_TT_BOT: s.q_bot}[which]
+        o = np.empty(max(n, 1))
+        self._check(lib.sa_batch_get_field(self.ptr, int(inst), int(which), _ptr(o), int(n)))
+        return o[:n]
+
+    def iters(self):
+        m = np.zeros(len(self.contexts), dtype=np.int32)
+        b = np.zeros(len(self.contexts), dtype=np.int32)
+        self._check(lib.sa_batch_get_iters(self.ptr, _ptr(m), _ptr(b)))
+        return m, b
+
+    def autotune(self, cache_path=None):
+        P, W, ms = C.c_int(), C.c_int(), C.c_double()
+        path = cache_path.encode() if cache_path else None
+        self._check(lib.sa_batch_autotune(self.ptr, path, C.byref(P), C.byref(W), C.byref(ms)))
+        return P.value, W.value, ms.value
 
 
 def context_from_workload(wl, precision=SA_FP64, s_img=2.0, **opts):

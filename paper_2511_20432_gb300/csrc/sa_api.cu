@@ -101,13 +101,6 @@ void build_w_csr(int n_rows, const std::vector<int>& erow, const std::vector<int
 // SELL-32 layout of a row list: rows r = 0..n-1 with entries
 // (col, src) in [ptr[r], ptr[r+1]); diag = storage index of col == diag_col[r]
 // (diag_col may be empty: no diagonal needed).
-struct SellHost {
-    int n = 0, n_slices = 0;
-    std::vector<long long> sptr;
-    std::vector<int> col, src, diag;
-    std::vector<short> col16;   // column - row, filled when every offset fits
-};
-
 void build_sell(int n, const std::vector<long long>& ptr, const std::vector<int>& col,
                 const std::vector<int>& src, const std::vector<int>& diag_col, SellHost& out) {
     out.n = n;
@@ -531,6 +524,9 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             for (size_t e = 0; e < erow.size(); ++e) er[e] = rmap[erow[e]];
             build_w_csr((int)rows.size(), er, ecol, ptr, col, slot);
             c->wlat_rows = (int)rows.size();
+            c->wlat_rowdof_h = rows;
+            c->wlat_ptr_h = ptr;
+            c->wlat_col_h = col;
             c->q_lat = Q;
             SA_UPLOAD(c, c->wlat_rowdof, rows);
             SA_UPLOAD(c, c->wlat_ptr, ptr);
@@ -544,6 +540,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                 if (er[e] < 0) return sa_fail(c, SA_ERR_GEOMETRY, "Dirichlet face function is not a Dirichlet dof");
             }
             build_w_csr(c->n_dir, er, ecol, ptr, col, slot);
+            c->wbot_ptr_h = ptr;
+            c->wbot_col_h = col;
             for (int r = 0; r < c->n_dir; ++r)
                 if (ptr[r + 1] == ptr[r])
                     return sa_fail(c, SA_ERR_GEOMETRY, "Dirichlet dof without support on a Dirichlet face");
@@ -624,6 +622,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                 SellHost sh;
                 build_sell(c->n_dir, p64, mcol, srcs, dcol, sh);
                 SA_UPLOAD_SELL(c, c->mbot_s, sh);
+                c->mbot_h = sh;
                 SA_ALLOC(c, c->mbot_sval, sh.col.size());
                 e = launch_sell_fill(c->mbot_s.n_stored, c->mbot_s.src.p, c->mbot_val.p, 1.0,
                                      nullptr, 0.0, c->mbot_sval.p, s);
@@ -742,6 +741,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         SA_ALLOC(c, c->a_dinv, std::max(c->n_free, 1));
         build_sell(c->n_free, r_ptr, r_col, r_src, dcol, sr_h);
         SA_UPLOAD_SELL(c, c->r_s, sr_h);
+        c->a_h = sa_h;
+        c->r_h = sr_h;
         SA_ALLOC(c, c->r_M, sr_h.col.size());
         SA_ALLOC(c, c->r_K, sr_h.col.size());
         cudaError_t e = launch_sell_fill(c->r_s.n_stored, c->r_s.src.p, c->M.p, 1.0, nullptr, 0.0,
@@ -767,17 +768,18 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_ALLOC(c, c->bbot, std::max(c->n_dir, 1));
     SA_ALLOC(c, c->rhs, nwork);
     SA_ALLOC(c, c->r0, nwork);
-    SA_ALLOC(c, c->wr, nwork);
-    SA_ALLOC(c, c->wz, nwork);
-    SA_ALLOC(c, c->wp0, nwork);
-    SA_ALLOC(c, c->wp1, nwork);
-    SA_ALLOC(c, c->wq, nwork);
+    c->nwork = nwork;
+    SA_ALLOC(c, c->work64, (size_t)7 * nwork);
     SA_ALLOC(c, c->dev64, ndof);
     SA_ALLOC(c, c->dev32, ndof);
     if (c->opt.precision == SA_MIXED) {
-        SA_ALLOC(c, c->wzl, nwork);
-        SA_ALLOC(c, c->wpl0, nwork);
-        SA_ALLOC(c, c->wpl1, nwork);
+        SA_ALLOC(c, c->work32, (size_t)6 * nwork);
+        SA_ALLOC(c, c->a_dinv32, std::max(c->n_free, 1));
+        SA_ALLOC(c, c->mbot_dinv32, std::max(c->n_dir, 1));
+        if (c->n_dir > 0) {
+            cudaError_t e = launch_to_f32(c->n_dir, c->mbot_dinv.p, c->mbot_dinv32.p, s);
+            if (e != cudaSuccess) return sa_cuda_fail(c, e, "dinv FP32");
+        }
     }
     SA_ALLOC(c, c->s_lat, std::max(c->q_lat, 1));
     SA_ALLOC(c, c->tt_bot, std::max(c->q_bot, 1));
@@ -785,8 +787,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_CUDA(c, cudaMemsetAsync(c->F1.p, 0, sizeof(double) * ndof, s));
     SA_CUDA(c, cudaMemsetAsync(c->s_lat.p, 0, sizeof(double) * std::max(c->q_lat, 1), s));
     SA_CUDA(c, cudaMemsetAsync(c->tt_bot.p, 0, sizeof(double) * std::max(c->q_bot, 1), s));
-    SA_CUDA(c, cudaMemsetAsync(c->wp0.p, 0, sizeof(double) * nwork, s));
-    SA_CUDA(c, cudaMemsetAsync(c->wp1.p, 0, sizeof(double) * nwork, s));
+    SA_CUDA(c, cudaMemsetAsync(c->work64.p, 0, sizeof(double) * 7 * nwork, s));
     // PCG launch shape: co-resident blocks (cooperative launch)
     {
         int occ = 0;
@@ -800,7 +801,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         int ks = 1;
         while (ks < 8 && c->a_s.n_slices * ks * 2 <= warps) ks *= 2;
         c->pcg_ksplit = ks;
-        SA_ALLOC(c, c->partials, (size_t)6 * c->pcg_grid);
+        SA_ALLOC(c, c->partials, (size_t)11 * c->pcg_grid);
     }
     SA_CUDA(c, cudaStreamSynchronize(s));
     c->has_patch = true;
@@ -887,6 +888,8 @@ sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
     if (e == cudaSuccess) e = launch_sell_dinv(c->n_free, c->a_s.diag.p, c->a_val.p, c->a_dinv.p, c->stream);
     if (e == cudaSuccess && c->opt.precision == SA_MIXED)
         e = launch_to_f32(c->a_s.n_stored, c->a_val.p, c->a_val32.p, c->stream);
+    if (e == cudaSuccess && c->opt.precision == SA_MIXED)
+        e = launch_to_f32(c->n_free, c->a_dinv.p, c->a_dinv32.p, c->stream);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "build A");
     c->op_dt = dt;
     c->op_theta = theta;
@@ -939,17 +942,13 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.val = mixed ? (const void*)c->mbot_sval32.p : (const void*)c->mbot_sval.p;
         L.val_hi = c->mbot_sval.p;
         L.dinv = c->mbot_dinv.p;
+        L.dinvl = mixed ? (const void*)c->mbot_dinv32.p : (const void*)c->mbot_dinv.p;
         L.b = c->bbot.p;
         L.r0 = nullptr;
         L.x = c->gnew.p;
-        L.r = c->wr.p;
-        L.z = c->wz.p;
-        L.p0 = c->wp0.p;
-        L.p1 = c->wp1.p;
-        L.q = c->wq.p;
-        L.zl = c->wzl.p;
-        L.pl0 = c->wpl0.p;
-        L.pl1 = c->wpl1.p;
+        L.w64 = c->work64.p;
+        L.w32 = c->work32.p;
+        L.stride = c->nwork;
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.which = 1;
@@ -975,17 +974,13 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.val = mixed ? (const void*)c->a_val32.p : (const void*)c->a_val.p;
         L.val_hi = c->a_val.p;
         L.dinv = c->a_dinv.p;
+        L.dinvl = mixed ? (const void*)c->a_dinv32.p : (const void*)c->a_dinv.p;
         L.b = nullptr;
         L.r0 = c->r0.p;
         L.x = c->That.p;
-        L.r = c->wr.p;
-        L.z = c->wz.p;
-        L.p0 = c->wp0.p;
-        L.p1 = c->wp1.p;
-        L.q = c->wq.p;
-        L.zl = c->wzl.p;
-        L.pl0 = c->wpl0.p;
-        L.pl1 = c->wpl1.p;
+        L.w64 = c->work64.p;
+        L.w32 = c->work32.p;
+        L.stride = c->nwork;
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.which = 0;
@@ -1027,6 +1022,18 @@ sa_status init_state_if_needed(sa_ctx* c) {
 }
 
 }  // namespace
+
+// Sources, initial state and operator of (theta, dt), as the first sa_step
+// would prepare them (used by sa_batch).
+sa_status sa_prepare(sa_ctx* c, double theta, double dt) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!c->has_patch || !c->has_material || !c->has_scan)
+        return sa_fail(c, SA_ERR_STATE, "instance needs patch, material and scan");
+    if ((st = ensure_sources(c, dt))) return st;
+    if ((st = init_state_if_needed(c))) return st;
+    return ensure_operator(c, theta, dt);
+}
 
 extern "C" {
 

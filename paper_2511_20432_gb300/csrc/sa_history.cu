@@ -79,6 +79,56 @@ __global__ void k_prologue(PrologueArgs a) {
     }
 }
 
+// Batched prologue: every source of every instance; all instances share the
+// step index n (lockstep), dt and the material; E, r and s_img enter through
+// the per-instance coefE = s_img E / (rho c_p) and r2_8a = r^2 / (8 alpha).
+struct PrologueBatchArgs {
+    const DevStatus* st;
+    int n_src_total, n_inst;
+    const int* src_inst;
+    const int* src_off;
+    const int* n_src;
+    const double* coefE;
+    const double* r2_8a;
+    int* n_active;
+    const double2* pos;
+    double dt, alpha;
+    int precision;
+    double4* s64T;
+    double4* s64F;
+    float4* s32T;
+    float4* s32F;
+};
+
+__global__ void k_prologue_batch(PrologueBatchArgs a) {
+    const long long n1 = a.st->n + 1;
+    const double kPi = 3.141592653589793;
+    const double kLog2e = 1.4426950408889634;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < a.n_inst) a.n_active[g] = (int)(n1 < (long long)a.n_src[g] ? n1 : (long long)a.n_src[g]);
+    if (g >= a.n_src_total) return;
+    const int inst = a.src_inst[g];
+    const int l = g - a.src_off[inst];
+    const long long K = n1 < (long long)a.n_src[inst] ? n1 : (long long)a.n_src[inst];
+    if (l >= K) return;
+    const long long I = l + 1;
+    const double age = (double)(n1 - I) * a.dt + a.r2_8a[inst];
+    const double aI = 1.0 / (4.0 * a.alpha * age);
+    const double base = 4.0 * kPi * a.alpha * age;
+    const double cI = a.coefE[inst] / (base * sqrt(base));
+    const double gI = 2.0 * aI * cI;
+    const double2 p = a.pos[g];
+    if (a.precision != SA_MIXED) {
+        a.s64T[g] = make_double4(p.x, p.y, aI, cI);
+        a.s64F[g] = make_double4(p.x, p.y, aI, gI);
+    } else {
+        const float sx = (float)p.x, sy = (float)p.y;
+        const float na = (float)(-aI * kLog2e);
+        a.s32T[g] = make_float4(sx, sy, na, (float)log2(cI));
+        a.s32F[g] = make_float4(sx, sy, na, (float)log2(gI));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // history sum
 // ---------------------------------------------------------------------------
@@ -97,7 +147,37 @@ struct HistArgs {
     const double4* s64T;
     double* s_lat;
     double* tt_bot;
+    // batched mode (n_inst > 0): the points of instance i are
+    // [qlat_off[i], qlat_off[i+1]) / [qbot_off[i], qbot_off[i+1]) (multiples of
+    // 128, so a tile never straddles two instances); its sources start at
+    // src_off[i] and n_active[i] of them are in the sum
+    int n_inst;
+    const int* qlat_off;
+    const int* qbot_off;
+    const int* src_off;
+    const int* n_active;
 };
+
+// Instance of a tile (batched mode) and its active source count / offset.
+__device__ __forceinline__ void tile_sources(const HistArgs& a, bool flux, int q0, int& K,
+                                             int& off) {
+    if (a.n_inst == 0) {
+        K = a.st->n_active;
+        off = 0;
+        return;
+    }
+    const int* qo = flux ? a.qlat_off : a.qbot_off;
+    int lo = 0, hi = a.n_inst;   // qo[lo] <= q0 < qo[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (qo[mid] <= q0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    K = a.n_active[lo];
+    off = a.src_off[lo];
+}
 
 // Neumaier compensated addition of x into (s, c).
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
@@ -179,10 +259,11 @@ __device__ void tile_mixed(const HistArgs& a, int tile, double* red, Stage& sg) 
     int& abort_flag = sg.abort_flag;
     const int Q = FLUX ? a.q_lat : a.q_bot;
     const float* pts = FLUX ? a.lat32 : a.bot32;
-    const float4* src = FLUX ? a.s32F : a.s32T;
-    const int K = a.st->n_active;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q0 = tile * 32 * P;
+    int K, soff;
+    tile_sources(a, FLUX, q0, K, soff);
+    const float4* src = (FLUX ? a.s32F : a.s32T) + soff;
     float px[P], py[P], dz2[P], nzdz[P], nx[P], ny[P];
     float s[P], c[P];
 #pragma unroll
@@ -275,10 +356,11 @@ template <bool FLUX, int P, int NW>
 __device__ void tile_fp64(const HistArgs& a, int tile, double* red) {
     const int Q = FLUX ? a.q_lat : a.q_bot;
     const double* pts = FLUX ? a.lat64 : a.bot64;
-    const double4* src = FLUX ? a.s64F : a.s64T;
-    const int K = a.st->n_active;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q0 = tile * 32 * P;
+    int K, soff;
+    tile_sources(a, FLUX, q0, K, soff);
+    const double4* src = (FLUX ? a.s64F : a.s64T) + soff;
     double px[P], py[P], dz[P], nx[P], ny[P], nz[P], acc[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -409,6 +491,59 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
     a.s64T = s64T;
     a.s_lat = s_lat;
     a.tt_bot = tt_bot;
+    a.n_inst = 0;
+    a.qlat_off = a.qbot_off = a.src_off = a.n_active = nullptr;
+    if (warps == 4) {
+        if (P == 1) return launch_hist_t<1, 4>(precision, a, s);
+        if (P == 2) return launch_hist_t<2, 4>(precision, a, s);
+        return launch_hist_t<4, 4>(precision, a, s);
+    }
+    if (P == 1) return launch_hist_t<1, 8>(precision, a, s);
+    if (P == 2) return launch_hist_t<2, 8>(precision, a, s);
+    return launch_hist_t<4, 8>(precision, a, s);
+}
+
+cudaError_t launch_prologue_batch(const DevStatus* st, int n_src_total, int n_inst,
+                                  const int* src_inst, const int* src_off, const int* n_src,
+                                  const double* coefE, const double* r2_8a, int* n_active,
+                                  const double2* pos, double dt, double alpha, int precision,
+                                  double4* s64T, double4* s64F, float4* s32T, float4* s32F,
+                                  cudaStream_t s) {
+    PrologueBatchArgs a{st, n_src_total, n_inst, src_inst, src_off, n_src, coefE, r2_8a,
+                        n_active, pos, dt, alpha, precision, s64T, s64F, s32T, s32F};
+    const int n = n_src_total > n_inst ? n_src_total : n_inst;
+    k_prologue_batch<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_history_batch(int precision, int P, int warps, DevStatus* st, int q_lat,
+                                 int q_bot, const float* lat32, const float* bot32,
+                                 const double* lat64, const double* bot64, const float4* s32F,
+                                 const float4* s32T, const double4* s64F, const double4* s64T,
+                                 double* s_lat, double* tt_bot, int n_inst, const int* qlat_off,
+                                 const int* qbot_off, const int* src_off, const int* n_active,
+                                 cudaStream_t s) {
+    HistArgs a;
+    a.st = st;
+    a.q_lat = q_lat;
+    a.q_bot = q_bot;
+    a.b_lat = 0;
+    a.lat32 = lat32;
+    a.bot32 = bot32;
+    a.lat64 = lat64;
+    a.bot64 = bot64;
+    a.x_ref = a.y_ref = a.z_top = 0.0;   // batched points carry z - z_top in z (see sa_batch)
+    a.s32F = s32F;
+    a.s32T = s32T;
+    a.s64F = s64F;
+    a.s64T = s64T;
+    a.s_lat = s_lat;
+    a.tt_bot = tt_bot;
+    a.n_inst = n_inst;
+    a.qlat_off = qlat_off;
+    a.qbot_off = qbot_off;
+    a.src_off = src_off;
+    a.n_active = n_active;
     if (warps == 4) {
         if (P == 1) return launch_hist_t<1, 4>(precision, a, s);
         if (P == 2) return launch_hist_t<2, 4>(precision, a, s);

@@ -100,6 +100,14 @@ struct SellDev {
     DBuf<int> diag;           // n: storage index of the diagonal entry
 };
 
+// Host copy of a SELL pattern (built on the host, kept for batching).
+struct SellHost {
+    int n = 0, n_slices = 0;
+    std::vector<long long> sptr;
+    std::vector<int> col, src, diag;
+    std::vector<short> col16;   // column - row, filled when every offset fits
+};
+
 // What the kernels need of a SELL operator (no ownership).
 struct SellView {
     int n, n_slices;
@@ -124,18 +132,14 @@ struct PcgLaunch {
     const void* val;          // operator values in the path's precision
     const double* val_hi;     // FP64 values (initial residual when r0 == null)
     const double* dinv;
+    const void* dinvl;        // dinv in the path's precision (FP32 copy or = dinv)
     const double* b;
     const double* r0;         // given initial residual (x0 = x), or null
     double* x;
-    double* r;
-    double* z;
-    double* p0;
-    double* p1;
-    double* q;
-    void* zl;                 // FP32 copies (mixed path)
-    void* pl0;
-    void* pl1;
-    double* partials;
+    double* w64;              // 7 FP64 work vectors of length stride (p, r[2], w[2], s[2])
+    void* w32;                // 6 FP32 work vectors of length stride (mixed path)
+    size_t stride;
+    double* partials;         // 8 x grid
     DevStatus* st;
     int which;
     double tol;
@@ -245,8 +249,10 @@ struct sa_ctx {
     DBuf<double> F0, F1;      // internal order (n_dof)
     DBuf<double> gnew, bbot;  // n_dir
     DBuf<double> rhs, r0;     // n_free
-    DBuf<double> wr, wz, wp0, wp1, wq;   // PCG work, max(n_free, n_dir)
-    DBuf<float> wzl, wpl0, wpl1;         // FP32 copies (mixed path)
+    DBuf<double> work64;                 // PCG work: 7 x nwork (FP64)
+    DBuf<float> work32;                  // PCG work: 6 x nwork (FP32, mixed path)
+    DBuf<float> a_dinv32, mbot_dinv32;   // Jacobi inverse in FP32 (mixed path)
+    size_t nwork = 0;
     DBuf<double> dev64;                  // T^n - T_c (n_dof)
     DBuf<float> dev32;
     DBuf<double> partials;    // 4 * max grid
@@ -262,6 +268,10 @@ struct sa_ctx {
     DBuf<double4> evT, evF;         // FP64 source coefficients at the current step
     DBuf<double> eval_pts, eval_out;
 
+    // host copies of the patterns (for sa_batch)
+    SellHost a_h, r_h, mbot_h;
+    std::vector<int> wlat_rowdof_h, wlat_ptr_h, wlat_col_h, wbot_ptr_h, wbot_col_h;
+
     // stage timing (sa_options::stage_timing)
     cudaEvent_t ev[SA_N_STAGES + 1] = {};
     double stage_ms[SA_N_STAGES] = {};
@@ -272,6 +282,7 @@ struct sa_ctx {
 // helpers
 // ---------------------------------------------------------------------------
 sa_status sa_fail(sa_ctx* c, sa_status s, const char* fmt, ...);
+sa_status sa_prepare(sa_ctx* c, double theta, double dt);
 sa_status sa_cuda_fail(sa_ctx* c, cudaError_t e, const char* where);
 
 #define SA_CUDA(ctx, call)                                           \

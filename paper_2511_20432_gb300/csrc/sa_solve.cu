@@ -260,17 +260,17 @@ struct PcgArgs {
     Op<VT> A;
     const double* val_hi;  // FP64 values of A (mode 0 initial residual); may equal A.val
     const double* dinv;
-    const double* b;       // mode 0: right-hand side
+    const VT* dinvl;       // dinv in the operator precision
+    const double* b;       // mode 0: right-hand side (r0 = b - A x)
     const double* r0;      // mode 1: initial residual (x0 = x); b = r0 + A x for the norm
     double* x;
-    double* r;
-    double* z;
-    double* p0;
-    double* p1;
-    double* q;
-    VT* zl;                // low-precision copies (mixed path; unused in FP64)
-    VT* pl0;
-    VT* pl1;
+    double* p;
+    double* r[2];
+    double* w[2];
+    double* s[2];
+    VT* rl[2];             // operator-precision copies of r, w, s (gathered by the SpMV)
+    VT* wl[2];
+    VT* sl[2];
     double* part;
     DevStatus* st;
     int which;             // 0 main solve, 1 bottom projection
@@ -280,167 +280,198 @@ struct PcgArgs {
     VT* sq;                // shared scratch for the split partial sums (set in-kernel)
 };
 
-// Jacobi-preconditioned CG (Hestenes-Stiefel).  The update p = z + beta p
-// is fused into the next SpMV (p double buffered), so one iteration is two
-// phases with one reduction each:
-//   B: p' = z + beta p ; q = A p' ; (p', q)
-//   C: x += alpha p' ; r -= alpha q ; z = D^{-1} r ; (r, r), (r, z)
-// SpMV: SELL-32, one warp per slice (lane = row), slices strided over the
-// warps (gw, nw); vectors strided over the threads (tid, nth).
+// SpMV over the warp units of a phase: slice sl = u / KS, part h = u % KS of
+// its k-range; the KS warps of a slice sit in one block and their partial
+// sums are added in fixed order in shared memory.  f(j) gives the gathered
+// vector entry; own(i, acc) consumes the row result (h == 0 warp only).
+template <typename VT, class Gather, class Own>
+__device__ __forceinline__ void spmv_units(const PcgArgs<VT>& a, int gw, int nw, Gather f,
+                                           Own own) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int KS = a.ksplit;
+    const int units = a.A.n_slices * KS;
+    const int rounds = (units + nw - 1) / nw;
+    const int n = a.A.n;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int u = rd * nw + gw;
+        const int sl = u / KS, h = u % KS;
+        VT acc = 0;
+        if (sl < a.A.n_slices) {
+            const long long base = a.A.sptr[sl];
+            const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
+            const int chunk = (w + KS - 1) / KS;
+            const int k0 = h * chunk, k1 = min(w, k0 + chunk);
+            const int ir = min(sl * 32 + lane, n - 1);
+#pragma unroll 8
+            for (int k = k0; k < k1; ++k) {
+                const long long e = base + 32ll * k + lane;
+                acc = fma(__ldg(a.A.val + e), f(a.A.col(e, ir)), acc);
+            }
+        }
+        if (KS > 1) {
+            a.sq[wib * 32 + lane] = acc;
+            __syncthreads();
+        }
+        if (h == 0 && sl < a.A.n_slices) {
+            VT tot = acc;
+            for (int hh = 1; hh < KS; ++hh) tot += a.sq[(wib + hh) * 32 + lane];
+            const int i = sl * 32 + lane;
+            if (i < n) own(i, tot);
+        }
+        if (KS > 1) __syncthreads();
+    }
+}
+
+// Jacobi-preconditioned CG in the Chronopoulos-Gear form: one global
+// reduction per iteration.  With u = D^{-1} r and w = A u:
+//   p = u + beta p ; s = w + beta s ; x += alpha p ; r -= alpha s ;
+//   u = D^{-1} r ; w = A u ; gamma = (r, u), delta = (w, u), (r, r) ;
+//   beta' = gamma'/gamma ; alpha' = gamma' / (delta' - beta' gamma'/alpha).
+// The SpMV of w needs u of the neighbouring rows after their update; each
+// lane recomputes it from the neighbours' previous r, w, s (double-buffered),
+// so one iteration is a single grid phase followed by one reduction.
 template <typename VT, class Sync>
 __device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw, int tid,
                          int nth) {
     constexpr bool LO = std::is_same<VT, float>::value;
     const int n = a.A.n;
-    const int lane = threadIdx.x & 31;
-    double red[3];
-    // ---- phase A
-    {
-        double v[3] = {0.0, 0.0, 0.0};
+    double bb;
+    // ---- mode 0: r0 = b - A x (FP64 values), then a grid sync
+    if (a.r0 == nullptr) {
+        double v[1] = {0.0};
+        // the FP64 residual: a plain FP64 pass over the rows (one warp per slice)
+        const int lane = threadIdx.x & 31;
         for (int sl = gw; sl < a.A.n_slices; sl += nw) {
             const long long base = a.A.sptr[sl];
             const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
             const int i = sl * 32 + lane;
             const int ir = min(i, n - 1);
             double acc = 0.0;
-            if (a.r0 == nullptr) {   // r = b - A x with the FP64 values
 #pragma unroll 4
-                for (int k = 0; k < w; ++k) {
-                    const long long e = base + 32ll * k + lane;
-                    acc = fma(__ldg(a.val_hi + e), a.x[a.A.col(e, ir)], acc);
-                }
-            } else {                 // A x for the norm of b only
-                VT s = 0;
-#pragma unroll 8
-                for (int k = 0; k < w; ++k) {
-                    const long long e = base + 32ll * k + lane;
-                    s = fma(__ldg(a.A.val + e), (VT)a.x[a.A.col(e, ir)], s);
-                }
-                acc = (double)s;
+            for (int k = 0; k < w; ++k) {
+                const long long e = base + 32ll * k + lane;
+                acc = fma(__ldg(a.val_hi + e), a.x[a.A.col(e, ir)], acc);
             }
             if (i < n) {
-                double ri, bi;
-                if (a.r0 == nullptr) {
-                    bi = a.b[i];
-                    ri = bi - acc;
-                } else {
-                    ri = a.r0[i];
-                    bi = ri + acc;
-                }
-                const double zi = a.dinv[i] * ri;
-                a.r[i] = ri;
-                a.z[i] = zi;
-                if (LO) a.zl[i] = (VT)zi;
-                v[0] += ri * zi;
-                v[1] += ri * ri;
-                v[2] += bi * bi;
+                const double ri = a.b[i] - acc;
+                a.r[0][i] = ri;
+                if (LO) a.rl[0][i] = (VT)ri;
+                v[0] += a.b[i] * a.b[i];
             }
         }
-        if (!sync.template reduce<3>(v, 0, red)) return;
+        double o[1];
+        if (!sync.template reduce<1>(v, 0, o)) return;
+        bb = o[0];
     }
-    double rz = red[0], rr = red[1];
-    const double bb = red[2];
+    // ---- w0 = A D^{-1} r0 ; gamma, delta, (r, r) [and (b, b) in mode 1]
+    double gamma, delta, rr;
+    {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        const bool m1 = a.r0 != nullptr;
+        const double* rsrc = m1 ? a.r0 : a.r[0];
+        if (m1) {
+            // A x for the norm of b = r0 + A x
+            spmv_units(
+                a, gw, nw, [&](int j) { return (VT)a.x[j]; },
+                [&](int i, VT ax) {
+                    const double bi = a.r0[i] + (double)ax;
+                    v[3] += bi * bi;
+                });
+        }
+        spmv_units(
+            a, gw, nw,
+            [&](int j) {
+                return LO ? a.dinvl[j] * (VT)rsrc[j] : (VT)(a.dinv[j] * rsrc[j]);
+            },
+            [&](int i, VT wacc) {
+                const double ri = rsrc[i];
+                const double ui = a.dinv[i] * ri;
+                const double wi = (double)wacc;
+                if (m1) {
+                    a.r[0][i] = ri;
+                    if (LO) a.rl[0][i] = (VT)ri;
+                }
+                a.w[0][i] = wi;
+                if (LO) a.wl[0][i] = (VT)wi;
+                v[0] += ri * ui;
+                v[1] += wi * ui;
+                v[2] += ri * ri;
+            });
+        double o[4];
+        if (!sync.template reduce<4>(v, 1, o)) return;
+        gamma = o[0];
+        delta = o[1];
+        rr = o[2];
+        if (m1) bb = o[3];
+    }
     const double stop2 = a.tol * a.tol * bb;
     int it = 0;
-    double beta = 0.0;
     bool conv = rr <= stop2;
-    bool nan = !(rr == rr);
-    double* pc = a.p0;
-    double* pn = a.p1;
-    VT* plc = LO ? a.pl0 : (VT*)a.p0;
-    VT* pln = LO ? a.pl1 : (VT*)a.p1;
-    const VT* zl = LO ? a.zl : (const VT*)a.z;
+    bool nan = !(rr == rr) || !(delta == delta);
+    double alpha = gamma / delta, beta = 0.0;
     while (!conv && !nan && it < a.max_iter) {
-        // ---- phase B (each slice split over KS consecutive warps of a block)
-        double pq;
-        {
-            double v[1] = {0.0};
-            const bool first = (it == 0);
-            const VT bl = (VT)beta;
-            const int nwb = blockDim.x >> 5;
-            const int wib = threadIdx.x >> 5;
-            const int KS = a.ksplit;
-            const int units = a.A.n_slices * KS;
-            const int rounds = (units + nw - 1) / nw;
-            for (int rd = 0; rd < rounds; ++rd) {
-                const int u = rd * nw + gw;
-                const int sl = u / KS, h = u % KS;
-                VT acc = 0;
-                if (sl < a.A.n_slices) {
-                    const long long base = a.A.sptr[sl];
-                    const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
-                    const int chunk = (w + KS - 1) / KS;
-                    const int k0 = h * chunk, k1 = min(w, k0 + chunk);
-                    const int ir = min(sl * 32 + lane, n - 1);
-                    if (first) {
-#pragma unroll 8
-                        for (int k = k0; k < k1; ++k) {
-                            const long long e = base + 32ll * k + lane;
-                            acc = fma(__ldg(a.A.val + e), zl[a.A.col(e, ir)], acc);
-                        }
-                    } else {
-#pragma unroll 8
-                        for (int k = k0; k < k1; ++k) {
-                            const long long e = base + 32ll * k + lane;
-                            const int j = a.A.col(e, ir);
-                            acc = fma(__ldg(a.A.val + e), fma(bl, plc[j], zl[j]), acc);
-                        }
-                    }
+        const int c = it & 1;
+        const bool first = (it == 0);
+        const VT al = (VT)alpha, bl = (VT)beta;
+        // buffer selection by value (no dynamic indexing of the argument arrays)
+        const double* rc = c ? a.r[1] : a.r[0];
+        const double* wc = c ? a.w[1] : a.w[0];
+        const double* sc = c ? a.s[1] : a.s[0];
+        double* rn = c ? a.r[0] : a.r[1];
+        double* wn = c ? a.w[0] : a.w[1];
+        double* sn = c ? a.s[0] : a.s[1];
+        VT* rln = c ? a.rl[0] : a.rl[1];
+        VT* wln = c ? a.wl[0] : a.wl[1];
+        VT* sln = c ? a.sl[0] : a.sl[1];
+        const VT* rlc = LO ? (c ? a.rl[1] : a.rl[0]) : (const VT*)rc;
+        const VT* wlc = LO ? (c ? a.wl[1] : a.wl[0]) : (const VT*)wc;
+        const VT* slc = LO ? (c ? a.sl[1] : a.sl[0]) : (const VT*)sc;
+        const VT* dl = LO ? a.dinvl : (const VT*)a.dinv;
+        double v[3] = {0.0, 0.0, 0.0};
+        spmv_units(
+            a, gw, nw,
+            [&](int j) {
+                const VT sj = first ? wlc[j] : fma(bl, slc[j], wlc[j]);
+                return dl[j] * fma(-al, sj, rlc[j]);
+            },
+            [&](int i, VT wacc) {
+                const double ui_old = a.dinv[i] * rc[i];
+                const double pi = first ? ui_old : fma(beta, a.p[i], ui_old);
+                const double si = first ? wc[i] : fma(beta, sc[i], wc[i]);
+                a.p[i] = pi;
+                a.x[i] = fma(alpha, pi, a.x[i]);
+                const double ri = fma(-alpha, si, rc[i]);
+                const double ui = a.dinv[i] * ri;
+                const double wi = (double)wacc;
+                rn[i] = ri;
+                sn[i] = si;
+                wn[i] = wi;
+                if (LO) {
+                    rln[i] = (VT)ri;
+                    sln[i] = (VT)si;
+                    wln[i] = (VT)wi;
                 }
-                if (KS > 1) {
-                    a.sq[wib * 32 + lane] = acc;
-                    __syncthreads();
-                }
-                if (h == 0 && sl < a.A.n_slices) {
-                    VT tot = acc;
-                    for (int hh = 1; hh < KS; ++hh) tot += a.sq[(wib + hh) * 32 + lane];
-                    const int i = sl * 32 + lane;
-                    if (i < n) {
-                        const double pi = first ? a.z[i] : fma(beta, pc[i], a.z[i]);
-                        pn[i] = pi;
-                        if (LO) pln[i] = (VT)pi;
-                        a.q[i] = (double)tot;
-                        v[0] += pi * (double)tot;
-                    }
-                }
-                if (KS > 1) __syncthreads();
-                (void)nwb;
-            }
-            double o[1];
-            if (!sync.template reduce<1>(v, 3, o)) return;
-            pq = o[0];
-        }
-        const double alpha = rz / pq;
-        // ---- phase C
-        {
-            double v[2] = {0.0, 0.0};
-            for (int i = tid; i < n; i += nth) {
-                a.x[i] = fma(alpha, pn[i], a.x[i]);
-                const double ri = fma(-alpha, a.q[i], a.r[i]);
-                const double zi = a.dinv[i] * ri;
-                a.r[i] = ri;
-                a.z[i] = zi;
-                if (LO) a.zl[i] = (VT)zi;
-                v[0] += ri * ri;
-                v[1] += ri * zi;
-            }
-            double o[2];
-            if (!sync.template reduce<2>(v, 4, o)) return;
-            rr = o[0];
-            const double rzn = o[1];
-            ++it;
-            nan = !(rr == rr) || !(pq == pq);
-            conv = rr <= stop2;
-            beta = rzn / rz;
-            rz = rzn;
-        }
-        double* t = pc;
-        pc = pn;
-        pn = t;
-        VT* tl = plc;
-        plc = pln;
-        pln = tl;
+                v[0] += ri * ui;
+                v[1] += wi * ui;
+                v[2] += ri * ri;
+            });
+        double o[3];
+        // partial rows alternate between two slot sets: a block may write the
+        // next iteration's partials while a slower one still reads these
+        if (!sync.template reduce<3>(v, 5 + 3 * c, o)) return;
+        const double gnew = o[0];
+        delta = o[1];
+        rr = o[2];
+        ++it;
+        beta = gnew / gamma;
+        alpha = gnew / (delta - beta * gnew / alpha);
+        gamma = gnew;
+        nan = !(rr == rr) || !(alpha == alpha);
+        conv = rr <= stop2;
     }
+    (void)tid;
+    (void)nth;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         int* err = &a.st->err;
@@ -508,17 +539,19 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     a.A = make_op<VT>(L.op, L.val);
     a.val_hi = L.val_hi;
     a.dinv = L.dinv;
+    a.dinvl = (const VT*)L.dinvl;
     a.b = L.b;
     a.r0 = L.r0;
     a.x = L.x;
-    a.r = L.r;
-    a.z = L.z;
-    a.p0 = L.p0;
-    a.p1 = L.p1;
-    a.q = L.q;
-    a.zl = (VT*)L.zl;
-    a.pl0 = (VT*)L.pl0;
-    a.pl1 = (VT*)L.pl1;
+    a.p = L.w64;
+    for (int k = 0; k < 2; ++k) {
+        a.r[k] = L.w64 + (size_t)(1 + k) * L.stride;
+        a.w[k] = L.w64 + (size_t)(3 + k) * L.stride;
+        a.s[k] = L.w64 + (size_t)(5 + k) * L.stride;
+        a.rl[k] = (VT*)L.w32 + (size_t)(0 + k) * L.stride;
+        a.wl[k] = (VT*)L.w32 + (size_t)(2 + k) * L.stride;
+        a.sl[k] = (VT*)L.w32 + (size_t)(4 + k) * L.stride;
+    }
     a.part = L.partials;
     a.st = L.st;
     a.which = L.which;
