@@ -2,6 +2,7 @@
 // patterns, Dirichlet elimination order, scan discretisation) and the
 // per-step launch sequence.  See include/sa.h for the contract of each call.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -801,6 +802,10 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         int ks = 1;
         while (ks < 8 && c->a_s.n_slices * ks * 2 <= warps) ks *= 2;
         c->pcg_ksplit = ks;
+        if (const char* e = getenv("SA_PCG_KSPLIT")) {   // tuning override (1, 2, 4, 8)
+            const int v = atoi(e);
+            if (v == 1 || v == 2 || v == 4 || v == 8) c->pcg_ksplit = v;
+        }
         SA_ALLOC(c, c->partials, (size_t)11 * c->pcg_grid);
     }
     SA_CUDA(c, cudaStreamSynchronize(s));

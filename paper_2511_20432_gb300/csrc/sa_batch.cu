@@ -320,12 +320,21 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
                 const int i = sl * 32 + lane;
                 const int ir = min(i, a.n - 1);
                 VT acc = 0;
-#pragma unroll 8
-                for (int k = 0; k < w; ++k) {
-                    const long long e = base + 32ll * k + lane;
-                    const int j = bcol(a, e, ir);
-                    const VT pj = first ? zl[j] : fma(bl, plc[j], zl[j]);
-                    acc = fma(__ldg(a.val + e), pj, acc);
+                constexpr int B = std::is_same<VT, float>::value ? 8 : 4;
+                for (int k = 0; k < w; k += B) {
+                    int jj[B];
+                    VT vv[B], gg[B];
+#pragma unroll
+                    for (int u = 0; u < B; ++u) {
+                        const bool ok = k + u < w;
+                        const long long e = base + 32ll * (ok ? k + u : 0) + lane;
+                        jj[u] = ok ? bcol(a, e, ir) : ir;
+                        vv[u] = ok ? __ldg(a.val + e) : (VT)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < B; ++u) gg[u] = first ? zl[jj[u]] : fma(bl, plc[jj[u]], zl[jj[u]]);
+#pragma unroll
+                    for (int u = 0; u < B; ++u) acc = fma(vv[u], gg[u], acc);
                 }
                 if (i < a.n) {
                     const double pi = first ? a.z[i] : fma(beta, pc[i], a.z[i]);

@@ -127,16 +127,28 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
     VT acc = 0;
     double accd = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < w; ++k) {
-        const long long e = base + 32ll * k + lane;
-        const int j = a.K.col(e, ir);
-        const VT kv = __ldg(a.K.val + e);
-        acc = fma(kv, a.dev[j], acc);
-        if (j >= a.n_free) {   // Dirichlet column: - A_ij (g^{n+1}_j - g^n_j)
-            const double Aij =
-                (double)__ldg(a.Mval + e) * a.inv_dt_rhocp + a.theta * a.k * (double)kv;
-            accd += Aij * (a.gnew[j - a.n_free] - a.That[j]);
+    for (int k = 0; k < w; k += 8) {
+        int jj[8];
+        VT kv[8], dv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool ok = k + u < w;
+            const long long e = base + 32ll * (ok ? k + u : 0) + lane;
+            jj[u] = ok ? a.K.col(e, ir) : ir;
+            kv[u] = ok ? __ldg(a.K.val + e) : (VT)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) dv[u] = a.dev[jj[u]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            acc = fma(kv[u], dv[u], acc);
+            const int j = jj[u];
+            if (k + u < w && j >= a.n_free) {   // Dirichlet column: - A_ij (g^{n+1}_j - g^n_j)
+                const long long e = base + 32ll * (k + u) + lane;
+                const double Aij = (double)__ldg(a.Mval + e) * a.inv_dt_rhocp +
+                                   a.theta * a.k * (double)kv[u];
+                accd += Aij * (a.gnew[j - a.n_free] - a.That[j]);
+            }
         }
     }
     if (i < a.n_free)
@@ -303,10 +315,26 @@ __device__ __forceinline__ void spmv_units(const PcgArgs<VT>& a, int gw, int nw,
             const int chunk = (w + KS - 1) / KS;
             const int k0 = h * chunk, k1 = min(w, k0 + chunk);
             const int ir = min(sl * 32 + lane, n - 1);
-#pragma unroll 8
-            for (int k = k0; k < k1; ++k) {
-                const long long e = base + 32ll * k + lane;
-                acc = fma(__ldg(a.A.val + e), f(a.A.col(e, ir)), acc);
+            // explicit batches of 8: all column/value loads, then all
+            // gathers, then the FMAs, so each lane keeps many independent
+            // memory requests in flight (a plain loop serialises on the
+            // column -> gather dependency of every entry)
+            constexpr int B = std::is_same<VT, float>::value ? 8 : 4;   // registers
+            for (int k = k0; k < k1; k += B) {
+                int jj[B];
+                VT vv[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const bool ok = k + u < k1;
+                    const long long e = base + 32ll * (ok ? k + u : k0) + lane;
+                    jj[u] = ok ? a.A.col(e, ir) : ir;
+                    vv[u] = ok ? __ldg(a.A.val + e) : (VT)0;
+                }
+                VT gg[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) gg[u] = f(jj[u]);
+#pragma unroll
+                for (int u = 0; u < B; ++u) acc = fma(vv[u], gg[u], acc);
             }
         }
         if (KS > 1) {
