@@ -156,6 +156,11 @@ void build_sell(int n, const std::vector<long long>& ptr, const std::vector<int>
         }
     }
     if (!fits) out.col16.clear();
+    out.dmin = out.dmax = 0;
+    for (short d : out.col16) {
+        out.dmin = std::min(out.dmin, (int)d);
+        out.dmax = std::max(out.dmax, (int)d);
+    }
 }
 
 template <class T>
@@ -171,6 +176,8 @@ cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
         (dev).n = (host).n;                       \
         (dev).n_slices = (host).n_slices;         \
         (dev).n_stored = (long long)(host).col.size(); \
+        (dev).dmin = (host).dmin;                 \
+        (dev).dmax = (host).dmax;                 \
         SA_UPLOAD(ctx, (dev).sptr, (host).sptr);  \
         if ((host).col16.empty())                 \
             SA_UPLOAD(ctx, (dev).col, (host).col);    \
@@ -769,12 +776,22 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_ALLOC(c, c->bbot, std::max(c->n_dir, 1));
     SA_ALLOC(c, c->rhs, nwork);
     SA_ALLOC(c, c->r0, nwork);
+    SA_ALLOC(c, c->bsq, nwork);
     c->nwork = nwork;
-    SA_ALLOC(c, c->work64, (size_t)7 * nwork);
+    SA_ALLOC(c, c->work64, (size_t)5 * nwork);
+    {
+        // halo of the padded SpMV vector: every column offset of A and M_bot
+        int halo = 0;
+        halo = std::max(halo, std::max(-c->a_s.dmin, c->a_s.dmax));
+        halo = std::max(halo, std::max(-c->mbot_s.dmin, c->mbot_s.dmax));
+        c->work_pad = (halo + 8 + 3) & ~3;
+        const size_t vt = c->opt.precision == SA_MIXED ? sizeof(float) : sizeof(double);
+        SA_ALLOC(c, c->workpad, (nwork + 2 * (size_t)c->work_pad) * vt);
+        SA_CUDA(c, cudaMemsetAsync(c->workpad.p, 0, (nwork + 2 * (size_t)c->work_pad) * vt, s));
+    }
     SA_ALLOC(c, c->dev64, ndof);
     SA_ALLOC(c, c->dev32, ndof);
     if (c->opt.precision == SA_MIXED) {
-        SA_ALLOC(c, c->work32, (size_t)6 * nwork);
         SA_ALLOC(c, c->a_dinv32, std::max(c->n_free, 1));
         SA_ALLOC(c, c->mbot_dinv32, std::max(c->n_dir, 1));
         if (c->n_dir > 0) {
@@ -788,7 +805,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_CUDA(c, cudaMemsetAsync(c->F1.p, 0, sizeof(double) * ndof, s));
     SA_CUDA(c, cudaMemsetAsync(c->s_lat.p, 0, sizeof(double) * std::max(c->q_lat, 1), s));
     SA_CUDA(c, cudaMemsetAsync(c->tt_bot.p, 0, sizeof(double) * std::max(c->q_bot, 1), s));
-    SA_CUDA(c, cudaMemsetAsync(c->work64.p, 0, sizeof(double) * 7 * nwork, s));
+    SA_CUDA(c, cudaMemsetAsync(c->work64.p, 0, sizeof(double) * 5 * nwork, s));
     // PCG launch shape: co-resident blocks (cooperative launch)
     {
         int occ = 0;
@@ -950,18 +967,20 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.dinvl = mixed ? (const void*)c->mbot_dinv32.p : (const void*)c->mbot_dinv.p;
         L.b = c->bbot.p;
         L.r0 = nullptr;
+        L.bsq = nullptr;
         L.x = c->gnew.p;
         L.w64 = c->work64.p;
-        L.w32 = c->work32.p;
+        L.vpad = c->workpad.p;
+        L.pad = c->work_pad;
         L.stride = c->nwork;
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
-        // small system: a few blocks (cheap barriers), slices split 4 ways
-        L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices * 4 + 31) / 32));
-        L.ksplit = 4;
+        // small system: a few blocks of ~8 slices (cheap barriers)
+        L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices + 7) / 8));
+        L.ksplit = 0;
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
@@ -970,7 +989,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                          mixed ? (const void*)c->r_K32.p : (const void*)c->r_K.p,
                          mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
                          mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
-                         c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->r0.p, s);
+                         c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
+                         c->r0.p, c->bsq.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     SA_MARK(SA_STAGE_PCG);
     {
@@ -982,9 +1002,11 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.dinvl = mixed ? (const void*)c->a_dinv32.p : (const void*)c->a_dinv.p;
         L.b = nullptr;
         L.r0 = c->r0.p;
+        L.bsq = c->bsq.p;
         L.x = c->That.p;
         L.w64 = c->work64.p;
-        L.w32 = c->work32.p;
+        L.vpad = c->workpad.p;
+        L.pad = c->work_pad;
         L.stride = c->nwork;
         L.partials = c->partials.p;
         L.st = c->st.p;
@@ -992,7 +1014,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
         L.grid = c->pcg_grid;
-        L.ksplit = c->pcg_ksplit;
+        L.ksplit = 0;
+        if (const char* ev = getenv("SA_PCG_KSPLIT")) L.ksplit = atoi(ev);
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
     }

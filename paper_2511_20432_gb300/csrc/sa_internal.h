@@ -98,6 +98,7 @@ struct SellDev {
     DBuf<short> col16;        // n_stored (column - row), when every offset fits
     DBuf<int> src;            // n_stored: slot in the source CSR, -1 for padding
     DBuf<int> diag;           // n: storage index of the diagonal entry
+    int dmin = 0, dmax = 0;
 };
 
 // Host copy of a SELL pattern (built on the host, kept for batching).
@@ -106,6 +107,7 @@ struct SellHost {
     std::vector<long long> sptr;
     std::vector<int> col, src, diag;
     std::vector<short> col16;   // column - row, filled when every offset fits
+    int dmin = 0, dmax = 0;     // extreme column - row offsets (when col16 is filled)
 };
 
 // What the kernels need of a SELL operator (no ownership).
@@ -114,6 +116,7 @@ struct SellView {
     const long long* sptr;
     const int* col32;         // null when col16 is used
     const short* col16;
+    int dmin, dmax;           // extreme column - row offsets (col16 only)
 };
 
 inline SellView sell_view(const SellDev& s) {
@@ -123,6 +126,8 @@ inline SellView sell_view(const SellDev& s) {
     v.sptr = s.sptr.p;
     v.col16 = s.col16.p;
     v.col32 = s.col16.p ? nullptr : s.col.p;
+    v.dmin = s.dmin;
+    v.dmax = s.dmax;
     return v;
 }
 
@@ -135,9 +140,12 @@ struct PcgLaunch {
     const void* dinvl;        // dinv in the path's precision (FP32 copy or = dinv)
     const double* b;
     const double* r0;         // given initial residual (x0 = x), or null
+    const double* bsq;        // with r0: b_i^2 per row (norm of the right-hand side)
     double* x;
-    double* w64;              // 7 FP64 work vectors of length stride (p, r[2], w[2], s[2])
-    void* w32;                // 6 FP32 work vectors of length stride (mixed path)
+    double* w64;              // FP64 work vectors of length stride: p, r, w, s, u
+    void* vpad;               // 2 padded vectors (u, x) in the path's precision:
+                              // [pad | stride | pad] each, pad = halo entries
+    int pad;
     size_t stride;
     double* partials;         // 8 x grid
     DevStatus* st;
@@ -248,9 +256,10 @@ struct sa_ctx {
     DBuf<double> That;        // internal order (n_dof)
     DBuf<double> F0, F1;      // internal order (n_dof)
     DBuf<double> gnew, bbot;  // n_dir
-    DBuf<double> rhs, r0;     // n_free
-    DBuf<double> work64;                 // PCG work: 7 x nwork (FP64)
-    DBuf<float> work32;                  // PCG work: 6 x nwork (FP32, mixed path)
+    DBuf<double> rhs, r0, bsq;   // n_free
+    DBuf<double> work64;                 // PCG work: 5 x nwork (FP64)
+    DBuf<unsigned char> workpad;         // PCG padded vectors (2 x (nwork + 2 pad) x VT)
+    int work_pad = 0;
     DBuf<float> a_dinv32, mbot_dinv32;   // Jacobi inverse in FP32 (mixed path)
     size_t nwork = 0;
     DBuf<double> dev64;                  // T^n - T_c (n_dof)
@@ -358,8 +367,8 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
 cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
-                             double inv_dt_rhocp, double k, double theta, double* r0,
-                             cudaStream_t s);
+                             double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
+                             double* bsq, cudaStream_t s);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
                             const double* F1, double* F0, DevStatus* st, cudaStream_t s);

@@ -112,10 +112,14 @@ struct RhsArgs {
     const double* F0;
     const double* F1;
     int n_free;
-    double inv_dt_rhocp, k, theta;
+    double inv_dt_rhocp, k, theta, Tc;
     double* r0;
+    double* bsq;           // b_i^2, for the norm of the right-hand side
 };
 
+// Also forms b itself (only its squares are kept, for the PCG stopping test):
+//   b = (rho c_p/dt) M T^n - (1-theta) k K T^n + theta F^{n+1} + (1-theta) F^n
+//       - A_fd g^{n+1},   with M T^n = T_c (M 1) + M (T^n - T_c).
 template <typename VT>
 __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -125,34 +129,32 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     const int ir = min(i, a.n_free - 1);
     const long long base = a.K.sptr[sl];
     const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
-    VT acc = 0;
-    double accd = 0.0;
-    for (int k = 0; k < w; k += 8) {
-        int jj[8];
-        VT kv[8], dv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const bool ok = k + u < w;
-            const long long e = base + 32ll * (ok ? k + u : 0) + lane;
-            jj[u] = ok ? a.K.col(e, ir) : ir;
-            kv[u] = ok ? __ldg(a.K.val + e) : (VT)0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) dv[u] = a.dev[jj[u]];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            acc = fma(kv[u], dv[u], acc);
-            const int j = jj[u];
-            if (k + u < w && j >= a.n_free) {   // Dirichlet column: - A_ij (g^{n+1}_j - g^n_j)
-                const long long e = base + 32ll * (k + u) + lane;
-                const double Aij = (double)__ldg(a.Mval + e) * a.inv_dt_rhocp +
-                                   a.theta * a.k * (double)kv[u];
-                accd += Aij * (a.gnew[j - a.n_free] - a.That[j]);
-            }
+    VT acck = 0, accm = 0, summ = 0;
+    double accd = 0.0, accg = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+        const long long e = base + 32ll * k + lane;
+        const int j = a.K.col(e, ir);
+        const VT kv = __ldg(a.K.val + e);
+        const VT mv = __ldg(a.Mval + e);
+        const VT dv = a.dev[j];
+        acck = fma(kv, dv, acck);
+        accm = fma(mv, dv, accm);
+        summ += mv;
+        if (j >= a.n_free) {   // Dirichlet column: A_ij (g^{n+1}_j - g^n_j) and A_ij g^{n+1}_j
+            const double Aij = (double)mv * a.inv_dt_rhocp + a.theta * a.k * (double)kv;
+            const double g1 = a.gnew[j - a.n_free];
+            accd += Aij * (g1 - a.That[j]);
+            accg += Aij * g1;
         }
     }
-    if (i < a.n_free)
-        a.r0[i] = a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i] - a.k * (double)acc - accd;
+    if (i < a.n_free) {
+        const double f = a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i];
+        a.r0[i] = f - a.k * (double)acck - accd;
+        const double b = a.inv_dt_rhocp * (a.Tc * (double)summ + (double)accm) -
+                         (1.0 - a.theta) * a.k * (double)acck + f - accg;
+        a.bsq[i] = b * b;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -239,9 +241,9 @@ struct GridSync {
         if (threadIdx.x < 32) {
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                const volatile double* pk = part + (slot + k) * G;
+                const double* pk = part + (slot + k) * G;
                 double t = 0.0;
-                for (int i = threadIdx.x; i < G; i += 32) t += pk[i];
+                for (int i = threadIdx.x; i < G; i += 32) t += __ldcg(pk + i);   // L2, not L1
                 t = warp_sum(t);
                 if (threadIdx.x == 0) res[k] = t;
             }
@@ -254,96 +256,95 @@ struct GridSync {
     }
 };
 
-// One block: __syncthreads only.
-struct BlockSync {
-    template <int NV>
-    __device__ bool reduce(double (&v)[NV], int, double (&out)[NV]) const {
-        __shared__ double res[NV];
-        block_reduce<NV>(v, res);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = res[k];
-        __syncthreads();
-        return true;
-    }
-};
+constexpr int kPcgBlock = 1024;
 
 template <typename VT>
 struct PcgArgs {
     Op<VT> A;
-    const double* val_hi;  // FP64 values of A (mode 0 initial residual); may equal A.val
+    int dmin, dmax;        // column - row offsets (window mode)
+    bool window;           // gathers from a shared-memory window of u
+    int wcap;              // window capacity (entries) per block
+    const double* val_hi;  // FP64 values of A (mode 0 initial residual)
     const double* dinv;
-    const VT* dinvl;       // dinv in the operator precision
     const double* b;       // mode 0: right-hand side (r0 = b - A x)
-    const double* r0;      // mode 1: initial residual (x0 = x); b = r0 + A x for the norm
+    const double* r0;      // mode 1: initial residual (x0 = x)
+    const double* bsq;     // mode 1: b_i^2 per row (for the norm of b)
     double* x;
     double* p;
-    double* r[2];
-    double* w[2];
-    double* s[2];
-    VT* rl[2];             // operator-precision copies of r, w, s (gathered by the SpMV)
-    VT* wl[2];
-    VT* sl[2];
+    double* r;
+    double* w;
+    double* s;
+    double* u;
+    VT* ul;                // u in the operator precision, padded: ul[-pad .. n + pad)
     double* part;
     DevStatus* st;
     int which;             // 0 main solve, 1 bottom projection
     double tol;
     int max_iter;
-    int ksplit;            // warps per slice in the SpMV (divides the warps of a block)
-    VT* sq;                // shared scratch for the split partial sums (set in-kernel)
+    int ksplit;            // warps per slice (divides the 32 warps of a block)
 };
 
-// SpMV over the warp units of a phase: slice sl = u / KS, part h = u % KS of
-// its k-range; the KS warps of a slice sit in one block and their partial
-// sums are added in fixed order in shared memory.  f(j) gives the gathered
-// vector entry; own(i, acc) consumes the row result (h == 0 warp only).
-template <typename VT, class Gather, class Own>
-__device__ __forceinline__ void spmv_units(const PcgArgs<VT>& a, int gw, int nw, Gather f,
-                                           Own own) {
+// Block b owns slices [s0, s1) (contiguous, balanced) and their rows.
+__device__ __forceinline__ void block_slices(int S, int& s0, int& s1) {
+    s0 = (int)(((long long)S * blockIdx.x) / gridDim.x);
+    s1 = (int)(((long long)S * (blockIdx.x + 1)) / gridDim.x);
+}
+
+// w = A u on the block's slices.  Window mode: the entries of u the block
+// can touch, ul[32 s0 + dmin .. 32 s1 + dmax), are first copied into shared
+// memory (coalesced L2 loads), so every gather is a shared-memory read.
+// Each slice is split over KS consecutive warps (partial sums combined in
+// fixed order).  own(i, w_i) runs once per row.
+template <typename VT, class Own>
+__device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int KS = a.ksplit;
-    const int units = a.A.n_slices * KS;
-    const int rounds = (units + nw - 1) / nw;
+    const int nwb = blockDim.x >> 5;
     const int n = a.A.n;
-    for (int rd = 0; rd < rounds; ++rd) {
-        const int u = rd * nw + gw;
-        const int sl = u / KS, h = u % KS;
+    int s0, s1;
+    block_slices(a.A.n_slices, s0, s1);
+    long long wlo = 0;
+    if (a.window) {
+        wlo = ((long long)32 * s0 + a.dmin) & ~3ll;               // aligned start
+        const long long whi = (long long)32 * s1 + a.dmax + 1;
+        const int len = (int)(whi - wlo);
+        for (int t = threadIdx.x; t < len; t += blockDim.x) win[t] = __ldcg(a.ul + wlo + t);
+        __syncthreads();
+    }
+    const int KS = a.ksplit;
+    const int units = (s1 - s0) * KS;
+    for (int base_u = 0; base_u < units; base_u += nwb) {
+        const int u = base_u + wib;
+        const int sl = s0 + u / KS, h = u % KS;
         VT acc = 0;
-        if (sl < a.A.n_slices) {
+        if (u < units) {
             const long long base = a.A.sptr[sl];
             const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
             const int chunk = (w + KS - 1) / KS;
             const int k0 = h * chunk, k1 = min(w, k0 + chunk);
             const int ir = min(sl * 32 + lane, n - 1);
-            // explicit batches of 8: all column/value loads, then all
-            // gathers, then the FMAs, so each lane keeps many independent
-            // memory requests in flight (a plain loop serialises on the
-            // column -> gather dependency of every entry)
-            constexpr int B = std::is_same<VT, float>::value ? 8 : 4;   // registers
-            for (int k = k0; k < k1; k += B) {
-                int jj[B];
-                VT vv[B];
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    const bool ok = k + u < k1;
-                    const long long e = base + 32ll * (ok ? k + u : k0) + lane;
-                    jj[u] = ok ? a.A.col(e, ir) : ir;
-                    vv[u] = ok ? __ldg(a.A.val + e) : (VT)0;
+            if (a.window) {
+                const VT* wv = win - wlo;
+#pragma unroll 8
+                for (int k = k0; k < k1; ++k) {
+                    const long long e = base + 32ll * k + lane;
+                    acc = fma(__ldg(a.A.val + e), wv[ir + (int)__ldg(a.A.col16 + e)], acc);
                 }
-                VT gg[B];
-#pragma unroll
-                for (int u = 0; u < B; ++u) gg[u] = f(jj[u]);
-#pragma unroll
-                for (int u = 0; u < B; ++u) acc = fma(vv[u], gg[u], acc);
+            } else {
+#pragma unroll 8
+                for (int k = k0; k < k1; ++k) {
+                    const long long e = base + 32ll * k + lane;
+                    acc = fma(__ldg(a.A.val + e), a.ul[a.A.col(e, ir)], acc);
+                }
             }
         }
         if (KS > 1) {
-            a.sq[wib * 32 + lane] = acc;
+            sq[wib * 32 + lane] = acc;
             __syncthreads();
         }
-        if (h == 0 && sl < a.A.n_slices) {
+        if (u < units && h == 0) {
             VT tot = acc;
-            for (int hh = 1; hh < KS; ++hh) tot += a.sq[(wib + hh) * 32 + lane];
+            for (int hh = 1; hh < KS; ++hh) tot += sq[(wib + hh) * 32 + lane];
             const int i = sl * 32 + lane;
             if (i < n) own(i, tot);
         }
@@ -351,87 +352,77 @@ __device__ __forceinline__ void spmv_units(const PcgArgs<VT>& a, int gw, int nw,
     }
 }
 
-// Jacobi-preconditioned CG in the Chronopoulos-Gear form: one global
-// reduction per iteration.  With u = D^{-1} r and w = A u:
-//   p = u + beta p ; s = w + beta s ; x += alpha p ; r -= alpha s ;
-//   u = D^{-1} r ; w = A u ; gamma = (r, u), delta = (w, u), (r, r) ;
-//   beta' = gamma'/gamma ; alpha' = gamma' / (delta' - beta' gamma'/alpha).
-// The SpMV of w needs u of the neighbouring rows after their update; each
-// lane recomputes it from the neighbours' previous r, w, s (double-buffered),
-// so one iteration is a single grid phase followed by one reduction.
-template <typename VT, class Sync>
-__device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw, int tid,
-                         int nth) {
-    constexpr bool LO = std::is_same<VT, float>::value;
+// Jacobi-preconditioned CG in the Chronopoulos-Gear form (u = D^{-1} r,
+// w = A u, s = A p):
+//   V: p = u + beta p ; s = w + beta s ; x += alpha p ; r -= alpha s ;
+//      u = D^{-1} r                                   (own rows; grid sync)
+//   S: w = A u ; gamma = (r, u), delta = (w, u), (r, r) (one reduction)
+//   beta' = gamma'/gamma ; alpha' = gamma' / (delta' - beta' gamma'/alpha)
+// Two grid syncs per iteration; the SpMV gathers only u, from shared memory.
+template <typename VT>
+__global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT* sq = (VT*)smem_raw;                 // 1024
+    VT* win = sq + 1024;                    // window
+    GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
     const int n = a.A.n;
+    int s0, s1;
+    block_slices(a.A.n_slices, s0, s1);
+    const int row0 = 32 * s0, row1 = min(32 * s1, n);
+    const int lane = threadIdx.x & 31;
+    // ---- initial residual, u0, the norm of b
     double bb;
-    // ---- mode 0: r0 = b - A x (FP64 values), then a grid sync
-    if (a.r0 == nullptr) {
+    {
         double v[1] = {0.0};
-        // the FP64 residual: a plain FP64 pass over the rows (one warp per slice)
-        const int lane = threadIdx.x & 31;
-        for (int sl = gw; sl < a.A.n_slices; sl += nw) {
-            const long long base = a.A.sptr[sl];
-            const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
-            const int i = sl * 32 + lane;
-            const int ir = min(i, n - 1);
-            double acc = 0.0;
+        if (a.r0 == nullptr) {   // mode 0: r = b - A x in FP64 (global gathers)
+            const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+            for (int sl = s0 + wib; sl < s1; sl += nwb) {
+                const long long base = a.A.sptr[sl];
+                const int w = (int)((a.A.sptr[sl + 1] - base) >> 5);
+                const int i = sl * 32 + lane;
+                const int ir = min(i, n - 1);
+                double acc = 0.0;
 #pragma unroll 4
-            for (int k = 0; k < w; ++k) {
-                const long long e = base + 32ll * k + lane;
-                acc = fma(__ldg(a.val_hi + e), a.x[a.A.col(e, ir)], acc);
+                for (int k = 0; k < w; ++k) {
+                    const long long e = base + 32ll * k + lane;
+                    acc = fma(__ldg(a.val_hi + e), a.x[a.A.col(e, ir)], acc);
+                }
+                if (i < n) {
+                    const double bi = a.b[i], ri = bi - acc, ui = a.dinv[i] * ri;
+                    a.r[i] = ri;
+                    a.u[i] = ui;
+                    a.ul[i] = (VT)ui;
+                    v[0] += bi * bi;
+                }
             }
-            if (i < n) {
-                const double ri = a.b[i] - acc;
-                a.r[0][i] = ri;
-                if (LO) a.rl[0][i] = (VT)ri;
-                v[0] += a.b[i] * a.b[i];
+        } else {                 // mode 1: r = r0 given
+            for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+                const double ri = a.r0[i], ui = a.dinv[i] * ri;
+                a.r[i] = ri;
+                a.u[i] = ui;
+                a.ul[i] = (VT)ui;
+                v[0] += a.bsq[i];
             }
         }
         double o[1];
         if (!sync.template reduce<1>(v, 0, o)) return;
         bb = o[0];
     }
-    // ---- w0 = A D^{-1} r0 ; gamma, delta, (r, r) [and (b, b) in mode 1]
     double gamma, delta, rr;
     {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        const bool m1 = a.r0 != nullptr;
-        const double* rsrc = m1 ? a.r0 : a.r[0];
-        if (m1) {
-            // A x for the norm of b = r0 + A x
-            spmv_units(
-                a, gw, nw, [&](int j) { return (VT)a.x[j]; },
-                [&](int i, VT ax) {
-                    const double bi = a.r0[i] + (double)ax;
-                    v[3] += bi * bi;
-                });
-        }
-        spmv_units(
-            a, gw, nw,
-            [&](int j) {
-                return LO ? a.dinvl[j] * (VT)rsrc[j] : (VT)(a.dinv[j] * rsrc[j]);
-            },
-            [&](int i, VT wacc) {
-                const double ri = rsrc[i];
-                const double ui = a.dinv[i] * ri;
-                const double wi = (double)wacc;
-                if (m1) {
-                    a.r[0][i] = ri;
-                    if (LO) a.rl[0][i] = (VT)ri;
-                }
-                a.w[0][i] = wi;
-                if (LO) a.wl[0][i] = (VT)wi;
-                v[0] += ri * ui;
-                v[1] += wi * ui;
-                v[2] += ri * ri;
-            });
-        double o[4];
-        if (!sync.template reduce<4>(v, 1, o)) return;
+        double v[3] = {0.0, 0.0, 0.0};
+        spmv_block(a, win, sq, [&](int i, VT wacc) {
+            const double wi = (double)wacc, ui = a.u[i], ri = a.r[i];
+            a.w[i] = wi;
+            v[0] += ri * ui;
+            v[1] += wi * ui;
+            v[2] += ri * ri;
+        });
+        double o[3];
+        if (!sync.template reduce<3>(v, 1, o)) return;
         gamma = o[0];
         delta = o[1];
         rr = o[2];
-        if (m1) bb = o[3];
     }
     const double stop2 = a.tol * a.tol * bb;
     int it = 0;
@@ -439,55 +430,35 @@ __device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw,
     bool nan = !(rr == rr) || !(delta == delta);
     double alpha = gamma / delta, beta = 0.0;
     while (!conv && !nan && it < a.max_iter) {
-        const int c = it & 1;
         const bool first = (it == 0);
-        const VT al = (VT)alpha, bl = (VT)beta;
-        // buffer selection by value (no dynamic indexing of the argument arrays)
-        const double* rc = c ? a.r[1] : a.r[0];
-        const double* wc = c ? a.w[1] : a.w[0];
-        const double* sc = c ? a.s[1] : a.s[0];
-        double* rn = c ? a.r[0] : a.r[1];
-        double* wn = c ? a.w[0] : a.w[1];
-        double* sn = c ? a.s[0] : a.s[1];
-        VT* rln = c ? a.rl[0] : a.rl[1];
-        VT* wln = c ? a.wl[0] : a.wl[1];
-        VT* sln = c ? a.sl[0] : a.sl[1];
-        const VT* rlc = LO ? (c ? a.rl[1] : a.rl[0]) : (const VT*)rc;
-        const VT* wlc = LO ? (c ? a.wl[1] : a.wl[0]) : (const VT*)wc;
-        const VT* slc = LO ? (c ? a.sl[1] : a.sl[0]) : (const VT*)sc;
-        const VT* dl = LO ? a.dinvl : (const VT*)a.dinv;
+        // ---- V (own rows)
+        for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+            const double ui = a.u[i], wi = a.w[i];
+            const double pi = first ? ui : fma(beta, a.p[i], ui);
+            const double si = first ? wi : fma(beta, a.s[i], wi);
+            a.p[i] = pi;
+            a.s[i] = si;
+            a.x[i] = fma(alpha, pi, a.x[i]);
+            const double ri = fma(-alpha, si, a.r[i]);
+            const double un = a.dinv[i] * ri;
+            a.r[i] = ri;
+            a.u[i] = un;
+            a.ul[i] = (VT)un;
+        }
+        if (!sync.barrier()) return;
+        // ---- S
         double v[3] = {0.0, 0.0, 0.0};
-        spmv_units(
-            a, gw, nw,
-            [&](int j) {
-                const VT sj = first ? wlc[j] : fma(bl, slc[j], wlc[j]);
-                return dl[j] * fma(-al, sj, rlc[j]);
-            },
-            [&](int i, VT wacc) {
-                const double ui_old = a.dinv[i] * rc[i];
-                const double pi = first ? ui_old : fma(beta, a.p[i], ui_old);
-                const double si = first ? wc[i] : fma(beta, sc[i], wc[i]);
-                a.p[i] = pi;
-                a.x[i] = fma(alpha, pi, a.x[i]);
-                const double ri = fma(-alpha, si, rc[i]);
-                const double ui = a.dinv[i] * ri;
-                const double wi = (double)wacc;
-                rn[i] = ri;
-                sn[i] = si;
-                wn[i] = wi;
-                if (LO) {
-                    rln[i] = (VT)ri;
-                    sln[i] = (VT)si;
-                    wln[i] = (VT)wi;
-                }
-                v[0] += ri * ui;
-                v[1] += wi * ui;
-                v[2] += ri * ri;
-            });
+        spmv_block(a, win, sq, [&](int i, VT wacc) {
+            const double wi = (double)wacc, ui = a.u[i], ri = a.r[i];
+            a.w[i] = wi;
+            v[0] += ri * ui;
+            v[1] += wi * ui;
+            v[2] += ri * ri;
+        });
         double o[3];
-        // partial rows alternate between two slot sets: a block may write the
-        // next iteration's partials while a slower one still reads these
-        if (!sync.template reduce<3>(v, 5 + 3 * c, o)) return;
+        // two slot sets: the next iteration's partials may be written while a
+        // slower block still reads these
+        if (!sync.template reduce<3>(v, 4 + 3 * (it & 1), o)) return;
         const double gnew = o[0];
         delta = o[1];
         rr = o[2];
@@ -498,8 +469,6 @@ __device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw,
         nan = !(rr == rr) || !(alpha == alpha);
         conv = rr <= stop2;
     }
-    (void)tid;
-    (void)nth;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         int* err = &a.st->err;
@@ -514,26 +483,6 @@ __device__ void pcg_body(const PcgArgs<VT>& a, const Sync& sync, int gw, int nw,
         }
         if (nan) atomicOr(err, SA_DEV_NAN);
     }
-}
-
-constexpr int kPcgBlock = 1024;
-
-template <typename VT>
-__global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_grid(PcgArgs<VT> a) {
-    __shared__ VT sq[kPcgBlock];
-    a.sq = sq;
-    GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
-    const int nwb = blockDim.x >> 5;
-    pcg_body<VT, GridSync>(a, sync, blockIdx.x * nwb + (threadIdx.x >> 5), gridDim.x * nwb,
-                           blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
-template <typename VT>
-__global__ void __launch_bounds__(kPcgBlock, 1) k_pcg_block(PcgArgs<VT> a) {
-    __shared__ VT sq[kPcgBlock];
-    a.sq = sq;
-    BlockSync sync;
-    pcg_body<VT, BlockSync>(a, sync, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x);
 }
 
 __global__ void k_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
@@ -565,45 +514,54 @@ template <typename VT>
 cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     PcgArgs<VT> a;
     a.A = make_op<VT>(L.op, L.val);
+    a.dmin = L.op.dmin;
+    a.dmax = L.op.dmax;
     a.val_hi = L.val_hi;
     a.dinv = L.dinv;
-    a.dinvl = (const VT*)L.dinvl;
     a.b = L.b;
     a.r0 = L.r0;
+    a.bsq = L.bsq;
     a.x = L.x;
     a.p = L.w64;
-    for (int k = 0; k < 2; ++k) {
-        a.r[k] = L.w64 + (size_t)(1 + k) * L.stride;
-        a.w[k] = L.w64 + (size_t)(3 + k) * L.stride;
-        a.s[k] = L.w64 + (size_t)(5 + k) * L.stride;
-        a.rl[k] = (VT*)L.w32 + (size_t)(0 + k) * L.stride;
-        a.wl[k] = (VT*)L.w32 + (size_t)(2 + k) * L.stride;
-        a.sl[k] = (VT*)L.w32 + (size_t)(4 + k) * L.stride;
-    }
+    a.r = L.w64 + L.stride;
+    a.w = L.w64 + 2 * L.stride;
+    a.s = L.w64 + 3 * L.stride;
+    a.u = L.w64 + 4 * L.stride;
+    a.ul = (VT*)L.vpad + L.pad;
     a.part = L.partials;
     a.st = L.st;
     a.which = L.which;
     a.tol = L.tol;
     a.max_iter = L.max_iter;
-    a.ksplit = L.ksplit > 0 ? L.ksplit : 1;
-    a.sq = nullptr;
-    if (L.grid <= 1) {
-        k_pcg_block<VT><<<1, kPcgBlock, 0, s>>>(a);
-        return cudaGetLastError();
-    }
-    cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
+    const int G = L.grid > 0 ? L.grid : 1;
+    // slices per block -> warps per slice so the 32 warps of a block are busy
+    const int spb = (L.op.n_slices + G - 1) / G;
+    int ks = 1;
+    while (ks < 8 && spb * ks * 2 <= 32) ks *= 2;
+    a.ksplit = L.ksplit > 0 ? L.ksplit : ks;
+    // window: 32 spb rows plus the halo, 4-entry alignment slack
+    const long long wl = 32ll * spb + (L.op.dmax - L.op.dmin) + 8;
+    const size_t smem_fixed = 1024 * sizeof(VT);
+    a.window = L.op.col16 != nullptr && L.pad >= -L.op.dmin + 4 && L.pad >= L.op.dmax + 4 &&
+               smem_fixed + wl * sizeof(VT) <= 200 * 1024;
+    a.wcap = a.window ? (int)wl : 0;
+    const size_t smem = smem_fixed + (size_t)a.wcap * sizeof(VT);
+    cudaError_t e = cudaFuncSetAttribute(k_pcg<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(L.grid);
+    cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(kPcgBlock);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pcg_grid<VT>, a);
+    return cudaLaunchKernelEx(&cfg, k_pcg<VT>, a);
 }
 
 }  // namespace
@@ -625,17 +583,17 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
 cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
-                             double inv_dt_rhocp, double k, double theta, double* r0,
-                             cudaStream_t s) {
+                             double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
+                             double* bsq, cudaStream_t s) {
     if (op.n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)(((long long)op.n_slices * 32 + 255) / 256);
     if (precision == SA_MIXED) {
         RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, That,
-                         gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, r0};
+                         gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
         k_theta_rhs<float><<<blocks, 256, 0, s>>>(a);
     } else {
         RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev,
-                          That, gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, r0};
+                          That, gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
         k_theta_rhs<double><<<blocks, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
@@ -643,7 +601,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
 
 int pcg_block_size() { return kPcgBlock; }
 const void* pcg_kernel_ptr(int precision) {
-    return precision == SA_MIXED ? (const void*)k_pcg_grid<float> : (const void*)k_pcg_grid<double>;
+    return precision == SA_MIXED ? (const void*)k_pcg<float> : (const void*)k_pcg<double>;
 }
 
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s) {

@@ -527,3 +527,28 @@ def test_R5_dirichlet_projection_reproduces_face_space_functions():
     # T~ chosen so that T_c - T~ = f on the bottom face
     g = m.dirichlet_g(wl.material.T_c - f(m.bot["x"]))
     np.testing.assert_allclose(g, f(ctrl[m.dir]), rtol=0, atol=1e-12)
+
+
+def test_mlp_oracle_gradients_by_finite_differences():
+    """The FP64 warm-start network reference: every analytic gradient entry
+    checked against central differences of the loss."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    sizes = [7, 5, 5, 5, 6]
+    params = [(rng.normal(0, 0.5, (o, i)), rng.normal(0, 0.1, o)) for i, o in zip(sizes[:-1], sizes[1:])]
+    X = rng.normal(size=(4, sizes[0]))
+    Y = rng.normal(size=(4, sizes[-1]))
+    loss, grads = mlp.loss_and_grads(params, X, Y)
+    h = 1e-6
+    for li, (W, b) in enumerate(params):
+        for arr, g in ((W, grads[li][0]), (b, grads[li][1])):
+            flat = arr.reshape(-1)
+            gf = g.reshape(-1)
+            for k in range(0, flat.size, max(1, flat.size // 7)):
+                old = flat[k]
+                flat[k] = old + h
+                lp, _ = mlp.loss_and_grads(params, X, Y)
+                flat[k] = old - h
+                lm, _ = mlp.loss_and_grads(params, X, Y)
+                flat[k] = old
+                assert abs((lp - lm) / (2 * h) - gf[k]) < 1e-7 * max(1.0, abs(gf[k]))
