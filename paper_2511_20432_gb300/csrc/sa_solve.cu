@@ -131,21 +131,31 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
     VT acck = 0, accm = 0, summ = 0;
     double accd = 0.0, accg = 0.0;
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-        const long long e = base + 32ll * k + lane;
-        const int j = a.K.col(e, ir);
-        const VT kv = __ldg(a.K.val + e);
-        const VT mv = __ldg(a.Mval + e);
-        const VT dv = a.dev[j];
-        acck = fma(kv, dv, acck);
-        accm = fma(mv, dv, accm);
-        summ += mv;
-        if (j >= a.n_free) {   // Dirichlet column: A_ij (g^{n+1}_j - g^n_j) and A_ij g^{n+1}_j
-            const double Aij = (double)mv * a.inv_dt_rhocp + a.theta * a.k * (double)kv;
-            const double g1 = a.gnew[j - a.n_free];
-            accd += Aij * (g1 - a.That[j]);
-            accg += Aij * g1;
+    for (int k = 0; k < w; k += 8) {
+        int jj[8];
+        VT kv[8], mv[8], dv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {     // independent loads first
+            const bool ok = k + u < w;
+            const long long e = base + 32ll * (ok ? k + u : 0) + lane;
+            jj[u] = ok ? a.K.col(e, ir) : ir;
+            kv[u] = ok ? __ldg(a.K.val + e) : (VT)0;
+            mv[u] = ok ? __ldg(a.Mval + e) : (VT)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) dv[u] = a.dev[jj[u]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            acck = fma(kv[u], dv[u], acck);
+            accm = fma(mv[u], dv[u], accm);
+            summ += mv[u];
+            const int j = jj[u];
+            if (j >= a.n_free) {   // Dirichlet column: A_ij (g^{n+1}_j - g^n_j) and A_ij g^{n+1}_j
+                const double Aij = (double)mv[u] * a.inv_dt_rhocp + a.theta * a.k * (double)kv[u];
+                const double g1 = a.gnew[j - a.n_free];
+                accd += Aij * (g1 - a.That[j]);
+                accg += Aij * g1;
+            }
         }
     }
     if (i < a.n_free) {
@@ -308,7 +318,20 @@ __device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
         wlo = ((long long)32 * s0 + a.dmin) & ~3ll;               // aligned start
         const long long whi = (long long)32 * s1 + a.dmax + 1;
         const int len = (int)(whi - wlo);
-        for (int t = threadIdx.x; t < len; t += blockDim.x) win[t] = __ldcg(a.ul + wlo + t);
+        // 8 independent loads in flight per thread, then the stores
+        for (int t0 = threadIdx.x; t0 < len; t0 += 8 * blockDim.x) {
+            VT tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + u * blockDim.x;
+                tmp[u] = t < len ? __ldcg(a.ul + wlo + t) : (VT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + u * blockDim.x;
+                if (t < len) win[t] = tmp[u];
+            }
+        }
         __syncthreads();
     }
     const int KS = a.ksplit;
@@ -325,10 +348,20 @@ __device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
             const int ir = min(sl * 32 + lane, n - 1);
             if (a.window) {
                 const VT* wv = win - wlo;
-#pragma unroll 8
-                for (int k = k0; k < k1; ++k) {
-                    const long long e = base + 32ll * k + lane;
-                    acc = fma(__ldg(a.A.val + e), wv[ir + (int)__ldg(a.A.col16 + e)], acc);
+                // batches of 16: every column/value load of the batch is in
+                // flight before the first (shared-memory) gather
+                for (int k = k0; k < k1; k += 16) {
+                    short dj[16];
+                    VT vv[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const bool ok = k + u < k1;
+                        const long long e = base + 32ll * (ok ? k + u : k0) + lane;
+                        dj[u] = ok ? __ldg(a.A.col16 + e) : (short)0;
+                        vv[u] = ok ? __ldg(a.A.val + e) : (VT)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) acc = fma(vv[u], wv[ir + (int)dj[u]], acc);
                 }
             } else {
 #pragma unroll 8
