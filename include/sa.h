@@ -139,6 +139,8 @@ typedef struct sa_step_stats {
     double rel_res_last;       /* ||r||/||b|| at exit of the last step's PCG       */
     int n_active_sources;      /* sources in the sum at the last step              */
     long long step_index;      /* n after the call                                 */
+    int ws_used_last;          /* 1: the last step's PCG started from the learned guess */
+    double ws_ratio_last;      /* |r0 - A dx| / |r0| of the last learned guess           */
 } sa_step_stats;
 
 /*
@@ -225,6 +227,40 @@ sa_status sa_get_matrix(sa_ctx* ctx, int which, long long* rowptr, int* colind, 
  * sources are recomputed from the scan.  Host buffers; synchronous. */
 sa_status sa_get_state(sa_ctx* ctx, long long* n, double* T_hat, double* F);
 sa_status sa_set_state(sa_ctx* ctx, long long n, const double* T_hat, const double* F);
+
+/*
+ * Learned warm start (the paper has no learned component: this only changes
+ * the initial guess of the free-block solve; PCG still converges to pcg_tol
+ * and keeps the cold start x0 = T^n whenever the proposal does not lower the
+ * residual).  A 4-layer perceptron of width H (BF16 weights, FP32
+ * accumulation, tensor-core GEMMs):
+ *   x -> silu(W1 x + b1) -> silu(W2 h + b2) -> silu(W3 h + b3) -> W4 h + b4
+ * Input: the initial residual r0 = b - A T^n of the free block at the rows
+ * in_idx, divided by |r0|_2; output: the increment of the free control
+ * variables divided by |r0|_2 (the solve is linear, so the scaling is exact).
+ */
+typedef struct sa_mlp sa_mlp;
+sa_status sa_mlp_create(int n_in, int hidden, int n_out, unsigned long long seed, sa_mlp** out);
+void sa_mlp_destroy(sa_mlp* m);
+long long sa_mlp_n_params(const sa_mlp* m);
+/* FP32 host arrays, per layer W_l (row-major, out x in) then b_l */
+sa_status sa_mlp_get_params(sa_mlp* m, float* host);
+sa_status sa_mlp_set_params(sa_mlp* m, const float* host);
+/* X: rows x n_in BF16 (device); Y: rows x n_out FP32 (device); synchronous */
+sa_status sa_mlp_forward(sa_mlp* m, const void* X, int rows, float* Y, void* stream);
+/* loss 1/(2 rows) sum |f(x) - y|^2 and its gradient (host FP32, parameter layout) */
+sa_status sa_mlp_gradients(sa_mlp* m, const void* X, const void* Y, int rows, float* grads,
+                           double* loss, void* stream);
+/* one Adam step (beta 0.9 / 0.999) on a minibatch; loss may be NULL (async) */
+sa_status sa_mlp_train_step(sa_mlp* m, const void* X, const void* Y, int rows, float lr,
+                            double* loss, void* stream);
+/* use net as the warm start of sa_step (NULL: cold start); n_out must be n_free */
+sa_status sa_set_warm_start(sa_ctx* ctx, sa_mlp* net, int n_in, const int* in_idx);
+/* training data: every following step writes row k of X (n_in BF16: r0[in_idx]/|r0|)
+ * and of Y (n_free BF16: increment/|r0|) into the caller's device buffers, up to
+ * capacity rows (graph replay is off while recording).  X = NULL stops. */
+sa_status sa_set_recorder(sa_ctx* ctx, void* X, void* Y, int capacity, int n_in, const int* in_idx);
+sa_status sa_get_recorded(sa_ctx* ctx, int* count);
 
 /* Stages of one step, in launch order. */
 enum { SA_STAGE_PROLOGUE = 0,  /* source coefficients of the step                       */

@@ -34,7 +34,8 @@ class sa_step_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int), ("pcg_iters_last", C.c_int),
                 ("pcg_iters_total", C.c_int), ("pcg_iters_max", C.c_int),
                 ("bot_iters_total", C.c_int), ("rel_res_last", C.c_double),
-                ("n_active_sources", C.c_int), ("step_index", C.c_longlong)]
+                ("n_active_sources", C.c_int), ("step_index", C.c_longlong),
+                ("ws_used_last", C.c_int), ("ws_ratio_last", C.c_double)]
 
 
 class sa_sizes(C.Structure):
@@ -73,6 +74,17 @@ def _load():
         "sa_get_state": (I, [P, C.POINTER(LL), P, P]),
         "sa_set_state": (I, [P, LL, P, P]),
         "sa_get_stage_times": (I, [P, P, C.POINTER(LL)]),
+        "sa_mlp_create": (I, [I, I, I, C.c_ulonglong, C.POINTER(P)]),
+        "sa_mlp_destroy": (V, [P]),
+        "sa_mlp_n_params": (LL, [P]),
+        "sa_mlp_get_params": (I, [P, P]),
+        "sa_mlp_set_params": (I, [P, P]),
+        "sa_mlp_forward": (I, [P, P, I, P, P]),
+        "sa_mlp_gradients": (I, [P, P, P, I, P, C.POINTER(D), P]),
+        "sa_mlp_train_step": (I, [P, P, P, I, C.c_float, C.POINTER(D), P]),
+        "sa_set_warm_start": (I, [P, P, I, P]),
+        "sa_set_recorder": (I, [P, P, P, I, I, P]),
+        "sa_get_recorded": (I, [P, C.POINTER(I)]),
         "sa_batch_create": (I, [P, I, C.POINTER(sa_options), C.POINTER(P)]),
         "sa_batch_step": (I, [P, D, D, I, C.POINTER(sa_step_stats)]),
         "sa_batch_get_field": (I, [P, I, I, P, LL]),
@@ -221,6 +233,26 @@ class Context:
         _check(self.ptr, lib.sa_get_stage_times(self.ptr, _ptr(ms), C.byref(k)))
         return dict(zip(STAGES, ms)), k.value
 
+    def set_warm_start(self, net, in_idx):
+        if net is None:
+            _check(self.ptr, lib.sa_set_warm_start(self.ptr, None, 0, None))
+            return
+        idx = np.ascontiguousarray(in_idx, dtype=np.int32)
+        _check(self.ptr, lib.sa_set_warm_start(self.ptr, net.ptr, int(idx.size), _ptr(idx)))
+
+    def set_recorder(self, X, Y, in_idx):
+        if X is None:
+            _check(self.ptr, lib.sa_set_recorder(self.ptr, None, None, 0, 0, None))
+            return
+        idx = np.ascontiguousarray(in_idx, dtype=np.int32)
+        _check(self.ptr, lib.sa_set_recorder(self.ptr, _ptr(X), _ptr(Y), int(X.shape[0]),
+                                             int(idx.size), _ptr(idx)))
+
+    def recorded(self):
+        k = C.c_int()
+        _check(self.ptr, lib.sa_get_recorded(self.ptr, C.byref(k)))
+        return k.value
+
     def get_state(self):
         n = self.sizes().n_dof
         T = np.empty(n)
@@ -233,6 +265,60 @@ class Context:
         T = np.ascontiguousarray(T, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.float64)
         _check(self.ptr, lib.sa_set_state(self.ptr, int(n), _ptr(T), _ptr(F)))
+
+
+class MLP:
+    """The warm-start network (sa_mlp): tensors are torch CUDA tensors."""
+
+    def __init__(self, n_in, hidden, n_out, seed=1):
+        self.ptr = C.c_void_p()
+        st = lib.sa_mlp_create(int(n_in), int(hidden), int(n_out), int(seed), C.byref(self.ptr))
+        if st != SA_OK:
+            raise SAError(st, "sa_mlp_create")
+        self.n_in, self.hidden, self.n_out = n_in, hidden, n_out
+
+    def close(self):
+        if self.ptr:
+            lib.sa_mlp_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_params(self):
+        return int(lib.sa_mlp_n_params(self.ptr))
+
+    def params(self):
+        out = np.empty(self.n_params(), dtype=np.float32)
+        _check(None, lib.sa_mlp_get_params(self.ptr, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(None, lib.sa_mlp_set_params(self.ptr, _ptr(p)))
+
+    def forward(self, X, out, stream=None):
+        s = None if stream is None else C.c_void_p(int(stream.cuda_stream))
+        _check(None, lib.sa_mlp_forward(self.ptr, _ptr(X), int(X.shape[0]), _ptr(out), s))
+        return out
+
+    def gradients(self, X, Y, stream=None):
+        g = np.empty(self.n_params(), dtype=np.float32)
+        loss = C.c_double()
+        s = None if stream is None else C.c_void_p(int(stream.cuda_stream))
+        _check(None, lib.sa_mlp_gradients(self.ptr, _ptr(X), _ptr(Y), int(X.shape[0]), _ptr(g),
+                                          C.byref(loss), s))
+        return loss.value, g
+
+    def train_step(self, X, Y, lr, want_loss=True, stream=None):
+        loss = C.c_double()
+        s = None if stream is None else C.c_void_p(int(stream.cuda_stream))
+        _check(None, lib.sa_mlp_train_step(self.ptr, _ptr(X), _ptr(Y), int(X.shape[0]), float(lr),
+                                           C.byref(loss) if want_loss else None, s))
+        return loss.value if want_loss else None
 
 
 class Batch:

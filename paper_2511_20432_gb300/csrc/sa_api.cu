@@ -823,7 +823,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             const int v = atoi(e);
             if (v == 1 || v == 2 || v == 4 || v == 8) c->pcg_ksplit = v;
         }
-        SA_ALLOC(c, c->partials, (size_t)11 * c->pcg_grid);
+        SA_ALLOC(c, c->partials, (size_t)12 * c->pcg_grid);
     }
     SA_CUDA(c, cudaStreamSynchronize(s));
     c->has_patch = true;
@@ -965,6 +965,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.val_hi = c->mbot_sval.p;
         L.dinv = c->mbot_dinv.p;
         L.dinvl = mixed ? (const void*)c->mbot_dinv32.p : (const void*)c->mbot_dinv.p;
+        L.dx0 = nullptr;
+        L.dx0_scale = nullptr;
         L.b = c->bbot.p;
         L.r0 = nullptr;
         L.bsq = nullptr;
@@ -993,8 +995,29 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                          c->r0.p, c->bsq.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     SA_MARK(SA_STAGE_PCG);
+    const bool rec = c->rec_X != nullptr && c->rec_count < c->rec_cap;
+    if (c->ws_net || rec) {
+        e = launch_norm(c->n_free, c->r0.p, c->ws_part.p, c->ws_norm.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "warm-start norm");
+    }
+    const float* dx0 = nullptr;
+    if (c->ws_net) {
+        e = launch_ws_input(c->ws_n_in, c->ws_idx.p, c->r0.p, c->ws_norm.p, c->ws_in.p, s);
+        if (e == cudaSuccess) e = mlp_forward(c->ws_net, c->ws_in.p, 1, &dx0, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "warm-start network");
+    }
+    if (rec) {
+        e = launch_ws_input(c->rec_n_in, c->rec_idx.p, c->r0.p, c->ws_norm.p,
+                            (unsigned char*)c->rec_X + (size_t)c->rec_count * c->rec_n_in * 2, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws_xold.p, c->That.p, sizeof(double) * c->n_free,
+                                cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "recorder input");
+    }
     {
         PcgLaunch L;
+        L.dx0 = dx0;
+        L.dx0_scale = c->ws_norm.p;
         L.op = sell_view(c->a_s);
         L.val = mixed ? (const void*)c->a_val32.p : (const void*)c->a_val.p;
         L.val_hi = c->a_val.p;
@@ -1018,6 +1041,12 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         if (const char* ev = getenv("SA_PCG_KSPLIT")) L.ksplit = atoi(ev);
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
+    }
+    if (rec) {
+        e = launch_ws_target(c->n_free, c->That.p, c->ws_xold.p, c->ws_norm.p,
+                             (unsigned char*)c->rec_Y + (size_t)c->rec_count * c->n_free * 2, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "recorder target");
+        c->rec_count += 1;
     }
     SA_MARK(SA_STAGE_FINALIZE);
     e = launch_finalize(c->n_dir, c->n_free, c->n_dof, c->gnew.p, c->That.p, c->F1.p, c->F0.p,
@@ -1077,7 +1106,7 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
     if ((st = init_state_if_needed(c))) return st;
     if ((st = ensure_operator(c, theta, dt))) return st;
     cudaStream_t s = c->stream;
-    const bool graph = c->opt.use_graph && s != nullptr && !c->opt.stage_timing;
+    const bool graph = c->opt.use_graph && s != nullptr && !c->opt.stage_timing && c->rec_X == nullptr;
     for (int i = 0; i < n_steps; ++i) {
         if (graph) {
             if (!c->graph_exec) {
@@ -1109,6 +1138,8 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
         stats->rel_res_last = h.rel_res;
         stats->n_active_sources = h.n_active;
         stats->step_index = h.n;
+        stats->ws_used_last = h.ws_used;
+        stats->ws_ratio_last = h.ws_ratio;
         // reset the counters read above (not n, not the barrier words): the
         // next stats report covers the steps since this call
         DevStatus z;
@@ -1123,6 +1154,69 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
         if (h.err & (SA_DEV_NOT_CONVERGED | SA_DEV_BOT_NOT_CONVERGED))
             return sa_fail(c, SA_ERR_NOT_CONVERGED, "PCG did not converge (flags %d, rel res %g)", h.err, h.rel_res);
     }
+    return SA_OK;
+}
+
+sa_status sa_set_warm_start(sa_ctx* c, sa_mlp* net, int n_in, const int* in_idx) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!c->has_patch) return sa_fail(c, SA_ERR_STATE, "no patch");
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    if (!net) {
+        c->ws_net = nullptr;
+        return SA_OK;
+    }
+    if (n_in <= 0 || !in_idx || mlp_n_in(net) != n_in || mlp_n_out(net) != c->n_free)
+        return sa_fail(c, SA_ERR_ARG, "network sizes (%d in, %d out) do not match (%d, %d)",
+                       mlp_n_in(net), mlp_n_out(net), n_in, c->n_free);
+    for (int k = 0; k < n_in; ++k)
+        if (in_idx[k] < 0 || in_idx[k] >= c->n_free) return sa_fail(c, SA_ERR_ARG, "in_idx[%d]", k);
+    std::vector<int> idx(in_idx, in_idx + n_in);
+    SA_UPLOAD(c, c->ws_idx, idx);
+    SA_ALLOC(c, c->ws_in, (size_t)n_in * 2);
+    if (!c->ws_norm.p) {
+        SA_ALLOC(c, c->ws_norm, 1);
+        SA_ALLOC(c, c->ws_part, 64);
+    }
+    if (mlp_prepare(net, 1) != 0) return sa_fail(c, SA_ERR_OOM, "network buffers");
+    c->ws_net = net;
+    c->ws_n_in = n_in;
+    return SA_OK;
+}
+
+sa_status sa_set_recorder(sa_ctx* c, void* X, void* Y, int capacity, int n_in, const int* in_idx) {
+    sa_status st = check_usable(c);
+    if (st) return st;
+    if (!c->has_patch) return sa_fail(c, SA_ERR_STATE, "no patch");
+    if (!X) {
+        c->rec_X = c->rec_Y = nullptr;
+        c->rec_cap = c->rec_count = 0;
+        return SA_OK;
+    }
+    if (!Y || capacity <= 0 || n_in <= 0 || !in_idx) return sa_fail(c, SA_ERR_ARG, "recorder arguments");
+    for (int k = 0; k < n_in; ++k)
+        if (in_idx[k] < 0 || in_idx[k] >= c->n_free) return sa_fail(c, SA_ERR_ARG, "in_idx[%d]", k);
+    std::vector<int> idx(in_idx, in_idx + n_in);
+    SA_UPLOAD(c, c->rec_idx, idx);
+    if (!c->ws_norm.p) {
+        SA_ALLOC(c, c->ws_norm, 1);
+        SA_ALLOC(c, c->ws_part, 64);
+    }
+    if (c->ws_xold.n < (size_t)std::max(c->n_free, 1)) SA_ALLOC(c, c->ws_xold, std::max(c->n_free, 1));
+    c->rec_X = X;
+    c->rec_Y = Y;
+    c->rec_cap = capacity;
+    c->rec_count = 0;
+    c->rec_n_in = n_in;
+    return SA_OK;
+}
+
+sa_status sa_get_recorded(sa_ctx* c, int* count) {
+    if (!c || !count) return SA_ERR_ARG;
+    *count = c->rec_count;
     return SA_OK;
 }
 

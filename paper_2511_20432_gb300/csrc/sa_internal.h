@@ -37,6 +37,9 @@ struct DevStatus {
     int n_active;             // sources in the sum at the last step
     double rel_res;           // last main solve
     double bot_rel_res;
+    int ws_used;              // last main solve started from the learned guess
+    int ws_pad;
+    double ws_ratio;          // |r0 - A dx| / |r0| of the last learned guess
     long long n;              // step index (device copy)
     long long iters_total;    // accumulated since the last reset by the host
     long long bot_total;
@@ -147,7 +150,9 @@ struct PcgLaunch {
                               // [pad | stride | pad] each, pad = halo entries
     int pad;
     size_t stride;
-    double* partials;         // 8 x grid
+    double* partials;         // 12 x grid
+    const float* dx0;         // proposed increment (mode 1), or null
+    const double* dx0_scale;  // device scalar multiplying dx0
     DevStatus* st;
     int which;
     double tol;
@@ -159,6 +164,17 @@ struct PcgLaunch {
 // ---------------------------------------------------------------------------
 // the context
 // ---------------------------------------------------------------------------
+struct sa_mlp;
+cudaError_t mlp_forward(sa_mlp* m, const void* X, int rows, const float** out, cudaStream_t s);
+int mlp_n_in(const sa_mlp* m);
+int mlp_n_out(const sa_mlp* m);
+int mlp_prepare(sa_mlp* m, int rows);
+cudaError_t launch_norm(int n, const double* r, double* part, double* norm, cudaStream_t s);
+cudaError_t launch_ws_input(int n_in, const int* idx, const double* r0, const double* norm,
+                            void* out, cudaStream_t s);
+cudaError_t launch_ws_target(int n, const double* xnew, const double* xold, const double* norm,
+                             void* out, cudaStream_t s);
+
 struct sa_ctx {
     sa_options opt;
     int device = 0;
@@ -280,6 +296,17 @@ struct sa_ctx {
     // host copies of the patterns (for sa_batch)
     SellHost a_h, r_h, mbot_h;
     std::vector<int> wlat_rowdof_h, wlat_ptr_h, wlat_col_h, wbot_ptr_h, wbot_col_h;
+
+    // learned warm start and training-data recorder
+    sa_mlp* ws_net = nullptr;
+    int ws_n_in = 0;
+    DBuf<int> ws_idx;
+    DBuf<double> ws_norm, ws_part, ws_xold;
+    DBuf<unsigned char> ws_in;       // BF16 input row (n_in)
+    void* rec_X = nullptr;           // recorder: caller's device buffers (BF16)
+    void* rec_Y = nullptr;
+    int rec_cap = 0, rec_count = 0, rec_n_in = 0;
+    DBuf<int> rec_idx;
 
     // stage timing (sa_options::stage_timing)
     cudaEvent_t ev[SA_N_STAGES + 1] = {};

@@ -9,6 +9,8 @@
 // increment from its FP64 initial guess, so the FP32 operator perturbs the
 // increment only (relative ~1e-7), far below the residual tolerance measured
 // against the full right-hand side.
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "sa_internal.h"
@@ -292,6 +294,8 @@ struct PcgArgs {
     double tol;
     int max_iter;
     int ksplit;            // warps per slice (divides the 32 warps of a block)
+    const float* dx0;      // mode 1: proposed increment (scaled by *dx0_scale), or null
+    const double* dx0_scale;
 };
 
 // Block b owns slices [s0, s1) (contiguous, balanced) and their rows.
@@ -429,8 +433,33 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
                 }
             }
         } else {                 // mode 1: r = r0 given
+            bool warm = false;
+            if (a.dx0) {
+                // proposed start x0 + dx: its residual r0 - A dx, kept only if
+                // smaller than r0 (otherwise the cold start x0 stays)
+                const double sc = *a.dx0_scale;
+                for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) a.ul[i] = (VT)(sc * a.dx0[i]);
+                if (!sync.barrier()) return;
+                double vw[2] = {0.0, 0.0};
+                spmv_block(a, win, sq, [&](int i, VT t) {
+                    const double rw = a.r0[i] - (double)t;
+                    a.r[i] = rw;
+                    vw[0] += rw * rw;
+                    vw[1] += a.r0[i] * a.r0[i];
+                });
+                double ow[2];
+                if (!sync.template reduce<2>(vw, 10, ow)) return;
+                warm = ow[0] < ow[1];
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    a.st->ws_used = warm ? 1 : 0;
+                    a.st->ws_ratio = ow[1] > 0.0 ? sqrt(ow[0] / ow[1]) : 0.0;
+                }
+                if (warm)
+                    for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
+                        a.x[i] = fma(sc, (double)a.dx0[i], a.x[i]);
+            }
             for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
-                const double ri = a.r0[i], ui = a.dinv[i] * ri;
+                const double ri = warm ? a.r[i] : a.r0[i], ui = a.dinv[i] * ri;
                 a.r[i] = ri;
                 a.u[i] = ui;
                 a.ul[i] = (VT)ui;
@@ -457,11 +486,21 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
         delta = o[1];
         rr = o[2];
     }
+    // scalar recurrences in one thread per block (FP64 division is slow on
+    // this part: every other thread only reads the results)
+    __shared__ double sc[4];   // alpha, beta, gamma, state (0 run, 1 converged, 2 nan)
     const double stop2 = a.tol * a.tol * bb;
+    if (threadIdx.x == 0) {
+        sc[0] = gamma / delta;
+        sc[1] = 0.0;
+        sc[2] = gamma;
+        sc[3] = !(rr == rr) || !(delta == delta) ? 2.0 : (rr <= stop2 ? 1.0 : 0.0);
+    }
+    __syncthreads();
     int it = 0;
-    bool conv = rr <= stop2;
-    bool nan = !(rr == rr) || !(delta == delta);
-    double alpha = gamma / delta, beta = 0.0;
+    double alpha = sc[0], beta = sc[1];
+    bool conv = sc[3] == 1.0, nan = sc[3] == 2.0;
+    __syncthreads();
     while (!conv && !nan && it < a.max_iter) {
         const bool first = (it == 0);
         // ---- V (own rows)
@@ -492,16 +531,26 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
         // two slot sets: the next iteration's partials may be written while a
         // slower block still reads these
         if (!sync.template reduce<3>(v, 4 + 3 * (it & 1), o)) return;
-        const double gnew = o[0];
-        delta = o[1];
-        rr = o[2];
         ++it;
-        beta = gnew / gamma;
-        alpha = gnew / (delta - beta * gnew / alpha);
-        gamma = gnew;
-        nan = !(rr == rr) || !(alpha == alpha);
-        conv = rr <= stop2;
+        rr = o[2];
+        if (threadIdx.x == 0) {
+            const double gnew = o[0], dl = o[1];
+            const double bt = gnew / sc[2];
+            const double al = gnew / (dl - bt * gnew / sc[0]);
+            sc[0] = al;
+            sc[1] = bt;
+            sc[2] = gnew;
+            sc[3] = !(rr == rr) || !(al == al) ? 2.0 : (rr <= stop2 ? 1.0 : 0.0);
+        }
+        __syncthreads();
+        alpha = sc[0];
+        beta = sc[1];
+        conv = sc[3] == 1.0;
+        nan = sc[3] == 2.0;
+        __syncthreads();
     }
+    (void)gamma;
+    (void)delta;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         int* err = &a.st->err;
@@ -566,6 +615,8 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     a.which = L.which;
     a.tol = L.tol;
     a.max_iter = L.max_iter;
+    a.dx0 = L.dx0;
+    a.dx0_scale = L.dx0_scale;
     const int G = L.grid > 0 ? L.grid : 1;
     // slices per block -> warps per slice so the 32 warps of a block are busy
     const int spb = (L.op.n_slices + G - 1) / G;
@@ -597,7 +648,70 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, k_pcg<VT>, a);
 }
 
+// ---------------------------------------------------------------------------
+// warm start / training-data recorder helpers
+// ---------------------------------------------------------------------------
+// ||r0||_2 over n entries: per-block partials then one block in fixed order.
+__global__ void k_norm_part(int n, const double* r, double* part) {
+    __shared__ double sh[256];
+    double t = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        t += r[i] * r[i];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_norm_final(int nb, const double* part, double* norm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int i = 0; i < nb; ++i) t += part[i];
+    *norm = sqrt(t);
+}
+
+// x_in[k] = r0[idx[k]] / ||r0|| as BF16 (recorder: appended at row `slot`)
+__global__ void k_ws_input(int n_in, const int* idx, const double* r0, const double* norm,
+                           __nv_bfloat16* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_in) return;
+    const double nr = *norm;
+    out[k] = __float2bfloat16(nr > 0.0 ? (float)(r0[idx[k]] / nr) : 0.f);
+}
+
+// y = (x_new - x_old) / ||r0|| as BF16
+__global__ void k_ws_target(int n, const double* xnew, const double* xold, const double* norm,
+                            __nv_bfloat16* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double nr = *norm;
+    out[i] = __float2bfloat16(nr > 0.0 ? (float)((xnew[i] - xold[i]) / nr) : 0.f);
+}
+
 }  // namespace
+
+cudaError_t launch_norm(int n, const double* r, double* part, double* norm, cudaStream_t s) {
+    k_norm_part<<<64, 256, 0, s>>>(n, r, part);
+    k_norm_final<<<1, 32, 0, s>>>(64, part, norm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ws_input(int n_in, const int* idx, const double* r0, const double* norm,
+                            void* out, cudaStream_t s) {
+    if (n_in == 0) return cudaSuccess;
+    k_ws_input<<<(n_in + 255) / 256, 256, 0, s>>>(n_in, idx, r0, norm, (__nv_bfloat16*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ws_target(int n, const double* xnew, const double* xold, const double* norm,
+                             void* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_ws_target<<<(n + 255) / 256, 256, 0, s>>>(n, xnew, xold, norm, (__nv_bfloat16*)out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat_ptr,
                           const int* wlat_col, const double* wlat_val, const double* s_lat,
