@@ -73,7 +73,28 @@ typedef struct sa_options {
     int stage_timing;          /* 1: CUDA events around every stage of each step (direct
                                   launches, the graph path is off while set); the step then
                                   synchronises; read the times with sa_get_stage_times   */
+    int pcg_variant;           /* where both solves keep their Krylov vectors (same
+                                  Jacobi-PCG recurrences, Chronopoulos-Gear form, FP64
+                                  vectors, two grid barriers per iteration):
+                                  SA_PCG_AUTO (0, default): shared memory when a block's
+                                    rows fit, global memory otherwise;
+                                  SA_PCG_SHARED (1): shared memory (SA_ERR_ARG at set-up
+                                    if the rows do not fit);
+                                  SA_PCG_GLOBAL (2): global memory                  */
+    int initial_guess;         /* start of each theta-step solve:
+                                  SA_GUESS_PREVIOUS (0, default): T^n (and g^n for
+                                    the bottom projection);
+                                  SA_GUESS_EXTRAPOLATE (1): T^n + (T^n - T^{n-1}),
+                                    kept only when its residual is below that of
+                                    T^n, and 2 g^n - g^{n-1} for the projection.  The
+                                    converged step is the same to the solver tolerance;
+                                    after sa_set_state the first step starts from T^n.
+                                  A learned warm start (sa_set_warm_start) replaces
+                                  the extrapolated proposal of the main solve.     */
 } sa_options;
+
+enum { SA_PCG_AUTO = 0, SA_PCG_SHARED = 1, SA_PCG_GLOBAL = 2 };
+enum { SA_GUESS_PREVIOUS = 0, SA_GUESS_EXTRAPOLATE = 1 };
 
 /* Fill o with the defaults listed above. */
 void sa_options_default(sa_options* o);

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libsa.so")
 SA_OK, SA_ERR_ARG, SA_ERR_GEOMETRY, SA_ERR_STATE, SA_ERR_CUDA, SA_ERR_OOM, \
     SA_ERR_NOT_CONVERGED, SA_ERR_TIMEOUT, SA_ERR_NAN = range(9)
 SA_FP64, SA_MIXED = 0, 1
+SA_PCG_AUTO, SA_PCG_SHARED, SA_PCG_GLOBAL = 0, 1, 2
+SA_GUESS_PREVIOUS, SA_GUESS_EXTRAPOLATE = 0, 1
 SA_FACE_NONE, SA_FACE_NEUMANN, SA_FACE_DIRICHLET = 0, 1, 2
 SA_FIELD_THAT, SA_FIELD_F, SA_FIELD_DTDN_LAT, SA_FIELD_TT_BOT, SA_FIELD_LAT_X, SA_FIELD_BOT_X = range(6)
 STAGES = ("prologue", "history", "gather", "bottom", "rhs", "pcg", "finalize")
@@ -27,7 +29,8 @@ class sa_options(C.Structure):
                 ("half_space_factor", C.c_double), ("cuda_stream", C.c_void_p),
                 ("use_graph", C.c_int), ("device", C.c_int),
                 ("hist_points_per_lane", C.c_int), ("hist_warps", C.c_int),
-                ("stage_timing", C.c_int)]
+                ("stage_timing", C.c_int), ("pcg_variant", C.c_int),
+                ("initial_guess", C.c_int)]
 
 
 class sa_step_stats(C.Structure):

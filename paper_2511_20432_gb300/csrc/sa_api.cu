@@ -185,6 +185,7 @@ cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
             SA_UPLOAD(ctx, (dev).col16, (host).col16); \
         SA_UPLOAD(ctx, (dev).src, (host).src);    \
         SA_UPLOAD(ctx, (dev).diag, (host).diag);  \
+        SA_UPLOAD(ctx, (dev).hi, sell_hi_flags(host)); \
     } while (0)
 
 #define SA_UPLOAD(ctx, buf, vec)                                                              \
@@ -244,6 +245,9 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
     if (opt.precision != SA_FP64 && opt.precision != SA_MIXED) return SA_ERR_ARG;
     if (!(opt.pcg_tol > 0.0) || opt.pcg_max_iter <= 0) return SA_ERR_ARG;
     if (!(opt.half_space_factor > 0.0) || !is_fin(opt.half_space_factor)) return SA_ERR_ARG;
+    if (opt.pcg_variant < SA_PCG_AUTO || opt.pcg_variant > SA_PCG_GLOBAL) return SA_ERR_ARG;
+    if (opt.initial_guess != SA_GUESS_PREVIOUS && opt.initial_guess != SA_GUESS_EXTRAPOLATE)
+        return SA_ERR_ARG;
     if (opt.hist_points_per_lane != 0 && opt.hist_points_per_lane != 1 &&
         opt.hist_points_per_lane != 2 && opt.hist_points_per_lane != 4)
         return SA_ERR_ARG;
@@ -777,6 +781,14 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_ALLOC(c, c->rhs, nwork);
     SA_ALLOC(c, c->r0, nwork);
     SA_ALLOC(c, c->bsq, nwork);
+    SA_ALLOC(c, c->dirv, 2 * (size_t)std::max(c->n_dir, 1));
+    if (c->opt.initial_guess == SA_GUESS_EXTRAPOLATE) {
+        SA_ALLOC(c, c->x_prev, ndof);
+        SA_ALLOC(c, c->dx_extrap, std::max(c->n_free, 1));
+        SA_ALLOC(c, c->one, 1);
+        const double one = 1.0;
+        SA_CUDA(c, cudaMemcpy(c->one.p, &one, sizeof(double), cudaMemcpyHostToDevice));
+    }
     c->nwork = nwork;
     SA_ALLOC(c, c->work64, (size_t)5 * nwork);
     {
@@ -784,10 +796,13 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         int halo = 0;
         halo = std::max(halo, std::max(-c->a_s.dmin, c->a_s.dmax));
         halo = std::max(halo, std::max(-c->mbot_s.dmin, c->mbot_s.dmax));
-        c->work_pad = (halo + 8 + 3) & ~3;
+        // a block's window reaches 32 s1 + dmax, up to 31 rows past n, and
+        // starts up to 3 entries before 32 s0 + dmin (16-byte alignment)
+        c->work_pad = (halo + 40 + 3) & ~3;
         const size_t vt = c->opt.precision == SA_MIXED ? sizeof(float) : sizeof(double);
-        SA_ALLOC(c, c->workpad, (nwork + 2 * (size_t)c->work_pad) * vt);
-        SA_CUDA(c, cudaMemsetAsync(c->workpad.p, 0, (nwork + 2 * (size_t)c->work_pad) * vt, s));
+        // two padded vectors (the pipelined PCG publishes into them alternately)
+        SA_ALLOC(c, c->workpad, 2 * (nwork + 2 * (size_t)c->work_pad) * vt);
+        SA_CUDA(c, cudaMemsetAsync(c->workpad.p, 0, 2 * (nwork + 2 * (size_t)c->work_pad) * vt, s));
     }
     SA_ALLOC(c, c->dev64, ndof);
     SA_ALLOC(c, c->dev32, ndof);
@@ -824,6 +839,16 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             if (v == 1 || v == 2 || v == 4 || v == 8) c->pcg_ksplit = v;
         }
         SA_ALLOC(c, c->partials, (size_t)12 * c->pcg_grid);
+        if (c->opt.pcg_variant == SA_PCG_SHARED) {
+            PcgLaunch L{};
+            L.op = sell_view(c->a_s);
+            L.pad = c->work_pad;
+            L.grid = c->pcg_grid;
+            if (!pcg_shared_fits(c->opt.precision, L))
+                return sa_fail(c, SA_ERR_ARG,
+                               "shared-memory PCG: %d rows per block do not fit in shared memory",
+                               32 * ((c->a_s.n_slices + c->pcg_grid - 1) / c->pcg_grid));
+        }
     }
     SA_CUDA(c, cudaStreamSynchronize(s));
     c->has_patch = true;
@@ -954,11 +979,20 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
     const bool mixed = c->opt.precision == SA_MIXED;
     SA_MARK(SA_STAGE_BOTTOM);
+    const bool extrap = c->opt.initial_guess == SA_GUESS_EXTRAPOLATE;
+    if (extrap) {
+        // proposals T^n - T^{n-1} (main solve) and 2 g^n - g^{n-1} (projection)
+        e = launch_extrap(c->n_free, c->n_dir, c->That.p, c->x_prev.p, c->dx_extrap.p,
+                          c->x_prev.p + c->n_free, c->gnew.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "extrapolated guess");
+    }
     if (c->n_dir > 0) {
-        // x0 = g^n (the Dirichlet part of the state)
-        e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
-                            cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
+        // x0 = g^n (the Dirichlet part of the state), or its extrapolation
+        if (!extrap) {
+            e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
+                                cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
+        }
         PcgLaunch L;
         L.op = sell_view(c->mbot_s);
         L.val = mixed ? (const void*)c->mbot_sval32.p : (const void*)c->mbot_sval.p;
@@ -977,6 +1011,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.stride = c->nwork;
         L.partials = c->partials.p;
         L.st = c->st.p;
+        L.variant = c->opt.pcg_variant;
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
@@ -992,7 +1027,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                          mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
                          mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
                          c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
-                         c->r0.p, c->bsq.p, s);
+                         c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     SA_MARK(SA_STAGE_PCG);
     const bool rec = c->rec_X != nullptr && c->rec_count < c->rec_cap;
@@ -1000,7 +1035,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         e = launch_norm(c->n_free, c->r0.p, c->ws_part.p, c->ws_norm.p, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "warm-start norm");
     }
-    const float* dx0 = nullptr;
+    const float* dx0 = extrap ? c->dx_extrap.p : nullptr;
+    const double* dx0_scale = extrap ? c->one.p : nullptr;
     if (c->ws_net) {
         e = launch_ws_input(c->ws_n_in, c->ws_idx.p, c->r0.p, c->ws_norm.p, c->ws_in.p, s);
         if (e == cudaSuccess) e = mlp_forward(c->ws_net, c->ws_in.p, 1, &dx0, s);
@@ -1017,7 +1053,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     {
         PcgLaunch L;
         L.dx0 = dx0;
-        L.dx0_scale = c->ws_norm.p;
+        L.dx0_scale = c->ws_net ? c->ws_norm.p : dx0_scale;
         L.op = sell_view(c->a_s);
         L.val = mixed ? (const void*)c->a_val32.p : (const void*)c->a_val.p;
         L.val_hi = c->a_val.p;
@@ -1033,6 +1069,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.stride = c->nwork;
         L.partials = c->partials.p;
         L.st = c->st.p;
+        L.variant = c->opt.pcg_variant;
         L.which = 0;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
@@ -1074,6 +1111,8 @@ sa_status init_state_if_needed(sa_ctx* c) {
     // T^(x, 0) = T_c (Section 2.1): constants are exact in the spline space
     std::vector<double> T0(c->n_dof, c->Tc);
     SA_CUDA(c, cudaMemcpy(c->That.p, T0.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
+    if (c->x_prev.p)
+        SA_CUDA(c, cudaMemcpy(c->x_prev.p, T0.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
     c->state_init = true;
     return SA_OK;
 }
@@ -1359,6 +1398,8 @@ sa_status sa_set_state(sa_ctx* c, long long n, const double* T_hat, const double
     SA_CUDA(c, cudaStreamSynchronize(s));
     SA_CUDA(c, cudaMemcpy(c->That.p, Ti.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
     SA_CUDA(c, cudaMemcpy(c->F0.p, Fi.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
+    if (c->x_prev.p)   // the first step after a restore starts from T^n
+        SA_CUDA(c, cudaMemcpy(c->x_prev.p, Ti.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
     SA_CUDA(c, cudaMemcpy(&c->st.p->n, &n, sizeof(long long), cudaMemcpyHostToDevice));
     c->n_step = n;
     return SA_OK;

@@ -66,7 +66,7 @@ struct sa_batch {
     DBuf<float> a_val32, r_K32, r_M32, mbot_val32;
     DBuf<int> slice_inst_a, slice_inst_b, d_slice_off_a, d_slice_off_b;
     // state and work
-    DBuf<double> That, F0, F1, gnew, bbot, r0, bsq, wr, wz, wp0, wp1, wq, dev64, partials, inst_state;
+    DBuf<double> That, F0, F1, gnew, bbot, r0, bsq, dirv, wr, wz, wp0, wp1, wq, dev64, partials, inst_state;
     DBuf<float> dev32, wzl, wpl0, wpl1;
     DBuf<int> inst_iters;
     DBuf<unsigned> counters;
@@ -688,6 +688,7 @@ sa_status build(sa_batch* b, double theta, double dt) {
             } else {
                 if ((st = bupload(b, d.col, h.col, what))) return st;
             }
+            if ((st = bupload(b, d.hi, sell_hi_flags(h), what))) return st;
             return SA_OK;
         };
         sa_status st;
@@ -743,6 +744,7 @@ sa_status build(sa_batch* b, double theta, double dt) {
         B_ALLOC(b, b->bbot, std::max(b->n_dir, 1));
         B_ALLOC(b, b->r0, nwork);
         B_ALLOC(b, b->bsq, nwork);
+        B_ALLOC(b, b->dirv, 2 * std::max(b->n_dir, 1));
         B_ALLOC(b, b->wr, nwork);
         B_ALLOC(b, b->wz, nwork);
         B_ALLOC(b, b->wp0, nwork);
@@ -832,7 +834,7 @@ sa_status enqueue_batch_step(sa_batch* b) {
                          mixed ? (const void*)b->r_M32.p : (const void*)b->r_M.p,
                          mixed ? (const void*)b->dev32.p : (const void*)b->dev64.p, b->That.p,
                          b->gnew.p, b->F0.p, b->F1.p, b->rho * b->cp / b->dt, b->k, b->theta,
-                         b->Tc, b->r0.p, b->bsq.p, s);
+                         b->Tc, b->r0.p, b->bsq.p, b->n_dir, b->dirv.p, s);
     if (e != cudaSuccess) return bcuda(b, e, "batched rhs");
     if (mixed)
         e = launch_pcg_batch<float>(b, 0, b->a_s, b->a_val32.p, b->a_val.p, b->slice_inst_a.p,

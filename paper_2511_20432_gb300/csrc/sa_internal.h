@@ -101,6 +101,7 @@ struct SellDev {
     DBuf<short> col16;        // n_stored (column - row), when every offset fits
     DBuf<int> src;            // n_stored: slot in the source CSR, -1 for padding
     DBuf<int> diag;           // n: storage index of the diagonal entry
+    DBuf<unsigned char> hi;   // n_slices: 1 when the slice holds a column >= n
     int dmin = 0, dmax = 0;
 };
 
@@ -113,12 +114,27 @@ struct SellHost {
     int dmin = 0, dmax = 0;     // extreme column - row offsets (when col16 is filled)
 };
 
+// Per slice: 1 when a stored entry has a column >= n, i.e. for the free-row
+// operators, a Dirichlet column (padding entries hold a column < n).
+inline std::vector<unsigned char> sell_hi_flags(const SellHost& h) {
+    std::vector<unsigned char> f(h.n_slices > 0 ? h.n_slices : 1, 0);
+    if (h.col.empty()) return f;
+    for (int s = 0; s < h.n_slices; ++s)
+        for (long long e = h.sptr[s]; e < h.sptr[s + 1]; ++e)
+            if (h.col[e] >= h.n) {
+                f[s] = 1;
+                break;
+            }
+    return f;
+}
+
 // What the kernels need of a SELL operator (no ownership).
 struct SellView {
     int n, n_slices;
     const long long* sptr;
     const int* col32;         // null when col16 is used
     const short* col16;
+    const unsigned char* hi;  // per slice: holds a column >= n (may be null)
     int dmin, dmax;           // extreme column - row offsets (col16 only)
 };
 
@@ -129,6 +145,7 @@ inline SellView sell_view(const SellDev& s) {
     v.sptr = s.sptr.p;
     v.col16 = s.col16.p;
     v.col32 = s.col16.p ? nullptr : s.col.p;
+    v.hi = s.hi.p;
     v.dmin = s.dmin;
     v.dmax = s.dmax;
     return v;
@@ -146,10 +163,12 @@ struct PcgLaunch {
     const double* bsq;        // with r0: b_i^2 per row (norm of the right-hand side)
     double* x;
     double* w64;              // FP64 work vectors of length stride: p, r, w, s, u
-    void* vpad;               // 2 padded vectors (u, x) in the path's precision:
-                              // [pad | stride | pad] each, pad = halo entries
+    void* vpad;               // 2 padded vectors in the path's precision, each
+                              // [pad | stride | pad], pad = halo entries; vector k
+                              // starts at k (stride + 2 pad)
     int pad;
     size_t stride;
+    int variant;              // SA_PCG_AUTO / SA_PCG_SHARED / SA_PCG_GLOBAL
     double* partials;         // 12 x grid
     const float* dx0;         // proposed increment (mode 1), or null
     const double* dx0_scale;  // device scalar multiplying dx0
@@ -273,6 +292,7 @@ struct sa_ctx {
     DBuf<double> F0, F1;      // internal order (n_dof)
     DBuf<double> gnew, bbot;  // n_dir
     DBuf<double> rhs, r0, bsq;   // n_free
+    DBuf<double> dirv;           // 2 n_dir: Dirichlet increments for the theta RHS
     DBuf<double> work64;                 // PCG work: 5 x nwork (FP64)
     DBuf<unsigned char> workpad;         // PCG padded vectors (2 x (nwork + 2 pad) x VT)
     int work_pad = 0;
@@ -296,6 +316,11 @@ struct sa_ctx {
     // host copies of the patterns (for sa_batch)
     SellHost a_h, r_h, mbot_h;
     std::vector<int> wlat_rowdof_h, wlat_ptr_h, wlat_col_h, wbot_ptr_h, wbot_col_h;
+
+    // extrapolated initial guesses (sa_options::initial_guess)
+    DBuf<double> x_prev;             // T^{n-1}: free part, then the Dirichlet part
+    DBuf<float> dx_extrap;           // n_free: proposed increment T^n - T^{n-1}
+    DBuf<double> one;                // device scalar 1.0 (scale of dx_extrap)
 
     // learned warm start and training-data recorder
     sa_mlp* ws_net = nullptr;
@@ -395,8 +420,12 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
-                             double* bsq, cudaStream_t s);
+                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
+cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
+                          double* gprev, double* g0, cudaStream_t s);
+// Whether the shared-memory PCG of this launch keeps its rows in shared memory.
+bool pcg_shared_fits(int precision, const PcgLaunch& L);
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
                             const double* F1, double* F0, DevStatus* st, cudaStream_t s);
 int pcg_block_size();

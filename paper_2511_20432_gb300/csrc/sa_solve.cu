@@ -89,6 +89,7 @@ struct Op {
     const long long* sptr;
     const int* col32;      // absolute column, or
     const short* col16;    // column - row (when every offset fits in 16 bits)
+    const unsigned char* hi;   // per slice: holds a column >= n (null: unknown)
     const VT* val;
     __device__ __forceinline__ int col(long long e, int row) const {
         return col16 ? row + (int)__ldg(col16 + e) : __ldg(col32 + e);
@@ -101,16 +102,15 @@ struct Op {
 //   r0 = b - A_ff T^n_f = theta F^{n+1} + (1-theta) F^n - [K (T^n - T_c)]_f
 //        - A_fd (g^{n+1} - g^n)
 // (B - A = -K and K 1 = 0).  No large terms cancel, so the FP32 operator of
-// the mixed path keeps r0 accurate relative to the increment.  The M values
-// are read only for Dirichlet columns.
+// the mixed path keeps r0 accurate relative to the increment.
 // ---------------------------------------------------------------------------
 template <typename VT>
 struct RhsArgs {
     Op<VT> K;              // free rows of K (unit k), all columns (internal)
     const VT* Mval;        // free rows of M (unit rho c_p), same storage as K
     const VT* dev;         // T^n - T_c
-    const double* That;
-    const double* gnew;
+    const VT* dg;          // Dirichlet dofs: g^{n+1} - g^n
+    const VT* g1;          // Dirichlet dofs: g^{n+1}
     const double* F0;
     const double* F1;
     int n_free;
@@ -119,20 +119,25 @@ struct RhsArgs {
     double* bsq;           // b_i^2, for the norm of the right-hand side
 };
 
-// Also forms b itself (only its squares are kept, for the PCG stopping test):
-//   b = (rho c_p/dt) M T^n - (1-theta) k K T^n + theta F^{n+1} + (1-theta) F^n
-//       - A_fd g^{n+1},   with M T^n = T_c (M 1) + M (T^n - T_c).
+// g^{n+1} - g^n and g^{n+1} in the operator precision, so that the rows
+// coupled to Dirichlet columns need no FP64 arithmetic per entry.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
-    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (sl >= a.K.n_slices) return;
-    const int i = sl * 32 + lane;
-    const int ir = min(i, a.n_free - 1);
-    const long long base = a.K.sptr[sl];
-    const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
-    VT acck = 0, accm = 0, summ = 0;
-    double accd = 0.0, accg = 0.0;
+__global__ void k_dir_prep(int n_dir, int n_free, const double* That, const double* gnew,
+                           VT* dg, VT* g1) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= n_dir) return;
+    const double g = gnew[d];
+    dg[d] = (VT)(g - That[n_free + d]);
+    g1[d] = (VT)g;
+}
+
+// One slice (warp; lane = row): K dev, M dev and the row sum of M; with DIR,
+// also the M and K products with (g^{n+1} - g^n) and g^{n+1} on the
+// Dirichlet columns.  DIR is uniform over the warp (a flag per slice), so
+// slices without Dirichlet columns carry none of that work.
+template <bool DIR, typename VT>
+__device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, int w, int lane,
+                                          int ir, VT (&acc)[7]) {
     for (int k = 0; k < w; k += 8) {
         int jj[8];
         VT kv[8], mv[8], dv[8];
@@ -148,23 +153,55 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
         for (int u = 0; u < 8; ++u) dv[u] = a.dev[jj[u]];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            acck = fma(kv[u], dv[u], acck);
-            accm = fma(mv[u], dv[u], accm);
-            summ += mv[u];
-            const int j = jj[u];
-            if (j >= a.n_free) {   // Dirichlet column: A_ij (g^{n+1}_j - g^n_j) and A_ij g^{n+1}_j
-                const double Aij = (double)mv[u] * a.inv_dt_rhocp + a.theta * a.k * (double)kv[u];
-                const double g1 = a.gnew[j - a.n_free];
-                accd += Aij * (g1 - a.That[j]);
-                accg += Aij * g1;
+            acc[0] = fma(kv[u], dv[u], acc[0]);
+            acc[1] = fma(mv[u], dv[u], acc[1]);
+            acc[2] += mv[u];
+        }
+        if (DIR) {
+            VT dg[8], g1[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int jd = jj[u] - a.n_free;
+                dg[u] = jd >= 0 ? a.dg[jd] : (VT)0;
+                g1[u] = jd >= 0 ? a.g1[jd] : (VT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                acc[3] = fma(mv[u], dg[u], acc[3]);
+                acc[4] = fma(kv[u], dg[u], acc[4]);
+                acc[5] = fma(mv[u], g1[u], acc[5]);
+                acc[6] = fma(kv[u], g1[u], acc[6]);
             }
         }
     }
+}
+
+// Also forms b itself (only its squares are kept, for the PCG stopping test):
+//   b = (rho c_p/dt) M T^n - (1-theta) k K T^n + theta F^{n+1} + (1-theta) F^n
+//       - A_fd g^{n+1},   with M T^n = T_c (M 1) + M (T^n - T_c)
+// and A_fd = (rho c_p/dt) M_fd + theta k K_fd.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
+    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= a.K.n_slices) return;
+    const int i = sl * 32 + lane;
+    const int ir = min(i, a.n_free - 1);
+    const long long base = a.K.sptr[sl];
+    const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
+    VT acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (a.K.hi == nullptr || a.K.hi[sl])
+        rhs_slice<true>(a, base, w, lane, ir, acc);
+    else
+        rhs_slice<false>(a, base, w, lane, ir, acc);
     if (i < a.n_free) {
+        const double tk = a.theta * a.k;
+        const double accd = a.inv_dt_rhocp * (double)acc[3] + tk * (double)acc[4];
+        const double accg = a.inv_dt_rhocp * (double)acc[5] + tk * (double)acc[6];
         const double f = a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i];
-        a.r0[i] = f - a.k * (double)acck - accd;
-        const double b = a.inv_dt_rhocp * (a.Tc * (double)summ + (double)accm) -
-                         (1.0 - a.theta) * a.k * (double)acck + f - accg;
+        a.r0[i] = f - a.k * (double)acc[0] - accd;
+        const double b = a.inv_dt_rhocp * (a.Tc * (double)acc[2] + (double)acc[1]) -
+                         (1.0 - a.theta) * a.k * (double)acc[0] + f - accg;
         a.bsq[i] = b * b;
     }
 }
@@ -198,9 +235,32 @@ __device__ void block_reduce(double (&v)[NV], double* out) {
     __syncthreads();
 }
 
+// Memory-model primitives of the grid barrier (PTX acquire/release at GPU
+// scope: no separate fences).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide: per-block partials, a bounded-wait barrier (co-residency from
 // the cooperative launch; a wait over the limit flags SA_DEV_TIMEOUT and the
 // kernel returns), then every block sums all partials in the same order.
+// Barrier: thread 0 reads the generation, arrives with an acq_rel atomic
+// (releasing the block's writes, ordered before it by the CTA barrier); the
+// last arrival resets the count and publishes the next generation with a
+// release store; the others poll the generation with acquire loads.
 struct GridSync {
     unsigned* count;
     unsigned* gen;
@@ -211,18 +271,15 @@ struct GridSync {
         __syncthreads();
         if (threadIdx.x == 0) {
             ok = 1;
-            volatile unsigned* vgen = gen;
-            const unsigned my = *vgen;
-            __threadfence();
-            const unsigned arrived = atomicAdd(count, 1u) + 1u;
+            const unsigned my = ld_acquire(gen);
+            const unsigned arrived = atom_add_acq_rel(count, 1u) + 1u;
             if (arrived == gridDim.x) {
-                atomicExch(count, 0u);
-                __threadfence();
-                atomicAdd(gen, 1u);
+                st_relaxed(count, 0u);
+                st_release(gen, my + 1u);
             } else {
                 const unsigned long long t0 = global_ns();
                 long long spins = 0;
-                while (*vgen == my) {
+                while (ld_acquire(gen) == my) {
                     if ((++spins & 255) == 0) {
                         if (global_ns() - t0 > 2000000000ull || spins > (1ll << 30)) {
                             atomicOr(err, SA_DEV_TIMEOUT);
@@ -236,7 +293,6 @@ struct GridSync {
                     }
                 }
             }
-            __threadfence();
         }
         __syncthreads();
         return ok != 0;
@@ -304,13 +360,24 @@ __device__ __forceinline__ void block_slices(int S, int& s0, int& s1) {
     s1 = (int)(((long long)S * (blockIdx.x + 1)) / gridDim.x);
 }
 
-// w = A u on the block's slices.  Window mode: the entries of u the block
-// can touch, ul[32 s0 + dmin .. 32 s1 + dmax), are first copied into shared
-// memory (coalesced L2 loads), so every gather is a shared-memory read.
-// Each slice is split over KS consecutive warps (partial sums combined in
-// fixed order).  own(i, w_i) runs once per row.
+// What a block's SpMV needs of the operator and of the vector it gathers.
+template <typename VT>
+struct SpmvPlan {
+    Op<VT> A;
+    int dmin, dmax;        // column - row offsets (window mode)
+    bool window;           // gathers from a shared-memory window of src
+    int ksplit;            // warps per slice (divides the 32 warps of a block)
+};
+
+// y = A src on the block's slices.  Window mode: the entries of src the
+// block can touch, src[32 s0 + dmin .. 32 s1 + dmax), are first copied into
+// shared memory (coalesced L2 loads), so every gather is a shared-memory
+// read.  src is written by other blocks during the kernel, so it is read
+// through L2 (ld.global.cg), never from a stale L1 line.  Each slice is split
+// over KS consecutive warps (partial sums combined in fixed order).
+// own(i, y_i) runs once per row.
 template <typename VT, class Own>
-__device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
+__device__ void spmv_block(const SpmvPlan<VT>& a, const VT* src, VT* win, VT* sq, Own own) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int nwb = blockDim.x >> 5;
@@ -328,7 +395,7 @@ __device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int t = t0 + u * blockDim.x;
-                tmp[u] = t < len ? __ldcg(a.ul + wlo + t) : (VT)0;
+                tmp[u] = t < len ? __ldcg(src + wlo + t) : (VT)0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -371,7 +438,7 @@ __device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
 #pragma unroll 8
                 for (int k = k0; k < k1; ++k) {
                     const long long e = base + 32ll * k + lane;
-                    acc = fma(__ldg(a.A.val + e), a.ul[a.A.col(e, ir)], acc);
+                    acc = fma(__ldg(a.A.val + e), __ldcg(src + a.A.col(e, ir)), acc);
                 }
             }
         }
@@ -387,6 +454,11 @@ __device__ void spmv_block(const PcgArgs<VT>& a, VT* win, VT* sq, Own own) {
         }
         if (KS > 1) __syncthreads();
     }
+}
+
+template <typename VT>
+__device__ __forceinline__ SpmvPlan<VT> plan_of(const PcgArgs<VT>& a) {
+    return SpmvPlan<VT>{a.A, a.dmin, a.dmax, a.window, a.ksplit};
 }
 
 // Jacobi-preconditioned CG in the Chronopoulos-Gear form (u = D^{-1} r,
@@ -441,7 +513,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
                 for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) a.ul[i] = (VT)(sc * a.dx0[i]);
                 if (!sync.barrier()) return;
                 double vw[2] = {0.0, 0.0};
-                spmv_block(a, win, sq, [&](int i, VT t) {
+                spmv_block(plan_of(a), a.ul, win, sq, [&](int i, VT t) {
                     const double rw = a.r0[i] - (double)t;
                     a.r[i] = rw;
                     vw[0] += rw * rw;
@@ -473,7 +545,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
     double gamma, delta, rr;
     {
         double v[3] = {0.0, 0.0, 0.0};
-        spmv_block(a, win, sq, [&](int i, VT wacc) {
+        spmv_block(plan_of(a), a.ul, win, sq, [&](int i, VT wacc) {
             const double wi = (double)wacc, ui = a.u[i], ri = a.r[i];
             a.w[i] = wi;
             v[0] += ri * ui;
@@ -520,7 +592,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
         if (!sync.barrier()) return;
         // ---- S
         double v[3] = {0.0, 0.0, 0.0};
-        spmv_block(a, win, sq, [&](int i, VT wacc) {
+        spmv_block(plan_of(a), a.ul, win, sq, [&](int i, VT wacc) {
             const double wi = (double)wacc, ui = a.u[i], ri = a.r[i];
             a.w[i] = wi;
             v[0] += ri * ui;
@@ -567,6 +639,309 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Jacobi-PCG in the Chronopoulos-Gear form with every block's vectors in
+// shared memory (FP64; u = D^{-1} r also published in the operator
+// precision for the other blocks' gathers).  Per iteration:
+//   V: p = u + beta p ; s = w + beta s ; d += alpha p ; r -= alpha s ;
+//      u = D^{-1} r, published                         (grid barrier)
+//   S: w = A u ; partial (r, u), (w, u), (r, r)         (grid reduction)
+//   beta' = gamma'/gamma ; alpha' = gamma' / (delta' - beta' gamma'/alpha)
+// d is the increment from the initial guess; x += d on exit.  Block partial
+// sums are combined across blocks in a fixed order (deterministic).  The
+// pipelined recurrences (one barrier per iteration) were tried and
+// rejected: with the FP32 operator they stall near 1e-8 of ||b||.
+// ---------------------------------------------------------------------------
+constexpr int kSmemVecs = 7;   // d r u w s p dinv (FP64), then sigma r, sigma u in VT
+
+template <typename VT>
+struct SmemArgs {
+    SpmvPlan<VT> plan;
+    int rcap;              // rows per block (shared-memory vector length)
+    const double* val_hi;  // FP64 values of A (mode 0 initial residual)
+    const double* dinv;    // D^{-1}
+    const double* b;       // mode 0: right-hand side (r0 = b - A x)
+    const double* r0;      // mode 1: initial residual
+    const double* bsq;     // mode 1: b_i^2 per row (for the norm of b)
+    double* x;
+    VT* ul;                // u published in VT, padded: ul[-pad .. n + pad)
+    double* part;
+    DevStatus* st;
+    int which;
+    double tol;
+    int max_iter;
+    const float* dx0;      // mode 1: proposed increment (scaled by *dx0_scale), or null
+    const double* dx0_scale;
+    const void* dinvl;     // D^{-1} in VT
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sums of NV per-thread values (warp tree in AT, the 32 warp results
+// in AT by warp 0, in fixed order) -> out[k] (shared, all threads).
+template <int NV, typename AT>
+__device__ void block_sum(AT (&v)[NV], AT* out) {
+    __shared__ AT sb[NV][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum_t(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sb[k][w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            AT t = lane < nw ? sb[k][lane] : (AT)0;
+            t = warp_sum_t(t);
+            if (lane == 0) out[k] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// Block values bl[0..NV) -> partial slots (AT), grid barrier, the sum over
+// all blocks in AT in a fixed order (identical in every block) -> res[k]
+// (FP64, shared, all threads).
+template <int NV, typename AT>
+__device__ bool grid_exchange(const GridSync& g, const AT* bl, int slot, double* res) {
+    const int G = gridDim.x;
+    AT* part = (AT*)g.part;
+    if (threadIdx.x < NV) part[(slot + threadIdx.x) * G + blockIdx.x] = bl[threadIdx.x];
+    if (!g.barrier()) return false;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const AT* pk = part + (slot + k) * G;
+            AT t = (AT)0;
+            for (int i = threadIdx.x; i < G; i += 32) t += __ldcg(pk + i);
+            t = warp_sum_t(t);
+            if (threadIdx.x == 0) res[k] = (double)t;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
+    // AT: type of the dot products (the operator precision).  The mixed
+    // path forms them in FP32 from copies of r and u scaled by 1/||b||
+    // (range), with FP32 scalars; the vectors and their updates stay FP64.
+    using AT = VT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* V = (double*)smem_raw;          // kSmemVecs x rcap (FP64)
+    AT* R32 = (AT*)(V + kSmemVecs * a.rcap);   // sigma r
+    AT* U32 = R32 + a.rcap;                 // sigma u
+    VT* sq = (VT*)(U32 + a.rcap);           // 1024 (k-split partial sums)
+    VT* win = sq + 1024;                    // window
+    double* const D = V;
+    double* const R = V + a.rcap;
+    double* const U = V + 2 * a.rcap;
+    double* const W = V + 3 * a.rcap;
+    double* const S = V + 4 * a.rcap;
+    double* const P = V + 5 * a.rcap;
+    double* const DI = V + 6 * a.rcap;
+    __shared__ double bl64[4];
+    __shared__ AT blt[4];
+    __shared__ double res[4];
+    __shared__ double sc[4];                // alpha, beta (applied), sigma
+    __shared__ AT scl[4];                   // alpha, gamma (previous) in AT
+    __shared__ int state;                   // 0 run, 1 converged, 2 nan, 3 iteration cap
+    GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
+    const Op<VT>& A = a.plan.A;
+    const int n = A.n;
+    int s0, s1;
+    block_slices(A.n_slices, s0, s1);
+    const int row0 = 32 * s0, row1 = max(row0, min(32 * s1, n));
+    const int nr = row1 - row0;
+    const int lane = threadIdx.x & 31;
+    // ---- initial residual and the norm of b
+    double bbp = 0.0;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        DI[t] = a.dinv[row0 + t];
+        D[t] = S[t] = P[t] = 0.0;
+    }
+    if (a.r0 == nullptr) {      // mode 0: r = b - A x in FP64 (global gathers of x)
+        const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+        for (int sl = s0 + wib; sl < s1; sl += nwb) {
+            const long long base = A.sptr[sl];
+            const int w = (int)((A.sptr[sl + 1] - base) >> 5);
+            const int i = sl * 32 + lane;
+            const int ir = min(i, n - 1);
+            double acc = 0.0;
+#pragma unroll 4
+            for (int k = 0; k < w; ++k) {
+                const long long e = base + 32ll * k + lane;
+                acc = fma(__ldg(a.val_hi + e), a.x[A.col(e, ir)], acc);
+            }
+            if (i < n) {
+                const double bi = a.b[i];
+                R[i - row0] = bi - acc;
+                bbp += bi * bi;
+            }
+        }
+    } else {
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            R[t] = a.r0[row0 + t];
+            bbp += a.bsq[row0 + t];
+        }
+    }
+    __syncthreads();
+    // ---- optional proposed start: kept only if its residual is smaller
+    if (a.dx0) {
+        const double scx = *a.dx0_scale;
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            const double d = scx * (double)a.dx0[row0 + t];
+            D[t] = d;
+            a.ul[row0 + t] = (VT)d;
+        }
+        if (!sync.barrier()) return;
+        double vw[2] = {0.0, 0.0};
+        spmv_block(a.plan, a.ul, win, sq, [&](int i, VT t) {
+            const int l = i - row0;
+            const double rw = R[l] - (double)t;
+            W[l] = rw;
+            vw[0] += rw * rw;
+            vw[1] += R[l] * R[l];
+        });
+        block_sum<2>(vw, bl64);
+        if (!grid_exchange<2>(sync, bl64, 10, res)) return;
+        const bool warm = res[0] < res[1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.st->ws_used = warm ? 1 : 0;
+            a.st->ws_ratio = res[1] > 0.0 ? sqrt(res[0] / res[1]) : 0.0;
+        }
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            if (warm) R[t] = W[t];
+            else D[t] = 0.0;
+        }
+        __syncthreads();
+    }
+    // ---- the norm of b -> sigma; u = D^{-1} r published
+    double bb;
+    {
+        double v1[1] = {bbp};
+        block_sum<1>(v1, bl64);
+        if (!grid_exchange<1>(sync, bl64, 0, res)) return;
+        bb = res[0];
+        if (threadIdx.x == 0) sc[2] = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
+        __syncthreads();
+    }
+    const AT sig = (AT)sc[2];
+    const AT* DL = (const AT*)a.dinvl;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        const double u = DI[t] * R[t];
+        const AT r32 = (AT)R[t] * sig;
+        U[t] = u;
+        R32[t] = r32;
+        U32[t] = DL[row0 + t] * r32;
+        a.ul[row0 + t] = (VT)u;
+    }
+    // stop when (sigma r, sigma r) <= tol^2 (sigma^2 ||b||^2 = 1)
+    const double stop2 = bb > 0.0 ? a.tol * a.tol : 0.0;
+    int it = 0;
+    if (!sync.barrier()) return;
+    for (;;) {
+        // ---- S: w = A u and the three (scaled) dot products
+        AT v[3] = {(AT)0, (AT)0, (AT)0};
+        spmv_block(a.plan, a.ul, win, sq, [&](int i, VT wt) {
+            const int l = i - row0;
+            W[l] = (double)wt;
+            const AT ws = (AT)wt * sig;
+            v[0] += R32[l] * U32[l];
+            v[1] += ws * U32[l];
+            v[2] += R32[l] * R32[l];
+        });
+        block_sum<3>(v, blt);
+        // two slot sets: the next iteration's partials may be written while a
+        // slower block still reads these
+        if (!grid_exchange<3>(sync, blt, 1 + 3 * (it & 1), res)) return;
+        // scalars and the stopping decision once per block
+        if (threadIdx.x == 0) {
+            const double rr = res[2];
+            const AT gamma = (AT)res[0], delta = (AT)res[1];
+            int stt = 0;
+            if (!(rr == rr) || !(gamma == gamma) || !(delta == delta)) stt = 2;
+            else if (rr <= stop2) stt = 1;
+            else if (it >= a.max_iter) stt = 3;
+            if (stt == 0) {
+                AT be = (AT)0, al = gamma / delta;
+                if (it > 0) {
+                    be = gamma / scl[1];
+                    al = gamma / (delta - be * gamma / scl[0]);
+                }
+                if (!(al == al)) stt = 2;
+                scl[0] = al;
+                scl[1] = gamma;
+                sc[0] = (double)al;
+                sc[1] = (double)be;
+            }
+            sc[3] = rr;
+            state = stt;
+        }
+        __syncthreads();
+        if (state != 0) break;
+        const double al = sc[0], be = sc[1];
+        // ---- V: own rows only
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            const double p = fma(be, P[t], U[t]);
+            const double s = fma(be, S[t], W[t]);
+            P[t] = p;
+            S[t] = s;
+            D[t] = fma(al, p, D[t]);
+            const double r = fma(-al, s, R[t]);
+            const double u = DI[t] * r;
+            const AT r32 = (AT)r * sig;
+            R[t] = r;
+            U[t] = u;
+            R32[t] = r32;
+            U32[t] = DL[row0 + t] * r32;
+            a.ul[row0 + t] = (VT)u;
+        }
+        ++it;
+        if (!sync.barrier()) return;
+    }
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) a.x[row0 + t] += D[t];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double rel = sqrt(sc[3]);      // (sigma r, sigma r) = ||r||^2 / ||b||^2
+        int* err = &a.st->err;
+        if (a.which == 0) {
+            a.st->pcg_iters = it;
+            a.st->rel_res = rel;
+            if (state != 1) atomicOr(err, SA_DEV_NOT_CONVERGED);
+        } else {
+            a.st->bot_iters = it;
+            a.st->bot_rel_res = rel;
+            if (state != 1) atomicOr(err, SA_DEV_BOT_NOT_CONVERGED);
+        }
+        if (state == 2) atomicOr(err, SA_DEV_NAN);
+    }
+}
+
+// Extrapolated initial guesses (x0 = x^n + (x^n - x^{n-1})):
+// free part: the previous increment as the proposed dx0, and x^{n-1} <- x^n;
+// Dirichlet part: g0 = 2 g^n - g^{n-1}, and g^{n-1} <- g^n.
+__global__ void k_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
+                         double* gprev, double* g0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_free) {
+        const double t = That[i];
+        dx0[i] = (float)(t - Tprev[i]);
+        Tprev[i] = t;
+    } else if (i < n_free + n_dir) {
+        const int d = i - n_free;
+        const double g = That[i];
+        g0[d] = 2.0 * g - gprev[d];
+        gprev[d] = g;
+    }
+}
+
 __global__ void k_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,
                            const double* F1, double* F0, DevStatus* st) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -588,12 +963,81 @@ Op<VT> make_op(const SellView& s, const void* val) {
     o.sptr = s.sptr;
     o.col32 = s.col32;
     o.col16 = s.col16;
+    o.hi = s.hi;
     o.val = (const VT*)val;
     return o;
 }
 
+// Launch shape shared by both variants: slices per block -> warps per slice
+// (so the 32 warps of a block are busy), window length, shared memory.
+template <typename VT>
+struct PcgShape {
+    int G, spb, ks, rcap;
+    long long wl;
+    bool window;
+    size_t smem;
+    bool fits;             // (shared-memory variant) vectors + k-split scratch fit
+};
+
+constexpr size_t kSmemCap = 200 * 1024;
+
+template <typename VT>
+PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
+    PcgShape<VT> sh;
+    sh.G = L.grid > 0 ? L.grid : 1;
+    sh.spb = (L.op.n_slices + sh.G - 1) / sh.G;
+    int ks = 1;
+    while (ks < 8 && sh.spb * ks * 2 <= 32) ks *= 2;
+    sh.ks = L.ksplit > 0 ? L.ksplit : ks;
+    sh.rcap = 32 * std::max(sh.spb, 1);
+    // window: 32 spb rows plus the halo, 4-entry alignment slack
+    sh.wl = 32ll * sh.spb + (L.op.dmax - L.op.dmin) + 8;
+    const size_t fixed = 1024 * sizeof(VT) + (pipelined ? (size_t)kSmemVecs * sh.rcap * sizeof(double) + 2 * sh.rcap * sizeof(VT) : 0);
+    sh.fits = fixed <= kSmemCap;
+    sh.window = L.op.col16 != nullptr && L.pad >= -L.op.dmin + 4 && L.pad >= L.op.dmax + 4 &&
+                fixed + sh.wl * sizeof(VT) <= kSmemCap;
+    sh.smem = fixed + (sh.window ? (size_t)sh.wl * sizeof(VT) : 0);
+    return sh;
+}
+
+cudaError_t launch_coop(const void* fn, int G, size_t smem, void* args, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* params[1] = {args};
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kPcgBlock), params, smem, s);
+}
+
 template <typename VT>
 cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
+    const bool want_pipe = L.variant != SA_PCG_GLOBAL;
+    if (want_pipe) {
+        const PcgShape<VT> sh = pcg_shape<VT>(L, true);
+        if (sh.fits) {
+            SmemArgs<VT> a;
+            a.plan = SpmvPlan<VT>{make_op<VT>(L.op, L.val), L.op.dmin, L.op.dmax, sh.window, sh.ks};
+            a.rcap = sh.rcap;
+            a.val_hi = L.val_hi;
+            a.dinv = L.dinv;
+            a.b = L.b;
+            a.r0 = L.r0;
+            a.bsq = L.bsq;
+            a.x = L.x;
+            a.ul = (VT*)L.vpad + L.pad;
+            a.part = L.partials;
+            a.st = L.st;
+            a.which = L.which;
+            a.tol = L.tol;
+            a.max_iter = L.max_iter;
+            a.dx0 = L.dx0;
+            a.dx0_scale = L.dx0_scale;
+            a.dinvl = L.dinvl;
+            cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
+            if (e != cudaSuccess) return e;
+            return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.smem, &a, s);
+        }
+        if (L.variant == SA_PCG_SHARED) return cudaErrorInvalidConfiguration;
+    }
+    const PcgShape<VT> sh = pcg_shape<VT>(L, false);
     PcgArgs<VT> a;
     a.A = make_op<VT>(L.op, L.val);
     a.dmin = L.op.dmin;
@@ -617,35 +1061,12 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     a.max_iter = L.max_iter;
     a.dx0 = L.dx0;
     a.dx0_scale = L.dx0_scale;
-    const int G = L.grid > 0 ? L.grid : 1;
-    // slices per block -> warps per slice so the 32 warps of a block are busy
-    const int spb = (L.op.n_slices + G - 1) / G;
-    int ks = 1;
-    while (ks < 8 && spb * ks * 2 <= 32) ks *= 2;
-    a.ksplit = L.ksplit > 0 ? L.ksplit : ks;
-    // window: 32 spb rows plus the halo, 4-entry alignment slack
-    const long long wl = 32ll * spb + (L.op.dmax - L.op.dmin) + 8;
-    const size_t smem_fixed = 1024 * sizeof(VT);
-    a.window = L.op.col16 != nullptr && L.pad >= -L.op.dmin + 4 && L.pad >= L.op.dmax + 4 &&
-               smem_fixed + wl * sizeof(VT) <= 200 * 1024;
-    a.wcap = a.window ? (int)wl : 0;
-    const size_t smem = smem_fixed + (size_t)a.wcap * sizeof(VT);
-    cudaError_t e = cudaFuncSetAttribute(k_pcg<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    a.ksplit = sh.ks;
+    a.window = sh.window;
+    a.wcap = sh.window ? (int)sh.wl : 0;
+    cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(G);
-    cfg.blockDim = dim3(kPcgBlock);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pcg<VT>, a);
+    return launch_coop((const void*)k_pcg<VT>, sh.G, sh.smem, &a, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -731,16 +1152,23 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
-                             double* bsq, cudaStream_t s) {
+                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s) {
     if (op.n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)(((long long)op.n_slices * 32 + 255) / 256);
+    const unsigned pblocks = (unsigned)((n_dir + 255) / 256);
     if (precision == SA_MIXED) {
-        RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, That,
-                         gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
+        float* dg = (float*)dir_scratch;
+        float* g1 = dg + n_dir;
+        if (n_dir > 0) k_dir_prep<float><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
+        RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, dg, g1,
+                         F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
         k_theta_rhs<float><<<blocks, 256, 0, s>>>(a);
     } else {
-        RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev,
-                          That, gnew, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
+        double* dg = (double*)dir_scratch;
+        double* g1 = dg + n_dir;
+        if (n_dir > 0) k_dir_prep<double><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
+        RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev, dg,
+                          g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
         k_theta_rhs<double><<<blocks, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
@@ -754,6 +1182,18 @@ const void* pcg_kernel_ptr(int precision) {
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s) {
     if (L.op.n == 0) return cudaSuccess;
     return precision == SA_MIXED ? launch_pcg_t<float>(L, s) : launch_pcg_t<double>(L, s);
+}
+
+cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
+                          double* gprev, double* g0, cudaStream_t s) {
+    const int n = n_free + n_dir;
+    if (n == 0) return cudaSuccess;
+    k_extrap<<<(n + 255) / 256, 256, 0, s>>>(n_free, n_dir, That, Tprev, dx0, gprev, g0);
+    return cudaGetLastError();
+}
+
+bool pcg_shared_fits(int precision, const PcgLaunch& L) {
+    return precision == SA_MIXED ? pcg_shape<float>(L, true).fits : pcg_shape<double>(L, true).fits;
 }
 
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,

@@ -102,10 +102,14 @@ def _lockstep(sa, wl, precision, n_check, every=1, **opts):
     return err, ctx, m
 
 
+VARIANTS = {"shared": 1, "global": 2}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("theta", [1.0, 0.5])
-def test_cuboid_single_track_fp64(sa, theta):
+def test_cuboid_single_track_fp64(sa, theta, variant):
     wl = W.cuboid_single_track(theta=theta, n_steps=150)
-    err, ctx, m = _lockstep(sa, wl, sa.SA_FP64, 150, every=25)
+    err, ctx, m = _lockstep(sa, wl, sa.SA_FP64, 150, every=25, pcg_variant=VARIANTS[variant])
     assert err["s_lat"] <= 1e-12 and err["tt_bot"] <= 1e-12, err
     assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
     # reconstruction T = T~ + T^ at interior and boundary points
@@ -117,12 +121,37 @@ def test_cuboid_single_track_fp64(sa, theta):
     assert rel_linf(T, T_ref) <= TOL_FP64
 
 
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("theta", [1.0, 0.5])
-def test_cuboid_single_track_mixed(sa, theta):
+def test_cuboid_single_track_mixed(sa, theta, variant):
     wl = W.cuboid_single_track(theta=theta, n_steps=150)
-    err, ctx, m = _lockstep(sa, wl, sa.SA_MIXED, 150, every=15)
+    err, ctx, m = _lockstep(sa, wl, sa.SA_MIXED, 150, every=15, pcg_variant=VARIANTS[variant])
     assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
     assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_extrapolated_guess(sa, prec):
+    """x0 = T^n + (T^n - T^{n-1}) (and 2 g^n - g^{n-1} for the projection):
+    the same steps as the oracle to the parity tolerance, in fewer PCG
+    iterations than the start from T^n."""
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    wl = W.cuboid_single_track(theta=0.5, n_steps=150)
+    err, ctx, m = _lockstep(sa, wl, p, 150, every=25, initial_guess=sa.SA_GUESS_EXTRAPOLATE)
+    if p == sa.SA_FP64:
+        assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+    else:
+        assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+    tol = 1e-15 if p == sa.SA_FP64 else 1e-10
+    iters = {}
+    for g in (sa.SA_GUESS_PREVIOUS, sa.SA_GUESS_EXTRAPOLATE):
+        c = gpu_context(wl, p, pcg_tol=tol, initial_guess=g)
+        c.step(wl.theta, wl.dt, 20)
+        c.step(wl.theta, wl.dt, 0)
+        st = c.step(wl.theta, wl.dt, 100)
+        iters[g] = (st.pcg_iters_total, st.bot_iters_total)
+    assert iters[sa.SA_GUESS_EXTRAPOLATE][0] < iters[sa.SA_GUESS_PREVIOUS][0], iters
+    assert iters[sa.SA_GUESS_EXTRAPOLATE][1] <= iters[sa.SA_GUESS_PREVIOUS][1], iters
 
 
 @pytest.mark.parametrize("P,NW", [(1, 4), (2, 8), (4, 8), (4, 4)])
@@ -134,8 +163,9 @@ def test_multichunk_ragged_tiles(sa, P, NW):
     scan = W.meander(0.2e-3, 1.2e-3, 0.25e-3, 0.15e-3, 4, z, 180.0, 0.4, 1.5)
     wl = W.Workload("mc", patch, W.MAT_DEFAULT, scan, dt=4e-6, theta=0.5, n_steps=420)
     for prec in (sa.SA_FP64, sa.SA_MIXED):
+        # both PCG variants over the tile shapes
         err, ctx, m = _lockstep(sa, wl, prec, 420, every=70, hist_points_per_lane=P,
-                                hist_warps=NW)
+                                hist_warps=NW, pcg_variant=1 + (P + NW + prec) % 2)
         if prec == sa.SA_FP64:
             assert err["s_lat"] <= 1e-12 and err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
         else:
