@@ -46,7 +46,7 @@ def _compile(src, verbose_ptxas=False):
 def build(verbose_ptxas=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "sa_internal.h"),
+    deps = srcs + [os.path.join(CSRC, "sa_internal.h"), os.path.join(CSRC, "sa_async.cuh"),
                    os.path.join(HERE, "..", "include", "sa.h")]
     if not force and os.path.exists(LIB):
         t_lib = os.path.getmtime(LIB)

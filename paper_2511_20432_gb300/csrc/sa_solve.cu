@@ -13,9 +13,11 @@
 
 #include <type_traits>
 
+#include "sa_async.cuh"
 #include "sa_internal.h"
 
 namespace {
+using namespace sa_dev;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -209,11 +211,6 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
 // ---------------------------------------------------------------------------
 // synchronisation policies for the PCG body
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Deterministic block reduction of NV values per thread into out[] (visible
 // to every thread on return): fixed xor tree in the warps, fixed warp order.
@@ -369,15 +366,27 @@ struct SpmvPlan {
     int ksplit;            // warps per slice (divides the 32 warps of a block)
 };
 
+// Asynchronous window copy: an mbarrier in shared memory and the number of
+// copies issued so far (every thread of the block counts the same calls).
+struct WinAsync {
+    unsigned long long* mbar;
+    unsigned count;
+    int* err;
+};
+
 // y = A src on the block's slices.  Window mode: the entries of src the
 // block can touch, src[32 s0 + dmin .. 32 s1 + dmax), are first copied into
-// shared memory (coalesced L2 loads), so every gather is a shared-memory
-// read.  src is written by other blocks during the kernel, so it is read
-// through L2 (ld.global.cg), never from a stale L1 line.  Each slice is split
-// over KS consecutive warps (partial sums combined in fixed order).
-// own(i, y_i) runs once per row.
+// shared memory, so every gather is a shared-memory read.  With wa, one
+// thread issues that copy as one bulk asynchronous copy (TMA engine) and the
+// warps load their first batch of matrix entries before waiting for it;
+// otherwise the threads copy it (coalesced loads).  src is written by other
+// blocks during the kernel, so it is read through L2 (ld.global.cg, or the
+// bulk copy), never from a stale L1 line.  Each slice is split over KS
+// consecutive warps (partial sums combined in fixed order).  own(i, y_i)
+// runs once per row.
 template <typename VT, class Own>
-__device__ void spmv_block(const SpmvPlan<VT>& a, const VT* src, VT* win, VT* sq, Own own) {
+__device__ void spmv_block(const SpmvPlan<VT>& a, const VT* src, VT* win, VT* sq, Own own,
+                           WinAsync* wa = nullptr) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int nwb = blockDim.x >> 5;
@@ -385,25 +394,39 @@ __device__ void spmv_block(const SpmvPlan<VT>& a, const VT* src, VT* win, VT* sq
     int s0, s1;
     block_slices(a.A.n_slices, s0, s1);
     long long wlo = 0;
+    bool pending = false;       // window copy issued, not yet waited for
+    unsigned parity = 0;
     if (a.window) {
         wlo = ((long long)32 * s0 + a.dmin) & ~3ll;               // aligned start
         const long long whi = (long long)32 * s1 + a.dmax + 1;
         const int len = (int)(whi - wlo);
-        // 8 independent loads in flight per thread, then the stores
-        for (int t0 = threadIdx.x; t0 < len; t0 += 8 * blockDim.x) {
-            VT tmp[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int t = t0 + u * blockDim.x;
-                tmp[u] = t < len ? __ldcg(src + wlo + t) : (VT)0;
+        if (wa != nullptr) {
+            // 16-byte multiple (the padding of src covers the rounding)
+            const unsigned bytes = (unsigned)((len * sizeof(VT) + 15) & ~(size_t)15);
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                bulk_load(win, src + wlo, bytes, wa->mbar);
             }
+            parity = wa->count & 1u;
+            wa->count += 1;
+            pending = true;
+        } else {
+            // 8 independent loads in flight per thread, then the stores
+            for (int t0 = threadIdx.x; t0 < len; t0 += 8 * blockDim.x) {
+                VT tmp[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int t = t0 + u * blockDim.x;
-                if (t < len) win[t] = tmp[u];
+                for (int u = 0; u < 8; ++u) {
+                    const int t = t0 + u * blockDim.x;
+                    tmp[u] = t < len ? __ldcg(src + wlo + t) : (VT)0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int t = t0 + u * blockDim.x;
+                    if (t < len) win[t] = tmp[u];
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
     const int KS = a.ksplit;
     const int units = (s1 - s0) * KS;
@@ -431,6 +454,10 @@ __device__ void spmv_block(const SpmvPlan<VT>& a, const VT* src, VT* win, VT* sq
                         dj[u] = ok ? __ldg(a.A.col16 + e) : (short)0;
                         vv[u] = ok ? __ldg(a.A.val + e) : (VT)0;
                     }
+                    if (pending) {
+                        if (!mbar_wait_bounded(wa->mbar, parity)) atomicOr(wa->err, SA_DEV_TIMEOUT);
+                        pending = false;
+                    }
 #pragma unroll
                     for (int u = 0; u < 16; ++u) acc = fma(vv[u], wv[ir + (int)dj[u]], acc);
                 }
@@ -454,6 +481,9 @@ __device__ void spmv_block(const SpmvPlan<VT>& a, const VT* src, VT* win, VT* sq
         }
         if (KS > 1) __syncthreads();
     }
+    // a thread without matrix work still observes the copy's completion, so
+    // that no copy is in flight into the window when the block reuses it
+    if (pending && !mbar_wait_bounded(wa->mbar, parity)) atomicOr(wa->err, SA_DEV_TIMEOUT);
 }
 
 template <typename VT>
@@ -708,21 +738,29 @@ __device__ void block_sum(AT (&v)[NV], AT* out) {
 // Block values bl[0..NV) -> partial slots (AT), grid barrier, the sum over
 // all blocks in AT in a fixed order (identical in every block) -> res[k]
 // (FP64, shared, all threads).
+constexpr int kMaxGrid = 256;
+
 template <int NV, typename AT>
 __device__ bool grid_exchange(const GridSync& g, const AT* bl, int slot, double* res) {
+    __shared__ AT gv[NV * kMaxGrid];
     const int G = gridDim.x;
     AT* part = (AT*)g.part;
     if (threadIdx.x < NV) part[(slot + threadIdx.x) * G + blockIdx.x] = bl[threadIdx.x];
     if (!g.barrier()) return false;
-    if (threadIdx.x < 32) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const AT* pk = part + (slot + k) * G;
-            AT t = (AT)0;
-            for (int i = threadIdx.x; i < G; i += 32) t += __ldcg(pk + i);
-            t = warp_sum_t(t);
-            if (threadIdx.x == 0) res[k] = (double)t;
-        }
+    // the NV rows of partials are contiguous: one load per thread, all in
+    // flight together, then fixed-order sums from shared memory
+    const AT* src = part + slot * G;
+    const bool staged = G <= kMaxGrid;
+    if (staged) {
+        for (int t = threadIdx.x; t < NV * G; t += blockDim.x) gv[t] = __ldcg(src + t);
+        __syncthreads();
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < NV) {
+        AT t = (AT)0;
+        for (int i = lane; i < G; i += 32) t += staged ? gv[w * G + i] : __ldcg(src + w * G + i);
+        t = warp_sum_t(t);
+        if (lane == 0) res[w] = (double)t;
     }
     __syncthreads();
     return true;
@@ -753,7 +791,14 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     __shared__ double sc[4];                // alpha, beta (applied), sigma
     __shared__ AT scl[4];                   // alpha, gamma (previous) in AT
     __shared__ int state;                   // 0 run, 1 converged, 2 nan, 3 iteration cap
+    __shared__ unsigned long long wmbar;    // window copy completion
     GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
+    if (threadIdx.x == 0) {
+        mbar_init(&wmbar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    WinAsync wa{&wmbar, 0u, &a.st->err};
     const Op<VT>& A = a.plan.A;
     const int n = A.n;
     int s0, s1;
@@ -809,7 +854,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             W[l] = rw;
             vw[0] += rw * rw;
             vw[1] += R[l] * R[l];
-        });
+        }, &wa);
         block_sum<2>(vw, bl64);
         if (!grid_exchange<2>(sync, bl64, 10, res)) return;
         const bool warm = res[0] < res[1];
@@ -857,7 +902,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             v[0] += R32[l] * U32[l];
             v[1] += ws * U32[l];
             v[2] += R32[l] * R32[l];
-        });
+        }, &wa);
         block_sum<3>(v, blt);
         // two slot sets: the next iteration's partials may be written while a
         // slower block still reads these
