@@ -12,8 +12,10 @@ grows by one per step).
 A "step" is one theta-step of the whole hot path: source coefficients,
 history sums at every boundary quadrature point, boundary integrals, bottom
 projection, theta right-hand side, PCG.  ``value`` is theta-steps/s of the
-mixed path (FP32 history sum, FP64 elsewhere) replayed as CUDA graphs with
-the inputs resident in HBM; the plain FP64 path is timed beside it.
+mixed path (FP32 history sum and operator values; FP64 state, boundary
+integrals and Krylov vectors) with extrapolated initial guesses, replayed as
+CUDA graphs with the inputs resident in HBM.  Timed beside it: the same path
+started from T^n, and the plain FP64 path.
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
 bounded sample of the same step.
@@ -39,15 +41,24 @@ START_STEP = 5840
 N_MONITOR = 64
 
 
+def start_step(args):
+    if args.start_step is not None:
+        return args.start_step
+    return max(0, START_STEP - args.steps // 2 - args.warmup)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--start-step", type=int, default=START_STEP)
+    ap.add_argument("--start-step", type=int, default=None,
+                    help="first timed step; default: the timed steps are centred on step 5,840")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="path timed in the main region")
+    ap.add_argument("--guess", default="extrapolate", choices=["extrapolate", "previous"],
+                    help="initial guess of the theta-step solves in the main region")
     ap.add_argument("--quick", action="store_true",
                     help="main timed region only (no stage, FP64, e2e or CPU legs): "
                          "the form used under ncu")
@@ -71,7 +82,7 @@ def clocks_start(dev):
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
     try:
         p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
-                              "-lms", "200", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
+                              "-lms", "100", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
     except OSError:
         p = None
     return p, f.name
@@ -108,6 +119,21 @@ def clocks_stop(h):
             "samples": len(sm)}
 
 
+def profile_traffic(name, src):
+    """DRAM bytes per launch from the committed ncu summary profiles/<name>.md,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
+        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2511_20432_gb300", "csrc", src), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("source_sha256:", "dram_bytes_per_launch:")))
+    if vals.get("source_sha256", "").strip() != sha:
+        return None
+    return float(vals["dram_bytes_per_launch"])
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -130,7 +156,7 @@ def run_reference(args):
     geom = PatchGeom(wl.patch)
     xs = sources.discretize(wl.scan, wl.dt)
     E = sources.energy(wl.scan, wl.dt)
-    n = args.start_step
+    n = START_STEP
     age = pointsource.ages(n, n, wl.dt, wl.material, wl.scan.spot_radius)
     rng = np.random.default_rng(0)
     lat = geom.face_points(0)
@@ -205,6 +231,18 @@ def cpu_baseline_block(wl, n, seconds_target=10.0):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def time_graph(ctx, th, dt, K, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(th, dt, K, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -221,8 +259,10 @@ def run_ours(args):
     th, dt = wl.theta, wl.dt
     stream = torch.cuda.Stream()
     prec = sa.SA_MIXED if args.precision == "mixed" else sa.SA_FP64
-    ctx = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1)
-    n0 = args.start_step
+    guess = sa.SA_GUESS_EXTRAPOLATE if args.guess == "extrapolate" else sa.SA_GUESS_PREVIOUS
+    ctx = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1,
+                                   initial_guess=guess)
+    n0 = start_step(args)
     ctx.step(th, dt, n0)                       # untimed fast-forward to mid-scan
     ctx.step(th, dt, args.warmup)              # warm-up (graph instantiated, caches warm)
     sz = ctx.sizes()
@@ -232,19 +272,13 @@ def run_ours(args):
     n_first = n0 + args.warmup + 1
     pairs = q_pts * sum(min(n_first + i, sz.n_src) for i in range(K))
 
-    # ---- timed region: K graph replays of the mixed path ------------------
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # ---- timed region: K graph replays ---------------------------------------
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks_start(local)
-    e0.record(stream)
-    ctx.step(th, dt, K, stats=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = time_graph(ctx, th, dt, K, stream)
     clocks = clocks_stop(clk)
-    ms = e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -258,19 +292,23 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
-                              "precision": args.precision, "start_step": n0,
+                              "precision": args.precision, "guess": args.guess, "start_step": n0,
                               "point_source_evals_per_s": evals, "pcg_iters_per_step": iters_avg,
                               "bot_iters_per_step": bot_avg, "clocks": clocks}))
         if dist:
             dist.destroy_process_group()
         return
 
-    # ---- stage breakdown (CUDA events on the launching stream) --------------
+    def fresh(precision, g, **kw):
+        c = sa.context_from_workload(wl, precision=precision, cuda_stream=stream, initial_guess=g, **kw)
+        c.step(th, dt, 0)
+        c.set_state(*state)
+        return c
+
+    # ---- stage breakdown (CUDA events on the launching stream, direct launches)
     K_t = min(K, 40)
-    ctx_t = sa.context_from_workload(wl, precision=sa.SA_MIXED, cuda_stream=stream, stage_timing=1)
-    ctx_t.step(th, dt, 0)
-    ctx_t.set_state(*state)
-    ctx_t.step(th, dt, 2)
+    ctx_t = fresh(prec, guess, stage_timing=1)
+    ctx_t.step(th, dt, 3)
     ctx_t.stage_times()
     st_t = ctx_t.step(th, dt, K_t)
     stage_ms, k_timed = ctx_t.stage_times()
@@ -279,18 +317,19 @@ def run_ours(args):
     pairs_t = q_pts * (min(state[0] + 3 + K_t // 2, sz.n_src))
     ctx_t.close()
 
-    # ---- plain FP64 path at the same point of the scan ------------------------
+    # ---- same path from x0 = T^n (no extrapolation), and the plain FP64 path
+    K_c = min(K, 60)
+    ctx_c = fresh(prec, sa.SA_GUESS_PREVIOUS, use_graph=1)
+    ctx_c.step(th, dt, 3)
+    ctx_c.step(th, dt, 0)
+    ms_c = time_graph(ctx_c, th, dt, K_c, stream)
+    st_c = ctx_c.step(th, dt, 0)
+    cold_steps = K_c / (ms_c / 1e3)
+    ctx_c.close()
     K64 = min(K, 12)
-    ctx64 = sa.context_from_workload(wl, precision=sa.SA_FP64, cuda_stream=stream, use_graph=1)
-    ctx64.step(th, dt, 0)
-    ctx64.set_state(*state)
+    ctx64 = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1)
     ctx64.step(th, dt, 2)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    ctx64.step(th, dt, K64, stats=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1)
+    ms64 = time_graph(ctx64, th, dt, K64, stream)
     fp64_steps = K64 / (ms64 / 1e3)
     ctx64.close()
 
@@ -309,35 +348,48 @@ def run_ours(args):
     e2e = world * K_e / t_e2e
     assert np.isfinite(T_mon).all()
 
-    # ---- roofline of the dominant stage ---------------------------------------------
+    # ---- roofline of the dominant kernel ------------------------------------------
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     total = sum(stage_avg.values())
     shares = {k: v / total for k, v in stage_avg.items()}
-    dom = max(stage_avg, key=stage_avg.get)
     n_free, nnz_a = sz.n_free, sz.nnz_a
-    pcg_bytes = iters_t * (12 * nnz_a + 100 * n_free) + 40 * n_free
+    warm = 1 if guess == sa.SA_GUESS_EXTRAPOLATE else 0
+    # algorithmic bytes of one main-solve launch: every SpMV reads the FP32
+    # values and 16-bit column offsets once and the published vector once;
+    # set-up reads r0, b^2, D^{-1} (FP64 and FP32), reads and writes x
+    pcg_bytes = (iters_t + warm) * (6 * nnz_a + 4 * n_free) + (44 + 4 * warm) * n_free
+    # history: FP32 lane-operations per pair (flux 8, T 6) on 128 FP32
+    # lanes/clk/SM; MUFU ex2 (32/clk/SM) is not binding
+    pairs_clk = 128.0 * q_pts / (8 * sz.q_lat + 6 * sz.q_bot)
     kernels = {
         "pcg": {"bound": "hbm", "bytes_per_launch": pcg_bytes, "ms": stage_avg["pcg"],
                 "achieved_gbs": pcg_bytes / (stage_avg["pcg"] * 1e-3) / 1e9,
-                "iters_per_step": iters_t},
+                "iters_per_step": iters_t, "warm_start_spmv": warm},
         "history": {"bound": "alu", "pairs_per_launch": pairs_t, "ms": stage_avg["history"],
                     "achieved_gpairs": pairs_t / (stage_avg["history"] * 1e-3) / 1e9,
-                    "peak_gpairs": n_sm * sm_max * 1e6 * 16 / 1e9},
+                    "peak_gpairs": n_sm * sm_max * 1e6 * pairs_clk / 1e9},
     }
+    dom = "history" if stage_avg["history"] >= stage_avg["pcg"] else "pcg"
     if dom == "history":
         k = kernels["history"]
         roof = {"bound": "alu", "achieved": k["achieved_gpairs"], "peak": k["peak_gpairs"],
                 "unit": "Gpairs/s", "frac": k["achieved_gpairs"] / k["peak_gpairs"],
-                "traffic": None, "kernel": "k_history_mixed",
-                "peak_basis": f"{n_sm} SMs x {sm_max:.0f} MHz x 16 pairs/clk/SM (MUFU ex2 16/clk)"}
+                "traffic": profile_traffic("k_history_mixed_block_meander", "sa_history.cu"),
+                "kernel": "k_history_mixed",
+                "peak_basis": f"{n_sm} SMs x {sm_max:.0f} MHz x {pairs_clk:.1f} pairs/clk/SM "
+                              "(FP32 pipe: 128 lanes/clk, 8 ops a flux pair, 6 a T pair)"}
     else:
         k = kernels["pcg"]
         roof = {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": k["achieved_gbs"] / hbm if hbm else None, "traffic": None,
-                "kernel": "k_pcg (free block)", "peak_basis": "hbm_gbs of measured"}
+                "frac": k["achieved_gbs"] / hbm if hbm else None,
+                "traffic": profile_traffic("k_pcg_smem_block_meander", "sa_solve.cu"),
+                "kernel": "k_pcg_smem (free block)", "peak_basis": "hbm_gbs of measured",
+                "note": "algorithmic bytes count every SpMV's pass over the operator; later "
+                        "passes of a launch hit L2 (traffic: one ncu-captured launch)"}
+    launches_per_step = 8 + warm
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
@@ -345,10 +397,15 @@ def run_ours(args):
         "config": {"workload": wl.name + f" mid-scan from step {n0}", "n_dof": sz.n_dof,
                    "q_lat": sz.q_lat, "q_bot": sz.q_bot, "nnz_a": nnz_a,
                    "active_sources_first": n_first, "theta": th, "dt": dt,
-                   "precision": "mixed: FP32 history sum, FP64 boundary integrals and PCG",
-                   "l2": "per-step inputs larger than L2 (M, K and A in CSR, ~370 MB)",
+                   "precision": "mixed: FP32 history sum and operator values, FP64 state, "
+                                "boundary integrals and Krylov vectors",
+                   "initial_guess": args.guess,
+                   "l2": "no flush: per-step inputs larger than L2 (operators in SELL-32: "
+                         "~170 MB of FP32 values and indices; 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "point_source_evals_per_s": evals,
+        "steps_per_s_guess_previous": world * cold_steps,
+        "pcg_iters_per_step_guess_previous": st_c.pcg_iters_total / K_c,
         "fp64_steps_per_s": world * fp64_steps,
         "mixed_over_fp64": value / (world * fp64_steps),
         "pcg_iters_per_step": iters_avg, "bot_iters_per_step": bot_avg,
@@ -356,7 +413,7 @@ def run_ours(args):
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
                 "d2h_bytes_per_step": N_MONITOR * 8 + 96},
-        "gpu_launches": 7 * K,
+        "gpu_launches": launches_per_step * K,
         "clocks": clocks,
     }
     if rank == 0 and world == 1:
