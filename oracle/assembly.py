@@ -62,17 +62,18 @@ def assemble_MK(geom: PatchGeom, rho_cp, k, elements=None):
 
 
 def elements_touching_dof(geom: PatchGeom, dof):
-    """Elements on which basis function ``dof`` can be non-zero."""
-    n0, n1, _ = geom.n
-    idx = (dof % n0, (dof // n0) % n1, dof // (n0 * n1))
-    lists = []
-    for d in range(3):
-        lists.append([e for e in geom.elems[d] if e[2] - geom.p[d] <= idx[d] <= e[2]])
+    """Elements on which the basis function(s) of control variable ``dof``
+    can be non-zero."""
     out = []
-    for e2 in lists[2]:
-        for e1 in lists[1]:
-            for e0 in lists[0]:
-                out.append((e0, e1, e2))
+    for idx in geom.ctrl_points_of(dof):
+        lists = []
+        for d in range(3):
+            lists.append([e for e in geom.elems[d] if e[2] - geom.p[d] <= idx[d] <= e[2]])
+        for e2 in lists[2]:
+            for e1 in lists[1]:
+                for e0 in lists[0]:
+                    if (e0, e1, e2) not in out:
+                        out.append((e0, e1, e2))
     return out
 
 

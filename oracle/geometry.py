@@ -6,6 +6,12 @@ dV = det(J) dxi.  Faces: dS = |x_u x x_v| du dv with the outward unit normal.
 
 Quadrature (reading R4): (p_d + 1) Gauss-Legendre points per direction on
 every non-empty knot span, and on every face element.
+
+Closed patches (a seam in direction d: the control layers i_d = 0 and
+i_d = n_d - 1 coincide): the two layers are one set of control variables,
+so the discrete space is the span of the merged basis functions R_0 + R_{n-1}
+and every assembled quantity is P^T (.) P with P the 0/1 map from control
+points to control variables.
 """
 from __future__ import annotations
 
@@ -27,6 +33,19 @@ class PatchGeom:
         w = patch.weights
         self.w = np.ones((n2, n1, n0)) if w is None else np.asarray(w, dtype=np.float64)
         self.faces = tuple(patch.faces)
+        self.seam = int(getattr(patch, "seam", -1))
+        nd = list(self.n)
+        if self.seam >= 0:
+            d = self.seam
+            sl0 = [slice(None)] * 3
+            sl1 = [slice(None)] * 3
+            sl0[2 - d] = 0
+            sl1[2 - d] = self.n[d] - 1
+            assert np.allclose(self.ctrl[tuple(sl0)], self.ctrl[tuple(sl1)], rtol=0, atol=1e-15)
+            assert np.allclose(self.w[tuple(sl0)], self.w[tuple(sl1)], rtol=0, atol=1e-15)
+            assert self.faces[2 * d] == 0 and self.faces[2 * d + 1] == 0, "seam faces carry no boundary term"
+            nd[d] -= 1
+        self.nd = tuple(nd)                       # shape of the control-variable grid
         for d in range(3):
             assert bspline.n_basis(self.U[d], self.p[d]) == self.n[d]
         self.elems = [bspline.elements(self.U[d]) for d in range(3)]
@@ -34,12 +53,28 @@ class PatchGeom:
 
     # ---- indexing -------------------------------------------------------
     def dof(self, i, j, k):
-        n0, n1, _ = self.n
-        return (k * n1 + j) * n0 + i
+        """Control variable of control point (i, j, k): natural order over the
+        control-variable grid (the seam layer n_d - 1 is layer 0)."""
+        idx = [np.asarray(i), np.asarray(j), np.asarray(k)]
+        if self.seam >= 0:
+            idx[self.seam] = idx[self.seam] % self.nd[self.seam]
+        n0, n1, _ = self.nd
+        return (idx[2] * n1 + idx[1]) * n0 + idx[0]
+
+    def ctrl_points_of(self, dof):
+        """Control-point index triples (i, j, k) of one control variable."""
+        n0, n1, _ = self.nd
+        base = [dof % n0, (dof // n0) % n1, dof // (n0 * n1)]
+        out = [tuple(base)]
+        if self.seam >= 0 and base[self.seam] == 0:
+            other = list(base)
+            other[self.seam] = self.n[self.seam] - 1
+            out.append(tuple(other))
+        return out
 
     @property
     def n_dof(self):
-        return self.n[0] * self.n[1] * self.n[2]
+        return self.nd[0] * self.nd[1] * self.nd[2]
 
     # ---- evaluation at one parametric point -----------------------------
     def local_eval(self, xi, spans=None):
@@ -181,9 +216,9 @@ class PatchGeom:
             Nd = bspline.basis_all(self.U[d], self.p[d], fixed)
             layers = np.nonzero(Nd != 0.0)[0]
             n0, n1, n2 = self.n
-            idx = np.arange(self.n_dof).reshape(n2, n1, n0)
+            K, J, I = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+            idx = [I, J, K]
             for L in layers:
-                sl = [slice(None)] * 3
-                sl[2 - d] = L
-                mask[idx[tuple(sl)].ravel()] = True
+                sel = idx[d] == L
+                mask[self.dof(I[sel], J[sel], K[sel])] = True
         return mask

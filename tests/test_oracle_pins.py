@@ -8,6 +8,7 @@ conservation identities, convergence rates, values printed in the paper).
 import os
 
 import numpy as np
+import scipy.sparse.linalg as spla
 import pytest
 import scipy.integrate as si
 import scipy.sparse as sp
@@ -552,3 +553,91 @@ def test_mlp_oracle_gradients_by_finite_differences():
                 lm, _ = mlp.loss_and_grads(params, X, Y)
                 flat[k] = old
                 assert abs((lp - lm) / (2 * h) - gf[k]) < 1e-7 * max(1.0, abs(gf[k]))
+
+
+# ---------------------------------------------------------------------------
+# P12: the closed (seam) patch of the plate with a hole.
+# ---------------------------------------------------------------------------
+def _coarse_plate():
+    return W.plate_with_hole_patch(n_el=(8, 4, 2))
+
+
+def test_P12_plate_faces_lie_on_the_circle_and_the_square():
+    """The hole face is the exact circle of radius R (rational quadratic
+    arcs, elevated and refined exactly) and the outer face the square."""
+    g = PatchGeom(_coarse_plate())
+    hole = g.face_points(3)
+    outer = g.face_points(2)
+    r = np.hypot(hole["x"][:, 0], hole["x"][:, 1])
+    np.testing.assert_allclose(r, 0.75e-3, rtol=1e-14, atol=0)
+    # outward normal of the plate on the hole face points towards the axis
+    radial = hole["x"][:, :2] / r[:, None]
+    np.testing.assert_allclose(np.einsum("qc,qc->q", hole["n"][:, :2], radial), -1.0, atol=1e-12)
+    m = np.max(np.abs(outer["x"][:, :2]), axis=1)
+    np.testing.assert_allclose(m, 1.5e-3, rtol=1e-14, atol=0)
+
+
+def test_P12_seam_merge_is_PtMP_of_the_open_patch():
+    """Assembling on the merged control variables equals P^T M P of the same
+    patch assembled with both seam layers kept (P: 0/1 control point ->
+    control variable)."""
+    plate = _coarse_plate()
+    g = PatchGeom(plate)
+    M, K = assembly.assemble_MK(g, 1.0, 1.0)
+    open_patch = W.Patch(plate.degree, plate.knots, plate.ctrl, plate.weights,
+                         faces=plate.faces, seam=-1)
+    go = PatchGeom(open_patch)
+    Mo, Ko = assembly.assemble_MK(go, 1.0, 1.0)
+    n0, n1, n2 = go.n
+    K3, J3, I3 = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    to = g.dof(I3.ravel(), J3.ravel(), K3.ravel())
+    P = np.zeros((go.n_dof, g.n_dof))
+    P[np.arange(go.n_dof), to] = 1.0
+    np.testing.assert_allclose(M.toarray(), P.T @ Mo.toarray() @ P, rtol=0,
+                               atol=1e-13 * abs(M).max())
+    np.testing.assert_allclose(K.toarray(), P.T @ Ko.toarray() @ P, rtol=0,
+                               atol=1e-13 * abs(K).max())
+    assert g.n_dof == go.n_dof - n1 * n2
+
+
+def test_P12_plate_volume_symmetry_and_constants():
+    g = PatchGeom(_coarse_plate())
+    M, K = assembly.assemble_MK(g, 1.0, 1.0)
+    assert abs(M - M.T).max() < 1e-14 * abs(M).max()
+    assert abs(K - K.T).max() < 1e-14 * abs(K).max()
+    assert np.abs(K @ np.ones(g.n_dof)).max() < 1e-12 * abs(K).max()
+    V = (4 * 1.5e-3 ** 2 - np.pi * 0.75e-3 ** 2) * 0.5e-3      # closed form
+    assert M.sum() == pytest.approx(V, rel=1e-7)
+
+
+def _plate_patch_test_error(n_el):
+    plate = W.plate_with_hole_patch(n_el=n_el)
+    plate.faces = (0, 0, 1, 1, 2, 1)
+    g = PatchGeom(plate)
+    M, K = assembly.assemble_MK(g, 1.0, MAT.k)
+    a, b = 300.0, np.array([2.0e4, -1.5e4, 3.0e4])
+    T_exact = np.empty(g.n_dof)
+    for dof in range(g.n_dof):
+        i, j, k = g.ctrl_points_of(dof)[0]
+        T_exact[dof] = a + plate.ctrl[k, j, i] @ b
+    pts = assembly.boundary_points(g, 1)
+    F = assembly.weight_matrix(g, pts) @ (MAT.k * pts["n"] @ b)
+    d = g.dirichlet_dofs()
+    f = ~d
+    rhs = F[f] - K[f][:, d] @ T_exact[d]
+    T_f = spla.spsolve(K[f][:, f].tocsc(), rhs)
+    return np.abs(T_f - T_exact[f]).max()
+
+
+def test_P12_patch_test_on_the_closed_plate():
+    """Linear field (45 K across the plate) with its flux on the hole, outer
+    and top faces and its values on the bottom: the space contains it
+    (isoparametric, merged seam), so the Galerkin solution reproduces it up
+    to the quadrature error of the rational map, which falls at the rate of
+    the (p+1)-point Gauss rule (h^8 for p = 3) when the angular and radial
+    spans are halved.  A wrong seam merge or flux sign leaves an O(1 K)
+    error that does not fall."""
+    e8 = _plate_patch_test_error((8, 4, 2))
+    e16 = _plate_patch_test_error((16, 8, 2))
+    assert e16 <= 1e-5, (e8, e16)
+    assert e8 / e16 >= 64.0, (e8, e16)

@@ -39,6 +39,8 @@ class Patch:
     ctrl: np.ndarray                 # (n2, n1, n0, 3) control points [m]
     weights: Optional[np.ndarray] = None   # (n2, n1, n0) or None (B-spline)
     faces: tuple = DEFAULT_FACES
+    seam: int = -1                   # parametric direction whose end layers coincide
+                                     # (closed patch: merged into one layer), or -1
 
     @property
     def n_ctrl(self):
@@ -47,8 +49,10 @@ class Patch:
 
     @property
     def n_dof(self):
-        n0, n1, n2 = self.n_ctrl
-        return n0 * n1 * n2
+        n = list(self.n_ctrl)
+        if self.seam >= 0:
+            n[self.seam] -= 1
+        return n[0] * n[1] * n[2]
 
 
 @dataclass
@@ -114,6 +118,97 @@ def cuboid_patch(size, n_el, degree=2, origin=(0.0, 0.0, 0.0),
 
 
 # --------------------------------------------------------------------------
+# the plate with a hole (closed ring in xi): curve construction on control
+# points only (Bezier degree elevation and Boehm knot insertion in
+# homogeneous coordinates), no evaluation of basis functions
+# --------------------------------------------------------------------------
+def _elevate_quadratic_segments(Pw):
+    """Rational quadratic Bezier segments (homogeneous points, consecutive
+    segments sharing end points) -> the same curve as cubic segments:
+    Q0 = P0, Q1 = (P0 + 2 P1)/3, Q2 = (2 P1 + P2)/3, Q3 = P2."""
+    n_seg = (len(Pw) - 1) // 2
+    out = [Pw[0]]
+    for s in range(n_seg):
+        P0, P1, P2 = Pw[2 * s], Pw[2 * s + 1], Pw[2 * s + 2]
+        out += [(P0 + 2 * P1) / 3.0, (2 * P1 + P2) / 3.0, P2]
+    return np.array(out)
+
+
+def _insert_knot(U, Pw, p, u):
+    """Boehm: insert u once into knot vector U of a degree-p curve with
+    homogeneous control points Pw; returns the new knots and points."""
+    k = int(np.searchsorted(U, u, side="right")) - 1       # U[k] <= u < U[k+1]
+    Q = np.empty((len(Pw) + 1, Pw.shape[1]))
+    for i in range(len(Q)):
+        if i <= k - p:
+            Q[i] = Pw[i]
+        elif i >= k + 1:
+            Q[i] = Pw[i - 1]
+        else:
+            a = (u - U[i]) / (U[i + p] - U[i])
+            Q[i] = a * Pw[i] + (1.0 - a) * Pw[i - 1]
+    return np.insert(U, k + 1, u), Q
+
+
+def plate_with_hole_patch(n_el=(48, 48, 8), radius=0.75e-3, half=1.5e-3,
+                          thickness=0.5e-3, degree=3) -> Patch:
+    """Square plate [-half, half]^2 x [0, thickness] with a centred round
+    hole, as ONE trivariate NURBS patch closed in xi (seam at angle -45 deg,
+    a C0 corner).  xi: angle, four C0 sections of 90 deg (rational quadratic
+    arcs with middle weight cos 45 deg, elevated to ``degree`` and refined to
+    n_el[0]/4 spans each); eta: from the outer square (eta = 0) to the hole
+    (eta = 1), straight lines between matching points of the square and of
+    the circle; zeta: through the thickness.  Faces: xi ends are the seam
+    (no boundary), eta = 0 and eta = 1 lateral (Neumann), zeta = 0 bottom
+    (Dirichlet), zeta = 1 top."""
+    assert degree == 3 and n_el[0] % 4 == 0
+    c45 = np.cos(np.pi / 4)
+    hole, square, wts = [], [], []
+    for s in range(4):
+        a0, am = np.pi / 2 * s - np.pi / 4, np.pi / 2 * s
+        d0, dm = np.array([np.cos(a0), np.sin(a0)]), np.array([np.cos(am), np.sin(am)])
+        hole += [radius * d0, radius / c45 * dm]
+        square += [half / c45 * d0, half * dm]
+        wts += [1.0, c45]
+    hole.append(hole[0])
+    square.append(square[0])
+    wts.append(1.0)
+    wts = np.array(wts)
+
+    def ring(points):
+        Pw = np.column_stack([np.array(points) * wts[:, None], wts])     # (9, 3)
+        Pw = _elevate_quadratic_segments(Pw)                              # (13, 3)
+        U = np.concatenate([[0.0] * 4, np.repeat([0.25, 0.5, 0.75], 3), [1.0] * 4])
+        m = n_el[0] // 4
+        for s in range(4):
+            for t in range(1, m):
+                U, Pw = _insert_knot(U, Pw, 3, (s + t / m) / 4.0)
+        return U, Pw
+
+    U0, Hw = ring(hole)
+    _, Sw = ring(square)
+    w0 = Hw[:, 2]
+    assert np.allclose(w0, Sw[:, 2])
+    H = Hw[:, :2] / w0[:, None]
+    S = Sw[:, :2] / w0[:, None]
+    U1 = open_uniform_knots(degree, n_el[1])
+    U2 = open_uniform_knots(degree, n_el[2])
+    t = greville(U1, degree)                     # eta: square (0) -> hole (1)
+    z = thickness * greville(U2, degree)
+    n0, n1, n2 = len(w0), len(t), len(z)
+    ctrl = np.empty((n2, n1, n0, 3))
+    for j in range(n1):
+        ctrl[:, j, :, 0] = (1.0 - t[j]) * S[:, 0] + t[j] * H[:, 0]
+        ctrl[:, j, :, 1] = (1.0 - t[j]) * S[:, 1] + t[j] * H[:, 1]
+    ctrl[..., 2] = z[:, None, None]
+    ctrl[:, :, -1, :] = ctrl[:, :, 0, :]         # the seam layers coincide exactly
+    weights = np.broadcast_to(w0[None, None, :], (n2, n1, n0)).copy()
+    faces = (FACE_NONE, FACE_NONE, FACE_NEUMANN, FACE_NEUMANN, FACE_DIRICHLET, FACE_NONE)
+    return Patch(degree=(degree,) * 3, knots=[U0, U1, U2], ctrl=np.ascontiguousarray(ctrl),
+                 weights=weights, faces=faces, seam=0)
+
+
+# --------------------------------------------------------------------------
 # scans
 # --------------------------------------------------------------------------
 def straight_track(p0, p1, power, absorptivity, speed, spot_radius=20e-6) -> Scan:
@@ -144,6 +239,29 @@ def meander(x_a, x_b, y0, hatch, n_tracks, z, power, absorptivity, speed,
         path[:, :2] = (path[:, :2] - c) @ R.T + c
     return Scan(path=path, seg_on=np.array(on, np.uint8), power=power,
                 absorptivity=absorptivity, speed=speed, spot_radius=spot_radius)
+
+
+def contour_and_radial_hatches(r_contour, r_in, half, margin, n_hatch, z, power,
+                               absorptivity, speed, n_arc=720, spot_radius=20e-6) -> Scan:
+    """One full counter-clockwise circle of radius r_contour about the origin
+    (a polyline of n_arc chords, starting at angle pi/4), then n_hatch radial
+    tracks at angles pi/4 + 2 pi k / n_hatch from radius r_in outwards to
+    ``margin`` inside the square [-half, half]^2; laser-off jumps between
+    tracks."""
+    a0 = np.pi / 4
+    ang = a0 + 2 * np.pi * np.arange(n_arc + 1) / n_arc
+    verts = [(r_contour * np.cos(a), r_contour * np.sin(a), z) for a in ang]
+    on = [1] * n_arc
+    for k in range(n_hatch):
+        a = a0 + 2 * np.pi * k / n_hatch
+        d = np.array([np.cos(a), np.sin(a)])
+        r_out = half / max(abs(d[0]), abs(d[1])) - margin
+        on.append(0)
+        verts.append((r_in * d[0], r_in * d[1], z))
+        verts.append((r_out * d[0], r_out * d[1], z))
+        on.append(1)
+    return Scan(path=np.array(verts, dtype=np.float64), seg_on=np.array(on, np.uint8),
+                power=power, absorptivity=absorptivity, speed=speed, spot_radius=spot_radius)
 
 
 # --------------------------------------------------------------------------
@@ -204,6 +322,37 @@ def block_meander(n_tracks=20, theta=0.5, n_steps=None, n_el=(64, 64, 16)) -> Wo
         n_steps = per_track * n_tracks
     return Workload(f"block_4x4x1mm_p2_{n_el[0]}x{n_el[1]}x{n_el[2]}_meander{n_tracks}",
                     patch, MAT_DEFAULT, scan, dt=5e-6, theta=theta, n_steps=n_steps)
+
+
+def plate_with_hole(n_el=(48, 48, 8), theta=0.5, n_steps=None) -> Workload:
+    """3 x 3 x 0.5 mm plate with a centred hole of radius 0.75 mm, one
+    degree-3 NURBS patch closed in xi (48 x 48 x 8 elements: 31,416 control
+    variables after the seam merge); a contour at r = 0.85 mm (100 um from
+    the hole edge) then 10 radial hatches from r = 0.95 mm to 0.1 mm inside
+    the outer edge; P = 180 W, A = 0.4, v = 0.8 m/s, dt = 5 us."""
+    patch = plate_with_hole_patch(n_el=n_el)
+    scan = contour_and_radial_hatches(0.85e-3, 0.95e-3, 1.5e-3, 0.1e-3, 10, 0.5e-3,
+                                      power=180.0, absorptivity=0.4, speed=0.8)
+    if n_steps is None:
+        n_steps = int(sum(np.floor(L / (0.8 * 5e-6) + 1e-9) + 1 for L in
+                          _track_lengths(scan)))
+    return Workload(f"plate_hole_3x3x0.5mm_p3_{n_el[0]}x{n_el[1]}x{n_el[2]}_contour_hatch10",
+                    patch, MAT_DEFAULT, scan, dt=5e-6, theta=theta, n_steps=n_steps)
+
+
+def _track_lengths(scan):
+    """Lengths of the maximal runs of laser-on segments."""
+    seg = np.linalg.norm(np.diff(scan.path, axis=0), axis=1)
+    out, cur = [], 0.0
+    for L, on in zip(seg, scan.seg_on):
+        if on:
+            cur += L
+        elif cur > 0.0:
+            out.append(cur)
+            cur = 0.0
+    if cur > 0.0:
+        out.append(cur)
+    return out
 
 
 def small_block(n_el=(6, 5, 3), degree=2, n_tracks=3, n_steps=None, theta=0.5,
