@@ -112,16 +112,25 @@ sa_status sa_create(const sa_options* o, sa_ctx** out);
  *   weights     same count without the *3, > 0; NULL = B-spline (all 1)
  *   knots[d]    n_knots[d] = n_ctrl[d] + degree[d] + 1 nondecreasing values,
  *               open (first and last value repeated degree+1 times)
+ *   seam_dir    -1: an open patch.  0, 1 or 2: the patch is closed in that
+ *               parametric direction (a ring): the control layers i_d = 0 and
+ *               i_d = n_ctrl[d] - 1 coincide (points and weights) and are ONE
+ *               set of control variables, so the space holds the merged
+ *               functions R_0 + R_{n-1}.  Both faces of that direction must be
+ *               SA_FACE_NONE (they are interior).  Control variables, fields
+ *               and matrices are then indexed over the merged grid (n_ctrl[d]
+ *               - 1 layers in direction d, natural order, layer n-1 = layer 0).
  * The top face (zeta = 1) must be the plane z = const: the point sources
  * lie on it.  Set-up (on the device): element and face Gauss points
  * ((p+1) per direction), the assembly of M and K in CSR form and the
- * boundary weight matrices.  Errors: SA_ERR_ARG, SA_ERR_GEOMETRY
- * (non-open or decreasing knots, weights <= 0, non-planar top, det J <= 0 at
- * a Gauss point), SA_ERR_OOM, SA_ERR_CUDA.
+ * boundary weight matrices.  Errors: SA_ERR_ARG (also: seam faces not NONE),
+ * SA_ERR_GEOMETRY (non-open or decreasing knots, weights <= 0, non-planar
+ * top, seam layers that do not coincide, det J <= 0 at a Gauss point),
+ * SA_ERR_OOM, SA_ERR_CUDA.
  */
 sa_status sa_create_patch(sa_ctx* ctx, const int degree[3], const int n_ctrl[3],
                           const double* ctrl_xyz, const double* weights,
-                          const double* const knots[3], const int n_knots[3]);
+                          const double* const knots[3], const int n_knots[3], int seam_dir);
 
 /* Face kinds (SA_FACE_*), face ids as above.  Default: faces 0-3 NEUMANN,
  * face 4 DIRICHLET, face 5 NONE.  Must be called before sa_create_patch to

@@ -63,7 +63,7 @@ def _load():
     sig = {
         "sa_options_default": (V, [C.POINTER(sa_options)]),
         "sa_create": (I, [C.POINTER(sa_options), C.POINTER(P)]),
-        "sa_create_patch": (I, [P, P, P, P, P, P, P]),
+        "sa_create_patch": (I, [P, P, P, P, P, P, P, I]),
         "sa_set_boundary": (I, [P, P]),
         "sa_set_material": (I, [P, D, D, D, D]),
         "sa_set_scan": (I, [P, P, I, P, D, D, D, D]),
@@ -168,7 +168,7 @@ class Context:
         fk = np.ascontiguousarray(face_kind, dtype=np.int32)
         _check(self.ptr, lib.sa_set_boundary(self.ptr, _ptr(fk)))
 
-    def create_patch(self, degree, n_ctrl, ctrl_xyz, weights, knots):
+    def create_patch(self, degree, n_ctrl, ctrl_xyz, weights, knots, seam_dir=-1):
         deg = np.ascontiguousarray(degree, dtype=np.int32)
         nc = np.ascontiguousarray(n_ctrl, dtype=np.int32)
         ctrl = np.ascontiguousarray(ctrl_xyz, dtype=np.float64)
@@ -177,7 +177,7 @@ class Context:
         kp = (C.c_void_p * 3)(*[k.ctypes.data for k in ks])
         nk = np.array([len(k) for k in ks], dtype=np.int32)
         _check(self.ptr, lib.sa_create_patch(self.ptr, _ptr(deg), _ptr(nc), _ptr(ctrl), _ptr(w),
-                                             C.cast(kp, C.c_void_p), _ptr(nk)))
+                                             C.cast(kp, C.c_void_p), _ptr(nk), int(seam_dir)))
 
     def set_material(self, k, rho, cp, T_c):
         _check(self.ptr, lib.sa_set_material(self.ptr, k, rho, cp, T_c))
@@ -386,7 +386,7 @@ def context_from_workload(wl, precision=SA_FP64, s_img=2.0, **opts):
     p = wl.patch
     ctx.set_boundary(p.faces)
     ctx.create_patch(p.degree, p.n_ctrl, p.ctrl.reshape(-1, 3), None if p.weights is None
-                     else p.weights.ravel(), p.knots)
+                     else p.weights.ravel(), p.knots, getattr(p, "seam", -1))
     m = wl.material
     ctx.set_material(m.k, m.rho, m.cp, m.T_c)
     s = wl.scan

@@ -353,7 +353,7 @@ sa_status sa_set_scan(sa_ctx* c, const double* path_xyz, int nv, const unsigned 
 
 sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                           const double* ctrl_xyz, const double* weights,
-                          const double* const knots[3], const int n_knots[3]) {
+                          const double* const knots[3], const int n_knots[3], int seam_dir) {
     sa_status st = check_usable(c);
     if (st) return st;
     if (c->has_patch) return sa_fail(c, SA_ERR_STATE, "patch already created");
@@ -406,6 +406,30 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         for (int i = 0; i < n0; ++i)
             if (std::fabs(ctrl_xyz[3 * (((n2 - 1) * n1 + j) * n0 + i) + 2] - zt) > 1e-12 * scale)
                 return sa_fail(c, SA_ERR_GEOMETRY, "top face (zeta = 1) is not a plane z = const");
+    // closed direction: coinciding end layers, interior faces, no wrap of a support
+    if (seam_dir < -1 || seam_dir > 2) return sa_fail(c, SA_ERR_ARG, "seam_dir = %d", seam_dir);
+    if (seam_dir >= 0) {
+        const int d = seam_dir;
+        if (c->face_kind[2 * d] != SA_FACE_NONE || c->face_kind[2 * d + 1] != SA_FACE_NONE)
+            return sa_fail(c, SA_ERR_ARG, "the faces of the seam direction %d must be SA_FACE_NONE", d);
+        if (n_ctrl[d] <= 2 * (degree[d] + 1))
+            return sa_fail(c, SA_ERR_ARG, "seam direction %d needs more than %d control points", d,
+                           2 * (degree[d] + 1));
+        for (int k = 0; k < n2; ++k)
+            for (int j = 0; j < n1; ++j)
+                for (int i = 0; i < n0; ++i) {
+                    int idx[3] = {i, j, k};
+                    if (idx[d] != 0) continue;
+                    const int a = (k * n1 + j) * n0 + i;
+                    idx[d] = n_ctrl[d] - 1;
+                    const int b = (idx[2] * n1 + idx[1]) * n0 + idx[0];
+                    for (int q = 0; q < 3; ++q)
+                        if (std::fabs(ctrl_xyz[3 * a + q] - ctrl_xyz[3 * b + q]) > 1e-12 * scale)
+                            return sa_fail(c, SA_ERR_GEOMETRY, "seam layers of direction %d do not coincide", d);
+                    if (weights && std::fabs(weights[a] - weights[b]) > 1e-12 * weights[a])
+                        return sa_fail(c, SA_ERR_GEOMETRY, "seam weights of direction %d differ", d);
+                }
+    }
 
     // ---- host copy and element lists -----------------------------------------
     for (int d = 0; d < 3; ++d) {
@@ -436,14 +460,26 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     c->ctrl.assign(ctrl_xyz, ctrl_xyz + 3 * ndof_ll);
     c->w.assign(ndof, 1.0);
     if (weights) c->w.assign(weights, weights + ndof);
-    c->n_dof = ndof;
+    // control variables: the control points, one layer fewer on the seam
+    c->seam = seam_dir;
+    for (int d = 0; d < 3; ++d) c->nd[d] = n_ctrl[d] - (d == seam_dir ? 1 : 0);
+    const int nvar = c->nd[0] * c->nd[1] * c->nd[2];
+    c->cmap.assign(ndof, 0);
+    for (int k = 0; k < n2; ++k)
+        for (int j = 0; j < n1; ++j)
+            for (int i = 0; i < n0; ++i) {
+                int idx[3] = {i, j, k};
+                if (seam_dir >= 0) idx[seam_dir] %= c->nd[seam_dir];
+                c->cmap[nat(c, i, j, k)] = (idx[2] * c->nd[1] + idx[1]) * c->nd[0] + idx[0];
+            }
+    c->n_dof = nvar;
     c->z_top = zt;
     c->x_ref = 0.5 * (lo[0] + hi[0]);
     c->y_ref = 0.5 * (lo[1] + hi[1]);
     c->length_scale = scale;
 
     // ---- Dirichlet control variables and the internal order -----------------
-    std::vector<char> isdir(ndof, 0);
+    std::vector<char> isdir(nvar, 0);
     for (int f = 0; f < 6; ++f) {
         if (c->face_kind[f] != SA_FACE_DIRICHLET) continue;
         const int d = f / 2, side = f % 2;
@@ -452,20 +488,20 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             for (int j = 0; j < n1; ++j)
                 for (int i = 0; i < n0; ++i) {
                     const int idx[3] = {i, j, k};
-                    if (idx[d] == layer) isdir[nat(c, i, j, k)] = 1;
+                    if (idx[d] == layer) isdir[c->cmap[nat(c, i, j, k)]] = 1;
                 }
     }
-    c->perm.assign(ndof, 0);
-    c->iperm.assign(ndof, 0);
+    c->perm.assign(nvar, 0);
+    c->iperm.assign(nvar, 0);
     int nf = 0;
-    for (int i = 0; i < ndof; ++i)
+    for (int i = 0; i < nvar; ++i)
         if (!isdir[i]) c->iperm[nf++] = i;
     c->n_free = nf;
     int nd = nf;
-    for (int i = 0; i < ndof; ++i)
+    for (int i = 0; i < nvar; ++i)
         if (isdir[i]) c->iperm[nd++] = i;
-    c->n_dir = ndof - nf;
-    for (int i = 0; i < ndof; ++i) c->perm[c->iperm[i]] = i;
+    c->n_dir = nvar - nf;
+    for (int i = 0; i < nvar; ++i) c->perm[c->iperm[i]] = i;
 
     // ---- upload geometry --------------------------------------------------
     std::vector<double4> cw(ndof);
@@ -476,7 +512,11 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         SA_UPLOAD(c, c->dU[d], c->U[d]);
         SA_UPLOAD(c, c->despan[d], c->espan[d]);
     }
-    SA_UPLOAD(c, c->dperm, c->perm);
+    {
+        std::vector<int> cp(ndof);   // control point -> internal control variable
+        for (int i = 0; i < ndof; ++i) cp[i] = c->perm[c->cmap[i]];
+        SA_UPLOAD(c, c->dperm, cp);
+    }
     DevPatch& dp = c->dp;
     for (int d = 0; d < 3; ++d) {
         dp.p[d] = c->p[d];
@@ -516,7 +556,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                                 idx[d] = layer;
                                 idx[ta] = c->espan[ta][ea] - c->p[ta] + la;
                                 idx[tb] = c->espan[tb][eb] - c->p[tb] + lb;
-                                const int in = c->perm[nat(c, idx[0], idx[1], idx[2])];
+                                const int in = c->perm[c->cmap[nat(c, idx[0], idx[1], idx[2])]];
                                 erow.push_back(in);
                                 ecol.push_back(q);
                             }
@@ -530,7 +570,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             std::vector<int> rows(erow.begin(), erow.end());
             std::sort(rows.begin(), rows.end());
             rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
-            std::vector<int> rmap(ndof, -1);
+            std::vector<int> rmap(c->n_dof, -1);
             for (size_t r = 0; r < rows.size(); ++r) rmap[rows[r]] = (int)r;
             std::vector<int> er(erow.size());
             for (size_t e = 0; e < erow.size(); ++e) er[e] = rmap[erow[e]];
@@ -666,23 +706,54 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
                 if (std::max(c->elo[d][i], c->elo[d][j]) <= std::min(c->ehi[d][i], c->ehi[d][j]))
                     nbr1[d][i].push_back(j);
     }
-    std::vector<long long> mk_ptr(ndof + 1, 0);
+    // control-point pattern (natural order)
+    std::vector<long long> cptr(ndof + 1, 0);
     for (int k = 0; k < n2; ++k)
         for (int j = 0; j < n1; ++j)
             for (int i = 0; i < n0; ++i)
-                mk_ptr[nat(c, i, j, k) + 1] =
+                cptr[nat(c, i, j, k) + 1] =
                     (long long)nbr1[0][i].size() * nbr1[1][j].size() * nbr1[2][k].size();
-    for (int r = 0; r < ndof; ++r) mk_ptr[r + 1] += mk_ptr[r];
-    c->nnz = mk_ptr[ndof];
-    std::vector<int> mk_col(c->nnz);
+    for (int r = 0; r < ndof; ++r) cptr[r + 1] += cptr[r];
+    const long long cnnz = cptr[ndof];
+    std::vector<int> ccol(cnnz);
     for (int k = 0; k < n2; ++k)
         for (int j = 0; j < n1; ++j)
             for (int i = 0; i < n0; ++i) {
-                long long s0 = mk_ptr[nat(c, i, j, k)];
+                long long s0 = cptr[nat(c, i, j, k)];
                 for (int kk : nbr1[2][k])
                     for (int jj : nbr1[1][j])
-                        for (int ii : nbr1[0][i]) mk_col[s0++] = nat(c, ii, jj, kk);
+                        for (int ii : nbr1[0][i]) ccol[s0++] = nat(c, ii, jj, kk);
             }
+    // pattern over control variables: the same on an open patch; on a closed
+    // one each entry lists the control-point entries summed into it
+    std::vector<long long> mk_ptr, sptr;
+    std::vector<int> mk_col, sidx;
+    if (seam_dir < 0) {
+        mk_ptr.swap(cptr);
+        mk_col.swap(ccol);
+    } else {
+        std::vector<std::vector<int>> rows_of(nvar);
+        for (int r = 0; r < ndof; ++r) rows_of[c->cmap[r]].push_back(r);
+        mk_ptr.assign(nvar + 1, 0);
+        sptr.assign(1, 0);
+        std::vector<std::pair<int, int>> ent;   // (column, control-point slot)
+        for (int R = 0; R < nvar; ++R) {
+            ent.clear();
+            for (int r : rows_of[R])
+                for (long long t = cptr[r]; t < cptr[r + 1]; ++t) ent.push_back({c->cmap[ccol[t]], (int)t});
+            std::sort(ent.begin(), ent.end());
+            for (size_t a = 0; a < ent.size(); ++a) {
+                if (a == 0 || ent[a].first != ent[a - 1].first) {
+                    mk_col.push_back(ent[a].first);
+                    sptr.push_back(sptr.back());
+                }
+                sidx.push_back(ent[a].second);
+                sptr.back() += 1;
+            }
+            mk_ptr[R + 1] = (long long)mk_col.size();
+        }
+    }
+    c->nnz = mk_ptr[nvar];
     SA_UPLOAD(c, c->mk_ptr, mk_ptr);
     SA_UPLOAD(c, c->mk_col, mk_col);
     SA_ALLOC(c, c->M, c->nnz);
@@ -711,9 +782,27 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "element matrices");
         const int* elo[3] = {c->d_elo[0].p, c->d_elo[1].p, c->d_elo[2].p};
         const int* ehi[3] = {c->d_ehi[0].p, c->d_ehi[1].p, c->d_ehi[2].p};
-        e = launch_mk_gather(dp, c->mk_ptr.p, c->mk_col.p, elo, ehi, Mloc.p, Kloc.p, c->M.p,
-                             c->K.p, s);
-        if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather M, K");
+        if (seam_dir < 0) {
+            e = launch_mk_gather(dp, c->mk_ptr.p, c->mk_col.p, elo, ehi, Mloc.p, Kloc.p, c->M.p,
+                                 c->K.p, s);
+            if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather M, K");
+        } else {
+            // control-point matrices, then P^T (.) P
+            DBuf<long long> gptr, gsptr;
+            DBuf<int> gcol, gsidx;
+            DBuf<double> Mc, Kc;
+            SA_UPLOAD(c, gptr, cptr);
+            SA_UPLOAD(c, gcol, ccol);
+            SA_UPLOAD(c, gsptr, sptr);
+            SA_UPLOAD(c, gsidx, sidx);
+            SA_ALLOC(c, Mc, cnnz);
+            SA_ALLOC(c, Kc, cnnz);
+            e = launch_mk_gather(dp, gptr.p, gcol.p, elo, ehi, Mloc.p, Kloc.p, Mc.p, Kc.p, s);
+            if (e == cudaSuccess)
+                e = launch_merge_csr(c->nnz, gsptr.p, gsidx.p, Mc.p, Kc.p, c->M.p, c->K.p, s);
+            if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather M, K");
+            SA_CUDA(c, cudaStreamSynchronize(s));   // temporaries freed on return
+        }
         int hbad = 0;
         SA_CUDA(c, cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SA_CUDA(c, cudaStreamSynchronize(s));
@@ -773,9 +862,9 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
 
     // ---- state and work vectors ---------------------------------------------------
     const int nwork = std::max(std::max(c->n_free, c->n_dir), 1);
-    SA_ALLOC(c, c->That, ndof);
-    SA_ALLOC(c, c->F0, ndof);
-    SA_ALLOC(c, c->F1, ndof);
+    SA_ALLOC(c, c->That, c->n_dof);
+    SA_ALLOC(c, c->F0, c->n_dof);
+    SA_ALLOC(c, c->F1, c->n_dof);
     SA_ALLOC(c, c->gnew, std::max(c->n_dir, 1));
     SA_ALLOC(c, c->bbot, std::max(c->n_dir, 1));
     SA_ALLOC(c, c->rhs, nwork);
@@ -783,7 +872,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_ALLOC(c, c->bsq, nwork);
     SA_ALLOC(c, c->dirv, 2 * (size_t)std::max(c->n_dir, 1));
     if (c->opt.initial_guess == SA_GUESS_EXTRAPOLATE) {
-        SA_ALLOC(c, c->x_prev, ndof);
+        SA_ALLOC(c, c->x_prev, c->n_dof);
         SA_ALLOC(c, c->dx_extrap, std::max(c->n_free, 1));
         SA_ALLOC(c, c->one, 1);
         const double one = 1.0;
@@ -804,8 +893,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         SA_ALLOC(c, c->workpad, 2 * (nwork + 2 * (size_t)c->work_pad) * vt);
         SA_CUDA(c, cudaMemsetAsync(c->workpad.p, 0, 2 * (nwork + 2 * (size_t)c->work_pad) * vt, s));
     }
-    SA_ALLOC(c, c->dev64, ndof);
-    SA_ALLOC(c, c->dev32, ndof);
+    SA_ALLOC(c, c->dev64, c->n_dof);
+    SA_ALLOC(c, c->dev32, c->n_dof);
     if (c->opt.precision == SA_MIXED) {
         SA_ALLOC(c, c->a_dinv32, std::max(c->n_free, 1));
         SA_ALLOC(c, c->mbot_dinv32, std::max(c->n_dir, 1));
@@ -816,8 +905,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     }
     SA_ALLOC(c, c->s_lat, std::max(c->q_lat, 1));
     SA_ALLOC(c, c->tt_bot, std::max(c->q_bot, 1));
-    SA_CUDA(c, cudaMemsetAsync(c->F0.p, 0, sizeof(double) * ndof, s));
-    SA_CUDA(c, cudaMemsetAsync(c->F1.p, 0, sizeof(double) * ndof, s));
+    SA_CUDA(c, cudaMemsetAsync(c->F0.p, 0, sizeof(double) * c->n_dof, s));
+    SA_CUDA(c, cudaMemsetAsync(c->F1.p, 0, sizeof(double) * c->n_dof, s));
     SA_CUDA(c, cudaMemsetAsync(c->s_lat.p, 0, sizeof(double) * std::max(c->q_lat, 1), s));
     SA_CUDA(c, cudaMemsetAsync(c->tt_bot.p, 0, sizeof(double) * std::max(c->q_bot, 1), s));
     SA_CUDA(c, cudaMemsetAsync(c->work64.p, 0, sizeof(double) * 5 * nwork, s));

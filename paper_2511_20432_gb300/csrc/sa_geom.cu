@@ -559,6 +559,22 @@ __global__ void k_eval(EvalArgs a) {
     for (int o = 16; o > 0; o >>= 1) Tt += __shfl_xor_sync(0xffffffffu, Tt, o);
     if (lane == 0) a.T_out[t] = ok ? Tt + That : nan("");
 }
+// Closed patches: every entry of the matrices over control variables is the
+// sum of the control-point entries that map to it (P^T M P), in the fixed
+// order of the source list.
+__global__ void k_merge_csr(long long n, const long long* sptr, const int* sidx, const double* Mc,
+                            const double* Kc, double* M, double* K) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double m = 0.0, k = 0.0;
+    for (long long t = sptr[e]; t < sptr[e + 1]; ++t) {
+        m += Mc[sidx[t]];
+        k += Kc[sidx[t]];
+    }
+    M[e] = m;
+    K[e] = k;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -627,6 +643,13 @@ cudaError_t launch_element_local(const DevPatch& dp, double rho_cp, double k, co
     if (e != cudaSuccess) return e;
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
     k_element_local<<<nel, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_csr(long long n, const long long* sptr, const int* sidx, const double* Mc,
+                             const double* Kc, double* M, double* K, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_merge_csr<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, sptr, sidx, Mc, Kc, M, K);
     return cudaGetLastError();
 }
 

@@ -212,7 +212,10 @@ struct sa_ctx {
     int face_kind[6] = {SA_FACE_NEUMANN, SA_FACE_NEUMANN, SA_FACE_NEUMANN, SA_FACE_NEUMANN,
                         SA_FACE_DIRICHLET, SA_FACE_NONE};
     int n_dof = 0, n_free = 0, n_dir = 0, n_elem = 0;
-    std::vector<int> perm;    // natural -> internal (free first, then Dirichlet)
+    int seam = -1;            // closed direction (merged end layers), or -1
+    int nd[3] = {0, 0, 0};    // control-variable grid (n, minus one layer on the seam)
+    std::vector<int> cmap;    // control point (natural) -> control variable (natural)
+    std::vector<int> perm;    // control variable: natural -> internal (free first, then Dirichlet)
     std::vector<int> iperm;   // internal -> natural
     double z_top = 0, x_ref = 0, y_ref = 0, length_scale = 1;
 
@@ -239,7 +242,7 @@ struct sa_ctx {
     DBuf<double> dU[3];
     DBuf<int> despan[3];
     DBuf<double4> dcw;
-    DBuf<int> dperm;          // natural -> internal
+    DBuf<int> dperm;          // control point (natural) -> internal control variable
     DevPatch dp;
 
     // quadrature points (canonical order)
@@ -379,6 +382,8 @@ cudaError_t launch_element_local(const DevPatch& dp, double rho_cp, double k, co
 cudaError_t launch_mk_gather(const DevPatch& dp, const long long* ptr, const int* col,
                              const int* const* elo, const int* const* ehi, const double* Mloc,
                              const double* Kloc, double* M, double* K, cudaStream_t s);
+cudaError_t launch_merge_csr(long long n, const long long* sptr, const int* sidx, const double* Mc,
+                             const double* Kc, double* M, double* K, cudaStream_t s);
 cudaError_t launch_elem_centers(const DevPatch& dp, double* ecent, cudaStream_t s);
 cudaError_t launch_mbot_fill(int n_rows, const int* mptr, const int* mcol, const int* wptr,
                              const int* wcol, const double* wval, const int* coo_dof,

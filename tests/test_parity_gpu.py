@@ -36,6 +36,7 @@ def _patch_cases():
         "bspline_p3": W.distorted_block(weights=False, degree=3, n_el=(3, 2, 2), seed=5),
         "quarter_cylinder": W.quarter_cylinder_part(),
         "mixed_degree": W.cuboid_patch((0.6e-3, 0.5e-3, 0.3e-3), (4, 3, 2), (3, 2, 1)),
+        "plate_seam": W.plate_with_hole_patch(n_el=(8, 4, 2)),
     }
 
 
@@ -128,6 +129,30 @@ def test_cuboid_single_track_mixed(sa, theta, variant):
     err, ctx, m = _lockstep(sa, wl, sa.SA_MIXED, 150, every=15, pcg_variant=VARIANTS[variant])
     assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
     assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_plate_with_hole_lockstep(sa, prec):
+    """The closed (seam) plate with a hole, coarse (8 x 4 x 2 elements of
+    degree 3): history sums, F and T^ step by step against the oracle along
+    the contour scan, and T near the hole edge."""
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    wl = W.plate_with_hole(n_el=(8, 4, 2), n_steps=60)
+    err, ctx, m = _lockstep(sa, wl, p, 60, every=20)
+    if p == sa.SA_FP64:
+        assert err["s_lat"] <= 1e-12 and err["tt_bot"] <= 1e-12, err
+        assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+    else:
+        assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
+        assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+    # points within 20 um of the hole edge (top surface and below), on both
+    # sides of the seam (xi = 0 is at -45 degrees)
+    xi = np.array([[u, v, w] for u in (0.0, 0.01, 0.3, 0.62, 0.99, 1.0)
+                   for v in (0.995, 1.0) for w in (1.0, 0.9)])
+    x, T_ref = m.eval_T(xi)
+    T = ctx.eval_T(x)
+    tol = TOL_FP64 if p == sa.SA_FP64 else TOL_MIXED_REL
+    assert rel_linf(T, T_ref) <= tol
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -328,3 +353,52 @@ def test_full_size_block_sampled(sa):
     rhs = (M / dt - (1 - th) * K) @ T_prev + th * F1 + (1 - th) * F_prev
     res = np.linalg.norm((lhs - rhs)[~dirm]) / np.linalg.norm(rhs[~dirm])
     assert res <= 1e-9, res
+
+
+def test_plate_with_hole_full_size_mixed_vs_fp64(sa):
+    """The 48 x 48 x 8 degree-3 plate with a hole (31,416 control variables,
+    closed seam): the mixed path against the FP64 path along the contour, at
+    points within 20 um of the hole edge and of the outer corners, and the
+    theta-system residual of the FP64 step (property at any size)."""
+    import torch
+    wl = W.plate_with_hole()
+    s = torch.cuda.Stream()
+    a = gpu_context(wl, sa.SA_MIXED, cuda_stream=s, use_graph=1)
+    b = gpu_context(wl, sa.SA_FP64, cuda_stream=s, use_graph=1, pcg_tol=1e-12)
+    n = 400
+    a.step(wl.theta, wl.dt, n)
+    b.step(wl.theta, wl.dt, n - 1)
+    T_prev = b.field(sa.SA_FIELD_THAT)
+    F_prev = b.field(sa.SA_FIELD_F)
+    b.step(wl.theta, wl.dt, 1)
+    R, h, t = 0.75e-3, 1.5e-3, 0.5e-3
+    ang = np.linspace(0, 2 * np.pi, 64, endpoint=False)
+    pts = []
+    for d in (2e-6, 10e-6, 20e-6):                   # ring outside the hole edge
+        for z in (t, t - 10e-6):
+            pts += [((R + d) * np.cos(a_), (R + d) * np.sin(a_), z) for a_ in ang]
+    for sx in (-1, 1):                               # the four outer corners
+        for sy in (-1, 1):
+            for d in (2e-6, 10e-6, 14e-6):
+                pts.append((sx * (h - d), sy * (h - d), t))
+    pts = np.array(pts)
+    Ta = a.eval_T(pts)
+    Tb = b.eval_T(pts)
+    assert np.isfinite(Ta).all() and np.isfinite(Tb).all()
+    assert rel_linf(Ta, Tb) <= TOL_MIXED_REL and np.abs(Ta - Tb).max() <= TOL_MIXED_ABS
+    assert Tb.max() > wl.material.T_c + 50.0         # the contour heats the hole edge
+    # theta-system residual of the last FP64 step
+    import scipy.sparse as sp
+    from oracle.geometry import PatchGeom
+    nd = b.sizes().n_dof
+    ptr, col, Mv = b.matrix(0)
+    _, _, Kv = b.matrix(1)
+    M = sp.csr_matrix((Mv, col, ptr), shape=(nd, nd))
+    K = sp.csr_matrix((Kv, col, ptr), shape=(nd, nd))
+    T1 = b.field(sa.SA_FIELD_THAT)
+    F1 = b.field(sa.SA_FIELD_F)
+    th, dt = wl.theta, wl.dt
+    free = ~PatchGeom(wl.patch).dirichlet_dofs()
+    lhs = (M / dt + th * K) @ T1
+    rhs = (M / dt - (1 - th) * K) @ T_prev + th * F1 + (1 - th) * F_prev
+    assert np.linalg.norm((lhs - rhs)[free]) <= 1e-10 * np.linalg.norm(rhs[free])
