@@ -91,9 +91,23 @@ typedef struct sa_options {
                                     after sa_set_state the first step starts from T^n.
                                   A learned warm start (sa_set_warm_start) replaces
                                   the extrapolated proposal of the main solve.     */
+    int precond;               /* preconditioner of the main theta-step solve:
+                                  SA_PRECOND_AUTO (0, default): fast diagonalization
+                                    (below) when the shared-memory PCG runs and the free
+                                    control variables form the tensor grid, Jacobi
+                                    otherwise;
+                                  SA_PRECOND_JACOBI (1): D^{-1};
+                                  SA_PRECOND_FD (2): fast diagonalization of the box with
+                                    the patch's knot vectors and mean lengths, scaled to
+                                    the diagonal of A (exact on a box), SA_ERR_ARG at
+                                    set-up where it does not apply (more than 128
+                                    control variables along a direction).  The bottom
+                                    projection keeps Jacobi.  Same solution to the
+                                    solver tolerance.                                */
 } sa_options;
 
 enum { SA_PCG_AUTO = 0, SA_PCG_SHARED = 1, SA_PCG_GLOBAL = 2 };
+enum { SA_PRECOND_AUTO = 0, SA_PRECOND_JACOBI = 1, SA_PRECOND_FD = 2 };
 enum { SA_GUESS_PREVIOUS = 0, SA_GUESS_EXTRAPOLATE = 1 };
 
 /* Fill o with the defaults listed above. */

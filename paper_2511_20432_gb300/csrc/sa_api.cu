@@ -34,8 +34,6 @@ sa_status sa_cuda_fail(sa_ctx* c, cudaError_t e, const char* where) {
     return SA_ERR_CUDA;
 }
 
-namespace {
-
 // Gauss-Legendre nodes and weights on [-1, 1] for 1..4 points (closed forms).
 void gauss_legendre(int n, double* x, double* w) {
     switch (n) {
@@ -71,6 +69,8 @@ void gauss_legendre(int n, double* x, double* w) {
         }
     }
 }
+
+namespace {
 
 bool is_fin(double v) { return std::isfinite(v); }
 
@@ -248,6 +248,7 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
     if (opt.pcg_variant < SA_PCG_AUTO || opt.pcg_variant > SA_PCG_GLOBAL) return SA_ERR_ARG;
     if (opt.initial_guess != SA_GUESS_PREVIOUS && opt.initial_guess != SA_GUESS_EXTRAPOLATE)
         return SA_ERR_ARG;
+    if (opt.precond < SA_PRECOND_AUTO || opt.precond > SA_PRECOND_FD) return SA_ERR_ARG;
     if (opt.hist_points_per_lane != 0 && opt.hist_points_per_lane != 1 &&
         opt.hist_points_per_lane != 2 && opt.hist_points_per_lane != 4)
         return SA_ERR_ARG;
@@ -928,11 +929,21 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             if (v == 1 || v == 2 || v == 4 || v == 8) c->pcg_ksplit = v;
         }
         SA_ALLOC(c, c->partials, (size_t)12 * c->pcg_grid);
-        if (c->opt.pcg_variant == SA_PCG_SHARED) {
+        if (c->opt.precond != SA_PRECOND_JACOBI) {
+            sa_status fst = fd_setup(c);
+            if (fst) return fst;
+            if (c->opt.precond == SA_PRECOND_FD && !c->fd_ok)
+                return sa_fail(c, SA_ERR_ARG, "fast diagonalization needs the tensor grid of free "
+                                              "control variables with at most 128 per direction");
+            if (c->opt.precond == SA_PRECOND_FD && c->opt.pcg_variant == SA_PCG_GLOBAL)
+                return sa_fail(c, SA_ERR_ARG, "fast diagonalization runs in the shared-memory PCG only");
+        }
+        if (c->opt.pcg_variant == SA_PCG_SHARED || c->opt.precond == SA_PRECOND_FD) {
             PcgLaunch L{};
             L.op = sell_view(c->a_s);
             L.pad = c->work_pad;
             L.grid = c->pcg_grid;
+            L.fd = fd_view(c);
             if (!pcg_shared_fits(c->opt.precision, L))
                 return sa_fail(c, SA_ERR_ARG,
                                "shared-memory PCG: %d rows per block do not fit in shared memory",
@@ -1026,6 +1037,7 @@ sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
         e = launch_to_f32(c->a_s.n_stored, c->a_val.p, c->a_val32.p, c->stream);
     if (e == cudaSuccess && c->opt.precision == SA_MIXED)
         e = launch_to_f32(c->n_free, c->a_dinv.p, c->a_dinv32.p, c->stream);
+    if (e == cudaSuccess) e = fd_prepare(c, theta, dt, c->stream);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "build A");
     c->op_dt = dt;
     c->op_theta = theta;
@@ -1159,6 +1171,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.variant = c->opt.pcg_variant;
+        L.fd = fd_view(c);
         L.which = 0;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;

@@ -151,6 +151,19 @@ inline SellView sell_view(const SellDev& s) {
     return v;
 }
 
+// Fast-diagonalization preconditioner as the PCG kernel sees it (device
+// pointers in the operator precision; m[d] free sizes per direction).
+struct FdView {
+    bool on;
+    int m[3];
+    const void* U[3];      // m x m row-major: U[a][o] (columns = eigenvectors)
+    const void* Ut[3];     // transposes
+    const void* lamc[3];   // c_d lambda_d
+    double cM;
+    const void* S;         // n_free diagonal scaling
+    void* Z;               // n_free work vector
+};
+
 // Arguments of one PCG solve.
 struct PcgLaunch {
     SellView op;
@@ -169,6 +182,7 @@ struct PcgLaunch {
     int pad;
     size_t stride;
     int variant;              // SA_PCG_AUTO / SA_PCG_SHARED / SA_PCG_GLOBAL
+    FdView fd{};              // preconditioner (fd.on false: Jacobi)
     double* partials;         // 12 x grid
     const float* dx0;         // proposed increment (mode 1), or null
     const double* dx0_scale;  // device scalar multiplying dx0
@@ -320,6 +334,13 @@ struct sa_ctx {
     SellHost a_h, r_h, mbot_h;
     std::vector<int> wlat_rowdof_h, wlat_ptr_h, wlat_col_h, wbot_ptr_h, wbot_col_h;
 
+    // fast-diagonalization preconditioner (csrc/sa_fd.cu)
+    bool fd_ok = false;
+    int fd_m[3] = {0, 0, 0};
+    double fd_L[3] = {0, 0, 0}, fd_cM = 0, fd_c[3] = {0, 0, 0};
+    std::vector<double> fd_U[3], fd_lam[3], fd_md[3], fd_kd[3];
+    DBuf<unsigned char> fdU[3], fdUt[3], fdlamc[3], fdmd[3], fdkd[3], fdS, fdZ;
+
     // extrapolated initial guesses (sa_options::initial_guess)
     DBuf<double> x_prev;             // T^{n-1}: free part, then the Dirichlet part
     DBuf<float> dx_extrap;           // n_free: proposed increment T^n - T^{n-1}
@@ -429,6 +450,10 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
                           double* gprev, double* g0, cudaStream_t s);
+sa_status fd_setup(sa_ctx* c);
+cudaError_t fd_prepare(sa_ctx* c, double theta, double dt, cudaStream_t s);
+FdView fd_view(const sa_ctx* c);
+void gauss_legendre(int n, double* x, double* w);
 // Whether the shared-memory PCG of this launch keeps its rows in shared memory.
 bool pcg_shared_fits(int precision, const PcgLaunch& L);
 cudaError_t launch_finalize(int n_dir, int n_free, int n_dof, const double* gnew, double* That,

@@ -703,6 +703,9 @@ struct SmemArgs {
     const float* dx0;      // mode 1: proposed increment (scaled by *dx0_scale), or null
     const double* dx0_scale;
     const void* dinvl;     // D^{-1} in VT
+    FdView fd;             // fast-diagonalization preconditioner (fd.on), else Jacobi
+    int fd_mmax;           // longest grid line (per-warp scratch entries)
+    int plan_wcap;         // window entries reserved in shared memory
 };
 
 template <typename T>
@@ -766,6 +769,111 @@ __device__ bool grid_exchange(const GridSync& g, const AT* bl, int slot, double*
     return true;
 }
 
+constexpr int kFdPerLane = 4;   // line entries per lane: lines of at most 128
+
+// Fast-diagonalization preconditioner u = S A_box^{-1} S r over all rows.
+// On entry Z = S r (every block wrote its rows, then a grid barrier).  Five
+// passes over lines of the free grid (U_0^T, U_1^T, U_2 D U_2^T, U_1, U_0),
+// one warp per line (in place: a line is read and written by one warp), a
+// grid barrier between passes; the last pass writes S y into out.  Each
+// block first copies the pass's m x m matrix into shared memory (wbuf, at
+// least m^2 entries; the SpMV window is idle here).  Lines have at most 128
+// entries (4 per lane).
+template <typename VT>
+__device__ void fd_stage(VT* wbuf, const VT* W, int m) {
+    __syncthreads();                       // the previous pass is done with wbuf
+    const int mm = m * m;
+    for (int t = threadIdx.x; t < mm; t += blockDim.x) wbuf[t] = __ldg(W + t);
+    __syncthreads();
+}
+
+template <typename VT>
+__device__ __forceinline__ void fd_line_matvec(const VT* Wb, const VT* xs, int m, int lane, VT (&y)[kFdPerLane]) {
+    // y[o] = sum_a Wb[a][o] xs[a], o = lane + 32 t
+#pragma unroll
+    for (int t = 0; t < kFdPerLane; ++t) y[t] = (VT)0;
+#pragma unroll 4
+    for (int a = 0; a < m; ++a) {
+        const VT xa = xs[a];
+        const VT* Wa = Wb + a * m;
+#pragma unroll
+        for (int t = 0; t < kFdPerLane; ++t) {
+            const int o = lane + 32 * t;
+            if (o < m) y[t] = fma(Wa[o], xa, y[t]);
+        }
+    }
+}
+
+template <typename VT>
+__device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* xs, VT* out) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int m0 = fd.m[0], m1 = fd.m[1], m2 = fd.m[2];
+    VT* Z = (VT*)fd.Z;
+    const VT* S = (const VT*)fd.S;
+    const VT* l0 = (const VT*)fd.lamc[0];
+    const VT* l1 = (const VT*)fd.lamc[1];
+    const VT* l2 = (const VT*)fd.lamc[2];
+    const VT cM = (VT)fd.cM;
+    for (int pass = 0; pass < 5; ++pass) {
+        const int d = pass < 3 ? pass : 4 - pass;           // directions 0 1 2 1 0
+        const int m = fd.m[d];
+        const int stride = d == 0 ? 1 : (d == 1 ? m0 : m0 * m1);
+        const int nlines = (m0 * m1 * m2) / m;
+        const bool busy = blockIdx.x * (blockDim.x >> 5) < nlines;   // block has lines
+        // y[o] = sum_a W[a][o] x[a]: W = U_d (applies U_d^T) or U_d^T (applies U_d)
+        if (busy) fd_stage(wbuf, (const VT*)(pass < 3 ? fd.U[d] : fd.Ut[d]), m);
+        for (int L = gw; L < nlines; L += nw) {
+            const int base = d == 0 ? L * m0 : (d == 1 ? (L / m0) * (m0 * m1) + (L % m0) : L);
+            for (int a = lane; a < m; a += 32) xs[a] = __ldcg(Z + base + (long long)a * stride);
+            __syncwarp();
+            VT y[kFdPerLane];
+            fd_line_matvec(wbuf, xs, m, lane, y);
+            if (pass == 2) {
+                // D = 1 / (c_M + c_0 lambda_0[i] + c_1 lambda_1[j] + c_2 lambda_2[k]),
+                // then U_2 (from global: wbuf holds U_2) on the same line
+                const VT li = cM + l0[L % m0] + l1[L / m0];
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < kFdPerLane; ++t) {
+                    const int o = lane + 32 * t;
+                    if (o < m) xs[o] = y[t] / (li + l2[o]);
+                }
+                __syncwarp();
+                const VT* W2 = (const VT*)fd.Ut[2];
+#pragma unroll
+                for (int t = 0; t < kFdPerLane; ++t) y[t] = (VT)0;
+#pragma unroll 4
+                for (int a = 0; a < m; ++a) {
+                    const VT xa = xs[a];
+                    const VT* Wa = W2 + a * m;
+#pragma unroll
+                    for (int t = 0; t < kFdPerLane; ++t) {
+                        const int o = lane + 32 * t;
+                        if (o < m) y[t] = fma(__ldg(Wa + o), xa, y[t]);
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kFdPerLane; ++t) {
+                const int o = lane + 32 * t;
+                if (o < m) {
+                    const long long idx = base + (long long)o * stride;
+                    if (pass == 4)
+                        out[idx] = S[idx] * y[t];
+                    else
+                        Z[idx] = y[t];
+                }
+            }
+            __syncwarp();
+        }
+        if (pass < 4 && !sync.barrier()) return false;
+    }
+    return true;
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     // AT: type of the dot products (the operator precision).  The mixed
@@ -777,7 +885,12 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     AT* R32 = (AT*)(V + kSmemVecs * a.rcap);   // sigma r
     AT* U32 = R32 + a.rcap;                 // sigma u
     VT* sq = (VT*)(U32 + a.rcap);           // 1024 (k-split partial sums)
-    VT* win = sq + 1024;                    // window
+    VT* win = sq + 1024;                    // SpMV window; the preconditioner's matrix
+    VT* xsw = win + a.plan_wcap;            // per-warp line scratch (preconditioner)
+    VT* xs = xsw + (threadIdx.x >> 5) * a.fd_mmax;
+    const bool fd = a.fd.on;
+    VT* const Zf = (VT*)a.fd.Z;
+    const VT* const Sf = (const VT*)a.fd.S;
     double* const D = V;
     double* const R = V + a.rcap;
     double* const U = V + 2 * a.rcap;
@@ -868,72 +981,86 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
         }
         __syncthreads();
     }
-    // ---- the norm of b -> sigma; u = D^{-1} r published
+    // ---- the norms of b and r0 -> sigma; convergence at the start
+    if (fd)
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) Zf[row0 + t] = Sf[row0 + t] * (VT)R[t];
     double bb;
+    int it = 0;
     {
-        double v1[1] = {bbp};
-        block_sum<1>(v1, bl64);
-        if (!grid_exchange<1>(sync, bl64, 0, res)) return;
+        double rrp = 0.0;
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) rrp += R[t] * R[t];
+        double v2[2] = {bbp, rrp};
+        block_sum<2>(v2, bl64);
+        if (!grid_exchange<2>(sync, bl64, 8, res)) return;
         bb = res[0];
-        if (threadIdx.x == 0) sc[2] = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
+        if (threadIdx.x == 0) {
+            sc[2] = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
+            const double rr0 = bb > 0.0 ? res[1] / bb : res[1];
+            sc[3] = rr0;
+            state = !(rr0 == rr0) ? 2 : (rr0 <= a.tol * a.tol ? 1 : 0);
+        }
         __syncthreads();
     }
     const AT sig = (AT)sc[2];
     const AT* DL = (const AT*)a.dinvl;
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-        const double u = DI[t] * R[t];
-        const AT r32 = (AT)R[t] * sig;
-        U[t] = u;
-        R32[t] = r32;
-        U32[t] = DL[row0 + t] * r32;
-        a.ul[row0 + t] = (VT)u;
-    }
     // stop when (sigma r, sigma r) <= tol^2 (sigma^2 ||b||^2 = 1)
     const double stop2 = bb > 0.0 ? a.tol * a.tol : 0.0;
-    int it = 0;
-    if (!sync.barrier()) return;
-    for (;;) {
-        // ---- S: w = A u and the three (scaled) dot products
-        AT v[3] = {(AT)0, (AT)0, (AT)0};
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) R32[t] = (AT)R[t] * sig;
+    // u = P^{-1} r, published (Jacobi: local; fast diagonalization: passes)
+    auto precondition = [&]() -> bool {
+        if (fd) {
+            if (!fd_apply<VT>(a.fd, sync, win, xs, a.ul)) return false;
+            if (!sync.barrier()) return false;
+            for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+                const VT u = __ldcg(a.ul + row0 + t);
+                U[t] = (double)u;
+                U32[t] = (AT)u * sig;
+            }
+        }
+        return true;
+    };
+    if (!fd)
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+            const double u = DI[t] * R[t];
+            U[t] = u;
+            U32[t] = DL[row0 + t] * R32[t];
+            a.ul[row0 + t] = (VT)u;
+        }
+    if (state == 0) {
+        if (!fd && !sync.barrier()) return;
+        if (!precondition()) return;
+    }
+    while (state == 0) {
+        // ---- S: w = A u and (r, u), (w, u)
+        AT v[2] = {(AT)0, (AT)0};
         spmv_block(a.plan, a.ul, win, sq, [&](int i, VT wt) {
             const int l = i - row0;
             W[l] = (double)wt;
-            const AT ws = (AT)wt * sig;
             v[0] += R32[l] * U32[l];
-            v[1] += ws * U32[l];
-            v[2] += R32[l] * R32[l];
+            v[1] += ((AT)wt * sig) * U32[l];
         }, &wa);
-        block_sum<3>(v, blt);
-        // two slot sets: the next iteration's partials may be written while a
-        // slower block still reads these
-        if (!grid_exchange<3>(sync, blt, 1 + 3 * (it & 1), res)) return;
-        // scalars and the stopping decision once per block
+        block_sum<2>(v, blt);
+        // partial slots: warm start 10-11, norms 8-9, then S 0-1 / 4-5 and
+        // V 2 / 6 alternating (a slot set is rewritten only two barriers later)
+        if (!grid_exchange<2>(sync, blt, 4 * (it & 1), res)) return;
         if (threadIdx.x == 0) {
-            const double rr = res[2];
             const AT gamma = (AT)res[0], delta = (AT)res[1];
-            int stt = 0;
-            if (!(rr == rr) || !(gamma == gamma) || !(delta == delta)) stt = 2;
-            else if (rr <= stop2) stt = 1;
-            else if (it >= a.max_iter) stt = 3;
-            if (stt == 0) {
-                AT be = (AT)0, al = gamma / delta;
-                if (it > 0) {
-                    be = gamma / scl[1];
-                    al = gamma / (delta - be * gamma / scl[0]);
-                }
-                if (!(al == al)) stt = 2;
-                scl[0] = al;
-                scl[1] = gamma;
-                sc[0] = (double)al;
-                sc[1] = (double)be;
+            AT be = (AT)0, al = gamma / delta;
+            if (it > 0) {
+                be = gamma / scl[1];
+                al = gamma / (delta - be * gamma / scl[0]);
             }
-            sc[3] = rr;
-            state = stt;
+            scl[0] = al;
+            scl[1] = gamma;
+            sc[0] = (double)al;
+            sc[1] = (double)be;
+            state = !(al == al) ? 2 : 0;
         }
         __syncthreads();
         if (state != 0) break;
         const double al = sc[0], be = sc[1];
-        // ---- V: own rows only
+        // ---- V: own rows; (r, r) of the update
+        AT vr[1] = {(AT)0};
         for (int t = threadIdx.x; t < nr; t += blockDim.x) {
             const double p = fma(be, P[t], U[t]);
             const double s = fma(be, S[t], W[t]);
@@ -941,16 +1068,30 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             S[t] = s;
             D[t] = fma(al, p, D[t]);
             const double r = fma(-al, s, R[t]);
-            const double u = DI[t] * r;
             const AT r32 = (AT)r * sig;
             R[t] = r;
-            U[t] = u;
             R32[t] = r32;
-            U32[t] = DL[row0 + t] * r32;
-            a.ul[row0 + t] = (VT)u;
+            vr[0] += r32 * r32;
+            if (fd) {
+                Zf[row0 + t] = Sf[row0 + t] * (VT)r;
+            } else {
+                const double u = DI[t] * r;
+                U[t] = u;
+                U32[t] = DL[row0 + t] * r32;
+                a.ul[row0 + t] = (VT)u;
+            }
         }
         ++it;
-        if (!sync.barrier()) return;
+        block_sum<1>(vr, blt);
+        if (!grid_exchange<1>(sync, blt, 2 + 4 * (it & 1), res)) return;
+        if (threadIdx.x == 0) {
+            const double rr = res[0];
+            sc[3] = rr;
+            state = !(rr == rr) ? 2 : (rr <= stop2 ? 1 : (it >= a.max_iter ? 3 : 0));
+        }
+        __syncthreads();
+        if (state != 0) break;
+        if (!precondition()) return;
     }
     for (int t = threadIdx.x; t < nr; t += blockDim.x) a.x[row0 + t] += D[t];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -969,9 +1110,6 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     }
 }
 
-// Extrapolated initial guesses (x0 = x^n + (x^n - x^{n-1})):
-// free part: the previous increment as the proposed dx0, and x^{n-1} <- x^n;
-// Dirichlet part: g0 = 2 g^n - g^{n-1}, and g^{n-1} <- g^n.
 __global__ void k_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
                          double* gprev, double* g0) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1017,8 +1155,8 @@ Op<VT> make_op(const SellView& s, const void* val) {
 // (so the 32 warps of a block are busy), window length, shared memory.
 template <typename VT>
 struct PcgShape {
-    int G, spb, ks, rcap;
-    long long wl;
+    int G, spb, ks, rcap, fd_mmax;
+    long long wl, region;
     bool window;
     size_t smem;
     bool fits;             // (shared-memory variant) vectors + k-split scratch fit
@@ -1037,11 +1175,19 @@ PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
     sh.rcap = 32 * std::max(sh.spb, 1);
     // window: 32 spb rows plus the halo, 4-entry alignment slack
     sh.wl = 32ll * sh.spb + (L.op.dmax - L.op.dmin) + 8;
-    const size_t fixed = 1024 * sizeof(VT) + (pipelined ? (size_t)kSmemVecs * sh.rcap * sizeof(double) + 2 * sh.rcap * sizeof(VT) : 0);
-    sh.fits = fixed <= kSmemCap;
+    // the preconditioner's m x m matrix reuses the window region
+    const int mmax = (pipelined && L.fd.on) ? std::max(L.fd.m[0], std::max(L.fd.m[1], L.fd.m[2])) : 0;
+    const long long fdw = (long long)mmax * mmax;
+    sh.fd_mmax = mmax;
+    const size_t fixed = 1024 * sizeof(VT) +
+                         (pipelined ? (size_t)kSmemVecs * sh.rcap * sizeof(double) + 2 * sh.rcap * sizeof(VT) +
+                                          (size_t)32 * mmax * sizeof(VT)
+                                    : 0);
+    sh.fits = fixed + fdw * sizeof(VT) <= kSmemCap;
     sh.window = L.op.col16 != nullptr && L.pad >= -L.op.dmin + 4 && L.pad >= L.op.dmax + 4 &&
-                fixed + sh.wl * sizeof(VT) <= kSmemCap;
-    sh.smem = fixed + (sh.window ? (size_t)sh.wl * sizeof(VT) : 0);
+                fixed + std::max(sh.wl, fdw) * sizeof(VT) <= kSmemCap;
+    sh.region = sh.window ? std::max(sh.wl, fdw) : fdw;
+    sh.smem = fixed + (size_t)sh.region * sizeof(VT);
     return sh;
 }
 
@@ -1076,6 +1222,9 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.dx0 = L.dx0;
             a.dx0_scale = L.dx0_scale;
             a.dinvl = L.dinvl;
+            a.fd = L.fd;
+            a.fd_mmax = sh.fd_mmax;
+            a.plan_wcap = (int)sh.region;
             cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
             if (e != cudaSuccess) return e;
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.smem, &a, s);

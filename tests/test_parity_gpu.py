@@ -170,7 +170,9 @@ def test_extrapolated_guess(sa, prec):
     tol = 1e-15 if p == sa.SA_FP64 else 1e-10
     iters = {}
     for g in (sa.SA_GUESS_PREVIOUS, sa.SA_GUESS_EXTRAPOLATE):
-        c = gpu_context(wl, p, pcg_tol=tol, initial_guess=g)
+        # Jacobi: with the fast-diagonalization preconditioner a box solves
+        # in one iteration from either start
+        c = gpu_context(wl, p, pcg_tol=tol, initial_guess=g, precond=sa.SA_PRECOND_JACOBI)
         c.step(wl.theta, wl.dt, 20)
         c.step(wl.theta, wl.dt, 0)
         st = c.step(wl.theta, wl.dt, 100)
@@ -402,3 +404,37 @@ def test_plate_with_hole_full_size_mixed_vs_fp64(sa):
     lhs = (M / dt + th * K) @ T1
     rhs = (M / dt - (1 - th) * K) @ T_prev + th * F1 + (1 - th) * F_prev
     assert np.linalg.norm((lhs - rhs)[free]) <= 1e-10 * np.linalg.norm(rhs[free])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fast_diagonalization_is_exact_on_a_box(sa, prec):
+    """On an affine box the fast-diagonalization preconditioner is A_ff^{-1}
+    (up to rounding): every theta-step solve stops after one iteration, with
+    the same steps as the oracle; Jacobi needs several."""
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    wl = W.cuboid_single_track(theta=0.5, n_steps=60)
+    err, ctx, m = _lockstep(sa, wl, p, 60, every=20, precond=sa.SA_PRECOND_FD)
+    if p == sa.SA_FP64:
+        assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+    else:
+        assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+    st = ctx.step(wl.theta, wl.dt, 20)
+    assert st.pcg_iters_max <= 2, st.pcg_iters_max
+    c = gpu_context(wl, p, pcg_tol=1e-15 if p == sa.SA_FP64 else 1e-10, precond=sa.SA_PRECOND_JACOBI)
+    c.step(wl.theta, wl.dt, 60)
+    stj = c.step(wl.theta, wl.dt, 20)
+    assert stj.pcg_iters_total > 2 * st.pcg_iters_total
+
+
+def test_fast_diagonalization_on_the_curved_closed_plate(sa):
+    """On the plate with a hole (curved, closed in xi) the preconditioner is
+    approximate: the steps match the oracle and the solves need far fewer
+    iterations than with Jacobi."""
+    wl = W.plate_with_hole(n_el=(8, 4, 2), n_steps=40)
+    err, ctx, m = _lockstep(sa, wl, sa.SA_FP64, 40, every=20, precond=sa.SA_PRECOND_FD)
+    assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+    st = ctx.step(wl.theta, wl.dt, 20)
+    c = gpu_context(wl, sa.SA_FP64, pcg_tol=1e-15, precond=sa.SA_PRECOND_JACOBI)
+    c.step(wl.theta, wl.dt, 40)
+    stj = c.step(wl.theta, wl.dt, 20)
+    assert 2 * st.pcg_iters_total < stj.pcg_iters_total, (st.pcg_iters_total, stj.pcg_iters_total)
