@@ -13,9 +13,10 @@ A "step" is one theta-step of the whole hot path: source coefficients,
 history sums at every boundary quadrature point, boundary integrals, bottom
 projection, theta right-hand side, PCG.  ``value`` is theta-steps/s of the
 mixed path (FP32 history sum and operator values; FP64 state, boundary
-integrals and Krylov vectors) with extrapolated initial guesses, replayed as
-CUDA graphs with the inputs resident in HBM.  Timed beside it: the same path
-started from T^n, and the plain FP64 path.
+integrals and Krylov vectors; fast-diagonalization preconditioners, solves
+started from T^n), replayed as CUDA graphs with the inputs resident in HBM.
+Timed beside it: the same path with extrapolated initial guesses, with the
+Jacobi preconditioner, and the plain FP64 path.
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
 bounded sample of the same step.
@@ -57,7 +58,7 @@ def parse():
                     help="first timed step; default: the timed steps are centred on step 5,840")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="path timed in the main region")
-    ap.add_argument("--guess", default="extrapolate", choices=["extrapolate", "previous"],
+    ap.add_argument("--guess", default="previous", choices=["extrapolate", "previous"],
                     help="initial guess of the theta-step solves in the main region")
     ap.add_argument("--quick", action="store_true",
                     help="main timed region only (no stage, FP64, e2e or CPU legs): "
@@ -317,15 +318,24 @@ def run_ours(args):
     pairs_t = q_pts * (min(state[0] + 3 + K_t // 2, sz.n_src))
     ctx_t.close()
 
-    # ---- same path from x0 = T^n (no extrapolation), and the plain FP64 path
+    # ---- the other initial guess, Jacobi, and the plain FP64 path
     K_c = min(K, 60)
-    ctx_c = fresh(prec, sa.SA_GUESS_PREVIOUS, use_graph=1)
+    other = sa.SA_GUESS_EXTRAPOLATE if guess == sa.SA_GUESS_PREVIOUS else sa.SA_GUESS_PREVIOUS
+    ctx_c = fresh(prec, other, use_graph=1)
     ctx_c.step(th, dt, 3)
     ctx_c.step(th, dt, 0)
     ms_c = time_graph(ctx_c, th, dt, K_c, stream)
     st_c = ctx_c.step(th, dt, 0)
     cold_steps = K_c / (ms_c / 1e3)
     ctx_c.close()
+    # the same path with the Jacobi preconditioner
+    ctx_j = fresh(prec, guess, use_graph=1, precond=sa.SA_PRECOND_JACOBI)
+    ctx_j.step(th, dt, 3)
+    ctx_j.step(th, dt, 0)
+    ms_j = time_graph(ctx_j, th, dt, K_c, stream)
+    st_j = ctx_j.step(th, dt, 0)
+    jacobi_steps = K_c / (ms_j / 1e3)
+    ctx_j.close()
     K64 = min(K, 12)
     ctx64 = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1)
     ctx64.step(th, dt, 2)
@@ -359,8 +369,11 @@ def run_ours(args):
     warm = 1 if guess == sa.SA_GUESS_EXTRAPOLATE else 0
     # algorithmic bytes of one main-solve launch: every SpMV reads the FP32
     # values and 16-bit column offsets once and the published vector once;
-    # set-up reads r0, b^2, D^{-1} (FP64 and FP32), reads and writes x
-    pcg_bytes = (iters_t + warm) * (6 * nnz_a + 4 * n_free) + (44 + 4 * warm) * n_free
+    # set-up reads r0, b^2, D^{-1} (FP64 and FP32), reads and writes x;
+    # fast diagonalization: each application (one at set-up, one per further
+    # iteration) reads and writes the FP32 vector in five line passes
+    pcg_bytes = ((iters_t + warm) * (6 * nnz_a + 4 * n_free) + (44 + 4 * warm) * n_free +
+                 max(iters_t, 1.0) * 5 * 8 * n_free)
     # history: FP32 lane-operations per pair (flux 8, T 6) on 128 FP32
     # lanes/clk/SM; MUFU ex2 (32/clk/SM) is not binding
     pairs_clk = 128.0 * q_pts / (8 * sz.q_lat + 6 * sz.q_bot)
@@ -400,12 +413,16 @@ def run_ours(args):
                    "precision": "mixed: FP32 history sum and operator values, FP64 state, "
                                 "boundary integrals and Krylov vectors",
                    "initial_guess": args.guess,
+                   "preconditioner": "fast diagonalization (main solve and bottom projection)",
                    "l2": "no flush: per-step inputs larger than L2 (operators in SELL-32: "
                          "~170 MB of FP32 values and indices; 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "point_source_evals_per_s": evals,
-        "steps_per_s_guess_previous": world * cold_steps,
-        "pcg_iters_per_step_guess_previous": st_c.pcg_iters_total / K_c,
+        "steps_per_s_other_guess": world * cold_steps,
+        "pcg_iters_per_step_other_guess": st_c.pcg_iters_total / K_c,
+        "other_guess": "extrapolate" if other == sa.SA_GUESS_EXTRAPOLATE else "previous",
+        "steps_per_s_jacobi": world * jacobi_steps,
+        "pcg_iters_per_step_jacobi": st_j.pcg_iters_total / K_c,
         "fp64_steps_per_s": world * fp64_steps,
         "mixed_over_fp64": value / (world * fp64_steps),
         "pcg_iters_per_step": iters_avg, "bot_iters_per_step": bot_avg,

@@ -932,7 +932,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         if (c->opt.precond != SA_PRECOND_JACOBI) {
             sa_status fst = fd_setup(c);
             if (fst) return fst;
-            if (c->opt.precond == SA_PRECOND_FD && !c->fd_ok)
+            if (c->opt.precond == SA_PRECOND_FD && !c->fdm.ok)
                 return sa_fail(c, SA_ERR_ARG, "fast diagonalization needs the tensor grid of free "
                                               "control variables with at most 128 per direction");
             if (c->opt.precond == SA_PRECOND_FD && c->opt.pcg_variant == SA_PCG_GLOBAL)
@@ -943,7 +943,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             L.op = sell_view(c->a_s);
             L.pad = c->work_pad;
             L.grid = c->pcg_grid;
-            L.fd = fd_view(c);
+            L.fd = fd_view(c, c->fdm);
             if (!pcg_shared_fits(c->opt.precision, L))
                 return sa_fail(c, SA_ERR_ARG,
                                "shared-memory PCG: %d rows per block do not fit in shared memory",
@@ -1113,6 +1113,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.variant = c->opt.pcg_variant;
+        L.fd = fd_view(c, c->fdb);
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
@@ -1171,7 +1172,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.variant = c->opt.pcg_variant;
-        L.fd = fd_view(c);
+        L.fd = fd_view(c, c->fdm);
         L.which = 0;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;

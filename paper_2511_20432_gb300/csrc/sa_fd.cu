@@ -180,8 +180,9 @@ __global__ void k_fd_scale(int n, int m0, int m1, const double* md0, const doubl
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n) return;
     const int i = f % m0, j = (f / m0) % m1, k = f / (m0 * m1);
-    const double d = cM * md0[i] * md1[j] * md2[k] + c0 * kd0[i] * md1[j] * md2[k] +
-                     c1 * md0[i] * kd1[j] * md2[k] + c2 * md0[i] * md1[j] * kd2[k];
+    const double mz = md2 ? md2[k] : 1.0, kz = kd2 ? kd2[k] : 0.0;
+    const double d = cM * md0[i] * md1[j] * mz + c0 * kd0[i] * md1[j] * mz +
+                     c1 * md0[i] * kd1[j] * mz + c2 * md0[i] * md1[j] * kz;
     const double sc = sqrt(d * dinv[f]);
     if (f32)
         ((float*)S)[f] = (float)sc;
@@ -197,148 +198,192 @@ cudaError_t upload_as(DBuf<unsigned char>& buf, const std::vector<double>& v) {
     return cudaMemcpy(buf.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-}  // namespace
-
-// Geometry part (once per patch): 1-D matrices, eigenpairs, mean lengths.
-sa_status fd_setup(sa_ctx* c) {
-    c->fd_ok = false;
-    const int nfree_dir[3][2] = {{c->face_kind[0] == SA_FACE_DIRICHLET, c->face_kind[1] == SA_FACE_DIRICHLET},
-                                 {c->face_kind[2] == SA_FACE_DIRICHLET, c->face_kind[3] == SA_FACE_DIRICHLET},
-                                 {c->face_kind[4] == SA_FACE_DIRICHLET, c->face_kind[5] == SA_FACE_DIRICHLET}};
-    long long prod = 1;
-    for (int d = 0; d < 3; ++d) {
-        const int n = c->n[d], p = c->p[d];
-        std::vector<double> M, K;
-        matrices_1d(c->U[d], p, n, M, K);
-        // closed direction: fold index n-1 into 0
-        int nd = n;
-        if (c->seam == d) {
-            nd = n - 1;
-            std::vector<double> Mf((size_t)nd * nd, 0.0), Kf((size_t)nd * nd, 0.0);
-            for (int a = 0; a < n; ++a)
-                for (int b = 0; b < n; ++b) {
-                    const int A = a % nd, B = b % nd;
-                    Mf[(size_t)A * nd + B] += M[(size_t)a * n + b];
-                    Kf[(size_t)A * nd + B] += K[(size_t)a * n + b];
-                }
-            M.swap(Mf);
-            K.swap(Kf);
-        }
-        // free indices: drop the Dirichlet end layers
-        const int lo = nfree_dir[d][0] ? 1 : 0, hi = nd - (nfree_dir[d][1] ? 1 : 0);
-        const int m = hi - lo;
-        if (m <= 0 || m > 128) return SA_OK;   // the device passes hold 4 entries per lane
-        std::vector<double> Mr((size_t)m * m), Kr((size_t)m * m);
-        for (int a = 0; a < m; ++a)
-            for (int b = 0; b < m; ++b) {
-                Mr[(size_t)a * m + b] = M[(size_t)(a + lo) * nd + (b + lo)];
-                Kr[(size_t)a * m + b] = K[(size_t)(a + lo) * nd + (b + lo)];
+// 1-D data of parametric direction d: matrices on the knot vector, the seam
+// folded, the end layers dropped (drop_lo / drop_hi), eigenpairs; the mean
+// control-polygon length.  False when not usable.
+bool direction_data(const sa_ctx* c, int d, bool drop_lo, bool drop_hi, FdData& f, int slot) {
+    const int n = c->n[d], p = c->p[d];
+    std::vector<double> M, K;
+    matrices_1d(c->U[d], p, n, M, K);
+    int nd = n;
+    if (c->seam == d) {   // fold index n-1 into 0
+        nd = n - 1;
+        std::vector<double> Mf((size_t)nd * nd, 0.0), Kf((size_t)nd * nd, 0.0);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                Mf[(size_t)(a % nd) * nd + (b % nd)] += M[(size_t)a * n + b];
+                Kf[(size_t)(a % nd) * nd + (b % nd)] += K[(size_t)a * n + b];
             }
-        std::vector<double> U, lam;
-        if (!gen_eig(m, Mr, Kr, U, lam)) return SA_OK;   // not usable: Jacobi stays
-        c->fd_m[d] = m;
-        c->fd_U[d] = U;
-        c->fd_lam[d] = lam;
-        c->fd_md[d].resize(m);
-        c->fd_kd[d].resize(m);
-        for (int a = 0; a < m; ++a) {
-            c->fd_md[d][a] = Mr[(size_t)a * m + a];
-            c->fd_kd[d][a] = Kr[(size_t)a * m + a];
-        }
-        prod *= m;
-        // mean control-polygon length along d
-        const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
-        const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
-        double sum = 0.0;
-        int lines = 0;
-        for (int ib = 0; ib < c->n[tb]; ++ib)
-            for (int ia = 0; ia < c->n[ta]; ++ia) {
-                double len = 0.0;
-                for (int a = 0; a + 1 < n; ++a) {
-                    int i0[3], i1[3];
-                    i0[d] = a;
-                    i1[d] = a + 1;
-                    i0[ta] = i1[ta] = ia;
-                    i0[tb] = i1[tb] = ib;
-                    const double* P0 = &c->ctrl[3 * ((i0[2] * n1 + i0[1]) * n0 + i0[0])];
-                    const double* P1 = &c->ctrl[3 * ((i1[2] * n1 + i1[1]) * n0 + i1[0])];
-                    len += std::sqrt((P1[0] - P0[0]) * (P1[0] - P0[0]) + (P1[1] - P0[1]) * (P1[1] - P0[1]) +
-                                     (P1[2] - P0[2]) * (P1[2] - P0[2]));
-                }
-                sum += len;
-                ++lines;
-            }
-        c->fd_L[d] = sum / std::max(lines, 1);
-        if (!(c->fd_L[d] > 0.0)) return SA_OK;
+        M.swap(Mf);
+        K.swap(Kf);
     }
-    if (prod != c->n_free) return SA_OK;   // the free set is not the tensor grid
+    const int lo = drop_lo ? 1 : 0, hi = nd - (drop_hi ? 1 : 0);
+    const int m = hi - lo;
+    if (m <= 0 || m > 128) return false;   // the device passes hold 4 entries per lane
+    std::vector<double> Mr((size_t)m * m), Kr((size_t)m * m);
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            Mr[(size_t)a * m + b] = M[(size_t)(a + lo) * nd + (b + lo)];
+            Kr[(size_t)a * m + b] = K[(size_t)(a + lo) * nd + (b + lo)];
+        }
+    std::vector<double> U, lam;
+    if (!gen_eig(m, Mr, Kr, U, lam)) return false;
+    f.m[slot] = m;
+    f.U[slot] = U;
+    f.lam[slot] = lam;
+    f.md[slot].resize(m);
+    f.kd[slot].resize(m);
+    for (int a = 0; a < m; ++a) {
+        f.md[slot][a] = Mr[(size_t)a * m + a];
+        f.kd[slot][a] = Kr[(size_t)a * m + a];
+    }
+    const int n0 = c->n[0], n1 = c->n[1];
+    const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;
+    double sum = 0.0;
+    int lines = 0;
+    for (int ib = 0; ib < c->n[tb]; ++ib)
+        for (int ia = 0; ia < c->n[ta]; ++ia) {
+            double len = 0.0;
+            for (int a = 0; a + 1 < n; ++a) {
+                int i0[3], i1[3];
+                i0[d] = a;
+                i1[d] = a + 1;
+                i0[ta] = i1[ta] = ia;
+                i0[tb] = i1[tb] = ib;
+                const double* P0 = &c->ctrl[3 * ((i0[2] * n1 + i0[1]) * n0 + i0[0])];
+                const double* P1 = &c->ctrl[3 * ((i1[2] * n1 + i1[1]) * n0 + i1[0])];
+                len += std::sqrt((P1[0] - P0[0]) * (P1[0] - P0[0]) + (P1[1] - P0[1]) * (P1[1] - P0[1]) +
+                                 (P1[2] - P0[2]) * (P1[2] - P0[2]));
+            }
+            sum += len;
+            ++lines;
+        }
+    f.L[slot] = sum / std::max(lines, 1);
+    return f.L[slot] > 0.0;
+}
+
+sa_status upload_fd(sa_ctx* c, FdData& f, int n_rows) {
     const bool f32 = c->opt.precision == SA_MIXED;
-    for (int d = 0; d < 3; ++d) {
-        const int m = c->fd_m[d];
+    for (int d = 0; d < f.nd; ++d) {
+        const int m = f.m[d];
         std::vector<double> Ut((size_t)m * m);
         for (int a = 0; a < m; ++a)
-            for (int o = 0; o < m; ++o) Ut[(size_t)a * m + o] = c->fd_U[d][(size_t)o * m + a];
-        cudaError_t e = f32 ? upload_as<float>(c->fdU[d], c->fd_U[d]) : upload_as<double>(c->fdU[d], c->fd_U[d]);
-        if (e == cudaSuccess) e = f32 ? upload_as<float>(c->fdUt[d], Ut) : upload_as<double>(c->fdUt[d], Ut);
-        if (e == cudaSuccess) e = c->fdlamc[d].alloc((size_t)m * (f32 ? 4 : 8));
-        if (e == cudaSuccess) e = upload_as<double>(c->fdmd[d], c->fd_md[d]);
-        if (e == cudaSuccess) e = upload_as<double>(c->fdkd[d], c->fd_kd[d]);
+            for (int o = 0; o < m; ++o) Ut[(size_t)a * m + o] = f.U[d][(size_t)o * m + a];
+        cudaError_t e = f32 ? upload_as<float>(f.dU[d], f.U[d]) : upload_as<double>(f.dU[d], f.U[d]);
+        if (e == cudaSuccess) e = f32 ? upload_as<float>(f.dUt[d], Ut) : upload_as<double>(f.dUt[d], Ut);
+        if (e == cudaSuccess) e = f.dlamc[d].alloc((size_t)m * (f32 ? 4 : 8));
+        if (e == cudaSuccess) e = upload_as<double>(f.dmd[d], f.md[d]);
+        if (e == cudaSuccess) e = upload_as<double>(f.dkd[d], f.kd[d]);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return sa_fail(c, SA_ERR_OOM, "fast-diagonalization data");
         }
     }
-    cudaError_t e = c->fdS.alloc((size_t)std::max(c->n_free, 1) * (f32 ? 4 : 8));
-    if (e == cudaSuccess) e = c->fdZ.alloc((size_t)std::max(c->n_free, 1) * (f32 ? 4 : 8));
+    cudaError_t e = f.S.alloc((size_t)std::max(n_rows, 1) * (f32 ? 4 : 8));
+    if (e == cudaSuccess) e = f.Z.alloc((size_t)std::max(n_rows, 1) * (f32 ? 4 : 8));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return sa_fail(c, SA_ERR_OOM, "fast-diagonalization vectors");
     }
-    c->fd_ok = true;
+    f.ok = true;
     return SA_OK;
 }
 
-// Operator part (per theta, dt): the scalings c_M, c_d, c_d lambda_d and S.
-cudaError_t fd_prepare(sa_ctx* c, double theta, double dt, cudaStream_t s) {
-    if (!c->fd_ok) return cudaSuccess;
-    const double vol = c->fd_L[0] * c->fd_L[1] * c->fd_L[2];
-    c->fd_cM = c->rho * c->cp * vol / dt;
-    for (int d = 0; d < 3; ++d) c->fd_c[d] = theta * c->k * vol / (c->fd_L[d] * c->fd_L[d]);
-    const bool f32 = c->opt.precision == SA_MIXED;
-    for (int d = 0; d < 3; ++d) {
-        std::vector<double> lc(c->fd_lam[d]);
-        for (double& x : lc) x *= c->fd_c[d];
-        cudaError_t e;
-        if (f32) {
-            std::vector<float> h(lc.begin(), lc.end());
-            e = cudaMemcpyAsync(c->fdlamc[d].p, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        } else {
-            e = cudaMemcpyAsync(c->fdlamc[d].p, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+}  // namespace
+
+// Geometry part (once per patch): 1-D matrices, eigenpairs, mean lengths,
+// for the free control variables (3-D) and for the bottom Dirichlet layer
+// (2-D, the projection's mass matrix) when that layer is the whole
+// Dirichlet set.
+sa_status fd_setup(sa_ctx* c) {
+    c->fdm.ok = c->fdb.ok = false;
+    bool dir[6];
+    for (int f = 0; f < 6; ++f) dir[f] = c->face_kind[f] == SA_FACE_DIRICHLET;
+    {
+        FdData& f = c->fdm;
+        f.nd = 3;
+        bool ok = true;
+        long long prod = 1;
+        for (int d = 0; d < 3 && ok; ++d) {
+            ok = direction_data(c, d, dir[2 * d], dir[2 * d + 1], f, d);
+            prod *= f.m[d];
         }
-        if (e != cudaSuccess) return e;
+        if (ok && prod == c->n_free) {
+            sa_status st = upload_fd(c, f, c->n_free);
+            if (st) return st;
+        }
     }
-    if (c->n_free == 0) return cudaSuccess;
-    k_fd_scale<<<(c->n_free + 255) / 256, 256, 0, s>>>(
-        c->n_free, c->fd_m[0], c->fd_m[1], (const double*)c->fdmd[0].p, (const double*)c->fdkd[0].p,
-        (const double*)c->fdmd[1].p, (const double*)c->fdkd[1].p, (const double*)c->fdmd[2].p,
-        (const double*)c->fdkd[2].p, c->fd_cM, c->fd_c[0], c->fd_c[1], c->fd_c[2], c->a_dinv.p,
-        c->fdS.p, f32 ? 1 : 0);
-    return cudaGetLastError();
+    const bool bottom_only = dir[4] && !dir[0] && !dir[1] && !dir[2] && !dir[3] && !dir[5];
+    if (bottom_only && c->seam != 2) {
+        FdData& f = c->fdb;
+        f.nd = 2;
+        f.m[2] = 1;
+        f.L[2] = 1.0;
+        const bool ok = direction_data(c, 0, false, false, f, 0) && direction_data(c, 1, false, false, f, 1);
+        if (ok && (long long)f.m[0] * f.m[1] == c->n_dir) {
+            f.md[2].assign(1, 1.0);
+            f.kd[2].assign(1, 0.0);
+            sa_status st = upload_fd(c, f, c->n_dir);
+            if (st) return st;
+        }
+    }
+    return SA_OK;
 }
 
-FdView fd_view(const sa_ctx* c) {
-    FdView v{};
-    v.on = c->fd_ok && c->opt.precond != SA_PRECOND_JACOBI;
-    for (int d = 0; d < 3; ++d) {
-        v.m[d] = c->fd_m[d];
-        v.U[d] = c->fdU[d].p;
-        v.Ut[d] = c->fdUt[d].p;
-        v.lamc[d] = c->fdlamc[d].p;
+// Operator part (per theta, dt): the scalings and S.  Main solve:
+// c_M = rho c_p L0 L1 L2 / dt, c_d = theta k L0 L1 L2 / L_d^2.  Bottom
+// projection (the face mass matrix): c_M = L0 L1, no stiffness.
+cudaError_t fd_prepare(sa_ctx* c, double theta, double dt, cudaStream_t s) {
+    const bool f32 = c->opt.precision == SA_MIXED;
+    for (int which = 0; which < 2; ++which) {
+        FdData& f = which == 0 ? c->fdm : c->fdb;
+        if (!f.ok) continue;
+        const int n = which == 0 ? c->n_free : c->n_dir;
+        if (which == 0) {
+            const double vol = f.L[0] * f.L[1] * f.L[2];
+            f.cM = c->rho * c->cp * vol / dt;
+            for (int d = 0; d < 3; ++d) f.c[d] = theta * c->k * vol / (f.L[d] * f.L[d]);
+        } else {
+            f.cM = f.L[0] * f.L[1];
+            f.c[0] = f.c[1] = f.c[2] = 0.0;
+        }
+        for (int d = 0; d < f.nd; ++d) {
+            std::vector<double> lc(f.lam[d]);
+            for (double& x : lc) x *= f.c[d];
+            cudaError_t e;
+            if (f32) {
+                std::vector<float> h(lc.begin(), lc.end());
+                e = cudaMemcpy(f.dlamc[d].p, h.data(), h.size() * 4, cudaMemcpyHostToDevice);
+            } else {
+                e = cudaMemcpy(f.dlamc[d].p, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice);
+            }
+            if (e != cudaSuccess) return e;
+        }
+        if (n == 0) continue;
+        const double* md2 = f.nd == 3 ? (const double*)f.dmd[2].p : nullptr;
+        const double* kd2 = f.nd == 3 ? (const double*)f.dkd[2].p : nullptr;
+        k_fd_scale<<<(n + 255) / 256, 256, 0, s>>>(
+            n, f.m[0], f.m[1], (const double*)f.dmd[0].p, (const double*)f.dkd[0].p,
+            (const double*)f.dmd[1].p, (const double*)f.dkd[1].p, md2, kd2, f.cM, f.c[0], f.c[1],
+            f.c[2], which == 0 ? c->a_dinv.p : c->mbot_dinv.p, f.S.p, f32 ? 1 : 0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    v.cM = c->fd_cM;
-    v.S = c->fdS.p;
-    v.Z = c->fdZ.p;
+    return cudaSuccess;
+}
+
+FdView fd_view(const sa_ctx* c, const FdData& f) {
+    FdView v{};
+    v.on = f.ok && c->opt.precond != SA_PRECOND_JACOBI;
+    v.nd = f.nd;
+    for (int d = 0; d < 3; ++d) {
+        v.m[d] = f.m[d];
+        v.U[d] = f.dU[d].p;
+        v.Ut[d] = f.dUt[d].p;
+        v.lamc[d] = f.dlamc[d].p;
+    }
+    v.cM = f.cM;
+    v.S = f.S.p;
+    v.Z = f.Z.p;
     return v;
 }

@@ -155,6 +155,7 @@ inline SellView sell_view(const SellDev& s) {
 // pointers in the operator precision; m[d] free sizes per direction).
 struct FdView {
     bool on;
+    int nd;                // 3 (passes 0 1 2f 1 0) or 2 (passes 0 1f 0)
     int m[3];
     const void* U[3];      // m x m row-major: U[a][o] (columns = eigenvectors)
     const void* Ut[3];     // transposes
@@ -162,6 +163,19 @@ struct FdView {
     double cM;
     const void* S;         // n_free diagonal scaling
     void* Z;               // n_free work vector
+};
+
+// Host and device data of one fast-diagonalization preconditioner over an
+// nd-dimensional grid of control variables (m[d] per direction, m[2] = 1 for
+// nd = 2): eigenvectors U_d (U_d^T M^_d U_d = I), eigenvalues, the diagonals
+// of M^_d and K^_d, mean lengths, the scalings of the current (theta, dt).
+struct FdData {
+    bool ok = false;
+    int nd = 3;
+    int m[3] = {1, 1, 1};
+    double L[3] = {0, 0, 0}, cM = 0, c[3] = {0, 0, 0};
+    std::vector<double> U[3], lam[3], md[3], kd[3];
+    DBuf<unsigned char> dU[3], dUt[3], dlamc[3], dmd[3], dkd[3], S, Z;
 };
 
 // Arguments of one PCG solve.
@@ -334,12 +348,9 @@ struct sa_ctx {
     SellHost a_h, r_h, mbot_h;
     std::vector<int> wlat_rowdof_h, wlat_ptr_h, wlat_col_h, wbot_ptr_h, wbot_col_h;
 
-    // fast-diagonalization preconditioner (csrc/sa_fd.cu)
-    bool fd_ok = false;
-    int fd_m[3] = {0, 0, 0};
-    double fd_L[3] = {0, 0, 0}, fd_cM = 0, fd_c[3] = {0, 0, 0};
-    std::vector<double> fd_U[3], fd_lam[3], fd_md[3], fd_kd[3];
-    DBuf<unsigned char> fdU[3], fdUt[3], fdlamc[3], fdmd[3], fdkd[3], fdS, fdZ;
+    // fast-diagonalization preconditioners (csrc/sa_fd.cu): the main solve
+    // (3-D) and the bottom projection (2-D)
+    FdData fdm, fdb;
 
     // extrapolated initial guesses (sa_options::initial_guess)
     DBuf<double> x_prev;             // T^{n-1}: free part, then the Dirichlet part
@@ -452,7 +463,7 @@ cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tpr
                           double* gprev, double* g0, cudaStream_t s);
 sa_status fd_setup(sa_ctx* c);
 cudaError_t fd_prepare(sa_ctx* c, double theta, double dt, cudaStream_t s);
-FdView fd_view(const sa_ctx* c);
+FdView fd_view(const sa_ctx* c, const FdData& f);
 void gauss_legendre(int n, double* x, double* w);
 // Whether the shared-memory PCG of this launch keeps its rows in shared memory.
 bool pcg_shared_fits(int precision, const PcgLaunch& L);

@@ -780,11 +780,9 @@ constexpr int kFdPerLane = 4;   // line entries per lane: lines of at most 128
 // least m^2 entries; the SpMV window is idle here).  Lines have at most 128
 // entries (4 per lane).
 template <typename VT>
-__device__ void fd_stage(VT* wbuf, const VT* W, int m) {
-    __syncthreads();                       // the previous pass is done with wbuf
+__device__ __forceinline__ void fd_stage(VT* wbuf, const VT* W, int m) {
     const int mm = m * m;
     for (int t = threadIdx.x; t < mm; t += blockDim.x) wbuf[t] = __ldg(W + t);
-    __syncthreads();
 }
 
 template <typename VT>
@@ -807,41 +805,49 @@ __device__ __forceinline__ void fd_line_matvec(const VT* Wb, const VT* xs, int m
 template <typename VT>
 __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* xs, VT* out) {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // lines go to warp w of every block before warp w + 1 of any: spread over SMs
+    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * (blockDim.x >> 5);
+    const int nd = fd.nd;                  // 3: passes 0 1 2f 1 0; 2: passes 0 1f 0
+    const int npass = 2 * nd - 1;
     const int m0 = fd.m[0], m1 = fd.m[1], m2 = fd.m[2];
+    const int mmax = max(m0, max(m1, m2));
     VT* Z = (VT*)fd.Z;
     const VT* S = (const VT*)fd.S;
     const VT* l0 = (const VT*)fd.lamc[0];
     const VT* l1 = (const VT*)fd.lamc[1];
-    const VT* l2 = (const VT*)fd.lamc[2];
+    const VT* ll = (const VT*)fd.lamc[nd - 1];
     const VT cM = (VT)fd.cM;
-    for (int pass = 0; pass < 5; ++pass) {
-        const int d = pass < 3 ? pass : 4 - pass;           // directions 0 1 2 1 0
+    for (int pass = 0; pass < npass; ++pass) {
+        const int d = pass < nd ? pass : npass - 1 - pass;
+        const bool fused = pass == nd - 1;
         const int m = fd.m[d];
         const int stride = d == 0 ? 1 : (d == 1 ? m0 : m0 * m1);
         const int nlines = (m0 * m1 * m2) / m;
-        const bool busy = blockIdx.x * (blockDim.x >> 5) < nlines;   // block has lines
-        // y[o] = sum_a W[a][o] x[a]: W = U_d (applies U_d^T) or U_d^T (applies U_d)
-        if (busy) fd_stage(wbuf, (const VT*)(pass < 3 ? fd.U[d] : fd.Ut[d]), m);
+        // y[o] = sum_a W[a][o] x[a]: W = U_d (applies U_d^T) or U_d^T (applies
+        // U_d), staged in wbuf + (pass & 1) mmax^2: the first by itself, the
+        // next ones while the block waits at the grid barrier
+        VT* Wb = wbuf + (pass & 1) * mmax * mmax;
+        if (pass == 0) fd_stage(Wb, (const VT*)fd.U[0], m);
+        __syncthreads();
         for (int L = gw; L < nlines; L += nw) {
             const int base = d == 0 ? L * m0 : (d == 1 ? (L / m0) * (m0 * m1) + (L % m0) : L);
             for (int a = lane; a < m; a += 32) xs[a] = __ldcg(Z + base + (long long)a * stride);
             __syncwarp();
             VT y[kFdPerLane];
-            fd_line_matvec(wbuf, xs, m, lane, y);
-            if (pass == 2) {
-                // D = 1 / (c_M + c_0 lambda_0[i] + c_1 lambda_1[j] + c_2 lambda_2[k]),
-                // then U_2 (from global: wbuf holds U_2) on the same line
-                const VT li = cM + l0[L % m0] + l1[L / m0];
+            fd_line_matvec(Wb, xs, m, lane, y);
+            if (fused) {
+                // D = 1 / (c_M + sum_d c_d lambda_d), then U on the same line
+                // (the last direction's U^T from global memory)
+                const VT li = cM + l0[L % m0] + (nd == 3 ? l1[L / m0] : (VT)0);
                 __syncwarp();
 #pragma unroll
                 for (int t = 0; t < kFdPerLane; ++t) {
                     const int o = lane + 32 * t;
-                    if (o < m) xs[o] = y[t] / (li + l2[o]);
+                    if (o < m) xs[o] = y[t] / (li + ll[o]);
                 }
                 __syncwarp();
-                const VT* W2 = (const VT*)fd.Ut[2];
+                const VT* W2 = (const VT*)fd.Ut[d];
 #pragma unroll
                 for (int t = 0; t < kFdPerLane; ++t) y[t] = (VT)0;
 #pragma unroll 4
@@ -861,7 +867,7 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
                 const int o = lane + 32 * t;
                 if (o < m) {
                     const long long idx = base + (long long)o * stride;
-                    if (pass == 4)
+                    if (pass == npass - 1)
                         out[idx] = S[idx] * y[t];
                     else
                         Z[idx] = y[t];
@@ -869,7 +875,12 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
             }
             __syncwarp();
         }
-        if (pass < 4 && !sync.barrier()) return false;
+        if (pass < npass - 1) {
+            const int np = pass + 1;
+            const int dn = np < nd ? np : npass - 1 - np;
+            fd_stage(wbuf + (np & 1) * mmax * mmax, (const VT*)(np < nd ? fd.U[dn] : fd.Ut[dn]), fd.m[dn]);
+            if (!sync.barrier()) return false;
+        }
     }
     return true;
 }
@@ -1177,7 +1188,7 @@ PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
     sh.wl = 32ll * sh.spb + (L.op.dmax - L.op.dmin) + 8;
     // the preconditioner's m x m matrix reuses the window region
     const int mmax = (pipelined && L.fd.on) ? std::max(L.fd.m[0], std::max(L.fd.m[1], L.fd.m[2])) : 0;
-    const long long fdw = (long long)mmax * mmax;
+    const long long fdw = 2ll * mmax * mmax;   // two staged matrices
     sh.fd_mmax = mmax;
     const size_t fixed = 1024 * sizeof(VT) +
                          (pipelined ? (size_t)kSmemVecs * sh.rcap * sizeof(double) + 2 * sh.rcap * sizeof(VT) +

@@ -282,7 +282,7 @@ def test_errors_are_reported(sa):
     assert e.value.status == sa.SA_ERR_ARG
     # a capped PCG reports non-convergence and the context stays usable
     # (the first steps carry no flux to the walls and converge at iteration 0)
-    c3 = gpu_context(wl, sa.SA_FP64, pcg_max_iter=1, pcg_tol=1e-15)
+    c3 = gpu_context(wl, sa.SA_FP64, pcg_max_iter=1, pcg_tol=1e-15, precond=sa.SA_PRECOND_JACOBI)
     with pytest.raises(sa.SAError) as e:
         c3.step(0.5, wl.dt, 80)
     assert e.value.status == sa.SA_ERR_NOT_CONVERGED
