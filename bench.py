@@ -60,6 +60,9 @@ def parse():
                     help="path timed in the main region")
     ap.add_argument("--guess", default="previous", choices=["extrapolate", "previous"],
                     help="initial guess of the theta-step solves in the main region")
+    ap.add_argument("--learned-pairs", type=int, default=2000,
+                    help="training pairs of the learned warm-start leg (0: skip the leg)")
+    ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--quick", action="store_true",
                     help="main timed region only (no stage, FP64, e2e or CPU legs): "
                          "the form used under ncu")
@@ -230,6 +233,120 @@ def cpu_baseline_block(wl, n, seconds_target=10.0):
 
 
 # ---------------------------------------------------------------------------
+# learned warm start on the block mesh: training pairs from seeded meanders
+# (random hatch angle and spacing, power, speed), evaluated on the benchmark
+# scan at the benchmark state
+# ---------------------------------------------------------------------------
+def boundary_inputs(patch):
+    """Free control variables on the lateral faces and in the first free
+    layer above the bottom (internal free order: natural order without the
+    bottom layer): the rows of r0 the network reads."""
+    n0, n1, n2 = patch.n_ctrl
+    idx = [(k * n1 + j) * n0 + i - n0 * n1 for k in range(1, n2) for j in range(n1) for i in range(n0)
+           if k == 1 or i in (0, n0 - 1) or j in (0, n1 - 1)]
+    return idx
+
+
+def learned_leg(sa, W, wl, state, stream, n_pairs, epochs, K_eval):
+    import numpy as np
+    import torch
+    th, dt = wl.theta, wl.dt
+    idx = np.array(boundary_inputs(wl.patch), dtype=np.int32)
+    probe = sa.context_from_workload(wl, precision=sa.SA_MIXED)
+    n_free = probe.sizes().n_free
+    probe.close()
+    n_scans = 4
+    per = max(1, n_pairs // n_scans)
+    X = torch.empty((per * n_scans, len(idx)), dtype=torch.bfloat16, device="cuda")
+    Y = torch.empty((per * n_scans, n_free), dtype=torch.bfloat16, device="cuda")
+    t0 = time.perf_counter()
+    row = 0
+    for k in range(n_scans):
+        rng = W.SplitMix64(W.SEED_BASE + 4000 + k)
+        P, v = rng.uniform(150.0, 350.0), rng.uniform(0.6, 1.6)
+        hatch, n_tr = rng.uniform(0.08e-3, 0.12e-3), rng.randint(5, 20)
+        angle = rng.uniform(0.0, np.pi)
+        y0 = 2.0e-3 - 0.5 * (n_tr - 1) * hatch
+        scan = W.meander(0.8e-3, 3.2e-3, y0, hatch, n_tr, 1.0e-3, P, 0.4, v, angle=angle,
+                         center=(2.0e-3, 2.0e-3))
+        wtr = W.Workload(f"train_{k}", wl.patch, wl.material, scan, dt=dt, theta=th, n_steps=10 ** 6)
+        c = sa.context_from_workload(wtr, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
+        c.step(th, dt, 200)
+        c.set_recorder(X[row:row + per], Y[row:row + per], idx)
+        c.step(th, dt, per)
+        row += c.recorded()
+        c.set_recorder(None, None, None)
+        c.close()
+    t_rec = time.perf_counter() - t0
+    net = sa.MLP(len(idx), 256, n_free, seed=7)
+    t0 = time.perf_counter()
+    loss = None
+    for ep in range(epochs):
+        perm = torch.randperm(row, device="cuda")
+        for b in range(0, row, 64):
+            sel = perm[b:b + 64]
+            net.train_step(X[sel].contiguous(), Y[sel].contiguous(), 1e-3, want_loss=False)
+    torch.cuda.synchronize()
+    loss, _ = net.gradients(X[:64].contiguous(), Y[:64].contiguous())
+    t_train = time.perf_counter() - t0
+    out = {"training_pairs": row, "epochs": epochs, "record_s": t_rec, "train_s": t_train,
+           "final_minibatch_loss": loss, "n_in": int(len(idx)), "hidden": 256, "n_out": n_free,
+           "params": net.n_params(), "evaluation": {}}
+    for pre_name, pre in (("jacobi", sa.SA_PRECOND_JACOBI), ("fd", sa.SA_PRECOND_AUTO)):
+        for learned in (False, True):
+            c = sa.context_from_workload(wl, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1,
+                                         precond=pre)
+            c.step(th, dt, 0)
+            c.set_state(*state)
+            if learned:
+                c.set_warm_start(net, idx)
+            c.step(th, dt, 3)
+            c.step(th, dt, 0)
+            ms = time_graph(c, th, dt, K_eval, stream)
+            st = c.step(th, dt, 0)
+            key = pre_name + ("_learned" if learned else "_cold")
+            out["evaluation"][key] = {"steps_per_s": K_eval / (ms / 1e3),
+                                      "pcg_iters_per_step": st.pcg_iters_total / K_eval}
+            if learned:
+                used = 0
+                for _ in range(10):
+                    used += c.step(th, dt, 1).ws_used_last
+                out["evaluation"][key]["learned_guess_kept_fraction"] = used / 10
+            c.close()
+    net.close()
+    return out
+
+
+def plate_leg(sa, W, stream, n_ff, K):
+    """The 3 x 3 x 0.5 mm plate with a hole (degree 3, 48 x 48 x 8, closed
+    seam): theta-steps/s over K steps after n_ff untimed steps of its
+    contour scan, fast diagonalization against Jacobi."""
+    wl = W.plate_with_hole()
+    out = {"workload": wl.name, "first_step": n_ff + 3, "steps": K}
+    state = None
+    for name, pre in (("fd", sa.SA_PRECOND_AUTO), ("jacobi", sa.SA_PRECOND_JACOBI)):
+        c = sa.context_from_workload(wl, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1,
+                                     precond=pre)
+        if state is None:
+            c.step(wl.theta, wl.dt, n_ff)
+            state = c.get_state()
+        else:
+            c.step(wl.theta, wl.dt, 0)
+            c.set_state(*state)
+        c.step(wl.theta, wl.dt, 3)
+        c.step(wl.theta, wl.dt, 0)
+        ms = time_graph(c, wl.theta, wl.dt, K, stream)
+        st = c.step(wl.theta, wl.dt, 0)
+        out[name] = {"steps_per_s": K / (ms / 1e3), "pcg_iters_per_step": st.pcg_iters_total / K,
+                     "bottom_iters_per_step": st.bot_iters_total / K}
+        if name == "fd":
+            out["n_dof"] = c.sizes().n_dof
+            out["nnz_a"] = c.sizes().nnz_a
+        c.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def time_graph(ctx, th, dt, K, stream):
@@ -358,6 +475,15 @@ def run_ours(args):
     e2e = world * K_e / t_e2e
     assert np.isfinite(T_mon).all()
 
+    # ---- the plate with a hole ---------------------------------------------------
+    plate = plate_leg(sa, W, stream, 1000, min(K, 300)) if world == 1 else None
+
+    # ---- learned warm start (bounded: a few thousand training pairs) -------------
+    learned = None
+    if args.learned_pairs > 0 and world == 1:
+        learned = learned_leg(sa, W, wl, state, stream, args.learned_pairs, args.learned_epochs,
+                              min(K, 100))
+
     # ---- roofline of the dominant kernel ------------------------------------------
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
@@ -430,6 +556,8 @@ def run_ours(args):
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
                 "d2h_bytes_per_step": N_MONITOR * 8 + 96},
+        "plate_with_hole": plate,
+        "learned_warm_start": learned,
         "gpu_launches": launches_per_step * K,
         "clocks": clocks,
     }
