@@ -60,6 +60,8 @@ def parse():
                     help="path timed in the main region")
     ap.add_argument("--guess", default="previous", choices=["extrapolate", "previous"],
                     help="initial guess of the theta-step solves in the main region")
+    ap.add_argument("--batch-steps", type=int, default=2000,
+                    help="theta-steps of the 256-instance batched leg (0: skip the leg)")
     ap.add_argument("--learned-pairs", type=int, default=2000,
                     help="training pairs of the learned warm-start leg (0: skip the leg)")
     ap.add_argument("--learned-epochs", type=int, default=20)
@@ -346,6 +348,35 @@ def plate_leg(sa, W, stream, n_ff, K):
     return out
 
 
+def batched_leg(sa, W, stream, n_inst, n_steps):
+    """The batched sweep: n_inst seeded instances (uneven boxes, powers,
+    speeds, track counts) stepped together for n_steps theta-steps (the
+    first 3 untimed), one launch per stage for all instances."""
+    import numpy as np
+    t0 = time.perf_counter()
+    wls = [W.batched_instance(i, n_steps=n_steps) for i in range(n_inst)]
+    ctxs = [sa.context_from_workload(wl, precision=sa.SA_MIXED) for wl in wls]
+    b = sa.Batch(ctxs, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
+    setup_s = time.perf_counter() - t0
+    th, dt = wls[0].theta, wls[0].dt
+    b.step(th, dt, 3)
+    sz = [c.sizes() for c in ctxs]
+    K = n_steps - 3
+    pairs = sum((z.q_lat + z.q_bot) * sum(min(n, z.n_src) for n in range(4, n_steps + 1)) for z in sz)
+    ms = time_graph(b, th, dt, K, stream)
+    m_it, b_it = b.iters()
+    out = {"instances": n_inst, "steps": n_steps, "timed_steps": K, "setup_s": setup_s,
+           "ms_per_step": ms / K, "instance_steps_per_s": n_inst * K / (ms / 1e3),
+           "point_source_evals_per_s": pairs / (ms / 1e3),
+           "total_control_variables": int(sum(z.n_dof for z in sz)),
+           "total_boundary_points": int(sum(z.q_lat + z.q_bot for z in sz)),
+           "last_step_main_iters_max": int(m_it.max()), "last_step_bottom_iters_max": int(b_it.max())}
+    b.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -475,6 +506,9 @@ def run_ours(args):
     e2e = world * K_e / t_e2e
     assert np.isfinite(T_mon).all()
 
+    # ---- the batched sweep (256 instances, 2000 steps) ------------------------------
+    batched = batched_leg(sa, W, stream, 256, args.batch_steps) if world == 1 and args.batch_steps > 3 else None
+
     # ---- the plate with a hole ---------------------------------------------------
     plate = plate_leg(sa, W, stream, 1000, min(K, 300)) if world == 1 else None
 
@@ -557,6 +591,7 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
                 "d2h_bytes_per_step": N_MONITOR * 8 + 96},
         "plate_with_hole": plate,
+        "batched_256": batched,
         "learned_warm_start": learned,
         "gpu_launches": launches_per_step * K,
         "clocks": clocks,

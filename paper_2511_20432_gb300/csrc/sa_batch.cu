@@ -71,6 +71,12 @@ struct sa_batch {
     DBuf<int> inst_iters;
     DBuf<unsigned> counters;
     DBuf<DevStatus> st;
+    // fast diagonalization of every instance's main solve (when all have it)
+    bool fd_on = false;
+    int fd_mmax = 0;
+    DBuf<unsigned char> fd_desc;   // BFd per instance
+    DBuf<int> fd_loff;             // 3 x (n_inst + 1): line offsets per direction
+    DBuf<unsigned char> fdS, fdZ;  // n_free x VT
     int pcg_grid = 0;
     int hist_P = 4, hist_W = 8;
     cudaGraphExec_t graph_exec = nullptr;
@@ -182,6 +188,16 @@ __device__ bool bgrid_barrier(unsigned* count, unsigned* gen, int* err) {
     return ok != 0;
 }
 
+// One instance's fast-diagonalization data (device pointers of its context).
+struct BFd {
+    int m[3];
+    int row0;                 // first batch row of the instance
+    const void* U[3];
+    const void* Ut[3];
+    const void* lamc[3];
+    double cM;
+};
+
 // per-instance solver scalars (FP64), laid out [field][instance]
 enum { IS_RZ = 0, IS_BB, IS_ALPHA, IS_BETA, IS_RR, IS_CONV, IS_NFIELDS };
 
@@ -198,6 +214,7 @@ struct BPcgArgs {
     const double* dinv;
     const double* b;
     const double* r0;
+    const double* bsq;        // with r0: b_i^2 per row (else b = r0 + A x by an SpMV)
     double* x;
     double* r;
     double* z;
@@ -215,11 +232,104 @@ struct BPcgArgs {
     int which;
     double tol;
     int max_iter;
+    const BFd* fd;            // per-instance fast diagonalization, or null (Jacobi)
+    const int* fd_loff;       // 3 x (n_inst + 1)
+    const VT* fdS;            // scaling per row
+    VT* fdZ;                  // work vector
 };
 
 template <typename VT>
 __device__ __forceinline__ int bcol(const BPcgArgs<VT>& a, long long e, int row) {
     return a.col16 ? row + (int)__ldg(a.col16 + e) : __ldg(a.col32 + e);
+}
+
+// Batched fast-diagonalization preconditioner z = S A_box^{-1} S r over
+// every instance (independent grids): on entry fdZ = S r on all rows (grid
+// barrier passed); five passes over the lines of all instances (a line ->
+// its instance by the per-direction line offsets), one warp per line, the
+// line's matrix read through L1; the last pass writes z (FP64) and its
+// operator-precision copy.  Lines have at most 128 entries.
+template <typename VT>
+__device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsigned* bc,
+                          unsigned* bg, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int NI = a.n_inst;
+    VT* Z = a.fdZ;
+    for (int pass = 0; pass < 5; ++pass) {
+        const int d = pass < 3 ? pass : 4 - pass;
+        const int* loff = a.fd_loff + d * (NI + 1);
+        const int nlines = loff[NI];
+        for (int Lg = gw; Lg < nlines; Lg += nw) {
+            int lo = 0, hi = NI;          // loff[lo] <= Lg < loff[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (loff[mid] <= Lg) lo = mid;
+                else hi = mid;
+            }
+            const BFd& f = a.fd[lo];
+            const int L = Lg - loff[lo];
+            const int m0 = f.m[0], m1 = f.m[1];
+            const int m = f.m[d];
+            const int stride = d == 0 ? 1 : (d == 1 ? m0 : m0 * m1);
+            const long long base = f.row0 + (d == 0 ? (long long)L * m0
+                                            : (d == 1 ? (long long)(L / m0) * (m0 * m1) + (L % m0) : L));
+            for (int q = lane; q < m; q += 32) xs[q] = __ldcg(Z + base + (long long)q * stride);
+            __syncwarp();
+            const VT* W = (const VT*)(pass < 3 ? f.U[d] : f.Ut[d]);
+            VT y[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
+#pragma unroll 4
+            for (int q = 0; q < m; ++q) {
+                const VT xq = xs[q];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int o = lane + 32 * t;
+                    if (o < m) y[t] = fma(__ldg(W + q * m + o), xq, y[t]);
+                }
+            }
+            if (pass == 2) {
+                const VT li = (VT)f.cM + ((const VT*)f.lamc[0])[L % m0] + ((const VT*)f.lamc[1])[L / m0];
+                const VT* l2 = (const VT*)f.lamc[2];
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int o = lane + 32 * t;
+                    if (o < m) xs[o] = y[t] / (li + l2[o]);
+                    y[t] = (VT)0;
+                }
+                __syncwarp();
+                const VT* W2 = (const VT*)f.Ut[2];
+#pragma unroll 4
+                for (int q = 0; q < m; ++q) {
+                    const VT xq = xs[q];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int o = lane + 32 * t;
+                        if (o < m) y[t] = fma(__ldg(W2 + q * m + o), xq, y[t]);
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int o = lane + 32 * t;
+                if (o < m) {
+                    const long long idx = base + (long long)o * stride;
+                    if (pass == 4) {
+                        const VT u = a.fdS[idx] * y[t];
+                        z[idx] = (double)u;
+                        zl[idx] = u;
+                    } else {
+                        Z[idx] = y[t];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (!bgrid_barrier(bc, bg, err)) return false;
+    }
+    return true;
 }
 
 template <typename VT>
@@ -234,6 +344,10 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
     int* err = &a.st->err;
     const int S = a.n_slices, NI = a.n_inst;
     volatile double* is = a.is;
+    __shared__ VT xsb[32][128];            // per-warp line scratch (fast diagonalization)
+    VT* xs = xsb[threadIdx.x >> 5];
+    const bool fd = a.fd != nullptr;
+    VT* const zlw = LO ? a.zl : (VT*)a.z;
     // ---- phase A: r = b - A x (FP64 values) or r = r0 (b = r0 + A x)
     for (int sl = gw; sl < S; sl += nw) {
         const long long base = a.sptr[sl];
@@ -246,7 +360,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
                 const long long e = base + 32ll * k + lane;
                 acc = fma(__ldg(a.val_hi + e), a.x[bcol(a, e, ir)], acc);
             }
-        } else {
+        } else if (a.bsq == nullptr) {
             VT s = 0;
             for (int k = 0; k < w; ++k) {
                 const long long e = base + 32ll * k + lane;
@@ -261,12 +375,17 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
                 ri = bi - acc;
             } else {
                 ri = a.r0[i];
-                bi = ri + acc;
+                // |b_i| from the right-hand-side kernel when given (no SpMV)
+                bi = a.bsq ? sqrt(a.bsq[i]) : ri + acc;
             }
-            zi = a.dinv[i] * ri;
             a.r[i] = ri;
-            a.z[i] = zi;
-            if (LO) a.zl[i] = (VT)zi;
+            if (fd) {
+                a.fdZ[i] = a.fdS[i] * (VT)ri;
+            } else {
+                zi = a.dinv[i] * ri;
+                a.z[i] = zi;
+                if (LO) a.zl[i] = (VT)zi;
+            }
         }
         const double t0 = warp_sum(ri * zi), t1 = warp_sum(ri * ri), t2 = warp_sum(bi * bi);
         if (lane == 0) {
@@ -276,6 +395,16 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
         }
     }
     if (!bgrid_barrier(bc, bg, err)) return;
+    if (fd) {
+        // z = P^{-1} r, then (r, z) per slice
+        if (!bfd_apply(a, xs, a.z, zlw, bc, bg, err)) return;
+        for (int sl = gw; sl < S; sl += nw) {
+            const int i = sl * 32 + lane;
+            const double t0 = warp_sum(i < a.n ? a.r[i] * a.z[i] : 0.0);
+            if (lane == 0) a.part[sl] = t0;
+        }
+        if (!bgrid_barrier(bc, bg, err)) return;
+    }
     // R0: per-instance rz, rr, bb; convergence; active count
     for (int i = gw; i < NI; i += nw) {
         const int s0 = a.slice_off[i], s1 = a.slice_off[i + 1];
@@ -375,12 +504,16 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
                 if (i < a.n) {
                     a.x[i] = fma(alpha, pn[i], a.x[i]);
                     const double ri = fma(-alpha, a.q[i], a.r[i]);
-                    const double zi = a.dinv[i] * ri;
                     a.r[i] = ri;
-                    a.z[i] = zi;
-                    if (LO) a.zl[i] = (VT)zi;
                     rr = ri * ri;
-                    rz = ri * zi;
+                    if (fd) {
+                        a.fdZ[i] = a.fdS[i] * (VT)ri;
+                    } else {
+                        const double zi = a.dinv[i] * ri;
+                        a.z[i] = zi;
+                        if (LO) a.zl[i] = (VT)zi;
+                        rz = ri * zi;
+                    }
                 }
             }
             rr = warp_sum(rr);
@@ -391,6 +524,19 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
             }
         }
         if (!bgrid_barrier(bc, bg, err)) return;
+        if (fd) {
+            // z = P^{-1} r (every row; converged instances ignore theirs), then (r, z)
+            if (!bfd_apply(a, xs, a.z, zlw, bc, bg, err)) return;
+            for (int sl = gw; sl < S; sl += nw) {
+                const int inst = a.slice_inst[sl];
+                const int i = sl * 32 + lane;
+                double rz = 0.0;
+                if (is[IS_CONV * NI + inst] == 0.0 && i < a.n) rz = a.r[i] * a.z[i];
+                rz = warp_sum(rz);
+                if (lane == 0) a.part[2 * S + sl] = rz;
+            }
+            if (!bgrid_barrier(bc, bg, err)) return;
+        }
         // R2: convergence, beta, active count
         for (int i = gw; i < NI; i += nw) {
             const int s0 = a.slice_off[i], s1 = a.slice_off[i + 1];
@@ -456,6 +602,7 @@ cudaError_t launch_pcg_batch(sa_batch* b, int which, const SellDev& s, const voi
     a.dinv = dinv;
     a.b = rhs;
     a.r0 = r0;
+    a.bsq = (r0 != nullptr && which == 0) ? b->bsq.p : nullptr;
     a.x = x;
     a.r = b->wr.p;
     a.z = b->wz.p;
@@ -473,6 +620,11 @@ cudaError_t launch_pcg_batch(sa_batch* b, int which, const SellDev& s, const voi
     a.which = which;
     a.tol = b->opt.pcg_tol;
     a.max_iter = b->opt.pcg_max_iter;
+    const bool fd = which == 0 && b->fd_on;
+    a.fd = fd ? (const BFd*)b->fd_desc.p : nullptr;
+    a.fd_loff = fd ? b->fd_loff.p : nullptr;
+    a.fdS = fd ? (const VT*)b->fdS.p : nullptr;
+    a.fdZ = fd ? (VT*)b->fdZ.p : nullptr;
     cudaError_t e = cudaMemsetAsync(&b->st.p->bar_count[2 + which], 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->counters.p, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -757,6 +909,39 @@ sa_status build(sa_batch* b, double theta, double dt) {
         B_ALLOC(b, b->wpl1, nwork);
         const int smax = std::max(b->a_s.n_slices, b->mbot_s.n_slices);
         B_ALLOC(b, b->partials, (size_t)3 * std::max(smax, 1));
+        // fast diagonalization of the main solves: every instance has it, in
+        // the batch's precision
+        b->fd_on = b->opt.precond != SA_PRECOND_JACOBI;
+        for (int i = 0; i < NI && b->fd_on; ++i)
+            b->fd_on = b->inst[i]->fdm.ok && b->inst[i]->opt.precision == b->opt.precision;
+        if (b->fd_on) {
+            const size_t vt = mixed ? sizeof(float) : sizeof(double);
+            std::vector<BFd> desc(NI);
+            std::vector<int> loff(3 * (NI + 1), 0);
+            for (int i = 0; i < NI; ++i) {
+                const FdData& f = b->inst[i]->fdm;
+                for (int d = 0; d < 3; ++d) {
+                    desc[i].m[d] = f.m[d];
+                    desc[i].U[d] = f.dU[d].p;
+                    desc[i].Ut[d] = f.dUt[d].p;
+                    desc[i].lamc[d] = f.dlamc[d].p;
+                    loff[d * (NI + 1) + i + 1] = loff[d * (NI + 1) + i] + b->inst[i]->n_free / f.m[d];
+                }
+                desc[i].row0 = b->free_off[i];
+                desc[i].cM = f.cM;
+            }
+            std::vector<unsigned char> raw(sizeof(BFd) * NI);
+            std::memcpy(raw.data(), desc.data(), raw.size());
+            sa_status st2;
+            if ((st2 = bupload(b, b->fd_desc, raw, "fd_desc"))) return st2;
+            if ((st2 = bupload(b, b->fd_loff, loff, "fd_loff"))) return st2;
+            B_ALLOC(b, b->fdS, nwork * vt);
+            B_ALLOC(b, b->fdZ, nwork * vt);
+            B_CUDA(b, cudaMemsetAsync(b->fdS.p, 0, nwork * vt, s));
+            for (int i = 0; i < NI; ++i)
+                B_CUDA(b, d2d(b->fdS.p + (size_t)b->free_off[i] * vt, b->inst[i]->fdm.S.p,
+                              (size_t)b->inst[i]->n_free * vt, s));
+        }
         B_ALLOC(b, b->inst_state, (size_t)IS_NFIELDS * std::max(NI, 1));
         B_ALLOC(b, b->inst_iters, (size_t)2 * std::max(NI, 1));
         B_ALLOC(b, b->counters, 2);

@@ -32,22 +32,26 @@ def _instances():
     return out
 
 
+@pytest.mark.parametrize("precond", ["fd", "jacobi"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_matches_single_contexts(sa, prec):
+def test_batch_matches_single_contexts(sa, prec, precond):
     import torch
     p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    pc = sa.SA_PRECOND_AUTO if precond == "fd" else sa.SA_PRECOND_JACOBI
     wls = _instances()
     s = torch.cuda.Stream()
     tol = 1e-15 if p == sa.SA_FP64 else 1e-10
-    ctxs = [gpu_context(wl, p, pcg_tol=tol) for wl in wls]
-    singles = [gpu_context(wl, p, pcg_tol=tol) for wl in wls]
-    batch = sa.Batch(ctxs, precision=p, pcg_tol=tol, cuda_stream=s, use_graph=1)
+    ctxs = [gpu_context(wl, p, pcg_tol=tol, precond=pc) for wl in wls]
+    singles = [gpu_context(wl, p, pcg_tol=tol, precond=pc) for wl in wls]
+    batch = sa.Batch(ctxs, precision=p, pcg_tol=tol, cuda_stream=s, use_graph=1, precond=pc)
     n = 60
     batch.step(0.5, 5e-6, n)
     for c in singles:
         c.step(0.5, 5e-6, n)
     m_it, b_it = batch.iters()
     assert (m_it >= 0).all() and (b_it >= 0).all()
+    if precond == "fd":   # boxes: the preconditioner is the inverse
+        assert m_it.max() <= 2, m_it
     for i, c in enumerate(singles):
         Tb = batch.field(i, sa.SA_FIELD_THAT)
         Ts = c.field(sa.SA_FIELD_THAT)
