@@ -138,14 +138,14 @@ __global__ void k_dir_prep(int n_dir, int n_free, const double* That, const doub
 // Dirichlet columns.  DIR is uniform over the warp (a flag per slice), so
 // slices without Dirichlet columns carry none of that work.
 template <bool DIR, typename VT>
-__device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, int w, int lane,
-                                          int ir, VT (&acc)[7]) {
-    for (int k = 0; k < w; k += 8) {
+__device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, int k0, int k1,
+                                          int lane, int ir, VT (&acc)[7]) {
+    for (int k = k0; k < k1; k += 8) {
         int jj[8];
         VT kv[8], mv[8], dv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {     // independent loads first
-            const bool ok = k + u < w;
+            const bool ok = k + u < k1;
             const long long e = base + 32ll * (ok ? k + u : 0) + lane;
             jj[u] = ok ? a.K.col(e, ir) : ir;
             kv[u] = ok ? __ldg(a.K.val + e) : (VT)0;
@@ -182,20 +182,41 @@ __device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, 
 //   b = (rho c_p/dt) M T^n - (1-theta) k K T^n + theta F^{n+1} + (1-theta) F^n
 //       - A_fd g^{n+1},   with M T^n = T_c (M 1) + M (T^n - T_c)
 // and A_fd = (rho c_p/dt) M_fd + theta k K_fd.
+constexpr int kRhsSplit = 4;   // warps sharing one slice's columns
+
 template <typename VT>
 __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
-    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (sl >= a.K.n_slices) return;
-    const int i = sl * 32 + lane;
-    const int ir = min(i, a.n_free - 1);
-    const long long base = a.K.sptr[sl];
-    const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
+    // 8 warps: two slices, each split over kRhsSplit warps by columns (enough
+    // warps in flight to cover the memory latency); partial sums combined in
+    // fixed order
+    __shared__ VT part[8][7][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sl = blockIdx.x * (8 / kRhsSplit) + wib / kRhsSplit;
+    const int h = wib % kRhsSplit;
     VT acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (a.K.hi == nullptr || a.K.hi[sl])
-        rhs_slice<true>(a, base, w, lane, ir, acc);
-    else
-        rhs_slice<false>(a, base, w, lane, ir, acc);
+    const bool live = sl < a.K.n_slices;
+    const int i = sl * 32 + lane;
+    if (live) {
+        const int ir = min(i, a.n_free - 1);
+        const long long base = a.K.sptr[sl];
+        const int w = (int)((a.K.sptr[sl + 1] - base) >> 5);
+        const int chunk = (((w + kRhsSplit - 1) / kRhsSplit) + 7) & ~7;
+        const int k0 = min(w, h * chunk), k1 = min(w, k0 + chunk);
+        if (a.K.hi == nullptr || a.K.hi[sl])
+            rhs_slice<true>(a, base, k0, k1, lane, ir, acc);
+        else
+            rhs_slice<false>(a, base, k0, k1, lane, ir, acc);
+    }
+#pragma unroll
+    for (int v = 0; v < 7; ++v) part[wib][v][lane] = acc[v];
+    __syncthreads();
+    if (!live || h != 0) return;
+#pragma unroll
+    for (int v = 0; v < 7; ++v) {
+        VT t = part[wib][v][lane];
+        for (int hh = 1; hh < kRhsSplit; ++hh) t += part[wib + hh][v][lane];
+        acc[v] = t;
+    }
     if (i < a.n_free) {
         const double tk = a.theta * a.k;
         const double accd = a.inv_dt_rhocp * (double)acc[3] + tk * (double)acc[4];
@@ -1359,7 +1380,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s) {
     if (op.n == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)(((long long)op.n_slices * 32 + 255) / 256);
+    const unsigned blocks = (unsigned)((op.n_slices + (8 / kRhsSplit) - 1) / (8 / kRhsSplit));
     const unsigned pblocks = (unsigned)((n_dir + 255) / 256);
     if (precision == SA_MIXED) {
         float* dg = (float*)dir_scratch;
