@@ -562,7 +562,9 @@ def run_ours(args):
                 "kernel": "k_pcg_smem (free block)", "peak_basis": "hbm_gbs of measured",
                 "note": "algorithmic bytes count every SpMV's pass over the operator; later "
                         "passes of a launch hit L2 (traffic: one ncu-captured launch)"}
-    launches_per_step = 8 + warm
+    # prologue, history (bottom, lateral), gather (bottom, lateral), projection,
+    # Dirichlet increments, right-hand side (two slice sets), PCG, finalize
+    launches_per_step = 11 + warm
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,

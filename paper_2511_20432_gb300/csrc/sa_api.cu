@@ -283,6 +283,16 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
                 delete c;
                 return SA_ERR_CUDA;
             }
+    if (!opt.stage_timing &&
+        (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        if (c->aux) cudaStreamDestroy(c->aux);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        delete c;
+        return SA_ERR_CUDA;
+    }
     c->hist_P = opt.hist_points_per_lane ? opt.hist_points_per_lane : 4;
     c->hist_W = opt.hist_warps ? opt.hist_warps : 8;
     *out = c;
@@ -294,6 +304,9 @@ void sa_destroy(sa_ctx* c) {
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (int i = 0; i <= SA_N_STAGES; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
 
@@ -1066,32 +1079,47 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                         c->opt.precision == SA_MIXED ? c->src32T.p : nullptr,
                         c->opt.precision == SA_MIXED ? c->src32F.p : nullptr, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "prologue");
+    // Two chains after the prologue: the bottom chain (history of the bottom
+    // points, b_bot, the projection) on the second stream, beside the
+    // lateral chain (history of the lateral points, F, the right-hand side of
+    // the slices without Dirichlet columns); they join before the slices
+    // with Dirichlet columns.  Stage timing keeps one stream.
+    const bool overlap = !timing && c->aux != nullptr && c->n_dir > 0;
+    cudaStream_t sb = overlap ? c->aux : s;
+    if (overlap) {
+        SA_CUDA(c, cudaEventRecord(c->ev_fork, s));
+        SA_CUDA(c, cudaStreamWaitEvent(sb, c->ev_fork, 0));
+    }
     SA_MARK(SA_STAGE_HISTORY);
-    e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat, c->q_bot,
-                       c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p, c->x_ref, c->y_ref,
-                       c->z_top, c->src32F.p, c->src32T.p, c->src64F.p, c->src64T.p,
-                       c->s_lat.p, c->tt_bot.p, s);
-    if (e != cudaSuccess) return sa_cuda_fail(c, e, "history");
+    for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
+        e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat, c->q_bot,
+                           c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p, c->x_ref, c->y_ref,
+                           c->z_top, c->src32F.p, c->src32T.p, c->src64F.p, c->src64T.p,
+                           c->s_lat.p, c->tt_bot.p, part == 2 ? sb : s, part);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "history");
+    }
     SA_MARK(SA_STAGE_GATHER);
-    e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
-                      c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
-                      c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, c->n_dof, c->That.p,
-                      c->dev64.p, c->dev32.p, s);
-    if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
+    for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
+        e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
+                          c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
+                          c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, c->n_dof,
+                          c->That.p, c->dev64.p, c->dev32.p, part == 2 ? sb : s, part);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
+    }
     const bool mixed = c->opt.precision == SA_MIXED;
     SA_MARK(SA_STAGE_BOTTOM);
     const bool extrap = c->opt.initial_guess == SA_GUESS_EXTRAPOLATE;
     if (extrap) {
         // proposals T^n - T^{n-1} (main solve) and 2 g^n - g^{n-1} (projection)
         e = launch_extrap(c->n_free, c->n_dir, c->That.p, c->x_prev.p, c->dx_extrap.p,
-                          c->x_prev.p + c->n_free, c->gnew.p, s);
+                          c->x_prev.p + c->n_free, c->gnew.p, sb);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "extrapolated guess");
     }
     if (c->n_dir > 0) {
         // x0 = g^n (the Dirichlet part of the state), or its extrapolation
         if (!extrap) {
             e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
-                                cudaMemcpyDeviceToDevice, s);
+                                cudaMemcpyDeviceToDevice, sb);
             if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
         }
         PcgLaunch L;
@@ -1117,20 +1145,28 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
-        // small system: a few blocks of ~8 slices (cheap barriers)
+        // small system: a few blocks of ~8 slices (cheap barriers); 256
+        // threads a block beside the lateral chain, so it fits next to it
         L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices + 7) / 8));
+        L.block = overlap ? 256 : 0;
         L.ksplit = 0;
-        e = launch_pcg(c->opt.precision, L, s);
+        e = launch_pcg(c->opt.precision, L, sb);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
     SA_MARK(SA_STAGE_RHS);
-    e = launch_theta_rhs(c->opt.precision, sell_view(c->r_s),
-                         mixed ? (const void*)c->r_K32.p : (const void*)c->r_K.p,
-                         mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
-                         mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
-                         c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
-                         c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s);
-    if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
+    for (int only = overlap ? 1 : 0; only <= (overlap ? 2 : 0); ++only) {
+        if (only == 2) {   // join: the projection is done
+            SA_CUDA(c, cudaEventRecord(c->ev_join, sb));
+            SA_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+        }
+        e = launch_theta_rhs(c->opt.precision, sell_view(c->r_s),
+                             mixed ? (const void*)c->r_K32.p : (const void*)c->r_K.p,
+                             mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
+                             mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
+                             c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
+                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s, only);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
+    }
     SA_MARK(SA_STAGE_PCG);
     const bool rec = c->rec_X != nullptr && c->rec_count < c->rec_cap;
     if (c->ws_net || rec) {

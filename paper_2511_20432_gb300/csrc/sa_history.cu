@@ -138,6 +138,7 @@ struct HistArgs {
     DevStatus* st;
     int q_lat, q_bot;
     int b_lat;                 // CTAs on lateral tiles; the rest on bottom tiles
+    int blk0;                  // tile of block 0 (a launch can cover only the bottom tiles)
     const float* lat32;
     const float* bot32;
     const double* lat64;
@@ -359,28 +360,32 @@ template <int P, int NW>
 __global__ void __launch_bounds__(32 * NW) k_history_mixed(HistArgs a) {
     __shared__ double red[NW * 32 * P];
     __shared__ __align__(128) Stage sg;
-    if ((int)blockIdx.x < a.b_lat)
-        tile_mixed<true, P, NW>(a, blockIdx.x, red, sg);
+    const int b = (int)blockIdx.x + a.blk0;
+    if (b < a.b_lat)
+        tile_mixed<true, P, NW>(a, b, red, sg);
     else
-        tile_mixed<false, P, NW>(a, blockIdx.x - a.b_lat, red, sg);
+        tile_mixed<false, P, NW>(a, b - a.b_lat, red, sg);
 }
 
 template <int P, int NW>
 __global__ void __launch_bounds__(32 * NW) k_history_fp64(HistArgs a) {
     __shared__ double red[NW * 32 * P];
-    if ((int)blockIdx.x < a.b_lat)
-        tile_fp64<true, P, NW>(a, blockIdx.x, red);
+    const int b = (int)blockIdx.x + a.blk0;
+    if (b < a.b_lat)
+        tile_fp64<true, P, NW>(a, b, red);
     else
-        tile_fp64<false, P, NW>(a, blockIdx.x - a.b_lat, red);
+        tile_fp64<false, P, NW>(a, b - a.b_lat, red);
 }
 
 template <int P, int NW>
-cudaError_t launch_hist_t(int precision, const HistArgs& a0, cudaStream_t s) {
+cudaError_t launch_hist_t(int precision, const HistArgs& a0, cudaStream_t s, int part = 0) {
     HistArgs a = a0;
     const int tile = 32 * P;
     a.b_lat = (a.q_lat + tile - 1) / tile;
     const int b_bot = (a.q_bot + tile - 1) / tile;
-    const int grid = a.b_lat + b_bot;
+    // part 0: every tile; 1: lateral tiles; 2: bottom tiles
+    a.blk0 = part == 2 ? a.b_lat : 0;
+    const int grid = part == 1 ? a.b_lat : (part == 2 ? b_bot : a.b_lat + b_bot);
     if (grid == 0) return cudaSuccess;
     if (precision == SA_MIXED)
         k_history_mixed<P, NW><<<grid, 32 * NW, 0, s>>>(a);
@@ -421,12 +426,13 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
                            const double* lat64, const double* bot64, double x_ref,
                            double y_ref, double z_top, const float4* s32F,
                            const float4* s32T, const double4* s64F, const double4* s64T,
-                           double* s_lat, double* tt_bot, cudaStream_t s) {
+                           double* s_lat, double* tt_bot, cudaStream_t s, int part) {
     HistArgs a;
     a.st = st;
     a.q_lat = q_lat;
     a.q_bot = q_bot;
     a.b_lat = 0;
+    a.blk0 = 0;
     a.lat32 = lat32;
     a.bot32 = bot32;
     a.lat64 = lat64;
@@ -443,13 +449,13 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
     a.n_inst = 0;
     a.qlat_off = a.qbot_off = a.src_off = a.n_active = nullptr;
     if (warps == 4) {
-        if (P == 1) return launch_hist_t<1, 4>(precision, a, s);
-        if (P == 2) return launch_hist_t<2, 4>(precision, a, s);
-        return launch_hist_t<4, 4>(precision, a, s);
+        if (P == 1) return launch_hist_t<1, 4>(precision, a, s, part);
+        if (P == 2) return launch_hist_t<2, 4>(precision, a, s, part);
+        return launch_hist_t<4, 4>(precision, a, s, part);
     }
-    if (P == 1) return launch_hist_t<1, 8>(precision, a, s);
-    if (P == 2) return launch_hist_t<2, 8>(precision, a, s);
-    return launch_hist_t<4, 8>(precision, a, s);
+    if (P == 1) return launch_hist_t<1, 8>(precision, a, s, part);
+    if (P == 2) return launch_hist_t<2, 8>(precision, a, s, part);
+    return launch_hist_t<4, 8>(precision, a, s, part);
 }
 
 cudaError_t launch_prologue_batch(const DevStatus* st, int n_src_total, int n_inst,
@@ -477,6 +483,7 @@ cudaError_t launch_history_batch(int precision, int P, int warps, DevStatus* st,
     a.q_lat = q_lat;
     a.q_bot = q_bot;
     a.b_lat = 0;
+    a.blk0 = 0;
     a.lat32 = lat32;
     a.bot32 = bot32;
     a.lat64 = lat64;

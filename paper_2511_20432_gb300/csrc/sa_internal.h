@@ -205,6 +205,7 @@ struct PcgLaunch {
     double tol;
     int max_iter;
     int grid;                 // 1: one block, no grid barrier
+    int block = 0;            // threads per block (0: 1024)
     int ksplit;               // warps per SELL slice in the SpMV (1, 2, 4, 8)
 };
 
@@ -370,6 +371,10 @@ struct sa_ctx {
 
     // stage timing (sa_options::stage_timing)
     cudaEvent_t ev[SA_N_STAGES + 1] = {};
+    // second stream of a step: the bottom chain (history of the bottom
+    // points, b_bot, the projection) runs beside the lateral chain
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double stage_ms[SA_N_STAGES] = {};
     long long stage_steps = 0;
 };
@@ -440,7 +445,7 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
                            const double* lat64, const double* bot64, double x_ref,
                            double y_ref, double z_top, const float4* s32F,
                            const float4* s32T, const double4* s64F, const double4* s64T,
-                           double* s_lat, double* tt_bot, cudaStream_t s);
+                           double* s_lat, double* tt_bot, cudaStream_t s, int part = 0);
 cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,
@@ -452,12 +457,12 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, int n_dof, const double* That, double* dev64,
-                          float* dev32, cudaStream_t s);
+                          float* dev32, cudaStream_t s, int part = 0);
 cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
-                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s);
+                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only = 0);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
                           double* gprev, double* g0, cudaStream_t s);

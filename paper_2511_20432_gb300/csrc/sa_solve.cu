@@ -50,12 +50,17 @@ struct GatherArgs {
     const double* That;
     double* dev64;
     float* dev32;
+    int part;              // 0: everything; 1: lateral rows and dev; 2: bottom rows
 };
 
 __global__ void k_gather(GatherArgs a) {
-    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long row_threads = 32ll * (a.wlat_rows + a.n_dir);
+    long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // thread space: [lateral rows x 32 | bottom rows x 32 | dev], parts skip a range
+    if (a.part == 2) gt += 32ll * a.wlat_rows;
+    const long long lat_threads = 32ll * a.wlat_rows;
+    const long long row_threads = lat_threads + (a.part == 1 ? 0 : 32ll * a.n_dir);
     if (gt >= row_threads) {
+        if (a.part == 2) return;
         const long long i = gt - row_threads;
         if (i < a.n_dof) {
             const double d = a.That[i] - a.Tc;
@@ -119,6 +124,7 @@ struct RhsArgs {
     double inv_dt_rhocp, k, theta, Tc;
     double* r0;
     double* bsq;           // b_i^2, for the norm of the right-hand side
+    int only;              // 0: every slice; 1: slices without Dirichlet columns; 2: with
 };
 
 // g^{n+1} - g^n and g^{n+1} in the operator precision, so that the rows
@@ -194,7 +200,11 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     const int sl = blockIdx.x * (8 / kRhsSplit) + wib / kRhsSplit;
     const int h = wib % kRhsSplit;
     VT acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    const bool live = sl < a.K.n_slices;
+    bool live = sl < a.K.n_slices;
+    if (live && a.only != 0) {
+        const bool dir = a.K.hi == nullptr || a.K.hi[sl];
+        live = (a.only == 2) == dir;
+    }
     const int i = sl * 32 + lane;
     if (live) {
         const int ir = min(i, a.n_free - 1);
@@ -1187,7 +1197,7 @@ Op<VT> make_op(const SellView& s, const void* val) {
 // (so the 32 warps of a block are busy), window length, shared memory.
 template <typename VT>
 struct PcgShape {
-    int G, spb, ks, rcap, fd_mmax;
+    int G, block, spb, ks, rcap, fd_mmax;
     long long wl, region;
     bool window;
     size_t smem;
@@ -1200,9 +1210,11 @@ template <typename VT>
 PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
     PcgShape<VT> sh;
     sh.G = L.grid > 0 ? L.grid : 1;
+    sh.block = L.block > 0 ? L.block : kPcgBlock;
     sh.spb = (L.op.n_slices + sh.G - 1) / sh.G;
+    const int warps = sh.block / 32;
     int ks = 1;
-    while (ks < 8 && sh.spb * ks * 2 <= 32) ks *= 2;
+    while (ks < 8 && ks * 2 <= warps && sh.spb * ks * 2 <= warps) ks *= 2;
     sh.ks = L.ksplit > 0 ? L.ksplit : ks;
     sh.rcap = 32 * std::max(sh.spb, 1);
     // window: 32 spb rows plus the halo, 4-entry alignment slack
@@ -1223,11 +1235,11 @@ PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
     return sh;
 }
 
-cudaError_t launch_coop(const void* fn, int G, size_t smem, void* args, cudaStream_t s) {
+cudaError_t launch_coop(const void* fn, int G, int block, size_t smem, void* args, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void* params[1] = {args};
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kPcgBlock), params, smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), params, smem, s);
 }
 
 template <typename VT>
@@ -1259,7 +1271,7 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.plan_wcap = (int)sh.region;
             cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
             if (e != cudaSuccess) return e;
-            return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.smem, &a, s);
+            return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
         }
         if (L.variant == SA_PCG_SHARED) return cudaErrorInvalidConfiguration;
     }
@@ -1292,7 +1304,7 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     a.wcap = sh.window ? (int)sh.wl : 0;
     cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    return launch_coop((const void*)k_pcg<VT>, sh.G, sh.smem, &a, s);
+    return launch_coop((const void*)k_pcg<VT>, sh.G, sh.block, sh.smem, &a, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1365,10 +1377,13 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, int n_dof, const double* That, double* dev64,
-                          float* dev32, cudaStream_t s) {
+                          float* dev32, cudaStream_t s, int part) {
     GatherArgs a{wlat_rows, wlat_rowdof, wlat_ptr, wlat_col, wlat_val, s_lat, k, n_dir,
-                 wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot, n_dof, That, dev64, dev32};
-    const long long threads = 32ll * ((long long)wlat_rows + n_dir) + n_dof;
+                 wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot, n_dof, That, dev64, dev32,
+                 part};
+    const long long threads = part == 1   ? 32ll * wlat_rows + n_dof
+                              : part == 2 ? 32ll * n_dir
+                                          : 32ll * ((long long)wlat_rows + n_dir) + n_dof;
     if (threads == 0) return cudaSuccess;
     k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -1378,23 +1393,24 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
-                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s) {
+                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only) {
     if (op.n == 0) return cudaSuccess;
+    const bool prep = only != 1 && n_dir > 0;   // Dirichlet increments for the flagged slices
     const unsigned blocks = (unsigned)((op.n_slices + (8 / kRhsSplit) - 1) / (8 / kRhsSplit));
     const unsigned pblocks = (unsigned)((n_dir + 255) / 256);
     if (precision == SA_MIXED) {
         float* dg = (float*)dir_scratch;
         float* g1 = dg + n_dir;
-        if (n_dir > 0) k_dir_prep<float><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
+        if (prep) k_dir_prep<float><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, dg, g1,
-                         F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
+                         F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only};
         k_theta_rhs<float><<<blocks, 256, 0, s>>>(a);
     } else {
         double* dg = (double*)dir_scratch;
         double* g1 = dg + n_dir;
-        if (n_dir > 0) k_dir_prep<double><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
+        if (prep) k_dir_prep<double><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev, dg,
-                          g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq};
+                          g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only};
         k_theta_rhs<double><<<blocks, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
