@@ -283,8 +283,12 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
                 delete c;
                 return SA_ERR_CUDA;
             }
+    // the bottom chain gets the higher priority: its projection then runs
+    // beside the lateral history sums instead of after them
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (!opt.stage_timing &&
-        (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
