@@ -484,12 +484,25 @@ def run_ours(args):
     st_j = ctx_j.step(th, dt, 0)
     jacobi_steps = K_c / (ms_j / 1e3)
     ctx_j.close()
+    # the same path with the pairwise history sums
+    ctx_p = fresh(prec, guess, use_graph=1, hist_mode=sa.SA_HIST_PAIRWISE)
+    ctx_p.step(th, dt, 3)
+    ms_p = time_graph(ctx_p, th, dt, K_c, stream)
+    pairwise_steps = K_c / (ms_p / 1e3)
+    ctx_p.close()
+    # plain FP64 (pairwise history sums, as the method states them) and FP64
+    # with the separable sums
     K64 = min(K, 12)
-    ctx64 = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1)
+    ctx64 = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1, hist_mode=sa.SA_HIST_PAIRWISE)
     ctx64.step(th, dt, 2)
     ms64 = time_graph(ctx64, th, dt, K64, stream)
     fp64_steps = K64 / (ms64 / 1e3)
     ctx64.close()
+    ctx64s = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1, hist_mode=sa.SA_HIST_SEPARABLE)
+    ctx64s.step(th, dt, 2)
+    ms64s = time_graph(ctx64s, th, dt, K_c, stream)
+    fp64_sep_steps = K_c / (ms64s / 1e3)
+    ctx64s.close()
 
     # ---- end to end through the public API with host buffers -------------------
     rng = np.random.default_rng(3)
@@ -534,9 +547,11 @@ def run_ours(args):
     # iteration) reads and writes the FP32 vector in five line passes
     pcg_bytes = ((iters_t + warm) * (6 * nnz_a + 4 * n_free) + (44 + 4 * warm) * n_free +
                  max(iters_t, 1.0) * 5 * 8 * n_free)
-    # history: FP32 lane-operations per pair (flux 8, T 6) on 128 FP32
-    # lanes/clk/SM; MUFU ex2 (32/clk/SM) is not binding
-    pairs_clk = 128.0 * q_pts / (8 * sz.q_lat + 6 * sz.q_bot)
+    # history: pairwise, FP32 lane-operations per pair (flux 8, T 6) on 128
+    # FP32 lanes/clk/SM (MUFU ex2, 32/clk/SM, not binding); separable, one
+    # FFMA per pair (the factors' exponentials are overhead)
+    sep = bool(sz.hist_separable)
+    pairs_clk = 128.0 if sep else 128.0 * q_pts / (8 * sz.q_lat + 6 * sz.q_bot)
     kernels = {
         "pcg": {"bound": "hbm", "bytes_per_launch": pcg_bytes, "ms": stage_avg["pcg"],
                 "achieved_gbs": pcg_bytes / (stage_avg["pcg"] * 1e-3) / 1e9,
@@ -550,10 +565,12 @@ def run_ours(args):
         k = kernels["history"]
         roof = {"bound": "alu", "achieved": k["achieved_gpairs"], "peak": k["peak_gpairs"],
                 "unit": "Gpairs/s", "frac": k["achieved_gpairs"] / k["peak_gpairs"],
-                "traffic": profile_traffic("k_history_mixed_block_meander", "sa_history.cu"),
-                "kernel": "k_history_mixed",
-                "peak_basis": f"{n_sm} SMs x {sm_max:.0f} MHz x {pairs_clk:.1f} pairs/clk/SM "
-                              "(FP32 pipe: 128 lanes/clk, 8 ops a flux pair, 6 a T pair)"}
+                "traffic": (profile_traffic("k_sep_gemm_block_meander", "sa_sep.cu") if sep else
+                            profile_traffic("k_history_mixed_block_meander", "sa_history.cu")),
+                "kernel": "k_sep_gemm + k_sep_reduce" if sep else "k_history_mixed",
+                "peak_basis": f"{n_sm} SMs x {sm_max:.0f} MHz x {pairs_clk:.1f} pairs/clk/SM " +
+                              ("(FP32 pipe: 128 lanes/clk, one FFMA a pair)" if sep else
+                               "(FP32 pipe: 128 lanes/clk, 8 ops a flux pair, 6 a T pair)")}
     else:
         k = kernels["pcg"]
         roof = {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
@@ -562,9 +579,10 @@ def run_ours(args):
                 "kernel": "k_pcg_smem (free block)", "peak_basis": "hbm_gbs of measured",
                 "note": "algorithmic bytes count every SpMV's pass over the operator; later "
                         "passes of a launch hit L2 (traffic: one ncu-captured launch)"}
-    # prologue, history (bottom, lateral), gather (bottom, lateral), projection,
-    # Dirichlet increments, right-hand side (two slice sets), PCG, finalize
-    launches_per_step = 11 + warm
+    # prologue, history (bottom, lateral; separable: a product and a reduction
+    # each), gather (bottom, lateral), projection, Dirichlet increments,
+    # right-hand side (two slice sets), PCG, finalize
+    launches_per_step = 11 + warm + (2 if sep else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
@@ -585,8 +603,13 @@ def run_ours(args):
         "other_guess": "extrapolate" if other == sa.SA_GUESS_EXTRAPOLATE else "previous",
         "steps_per_s_jacobi": world * jacobi_steps,
         "pcg_iters_per_step_jacobi": st_j.pcg_iters_total / K_c,
+        "steps_per_s_pairwise_history": world * pairwise_steps,
+        "history_evaluation": "separable" if sep else "pairwise",
         "fp64_steps_per_s": world * fp64_steps,
+        "fp64_history": "pairwise",
         "mixed_over_fp64": value / (world * fp64_steps),
+        "fp64_separable_steps_per_s": world * fp64_sep_steps,
+        "mixed_over_fp64_separable": value / (world * fp64_sep_steps),
         "pcg_iters_per_step": iters_avg, "bot_iters_per_step": bot_avg,
         "stage_ms": stage_avg, "stage_share": shares, "kernels": kernels,
         "roofline": roof,

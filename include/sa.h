@@ -104,11 +104,24 @@ typedef struct sa_options {
                                     control variables along a direction).  The bottom
                                     projection keeps Jacobi.  Same solution to the
                                     solver tolerance.                                */
+    int hist_mode;             /* evaluation of the history sums (same sums):
+                                  SA_HIST_AUTO (0, default): separable where every
+                                    lateral and Dirichlet face is an axis-aligned
+                                    rectangle (its quadrature points a tensor grid, the
+                                    normal a coordinate axis), pairwise otherwise;
+                                  SA_HIST_PAIRWISE (1): one exponential per
+                                    (point, source) pair;
+                                  SA_HIST_SEPARABLE (2): the Gaussian of each source
+                                    factorised along the face's two axes, each face's
+                                    sum a matrix product over the sources (one FMA a
+                                    pair); SA_ERR_ARG at sa_create_patch where a face
+                                    is not such a rectangle                          */
 } sa_options;
 
 enum { SA_PCG_AUTO = 0, SA_PCG_SHARED = 1, SA_PCG_GLOBAL = 2 };
 enum { SA_PRECOND_AUTO = 0, SA_PRECOND_JACOBI = 1, SA_PRECOND_FD = 2 };
 enum { SA_GUESS_PREVIOUS = 0, SA_GUESS_EXTRAPOLATE = 1 };
+enum { SA_HIST_AUTO = 0, SA_HIST_PAIRWISE = 1, SA_HIST_SEPARABLE = 2 };
 
 /* Fill o with the defaults listed above. */
 void sa_options_default(sa_options* o);
@@ -244,6 +257,7 @@ typedef struct sa_sizes {
     long long nnz_a;               /* nonzeros of the free-free operator              */
     long long step_index;          /* current n                                       */
     int n_elem;                    /* volume elements                                 */
+    int hist_separable;            /* 1: the history sums are evaluated separably     */
 } sa_sizes;
 sa_status sa_get_sizes(sa_ctx* ctx, sa_sizes* out);
 

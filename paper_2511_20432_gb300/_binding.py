@@ -20,6 +20,7 @@ SA_FP64, SA_MIXED = 0, 1
 SA_PCG_AUTO, SA_PCG_SHARED, SA_PCG_GLOBAL = 0, 1, 2
 SA_GUESS_PREVIOUS, SA_GUESS_EXTRAPOLATE = 0, 1
 SA_PRECOND_AUTO, SA_PRECOND_JACOBI, SA_PRECOND_FD = 0, 1, 2
+SA_HIST_AUTO, SA_HIST_PAIRWISE, SA_HIST_SEPARABLE = 0, 1, 2
 SA_FACE_NONE, SA_FACE_NEUMANN, SA_FACE_DIRICHLET = 0, 1, 2
 SA_FIELD_THAT, SA_FIELD_F, SA_FIELD_DTDN_LAT, SA_FIELD_TT_BOT, SA_FIELD_LAT_X, SA_FIELD_BOT_X = range(6)
 STAGES = ("prologue", "history", "gather", "bottom", "rhs", "pcg", "finalize")
@@ -31,7 +32,7 @@ class sa_options(C.Structure):
                 ("use_graph", C.c_int), ("device", C.c_int),
                 ("hist_points_per_lane", C.c_int), ("hist_warps", C.c_int),
                 ("stage_timing", C.c_int), ("pcg_variant", C.c_int),
-                ("initial_guess", C.c_int), ("precond", C.c_int)]
+                ("initial_guess", C.c_int), ("precond", C.c_int), ("hist_mode", C.c_int)]
 
 
 class sa_step_stats(C.Structure):
@@ -46,7 +47,8 @@ class sa_sizes(C.Structure):
     _fields_ = [("n_dof", C.c_int), ("n_free", C.c_int), ("n_dir", C.c_int),
                 ("q_lat", C.c_int), ("q_bot", C.c_int), ("n_src", C.c_int),
                 ("nnz_mk", C.c_longlong), ("nnz_a", C.c_longlong),
-                ("step_index", C.c_longlong), ("n_elem", C.c_int)]
+                ("step_index", C.c_longlong), ("n_elem", C.c_int),
+                ("hist_separable", C.c_int)]
 
 
 class SAError(RuntimeError):

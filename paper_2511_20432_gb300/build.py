@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsa.so")
-SOURCES = ["sa_api.cu", "sa_geom.cu", "sa_history.cu", "sa_solve.cu", "sa_noalloc.cu", "sa_batch.cu", "sa_mlp.cu", "sa_fd.cu"]
+SOURCES = ["sa_api.cu", "sa_geom.cu", "sa_history.cu", "sa_solve.cu", "sa_noalloc.cu", "sa_batch.cu", "sa_mlp.cu", "sa_fd.cu", "sa_sep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -249,6 +249,7 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
     if (opt.initial_guess != SA_GUESS_PREVIOUS && opt.initial_guess != SA_GUESS_EXTRAPOLATE)
         return SA_ERR_ARG;
     if (opt.precond < SA_PRECOND_AUTO || opt.precond > SA_PRECOND_FD) return SA_ERR_ARG;
+    if (opt.hist_mode < SA_HIST_AUTO || opt.hist_mode > SA_HIST_SEPARABLE) return SA_ERR_ARG;
     if (opt.hist_points_per_lane != 0 && opt.hist_points_per_lane != 1 &&
         opt.hist_points_per_lane != 2 && opt.hist_points_per_lane != 4)
         return SA_ERR_ARG;
@@ -582,6 +583,7 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         }
         face_q0.push_back(Q);
         face_e0.push_back((int)erow.size());
+        for (int f = 0; f <= 6; ++f) c->face_q0[lat ? 0 : 1][f] = face_q0[f];
         std::vector<int> ptr, col, slot;
         if (lat) {
             // compact rows: the distinct internal dofs, ascending
@@ -713,6 +715,11 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         cudaError_t e = launch_points32(c->q_lat, c->q_bot, c->lat64.p, c->bot64.p, c->x_ref,
                                         c->y_ref, c->z_top, c->lat32.p, c->bot32.p, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "points32");
+    }
+    {
+        SA_CUDA(c, cudaStreamSynchronize(s));
+        const sa_status st = sep_setup(c);
+        if (st != SA_OK) return st;
     }
 
     // ---- CSR pattern of M and K (natural order) ---------------------------------
@@ -1042,7 +1049,7 @@ sa_status ensure_sources(sa_ctx* c, double dt) {
     c->n_src = n;
     c->src_dt = dt;
     c->E = c->absorptivity * c->power * dt;
-    return SA_OK;
+    return sep_alloc(c);
 }
 
 sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
@@ -1096,10 +1103,14 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     }
     SA_MARK(SA_STAGE_HISTORY);
     for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
-        e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat, c->q_bot,
-                           c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p, c->x_ref, c->y_ref,
-                           c->z_top, c->src32F.p, c->src32T.p, c->src64F.p, c->src64T.p,
-                           c->s_lat.p, c->tt_bot.p, part == 2 ? sb : s, part);
+        if (c->sep.ok)
+            e = launch_sep(c, part, part == 2 ? sb : s);
+        else
+            e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat,
+                               c->q_bot, c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p,
+                               c->x_ref, c->y_ref, c->z_top, c->src32F.p, c->src32T.p,
+                               c->src64F.p, c->src64T.p, c->s_lat.p, c->tt_bot.p,
+                               part == 2 ? sb : s, part);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "history");
     }
     SA_MARK(SA_STAGE_GATHER);
@@ -1426,6 +1437,7 @@ sa_status sa_get_sizes(sa_ctx* c, sa_sizes* out) {
     out->nnz_a = c->nnz_a;
     out->step_index = c->n_step;
     out->n_elem = c->n_elem;
+    out->hist_separable = c->sep.ok ? 1 : 0;
     return SA_OK;
 }
 

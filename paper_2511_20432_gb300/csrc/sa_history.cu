@@ -25,6 +25,8 @@
 // path: warp-uniform global loads (L1/L2-resident table).  Every output point
 // is written by exactly one thread: deterministic, no atomics, no scratch
 // memory.
+#include <cmath>
+
 #include "sa_async.cuh"
 #include "sa_internal.h"
 
@@ -47,6 +49,7 @@ struct PrologueArgs {
     int n_src;
     const double2* pos;
     double dt, alpha, r2_8a, coefE;
+    float l2E;                // log2(coefE), for the FP32 coefficients
     int precision;
     double4* s64T;
     double4* s64F;
@@ -78,6 +81,30 @@ __global__ void k_prologue(PrologueArgs a) {
             a.s32T[i] = make_float4(sx, sy, na, (float)log2(cI));
             a.s32F[i] = make_float4(sx, sy, na, (float)log2(gI));
         }
+    }
+}
+
+// Mixed path: the FP32 coefficients from FP32 arithmetic on the age (the
+// FP64 transcendental functions run on GB300's narrow FP64 pipe; the FP32
+// results are rounded to FP32 in either case):
+//   log2 c = log2 E' - 1.5 log2(4 pi alpha age), log2 g = 1 - log2(4 alpha age) + log2 c.
+__global__ void k_prologue32(PrologueArgs a) {
+    const long long n1 = a.st_in ? a.st_in->n + 1 : a.n_explicit;
+    const int K = (int)(n1 < (long long)a.n_src ? n1 : (long long)a.n_src);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.st_out) a.st_out->n_active = K;
+    const float kLog2e = 1.44269504f, kLog2Pi = 1.65149613f;
+    const float four_alpha = (float)(4.0 * a.alpha);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) {
+        const long long I = i + 1;
+        const float age = (float)((double)(n1 - I) * a.dt + a.r2_8a);
+        const float fa = four_alpha * age;
+        const float l4a = log2f(fa);
+        const float na = -kLog2e / fa;
+        const float l2c = a.l2E - 1.5f * (kLog2Pi + l4a);
+        const double2 p = a.pos[i];
+        const float sx = (float)p.x, sy = (float)p.y;
+        a.s32T[i] = make_float4(sx, sy, na, l2c);
+        a.s32F[i] = make_float4(sx, sy, na, 1.0f - l4a + l2c);
     }
 }
 
@@ -114,20 +141,25 @@ __global__ void k_prologue_batch(PrologueBatchArgs a) {
     const long long K = n1 < (long long)a.n_src[inst] ? n1 : (long long)a.n_src[inst];
     if (l >= K) return;
     const long long I = l + 1;
-    const double age = (double)(n1 - I) * a.dt + a.r2_8a[inst];
-    const double aI = 1.0 / (4.0 * a.alpha * age);
-    const double base = 4.0 * kPi * a.alpha * age;
-    const double cI = a.coefE[inst] / (base * sqrt(base));
-    const double gI = 2.0 * aI * cI;
     const double2 p = a.pos[g];
     if (a.precision != SA_MIXED) {
+        const double age = (double)(n1 - I) * a.dt + a.r2_8a[inst];
+        const double aI = 1.0 / (4.0 * a.alpha * age);
+        const double base = 4.0 * kPi * a.alpha * age;
+        const double cI = a.coefE[inst] / (base * sqrt(base));
+        const double gI = 2.0 * aI * cI;
         a.s64T[g] = make_double4(p.x, p.y, aI, cI);
         a.s64F[g] = make_double4(p.x, p.y, aI, gI);
     } else {
+        // FP32 arithmetic on the age, as in k_prologue32
+        const float age = (float)((double)(n1 - I) * a.dt + a.r2_8a[inst]);
+        const float fa = (float)(4.0 * a.alpha) * age;
+        const float l4a = log2f(fa);
+        const float l2c = log2f((float)a.coefE[inst]) - 1.5f * (1.65149613f + l4a);
         const float sx = (float)p.x, sy = (float)p.y;
-        const float na = (float)(-aI * kLog2e);
-        a.s32T[g] = make_float4(sx, sy, na, (float)log2(cI));
-        a.s32F[g] = make_float4(sx, sy, na, (float)log2(gI));
+        const float na = -(float)kLog2e / fa;
+        a.s32T[g] = make_float4(sx, sy, na, l2c);
+        a.s32F[g] = make_float4(sx, sy, na, 1.0f - l4a + l2c);
     }
 }
 
@@ -415,9 +447,13 @@ cudaError_t launch_prologue(const DevStatus* st_in, long long n_explicit, DevSta
     a.s64F = s64F;
     a.s32T = s32T;
     a.s32F = s32F;
-    int blocks = (n_src + 255) / 256;
+    a.l2E = (float)std::log2(coefE);
+    int blocks = (n_src + 127) / 128;
     if (blocks < 1) blocks = 1;
-    k_prologue<<<blocks, 256, 0, s>>>(a);
+    if (s32T && !s64T)
+        k_prologue32<<<blocks, 128, 0, s>>>(a);
+    else
+        k_prologue<<<blocks, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -178,6 +178,40 @@ struct FdData {
     DBuf<unsigned char> dU[3], dUt[3], dlamc[3], dmd[3], dkd[3], S, Z;
 };
 
+// One face of the separable history evaluation: an axis-aligned rectangle
+// whose quadrature points are the tensor grid (A list) x (B list) at the
+// fixed coordinate dd along axis axd (coordinates relative: x - x_ref,
+// y - y_ref, z - z_top).  List index i = ea * nga + ga, j = eb * ngb + gb;
+// the point's output index is q0 + ((eb * nea + ea) * ngb + gb) * nga + ga.
+struct SepFace {
+    int q0;
+    int La, Lb;             // A and B list lengths
+    int nga, nea, ngb;
+    int axa, axb, axd;      // physical axes (0 x, 1 y, 2 z)
+    int a_off, b_off;       // list offsets in the coordinate array
+    int flux;               // 1: lateral flux (output s_lat = -sum); 0: bottom T~
+    double dd;              // fixed coordinate
+    double nsgn;            // outward normal along axd (flux faces), else 1
+};
+
+// Separable history plan: faces, tiles (lateral tiles first), the split of
+// the sources into units and the partial-sum buffers.
+struct SepPlan {
+    bool ok = false;
+    int tj[2] = {64, 64};          // tile width of lateral / bottom tiles
+    int n_tiles[2] = {0, 0};
+    int unit = 0, s_max = 0;       // sources per unit; units at the full scan
+    std::vector<SepFace> faces_h;
+    std::vector<int4> tiles_h;     // (face, i0, j0, 0)
+    std::vector<double> coord_h;
+    DBuf<SepFace> faces;
+    DBuf<int4> tiles;
+    DBuf<double> coord64;
+    DBuf<float> coord32;
+    DBuf<double> part64;           // [tile][unit][64 x 64]
+    DBuf<float> part32;
+};
+
 // Arguments of one PCG solve.
 struct PcgLaunch {
     SellView op;
@@ -353,6 +387,10 @@ struct sa_ctx {
     // (3-D) and the bottom projection (2-D)
     FdData fdm, fdb;
 
+    // separable history sums (csrc/sa_sep.cu)
+    SepPlan sep;
+    int face_q0[2][7] = {};          // first point of each face: lateral, bottom
+
     // extrapolated initial guesses (sa_options::initial_guess)
     DBuf<double> x_prev;             // T^{n-1}: free part, then the Dirichlet part
     DBuf<float> dx_extrap;           // n_free: proposed increment T^n - T^{n-1}
@@ -446,6 +484,10 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
                            double y_ref, double z_top, const float4* s32F,
                            const float4* s32T, const double4* s64F, const double4* s64T,
                            double* s_lat, double* tt_bot, cudaStream_t s, int part = 0);
+// sa_sep.cu
+sa_status sep_setup(sa_ctx* c);
+sa_status sep_alloc(sa_ctx* c);
+cudaError_t launch_sep(sa_ctx* c, int part, cudaStream_t s);
 cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,

@@ -104,13 +104,17 @@ def _lockstep(sa, wl, precision, n_check, every=1, **opts):
 
 
 VARIANTS = {"shared": 1, "global": 2}
+HIST = {"separable": 2, "pairwise": 1}
 
 
+@pytest.mark.parametrize("hist", list(HIST))
 @pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("theta", [1.0, 0.5])
-def test_cuboid_single_track_fp64(sa, theta, variant):
+def test_cuboid_single_track_fp64(sa, theta, variant, hist):
     wl = W.cuboid_single_track(theta=theta, n_steps=150)
-    err, ctx, m = _lockstep(sa, wl, sa.SA_FP64, 150, every=25, pcg_variant=VARIANTS[variant])
+    err, ctx, m = _lockstep(sa, wl, sa.SA_FP64, 150, every=25, pcg_variant=VARIANTS[variant],
+                            hist_mode=HIST[hist])
+    assert ctx.sizes().hist_separable == (hist == "separable")
     assert err["s_lat"] <= 1e-12 and err["tt_bot"] <= 1e-12, err
     assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
     # reconstruction T = T~ + T^ at interior and boundary points
@@ -122,11 +126,14 @@ def test_cuboid_single_track_fp64(sa, theta, variant):
     assert rel_linf(T, T_ref) <= TOL_FP64
 
 
+@pytest.mark.parametrize("hist", list(HIST))
 @pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("theta", [1.0, 0.5])
-def test_cuboid_single_track_mixed(sa, theta, variant):
+def test_cuboid_single_track_mixed(sa, theta, variant, hist):
     wl = W.cuboid_single_track(theta=theta, n_steps=150)
-    err, ctx, m = _lockstep(sa, wl, sa.SA_MIXED, 150, every=15, pcg_variant=VARIANTS[variant])
+    err, ctx, m = _lockstep(sa, wl, sa.SA_MIXED, 150, every=15, pcg_variant=VARIANTS[variant],
+                            hist_mode=HIST[hist])
+    assert ctx.sizes().hist_separable == (hist == "separable")
     assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
     assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
 
@@ -198,6 +205,61 @@ def test_multichunk_ragged_tiles(sa, P, NW):
         else:
             assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
             assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+
+
+def test_separable_ragged_tiles_and_units(sa):
+    """Separable history sums on a box whose lists are ragged (66 x 8, 66 x
+    9 and 8 x 9 points: two row tiles, 32-wide column tiles) with mixed
+    degrees, over a meander of several hundred sources (several units)."""
+    patch = W.cuboid_patch((2.2e-3, 0.4e-3, 0.3e-3), (22, 4, 3), (2, 1, 2))
+    z = float(patch.ctrl[-1, 0, 0, 2])
+    scan = W.meander(0.2e-3, 2.0e-3, 0.12e-3, 0.08e-3, 3, z, 180.0, 0.4, 1.5)
+    wl = W.Workload("sep", patch, W.MAT_DEFAULT, scan, dt=4e-6, theta=0.5, n_steps=400)
+    for prec in (sa.SA_FP64, sa.SA_MIXED):
+        err, ctx, m = _lockstep(sa, wl, prec, 400, every=50, hist_mode=2)
+        assert ctx.sizes().hist_separable == 1
+        assert ctx.sizes().n_src > 256
+        if prec == sa.SA_FP64:
+            assert err["s_lat"] <= 1e-12 and err["tt_bot"] <= 1e-12, err
+            assert err["F"] <= TOL_FP64 and err["That"] <= TOL_FP64, err
+        else:
+            assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
+            assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+
+
+def test_separable_requires_rectangular_faces(sa):
+    """SA_HIST_SEPARABLE is refused on a curved patch; AUTO falls back to the
+    pairwise sums there and picks the separable ones on a box."""
+    wl = _wl_for(W.distorted_block(weights=True))
+    with pytest.raises(sa.SAError) as e:
+        gpu_context(wl, sa.SA_MIXED, hist_mode=2)
+    assert e.value.status == sa.SA_ERR_ARG
+    assert gpu_context(wl, sa.SA_MIXED).sizes().hist_separable == 0
+    assert gpu_context(_wl_for(_patch_cases()["cuboid"]), sa.SA_MIXED).sizes().hist_separable == 1
+
+
+def test_separable_matches_pairwise_full_size(sa):
+    """64x64x16 block, 1,200 steps of the 20-track meander: the separable sums
+    (64 x 48 lateral and 64 x 64 bottom tiles) against the pairwise ones, in
+    both precisions, and the mixed ones against the FP64 pairwise sums."""
+    wl = W.block_meander(n_tracks=20, theta=0.5)
+    out = {}
+    for prec in (sa.SA_FP64, sa.SA_MIXED):
+        for hist in (1, 2):
+            ctx = gpu_context(wl, prec, use_graph=1, hist_mode=hist)
+            assert ctx.sizes().hist_separable == (hist == 2)
+            ctx.step(wl.theta, wl.dt, 1200)
+            out[prec, hist] = (ctx.field(sa.SA_FIELD_DTDN_LAT), ctx.field(sa.SA_FIELD_TT_BOT),
+                               ctx.field(sa.SA_FIELD_THAT))
+            ctx.close()
+    ref = out[sa.SA_FP64, 1]
+    for k in range(2):
+        scale = np.abs(ref[k]).max()
+        assert np.abs(out[sa.SA_FP64, 2][k] - ref[k]).max() <= 1e-12 * scale
+        assert np.abs(out[sa.SA_MIXED, 2][k] - ref[k]).max() <= TOL_MIXED_REL * scale
+        assert np.abs(out[sa.SA_MIXED, 1][k] - ref[k]).max() <= TOL_MIXED_REL * scale
+    assert np.abs(out[sa.SA_FP64, 2][2] - ref[2]).max() <= 1e-9 * np.abs(ref[2]).max()
+    assert np.abs(out[sa.SA_MIXED, 2][2] - ref[2]).max() <= TOL_MIXED_ABS
 
 
 def test_degenerate_cases(sa):
@@ -309,6 +371,7 @@ def test_full_size_block_sampled(sa):
     F_prev = ctx.field(sa.SA_FIELD_F)
     st = ctx.step(wl.theta, wl.dt, 1)
     assert st.n_active_sources == n_steps
+    assert ctx.sizes().hist_separable == 1
     geom = PatchGeom(wl.patch)
     from oracle import sources as osrc
     xs = osrc.discretize(wl.scan, wl.dt)
