@@ -1160,10 +1160,10 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
-        // small system: a few blocks of ~8 slices (cheap barriers); 256
-        // threads a block beside the lateral chain, so it fits next to it
+        // small system: a few blocks of ~8 slices, so that most SMs stay
+        // free for the lateral chain beside it
         L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices + 7) / 8));
-        L.block = overlap ? 256 : 0;
+        L.block = 0;
         L.ksplit = 0;
         e = launch_pcg(c->opt.precision, L, sb);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");

@@ -64,4 +64,42 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async;" ::: "memory");
 }
 
+// Grid barrier of a cooperative launch.  *count is zero at launch and only
+// grows: barrier k (nb counts them, every thread of every block alike)
+// completes when it reaches k x gridDim.x.  Thread 0 posts its block's arrival
+// with a release reduction (no reply to wait for) and polls with acquire
+// loads; a wait over 2 s or 2^30 polls, or a timeout flagged elsewhere, sets
+// timeout_flag in *err and returns false.
+__device__ __forceinline__ bool count_barrier(unsigned* count, unsigned& nb, int* err,
+                                              int timeout_flag) {
+    __shared__ int ok;
+    __syncthreads();
+    ++nb;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned target = nb * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+        const unsigned long long t0 = global_ns();
+        long long spins = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((++spins & 255) == 0) {
+                if (global_ns() - t0 > 2000000000ull || spins > (1ll << 30)) {
+                    atomicOr(err, timeout_flag);
+                    ok = 0;
+                    break;
+                }
+                if (*((volatile int*)err) & timeout_flag) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 }  // namespace sa_dev

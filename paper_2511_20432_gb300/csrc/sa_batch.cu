@@ -19,6 +19,7 @@
 #include <sstream>
 #include <type_traits>
 
+#include "sa_async.cuh"
 #include "sa_internal.h"
 
 cudaError_t launch_prologue_batch(const DevStatus* st, int n_src_total, int n_inst,
@@ -151,41 +152,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// grid barrier with a bounded wait (cooperative launch)
-__device__ bool bgrid_barrier(unsigned* count, unsigned* gen, int* err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned* vgen = gen;
-        const unsigned my = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            long long spins = 0;
-            while (*vgen == my) {
-                if ((++spins & 255) == 0) {
-                    if (global_ns() - t0 > 2000000000ull || spins > (1ll << 30)) {
-                        atomicOr(err, SA_DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    if (*((volatile int*)err) & SA_DEV_TIMEOUT) {
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
+// grid barrier with a bounded wait (cooperative launch; count starts at zero)
+__device__ __forceinline__ bool bgrid_barrier(unsigned* count, unsigned& nb, int* err) {
+    return sa_dev::count_barrier(count, nb, err, SA_DEV_TIMEOUT);
 }
 
 // One instance's fast-diagonalization data (device pointers of its context).
@@ -251,7 +220,7 @@ __device__ __forceinline__ int bcol(const BPcgArgs<VT>& a, long long e, int row)
 // operator-precision copy.  Lines have at most 128 entries.
 template <typename VT>
 __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsigned* bc,
-                          unsigned* bg, int* err) {
+                          unsigned& bg, int* err) {
     const int lane = threadIdx.x & 31;
     const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * (blockDim.x >> 5);
@@ -340,7 +309,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
     const int gw = blockIdx.x * nwb + (threadIdx.x >> 5);
     const int nw = gridDim.x * nwb;
     unsigned* bc = &a.st->bar_count[2 + a.which];
-    unsigned* bg = &a.st->bar_gen[2 + a.which];
+    unsigned bg = 0;                       // barriers passed
     int* err = &a.st->err;
     const int S = a.n_slices, NI = a.n_inst;
     volatile double* is = a.is;

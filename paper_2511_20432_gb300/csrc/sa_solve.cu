@@ -291,40 +291,10 @@ __device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
 // release store; the others poll the generation with acquire loads.
 struct GridSync {
     unsigned* count;
-    unsigned* gen;
     int* err;
     double* part;
-    __device__ bool barrier() const {
-        __shared__ int ok;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            ok = 1;
-            const unsigned my = ld_acquire(gen);
-            const unsigned arrived = atom_add_acq_rel(count, 1u) + 1u;
-            if (arrived == gridDim.x) {
-                st_relaxed(count, 0u);
-                st_release(gen, my + 1u);
-            } else {
-                const unsigned long long t0 = global_ns();
-                long long spins = 0;
-                while (ld_acquire(gen) == my) {
-                    if ((++spins & 255) == 0) {
-                        if (global_ns() - t0 > 2000000000ull || spins > (1ll << 30)) {
-                            atomicOr(err, SA_DEV_TIMEOUT);
-                            ok = 0;
-                            break;
-                        }
-                        if (*((volatile int*)err) & SA_DEV_TIMEOUT) {
-                            ok = 0;
-                            break;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        return ok != 0;
-    }
+    mutable unsigned nb = 0;   // barriers passed (every thread counts alike)
+    __device__ bool barrier() const { return count_barrier(count, nb, err, SA_DEV_TIMEOUT); }
     // slot: first of NV consecutive partial rows of length gridDim.x
     template <int NV>
     __device__ bool reduce(double (&v)[NV], int slot, double (&out)[NV]) const {
@@ -534,7 +504,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(PcgArgs<VT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VT* sq = (VT*)smem_raw;                 // 1024
     VT* win = sq + 1024;                    // window
-    GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
+    GridSync sync{&a.st->bar_count[a.which], &a.st->err, a.part};
     const int n = a.A.n;
     int s0, s1;
     block_slices(a.A.n_slices, s0, s1);
@@ -947,7 +917,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     __shared__ AT scl[4];                   // alpha, gamma (previous) in AT
     __shared__ int state;                   // 0 run, 1 converged, 2 nan, 3 iteration cap
     __shared__ unsigned long long wmbar;    // window copy completion
-    GridSync sync{&a.st->bar_count[a.which], &a.st->bar_gen[a.which], &a.st->err, a.part};
+    GridSync sync{&a.st->bar_count[a.which], &a.st->err, a.part};
     if (threadIdx.x == 0) {
         mbar_init(&wmbar, 1);
         mbar_fence_init();
