@@ -707,6 +707,8 @@ struct SmemArgs {
     FdView fd;             // fast-diagonalization preconditioner (fd.on), else Jacobi
     int fd_mmax;           // longest grid line (per-warp scratch entries)
     int plan_wcap;         // window entries reserved in shared memory
+    int fd_w2;             // 1: the region holds three m x m matrices (the fused
+                           // pass's second one staged too), 0: two
 };
 
 template <typename T>
@@ -804,7 +806,8 @@ __device__ __forceinline__ void fd_line_matvec(const VT* Wb, const VT* xs, int m
 }
 
 template <typename VT>
-__device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* xs, VT* out) {
+__device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* xs, VT* out,
+                         bool w2s) {
     const int lane = threadIdx.x & 31;
     // lines go to warp w of every block before warp w + 1 of any: spread over SMs
     const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
@@ -848,17 +851,21 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
                     if (o < m) xs[o] = y[t] / (li + ll[o]);
                 }
                 __syncwarp();
-                const VT* W2 = (const VT*)fd.Ut[d];
+                if (w2s) {
+                    fd_line_matvec(wbuf + 2 * mmax * mmax, xs, m, lane, y);
+                } else {
+                    const VT* W2 = (const VT*)fd.Ut[d];
 #pragma unroll
-                for (int t = 0; t < kFdPerLane; ++t) y[t] = (VT)0;
+                    for (int t = 0; t < kFdPerLane; ++t) y[t] = (VT)0;
 #pragma unroll 4
-                for (int a = 0; a < m; ++a) {
-                    const VT xa = xs[a];
-                    const VT* Wa = W2 + a * m;
+                    for (int a = 0; a < m; ++a) {
+                        const VT xa = xs[a];
+                        const VT* Wa = W2 + a * m;
 #pragma unroll
-                    for (int t = 0; t < kFdPerLane; ++t) {
-                        const int o = lane + 32 * t;
-                        if (o < m) y[t] = fma(__ldg(Wa + o), xa, y[t]);
+                        for (int t = 0; t < kFdPerLane; ++t) {
+                            const int o = lane + 32 * t;
+                            if (o < m) y[t] = fma(__ldg(Wa + o), xa, y[t]);
+                        }
                     }
                 }
             }
@@ -880,6 +887,8 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
             const int np = pass + 1;
             const int dn = np < nd ? np : npass - 1 - np;
             fd_stage(wbuf + (np & 1) * mmax * mmax, (const VT*)(np < nd ? fd.U[dn] : fd.Ut[dn]), fd.m[dn]);
+            // the fused pass's second matrix (U_d^T) in the third buffer
+            if (w2s && np == nd - 1) fd_stage(wbuf + 2 * mmax * mmax, (const VT*)fd.Ut[dn], fd.m[dn]);
             if (!sync.barrier()) return false;
         }
     }
@@ -1021,7 +1030,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     // u = P^{-1} r, published (Jacobi: local; fast diagonalization: passes)
     auto precondition = [&]() -> bool {
         if (fd) {
-            if (!fd_apply<VT>(a.fd, sync, win, xs, a.ul)) return false;
+            if (!fd_apply<VT>(a.fd, sync, win, xs, a.ul, a.fd_w2 != 0)) return false;
             if (!sync.barrier()) return false;
             for (int t = threadIdx.x; t < nr; t += blockDim.x) {
                 const VT u = __ldcg(a.ul + row0 + t);
@@ -1167,7 +1176,7 @@ Op<VT> make_op(const SellView& s, const void* val) {
 // (so the 32 warps of a block are busy), window length, shared memory.
 template <typename VT>
 struct PcgShape {
-    int G, block, spb, ks, rcap, fd_mmax;
+    int G, block, spb, ks, rcap, fd_mmax, fd_w2;
     long long wl, region;
     bool window;
     size_t smem;
@@ -1191,13 +1200,18 @@ PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
     sh.wl = 32ll * sh.spb + (L.op.dmax - L.op.dmin) + 8;
     // the preconditioner's m x m matrix reuses the window region
     const int mmax = (pipelined && L.fd.on) ? std::max(L.fd.m[0], std::max(L.fd.m[1], L.fd.m[2])) : 0;
-    const long long fdw = 2ll * mmax * mmax;   // two staged matrices
+    long long fdw = 2ll * mmax * mmax;   // two staged matrices (three when they fit)
     sh.fd_mmax = mmax;
     const size_t fixed = 1024 * sizeof(VT) +
                          (pipelined ? (size_t)kSmemVecs * sh.rcap * sizeof(double) + 2 * sh.rcap * sizeof(VT) +
                                           (size_t)32 * mmax * sizeof(VT)
                                     : 0);
     sh.fits = fixed + fdw * sizeof(VT) <= kSmemCap;
+    sh.fd_w2 = 0;
+    if (mmax > 0 && fixed + 3ll * mmax * mmax * sizeof(VT) <= kSmemCap) {
+        fdw = 3ll * mmax * mmax;
+        sh.fd_w2 = 1;
+    }
     sh.window = L.op.col16 != nullptr && L.pad >= -L.op.dmin + 4 && L.pad >= L.op.dmax + 4 &&
                 fixed + std::max(sh.wl, fdw) * sizeof(VT) <= kSmemCap;
     sh.region = sh.window ? std::max(sh.wl, fdw) : fdw;
@@ -1239,6 +1253,7 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.fd = L.fd;
             a.fd_mmax = sh.fd_mmax;
             a.plan_wcap = (int)sh.region;
+            a.fd_w2 = sh.fd_w2;
             cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
             if (e != cudaSuccess) return e;
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
