@@ -892,6 +892,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
     SA_ALLOC(c, c->F1, c->n_dof);
     SA_ALLOC(c, c->gnew, std::max(c->n_dir, 1));
     SA_ALLOC(c, c->bbot, std::max(c->n_dir, 1));
+    SA_ALLOC(c, c->r0bot, std::max(c->n_dir, 1));
+    SA_ALLOC(c, c->bsqbot, std::max(c->n_dir, 1));
     SA_ALLOC(c, c->rhs, nwork);
     SA_ALLOC(c, c->r0, nwork);
     SA_ALLOC(c, c->bsq, nwork);
@@ -1114,29 +1116,37 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "history");
     }
     SA_MARK(SA_STAGE_GATHER);
-    for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
-        e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
-                          c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
-                          c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, c->n_dof,
-                          c->That.p, c->dev64.p, c->dev32.p, part == 2 ? sb : s, part);
-        if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
-    }
-    const bool mixed = c->opt.precision == SA_MIXED;
-    SA_MARK(SA_STAGE_BOTTOM);
     const bool extrap = c->opt.initial_guess == SA_GUESS_EXTRAPOLATE;
     if (extrap) {
         // proposals T^n - T^{n-1} (main solve) and 2 g^n - g^{n-1} (projection)
         e = launch_extrap(c->n_free, c->n_dir, c->That.p, c->x_prev.p, c->dx_extrap.p,
                           c->x_prev.p + c->n_free, c->gnew.p, sb);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "extrapolated guess");
+    } else if (c->n_dir > 0) {
+        // x0 of the projection: g^n (the Dirichlet part of the state)
+        e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
+                            cudaMemcpyDeviceToDevice, sb);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
     }
+    // the bottom rows also form the projection's initial residual
+    BotResid br;
+    br.mptr = c->mbot_ptr.p;
+    br.mcol = c->mbot_col.p;
+    br.mval = c->mbot_val.p;
+    br.g0 = c->gnew.p;
+    br.r0 = c->r0bot.p;
+    br.bsq = c->bsqbot.p;
+    for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
+        e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
+                          c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
+                          c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, c->n_dof,
+                          c->That.p, c->dev64.p, c->dev32.p, part == 2 ? sb : s, part,
+                          c->n_dir > 0 ? br : BotResid());
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
+    }
+    const bool mixed = c->opt.precision == SA_MIXED;
+    SA_MARK(SA_STAGE_BOTTOM);
     if (c->n_dir > 0) {
-        // x0 = g^n (the Dirichlet part of the state), or its extrapolation
-        if (!extrap) {
-            e = cudaMemcpyAsync(c->gnew.p, c->That.p + c->n_free, sizeof(double) * c->n_dir,
-                                cudaMemcpyDeviceToDevice, sb);
-            if (e != cudaSuccess) return sa_cuda_fail(c, e, "g0");
-        }
         PcgLaunch L;
         L.op = sell_view(c->mbot_s);
         L.val = mixed ? (const void*)c->mbot_sval32.p : (const void*)c->mbot_sval.p;
@@ -1146,8 +1156,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.dx0 = nullptr;
         L.dx0_scale = nullptr;
         L.b = c->bbot.p;
-        L.r0 = nullptr;
-        L.bsq = nullptr;
+        L.r0 = c->r0bot.p;       // r0 = b_bot - M_bot g0 from the gather (FP64)
+        L.bsq = c->bsqbot.p;
         L.x = c->gnew.p;
         L.w64 = c->work64.p;
         L.vpad = c->workpad.p;

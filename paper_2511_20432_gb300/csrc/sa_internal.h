@@ -357,6 +357,7 @@ struct sa_ctx {
     DBuf<double> That;        // internal order (n_dof)
     DBuf<double> F0, F1;      // internal order (n_dof)
     DBuf<double> gnew, bbot;  // n_dir
+    DBuf<double> r0bot, bsqbot;   // n_dir: projection's initial residual and b_bot^2
     DBuf<double> rhs, r0, bsq;   // n_free
     DBuf<double> dirv;           // 2 n_dir: Dirichlet increments for the theta RHS
     DBuf<double> work64;                 // PCG work: 5 x nwork (FP64)
@@ -494,12 +495,23 @@ cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, con
                                double scale, double* T_out, cudaStream_t s);
 
 // sa_solve.cu
+// With the bottom rows of the gather, optionally the bottom projection's
+// initial residual r0 = b_bot - M_bot g0 (FP64) and b_bot^2.
+struct BotResid {
+    const int* mptr = nullptr;    // M_bot CSR over the Dirichlet control variables
+    const int* mcol = nullptr;
+    const double* mval = nullptr;
+    const double* g0 = nullptr;   // initial guess
+    double* r0 = nullptr;
+    double* bsq = nullptr;
+};
 cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat_ptr,
                           const int* wlat_col, const double* wlat_val, const double* s_lat,
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, int n_dof, const double* That, double* dev64,
-                          float* dev32, cudaStream_t s, int part = 0);
+                          float* dev32, cudaStream_t s, int part = 0,
+                          const BotResid& br = BotResid());
 cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,

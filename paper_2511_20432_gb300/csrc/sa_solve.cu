@@ -51,6 +51,7 @@ struct GatherArgs {
     double* dev64;
     float* dev32;
     int part;              // 0: everything; 1: lateral rows and dev; 2: bottom rows
+    BotResid br;           // br.mptr != null: also r0 = b_bot - M_bot g0 and b_bot^2
 };
 
 __global__ void k_gather(GatherArgs a) {
@@ -83,7 +84,19 @@ __global__ void k_gather(GatherArgs a) {
         for (int s = a.bptr[r] + lane; s < a.bptr[r + 1]; s += 32)
             acc += a.bval[s] * (a.Tc - a.tt_bot[a.bcol[s]]);
         acc = warp_sum(acc);
-        if (lane == 0) a.bbot[r] = acc;
+        double mg = 0.0;
+        if (a.br.mptr) {
+            for (int s = a.br.mptr[r] + lane; s < a.br.mptr[r + 1]; s += 32)
+                mg += a.br.mval[s] * a.br.g0[a.br.mcol[s]];
+            mg = warp_sum(mg);
+        }
+        if (lane == 0) {
+            a.bbot[r] = acc;
+            if (a.br.mptr) {
+                a.br.r0[r] = acc - mg;
+                a.br.bsq[r] = acc * acc;
+            }
+        }
     }
 }
 
@@ -1362,10 +1375,10 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, int n_dof, const double* That, double* dev64,
-                          float* dev32, cudaStream_t s, int part) {
+                          float* dev32, cudaStream_t s, int part, const BotResid& br) {
     GatherArgs a{wlat_rows, wlat_rowdof, wlat_ptr, wlat_col, wlat_val, s_lat, k, n_dir,
                  wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot, n_dof, That, dev64, dev32,
-                 part};
+                 part, br};
     const long long threads = part == 1   ? 32ll * wlat_rows + n_dof
                               : part == 2 ? 32ll * n_dir
                                           : 32ll * ((long long)wlat_rows + n_dir) + n_dof;
