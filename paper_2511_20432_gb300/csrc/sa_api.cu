@@ -1084,14 +1084,18 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     } while (0)
     cudaError_t e;
     SA_MARK(SA_STAGE_PROLOGUE);
-    e = launch_prologue(c->st.p, 0, c->st.p, c->n_src, c->src_pos.p, dt, alpha,
-                        c->spot_radius * c->spot_radius / (8.0 * alpha),
-                        c->opt.half_space_factor * c->E / (c->rho * c->cp), c->opt.precision,
-                        c->opt.precision == SA_FP64 ? c->src64T.p : nullptr,
-                        c->opt.precision == SA_FP64 ? c->src64F.p : nullptr,
-                        c->opt.precision == SA_MIXED ? c->src32T.p : nullptr,
-                        c->opt.precision == SA_MIXED ? c->src32F.p : nullptr, s);
-    if (e != cudaSuccess) return sa_cuda_fail(c, e, "prologue");
+    // the mixed separable sums form the source coefficients themselves
+    const bool fused_coef = c->sep.ok && c->opt.precision == SA_MIXED;
+    if (!fused_coef) {
+        e = launch_prologue(c->st.p, 0, c->st.p, c->n_src, c->src_pos.p, dt, alpha,
+                            c->spot_radius * c->spot_radius / (8.0 * alpha),
+                            c->opt.half_space_factor * c->E / (c->rho * c->cp), c->opt.precision,
+                            c->opt.precision == SA_FP64 ? c->src64T.p : nullptr,
+                            c->opt.precision == SA_FP64 ? c->src64F.p : nullptr,
+                            c->opt.precision == SA_MIXED ? c->src32T.p : nullptr,
+                            c->opt.precision == SA_MIXED ? c->src32F.p : nullptr, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "prologue");
+    }
     // Two chains after the prologue: the bottom chain (history of the bottom
     // points, b_bot, the projection) on the second stream, beside the
     // lateral chain (history of the lateral points, F, the right-hand side of
@@ -1106,7 +1110,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     SA_MARK(SA_STAGE_HISTORY);
     for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
         if (c->sep.ok)
-            e = launch_sep(c, part, part == 2 ? sb : s);
+            e = launch_sep(c, part, dt, part == 2 ? sb : s);
         else
             e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat,
                                c->q_bot, c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p,

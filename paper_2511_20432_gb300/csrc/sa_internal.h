@@ -488,7 +488,7 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
 // sa_sep.cu
 sa_status sep_setup(sa_ctx* c);
 sa_status sep_alloc(sa_ctx* c);
-cudaError_t launch_sep(sa_ctx* c, int part, cudaStream_t s);
+cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s);
 cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,

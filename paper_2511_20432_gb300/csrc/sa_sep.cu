@@ -27,8 +27,8 @@
 // into fresh registers and then added to the unit's sum (the rounding error
 // grows with the chunk length plus the number of chunks, not with the
 // unit); FP64 path: FP64 throughout.  The unit sums go to a partial buffer;
-// a second kernel adds the active units of every point in FP64, in unit
-// order, and writes the point's value: deterministic, no atomics.
+// a second kernel adds the active units of every point in a fixed order and
+// writes the point's value: deterministic, no atomics.
 //
 // This is not the paper's evaluation (it sums pairwise); it is the same sum
 // reordered by the distributive law, and applies only where the faces are
@@ -69,7 +69,15 @@ struct SepArgs {
     int tile0;                // first tile of this launch
     int n_tiles;              // tiles of this launch
     int unit, s_max;
-    const DevStatus* st;
+    DevStatus* st;
+    // coef = 1 (mixed path): the source coefficients are formed here from the
+    // positions and the step index, as the FP32 prologue forms them (no
+    // prologue launch; the reduction records the active count)
+    int coef;
+    int n_src;
+    const double2* pos;
+    double dt, r2_8a, four_alpha;
+    float l2E;
     const float* c32;
     const double* c64;
     const float4* s32F;
@@ -93,6 +101,13 @@ struct SrcOf<double> {
     using V = double4;
 };
 
+// Active sources at this step: min(n + 1, n_src) (the prologue's count).
+__device__ __forceinline__ int active_sources(const SepArgs& a) {
+    if (!a.coef) return a.st->n_active;
+    const long long n1 = a.st->n + 1;
+    return (int)(n1 < (long long)a.n_src ? n1 : (long long)a.n_src);
+}
+
 template <typename T, int TJ>
 __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
     constexpr int NT = 2 * TJ;           // (64 / 8) x (TJ / 4) threads
@@ -109,7 +124,7 @@ __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
     __shared__ T4 prm[kMaxUnit];         // per source: s_A, s_B, exponent scale, offset
     __shared__ T mul[kMaxUnit];
     const int tile = a.tile0 + (int)blockIdx.x;
-    const int K = a.st->n_active;
+    const int K = active_sources(a);
     const int u = unit_len(K, a.s_max, kKC);
     const int k0 = (int)blockIdx.y * u;
     if (k0 >= K) return;                 // no sources for this unit (uniform per CTA)
@@ -135,7 +150,24 @@ __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
         for (int t = threadIdx.x; t < npad; t += NT) {
             T sa = 0, sb = 0, sc = 0, off = 0, m = 0;
             if (t < n) {
-                const V sv = src[k0 + t];
+                V sv;
+                if (kMixed && a.coef) {
+                    // (sx, sy, -a log2 e, log2 w) from the age, in FP32:
+                    // log2 c = log2 E' - 1.5 log2(4 pi alpha age),
+                    // log2 g = 1 - log2(4 alpha age) + log2 c
+                    const long long I = k0 + t + 1;
+                    const float age = (float)((double)(a.st->n + 1 - I) * a.dt + a.r2_8a);
+                    const float fa = (float)a.four_alpha * age;
+                    const float l4a = log2f(fa);
+                    const float l2c = a.l2E - 1.5f * (1.65149613f + l4a);
+                    const double2 p = a.pos[k0 + t];
+                    sv.x = (float)p.x;
+                    sv.y = (float)p.y;
+                    sv.z = -1.44269504f / fa;
+                    sv.w = f.flux ? 1.0f - l4a + l2c : l2c;
+                } else {
+                    sv = src[k0 + t];
+                }
                 // sources lie on the top plane (relative z = 0)
                 auto sc3 = [&](int ax) { return ax == 0 ? (T)sv.x : (ax == 1 ? (T)sv.y : T(0)); };
                 sa = sc3(f.axa);
@@ -248,10 +280,12 @@ __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
     }
 }
 
-// Sum of the active units of every point of the launch's tiles, in unit
-// order, in FP64; writes s_lat = -sum (flux faces) or tt_bot = sum.
+// Sum of the active units of every point of the launch's tiles; writes
+// s_lat = -sum (flux faces) or tt_bot = sum.
 // Four lanes per point: lane g adds units g, g + 4, ... in order; the four
-// sums are combined by the same butterfly on every lane.
+// sums are combined by the same butterfly on every lane.  The sum runs in the
+// partials' precision (FP64 arithmetic is slow on this part; at most a few
+// dozen unit sums of one sign per point in the mixed path).
 template <typename T, int TJ>
 __global__ void __launch_bounds__(256) k_sep_reduce(SepArgs a) {
     constexpr int kKC = chunk_of<T>();
@@ -266,15 +300,16 @@ __global__ void __launch_bounds__(256) k_sep_reduce(SepArgs a) {
     const int jj = e / kTI, ii = e - jj * kTI;
     const int i = td.y + ii, j = td.z + jj;
     ok = ok && i < f.La && j < f.Lb;
-    const int K = a.st->n_active;
+    const int K = active_sources(a);
+    if (a.coef && g == 0) a.st->n_active = K;
     const int u = unit_len(K, a.s_max, kKC);
     const int ns = K > 0 ? (K + u - 1) / u : 0;
-    double tot = 0.0;
+    T tot = T(0);
     if (ok) {
         const T* p = (sizeof(T) == 4 ? (const T*)a.p32 : (const T*)a.p64) +
                      (size_t)tile * a.s_max * kPStride + e;
 #pragma unroll 4
-        for (int s = lane4; s < ns; s += 4) tot += (double)p[(size_t)s * kPStride];
+        for (int s = lane4; s < ns; s += 4) tot += p[(size_t)s * kPStride];
     }
     tot += __shfl_xor_sync(0xffffffffu, tot, 1);
     tot += __shfl_xor_sync(0xffffffffu, tot, 2);
@@ -283,9 +318,9 @@ __global__ void __launch_bounds__(256) k_sep_reduce(SepArgs a) {
     const int eb = j / f.ngb, gb = j - eb * f.ngb;
     const int q = f.q0 + ((eb * f.nea + ea) * f.ngb + gb) * f.nga + ga;
     if (f.flux)
-        a.s_lat[q] = -tot;
+        a.s_lat[q] = -(double)tot;
     else
-        a.tt_bot[q] = tot;
+        a.tt_bot[q] = (double)tot;
 }
 
 template <typename T, int TJ>
@@ -506,8 +541,10 @@ sa_status sep_alloc(sa_ctx* c) {
     return SA_OK;
 }
 
-// part 0: every face; 1: lateral faces; 2: Dirichlet faces.
-cudaError_t launch_sep(sa_ctx* c, int part, cudaStream_t s) {
+// part 0: every face; 1: lateral faces; 2: Dirichlet faces.  Mixed path:
+// the source coefficients of step n + 1 are formed in the product kernels
+// (no prologue launch before them).
+cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s) {
     const SepPlan& P = c->sep;
     for (int kind = 0; kind < 2; ++kind) {
         if (part == 1 && kind == 1) continue;
@@ -520,6 +557,14 @@ cudaError_t launch_sep(sa_ctx* c, int part, cudaStream_t s) {
         a.unit = P.unit;
         a.s_max = P.s_max;
         a.st = c->st.p;
+        const double alpha = c->k / (c->rho * c->cp);
+        a.coef = c->opt.precision == SA_MIXED ? 1 : 0;
+        a.n_src = c->n_src;
+        a.pos = c->src_pos.p;
+        a.dt = dt;
+        a.r2_8a = c->spot_radius * c->spot_radius / (8.0 * alpha);
+        a.four_alpha = 4.0 * alpha;
+        a.l2E = (float)std::log2(c->opt.half_space_factor * c->E / (c->rho * c->cp));
         a.c32 = P.coord32.p;
         a.c64 = P.coord64.p;
         a.s32F = c->src32F.p;
