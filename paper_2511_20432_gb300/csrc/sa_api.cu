@@ -1145,7 +1145,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                           c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
                           c->wbot_val.p, c->tt_bot.p, c->Tc, c->F1.p, c->bbot.p, c->n_dof,
                           c->That.p, c->dev64.p, c->dev32.p, part == 2 ? sb : s, part,
-                          c->n_dir > 0 ? br : BotResid());
+                          c->n_dir > 0 ? br : BotResid(), c->st.p);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "gather");
     }
     const bool mixed = c->opt.precision == SA_MIXED;

@@ -212,7 +212,9 @@ struct SepPlan {
     DBuf<float> part32;
 };
 
-// Arguments of one PCG solve.
+// Arguments of one PCG solve.  The grid-barrier counter st->bar_count[which]
+// must be zero at launch: the step's gather kernel zeroes it on the stream
+// the solve runs on.
 struct PcgLaunch {
     SellView op;
     const void* val;          // operator values in the path's precision
@@ -511,7 +513,7 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, int n_dof, const double* That, double* dev64,
                           float* dev32, cudaStream_t s, int part = 0,
-                          const BotResid& br = BotResid());
+                          const BotResid& br = BotResid(), DevStatus* st = nullptr);
 cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval,
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,

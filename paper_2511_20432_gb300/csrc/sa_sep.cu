@@ -22,8 +22,8 @@
 // unit of consecutive sources: the active sources split evenly over a fixed
 // number of units (about four CTAs per multiprocessor), so the grid is static
 // while the active count grows and every CTA has work.  Per chunk of 32 sources the CTA
-// writes FA and FB into shared memory, then each thread accumulates an 8 x 4
-// register tile.  Mixed path: FP32 factors and products, each chunk summed
+// writes FA and FB into shared memory, then each thread accumulates a 4 x 4
+// register tile (small, so that many warps hide the shared-memory latency).  Mixed path: FP32 factors and products, each chunk summed
 // into fresh registers and then added to the unit's sum (the rounding error
 // grows with the chunk length plus the number of chunks, not with the
 // unit); FP64 path: FP64 throughout.  The unit sums go to a partial buffer;
@@ -109,17 +109,15 @@ __device__ __forceinline__ int active_sources(const SepArgs& a) {
 }
 
 template <typename T, int TJ>
-__global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
-    constexpr int NT = 2 * TJ;           // (64 / 8) x (TJ / 4) threads
+__global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * TJ)) k_sep_gemm(SepArgs a) {
+    constexpr int NT = 4 * TJ;           // (64 / 4) x (TJ / 4) threads, 4 x 4 outputs each
     constexpr int NCOL = kTI + TJ;       // factor columns: FA then FB
-    constexpr int NX = NCOL - NT;        // columns beyond one per thread
     constexpr bool kMixed = sizeof(T) == 4;
     using V = typename SrcOf<T>::V;
     using T4 = typename std::conditional<kMixed, float4, double4>::type;
     constexpr int kKC = chunk_of<T>();
     constexpr int kMaxUnit = max_unit_of<T>();
-    __shared__ __align__(16) T fa[2][kKC][kTI];
-    __shared__ __align__(16) T fb[2][kKC][TJ];
+    __shared__ __align__(16) T fab[2][kKC][NCOL];   // per source: FA (64) then FB (TJ)
     __shared__ T xs[NCOL];               // A list then B list of the tile
     __shared__ T4 prm[kMaxUnit];         // per source: s_A, s_B, exponent scale, offset
     __shared__ T mul[kMaxUnit];
@@ -195,44 +193,43 @@ __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
         }
     }
     __syncthreads();
-    // factors of chunk c into buffer c & 1: thread t owns column t for all
-    // sources of the chunk; the NX further columns are shared out
-    const T xown = xs[threadIdx.x];
+    // factors of chunk c into buffer c & 1 (log2 units; FP64: natural ones
+    // with w folded into m):
+    //   FA = 2^(sc (x - s_A)^2)        thread t: column t % 64, sources
+    //                                  t / 64, + NT / 64, ...
+    //   FB = 2^(sc (x - s_B)^2 + off) m   thread t: column t % TJ, sources
+    //                                  t / TJ, + 4, ...
+    constexpr int GA = NT / kTI, GB = NT / TJ;
+    const int ca = threadIdx.x % kTI, ga = threadIdx.x / kTI;
+    const int cb = threadIdx.x % TJ, gb = threadIdx.x / TJ;
+    const T xa = xs[ca], xb = xs[kTI + cb];
     auto gen = [&](int c) {
         const int b = c & 1, s0 = c * kKC;
-        if (threadIdx.x < kTI) {
-#pragma unroll 8
-            for (int kk = 0; kk < kKC; ++kk) {
-                const T4 p4 = prm[s0 + kk];
-                const T d = xown - p4.x;
-                const T e = p4.z * (d * d);
-                fa[b][kk][threadIdx.x] = kMixed ? (T)ex2_approx((float)e) : (T)exp((double)e);
-            }
-        } else {
-#pragma unroll 8
-            for (int kk = 0; kk < kKC; ++kk) {
-                const T4 p4 = prm[s0 + kk];
-                const T d = xown - p4.y;
-                const T e = fma(p4.z, d * d, p4.w);
-                fb[b][kk][threadIdx.x - kTI] =
-                    (kMixed ? (T)ex2_approx((float)e) : (T)exp((double)e)) * mul[s0 + kk];
-            }
+#pragma unroll 4
+        for (int kk = ga; kk < kKC; kk += GA) {
+            const T4 p4 = prm[s0 + kk];
+            const T d = xa - p4.x;
+            const T e = p4.z * (d * d);
+            fab[b][kk][ca] = kMixed ? (T)ex2_approx((float)e) : (T)exp((double)e);
         }
-        if (NX > 0) {
-            for (int v = threadIdx.x; v < NX * kKC; v += NT) {
-                const int kk = v / NX, col = NT + (v - kk * NX);   // an FB column
-                const T4 p4 = prm[s0 + kk];
-                const T d = xs[col] - p4.y;
-                const T e = fma(p4.z, d * d, p4.w);
-                fb[b][kk][col - kTI] =
-                    (kMixed ? (T)ex2_approx((float)e) : (T)exp((double)e)) * mul[s0 + kk];
-            }
+#pragma unroll 4
+        for (int kk = gb; kk < kKC; kk += GB) {
+            const T4 p4 = prm[s0 + kk];
+            const T d = xb - p4.y;
+            const T e = fma(p4.z, d * d, p4.w);
+            fab[b][kk][kTI + cb] =
+                (kMixed ? (T)ex2_approx((float)e) : (T)exp((double)e)) * mul[s0 + kk];
         }
     };
-    const int ti = threadIdx.x & 7, tj = threadIdx.x >> 3;
-    T acc[8][4];
+    // warp w: rows (w & 1) 32 + 4 (lane & 7) .. + 3, columns (w >> 1) 16 +
+    // 4 (lane >> 3) .. + 3: a warp reads 128 contiguous bytes of FA and 64 of
+    // FB per source
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int r0 = (wi & 1) * 32 + (lane & 7) * 4;
+    const int c0 = (wi >> 1) * 16 + (lane >> 3) * 4;
+    T acc[4][4];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) acc[r][cc] = T(0);
     const int nch = (n + kKC - 1) / kKC;
@@ -241,27 +238,26 @@ __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
     for (int c = 0; c < nch; ++c) {
         if (c + 1 < nch) gen(c + 1);     // the other buffer
         const int b = c & 1;
-        T cs[8][4];
+        T cs[4][4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) cs[r][cc] = kMixed ? T(0) : acc[r][cc];
-#pragma unroll 4
+#pragma unroll 8
         for (int kk = 0; kk < kKC; ++kk) {
-            T av[8], bv[4];
+            T av[4], bv[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                av[r] = fa[b][kk][ti * 4 + r];
-                av[4 + r] = fa[b][kk][32 + ti * 4 + r];
-                bv[r] = fb[b][kk][tj * 4 + r];
+                av[r] = fab[b][kk][r0 + r];
+                bv[r] = fab[b][kk][kTI + c0 + r];
             }
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) cs[r][cc] = fma(av[r], bv[cc], cs[r][cc]);
         }
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) acc[r][cc] = kMixed ? acc[r][cc] + cs[r][cc] : cs[r][cc];
         __syncthreads();   // buffer b is consumed and the other one is written
@@ -271,12 +267,9 @@ __global__ void __launch_bounds__(2 * TJ, 4) k_sep_gemm(SepArgs a) {
               ((size_t)tile * a.s_max + blockIdx.y) * kPStride;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
-        T* col = part + (tj * 4 + cc) * kTI;
+        T* col = part + (c0 + cc) * kTI + r0;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            col[ti * 4 + r] = acc[r][cc];
-            col[32 + ti * 4 + r] = acc[4 + r][cc];
-        }
+        for (int r = 0; r < 4; ++r) col[r] = acc[r][cc];
     }
 }
 
@@ -326,7 +319,7 @@ __global__ void __launch_bounds__(256) k_sep_reduce(SepArgs a) {
 template <typename T, int TJ>
 cudaError_t launch_sep_t(const SepArgs& a, cudaStream_t s) {
     if (a.n_tiles == 0) return cudaSuccess;
-    k_sep_gemm<T, TJ><<<dim3(a.n_tiles, a.s_max), 2 * TJ, 0, s>>>(a);
+    k_sep_gemm<T, TJ><<<dim3(a.n_tiles, a.s_max), 4 * TJ, 0, s>>>(a);
     const int n = 4 * a.n_tiles * kTI * TJ;
     k_sep_reduce<T, TJ><<<(n + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();

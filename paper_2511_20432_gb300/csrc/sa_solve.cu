@@ -52,9 +52,15 @@ struct GatherArgs {
     float* dev32;
     int part;              // 0: everything; 1: lateral rows and dev; 2: bottom rows
     BotResid br;           // br.mptr != null: also r0 = b_bot - M_bot g0 and b_bot^2
+    DevStatus* st;         // non-null: zero the grid-barrier counter of the solve that
+                           // follows on the same stream (part 1: main, 2: bottom, 0: both)
 };
 
 __global__ void k_gather(GatherArgs a) {
+    if (a.st && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (a.part != 2) a.st->bar_count[0] = 0u;
+        if (a.part != 1) a.st->bar_count[1] = 0u;
+    }
     long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     // thread space: [lateral rows x 32 | bottom rows x 32 | dev], parts skip a range
     if (a.part == 2) gt += 32ll * a.wlat_rows;
@@ -1267,8 +1273,6 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.fd_mmax = sh.fd_mmax;
             a.plan_wcap = (int)sh.region;
             a.fd_w2 = sh.fd_w2;
-            cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
-            if (e != cudaSuccess) return e;
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
         }
         if (L.variant == SA_PCG_SHARED) return cudaErrorInvalidConfiguration;
@@ -1300,8 +1304,6 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
     a.ksplit = sh.ks;
     a.window = sh.window;
     a.wcap = sh.window ? (int)sh.wl : 0;
-    cudaError_t e = cudaMemsetAsync(&L.st->bar_count[L.which], 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
     return launch_coop((const void*)k_pcg<VT>, sh.G, sh.block, sh.smem, &a, s);
 }
 
@@ -1375,10 +1377,11 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
                           double k, int n_dir, const int* wbot_ptr, const int* wbot_col,
                           const double* wbot_val, const double* tt_bot, double Tc, double* F1,
                           double* bbot, int n_dof, const double* That, double* dev64,
-                          float* dev32, cudaStream_t s, int part, const BotResid& br) {
+                          float* dev32, cudaStream_t s, int part, const BotResid& br,
+                          DevStatus* st) {
     GatherArgs a{wlat_rows, wlat_rowdof, wlat_ptr, wlat_col, wlat_val, s_lat, k, n_dir,
                  wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot, n_dof, That, dev64, dev32,
-                 part, br};
+                 part, br, st};
     const long long threads = part == 1   ? 32ll * wlat_rows + n_dof
                               : part == 2 ? 32ll * n_dir
                                           : 32ll * ((long long)wlat_rows + n_dir) + n_dof;
