@@ -66,7 +66,10 @@ typedef struct sa_options {
                                   (image across the adiabatic top plane); 1 gives
                                   the printed full-space kernel                   */
     void* cuda_stream;         /* cudaStream_t to run on, NULL = default stream   */
-    int use_graph;             /* 1: each sa_step replays one captured CUDA graph */
+    int use_graph;             /* 1: sa_step replays captured CUDA graphs (needs a
+                                  non-default cuda_stream): 16 steps per graph while
+                                  at least 16 remain in the call, then one-step
+                                  graphs                                          */
     int device;                /* CUDA device ordinal; -1 = the current device   */
     int hist_points_per_lane;  /* history-sum tile: points per lane (1,2,4); 0=auto*/
     int hist_warps;            /* history-sum tile: warps splitting the sources (4,8); 0=auto */

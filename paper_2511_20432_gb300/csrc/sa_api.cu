@@ -201,6 +201,15 @@ cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
 
 }  // namespace
 
+// Captured step graphs depend on the operator, the warm start and the
+// options: dropped whenever one of them changes.
+void drop_graphs(sa_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph_multi) cudaGraphExecDestroy(c->graph_multi);
+    c->graph_exec = nullptr;
+    c->graph_multi = nullptr;
+}
+
 extern "C" {
 
 void sa_options_default(sa_options* o) {
@@ -306,7 +315,7 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
 
 void sa_destroy(sa_ctx* c) {
     if (!c) return;
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    drop_graphs(c);
     for (int i = 0; i <= SA_N_STAGES; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -1067,10 +1076,7 @@ sa_status ensure_operator(sa_ctx* c, double theta, double dt) {
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "build A");
     c->op_dt = dt;
     c->op_theta = theta;
-    if (c->graph_exec) {
-        cudaGraphExecDestroy(c->graph_exec);
-        c->graph_exec = nullptr;
-    }
+    drop_graphs(c);
     return SA_OK;
 }
 
@@ -1314,22 +1320,33 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
     if ((st = ensure_operator(c, theta, dt))) return st;
     cudaStream_t s = c->stream;
     const bool graph = c->opt.use_graph && s != nullptr && !c->opt.stage_timing && c->rec_X == nullptr;
-    for (int i = 0; i < n_steps; ++i) {
-        if (graph) {
-            if (!c->graph_exec) {
-                cudaGraph_t g;
-                SA_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                sa_status es = enqueue_step(c, theta, dt);
-                cudaError_t ee = cudaStreamEndCapture(s, &g);
-                if (es) return es;
-                if (ee != cudaSuccess) return sa_cuda_fail(c, ee, "end capture");
-                ee = cudaGraphInstantiate(&c->graph_exec, g, 0);
-                cudaGraphDestroy(g);
-                if (ee != cudaSuccess) return sa_cuda_fail(c, ee, "graph instantiate");
-            }
+    // graphs of kGraphSteps steps while that many remain (no gap between the
+    // steps inside one graph), then one-step graphs
+    auto capture = [&](cudaGraphExec_t* exec, int steps) -> sa_status {
+        cudaGraph_t g;
+        SA_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        sa_status es = SA_OK;
+        for (int k = 0; k < steps && es == SA_OK; ++k) es = enqueue_step(c, theta, dt);
+        cudaError_t ee = cudaStreamEndCapture(s, &g);
+        if (es) return es;
+        if (ee != cudaSuccess) return sa_cuda_fail(c, ee, "end capture");
+        ee = cudaGraphInstantiate(exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ee != cudaSuccess) return sa_cuda_fail(c, ee, "graph instantiate");
+        return SA_OK;
+    };
+    for (int i = 0; i < n_steps;) {
+        if (graph && n_steps - i >= kGraphSteps) {
+            if (!c->graph_multi && (st = capture(&c->graph_multi, kGraphSteps))) return st;
+            SA_CUDA(c, cudaGraphLaunch(c->graph_multi, s));
+            i += kGraphSteps;
+        } else if (graph) {
+            if (!c->graph_exec && (st = capture(&c->graph_exec, 1))) return st;
             SA_CUDA(c, cudaGraphLaunch(c->graph_exec, s));
+            ++i;
         } else {
             if ((st = enqueue_step(c, theta, dt))) return st;
+            ++i;
         }
     }
     c->n_step += n_steps;
@@ -1368,10 +1385,7 @@ sa_status sa_set_warm_start(sa_ctx* c, sa_mlp* net, int n_in, const int* in_idx)
     sa_status st = check_usable(c);
     if (st) return st;
     if (!c->has_patch) return sa_fail(c, SA_ERR_STATE, "no patch");
-    if (c->graph_exec) {
-        cudaGraphExecDestroy(c->graph_exec);
-        c->graph_exec = nullptr;
-    }
+    drop_graphs(c);
     if (!net) {
         c->ws_net = nullptr;
         return SA_OK;

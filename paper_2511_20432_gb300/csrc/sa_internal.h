@@ -248,6 +248,9 @@ struct PcgLaunch {
 // ---------------------------------------------------------------------------
 // the context
 // ---------------------------------------------------------------------------
+// Steps captured in one CUDA graph when a call asks for at least that many.
+constexpr int kGraphSteps = 16;
+
 struct sa_mlp;
 cudaError_t mlp_forward(sa_mlp* m, const void* X, int rows, const float** out, cudaStream_t s);
 int mlp_n_in(const sa_mlp* m);
@@ -301,7 +304,8 @@ struct sa_ctx {
     long long n_step = 0;     // host mirror of the step index
     double op_dt = 0, op_theta = -1;   // operator currently built
     bool state_dirty_graph = true;
-    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;    // one step
+    cudaGraphExec_t graph_multi = nullptr;   // kGraphSteps steps
 
     // ---- device: geometry -------------------------------------------------
     DBuf<double> dU[3];
