@@ -1156,6 +1156,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     }
     const bool mixed = c->opt.precision == SA_MIXED;
     SA_MARK(SA_STAGE_BOTTOM);
+    bool dir_ready = false;
     if (c->n_dir > 0) {
         PcgLaunch L;
         L.op = sell_view(c->mbot_s);
@@ -1185,6 +1186,13 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices + 7) / 8));
         L.block = 0;
         L.ksplit = 0;
+        // the shared-memory solve also writes g^{n+1} - g^n and g^{n+1} for
+        // the right-hand side (no separate kernel after it)
+        dir_ready = c->opt.pcg_variant != SA_PCG_GLOBAL && pcg_shared_fits(c->opt.precision, L);
+        if (dir_ready) {
+            L.dir_old = c->That.p + c->n_free;
+            L.dir_out = c->dirv.p;
+        }
         e = launch_pcg(c->opt.precision, L, sb);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
@@ -1199,7 +1207,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                              mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
                              mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
                              c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
-                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s, only);
+                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s, only, dir_ready);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     }
     SA_MARK(SA_STAGE_PCG);

@@ -243,6 +243,11 @@ struct PcgLaunch {
     int grid;                 // 1: one block, no grid barrier
     int block = 0;            // threads per block (0: 1024)
     int ksplit;               // warps per SELL slice in the SpMV (1, 2, 4, 8)
+    // shared-memory variant, optional: with x final, dir_out[i] = x_i - dir_old[i]
+    // and dir_out[n + i] = x_i in the operator precision (the Dirichlet
+    // increments the theta right-hand side needs)
+    const double* dir_old = nullptr;
+    void* dir_out = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -522,7 +527,8 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
-                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only = 0);
+                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only = 0,
+                             bool dir_ready = false);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
                           double* gprev, double* g0, cudaStream_t s);

@@ -726,6 +726,8 @@ struct SmemArgs {
     FdView fd;             // fast-diagonalization preconditioner (fd.on), else Jacobi
     int fd_mmax;           // longest grid line (per-warp scratch entries)
     int plan_wcap;         // window entries reserved in shared memory
+    const double* dir_old; // see PcgLaunch
+    VT* dir_out;
     int fd_w2;             // 1: the region holds three m x m matrices (the fused
                            // pass's second one staged too), 0: two
 };
@@ -1133,7 +1135,14 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
         if (state != 0) break;
         if (!precondition()) return;
     }
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) a.x[row0 + t] += D[t];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        const double xn = a.x[row0 + t] + D[t];
+        a.x[row0 + t] = xn;
+        if (a.dir_out) {
+            a.dir_out[row0 + t] = (VT)(xn - a.dir_old[row0 + t]);
+            a.dir_out[n + row0 + t] = (VT)xn;
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rel = sqrt(sc[3]);      // (sigma r, sigma r) = ||r||^2 / ||b||^2
         int* err = &a.st->err;
@@ -1272,6 +1281,8 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.fd = L.fd;
             a.fd_mmax = sh.fd_mmax;
             a.plan_wcap = (int)sh.region;
+            a.dir_old = L.dir_old;
+            a.dir_out = (VT*)L.dir_out;
             a.fd_w2 = sh.fd_w2;
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
         }
@@ -1394,9 +1405,11 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const void* Mval, const void* dev, const double* That,
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
-                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only) {
+                             double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only,
+                             bool dir_ready) {
     if (op.n == 0) return cudaSuccess;
-    const bool prep = only != 1 && n_dir > 0;   // Dirichlet increments for the flagged slices
+    // Dirichlet increments for the flagged slices (unless the projection wrote them)
+    const bool prep = only != 1 && n_dir > 0 && !dir_ready;
     const unsigned blocks = (unsigned)((op.n_slices + (8 / kRhsSplit) - 1) / (8 / kRhsSplit));
     const unsigned pblocks = (unsigned)((n_dir + 255) / 256);
     if (precision == SA_MIXED) {
