@@ -13,10 +13,13 @@ A "step" is one theta-step of the whole hot path: source coefficients,
 history sums at every boundary quadrature point, boundary integrals, bottom
 projection, theta right-hand side, PCG.  ``value`` is theta-steps/s of the
 mixed path (FP32 history sum and operator values; FP64 state, boundary
-integrals and Krylov vectors; fast-diagonalization preconditioners, solves
-started from T^n), replayed as CUDA graphs with the inputs resident in HBM.
-Timed beside it: the same path with extrapolated initial guesses, with the
-Jacobi preconditioner, and the plain FP64 path.
+integrals and Krylov vectors; the block's faces are axis-aligned rectangles,
+so the history sums are evaluated separably, as matrix products over the
+sources; fast-diagonalization preconditioners, solves started from T^n),
+replayed as CUDA graphs (16 steps per graph) with the inputs resident in
+HBM.  Timed beside it: the same path with extrapolated initial guesses, with
+the Jacobi preconditioner, with the pairwise history sums, the plain FP64
+path (pairwise sums) and FP64 with the separable sums.
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
 bounded sample of the same step.
@@ -54,6 +57,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--hist", default="auto", choices=["auto", "pairwise", "separable"],
+                    help="evaluation of the history sums of the main context")
     ap.add_argument("--start-step", type=int, default=None,
                     help="first timed step; default: the timed steps are centred on step 5,840")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
@@ -409,8 +414,10 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     prec = sa.SA_MIXED if args.precision == "mixed" else sa.SA_FP64
     guess = sa.SA_GUESS_EXTRAPOLATE if args.guess == "extrapolate" else sa.SA_GUESS_PREVIOUS
+    hist = {"auto": sa.SA_HIST_AUTO, "pairwise": sa.SA_HIST_PAIRWISE,
+            "separable": sa.SA_HIST_SEPARABLE}[args.hist]
     ctx = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1,
-                                   initial_guess=guess)
+                                   initial_guess=guess, hist_mode=hist)
     n0 = start_step(args)
     ctx.step(th, dt, n0)                       # untimed fast-forward to mid-scan
     ctx.step(th, dt, args.warmup)              # warm-up (graph instantiated, caches warm)
@@ -449,6 +456,7 @@ def run_ours(args):
         return
 
     def fresh(precision, g, **kw):
+        kw.setdefault("hist_mode", hist)
         c = sa.context_from_workload(wl, precision=precision, cuda_stream=stream, initial_guess=g, **kw)
         c.step(th, dt, 0)
         c.set_state(*state)
