@@ -78,6 +78,11 @@ struct sa_batch {
     DBuf<unsigned char> fd_desc;   // BFd per instance
     DBuf<int> fd_loff;             // 3 x (n_inst + 1): line offsets per direction
     DBuf<unsigned char> fdS, fdZ;  // n_free x VT
+    // the same for the bottom projections (2-D)
+    bool fdb_on = false;
+    DBuf<unsigned char> fdb_desc;
+    DBuf<int> fdb_loff;
+    DBuf<unsigned char> fdbS, fdbZ;   // n_dir x VT
     int pcg_grid = 0;
     int hist_P = 4, hist_W = 8;
     cudaGraphExec_t graph_exec = nullptr;
@@ -202,6 +207,7 @@ struct BPcgArgs {
     double tol;
     int max_iter;
     const BFd* fd;            // per-instance fast diagonalization, or null (Jacobi)
+    int fd_nd;                // its dimension: 3 (main solves) or 2 (bottom projections)
     const int* fd_loff;       // 3 x (n_inst + 1)
     const VT* fdS;            // scaling per row
     VT* fdZ;                  // work vector
@@ -214,7 +220,8 @@ __device__ __forceinline__ int bcol(const BPcgArgs<VT>& a, long long e, int row)
 
 // Batched fast-diagonalization preconditioner z = S A_box^{-1} S r over
 // every instance (independent grids): on entry fdZ = S r on all rows (grid
-// barrier passed); five passes over the lines of all instances (a line ->
+// barrier passed); 2 nd - 1 passes (3-D: U_0^T, U_1^T, U_2 D U_2^T, U_1, U_0;
+// 2-D: U_0^T, U_1 D U_1^T, U_0) over the lines of all instances (a line ->
 // its instance by the per-direction line offsets), one warp per line, the
 // line's matrix read through L1; the last pass writes z (FP64) and its
 // operator-precision copy.  Lines have at most 128 entries.
@@ -226,8 +233,9 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsi
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int NI = a.n_inst;
     VT* Z = a.fdZ;
-    for (int pass = 0; pass < 5; ++pass) {
-        const int d = pass < 3 ? pass : 4 - pass;
+    const int nd = a.fd_nd, npass = 2 * nd - 1;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int d = pass < nd ? pass : npass - 1 - pass;
         const int* loff = a.fd_loff + d * (NI + 1);
         const int nlines = loff[NI];
         for (int Lg = gw; Lg < nlines; Lg += nw) {
@@ -246,7 +254,7 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsi
                                             : (d == 1 ? (long long)(L / m0) * (m0 * m1) + (L % m0) : L));
             for (int q = lane; q < m; q += 32) xs[q] = __ldcg(Z + base + (long long)q * stride);
             __syncwarp();
-            const VT* W = (const VT*)(pass < 3 ? f.U[d] : f.Ut[d]);
+            const VT* W = (const VT*)(pass < nd ? f.U[d] : f.Ut[d]);
             VT y[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
 #pragma unroll 4
             for (int q = 0; q < m; ++q) {
@@ -257,9 +265,10 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsi
                     if (o < m) y[t] = fma(__ldg(W + q * m + o), xq, y[t]);
                 }
             }
-            if (pass == 2) {
-                const VT li = (VT)f.cM + ((const VT*)f.lamc[0])[L % m0] + ((const VT*)f.lamc[1])[L / m0];
-                const VT* l2 = (const VT*)f.lamc[2];
+            if (pass == nd - 1) {
+                const VT li = (VT)f.cM + ((const VT*)f.lamc[0])[L % m0] +
+                              (nd == 3 ? ((const VT*)f.lamc[1])[L / m0] : (VT)0);
+                const VT* l2 = (const VT*)f.lamc[nd - 1];
                 __syncwarp();
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -268,7 +277,7 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsi
                     y[t] = (VT)0;
                 }
                 __syncwarp();
-                const VT* W2 = (const VT*)f.Ut[2];
+                const VT* W2 = (const VT*)f.Ut[nd - 1];
 #pragma unroll 4
                 for (int q = 0; q < m; ++q) {
                     const VT xq = xs[q];
@@ -285,7 +294,7 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsi
                 const int o = lane + 32 * t;
                 if (o < m) {
                     const long long idx = base + (long long)o * stride;
-                    if (pass == 4) {
+                    if (pass == npass - 1) {
                         const VT u = a.fdS[idx] * y[t];
                         z[idx] = (double)u;
                         zl[idx] = u;
@@ -589,11 +598,12 @@ cudaError_t launch_pcg_batch(sa_batch* b, int which, const SellDev& s, const voi
     a.which = which;
     a.tol = b->opt.pcg_tol;
     a.max_iter = b->opt.pcg_max_iter;
-    const bool fd = which == 0 && b->fd_on;
-    a.fd = fd ? (const BFd*)b->fd_desc.p : nullptr;
-    a.fd_loff = fd ? b->fd_loff.p : nullptr;
-    a.fdS = fd ? (const VT*)b->fdS.p : nullptr;
-    a.fdZ = fd ? (VT*)b->fdZ.p : nullptr;
+    const bool fd = which == 0 ? b->fd_on : b->fdb_on;
+    a.fd = fd ? (const BFd*)(which == 0 ? b->fd_desc.p : b->fdb_desc.p) : nullptr;
+    a.fd_nd = which == 0 ? 3 : 2;
+    a.fd_loff = fd ? (which == 0 ? b->fd_loff.p : b->fdb_loff.p) : nullptr;
+    a.fdS = fd ? (const VT*)(which == 0 ? b->fdS.p : b->fdbS.p) : nullptr;
+    a.fdZ = fd ? (VT*)(which == 0 ? b->fdZ.p : b->fdbZ.p) : nullptr;
     cudaError_t e = cudaMemsetAsync(&b->st.p->bar_count[2 + which], 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->counters.p, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -910,6 +920,42 @@ sa_status build(sa_batch* b, double theta, double dt) {
             for (int i = 0; i < NI; ++i)
                 B_CUDA(b, d2d(b->fdS.p + (size_t)b->free_off[i] * vt, b->inst[i]->fdm.S.p,
                               (size_t)b->inst[i]->n_free * vt, s));
+        }
+        // the bottom projections' 2-D fast diagonalization, when every
+        // instance has one
+        b->fdb_on = b->opt.precond != SA_PRECOND_JACOBI && b->n_dir > 0;
+        for (int i = 0; i < NI && b->fdb_on; ++i)
+            b->fdb_on = b->inst[i]->fdb.ok && b->inst[i]->fdb.nd == 2 &&
+                        b->inst[i]->opt.precision == b->opt.precision;
+        if (b->fdb_on) {
+            const size_t vt = mixed ? sizeof(float) : sizeof(double);
+            std::vector<BFd> desc(NI);
+            std::vector<int> loff(3 * (NI + 1), 0);
+            for (int i = 0; i < NI; ++i) {
+                const FdData& f = b->inst[i]->fdb;
+                std::memset(&desc[i], 0, sizeof(BFd));
+                for (int d = 0; d < 3; ++d) desc[i].m[d] = f.m[d];
+                for (int d = 0; d < 2; ++d) {
+                    desc[i].U[d] = f.dU[d].p;
+                    desc[i].Ut[d] = f.dUt[d].p;
+                    desc[i].lamc[d] = f.dlamc[d].p;
+                    loff[d * (NI + 1) + i + 1] = loff[d * (NI + 1) + i] + b->inst[i]->n_dir / f.m[d];
+                }
+                desc[i].row0 = b->dir_off[i];
+                desc[i].cM = f.cM;
+            }
+            std::vector<unsigned char> raw(sizeof(BFd) * NI);
+            std::memcpy(raw.data(), desc.data(), raw.size());
+            sa_status st2;
+            if ((st2 = bupload(b, b->fdb_desc, raw, "fdb_desc"))) return st2;
+            if ((st2 = bupload(b, b->fdb_loff, loff, "fdb_loff"))) return st2;
+            const size_t ndw = (size_t)std::max(b->n_dir, 1);
+            B_ALLOC(b, b->fdbS, ndw * vt);
+            B_ALLOC(b, b->fdbZ, ndw * vt);
+            B_CUDA(b, cudaMemsetAsync(b->fdbS.p, 0, ndw * vt, s));
+            for (int i = 0; i < NI; ++i)
+                B_CUDA(b, d2d(b->fdbS.p + (size_t)b->dir_off[i] * vt, b->inst[i]->fdb.S.p,
+                              (size_t)b->inst[i]->n_dir * vt, s));
         }
         B_ALLOC(b, b->inst_state, (size_t)IS_NFIELDS * std::max(NI, 1));
         B_ALLOC(b, b->inst_iters, (size_t)2 * std::max(NI, 1));

@@ -50,8 +50,9 @@ def test_batch_matches_single_contexts(sa, prec, precond):
         c.step(0.5, 5e-6, n)
     m_it, b_it = batch.iters()
     assert (m_it >= 0).all() and (b_it >= 0).all()
-    if precond == "fd":   # boxes: the preconditioner is the inverse
+    if precond == "fd":   # boxes: the preconditioners are the inverses
         assert m_it.max() <= 2, m_it
+        assert b_it.max() <= 3, b_it
     for i, c in enumerate(singles):
         Tb = batch.field(i, sa.SA_FIELD_THAT)
         Ts = c.field(sa.SA_FIELD_THAT)
