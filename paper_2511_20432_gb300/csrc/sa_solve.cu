@@ -26,8 +26,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// F^{n+1} = W_lat (-k dT~/dn)  and  b_bot = W_bot (T_c - T~): one warp per
-// row of the constant weight matrices, fixed order, no atomics.  The same
+// F^{n+1} = W_lat (-k dT~/dn)  and  b_bot = W_bot (T_c - T~): eight lanes
+// per row of the constant weight matrices, fixed order, no atomics.  The same
 // launch writes dev = T^n - T_c (FP64 and FP32) for the right-hand side.
 // ---------------------------------------------------------------------------
 struct GatherArgs {
@@ -56,16 +56,31 @@ struct GatherArgs {
                            // follows on the same stream (part 1: main, 2: bottom, 0: both)
 };
 
+// Eight lanes per row (rows hold ~10-40 entries): four rows per warp.  The
+// lateral and the bottom row ranges are each padded to whole warps, so every
+// warp is in one range and all its lanes reach the shuffles.
+constexpr int kRowLanes = 8;
+
+__host__ __device__ inline long long gather_range(long long rows) {
+    return (kRowLanes * rows + 31) / 32 * 32;
+}
+
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void k_gather(GatherArgs a) {
     if (a.st && blockIdx.x == 0 && threadIdx.x == 0) {
         if (a.part != 2) a.st->bar_count[0] = 0u;
         if (a.part != 1) a.st->bar_count[1] = 0u;
     }
     long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    // thread space: [lateral rows x 32 | bottom rows x 32 | dev], parts skip a range
-    if (a.part == 2) gt += 32ll * a.wlat_rows;
-    const long long lat_threads = 32ll * a.wlat_rows;
-    const long long row_threads = lat_threads + (a.part == 1 ? 0 : 32ll * a.n_dir);
+    // thread space: [lateral rows | bottom rows | dev], parts skip a range
+    const long long lat_threads = gather_range(a.wlat_rows);
+    if (a.part == 2) gt += lat_threads;
+    const long long row_threads = lat_threads + (a.part == 1 ? 0 : gather_range(a.n_dir));
     if (gt >= row_threads) {
         if (a.part == 2) return;
         const long long i = gt - row_threads;
@@ -76,27 +91,30 @@ __global__ void k_gather(GatherArgs a) {
         }
         return;
     }
-    const int row = (int)(gt >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row < a.wlat_rows) {
+    const int sub = (int)(gt & (kRowLanes - 1));
+    if (gt < lat_threads) {
+        const int row = (int)(gt / kRowLanes);
+        const bool ok = row < a.wlat_rows;
         double acc = 0.0;
-        for (int s = a.lptr[row] + lane; s < a.lptr[row + 1]; s += 32)
-            acc += a.lval[s] * a.s_lat[a.lcol[s]];
-        acc = warp_sum(acc);
-        if (lane == 0) a.F1[a.rowdof[row]] = -a.k * acc;
+        if (ok)
+            for (int s = a.lptr[row] + sub; s < a.lptr[row + 1]; s += kRowLanes)
+                acc += a.lval[s] * a.s_lat[a.lcol[s]];
+        acc = group_sum(acc);
+        if (ok && sub == 0) a.F1[a.rowdof[row]] = -a.k * acc;
     } else {
-        const int r = row - a.wlat_rows;
-        double acc = 0.0;
-        for (int s = a.bptr[r] + lane; s < a.bptr[r + 1]; s += 32)
-            acc += a.bval[s] * (a.Tc - a.tt_bot[a.bcol[s]]);
-        acc = warp_sum(acc);
-        double mg = 0.0;
-        if (a.br.mptr) {
-            for (int s = a.br.mptr[r] + lane; s < a.br.mptr[r + 1]; s += 32)
-                mg += a.br.mval[s] * a.br.g0[a.br.mcol[s]];
-            mg = warp_sum(mg);
+        const int r = (int)((gt - lat_threads) / kRowLanes);
+        const bool ok = r < a.n_dir;
+        double acc = 0.0, mg = 0.0;
+        if (ok) {
+            for (int s = a.bptr[r] + sub; s < a.bptr[r + 1]; s += kRowLanes)
+                acc += a.bval[s] * (a.Tc - a.tt_bot[a.bcol[s]]);
+            if (a.br.mptr)
+                for (int s = a.br.mptr[r] + sub; s < a.br.mptr[r + 1]; s += kRowLanes)
+                    mg += a.br.mval[s] * a.br.g0[a.br.mcol[s]];
         }
-        if (lane == 0) {
+        acc = group_sum(acc);
+        mg = group_sum(mg);
+        if (ok && sub == 0) {
             a.bbot[r] = acc;
             if (a.br.mptr) {
                 a.br.r0[r] = acc - mg;
@@ -1393,9 +1411,9 @@ cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat
     GatherArgs a{wlat_rows, wlat_rowdof, wlat_ptr, wlat_col, wlat_val, s_lat, k, n_dir,
                  wbot_ptr, wbot_col, wbot_val, tt_bot, Tc, F1, bbot, n_dof, That, dev64, dev32,
                  part, br, st};
-    const long long threads = part == 1   ? 32ll * wlat_rows + n_dof
-                              : part == 2 ? 32ll * n_dir
-                                          : 32ll * ((long long)wlat_rows + n_dir) + n_dof;
+    const long long threads = part == 1   ? gather_range(wlat_rows) + n_dof
+                              : part == 2 ? gather_range(n_dir)
+                                          : gather_range(wlat_rows) + gather_range(n_dir) + n_dof;
     if (threads == 0) return cudaSuccess;
     k_gather<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
