@@ -1604,9 +1604,17 @@ sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_d
     if (n == 0) return SA_OK;
     if ((st = init_state_if_needed(c))) return st;
     cudaStream_t s = c->stream;
+    // mixed contexts: the centre search and the source sum in FP32 (the
+    // source coefficients in the step's FP32 tables, which the next step
+    // rewrites)
+    const bool mixed = c->opt.precision == SA_MIXED;
     if (!c->ecent.p) {
         SA_ALLOC(c, c->ecent, (size_t)3 * c->n_elem);
         cudaError_t e = launch_elem_centers(c->dp, c->ecent.p, s);
+        if (e == cudaSuccess && mixed) {
+            SA_ALLOC(c, c->ecent32, (size_t)3 * c->n_elem);
+            e = launch_to_f32((long long)3 * c->n_elem, c->ecent.p, c->ecent32.p, s);
+        }
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "element centres");
     }
     int n_active = 0;
@@ -1614,8 +1622,10 @@ sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_d
         const double alpha = c->k / (c->rho * c->cp);
         cudaError_t e = launch_prologue(nullptr, c->n_step, nullptr, c->n_src, c->src_pos.p, c->src_dt,
                                         alpha, c->spot_radius * c->spot_radius / (8.0 * alpha),
-                                        c->opt.half_space_factor * c->E / (c->rho * c->cp), SA_FP64,
-                                        c->evT.p, c->evF.p, nullptr, nullptr, s);
+                                        c->opt.half_space_factor * c->E / (c->rho * c->cp),
+                                        mixed ? SA_MIXED : SA_FP64, mixed ? nullptr : c->evT.p,
+                                        mixed ? nullptr : c->evF.p, mixed ? c->src32T.p : nullptr,
+                                        mixed ? c->src32F.p : nullptr, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "eval prologue");
         n_active = (int)std::min<long long>(c->n_step, c->n_src);
     }
@@ -1632,7 +1642,8 @@ sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_d
     }
     cudaError_t e = launch_eval_points(c->dp, dpts, n, c->ecent.p, c->dperm.p, c->That.p,
                                        c->evT.p, n_active, c->x_ref, c->y_ref, c->z_top,
-                                       c->length_scale, dout, s);
+                                       c->length_scale, dout, s, mixed ? c->ecent32.p : nullptr,
+                                       mixed ? c->src32T.p : nullptr);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "eval");
     if (!on_device)
         SA_CUDA(c, cudaMemcpyAsync(T_out, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s));

@@ -464,35 +464,67 @@ struct EvalArgs {
     const double* pts;
     int n;
     const double* ecent;
+    const float* ecent32;      // FP32 copy of the centres (search only), or null
     const int* perm;
     const double* That;
-    const double4* s64T;
+    const double4* s64T;       // FP64 coefficients (sx, sy, a, c), or
+    const float4* s32T;        // FP32 ones (sx, sy, -a log2 e, log2 c): mixed contexts
     int n_active;
     double x_ref, y_ref, z_top, scale;
     double* T_out;
 };
 
-// One warp per query point: the lanes search the element centres and sum
-// the sources; lane 0 runs the Newton iteration.  Reductions use a fixed
-// xor tree (deterministic).
-__global__ void k_eval(EvalArgs a) {
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+constexpr int kEvalThreads = 128;
+
+__device__ __forceinline__ float eval_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One block per query point: the threads search the element centres (in
+// FP32 when a copy is given: the centre only seeds Newton) and sum the
+// sources; thread 0 runs the Newton iteration.  Reductions in a fixed order
+// (ties of the search: lowest element index).
+__global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
+    const int t = blockIdx.x;
     if (t >= a.n) return;
+    __shared__ double s_d[kEvalThreads / 32];
+    __shared__ int s_e[kEvalThreads / 32];
+    __shared__ double s_T[kEvalThreads / 32];
+    __shared__ int s_best;
+    __shared__ double s_That;
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const DevPatch& dp = a.dp;
     const double xs[3] = {a.pts[3 * t], a.pts[3 * t + 1], a.pts[3 * t + 2]};
     // initial guess: parametric centre of the element with the nearest
-    // physical centre (ties: lowest element index)
+    // physical centre
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
     int best = 0x7fffffff;
     double bd = 1e300;
-    for (int e = lane; e < nel; e += 32) {
-        const double dx = a.ecent[3 * e] - xs[0], dy = a.ecent[3 * e + 1] - xs[1],
-                     dz = a.ecent[3 * e + 2] - xs[2];
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 < bd) {
-            bd = d2;
-            best = e;
+    if (a.ecent32) {
+        const float x0 = (float)xs[0], x1 = (float)xs[1], x2 = (float)xs[2];
+        float bf = 3.0e38f;
+        for (int e = threadIdx.x; e < nel; e += kEvalThreads) {
+            const float dx = a.ecent32[3 * e] - x0, dy = a.ecent32[3 * e + 1] - x1,
+                        dz = a.ecent32[3 * e + 2] - x2;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (d2 < bf) {
+                bf = d2;
+                best = e;
+            }
+        }
+        bd = bf;
+    } else {
+        for (int e = threadIdx.x; e < nel; e += kEvalThreads) {
+            const double dx = a.ecent[3 * e] - xs[0], dy = a.ecent[3 * e + 1] - xs[1],
+                         dz = a.ecent[3 * e + 2] - xs[2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < bd) {
+                bd = d2;
+                best = e;
+            }
         }
     }
 #pragma unroll
@@ -504,9 +536,17 @@ __global__ void k_eval(EvalArgs a) {
             best = ob;
         }
     }
-    double That = 0.0;
-    int ok = 0;
     if (lane == 0) {
+        s_d[w] = bd;
+        s_e[w] = best;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kEvalThreads / 32; ++k)
+            if (s_d[k] < bd || (s_d[k] == bd && s_e[k] < best)) {
+                bd = s_d[k];
+                best = s_e[k];
+            }
         const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1],
                            best / (dp.ne[0] * dp.ne[1])};
         double xi[3], lo[3], hi[3];
@@ -536,7 +576,8 @@ __global__ void k_eval(EvalArgs a) {
             }
             for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
         }
-        ok = res <= 1e-9 * a.scale;
+        const int ok = res <= 1e-9 * a.scale;
+        double That = 0.0;
         if (ok)
             for (int a2 = 0; a2 <= dp.p[2]; ++a2)
                 for (int a1 = 0; a1 <= dp.p[1]; ++a1)
@@ -546,18 +587,37 @@ __global__ void k_eval(EvalArgs a) {
                         const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
                         That += R * a.That[a.perm[nat]];
                     }
+        s_That = That;
+        s_ok = ok;
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
+    // the sources: FP32 terms (each thread sums its ~n / 128 in FP32) or FP64
     const double px = xs[0] - a.x_ref, py = xs[1] - a.y_ref, dz = xs[2] - a.z_top;
     double Tt = 0.0;
-    for (int j = lane; j < a.n_active; j += 32) {
-        const double4 sv = a.s64T[j];
-        const double dx = px - sv.x, dy = py - sv.y;
-        Tt += sv.w * exp(-sv.z * (dx * dx + dy * dy + dz * dz));
+    if (a.s32T) {
+        const float fx = (float)px, fy = (float)py, fz2 = (float)(dz * dz);
+        float acc = 0.0f;
+        for (int j = threadIdx.x; j < a.n_active; j += kEvalThreads) {
+            const float4 sv = a.s32T[j];
+            const float dx = fx - sv.x, dy = fy - sv.y;
+            acc += eval_ex2(fmaf(sv.z, fmaf(dx, dx, fmaf(dy, dy, fz2)), sv.w));
+        }
+        Tt = (double)acc;
+    } else {
+        for (int j = threadIdx.x; j < a.n_active; j += kEvalThreads) {
+            const double4 sv = a.s64T[j];
+            const double dx = px - sv.x, dy = py - sv.y;
+            Tt += sv.w * exp(-sv.z * (dx * dx + dy * dy + dz * dz));
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) Tt += __shfl_xor_sync(0xffffffffu, Tt, o);
-    if (lane == 0) a.T_out[t] = ok ? Tt + That : nan("");
+    if (lane == 0) s_T[w] = Tt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < kEvalThreads / 32; ++k) tot += s_T[k];
+        a.T_out[t] = s_ok ? tot + s_That : nan("");
+    }
 }
 // Closed patches: every entry of the matrices over control variables is the
 // sum of the control-point entries that map to it (P^T M P), in the fixed
@@ -724,9 +784,11 @@ cudaError_t launch_elem_centers(const DevPatch& dp, double* ecent, cudaStream_t 
 cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,
-                               double scale, double* T_out, cudaStream_t s) {
+                               double scale, double* T_out, cudaStream_t s, const float* ecent32,
+                               const float4* s32T) {
     if (n == 0) return cudaSuccess;
-    EvalArgs a{dp, pts, n, ecent, perm, That, s64T, n_active, x_ref, y_ref, z_top, scale, T_out};
-    k_eval<<<(unsigned)(((long long)n * 32 + 127) / 128), 128, 0, s>>>(a);
+    EvalArgs a{dp, pts, n, ecent, ecent32, perm, That, s64T, s32T, n_active, x_ref, y_ref,
+               z_top, scale, T_out};
+    k_eval<<<(unsigned)n, kEvalThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -390,6 +390,7 @@ struct sa_ctx {
     DBuf<double> ecent;             // physical element centres (eval initial guess)
     DBuf<double4> evT, evF;         // FP64 source coefficients at the current step
     DBuf<double> eval_pts, eval_out;
+    DBuf<float> ecent32;            // FP32 element centres (the eval's search)
 
     // host copies of the patterns (for sa_batch)
     SellHost a_h, r_h, mbot_h;
@@ -500,10 +501,14 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
 sa_status sep_setup(sa_ctx* c);
 sa_status sep_alloc(sa_ctx* c);
 cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s);
+// T = T~ + T^ at points; ecent32 (FP32 copy of the element centres) and
+// s32T (FP32 source coefficients) are optional: with them the search and the
+// source sum run in FP32 (mixed contexts).
 cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,
-                               double scale, double* T_out, cudaStream_t s);
+                               double scale, double* T_out, cudaStream_t s,
+                               const float* ecent32 = nullptr, const float4* s32T = nullptr);
 
 // sa_solve.cu
 // With the bottom rows of the gather, optionally the bottom projection's
