@@ -441,6 +441,51 @@ __device__ void eval_at(const DevPatch& dp, const double xi[3], Basis1D& b, doub
     nurbs_point(dp, b, x, J, W, dW);
 }
 
+// eval_at by one warp: every lane evaluates the 1-D bases, the lanes share
+// the (p0+1)(p1+1)(p2+1) tensor-product terms, and the sums (W, dW, x W,
+// d(x W)) are formed by an xor butterfly (the same value on every lane).
+__device__ void eval_at_warp(const DevPatch& dp, const double xi[3], Basis1D& b, double x[3],
+                             double J[3][3], double& Wsum) {
+    const int lane = threadIdx.x & 31;
+    for (int d = 0; d < 3; ++d) {
+        b.s[d] = find_span(dp.U[d], dp.p[d], dp.n[d], xi[d]);
+        bspline_1d(dp.U[d], dp.p[d], b.s[d], xi[d], b.N[d], b.dN[d]);
+    }
+    const int n0 = dp.p[0] + 1, n1 = dp.p[1] + 1, nb = n0 * n1 * (dp.p[2] + 1);
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = 0.0;
+    for (int l = lane; l < nb; l += 32) {
+        const int a0 = l % n0, a1 = (l / n0) % n1, a2 = l / (n0 * n1);
+        const double4 c = dp.cw[nat_index(dp, b.s[0] - dp.p[0] + a0, b.s[1] - dp.p[1] + a1,
+                                          b.s[2] - dp.p[2] + a2)];
+        const double Nv = b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
+        const double dd[3] = {b.dN[0][a0] * b.N[1][a1] * b.N[2][a2],
+                              b.N[0][a0] * b.dN[1][a1] * b.N[2][a2],
+                              b.N[0][a0] * b.N[1][a1] * b.dN[2][a2]};
+        const double wN = c.w * Nv;
+        const double P[3] = {c.x, c.y, c.z};
+        v[0] += wN;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[1 + d] += c.w * dd[d];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            v[4 + cc] += wN * P[cc];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[7 + 3 * cc + d] += c.w * dd[d] * P[cc];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    Wsum = v[0];
+    for (int cc = 0; cc < 3; ++cc) {
+        x[cc] = v[4 + cc] / Wsum;
+        for (int d = 0; d < 3; ++d) J[cc][d] = (v[7 + 3 * cc + d] - x[cc] * v[1 + d]) / Wsum;
+    }
+}
+
 __global__ void k_elem_centers(DevPatch dp, double* ecent) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
@@ -484,7 +529,7 @@ __device__ __forceinline__ float eval_ex2(float x) {
 
 // One block per query point: the threads search the element centres (in
 // FP32 when a copy is given: the centre only seeds Newton) and sum the
-// sources; thread 0 runs the Newton iteration.  Reductions in a fixed order
+// sources; warp 0 runs the Newton iteration (the basis terms over its lanes).  Reductions in a fixed order
 // (ties of the search: lowest element index).
 __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
     const int t = blockIdx.x;
@@ -547,6 +592,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
                 bd = s_d[k];
                 best = s_e[k];
             }
+        s_best = best;
+    }
+    __syncthreads();
+    if (w == 0) {
+        // Newton on x(xi) = x*, clamped to the parametric box, by warp 0
+        best = s_best;
         const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1],
                            best / (dp.ne[0] * dp.ne[1])};
         double xi[3], lo[3], hi[3];
@@ -556,12 +607,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
             lo[d] = dp.U[d][dp.p[d]];
             hi[d] = dp.U[d][dp.n[d]];
         }
-        // Newton on x(xi) = x*, clamped to the parametric box
         Basis1D b;
         double x[3], J[3][3], W;
         double res = 1e300;
         for (int it = 0; it < 60; ++it) {
-            eval_at(dp, xi, b, x, J, W);
+            eval_at_warp(dp, xi, b, x, J, W);
             const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
             res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
             if (res <= 1e-13 * a.scale) break;
@@ -576,19 +626,21 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
             }
             for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
         }
-        const int ok = res <= 1e-9 * a.scale;
-        double That = 0.0;
-        if (ok)
-            for (int a2 = 0; a2 <= dp.p[2]; ++a2)
-                for (int a1 = 0; a1 <= dp.p[1]; ++a1)
-                    for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
-                        const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
-                                                  b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
-                        const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
-                        That += R * a.That[a.perm[nat]];
-                    }
-        s_That = That;
-        s_ok = ok;
+        if (lane == 0) {
+            const int ok = res <= 1e-9 * a.scale;
+            double That = 0.0;
+            if (ok)
+                for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                    for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                        for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                            const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                      b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
+                            const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
+                            That += R * a.That[a.perm[nat]];
+                        }
+            s_That = That;
+            s_ok = ok;
+        }
     }
     // the sources: FP32 terms (each thread sums its ~n / 128 in FP32) or FP64
     const double px = xs[0] - a.x_ref, py = xs[1] - a.y_ref, dz = xs[2] - a.z_top;
