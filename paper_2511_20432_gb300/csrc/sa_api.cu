@@ -304,6 +304,7 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
         cudaGetLastError();
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
         delete c;
         return SA_ERR_CUDA;
     }
@@ -1359,8 +1360,16 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
     }
     c->n_step += n_steps;
     if (stats) {
+        // read the status, then (stream-ordered after the read) zero the
+        // counters read here (not n, not the barrier words): the next stats
+        // report covers the steps since this call; one synchronisation
         DevStatus h;
+        static const DevStatus zero{};
         SA_CUDA(c, cudaMemcpyAsync(&h, c->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->err, &zero.err, offsetof(DevStatus, n), cudaMemcpyHostToDevice, s));
+        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->iters_total, &zero.iters_total,
+                                   offsetof(DevStatus, pad) - offsetof(DevStatus, iters_total),
+                                   cudaMemcpyHostToDevice, s));
         SA_CUDA(c, cudaStreamSynchronize(s));
         stats->steps_done = n_steps;
         stats->pcg_iters_last = h.pcg_iters;
@@ -1372,15 +1381,6 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
         stats->step_index = h.n;
         stats->ws_used_last = h.ws_used;
         stats->ws_ratio_last = h.ws_ratio;
-        // reset the counters read above (not n, not the barrier words): the
-        // next stats report covers the steps since this call
-        DevStatus z;
-        std::memset(&z, 0, sizeof(z));
-        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->err, &z.err, offsetof(DevStatus, n), cudaMemcpyHostToDevice, s));
-        SA_CUDA(c, cudaMemcpyAsync(&c->st.p->iters_total, &z.iters_total,
-                                   offsetof(DevStatus, pad) - offsetof(DevStatus, iters_total),
-                                   cudaMemcpyHostToDevice, s));
-        SA_CUDA(c, cudaStreamSynchronize(s));
         if (h.err & SA_DEV_TIMEOUT) return sa_fail(c, SA_ERR_TIMEOUT, "a device-side wait timed out");
         if (h.err & SA_DEV_NAN) return sa_fail(c, SA_ERR_NAN, "non-finite value in the solve");
         if (h.err & (SA_DEV_NOT_CONVERGED | SA_DEV_BOT_NOT_CONVERGED))
