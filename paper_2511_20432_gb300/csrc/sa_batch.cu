@@ -83,6 +83,8 @@ struct sa_batch {
     DBuf<unsigned char> fdb_desc;
     DBuf<int> fdb_loff;
     DBuf<unsigned char> fdbS, fdbZ;   // n_dir x VT
+    // separable history sums over all instances (every face a rectangle)
+    SepPlan sep;
     int pcg_grid = 0;
     int hist_P = 4, hist_W = 8;
     cudaGraphExec_t graph_exec = nullptr;
@@ -888,6 +890,11 @@ sa_status build(sa_batch* b, double theta, double dt) {
         B_ALLOC(b, b->wpl1, nwork);
         const int smax = std::max(b->a_s.n_slices, b->mbot_s.n_slices);
         B_ALLOC(b, b->partials, (size_t)3 * std::max(smax, 1));
+        // separable history sums when every instance's faces allow them
+        if (b->opt.hist_mode != SA_HIST_PAIRWISE &&
+            !sep_batch_plan(b->inst, b->qlat_off, b->qbot_off, b->opt.precision, b->sep) &&
+            b->opt.hist_mode == SA_HIST_SEPARABLE)
+            return bfail(b, SA_ERR_ARG, "separable history sums: an instance's faces are not rectangles");
         // fast diagonalization of the main solves: every instance has it, in
         // the batch's precision
         b->fd_on = b->opt.precond != SA_PRECOND_JACOBI;
@@ -1004,10 +1011,15 @@ sa_status enqueue_batch_step(sa_batch* b) {
                                           b->src_pos.p, b->dt, alpha, b->opt.precision, b->s64T.p,
                                           b->s64F.p, b->s32T.p, b->s32F.p, s);
     if (e != cudaSuccess) return bcuda(b, e, "batched prologue");
-    e = launch_history_batch(b->opt.precision, b->hist_P, b->hist_W, b->st.p, b->q_lat, b->q_bot,
-                             b->lat32.p, b->bot32.p, b->lat64.p, b->bot64.p, b->s32F.p, b->s32T.p,
-                             b->s64F.p, b->s64T.p, b->s_lat.p, b->tt_bot.p, b->n_inst,
-                             b->d_qlat_off.p, b->d_qbot_off.p, b->d_src_off.p, b->d_n_active.p, s);
+    if (b->sep.ok)
+        e = launch_sep_batch(b->sep, b->opt.precision, b->st.p, b->d_n_active.p, b->d_src_off.p,
+                             b->s32F.p, b->s32T.p, b->s64F.p, b->s64T.p, b->s_lat.p, b->tt_bot.p, s);
+    else
+        e = launch_history_batch(b->opt.precision, b->hist_P, b->hist_W, b->st.p, b->q_lat,
+                                 b->q_bot, b->lat32.p, b->bot32.p, b->lat64.p, b->bot64.p,
+                                 b->s32F.p, b->s32T.p, b->s64F.p, b->s64T.p, b->s_lat.p,
+                                 b->tt_bot.p, b->n_inst, b->d_qlat_off.p, b->d_qbot_off.p,
+                                 b->d_src_off.p, b->d_n_active.p, s);
     if (e != cudaSuccess) return bcuda(b, e, "batched history");
     e = launch_gather(b->wlat_rows, b->wlat_rowdof.p, b->wlat_ptr.p, b->wlat_col.p, b->wlat_val.p,
                       b->s_lat.p, b->k, b->n_dir, b->wbot_ptr.p, b->wbot_col.p, b->wbot_val.p,
@@ -1060,7 +1072,8 @@ sa_status sa_batch_create(sa_ctx* const* insts, int n_inst, const sa_options* o,
         b->opt = *o;
     else
         sa_options_default(&b->opt);
-    if (b->opt.precision != SA_FP64 && b->opt.precision != SA_MIXED) {
+    if ((b->opt.precision != SA_FP64 && b->opt.precision != SA_MIXED) ||
+        b->opt.hist_mode < SA_HIST_AUTO || b->opt.hist_mode > SA_HIST_SEPARABLE) {
         delete b;
         return SA_ERR_ARG;
     }

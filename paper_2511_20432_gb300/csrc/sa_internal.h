@@ -192,6 +192,8 @@ struct SepFace {
     int flux;               // 1: lateral flux (output s_lat = -sum); 0: bottom T~
     double dd;              // fixed coordinate
     double nsgn;            // outward normal along axd (flux faces), else 1
+    int inst;               // instance of a batch (0 for one context)
+    int pad;
 };
 
 // Separable history plan: faces, tiles (lateral tiles first), the split of
@@ -501,6 +503,15 @@ cudaError_t launch_history(int precision, int P, int warps, DevStatus* st, int q
 sa_status sep_setup(sa_ctx* c);
 sa_status sep_alloc(sa_ctx* c);
 cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s);
+// Batched instances (each with its plan): one plan over all of them, faces
+// shifted to the batch's point offsets, one unit per tile.  False when an
+// instance has no separable plan.
+bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& qlat_off,
+                    const std::vector<int>& qbot_off, int precision, SepPlan& P);
+cudaError_t launch_sep_batch(const SepPlan& P, int precision, DevStatus* st, const int* n_active,
+                             const int* src_off, const float4* s32F, const float4* s32T,
+                             const double4* s64F, const double4* s64T, double* s_lat,
+                             double* tt_bot, cudaStream_t s);
 // T = T~ + T^ at points; ecent32 (FP32 copy of the element centres) and
 // s32T (FP32 source coefficients) are optional: with them the search and the
 // source sum run in FP32 (mixed contexts).

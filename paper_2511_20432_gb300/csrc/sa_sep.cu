@@ -78,6 +78,10 @@ struct SepArgs {
     const double2* pos;
     double dt, r2_8a, four_alpha;
     float l2E;
+    // batched instances: active sources and first source of each instance
+    // (null for one context)
+    const int* inst_K;
+    const int* inst_src;
     const float* c32;
     const double* c64;
     const float4* s32F;
@@ -102,7 +106,8 @@ struct SrcOf<double> {
 };
 
 // Active sources at this step: min(n + 1, n_src) (the prologue's count).
-__device__ __forceinline__ int active_sources(const SepArgs& a) {
+__device__ __forceinline__ int active_sources(const SepArgs& a, int inst) {
+    if (a.inst_K) return a.inst_K[inst];
     if (!a.coef) return a.st->n_active;
     const long long n1 = a.st->n + 1;
     return (int)(n1 < (long long)a.n_src ? n1 : (long long)a.n_src);
@@ -122,13 +127,14 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
     __shared__ T4 prm[kMaxUnit];         // per source: s_A, s_B, exponent scale, offset
     __shared__ T mul[kMaxUnit];
     const int tile = a.tile0 + (int)blockIdx.x;
-    const int K = active_sources(a);
+    const int4 td = a.tiles[tile];
+    const SepFace f = a.faces[td.x];
+    const int K = active_sources(a, f.inst);
     const int u = unit_len(K, a.s_max, kKC);
     const int k0 = (int)blockIdx.y * u;
     if (k0 >= K) return;                 // no sources for this unit (uniform per CTA)
     const int n = min(K - k0, u);
-    const int4 td = a.tiles[tile];
-    const SepFace f = a.faces[td.x];
+    const int so = a.inst_src ? a.inst_src[f.inst] : 0;   // the instance's first source
     const T* coord = kMixed ? (const T*)a.c32 : (const T*)a.c64;
     for (int t = threadIdx.x; t < NCOL; t += NT) {
         if (t < kTI) {
@@ -139,60 +145,7 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
             xs[t] = j < f.Lb ? coord[f.b_off + j] : T(0);
         }
     }
-    // the unit's source parameters, once (chunk padding: FB = 0)
-    {
-        const V* src = kMixed ? (const V*)(f.flux ? (const void*)a.s32F : (const void*)a.s32T)
-                              : (const V*)(f.flux ? (const void*)a.s64F : (const void*)a.s64T);
-        const T dd = (T)f.dd, nsgn = (T)f.nsgn;
-        const int npad = (n + kKC - 1) / kKC * kKC;
-        for (int t = threadIdx.x; t < npad; t += NT) {
-            T sa = 0, sb = 0, sc = 0, off = 0, m = 0;
-            if (t < n) {
-                V sv;
-                if (kMixed && a.coef) {
-                    // (sx, sy, -a log2 e, log2 w) from the age, in FP32:
-                    // log2 c = log2 E' - 1.5 log2(4 pi alpha age),
-                    // log2 g = 1 - log2(4 alpha age) + log2 c
-                    const long long I = k0 + t + 1;
-                    const float age = (float)((double)(a.st->n + 1 - I) * a.dt + a.r2_8a);
-                    const float fa = (float)a.four_alpha * age;
-                    const float l4a = log2f(fa);
-                    const float l2c = a.l2E - 1.5f * (1.65149613f + l4a);
-                    const double2 p = a.pos[k0 + t];
-                    sv.x = (float)p.x;
-                    sv.y = (float)p.y;
-                    sv.z = -1.44269504f / fa;
-                    sv.w = f.flux ? 1.0f - l4a + l2c : l2c;
-                } else {
-                    sv = src[k0 + t];
-                }
-                // sources lie on the top plane (relative z = 0)
-                auto sc3 = [&](int ax) { return ax == 0 ? (T)sv.x : (ax == 1 ? (T)sv.y : T(0)); };
-                sa = sc3(f.axa);
-                sb = sc3(f.axb);
-                const T dsd = dd - sc3(f.axd);
-                if (kMixed) {
-                    // log2 units: sv.z = -a log2 e, sv.w = log2 w
-                    sc = (T)sv.z;
-                    off = fma(sc, dsd * dsd, (T)sv.w);
-                    m = f.flux ? nsgn * dsd : T(1);
-                } else {
-                    // sv.z = a, sv.w = w
-                    sc = -(T)sv.z;
-                    off = sc * dsd * dsd;
-                    m = (T)sv.w * (f.flux ? nsgn * dsd : T(1));
-                }
-            }
-            T4 p4;
-            p4.x = sa;
-            p4.y = sb;
-            p4.z = sc;
-            p4.w = off;
-            prm[t] = p4;
-            mul[t] = m;
-        }
-    }
-    __syncthreads();
+    __syncthreads();   // xs written
     // factors of chunk c into buffer c & 1 (log2 units; FP64: natural ones
     // with w folded into m):
     //   FA = 2^(sc (x - s_A)^2)        thread t: column t % 64, sources
@@ -232,35 +185,94 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) acc[r][cc] = T(0);
-    const int nch = (n + kKC - 1) / kKC;
-    gen(0);
-    __syncthreads();
-    for (int c = 0; c < nch; ++c) {
-        if (c + 1 < nch) gen(c + 1);     // the other buffer
-        const int b = c & 1;
-        T cs[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) cs[r][cc] = kMixed ? T(0) : acc[r][cc];
-#pragma unroll 8
-        for (int kk = 0; kk < kKC; ++kk) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                av[r] = fab[b][kk][r0 + r];
-                bv[r] = fab[b][kk][kTI + c0 + r];
+    // the unit in rounds of at most kMaxUnit sources: their parameters staged
+    // once per round (chunk padding: FB = 0)
+    for (int rb = 0; rb < n; rb += kMaxUnit) {
+        const int nr = min(kMaxUnit, n - rb);
+        __syncthreads();   // the previous round's parameters and factors are consumed
+        {
+            const V* src = kMixed ? (const V*)(f.flux ? (const void*)a.s32F : (const void*)a.s32T)
+                                  : (const V*)(f.flux ? (const void*)a.s64F : (const void*)a.s64T);
+            const T dd = (T)f.dd, nsgn = (T)f.nsgn;
+            const int npad = (nr + kKC - 1) / kKC * kKC;
+            for (int t = threadIdx.x; t < npad; t += NT) {
+                T sa = 0, sb = 0, sc = 0, off = 0, m = 0;
+                if (t < nr) {
+                    V sv;
+                    if (kMixed && a.coef) {
+                        // (sx, sy, -a log2 e, log2 w) from the age, in FP32:
+                        // log2 c = log2 E' - 1.5 log2(4 pi alpha age),
+                        // log2 g = 1 - log2(4 alpha age) + log2 c
+                        const long long I = k0 + rb + t + 1;
+                        const float age = (float)((double)(a.st->n + 1 - I) * a.dt + a.r2_8a);
+                        const float fa = (float)a.four_alpha * age;
+                        const float l4a = log2f(fa);
+                        const float l2c = a.l2E - 1.5f * (1.65149613f + l4a);
+                        const double2 p = a.pos[k0 + rb + t];
+                        sv.x = (float)p.x;
+                        sv.y = (float)p.y;
+                        sv.z = -1.44269504f / fa;
+                        sv.w = f.flux ? 1.0f - l4a + l2c : l2c;
+                    } else {
+                        sv = src[so + k0 + rb + t];
+                    }
+                    // sources lie on the top plane (relative z = 0)
+                    auto sc3 = [&](int ax) { return ax == 0 ? (T)sv.x : (ax == 1 ? (T)sv.y : T(0)); };
+                    sa = sc3(f.axa);
+                    sb = sc3(f.axb);
+                    const T dsd = dd - sc3(f.axd);
+                    if (kMixed) {
+                        // log2 units: sv.z = -a log2 e, sv.w = log2 w
+                        sc = (T)sv.z;
+                        off = fma(sc, dsd * dsd, (T)sv.w);
+                        m = f.flux ? nsgn * dsd : T(1);
+                    } else {
+                        // sv.z = a, sv.w = w
+                        sc = -(T)sv.z;
+                        off = sc * dsd * dsd;
+                        m = (T)sv.w * (f.flux ? nsgn * dsd : T(1));
+                    }
+                }
+                T4 p4;
+                p4.x = sa;
+                p4.y = sb;
+                p4.z = sc;
+                p4.w = off;
+                prm[t] = p4;
+                mul[t] = m;
             }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) cs[r][cc] = fma(av[r], bv[cc], cs[r][cc]);
         }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) acc[r][cc] = kMixed ? acc[r][cc] + cs[r][cc] : cs[r][cc];
-        __syncthreads();   // buffer b is consumed and the other one is written
+        __syncthreads();
+        const int nch = (nr + kKC - 1) / kKC;
+        gen(0);
+        __syncthreads();
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) gen(c + 1);     // the other buffer
+            const int b = c & 1;
+            T cs[4][4];
+    #pragma unroll
+            for (int r = 0; r < 4; ++r)
+    #pragma unroll
+                for (int cc = 0; cc < 4; ++cc) cs[r][cc] = kMixed ? T(0) : acc[r][cc];
+    #pragma unroll 8
+            for (int kk = 0; kk < kKC; ++kk) {
+                T av[4], bv[4];
+    #pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    av[r] = fab[b][kk][r0 + r];
+                    bv[r] = fab[b][kk][kTI + c0 + r];
+                }
+    #pragma unroll
+                for (int r = 0; r < 4; ++r)
+    #pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) cs[r][cc] = fma(av[r], bv[cc], cs[r][cc]);
+            }
+    #pragma unroll
+            for (int r = 0; r < 4; ++r)
+    #pragma unroll
+                for (int cc = 0; cc < 4; ++cc) acc[r][cc] = kMixed ? acc[r][cc] + cs[r][cc] : cs[r][cc];
+            __syncthreads();   // buffer b is consumed and the other one is written
+        }
     }
     // unit sums: entry (jj, ii) of the tile at jj * 64 + ii
     T* part = (kMixed ? (T*)a.p32 : (T*)a.p64) +
@@ -293,7 +305,7 @@ __global__ void __launch_bounds__(256) k_sep_reduce(SepArgs a) {
     const int jj = e / kTI, ii = e - jj * kTI;
     const int i = td.y + ii, j = td.z + jj;
     ok = ok && i < f.La && j < f.Lb;
-    const int K = active_sources(a);
+    const int K = active_sources(a, f.inst);
     if (a.coef && g == 0) a.st->n_active = K;
     const int u = unit_len(K, a.s_max, kKC);
     const int ns = K > 0 ? (K + u - 1) / u : 0;
@@ -558,6 +570,8 @@ cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s) {
         a.r2_8a = c->spot_radius * c->spot_radius / (8.0 * alpha);
         a.four_alpha = 4.0 * alpha;
         a.l2E = (float)std::log2(c->opt.half_space_factor * c->E / (c->rho * c->cp));
+        a.inst_K = nullptr;
+        a.inst_src = nullptr;
         a.c32 = P.coord32.p;
         a.c64 = P.coord64.p;
         a.s32F = c->src32F.p;
@@ -570,6 +584,116 @@ cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s) {
         a.tt_bot = c->tt_bot.p;
         const cudaError_t e = c->opt.precision == SA_MIXED ? launch_sep_tj<float>(P.tj[kind], a, s)
                                                            : launch_sep_tj<double>(P.tj[kind], a, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One plan over batched instances: every instance's faces with their output
+// offsets moved to the batch's point ranges, their coordinate lists
+// concatenated, tiles rebuilt with one tile width per kind; one unit per
+// tile (the unit runs in staging rounds), so the unit sums are the tile's
+// sums.
+bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& qlat_off,
+                    const std::vector<int>& qbot_off, int precision, SepPlan& P) {
+    P.ok = false;
+    P.faces_h.clear();
+    P.tiles_h.clear();
+    P.coord_h.clear();
+    P.n_tiles[0] = P.n_tiles[1] = 0;
+    for (const sa_ctx* c : insts)
+        if (!c->sep.ok) return false;
+    std::vector<int> coff(insts.size());
+    for (size_t i = 0; i < insts.size(); ++i) {
+        coff[i] = (int)P.coord_h.size();
+        P.coord_h.insert(P.coord_h.end(), insts[i]->sep.coord_h.begin(), insts[i]->sep.coord_h.end());
+    }
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<int> mine;
+        for (size_t i = 0; i < insts.size(); ++i)
+            for (SepFace F : insts[i]->sep.faces_h) {
+                if (F.flux != (kind == 0)) continue;
+                F.q0 += kind == 0 ? qlat_off[i] : qbot_off[i];
+                F.a_off += coff[i];
+                F.b_off += coff[i];
+                F.inst = (int)i;
+                mine.push_back((int)P.faces_h.size());
+                P.faces_h.push_back(F);
+            }
+        long long best = -1;
+        for (int tj : {64, 48, 32}) {
+            long long area = 0;
+            for (int fi : mine) {
+                const SepFace& F = P.faces_h[fi];
+                area += (long long)((F.La + kTI - 1) / kTI) * kTI * ((F.Lb + tj - 1) / tj) * tj;
+            }
+            if (best < 0 || area < best) {
+                best = area;
+                P.tj[kind] = tj;
+            }
+        }
+        for (int fi : mine) {
+            const SepFace& F = P.faces_h[fi];
+            for (int i0 = 0; i0 < F.La; i0 += kTI)
+                for (int j0 = 0; j0 < F.Lb; j0 += P.tj[kind]) {
+                    P.tiles_h.push_back(make_int4(fi, i0, j0, 0));
+                    ++P.n_tiles[kind];
+                }
+        }
+    }
+    P.s_max = 1;
+    P.unit = 0;
+    const std::vector<float> c32(P.coord_h.begin(), P.coord_h.end());
+    const size_t len = (size_t)std::max(1, P.n_tiles[0] + P.n_tiles[1]) * kPStride;
+    bool ok = P.faces.alloc(P.faces_h.size()) == cudaSuccess &&
+              P.tiles.alloc(P.tiles_h.size()) == cudaSuccess &&
+              P.coord64.alloc(P.coord_h.size()) == cudaSuccess &&
+              P.coord32.alloc(c32.size()) == cudaSuccess &&
+              (precision == SA_MIXED ? P.part32.alloc(len) : P.part64.alloc(len)) == cudaSuccess;
+    ok = ok && cudaMemcpy(P.faces.p, P.faces_h.data(), sizeof(SepFace) * P.faces_h.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(P.tiles.p, P.tiles_h.data(), sizeof(int4) * P.tiles_h.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(P.coord64.p, P.coord_h.data(), sizeof(double) * P.coord_h.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(P.coord32.p, c32.data(), sizeof(float) * c32.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return false;
+    }
+    P.ok = true;
+    return true;
+}
+
+cudaError_t launch_sep_batch(const SepPlan& P, int precision, DevStatus* st, const int* n_active,
+                             const int* src_off, const float4* s32F, const float4* s32T,
+                             const double4* s64F, const double4* s64T, double* s_lat,
+                             double* tt_bot, cudaStream_t s) {
+    for (int kind = 0; kind < 2; ++kind) {
+        SepArgs a{};
+        a.faces = P.faces.p;
+        a.tiles = P.tiles.p;
+        a.tile0 = kind == 0 ? 0 : P.n_tiles[0];
+        a.n_tiles = P.n_tiles[kind];
+        a.unit = 0;
+        a.s_max = 1;
+        a.st = st;
+        a.coef = 0;
+        a.inst_K = n_active;
+        a.inst_src = src_off;
+        a.c32 = P.coord32.p;
+        a.c64 = P.coord64.p;
+        a.s32F = s32F;
+        a.s32T = s32T;
+        a.s64F = s64F;
+        a.s64T = s64T;
+        a.p32 = P.part32.p;
+        a.p64 = P.part64.p;
+        a.s_lat = s_lat;
+        a.tt_bot = tt_bot;
+        const cudaError_t e = precision == SA_MIXED ? launch_sep_tj<float>(P.tj[kind], a, s)
+                                                    : launch_sep_tj<double>(P.tj[kind], a, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -32,18 +32,21 @@ def _instances():
     return out
 
 
+@pytest.mark.parametrize("hist", ["separable", "pairwise"])
 @pytest.mark.parametrize("precond", ["fd", "jacobi"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_matches_single_contexts(sa, prec, precond):
+def test_batch_matches_single_contexts(sa, prec, precond, hist):
     import torch
     p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
     pc = sa.SA_PRECOND_AUTO if precond == "fd" else sa.SA_PRECOND_JACOBI
+    hm = sa.SA_HIST_SEPARABLE if hist == "separable" else sa.SA_HIST_PAIRWISE
     wls = _instances()
     s = torch.cuda.Stream()
     tol = 1e-15 if p == sa.SA_FP64 else 1e-10
-    ctxs = [gpu_context(wl, p, pcg_tol=tol, precond=pc) for wl in wls]
-    singles = [gpu_context(wl, p, pcg_tol=tol, precond=pc) for wl in wls]
-    batch = sa.Batch(ctxs, precision=p, pcg_tol=tol, cuda_stream=s, use_graph=1, precond=pc)
+    ctxs = [gpu_context(wl, p, pcg_tol=tol, precond=pc, hist_mode=hm) for wl in wls]
+    singles = [gpu_context(wl, p, pcg_tol=tol, precond=pc, hist_mode=hm) for wl in wls]
+    batch = sa.Batch(ctxs, precision=p, pcg_tol=tol, cuda_stream=s, use_graph=1, precond=pc,
+                     hist_mode=hm)
     n = 60
     batch.step(0.5, 5e-6, n)
     for c in singles:
@@ -60,8 +63,10 @@ def test_batch_matches_single_contexts(sa, prec, precond):
             assert rel_linf(Tb, Ts) <= 1e-11, i
         else:
             assert rel_linf(Tb, Ts) <= TOL_MIXED_REL and np.abs(Tb - Ts).max() <= TOL_MIXED_ABS, i
+        # separable, mixed: the batch sums a tile's sources in one unit, the
+        # context in several (other FP32 rounding, up to ~(32 + chunks) ulp)
         assert rel_linf(batch.field(i, sa.SA_FIELD_DTDN_LAT), c.field(sa.SA_FIELD_DTDN_LAT)) <= (
-            1e-12 if p == sa.SA_FP64 else 1e-6)
+            1e-12 if p == sa.SA_FP64 else (1e-5 if hist == "separable" else 1e-6))
 
 
 def test_batch_fp64_against_oracle(sa):
