@@ -21,14 +21,18 @@
 // Work layout: CTA (tile, unit) multiplies the 64 x TJ output tile over one
 // unit of consecutive sources: the active sources split evenly over a fixed
 // number of units (about four CTAs per multiprocessor), so the grid is static
-// while the active count grows and every CTA has work.  Per chunk of 32 sources the CTA
-// writes FA and FB into shared memory, then each thread accumulates a 4 x 4
-// register tile (small, so that many warps hide the shared-memory latency).  Mixed path: FP32 factors and products, each chunk summed
-// into fresh registers and then added to the unit's sum (the rounding error
-// grows with the chunk length plus the number of chunks, not with the
+// while the active count grows and every CTA has work; a unit is staged in
+// rounds of at most 512 sources (256 in FP64).  Per chunk of 32 sources the
+// CTA writes FA and FB into shared memory (double-buffered), then each thread
+// accumulates a 4 x 4 register tile (small, so that many warps hide the
+// shared-memory latency).  Mixed path: FP32 factors and products, each chunk
+// summed into fresh registers and then added to the unit's sum (the rounding
+// error grows with the chunk length plus the number of chunks, not with the
 // unit); FP64 path: FP64 throughout.  The unit sums go to a partial buffer;
 // a second kernel adds the active units of every point in a fixed order and
-// writes the point's value: deterministic, no atomics.
+// writes the point's value: deterministic, no atomics.  Batched instances
+// share one plan: each face records its instance, whose active count and
+// first source the kernels look up.
 //
 // This is not the paper's evaluation (it sums pairwise); it is the same sum
 // reordered by the distributive law, and applies only where the faces are
@@ -44,7 +48,7 @@ namespace {
 
 constexpr int kTI = 64;            // tile rows (A list)
 constexpr int kPStride = 64 * 64;  // partial-buffer entries per (tile, unit)
-// sources per chunk and per unit at most (static shared memory under 48 KB)
+// sources per chunk and per staging round (static shared memory under 48 KB)
 template <typename T>
 __host__ __device__ constexpr int chunk_of() { return sizeof(T) == 4 ? 32 : 16; }
 template <typename T>
