@@ -81,6 +81,34 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def shard(n, rank, world):
+    """Contiguous share [lo, hi) of n independent units (instances) for one
+    rank; the first n % world ranks take one more.  No unit is shared, so the
+    ranks need no collective on the data path."""
+    q, r = divmod(n, world)
+    lo = rank * q + min(rank, r)
+    return lo, lo + q + (1 if rank < r else 0)
+
+
+def max_over_ranks(value, dist, device="cpu"):
+    """The largest of the ranks' values (the job's time: the slowest rank)."""
+    return _reduce_ranks(value, dist, device, "MAX")
+
+
+def sum_over_ranks(value, dist, device="cpu"):
+    """The sum of the ranks' values (work done by the whole job)."""
+    return _reduce_ranks(value, dist, device, "SUM")
+
+
+def _reduce_ranks(value, dist, device, op):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op))
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -353,13 +381,16 @@ def plate_leg(sa, W, stream, n_ff, K):
     return out
 
 
-def batched_leg(sa, W, stream, n_inst, n_steps):
+def batched_leg(sa, W, stream, n_inst, n_steps, rank=0, world=1, dist=None):
     """The batched sweep: n_inst seeded instances (uneven boxes, powers,
     speeds, track counts) stepped together for n_steps theta-steps (the
-    first 3 untimed), one launch per stage for all instances."""
+    first 3 untimed), one launch per stage for all instances.  With several
+    ranks each takes a contiguous share of the instances (no collective on
+    the data path); the time is the slowest rank's."""
     import numpy as np
     t0 = time.perf_counter()
-    wls = [W.batched_instance(i, n_steps=n_steps) for i in range(n_inst)]
+    lo, hi = shard(n_inst, rank, world)
+    wls = [W.batched_instance(i, n_steps=n_steps) for i in range(lo, hi)]
     ctxs = [sa.context_from_workload(wl, precision=sa.SA_MIXED) for wl in wls]
     b = sa.Batch(ctxs, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
     setup_s = time.perf_counter() - t0
@@ -368,14 +399,19 @@ def batched_leg(sa, W, stream, n_inst, n_steps):
     sz = [c.sizes() for c in ctxs]
     K = n_steps - 3
     pairs = sum((z.q_lat + z.q_bot) * sum(min(n, z.n_src) for n in range(4, n_steps + 1)) for z in sz)
-    ms = time_graph(b, th, dt, K, stream)
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(time_graph(b, th, dt, K, stream), dist, "cuda")
+    pairs = sum_over_ranks(pairs, dist, "cuda")
     m_it, b_it = b.iters()
     out = {"instances": n_inst, "steps": n_steps, "timed_steps": K, "setup_s": setup_s,
            "ms_per_step": ms / K, "instance_steps_per_s": n_inst * K / (ms / 1e3),
            "point_source_evals_per_s": pairs / (ms / 1e3),
-           "total_control_variables": int(sum(z.n_dof for z in sz)),
-           "total_boundary_points": int(sum(z.q_lat + z.q_bot for z in sz)),
-           "last_step_main_iters_max": int(m_it.max()), "last_step_bottom_iters_max": int(b_it.max())}
+           "total_control_variables": int(sum_over_ranks(sum(z.n_dof for z in sz), dist, "cuda")),
+           "total_boundary_points": int(sum_over_ranks(sum(z.q_lat + z.q_bot for z in sz), dist, "cuda")),
+           "last_step_main_iters_max": int(max_over_ranks(int(m_it.max()), dist, "cuda")),
+           "last_step_bottom_iters_max": int(max_over_ranks(int(b_it.max()), dist, "cuda")),
+           "ranks": world}
     b.close()
     for c in ctxs:
         c.close()
@@ -435,10 +471,7 @@ def run_ours(args):
     clk = clocks_start(local)
     ms = time_graph(ctx, th, dt, K, stream)
     clocks = clocks_stop(clk)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     stats = ctx.step(th, dt, 0)                # counters accumulated over the timed steps
     iters_avg = stats.pcg_iters_total / K
     bot_avg = stats.bot_iters_total / K
@@ -528,7 +561,8 @@ def run_ours(args):
     assert np.isfinite(T_mon).all()
 
     # ---- the batched sweep (256 instances, 2000 steps) ------------------------------
-    batched = batched_leg(sa, W, stream, 256, args.batch_steps) if world == 1 and args.batch_steps > 3 else None
+    batched = (batched_leg(sa, W, stream, 256, args.batch_steps, rank, world, dist)
+               if args.batch_steps > 3 else None)
 
     # ---- the plate with a hole ---------------------------------------------------
     plate = plate_leg(sa, W, stream, 1000, min(K, 300)) if world == 1 else None
