@@ -960,10 +960,6 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         int ks = 1;
         while (ks < 8 && c->a_s.n_slices * ks * 2 <= warps) ks *= 2;
         c->pcg_ksplit = ks;
-        if (const char* e = getenv("SA_PCG_KSPLIT")) {   // tuning override (1, 2, 4, 8)
-            const int v = atoi(e);
-            if (v == 1 || v == 2 || v == 4 || v == 8) c->pcg_ksplit = v;
-        }
         SA_ALLOC(c, c->partials, (size_t)12 * c->pcg_grid);
         if (c->opt.precond != SA_PRECOND_JACOBI) {
             sa_status fst = fd_setup(c);
@@ -1258,7 +1254,6 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.max_iter = c->opt.pcg_max_iter;
         L.grid = c->pcg_grid;
         L.ksplit = 0;
-        if (const char* ev = getenv("SA_PCG_KSPLIT")) L.ksplit = atoi(ev);
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
     }
