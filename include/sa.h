@@ -253,6 +253,18 @@ sa_status sa_eval_T(sa_ctx* ctx, const double* pts, int n, double* T_out, int on
  */
 sa_status sa_eval_T_noalloc(sa_ctx* ctx, const double* pts, int n, double* T_out);
 
+/*
+ * Self-test of the device-side bounded waits (no paper counterpart; for the
+ * tests).  Launches (1) two blocks of which one leaves without arriving, so
+ * the other's grid-barrier wait never completes, and (2) one block waiting on
+ * an mbarrier that nothing arrives at.  Each wait gives up after its time
+ * limit (2 s, 1 s), records SA_DEV_TIMEOUT in a status word and returns; no
+ * fault, the device stays usable.  *barrier_flagged / *mbarrier_flagged
+ * (may be NULL) get 1 when the flag was recorded.  Uses the current device;
+ * synchronous.  Errors: SA_ERR_CUDA.
+ */
+sa_status sa_selftest_waits(int* barrier_flagged, int* mbarrier_flagged);
+
 /* Sizes of a context after set-up. */
 typedef struct sa_sizes {
     int n_dof, n_free, n_dir;      /* control variables; free / Dirichlet             */

@@ -100,6 +100,7 @@ def _load():
         "sa_batch_destroy": (V, [P]),
         "sa_destroy": (V, [P]),
         "sa_status_str": (C.c_char_p, [I]),
+        "sa_selftest_waits": (I, [C.POINTER(I), C.POINTER(I)]),
         "sa_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -381,6 +382,16 @@ class Batch:
         path = cache_path.encode() if cache_path else None
         self._check(lib.sa_batch_autotune(self.ptr, path, C.byref(P), C.byref(W), C.byref(ms)))
         return P.value, W.value, ms.value
+
+
+def selftest_waits():
+    """Run the bounded-wait self-test (see include/sa.h): returns whether the
+    grid-barrier wait and the mbarrier wait gave up and flagged a timeout."""
+    a, b = C.c_int(0), C.c_int(0)
+    st = lib.sa_selftest_waits(C.byref(a), C.byref(b))
+    if st != SA_OK:
+        raise SAError(st, "sa_selftest_waits: " + status_name(st))
+    return bool(a.value), bool(b.value)
 
 
 def context_from_workload(wl, precision=SA_FP64, s_img=2.0, **opts):

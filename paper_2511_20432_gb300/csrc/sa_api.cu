@@ -8,6 +8,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "sa_async.cuh"
 #include "sa_internal.h"
 
 
@@ -199,6 +200,23 @@ cudaError_t upload(DBuf<T>& b, const std::vector<T>& v) {
         }                                                                                     \
     } while (0)
 
+// Self-test kernels: waits that nothing completes (bounded, flag on give-up).
+__global__ void k_selftest_barrier(unsigned* count, int* err) {
+    if (blockIdx.x == 1) return;    // leaves without arriving
+    unsigned nb = 0;
+    sa_dev::count_barrier(count, nb, err, SA_DEV_TIMEOUT);
+}
+
+__global__ void k_selftest_mbarrier(int* err) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        sa_dev::mbar_init(&bar, 1);   // expects one arrival; none comes
+        sa_dev::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !sa_dev::mbar_wait_bounded(&bar, 0)) atomicOr(err, SA_DEV_TIMEOUT);
+}
+
 }  // namespace
 
 // Captured step graphs depend on the operator, the warm start and the
@@ -224,6 +242,33 @@ void sa_options_default(sa_options* o) {
     o->device = -1;
     o->hist_points_per_lane = 0;
     o->hist_warps = 0;
+}
+
+sa_status sa_selftest_waits(int* barrier_flagged, int* mbarrier_flagged) {
+    int* d = nullptr;   // [0] barrier counter, [1] status of (1), [2] status of (2)
+    if (cudaMalloc((void**)&d, 3 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return SA_ERR_CUDA;
+    }
+    int h[3] = {0, 0, 0};
+    cudaError_t e = cudaMemset(d, 0, 3 * sizeof(int));
+    if (e == cudaSuccess) {
+        k_selftest_barrier<<<2, 32>>>((unsigned*)d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_selftest_mbarrier<<<1, 32>>>(d + 2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SA_ERR_CUDA;
+    }
+    if (barrier_flagged) *barrier_flagged = (h[1] & SA_DEV_TIMEOUT) ? 1 : 0;
+    if (mbarrier_flagged) *mbarrier_flagged = (h[2] & SA_DEV_TIMEOUT) ? 1 : 0;
+    return SA_OK;
 }
 
 const char* sa_status_str(sa_status s) {

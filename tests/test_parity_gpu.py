@@ -262,6 +262,21 @@ def test_separable_matches_pairwise_full_size(sa):
     assert np.abs(out[sa.SA_MIXED, 2][2] - ref[2]).max() <= TOL_MIXED_ABS
 
 
+def test_bounded_waits_give_up(sa):
+    """Failure detection without a GPU fault: a grid-barrier wait and an
+    mbarrier wait that nothing completes give up within their limits (2 s,
+    1 s) and flag SA_DEV_TIMEOUT; the device keeps working afterwards."""
+    import time
+    t0 = time.time()
+    bar, mbar = sa.selftest_waits()
+    assert bar and mbar
+    assert time.time() - t0 < 30
+    wl = W.small_block()
+    ctx = gpu_context(wl, sa.SA_MIXED)
+    ctx.step(wl.theta, wl.dt, 5)
+    assert np.isfinite(ctx.field(sa.SA_FIELD_THAT)).all()
+
+
 def test_degenerate_cases(sa):
     """No sources before the first step; a scan whose laser is off: T^ stays
     T_c exactly; the empty eval call; one element, degree 1."""
