@@ -1000,11 +1000,6 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         if (occ < 1) return sa_fail(c, SA_ERR_CUDA, "PCG kernel cannot be resident");
         c->pcg_block = pcg_block_size();
         c->pcg_grid = c->num_sms;   // one co-resident block of 1024 threads per SM
-        // split each slice over enough warps to fill the grid (at most 8)
-        const int warps = c->pcg_grid * (pcg_block_size() / 32);
-        int ks = 1;
-        while (ks < 8 && c->a_s.n_slices * ks * 2 <= warps) ks *= 2;
-        c->pcg_ksplit = ks;
         SA_ALLOC(c, c->partials, (size_t)12 * c->pcg_grid);
         if (c->opt.precond != SA_PRECOND_JACOBI) {
             sa_status fst = fd_setup(c);

@@ -382,7 +382,7 @@ struct sa_ctx {
     DBuf<float> dev32;
     DBuf<double> partials;    // 4 * max grid
     DBuf<DevStatus> st;
-    int pcg_grid = 0, pcg_block = 0, pcg_ksplit = 1;
+    int pcg_grid = 0, pcg_block = 0;
     int hist_P = 0, hist_W = 0;
 
     // ---- device: set-up and evaluation helpers ---------------------------------
