@@ -641,3 +641,55 @@ def test_P12_patch_test_on_the_closed_plate():
     e16 = _plate_patch_test_error((16, 8, 2))
     assert e16 <= 1e-5, (e8, e16)
     assert e8 / e16 >= 64.0, (e8, e16)
+
+
+# ---------------------------------------------------------------------------
+# R12: on a face that is an axis-aligned rectangle the quadrature points are
+#      a tensor grid, and the history sums factorise along the face's axes
+#      (Eq. sum-of-point-temp summed in another order): a matrix product over
+#      the sources equals the oracle's pairwise sums.
+# ---------------------------------------------------------------------------
+def test_R12_separable_sums_equal_pairwise_on_box_faces():
+    patch = W.cuboid_patch((0.9e-3, 0.7e-3, 0.4e-3), (5, 4, 3), (2, 3, 2))
+    geom = PatchGeom(patch)
+    z = geom.top_z()
+    rng = np.random.default_rng(12)
+    K = 40
+    xs = np.column_stack([rng.uniform(0.1e-3, 0.8e-3, K), rng.uniform(0.1e-3, 0.6e-3, K),
+                          np.full(K, z)])
+    age = pointsource.ages(K + 5, K, 5e-6, MAT, 20e-6)
+    E = 1e-3
+    a = 1.0 / (4.0 * ALPHA * age)
+    c = 2.0 * E / (MAT.rho * MAT.cp * (4.0 * np.pi * ALPHA * age) ** 1.5)
+    g = 2.0 * a * c
+    checked = 0
+    for face, kind in enumerate(geom.faces):
+        if kind == 0:
+            continue
+        pts = geom.face_points(face)
+        x, nrm = pts["x"], pts["n"]
+        d = int(np.argmax(np.abs(nrm[0])))                  # the normal's axis
+        u, v = [ax for ax in range(3) if ax != d]
+        # distinct coordinates up to rounding (1e-12 of the extent)
+        key_u, key_v = np.round(x[:, u] / 1e-3, 9), np.round(x[:, v] / 1e-3, 9)
+        ku, iu = np.unique(key_u, return_index=True)
+        kv, iv = np.unique(key_v, return_index=True)
+        A, B = x[iu, u], x[iv, v]
+        assert len(A) * len(B) == len(x)                    # a full tensor grid
+        i, j = np.searchsorted(ku, key_u), np.searchsorted(kv, key_v)
+        assert np.abs(A[i] - x[:, u]).max() <= 1e-15 and np.abs(B[j] - x[:, v]).max() <= 1e-15
+        dd = x[0, d]
+        assert np.allclose(x[:, d], dd, rtol=0, atol=1e-15)
+        FA = np.exp(-a[:, None] * (A[None, :] - xs[:, u, None]) ** 2)            # (K, |A|)
+        ed = np.exp(-a * (dd - xs[:, d]) ** 2)
+        if kind == 1:   # dT~/dn = sum -g n_d (d - s_d) exp(-a R^2)
+            w = -g * nrm[0, d] * (dd - xs[:, d]) * ed
+            ref = pointsource.dTdn_tilde(x, nrm, xs, age, E, MAT)
+        else:           # T~ = sum c exp(-a R^2)
+            w = c * ed
+            ref = pointsource.T_tilde(x, xs, age, E, MAT)
+        FB = w[:, None] * np.exp(-a[:, None] * (B[None, :] - xs[:, v, None]) ** 2)
+        S = FA.T @ FB                                                           # (|A|, |B|)
+        assert np.abs(S[i, j] - ref).max() <= 1e-13 * np.abs(ref).max(), face
+        checked += 1
+    assert checked == 5
