@@ -362,7 +362,12 @@ sa_status sa_get_stage_times(sa_ctx* ctx, double* ms, long long* steps);
  * each instance, unchanged).  sa_batch_create takes contexts that have a
  * patch, material and scan and are at the same step; the batch copies their
  * state at its first step and owns it from then on (read it back with
- * sa_batch_get_field); the contexts must outlive the batch.
+ * sa_batch_get_field); the contexts must outlive the batch.  Options of the
+ * batch: precision, pcg_tol, pcg_max_iter, cuda_stream, use_graph (one
+ * graph per step), hist_points_per_lane / hist_warps (pairwise sums),
+ * precond (fast diagonalization of both solves when every instance has it)
+ * and hist_mode (separable sums when every instance's faces allow them, as
+ * for one context; SA_ERR_ARG with SA_HIST_SEPARABLE otherwise).
  */
 typedef struct sa_batch sa_batch;
 sa_status sa_batch_create(sa_ctx* const* insts, int n_inst, const sa_options* o, sa_batch** out);
