@@ -367,7 +367,8 @@ sa_status sa_get_stage_times(sa_ctx* ctx, double* ms, long long* steps);
  * graph per step), hist_points_per_lane / hist_warps (pairwise sums),
  * precond (fast diagonalization of both solves when every instance has it)
  * and hist_mode (separable sums when every instance's faces allow them, as
- * for one context; SA_ERR_ARG with SA_HIST_SEPARABLE otherwise).
+ * for one context; with SA_HIST_SEPARABLE otherwise the first
+ * sa_batch_step returns SA_ERR_ARG).
  */
 typedef struct sa_batch sa_batch;
 sa_status sa_batch_create(sa_ctx* const* insts, int n_inst, const sa_options* o, sa_batch** out);
