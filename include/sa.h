@@ -230,6 +230,20 @@ sa_status sa_step(sa_ctx* ctx, double theta, double dt, int n_steps, sa_step_sta
 sa_status sa_eval_T(sa_ctx* ctx, const double* pts, int n, double* T_out, int on_device);
 
 /*
+ * Heat-loss rates at n physical points with unit normals (Section 3.1, the
+ * diagnostic q~ + q^ = -k dT/dn of the adiabatic boundary): q~ = -k n . grad T~
+ * (the history sum's gradient at t_n) and q^ = -k n . grad T^ (grad T^ =
+ * J^{-T} sum_i T^_i grad_xi R_i at the inverted point).  On an adiabatic
+ * face the exact solution has q~ + q^ = 0.
+ *   pts, nrm  n*3 doubles each (nrm: unit outward normals), host or device
+ *   q_tilde, q_hat  n doubles each, same memory space; NaN outside the patch
+ * FP64, or FP32 history sums in an SA_MIXED context.  Synchronous.
+ * Errors: SA_ERR_ARG, SA_ERR_STATE, SA_ERR_CUDA.
+ */
+sa_status sa_eval_flux(sa_ctx* ctx, const double* pts, const double* nrm, int n, double* q_tilde,
+                       double* q_hat, int on_device);
+
+/*
  * Allocation-free variant of sa_eval_T (this entry point has no counterpart
  * in the paper; it exists for callers that cannot allocate device memory).
  * Some callers must not call cudaMalloc/cudaFree while they run: a

@@ -165,3 +165,25 @@ class Model:
         That = np.array([np.dot(self.geom.local_eval(xi)[1],
                                 self.T_hat[self.geom.local_eval(xi)[0]]) for xi in xi_pts])
         return x, self.T_tilde_at(x, self.n) + That
+
+    def eval_flux(self, xi_pts, nrm):
+        """Heat-loss rates at parametric points xi (P,3) with unit normals nrm
+        (P,3), current step (Section 3.1): q~ = -k n . grad T~ and
+        q^ = -k n . grad T^, grad T^ = sum_a T^_a grad_x R_a with
+        grad_x R_a = J^{-T} grad_xi R_a.  Returns x, q~, q^."""
+        xi_pts = np.atleast_2d(xi_pts)
+        nrm = np.atleast_2d(nrm)
+        x, qh = [], []
+        for xi, nv in zip(xi_pts, nrm):
+            dofs, R, dR, xp, J = self.geom.local_eval(xi)
+            gradR = np.linalg.solve(J.T, dR.T).T
+            qh.append(-self.mat.k * np.dot(nv, gradR.T @ self.T_hat[dofs]))
+            x.append(xp)
+        x = np.array(x)
+        K = self.n_active(self.n)
+        if K == 0:
+            qt = np.zeros(len(x))
+        else:
+            qt = -self.mat.k * pointsource.dTdn_tilde(x, nrm, self.xs[:K], self.source_ages(self.n),
+                                                       self.E, self.mat, self.s_img)
+        return x, qt, np.array(qh)

@@ -73,6 +73,7 @@ def _load():
         "sa_step": (I, [P, D, D, I, C.POINTER(sa_step_stats)]),
         "sa_eval_T": (I, [P, P, I, P, I]),
         "sa_eval_T_noalloc": (I, [P, P, I, P]),
+        "sa_eval_flux": (I, [P, P, P, I, P, P, I]),
         "sa_get_sizes": (I, [P, C.POINTER(sa_sizes)]),
         "sa_get_field": (I, [P, I, P, LL, I]),
         "sa_get_matrix_nnz": (I, [P, C.POINTER(LL)]),
@@ -208,6 +209,19 @@ class Context:
         o = np.empty(p.shape[0])
         _check(self.ptr, lib.sa_eval_T(self.ptr, _ptr(p), int(p.shape[0]), _ptr(o), 0))
         return o
+
+    def eval_flux(self, pts, nrm):
+        """Heat-loss rates (q~, q^) = (-k n . grad T~, -k n . grad T^) at host
+        points with unit normals."""
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        nv = np.ascontiguousarray(nrm, dtype=np.float64).reshape(-1, 3)
+        if nv.shape != p.shape:
+            raise ValueError("pts and nrm differ in shape")
+        qt = np.empty(p.shape[0])
+        qh = np.empty(p.shape[0])
+        _check(self.ptr, lib.sa_eval_flux(self.ptr, _ptr(p), _ptr(nv), int(p.shape[0]), _ptr(qt),
+                                          _ptr(qh), 0))
+        return qt, qh
 
     # ---- read-back --------------------------------------------------------------
     def sizes(self) -> sa_sizes:

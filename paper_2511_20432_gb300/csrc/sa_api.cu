@@ -1631,15 +1631,19 @@ sa_status sa_set_state(sa_ctx* c, long long n, const double* T_hat, const double
     return SA_OK;
 }
 
-sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_device) {
+// T (nrm null) or the heat-loss rates q~ (into out) and q^ (into out2) at
+// n points.
+static sa_status eval_points(sa_ctx* c, const double* pts, const double* nrm, int n, double* out,
+                             double* out2, int on_device) {
     sa_status st = check_usable(c);
     if (st) return st;
-    if (n < 0 || (n > 0 && (!pts || !T_out))) return sa_fail(c, SA_ERR_ARG, "bad argument");
+    if (n < 0 || (n > 0 && (!pts || !out || (nrm && !out2))))
+        return sa_fail(c, SA_ERR_ARG, "bad argument");
     if (!c->has_patch || !c->has_material) return sa_fail(c, SA_ERR_STATE, "needs patch and material");
     if (n == 0) return SA_OK;
     if ((st = init_state_if_needed(c))) return st;
     cudaStream_t s = c->stream;
-    // mixed contexts: the centre search and the source sum in FP32 (the
+    // mixed contexts: the centre search and the source sums in FP32 (the
     // source coefficients in the step's FP32 tables, which the next step
     // rewrites)
     const bool mixed = c->opt.precision == SA_MIXED;
@@ -1664,26 +1668,50 @@ sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_d
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "eval prologue");
         n_active = (int)std::min<long long>(c->n_step, c->n_src);
     }
+    const int nout = nrm ? 2 : 1;
     const double* dpts = pts;
-    double* dout = T_out;
+    const double* dnrm = nrm;
+    double* dout = out;
+    double* dout2 = out2;
     if (!on_device) {
-        if (c->eval_out.n < (size_t)n) {   // grown on demand, kept between calls
-            SA_ALLOC(c, c->eval_pts, (size_t)3 * n);
-            SA_ALLOC(c, c->eval_out, (size_t)n);
+        if (c->eval_out.n < (size_t)nout * n || c->eval_pts.n < (size_t)6 * n) {
+            // grown on demand, kept between calls
+            SA_ALLOC(c, c->eval_pts, (size_t)6 * n);
+            SA_ALLOC(c, c->eval_out, (size_t)2 * n);
         }
         SA_CUDA(c, cudaMemcpyAsync(c->eval_pts.p, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
         dpts = c->eval_pts.p;
+        if (nrm) {
+            SA_CUDA(c, cudaMemcpyAsync(c->eval_pts.p + 3 * (size_t)n, nrm, sizeof(double) * 3 * n,
+                                       cudaMemcpyHostToDevice, s));
+            dnrm = c->eval_pts.p + 3 * (size_t)n;
+        }
         dout = c->eval_out.p;
+        dout2 = c->eval_out.p + n;
     }
+    EvalFlux flux{dnrm, c->evF.p, mixed ? c->src32F.p : nullptr, c->k, dout2};
     cudaError_t e = launch_eval_points(c->dp, dpts, n, c->ecent.p, c->dperm.p, c->That.p,
                                        c->evT.p, n_active, c->x_ref, c->y_ref, c->z_top,
                                        c->length_scale, dout, s, mixed ? c->ecent32.p : nullptr,
-                                       mixed ? c->src32T.p : nullptr);
+                                       mixed ? c->src32T.p : nullptr, nrm ? &flux : nullptr);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "eval");
-    if (!on_device)
-        SA_CUDA(c, cudaMemcpyAsync(T_out, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (!on_device) {
+        SA_CUDA(c, cudaMemcpyAsync(out, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (nrm)
+            SA_CUDA(c, cudaMemcpyAsync(out2, dout2, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
     SA_CUDA(c, cudaStreamSynchronize(s));
     return SA_OK;
+}
+
+sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_device) {
+    return eval_points(c, pts, nullptr, n, T_out, nullptr, on_device);
+}
+
+sa_status sa_eval_flux(sa_ctx* c, const double* pts, const double* nrm, int n, double* q_tilde,
+                       double* q_hat, int on_device) {
+    if (!nrm && n > 0) return c ? sa_fail(c, SA_ERR_ARG, "nrm is NULL") : SA_ERR_ARG;
+    return eval_points(c, pts, nrm, n, q_tilde, q_hat, on_device);
 }
 
 }  // extern "C"

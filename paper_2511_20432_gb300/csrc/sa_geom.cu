@@ -517,6 +517,13 @@ struct EvalArgs {
     int n_active;
     double x_ref, y_ref, z_top, scale;
     double* T_out;
+    // heat-loss rates instead of T (nrm non-null): q~ = -k n . grad T~ into
+    // T_out, q^ = -k n . grad T^ into q_hat; the sources' (.., g) tables
+    const double* nrm;
+    const double4* s64F;
+    const float4* s32F;
+    double k;
+    double* q_hat;
 };
 
 constexpr int kEvalThreads = 128;
@@ -640,7 +647,86 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
                         }
             s_That = That;
             s_ok = ok;
+            if (ok && a.nrm) {
+                // grad T^ = J^{-T} sum_a T^_a grad_xi R_a (quotient rule)
+                double Wv = 0.0, dW[3] = {0.0, 0.0, 0.0};
+                for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                    for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                        for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                            const double w = dp.cw[nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                             b.s[1] - dp.p[1] + a1,
+                                                             b.s[2] - dp.p[2] + a2)].w;
+                            Wv += w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
+                            dW[0] += w * b.dN[0][a0] * b.N[1][a1] * b.N[2][a2];
+                            dW[1] += w * b.N[0][a0] * b.dN[1][a1] * b.N[2][a2];
+                            dW[2] += w * b.N[0][a0] * b.N[1][a1] * b.dN[2][a2];
+                        }
+                double gxi[3] = {0.0, 0.0, 0.0};
+                for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                    for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                        for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                            const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                      b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
+                            const double w = dp.cw[nat].w;
+                            const double Rv = w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / Wv;
+                            const double dd[3] = {w * b.dN[0][a0] * b.N[1][a1] * b.N[2][a2],
+                                                  w * b.N[0][a0] * b.dN[1][a1] * b.N[2][a2],
+                                                  w * b.N[0][a0] * b.N[1][a1] * b.dN[2][a2]};
+                            const double Ta = a.That[a.perm[nat]];
+                            for (int d = 0; d < 3; ++d) gxi[d] += Ta * (dd[d] - Rv * dW[d]) / Wv;
+                        }
+                // J^T g = gxi (Cramer)
+                double JT[3][3];
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) JT[r][c] = J[c][r];
+                const double det = det3(JT);
+                double g[3];
+                for (int c = 0; c < 3; ++c) {
+                    double Jc[3][3];
+                    for (int r = 0; r < 3; ++r)
+                        for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? gxi[r] : JT[r][k];
+                    g[c] = det3(Jc) / det;
+                }
+                const double* nv = a.nrm + 3 * t;
+                s_That = -a.k * (nv[0] * g[0] + nv[1] * g[1] + nv[2] * g[2]);
+            }
         }
+    }
+    if (a.nrm) {
+        // q~ = -k dT~/dn, dT~/dn = sum -g exp(-a R^2) n . (x - x_I)
+        const double* nv = a.nrm + 3 * t;
+        const double px = xs[0] - a.x_ref, py = xs[1] - a.y_ref, dz = xs[2] - a.z_top;
+        double Tt = 0.0;
+        if (a.s32F) {
+            const float fx = (float)px, fy = (float)py, fz2 = (float)(dz * dz);
+            const float nx = (float)nv[0], ny = (float)nv[1], nzdz = (float)(nv[2] * dz);
+            float acc = 0.0f;
+            for (int j = threadIdx.x; j < a.n_active; j += kEvalThreads) {
+                const float4 sv = a.s32F[j];
+                const float dx = fx - sv.x, dy = fy - sv.y;
+                const float e = eval_ex2(fmaf(sv.z, fmaf(dx, dx, fmaf(dy, dy, fz2)), sv.w));
+                acc = fmaf(e, fmaf(nx, dx, fmaf(ny, dy, nzdz)), acc);
+            }
+            Tt = (double)acc;
+        } else {
+            for (int j = threadIdx.x; j < a.n_active; j += kEvalThreads) {
+                const double4 sv = a.s64F[j];
+                const double dx = px - sv.x, dy = py - sv.y;
+                Tt += sv.w * exp(-sv.z * (dx * dx + dy * dy + dz * dz)) *
+                      (nv[0] * dx + nv[1] * dy + nv[2] * dz);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Tt += __shfl_xor_sync(0xffffffffu, Tt, o);
+        if (lane == 0) s_T[w] = Tt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int k = 0; k < kEvalThreads / 32; ++k) tot += s_T[k];
+            a.T_out[t] = s_ok ? a.k * tot : nan("");      // -k * (-sum)
+            a.q_hat[t] = s_ok ? s_That : nan("");
+        }
+        return;
     }
     // the sources: FP32 terms (each thread sums its ~n / 128 in FP32) or FP64
     const double px = xs[0] - a.x_ref, py = xs[1] - a.y_ref, dz = xs[2] - a.z_top;
@@ -837,10 +923,12 @@ cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, con
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,
                                double scale, double* T_out, cudaStream_t s, const float* ecent32,
-                               const float4* s32T) {
+                               const float4* s32T, const EvalFlux* flux) {
     if (n == 0) return cudaSuccess;
     EvalArgs a{dp, pts, n, ecent, ecent32, perm, That, s64T, s32T, n_active, x_ref, y_ref,
-               z_top, scale, T_out};
+               z_top, scale, T_out,
+               flux ? flux->nrm : nullptr, flux ? flux->s64F : nullptr,
+               flux ? flux->s32F : nullptr, flux ? flux->k : 0.0, flux ? flux->q_hat : nullptr};
     k_eval<<<(unsigned)n, kEvalThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

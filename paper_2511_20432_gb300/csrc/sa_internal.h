@@ -515,11 +515,21 @@ cudaError_t launch_sep_batch(const SepPlan& P, int precision, DevStatus* st, con
 // T = T~ + T^ at points; ecent32 (FP32 copy of the element centres) and
 // s32T (FP32 source coefficients) are optional: with them the search and the
 // source sum run in FP32 (mixed contexts).
+// flux != null: the heat-loss rates -k n . grad T~ (into T_out) and
+// -k n . grad T^ (into flux->q_hat) at the points with unit normals nrm.
+struct EvalFlux {
+    const double* nrm;
+    const double4* s64F;
+    const float4* s32F;
+    double k;
+    double* q_hat;
+};
 cudaError_t launch_eval_points(const DevPatch& dp, const double* pts, int n, const double* ecent,
                                const int* perm, const double* That, const double4* s64T,
                                int n_active, double x_ref, double y_ref, double z_top,
                                double scale, double* T_out, cudaStream_t s,
-                               const float* ecent32 = nullptr, const float4* s32T = nullptr);
+                               const float* ecent32 = nullptr, const float4* s32T = nullptr,
+                               const EvalFlux* flux = nullptr);
 
 // sa_solve.cu
 // With the bottom rows of the gather, optionally the bottom projection's

@@ -21,6 +21,7 @@ from oracle.solver import Model, ThetaSolver
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 MAT = W.MAT_DEFAULT
+MAT_TI = W.MAT_TI64
 ALPHA = MAT.k / (MAT.rho * MAT.cp)
 
 
@@ -693,3 +694,81 @@ def test_R12_separable_sums_equal_pairwise_on_box_faces():
         assert np.abs(S[i, j] - ref).max() <= 1e-13 * np.abs(ref).max(), face
         checked += 1
     assert checked == 5
+
+
+# ---------------------------------------------------------------------------
+# Heat-loss rates (Section 3.1, q~ + q^ = -k dT/dn): the oracle's q~ + q^
+# equals -k times the central difference of its own T = T~ + T^ along the
+# normal (points found by a Newton inversion with a finite-difference
+# Jacobian, independent of the oracle's J).
+# ---------------------------------------------------------------------------
+def _invert_map(geom, x, xi0):
+    xi = np.array(xi0, dtype=np.float64)
+    for _ in range(60):
+        f = geom.point(xi) - x
+        if np.linalg.norm(f) < 1e-17:
+            break
+        J = np.empty((3, 3))
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = 1e-7
+            J[:, d] = (geom.point(xi + e) - geom.point(xi - e)) / 2e-7
+        xi = xi - np.linalg.solve(J, f)
+    assert np.linalg.norm(geom.point(xi) - x) < 1e-14
+    return xi
+
+
+def test_heat_loss_rate_is_minus_k_times_the_normal_derivative():
+    wl = W.quarter_cylinder_single_source((4, 2, 2), n_steps=6)
+    m = Model(wl)
+    for _ in range(6):
+        m.step()
+    rng = np.random.default_rng(31)
+    xi = np.column_stack([rng.choice([rng.uniform(0.1, 0.4), rng.uniform(0.6, 0.9)], 6),
+                          rng.uniform(0.15, 0.85, 6), rng.uniform(0.5, 0.95, 6)])
+    nrm = rng.normal(size=(6, 3))
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    x, qt, qh = m.eval_flux(xi, nrm)
+    h = 1e-7
+    q_fd = []
+    for k in range(len(x)):
+        xp = _invert_map(m.geom, x[k] + h * nrm[k], xi[k])
+        xm = _invert_map(m.geom, x[k] - h * nrm[k], xi[k])
+        Tp, Tm = m.eval_T(xp)[1][0], m.eval_T(xm)[1][0]
+        q_fd.append(-MAT_TI.k * (Tp - Tm) / (2 * h))
+    q_fd = np.array(q_fd)
+    assert np.abs(qt + qh - q_fd).max() <= 1e-5 * np.abs(q_fd).max(), (qt + qh, q_fd)
+    assert np.abs(qh).max() > 0 and np.abs(qt).max() > 0
+
+
+# ---------------------------------------------------------------------------
+# Table 3: q~ on the top arc depends on the point sources alone (position,
+# energy, ages at t = 1.9e-4 s, image factor), so every column of the table
+# fixes int |q~| ds = net / ratio to within the rounding of its printed
+# figures.  The oracle's int |q~| ds must lie in all five intervals.
+# ---------------------------------------------------------------------------
+def _half_unit(s):
+    mant, _, ex = s.lower().partition("e")
+    dec = len(mant.split(".")[1]) if "." in mant else 0
+    return 0.5 * 10.0 ** (-dec) * 10.0 ** int(ex or 0)
+
+
+def test_table3_integrated_analytical_heat_loss():
+    lo, hi = 0.0, np.inf
+    for line in open(os.path.join(GOLDEN, "table3_heat_loss.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        _, _, net_s, pct_s = line.split()
+        net, dn = float(net_s), _half_unit(net_s)
+        r, dr = float(pct_s) / 100, _half_unit(pct_s) / 100
+        lo, hi = max(lo, (net - dn) / (r + dr)), min(hi, (net + dn) / (r - dr))
+    assert lo < hi
+    wl = W.quarter_cylinder_single_source((4, 2, 2), n_steps=19)
+    m = Model(wl, build_solver=False)
+    n = 19
+    K = m.n_active(n)
+    _, pts, nrm, ds = W.quarter_cylinder_arc_points(2001)
+    qt = -wl.material.k * pointsource.dTdn_tilde(pts, nrm, m.xs[:K], m.source_ages(n), m.E,
+                                                  wl.material, m.s_img)
+    ana = float(np.sum(np.abs(qt) * ds))
+    assert lo <= ana <= hi, (lo, ana, hi)

@@ -262,6 +262,40 @@ def test_separable_matches_pairwise_full_size(sa):
     assert np.abs(out[sa.SA_MIXED, 2][2] - ref[2]).max() <= TOL_MIXED_ABS
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_heat_loss_rates_match_oracle(sa, prec):
+    """Section 3.1 diagnostic on the quarter-cylinder part with the single
+    source: q~ = -k n . grad T~ and q^ = -k n . grad T^ at points of the top
+    arc (outward normals) and at interior points (random unit normals)
+    against the oracle."""
+    wl = W.quarter_cylinder_single_source((4, 2, 2), n_steps=8)
+    m = _oracle(wl)
+    for _ in range(8):
+        m.step()
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    ctx = gpu_context(wl, p, pcg_tol=1e-15 if p == sa.SA_FP64 else 1e-10)
+    ctx.step(wl.theta, wl.dt, 8)
+    u = np.linspace(0.02, 0.98, 9)
+    xi_arc = np.column_stack([u, np.zeros_like(u), np.ones_like(u)])
+    rng = np.random.default_rng(5)
+    xi_in = rng.uniform(0.1, 0.9, (6, 3))
+    xi = np.vstack([xi_arc, xi_in])
+    x = np.array([m.geom.point(v) for v in xi])
+    n_arc = np.column_stack([2e-3 - x[:9, 0], -x[:9, 1], np.zeros(9)])
+    n_arc /= np.linalg.norm(n_arc, axis=1)[:, None]
+    n_in = rng.normal(size=(6, 3))
+    n_in /= np.linalg.norm(n_in, axis=1)[:, None]
+    nrm = np.vstack([n_arc, n_in])
+    _, qt_ref, qh_ref = m.eval_flux(xi, nrm)
+    qt, qh = ctx.eval_flux(x, nrm)
+    et = np.abs(qt - qt_ref).max() / np.abs(qt_ref).max()
+    eh = np.abs(qh - qh_ref).max() / np.abs(qh_ref).max()
+    if p == sa.SA_FP64:
+        assert et <= 1e-12 and eh <= 1e-9, (et, eh)
+    else:   # FP32 history sums; q^ is the gradient of the mixed T^
+        assert et <= TOL_MIXED_REL and eh <= 1e-3, (et, eh)
+
+
 def test_bounded_waits_give_up(sa):
     """Failure detection without a GPU fault: a grid-barrier wait and an
     mbarrier wait that nothing completes give up within their limits (2 s,

@@ -430,3 +430,90 @@ def quarter_cylinder_part(n_refine=1) -> Patch:
     knots = [np.array([0, 0, 0, 0.5, 0.5, 1, 1, 1.0]), np.array([0, 0, 1, 1.0]),
              np.array([0, 0, 1, 1.0])]
     return Patch(degree=(2, 1, 1), knots=knots, ctrl=ctrl * 1e-3, weights=w)
+
+
+def _refine_direction(U, Pw, axis, p, new_knots):
+    """Boehm insertion of new_knots along one parametric direction of a
+    homogeneous control volume Pw (n2, n1, n0, 4); axis 0 = xi (last array
+    axis 2), 1 = eta, 2 = zeta."""
+    arr_axis = 2 - axis
+    A = np.moveaxis(Pw, arr_axis, -2)            # (..., n_axis, 4)
+    shp = A.shape
+    lines = A.reshape(-1, shp[-2], 4)
+    U_out = U
+    out = []
+    for line in lines:
+        Uc, Q = U, line
+        for u in new_knots:
+            Uc, Q = _insert_knot(Uc, Q, p, u)
+        out.append(Q)
+        U_out = Uc
+    A2 = np.array(out).reshape(shp[:-2] + (out[0].shape[0], 4))
+    return U_out, np.moveaxis(A2, -2, arr_axis)
+
+
+def _elevate_linear_direction(Pw, axis):
+    """Degree 1 -> 2 along a direction with one span: (P0, P1) -> (P0, (P0 +
+    P1)/2, P1) in homogeneous coordinates (the same map)."""
+    arr_axis = 2 - axis
+    A = np.moveaxis(Pw, arr_axis, 0)
+    assert A.shape[0] == 2
+    B = np.stack([A[0], 0.5 * (A[0] + A[1]), A[1]])
+    return np.moveaxis(B, 0, arr_axis)
+
+
+def quarter_cylinder_refined(n_el=(16, 8, 8)) -> Patch:
+    """The quarter-cylinder part of Section 3.1 as degree 2 in every
+    direction (the linear directions elevated) with n_el elements: the two
+    xi spans split into n_el[0] / 2 each, eta and zeta into n_el[1] and
+    n_el[2]; control-point operations only (the same geometry)."""
+    base = quarter_cylinder_part()
+    w = base.weights
+    Pw = np.concatenate([base.ctrl * w[..., None], w[..., None]], axis=-1)   # (2, 2, 5, 4)
+    Pw = _elevate_linear_direction(Pw, 1)
+    Pw = _elevate_linear_direction(Pw, 2)
+    U0 = base.knots[0]
+    U12 = np.array([0, 0, 0, 1, 1, 1.0])
+    assert n_el[0] % 2 == 0
+    m0 = n_el[0] // 2
+    ins0 = [(s + t / m0) / 2.0 for s in range(2) for t in range(1, m0)]
+    U0, Pw = _refine_direction(U0, Pw, 0, 2, ins0)
+    U1, Pw = _refine_direction(U12, Pw, 1, 2, [t / n_el[1] for t in range(1, n_el[1])])
+    U2, Pw = _refine_direction(U12, Pw, 2, 2, [t / n_el[2] for t in range(1, n_el[2])])
+    wts = Pw[..., 3]
+    ctrl = Pw[..., :3] / wts[..., None]
+    return Patch(degree=(2, 2, 2), knots=[U0, U1, U2], ctrl=np.ascontiguousarray(ctrl),
+                 weights=np.ascontiguousarray(wts))
+
+
+def quarter_cylinder_single_source(n_el=(16, 8, 8), n_steps=19, theta=0.5) -> Workload:
+    """Section 3.1 single heat source: one pulse of dt = 1e-5 s, P = 82.5 W,
+    A = 0.77 (E = 6.35e-4 J), r = 20 um, on the top surface 100 um from the
+    arc where the line from the cylinder's axis makes pi/4 with the x2 axis
+    (reading: the figure's origin is the cylinder's axis, x = 2 mm, y = 0 in
+    the Table 2 coordinates); Ti-6Al-4V; observed at t = 1.9e-4 s (19
+    steps)."""
+    patch = quarter_cylinder_refined(n_el)
+    rc = 1.1e-3
+    c = np.array([2e-3, 0.0])
+    xy = c + rc * np.array([-np.sin(np.pi / 4), np.cos(np.pi / 4)])
+    p = (xy[0], xy[1], 2e-3)
+    scan = Scan(path=np.array([p, p], dtype=np.float64), seg_on=np.array([1], dtype=np.uint8),
+                power=82.5, absorptivity=0.77, speed=0.5, spot_radius=20e-6)
+    return Workload("quarter_cylinder_single_source", patch, MAT_TI64, scan, dt=1e-5,
+                    theta=theta, n_steps=n_steps, meta={"source_xy": tuple(xy)})
+
+
+def quarter_cylinder_arc_points(n, z=2e-3):
+    """Points of the top arc (radius 1 mm about x = 2 mm, y = 0) from theta =
+    0 (on the x2 direction) to pi/2, with the outward normal of the part (into
+    the removed cylinder) and the arc-length weights of the trapezoid rule."""
+    th = np.linspace(0.0, np.pi / 2, n)
+    d = np.column_stack([-np.sin(th), np.cos(th)])      # from the axis to the arc
+    xy = np.array([2e-3, 0.0]) + 1e-3 * d
+    pts = np.column_stack([xy, np.full(n, z)])
+    nrm = np.column_stack([-d, np.zeros(n)])            # out of the part: toward the axis
+    ds = np.full(n, 1e-3 * (np.pi / 2) / (n - 1))
+    ds[0] *= 0.5
+    ds[-1] *= 0.5
+    return th, pts, nrm, ds
