@@ -418,32 +418,36 @@ def batched_leg(sa, W, stream, n_inst, n_steps, rank=0, world=1, dist=None):
     return out
 
 
-def quarter_cylinder_leg(sa, W, stream, n_el=(32, 16, 16), n_arc=721):
+def quarter_cylinder_leg(sa, W, stream, meshes=((32, 16, 16), (64, 32, 32)), n_arc=721):
     """Section 3.1 single source on the quarter-cylinder part (Table 2 net,
-    degree 2, n_el elements): T^ after 19 steps (t = 1.9e-4 s), the heat-loss
-    rates q~ and q^ at n_arc points of the top arc, the integrated |q~ + q^|
-    and |q~| (trapezoid rule along the arc) and their ratio, the adiabatic
-    residual of the discretisation, in FP64 and mixed."""
+    degree 2, uniform meshes of n_el elements): T^ after 19 steps (t = 1.9e-4
+    s), the heat-loss rates q~ and q^ at n_arc points of the top arc, the
+    integrated |q~ + q^| and |q~| (trapezoid rule along the arc) and their
+    ratio, the adiabatic residual of the discretisation, in FP64 and mixed."""
     import numpy as np
     import torch
-    wl = W.quarter_cylinder_single_source(n_el, n_steps=19)
     th, pts, nrm, ds = W.quarter_cylinder_arc_points(n_arc)
-    out = {"workload": wl.name, "n_el": list(n_el), "t_s": 19 * wl.dt, "arc_points": n_arc}
-    for name, prec in (("fp64", sa.SA_FP64), ("mixed", sa.SA_MIXED)):
-        c = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1)
-        c.step(wl.theta, wl.dt, wl.n_steps)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        qt, qh = c.eval_flux(pts, nrm)
-        t_eval = time.perf_counter() - t0
-        net = float(np.sum(np.abs(qt + qh) * ds))
-        ana = float(np.sum(np.abs(qt) * ds))
-        out[name] = {"n_dof": c.sizes().n_dof, "int_abs_net_W_per_m": net,
-                     "int_abs_qtilde_W_per_m": ana, "net_over_qtilde": net / ana,
-                     "max_abs_net_W_per_m2": float(np.abs(qt + qh).max()),
-                     "max_abs_qtilde_W_per_m2": float(np.abs(qt).max()),
-                     "eval_ms": 1e3 * t_eval}
-        c.close()
+    out = {"workload": "quarter_cylinder_single_source", "t_s": 1.9e-4, "arc_points": n_arc,
+           "meshes": []}
+    for n_el in meshes:
+        wl = W.quarter_cylinder_single_source(n_el, n_steps=19)
+        row = {"n_el": list(n_el)}
+        for name, prec in (("fp64", sa.SA_FP64), ("mixed", sa.SA_MIXED)):
+            c = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1)
+            c.step(wl.theta, wl.dt, wl.n_steps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            qt, qh = c.eval_flux(pts, nrm)
+            t_eval = time.perf_counter() - t0
+            net = float(np.sum(np.abs(qt + qh) * ds))
+            ana = float(np.sum(np.abs(qt) * ds))
+            row[name] = {"n_dof": c.sizes().n_dof, "int_abs_net_W_per_m": net,
+                         "int_abs_qtilde_W_per_m": ana, "net_over_qtilde": net / ana,
+                         "max_abs_net_W_per_m2": float(np.abs(qt + qh).max()),
+                         "max_abs_qtilde_W_per_m2": float(np.abs(qt).max()),
+                         "eval_ms": 1e3 * t_eval}
+            c.close()
+        out["meshes"].append(row)
     return out
 
 
