@@ -418,34 +418,49 @@ def batched_leg(sa, W, stream, n_inst, n_steps, rank=0, world=1, dist=None):
     return out
 
 
-def quarter_cylinder_leg(sa, W, stream, meshes=((32, 16, 16), (64, 32, 32)), n_arc=721):
-    """Section 3.1 single source on the quarter-cylinder part (Table 2 net,
-    degree 2, uniform meshes of n_el elements): T^ after 19 steps (t = 1.9e-4
-    s), the heat-loss rates q~ and q^ at n_arc points of the top arc, the
+def quarter_cylinder_leg(sa, W, stream, case="single_source",
+                         meshes=((32, 16, 16), (64, 32, 32)), n_arc=721):
+    """The quarter-cylinder part (Table 2 net, degree 2, uniform meshes of
+    n_el elements) under the Section 3.1 single source (observed after 19
+    steps, t = 1.9e-4 s) or the Section 3.2 contour scan (t = 2e-3 and 3e-3
+    s): the heat-loss rates q~ and q^ at n_arc points of the top arc, the
     integrated |q~ + q^| and |q~| (trapezoid rule along the arc) and their
-    ratio, the adiabatic residual of the discretisation, in FP64 and mixed."""
+    ratio, the adiabatic residual of the discretisation, in FP64 and mixed;
+    steps/s of the run (graph replay)."""
     import numpy as np
     import torch
+    if case == "single_source":
+        make, at = W.quarter_cylinder_single_source, (19,)
+    else:
+        make, at = W.quarter_cylinder_contour, (200, 300)
     th, pts, nrm, ds = W.quarter_cylinder_arc_points(n_arc)
-    out = {"workload": "quarter_cylinder_single_source", "t_s": 1.9e-4, "arc_points": n_arc,
-           "meshes": []}
+    out = {"workload": "quarter_cylinder_" + case, "arc_points": n_arc, "meshes": []}
     for n_el in meshes:
-        wl = W.quarter_cylinder_single_source(n_el, n_steps=19)
+        wl = make(n_el, n_steps=at[-1])
         row = {"n_el": list(n_el)}
         for name, prec in (("fp64", sa.SA_FP64), ("mixed", sa.SA_MIXED)):
             c = sa.context_from_workload(wl, precision=prec, cuda_stream=stream, use_graph=1)
-            c.step(wl.theta, wl.dt, wl.n_steps)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            qt, qh = c.eval_flux(pts, nrm)
-            t_eval = time.perf_counter() - t0
-            net = float(np.sum(np.abs(qt + qh) * ds))
-            ana = float(np.sum(np.abs(qt) * ds))
-            row[name] = {"n_dof": c.sizes().n_dof, "int_abs_net_W_per_m": net,
-                         "int_abs_qtilde_W_per_m": ana, "net_over_qtilde": net / ana,
-                         "max_abs_net_W_per_m2": float(np.abs(qt + qh).max()),
-                         "max_abs_qtilde_W_per_m2": float(np.abs(qt).max()),
-                         "eval_ms": 1e3 * t_eval}
+            res = {"n_dof": c.sizes().n_dof, "t": []}
+            done, t_steps = 0, 0.0
+            for n in at:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c.step(wl.theta, wl.dt, n - done)
+                torch.cuda.synchronize()
+                t_steps += time.perf_counter() - t0
+                done = n
+                t0 = time.perf_counter()
+                qt, qh = c.eval_flux(pts, nrm)
+                t_eval = time.perf_counter() - t0
+                net = float(np.sum(np.abs(qt + qh) * ds))
+                ana = float(np.sum(np.abs(qt) * ds))
+                res["t"].append({"t_s": n * wl.dt, "int_abs_net_W_per_m": net,
+                                 "int_abs_qtilde_W_per_m": ana, "net_over_qtilde": net / ana,
+                                 "max_abs_net_W_per_m2": float(np.abs(qt + qh).max()),
+                                 "max_abs_qtilde_W_per_m2": float(np.abs(qt).max()),
+                                 "eval_ms": 1e3 * t_eval})
+            res["steps_per_s"] = done / t_steps
+            row[name] = res
             c.close()
         out["meshes"].append(row)
     return out
@@ -602,6 +617,7 @@ def run_ours(args):
 
     # ---- the quarter-cylinder part: heat-loss rates along the top arc ------------
     qcyl = quarter_cylinder_leg(sa, W, stream) if world == 1 else None
+    qcon = quarter_cylinder_leg(sa, W, stream, "contour") if world == 1 else None
 
     # ---- learned warm start (bounded: a few thousand training pairs) -------------
     learned = None
@@ -697,6 +713,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": N_MONITOR * 8 + 96},
         "plate_with_hole": plate,
         "quarter_cylinder_single_source": qcyl,
+        "quarter_cylinder_contour": qcon,
         "batched_256": batched,
         "learned_warm_start": learned,
         "gpu_launches": launches_per_step * K,

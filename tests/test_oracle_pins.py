@@ -772,3 +772,34 @@ def test_table3_integrated_analytical_heat_loss():
                                                   wl.material, m.s_img)
     ana = float(np.sum(np.abs(qt) * ds))
     assert lo <= ana <= hi, (lo, ana, hi)
+
+
+# ---------------------------------------------------------------------------
+# Table 4: the same argument for the contour scan at t = 2e-3 s and 3e-3 s
+# (both columns at one time fix int |q~| ds).  It separates the readings of
+# the scan path: the arc part of the 100 um offset contour passes at both
+# times; the whole 1.1 mm quarter circle started at the x2 face does not
+# (0.35 % low at 2e-3 s).
+# ---------------------------------------------------------------------------
+def test_table4_integrated_analytical_heat_loss():
+    win = {}
+    for line in open(os.path.join(GOLDEN, "table4_heat_loss.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        t_s, _, _, net_s, pct_s = line.split()
+        net, dn = float(net_s), _half_unit(net_s)
+        r, dr = float(pct_s) / 100, _half_unit(pct_s) / 100
+        lo, hi = win.get(t_s, (0.0, np.inf))
+        win[t_s] = (max(lo, (net - dn) / (r + dr)), min(hi, (net + dn) / (r - dr)))
+    assert len(win) == 2
+    wl = W.quarter_cylinder_contour((4, 2, 2), n_steps=300)
+    m = Model(wl, build_solver=False)
+    _, pts, nrm, ds = W.quarter_cylinder_arc_points(4001)
+    for t_s, (lo, hi) in win.items():
+        assert lo < hi
+        n = int(round(float(t_s) / wl.dt))
+        K = m.n_active(n)
+        qt = -wl.material.k * pointsource.dTdn_tilde(pts, nrm, m.xs[:K], m.source_ages(n),
+                                                      m.E, wl.material, m.s_img)
+        ana = float(np.sum(np.abs(qt) * ds))
+        assert lo <= ana <= hi, (t_s, lo, ana, hi)

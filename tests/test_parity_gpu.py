@@ -262,19 +262,24 @@ def test_separable_matches_pairwise_full_size(sa):
     assert np.abs(out[sa.SA_MIXED, 2][2] - ref[2]).max() <= TOL_MIXED_ABS
 
 
+@pytest.mark.parametrize("case", ["single_source", "contour"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_heat_loss_rates_match_oracle(sa, prec):
-    """Section 3.1 diagnostic on the quarter-cylinder part with the single
-    source: q~ = -k n . grad T~ and q^ = -k n . grad T^ at points of the top
-    arc (outward normals) and at interior points (random unit normals)
-    against the oracle."""
-    wl = W.quarter_cylinder_single_source((4, 2, 2), n_steps=8)
+def test_heat_loss_rates_match_oracle(sa, prec, case):
+    """Section 3.1 diagnostic on the quarter-cylinder part, after 8 steps of
+    the single source or 40 steps of the contour scan (40 sources): q~ = -k
+    n . grad T~ and q^ = -k n . grad T^ at points of the top arc (outward
+    normals) and at interior points (random unit normals) against the
+    oracle."""
+    if case == "single_source":
+        wl = W.quarter_cylinder_single_source((4, 2, 2), n_steps=8)
+    else:
+        wl = W.quarter_cylinder_contour((4, 2, 2), n_steps=40)
     m = _oracle(wl)
-    for _ in range(8):
+    for _ in range(wl.n_steps):
         m.step()
     p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
     ctx = gpu_context(wl, p, pcg_tol=1e-15 if p == sa.SA_FP64 else 1e-10)
-    ctx.step(wl.theta, wl.dt, 8)
+    ctx.step(wl.theta, wl.dt, wl.n_steps)
     u = np.linspace(0.02, 0.98, 9)
     xi_arc = np.column_stack([u, np.zeros_like(u), np.ones_like(u)])
     rng = np.random.default_rng(5)

@@ -504,6 +504,27 @@ def quarter_cylinder_single_source(n_el=(16, 8, 8), n_steps=19, theta=0.5) -> Wo
                     theta=theta, n_steps=n_steps, meta={"source_xy": tuple(xy)})
 
 
+def quarter_cylinder_contour(n_el=(16, 8, 8), n_steps=300, theta=0.5, n_seg=2048) -> Workload:
+    """Section 3.2 continuous scan on the quarter-cylinder part: P = 82.5 W,
+    A = 0.77, v = 0.5 m/s, r = 20 um, dt = 1e-5 s, Ti-6Al-4V, the laser
+    starting at t = 0 on the scan path offset 100 um into the part from the
+    boundary.  Reading: the path is the arc part of that offset contour, the
+    circle of radius 1.1 mm about the cylinder's axis between the points
+    where it meets the offsets of the two flat faces (angles asin(0.1/1.1)
+    and pi/2 - asin(0.1/1.1) from the x2 direction), scanned from the x2
+    side as a polyline of n_seg chords; 1.53 mm long, so the laser is still
+    on it at t = 3e-3 s (1.5 mm)."""
+    patch = quarter_cylinder_refined(n_el)
+    a0 = np.arcsin(0.1 / 1.1)
+    th = np.linspace(a0, np.pi / 2 - a0, n_seg + 1)
+    xy = np.array([2e-3, 0.0]) + 1.1e-3 * np.column_stack([-np.sin(th), np.cos(th)])
+    path = np.column_stack([xy, np.full(n_seg + 1, 2e-3)])
+    scan = Scan(path=np.ascontiguousarray(path), seg_on=np.ones(n_seg, np.uint8), power=82.5,
+                absorptivity=0.77, speed=0.5, spot_radius=20e-6)
+    return Workload("quarter_cylinder_contour", patch, MAT_TI64, scan, dt=1e-5, theta=theta,
+                    n_steps=n_steps, meta={"arc_angles": (a0, np.pi / 2 - a0)})
+
+
 def quarter_cylinder_arc_points(n, z=2e-3):
     """Points of the top arc (radius 1 mm about x = 2 mm, y = 0) from theta =
     0 (on the x2 direction) to pi/2, with the outward normal of the part (into
