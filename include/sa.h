@@ -221,8 +221,11 @@ sa_status sa_step(sa_ctx* ctx, double theta, double dt, int n_steps, sa_step_sta
  * Reconstruction T = T~ + T^ (Section 2.4) at n physical points at the
  * current step t_n = n dt: point inversion x -> xi by Newton's method on the
  * NURBS map, sum_i R_i(xi) T^_i, plus the history sum at t_n (FP64; in an
- * SA_MIXED context the history sum is formed in FP32 like the step's, and
- * the nearest-element search that seeds Newton too).
+ * SA_MIXED context the history sum is formed in FP32 like the step's, and so
+ * are the nearest-element search that seeds Newton and the point inversion
+ * with its basis values: Newton in FP32 to 1e-6 of the patch size, or in
+ * FP64 for a point where FP32 does not settle).  In FP64 contexts Newton
+ * starts in FP32 and ends in FP64 at 1e-13 of the patch size.
  *   pts    n*3 doubles, host (on_device = 0) or device (on_device = 1)
  *   T_out  n doubles, same memory space; a point outside the patch gets NaN
  * Synchronous.  Errors: SA_ERR_ARG, SA_ERR_STATE, SA_ERR_CUDA.

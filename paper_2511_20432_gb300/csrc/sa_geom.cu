@@ -486,6 +486,117 @@ __device__ void eval_at_warp(const DevPatch& dp, const double xi[3], Basis1D& b,
     }
 }
 
+// FP32 counterparts for the first Newton phase of the point inversion (FP64
+// arithmetic is slow on this part): knots staged as FP32 in shared memory,
+// control points relative to the patch's reference point.
+constexpr int kEvalKnots = 512;   // knots per direction that the staging holds
+
+struct BasisF {
+    float N[3][SA_MAX_DEGREE + 1];
+    float dN[3][SA_MAX_DEGREE + 1];
+    int s[3];
+};
+
+__device__ int find_span_f(const float* U, int p, int n, float u) {
+    if (u >= U[n]) {
+        int s = n - 1;
+        while (s > p && U[s] == U[s + 1]) --s;
+        return s;
+    }
+    if (u <= U[p]) return p;
+    int lo = p, hi = n;                 // U[lo] <= u < U[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (U[mid] <= u)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// The recursion of bspline_1d in FP32 (the span is non-empty in FP32, so no
+// denominator vanishes).
+__device__ void bspline_1d_f(const float* U, int p, int s, float u, float* N, float* dN) {
+    float cur[SA_MAX_DEGREE + 1], prev[SA_MAX_DEGREE + 1];
+    cur[0] = 1.0f;
+    for (int q = 1; q <= p; ++q) {
+        for (int r = 0; r < q; ++r) prev[r] = cur[r];
+        for (int r = 0; r <= q; ++r) {
+            const int i = s - q + r;
+            float v = 0.0f;
+            if (r > 0) v += (u - U[i]) / (U[i + q] - U[i]) * prev[r - 1];
+            if (r < q) v += (U[i + q + 1] - u) / (U[i + q + 1] - U[i + 1]) * prev[r];
+            cur[r] = v;
+        }
+    }
+    for (int r = 0; r <= p; ++r) {
+        N[r] = cur[r];
+        if (p == 0) {
+            dN[r] = 0.0f;
+            continue;
+        }
+        const int i = s - p + r;
+        float d = 0.0f;
+        if (r > 0) d += p / (U[i + p] - U[i]) * prev[r - 1];
+        if (r < p) d -= p / (U[i + p + 1] - U[i + 1]) * prev[r];
+        dN[r] = d;
+    }
+}
+
+__device__ inline float det3f(const float J[3][3]) {
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// eval_at_warp in FP32: x relative to ref; sU holds the three knot vectors
+// at stride kEvalKnots.
+__device__ void eval_at_warp_f(const DevPatch& dp, const float* sU, const double ref[3],
+                               const float xi[3], BasisF& b, float x[3], float J[3][3],
+                               float& Wsum) {
+    const int lane = threadIdx.x & 31;
+    for (int d = 0; d < 3; ++d) {
+        b.s[d] = find_span_f(sU + d * kEvalKnots, dp.p[d], dp.n[d], xi[d]);
+        bspline_1d_f(sU + d * kEvalKnots, dp.p[d], b.s[d], xi[d], b.N[d], b.dN[d]);
+    }
+    const int n0 = dp.p[0] + 1, n1 = dp.p[1] + 1, nb = n0 * n1 * (dp.p[2] + 1);
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = 0.0f;
+    for (int l = lane; l < nb; l += 32) {
+        const int a0 = l % n0, a1 = (l / n0) % n1, a2 = l / (n0 * n1);
+        const double4 c = dp.cw[nat_index(dp, b.s[0] - dp.p[0] + a0, b.s[1] - dp.p[1] + a1,
+                                          b.s[2] - dp.p[2] + a2)];
+        const float cw = (float)c.w;
+        const float P[3] = {(float)(c.x - ref[0]), (float)(c.y - ref[1]), (float)(c.z - ref[2])};
+        const float Nv = b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
+        const float dd[3] = {b.dN[0][a0] * b.N[1][a1] * b.N[2][a2],
+                             b.N[0][a0] * b.dN[1][a1] * b.N[2][a2],
+                             b.N[0][a0] * b.N[1][a1] * b.dN[2][a2]};
+        const float wN = cw * Nv;
+        v[0] += wN;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[1 + d] += cw * dd[d];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            v[4 + cc] += wN * P[cc];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[7 + 3 * cc + d] += cw * dd[d] * P[cc];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    Wsum = v[0];
+    const float iW = 1.0f / Wsum;
+    for (int cc = 0; cc < 3; ++cc) {
+        x[cc] = v[4 + cc] * iW;
+        for (int d = 0; d < 3; ++d) J[cc][d] = (v[7 + 3 * cc + d] - x[cc] * v[1 + d]) * iW;
+    }
+}
+
 __global__ void k_elem_centers(DevPatch dp, double* ecent) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
@@ -536,8 +647,12 @@ __device__ __forceinline__ float eval_ex2(float x) {
 
 // One block per query point: the threads search the element centres (in
 // FP32 when a copy is given: the centre only seeds Newton) and sum the
-// sources; warp 0 runs the Newton iteration (the basis terms over its lanes).  Reductions in a fixed order
-// (ties of the search: lowest element index).
+// sources; warp 0 runs the Newton iteration (the basis terms over its
+// lanes), first in FP32 to 1e-6 of the patch size, then in FP64 to 1e-13 of
+// it.  With FP32 source tables (mixed contexts) and no flux the FP32 point
+// and its FP32 basis give T^; a point the FP32 phase does not settle goes
+// the FP64 way from the element centre.  Reductions in a fixed order (ties
+// of the search: lowest element index).
 __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
     const int t = blockIdx.x;
     if (t >= a.n) return;
@@ -550,6 +665,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const DevPatch& dp = a.dp;
     const double xs[3] = {a.pts[3 * t], a.pts[3 * t + 1], a.pts[3 * t + 2]};
+    // FP32 copies of the knot vectors (read after the search's barriers)
+    __shared__ float sU[3 * kEvalKnots];
+    const bool use32 = dp.n[0] + dp.p[0] + 1 <= kEvalKnots && dp.n[1] + dp.p[1] + 1 <= kEvalKnots &&
+                       dp.n[2] + dp.p[2] + 1 <= kEvalKnots;
+    if (use32)
+        for (int d = 0; d < 3; ++d)
+            for (int i = threadIdx.x; i < dp.n[d] + dp.p[d] + 1; i += kEvalThreads)
+                sU[d * kEvalKnots + i] = (float)dp.U[d][i];
     // initial guess: parametric centre of the element with the nearest
     // physical centre
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
@@ -614,10 +737,66 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
             lo[d] = dp.U[d][dp.p[d]];
             hi[d] = dp.U[d][dp.n[d]];
         }
+        bool ok32 = false;
+        BasisF bf;
+        float Wf = 1.0f, xf[3];
+        if (use32) {
+            const double ref[3] = {a.x_ref, a.y_ref, a.z_top};
+            const float xr[3] = {(float)(xs[0] - ref[0]), (float)(xs[1] - ref[1]),
+                                 (float)(xs[2] - ref[2])};
+            float lof[3], hif[3];
+            for (int d = 0; d < 3; ++d) {
+                xf[d] = (float)xi[d];
+                lof[d] = sU[d * kEvalKnots + dp.p[d]];
+                hif[d] = sU[d * kEvalKnots + dp.n[d]];
+            }
+            const float tol32 = 1e-6f * (float)a.scale;
+            for (int it = 0; it < 30; ++it) {
+                float x32[3], J32[3][3];
+                eval_at_warp_f(dp, sU, ref, xf, bf, x32, J32, Wf);
+                const float f[3] = {xr[0] - x32[0], xr[1] - x32[1], xr[2] - x32[2]};
+                if (sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) <= tol32) {
+                    ok32 = true;
+                    break;
+                }
+                const float det = det3f(J32);
+                if (!(fabsf(det) > 0.0f)) break;
+                float dxi[3];
+                for (int c = 0; c < 3; ++c) {
+                    float Jc[3][3];
+                    for (int r = 0; r < 3; ++r)
+                        for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J32[r][k];
+                    dxi[c] = det3f(Jc) / det;
+                }
+                for (int d = 0; d < 3; ++d) xf[d] = fminf(hif[d], fmaxf(lof[d], xf[d] + dxi[d]));
+            }
+        }
+        const bool done32 = ok32 && a.s32T && !a.nrm;
+        if (done32) {
+            // T^ = sum_a R_a T^_a with the FP32 basis, the terms over the lanes
+            const int n0 = dp.p[0] + 1, n1 = dp.p[1] + 1, nb = n0 * n1 * (dp.p[2] + 1);
+            const float iW = 1.0f / Wf;
+            double part = 0.0;
+            for (int l = lane; l < nb; l += 32) {
+                const int a0 = l % n0, a1 = (l / n0) % n1, a2 = l / (n0 * n1);
+                const int nat = nat_index(dp, bf.s[0] - dp.p[0] + a0, bf.s[1] - dp.p[1] + a1,
+                                          bf.s[2] - dp.p[2] + a2);
+                const float R = (float)dp.cw[nat].w * bf.N[0][a0] * bf.N[1][a1] * bf.N[2][a2] * iW;
+                part += (double)R * a.That[a.perm[nat]];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) {
+                s_That = part;
+                s_ok = 1;
+            }
+        }
+        if (ok32)
+            for (int d = 0; d < 3; ++d) xi[d] = (double)xf[d];
         Basis1D b;
         double x[3], J[3][3], W;
         double res = 1e300;
-        for (int it = 0; it < 60; ++it) {
+        for (int it = 0; it < 60 && !done32; ++it) {
             eval_at_warp(dp, xi, b, x, J, W);
             const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
             res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
@@ -633,8 +812,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
             }
             for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
         }
-        if (lane == 0) {
+        if (lane == 0 && !done32) {
             const int ok = res <= 1e-9 * a.scale;
+            const double iW = 1.0 / W;
             double That = 0.0;
             if (ok)
                 for (int a2 = 0; a2 <= dp.p[2]; ++a2)
@@ -642,7 +822,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
                         for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
                             const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
                                                       b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
-                            const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / W;
+                            const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] * iW;
                             That += R * a.That[a.perm[nat]];
                         }
             s_That = That;

@@ -122,8 +122,13 @@ def test_cuboid_single_track_fp64(sa, theta, variant, hist):
     xi = rng.uniform(0, 1, (40, 3))
     xi[:8, 2] = 1.0
     x, T_ref = m.eval_T(xi)
-    T = ctx.eval_T(x)
-    assert rel_linf(T, T_ref) <= TOL_FP64
+    T = ctx.eval_T(np.vstack([x, OUTSIDE_CUBOID]))
+    assert np.isnan(T[-2:]).all()
+    assert rel_linf(T[:-2], T_ref) <= TOL_FP64
+
+
+# points outside the 2 x 1 x 0.5 mm cuboid: NaN
+OUTSIDE_CUBOID = np.array([[3e-3, 0.5e-3, 0.25e-3], [1e-3, -0.2e-3, 0.25e-3]])
 
 
 @pytest.mark.parametrize("hist", list(HIST))
@@ -136,6 +141,15 @@ def test_cuboid_single_track_mixed(sa, theta, variant, hist):
     assert ctx.sizes().hist_separable == (hist == "separable")
     assert err["s_lat"] <= TOL_MIXED_REL and err["tt_bot"] <= TOL_MIXED_REL, err
     assert err["That"] <= TOL_MIXED_REL and err["That_abs"] <= TOL_MIXED_ABS, err
+    # reconstruction in the mixed context (FP32 point inversion and sums)
+    rng = np.random.default_rng(7)
+    xi = rng.uniform(0, 1, (40, 3))
+    xi[:8, 2] = 1.0
+    x, T_ref = m.eval_T(xi)
+    T = ctx.eval_T(np.vstack([x, OUTSIDE_CUBOID]))
+    assert np.isnan(T[-2:]).all()
+    assert rel_linf(T[:-2], T_ref) <= TOL_MIXED_REL
+    assert np.abs(T[:-2] - T_ref).max() <= TOL_MIXED_ABS
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
