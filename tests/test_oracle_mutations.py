@@ -113,7 +113,82 @@ def _model_full_space(self, workload, s_img=2.0, direct=True, build_solver=True)
     _model_init(self, workload, s_img=1.0, direct=direct, build_solver=build_solver)
 
 
+_ages = pointsource.ages
+
+
+def _ages_one_step_old(n, n_active, dt, mat, spot_radius):
+    return _ages(n + 1, n_active, dt, mat, spot_radius)
+
+
+_discretize = sources.discretize
+
+
+def _sources_one_step_late(scan, dt):
+    return _discretize(scan, dt)[1:]
+
+
+def _dirichlet_g_wrong_sign(self, T_tilde_bot):
+    if self.M_bot_lu is None:
+        return np.zeros(0)
+    return self.M_bot_lu.solve((self.W_bot @ (self.mat.T_c + T_tilde_bot))[self.dir])
+
+
+def _element_matrices_without_detJ(geom, elem, rho_cp, k):
+    Me = Ke = dofs = None
+    for xi, wt in geom.element_quadrature(elem):
+        dofs, R, dR, x, J = geom.local_eval(xi, [elem[d][2] for d in range(3)])
+        gradR = np.linalg.solve(J.T, dR.T).T
+        m = rho_cp * wt * np.outer(R, R)
+        kk = k * wt * (gradR @ gradR.T)
+        Me = m if Me is None else Me + m
+        Ke = kk if Ke is None else Ke + kk
+    return dofs, Me, Ke
+
+
+def _eval_flux_J_not_transposed(self, xi_pts, nrm):
+    xi_pts = np.atleast_2d(xi_pts)
+    nrm = np.atleast_2d(nrm)
+    x, qh = [], []
+    for xi, nv in zip(xi_pts, nrm):
+        dofs, R, dR, xp, J = self.geom.local_eval(xi)
+        gradR = np.linalg.solve(J, dR.T).T
+        qh.append(-self.mat.k * np.dot(nv, gradR.T @ self.T_hat[dofs]))
+        x.append(xp)
+    x = np.array(x)
+    _, qt, _ = _eval_flux(self, xi_pts, nrm)
+    return x, qt, np.array(qh)
+
+
+_boundary_points = assembly.boundary_points
+
+
+def _boundary_normals_inward(geom, kind):
+    pts = _boundary_points(geom, kind)
+    if pts is not None:
+        pts = dict(pts)
+        pts["n"] = -pts["n"]
+    return pts
+
+
 MUTATIONS = {
+    "ages one step too old": (
+        (pointsource, "ages", _ages_one_step_old),
+        [(pins.test_table3_integrated_analytical_heat_loss, ())]),
+    "first source one step late on each track": (
+        (sources, "discretize", _sources_one_step_late),
+        [(pins.test_R1_source_discretisation_counts_and_spacing, ())]),
+    "Dirichlet data T_c + T~": (
+        (solver.Model, "dirichlet_g", _dirichlet_g_wrong_sign),
+        [(pins.test_R5_dirichlet_projection_reproduces_face_space_functions, ())]),
+    "det J dropped from the volume quadrature": (
+        (assembly, "element_matrices", _element_matrices_without_detJ),
+        [(pins.test_P6_symmetry_constants_and_volume_on_curved_nurbs, ())]),
+    "grad T^ with J^-1 instead of J^-T": (
+        (solver.Model, "eval_flux", _eval_flux_J_not_transposed),
+        [(pins.test_heat_loss_rate_is_minus_k_times_the_normal_derivative, ())]),
+    "boundary normals pointing inward": (
+        (assembly, "boundary_points", _boundary_normals_inward),
+        [(pins.test_P9_energy_balance_all_neumann, (1.0,))]),
     "tau shift dropped from the ages": (
         (pointsource, "ages", _ages_without_tau_shift),
         [(pins.test_P4_sum_converges_to_rosenthal, ())]),
