@@ -45,3 +45,6 @@ def test_host_only_calls(lib):
     assert lib.lib.sa_set_material(None, 1.0, 1.0, 1.0, 1.0) == lib.SA_ERR_ARG
     assert lib.lib.sa_step(None, 0.5, 1e-5, 1, None) == lib.SA_ERR_ARG
     assert lib.lib.sa_last_error(None) == b"null context"
+    assert lib.lib.sa_eval_T(None, None, 0, None, 0) == lib.SA_ERR_ARG
+    assert lib.lib.sa_eval_flux(None, None, None, 0, None, None, 0) == lib.SA_ERR_ARG
+    assert lib.lib.sa_eval_flux(None, None, None, 3, None, None, 0) == lib.SA_ERR_ARG
