@@ -637,7 +637,7 @@ struct EvalArgs {
     double* q_hat;
 };
 
-constexpr int kEvalThreads = 128;
+constexpr int kEvalThreads = 512;   // the element search dominates a point's latency
 
 __device__ __forceinline__ float eval_ex2(float x) {
     float y;
@@ -653,7 +653,7 @@ __device__ __forceinline__ float eval_ex2(float x) {
 // and its FP32 basis give T^; a point the FP32 phase does not settle goes
 // the FP64 way from the element centre.  Reductions in a fixed order (ties
 // of the search: lowest element index).
-__global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs a) {
+__global__ void __maxnreg__(96) k_eval(EvalArgs a) {
     const int t = blockIdx.x;
     if (t >= a.n) return;
     __shared__ double s_d[kEvalThreads / 32];
