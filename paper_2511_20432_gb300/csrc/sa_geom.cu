@@ -638,11 +638,85 @@ struct EvalArgs {
 };
 
 constexpr int kEvalThreads = 512;   // the element search dominates a point's latency
+constexpr int kEvalStride = 4;      // coarse search: every 4th element per direction
+constexpr int kEvalFine = 8;        // then the elements within 8 of the best, per direction
+constexpr int kEvalCoarseMin = 4096;   // elements above which the search is coarse to fine
 
 __device__ __forceinline__ float eval_ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Block-wide nearest element centre to xs among the elements (i, j, k) with
+// lo[d] <= . <= hi[d], every st[d]-th (FP32 when a copy of the centres is
+// given: the centre only seeds Newton).  Ties go to the lowest element
+// index.  Every thread of the block calls it; the result is also left in
+// *s_best.
+__device__ int nearest_centre(const EvalArgs& a, const double xs[3], const int lo[3],
+                              const int hi[3], const int st[3], double* s_d, int* s_e,
+                              int* s_best) {
+    const DevPatch& dp = a.dp;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m0 = (hi[0] - lo[0]) / st[0] + 1, m1 = (hi[1] - lo[1]) / st[1] + 1;
+    const int nc = m0 * m1 * ((hi[2] - lo[2]) / st[2] + 1);
+    auto elem = [&](int c) {
+        const int i = lo[0] + (c % m0) * st[0], j = lo[1] + ((c / m0) % m1) * st[1],
+                  k = lo[2] + (c / (m0 * m1)) * st[2];
+        return (k * dp.ne[1] + j) * dp.ne[0] + i;
+    };
+    int best = 0x7fffffff;
+    double bd = 1e300;
+    if (a.ecent32) {
+        const float x0 = (float)xs[0], x1 = (float)xs[1], x2 = (float)xs[2];
+        float bf = 3.0e38f;
+        for (int c = threadIdx.x; c < nc; c += kEvalThreads) {
+            const int e = elem(c);
+            const float dx = a.ecent32[3 * e] - x0, dy = a.ecent32[3 * e + 1] - x1,
+                        dz = a.ecent32[3 * e + 2] - x2;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (d2 < bf) {
+                bf = d2;
+                best = e;
+            }
+        }
+        bd = bf;
+    } else {
+        for (int c = threadIdx.x; c < nc; c += kEvalThreads) {
+            const int e = elem(c);
+            const double dx = a.ecent[3 * e] - xs[0], dy = a.ecent[3 * e + 1] - xs[1],
+                         dz = a.ecent[3 * e + 2] - xs[2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < bd) {
+                bd = d2;
+                best = e;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (od < bd || (od == bd && ob < best)) {
+            bd = od;
+            best = ob;
+        }
+    }
+    if (lane == 0) {
+        s_d[w] = bd;
+        s_e[w] = best;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kEvalThreads / 32; ++k)
+            if (s_d[k] < bd || (s_d[k] == bd && s_e[k] < best)) {
+                bd = s_d[k];
+                best = s_e[k];
+            }
+        *s_best = best;
+    }
+    __syncthreads();
+    return *s_best;
 }
 
 // One block per query point: the threads search the element centres (in
@@ -674,203 +748,182 @@ __global__ void __maxnreg__(96) k_eval(EvalArgs a) {
             for (int i = threadIdx.x; i < dp.n[d] + dp.p[d] + 1; i += kEvalThreads)
                 sU[d * kEvalKnots + i] = (float)dp.U[d][i];
     // initial guess: parametric centre of the element with the nearest
-    // physical centre
+    // physical centre.  Large patches: coarse to fine (every kEvalStride-th
+    // element per direction, then the elements within kEvalFine of the best
+    // of them); a point whose Newton iteration fails from that seed is
+    // searched again over every element.
     const int nel = dp.ne[0] * dp.ne[1] * dp.ne[2];
-    int best = 0x7fffffff;
-    double bd = 1e300;
-    if (a.ecent32) {
-        const float x0 = (float)xs[0], x1 = (float)xs[1], x2 = (float)xs[2];
-        float bf = 3.0e38f;
-        for (int e = threadIdx.x; e < nel; e += kEvalThreads) {
-            const float dx = a.ecent32[3 * e] - x0, dy = a.ecent32[3 * e + 1] - x1,
-                        dz = a.ecent32[3 * e + 2] - x2;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (d2 < bf) {
-                bf = d2;
-                best = e;
-            }
-        }
-        bd = bf;
-    } else {
-        for (int e = threadIdx.x; e < nel; e += kEvalThreads) {
-            const double dx = a.ecent[3 * e] - xs[0], dy = a.ecent[3 * e + 1] - xs[1],
-                         dz = a.ecent[3 * e + 2] - xs[2];
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 < bd) {
-                bd = d2;
-                best = e;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
-        if (od < bd || (od == bd && ob < best)) {
-            bd = od;
-            best = ob;
-        }
-    }
-    if (lane == 0) {
-        s_d[w] = bd;
-        s_e[w] = best;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < kEvalThreads / 32; ++k)
-            if (s_d[k] < bd || (s_d[k] == bd && s_e[k] < best)) {
-                bd = s_d[k];
-                best = s_e[k];
-            }
-        s_best = best;
-    }
-    __syncthreads();
-    if (w == 0) {
-        // Newton on x(xi) = x*, clamped to the parametric box, by warp 0
-        best = s_best;
-        const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1],
-                           best / (dp.ne[0] * dp.ne[1])};
-        double xi[3], lo[3], hi[3];
+    const bool coarse = nel > kEvalCoarseMin;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int blo[3], bhi[3], bst[3];   // the element box searched
         for (int d = 0; d < 3; ++d) {
-            const int s = dp.espan[d][es[d]];
-            xi[d] = 0.5 * (dp.U[d][s] + dp.U[d][s + 1]);
-            lo[d] = dp.U[d][dp.p[d]];
-            hi[d] = dp.U[d][dp.n[d]];
+            blo[d] = 0;
+            bhi[d] = dp.ne[d] - 1;
+            bst[d] = 1;
         }
-        bool ok32 = false;
-        BasisF bf;
-        float Wf = 1.0f, xf[3];
-        if (use32) {
-            const double ref[3] = {a.x_ref, a.y_ref, a.z_top};
-            const float xr[3] = {(float)(xs[0] - ref[0]), (float)(xs[1] - ref[1]),
-                                 (float)(xs[2] - ref[2])};
-            float lof[3], hif[3];
+        if (attempt == 0 && coarse) {
             for (int d = 0; d < 3; ++d) {
-                xf[d] = (float)xi[d];
-                lof[d] = sU[d * kEvalKnots + dp.p[d]];
-                hif[d] = sU[d * kEvalKnots + dp.n[d]];
+                bst[d] = kEvalStride;
+                blo[d] = min(kEvalStride / 2, dp.ne[d] - 1);
             }
-            const float tol32 = 1e-6f * (float)a.scale;
-            for (int it = 0; it < 30; ++it) {
-                float x32[3], J32[3][3];
-                eval_at_warp_f(dp, sU, ref, xf, bf, x32, J32, Wf);
-                const float f[3] = {xr[0] - x32[0], xr[1] - x32[1], xr[2] - x32[2]};
-                if (sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) <= tol32) {
-                    ok32 = true;
-                    break;
+            const int ec = nearest_centre(a, xs, blo, bhi, bst, s_d, s_e, &s_best);
+            const int ic[3] = {ec % dp.ne[0], (ec / dp.ne[0]) % dp.ne[1], ec / (dp.ne[0] * dp.ne[1])};
+            for (int d = 0; d < 3; ++d) {
+                blo[d] = max(0, ic[d] - kEvalFine);
+                bhi[d] = min(dp.ne[d] - 1, ic[d] + kEvalFine);
+                bst[d] = 1;
+            }
+        }
+        nearest_centre(a, xs, blo, bhi, bst, s_d, s_e, &s_best);
+        if (w == 0) {
+            // Newton on x(xi) = x*, clamped to the parametric box, by warp 0
+            const int best = s_best;
+            const int es[3] = {best % dp.ne[0], (best / dp.ne[0]) % dp.ne[1],
+                               best / (dp.ne[0] * dp.ne[1])};
+            double xi[3], lo[3], hi[3];
+            for (int d = 0; d < 3; ++d) {
+                const int s = dp.espan[d][es[d]];
+                xi[d] = 0.5 * (dp.U[d][s] + dp.U[d][s + 1]);
+                lo[d] = dp.U[d][dp.p[d]];
+                hi[d] = dp.U[d][dp.n[d]];
+            }
+            bool ok32 = false;
+            BasisF bf;
+            float Wf = 1.0f, xf[3];
+            if (use32) {
+                const double ref[3] = {a.x_ref, a.y_ref, a.z_top};
+                const float xr[3] = {(float)(xs[0] - ref[0]), (float)(xs[1] - ref[1]),
+                                     (float)(xs[2] - ref[2])};
+                float lof[3], hif[3];
+                for (int d = 0; d < 3; ++d) {
+                    xf[d] = (float)xi[d];
+                    lof[d] = sU[d * kEvalKnots + dp.p[d]];
+                    hif[d] = sU[d * kEvalKnots + dp.n[d]];
                 }
-                const float det = det3f(J32);
-                if (!(fabsf(det) > 0.0f)) break;
-                float dxi[3];
-                for (int c = 0; c < 3; ++c) {
-                    float Jc[3][3];
-                    for (int r = 0; r < 3; ++r)
-                        for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J32[r][k];
-                    dxi[c] = det3f(Jc) / det;
+                const float tol32 = 1e-6f * (float)a.scale;
+                for (int it = 0; it < 30; ++it) {
+                    float x32[3], J32[3][3];
+                    eval_at_warp_f(dp, sU, ref, xf, bf, x32, J32, Wf);
+                    const float f[3] = {xr[0] - x32[0], xr[1] - x32[1], xr[2] - x32[2]};
+                    if (sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) <= tol32) {
+                        ok32 = true;
+                        break;
+                    }
+                    const float det = det3f(J32);
+                    if (!(fabsf(det) > 0.0f)) break;
+                    float dxi[3];
+                    for (int c = 0; c < 3; ++c) {
+                        float Jc[3][3];
+                        for (int r = 0; r < 3; ++r)
+                            for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J32[r][k];
+                        dxi[c] = det3f(Jc) / det;
+                    }
+                    for (int d = 0; d < 3; ++d) xf[d] = fminf(hif[d], fmaxf(lof[d], xf[d] + dxi[d]));
                 }
-                for (int d = 0; d < 3; ++d) xf[d] = fminf(hif[d], fmaxf(lof[d], xf[d] + dxi[d]));
             }
-        }
-        const bool done32 = ok32 && a.s32T && !a.nrm;
-        if (done32) {
-            // T^ = sum_a R_a T^_a with the FP32 basis, the terms over the lanes
-            const int n0 = dp.p[0] + 1, n1 = dp.p[1] + 1, nb = n0 * n1 * (dp.p[2] + 1);
-            const float iW = 1.0f / Wf;
-            double part = 0.0;
-            for (int l = lane; l < nb; l += 32) {
-                const int a0 = l % n0, a1 = (l / n0) % n1, a2 = l / (n0 * n1);
-                const int nat = nat_index(dp, bf.s[0] - dp.p[0] + a0, bf.s[1] - dp.p[1] + a1,
-                                          bf.s[2] - dp.p[2] + a2);
-                const float R = (float)dp.cw[nat].w * bf.N[0][a0] * bf.N[1][a1] * bf.N[2][a2] * iW;
-                part += (double)R * a.That[a.perm[nat]];
+            const bool done32 = ok32 && a.s32T && !a.nrm;
+            if (done32) {
+                // T^ = sum_a R_a T^_a with the FP32 basis, the terms over the lanes
+                const int n0 = dp.p[0] + 1, n1 = dp.p[1] + 1, nb = n0 * n1 * (dp.p[2] + 1);
+                const float iW = 1.0f / Wf;
+                double part = 0.0;
+                for (int l = lane; l < nb; l += 32) {
+                    const int a0 = l % n0, a1 = (l / n0) % n1, a2 = l / (n0 * n1);
+                    const int nat = nat_index(dp, bf.s[0] - dp.p[0] + a0, bf.s[1] - dp.p[1] + a1,
+                                              bf.s[2] - dp.p[2] + a2);
+                    const float R = (float)dp.cw[nat].w * bf.N[0][a0] * bf.N[1][a1] * bf.N[2][a2] * iW;
+                    part += (double)R * a.That[a.perm[nat]];
+                }
+    #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (lane == 0) {
+                    s_That = part;
+                    s_ok = 1;
+                }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) {
-                s_That = part;
-                s_ok = 1;
-            }
-        }
-        if (ok32)
-            for (int d = 0; d < 3; ++d) xi[d] = (double)xf[d];
-        Basis1D b;
-        double x[3], J[3][3], W;
-        double res = 1e300;
-        for (int it = 0; it < 60 && !done32; ++it) {
-            eval_at_warp(dp, xi, b, x, J, W);
-            const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
-            res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-            if (res <= 1e-13 * a.scale) break;
-            const double det = det3(J);
-            if (!(fabs(det) > 0.0)) break;
-            double dxi[3];
-            for (int c = 0; c < 3; ++c) {
-                double Jc[3][3];
-                for (int r = 0; r < 3; ++r)
-                    for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J[r][k];
-                dxi[c] = det3(Jc) / det;
-            }
-            for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
-        }
-        if (lane == 0 && !done32) {
-            const int ok = res <= 1e-9 * a.scale;
-            const double iW = 1.0 / W;
-            double That = 0.0;
-            if (ok)
-                for (int a2 = 0; a2 <= dp.p[2]; ++a2)
-                    for (int a1 = 0; a1 <= dp.p[1]; ++a1)
-                        for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
-                            const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
-                                                      b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
-                            const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] * iW;
-                            That += R * a.That[a.perm[nat]];
-                        }
-            s_That = That;
-            s_ok = ok;
-            if (ok && a.nrm) {
-                // grad T^ = J^{-T} sum_a T^_a grad_xi R_a (quotient rule)
-                double Wv = 0.0, dW[3] = {0.0, 0.0, 0.0};
-                for (int a2 = 0; a2 <= dp.p[2]; ++a2)
-                    for (int a1 = 0; a1 <= dp.p[1]; ++a1)
-                        for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
-                            const double w = dp.cw[nat_index(dp, b.s[0] - dp.p[0] + a0,
-                                                             b.s[1] - dp.p[1] + a1,
-                                                             b.s[2] - dp.p[2] + a2)].w;
-                            Wv += w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
-                            dW[0] += w * b.dN[0][a0] * b.N[1][a1] * b.N[2][a2];
-                            dW[1] += w * b.N[0][a0] * b.dN[1][a1] * b.N[2][a2];
-                            dW[2] += w * b.N[0][a0] * b.N[1][a1] * b.dN[2][a2];
-                        }
-                double gxi[3] = {0.0, 0.0, 0.0};
-                for (int a2 = 0; a2 <= dp.p[2]; ++a2)
-                    for (int a1 = 0; a1 <= dp.p[1]; ++a1)
-                        for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
-                            const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
-                                                      b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
-                            const double w = dp.cw[nat].w;
-                            const double Rv = w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / Wv;
-                            const double dd[3] = {w * b.dN[0][a0] * b.N[1][a1] * b.N[2][a2],
-                                                  w * b.N[0][a0] * b.dN[1][a1] * b.N[2][a2],
-                                                  w * b.N[0][a0] * b.N[1][a1] * b.dN[2][a2]};
-                            const double Ta = a.That[a.perm[nat]];
-                            for (int d = 0; d < 3; ++d) gxi[d] += Ta * (dd[d] - Rv * dW[d]) / Wv;
-                        }
-                // J^T g = gxi (Cramer)
-                double JT[3][3];
-                for (int r = 0; r < 3; ++r)
-                    for (int c = 0; c < 3; ++c) JT[r][c] = J[c][r];
-                const double det = det3(JT);
-                double g[3];
+            if (ok32)
+                for (int d = 0; d < 3; ++d) xi[d] = (double)xf[d];
+            Basis1D b;
+            double x[3], J[3][3], W;
+            double res = 1e300;
+            for (int it = 0; it < 60 && !done32; ++it) {
+                eval_at_warp(dp, xi, b, x, J, W);
+                const double f[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
+                res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+                if (res <= 1e-13 * a.scale) break;
+                const double det = det3(J);
+                if (!(fabs(det) > 0.0)) break;
+                double dxi[3];
                 for (int c = 0; c < 3; ++c) {
                     double Jc[3][3];
                     for (int r = 0; r < 3; ++r)
-                        for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? gxi[r] : JT[r][k];
-                    g[c] = det3(Jc) / det;
+                        for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? f[r] : J[r][k];
+                    dxi[c] = det3(Jc) / det;
                 }
-                const double* nv = a.nrm + 3 * t;
-                s_That = -a.k * (nv[0] * g[0] + nv[1] * g[1] + nv[2] * g[2]);
+                for (int d = 0; d < 3; ++d) xi[d] = fmin(hi[d], fmax(lo[d], xi[d] + dxi[d]));
+            }
+            if (lane == 0 && !done32) {
+                const int ok = res <= 1e-9 * a.scale;
+                const double iW = 1.0 / W;
+                double That = 0.0;
+                if (ok)
+                    for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                        for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                            for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                                const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                          b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
+                                const double R = dp.cw[nat].w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] * iW;
+                                That += R * a.That[a.perm[nat]];
+                            }
+                s_That = That;
+                s_ok = ok;
+                if (ok && a.nrm) {
+                    // grad T^ = J^{-T} sum_a T^_a grad_xi R_a (quotient rule)
+                    double Wv = 0.0, dW[3] = {0.0, 0.0, 0.0};
+                    for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                        for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                            for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                                const double w = dp.cw[nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                                 b.s[1] - dp.p[1] + a1,
+                                                                 b.s[2] - dp.p[2] + a2)].w;
+                                Wv += w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2];
+                                dW[0] += w * b.dN[0][a0] * b.N[1][a1] * b.N[2][a2];
+                                dW[1] += w * b.N[0][a0] * b.dN[1][a1] * b.N[2][a2];
+                                dW[2] += w * b.N[0][a0] * b.N[1][a1] * b.dN[2][a2];
+                            }
+                    double gxi[3] = {0.0, 0.0, 0.0};
+                    for (int a2 = 0; a2 <= dp.p[2]; ++a2)
+                        for (int a1 = 0; a1 <= dp.p[1]; ++a1)
+                            for (int a0 = 0; a0 <= dp.p[0]; ++a0) {
+                                const int nat = nat_index(dp, b.s[0] - dp.p[0] + a0,
+                                                          b.s[1] - dp.p[1] + a1, b.s[2] - dp.p[2] + a2);
+                                const double w = dp.cw[nat].w;
+                                const double Rv = w * b.N[0][a0] * b.N[1][a1] * b.N[2][a2] / Wv;
+                                const double dd[3] = {w * b.dN[0][a0] * b.N[1][a1] * b.N[2][a2],
+                                                      w * b.N[0][a0] * b.dN[1][a1] * b.N[2][a2],
+                                                      w * b.N[0][a0] * b.N[1][a1] * b.dN[2][a2]};
+                                const double Ta = a.That[a.perm[nat]];
+                                for (int d = 0; d < 3; ++d) gxi[d] += Ta * (dd[d] - Rv * dW[d]) / Wv;
+                            }
+                    // J^T g = gxi (Cramer)
+                    double JT[3][3];
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c) JT[r][c] = J[c][r];
+                    const double det = det3(JT);
+                    double g[3];
+                    for (int c = 0; c < 3; ++c) {
+                        double Jc[3][3];
+                        for (int r = 0; r < 3; ++r)
+                            for (int k = 0; k < 3; ++k) Jc[r][k] = (k == c) ? gxi[r] : JT[r][k];
+                        g[c] = det3(Jc) / det;
+                    }
+                    const double* nv = a.nrm + 3 * t;
+                    s_That = -a.k * (nv[0] * g[0] + nv[1] * g[1] + nv[2] * g[2]);
+                }
             }
         }
+        __syncthreads();   // s_ok written
+        if (s_ok || attempt == 1 || !coarse) break;
     }
     if (a.nrm) {
         // q~ = -k dT~/dn, dT~/dn = sum -g exp(-a R^2) n . (x - x_I)
