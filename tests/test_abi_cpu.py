@@ -48,3 +48,49 @@ def test_host_only_calls(lib):
     assert lib.lib.sa_eval_T(None, None, 0, None, 0) == lib.SA_ERR_ARG
     assert lib.lib.sa_eval_flux(None, None, None, 0, None, None, 0) == lib.SA_ERR_ARG
     assert lib.lib.sa_eval_flux(None, None, None, 3, None, None, 0) == lib.SA_ERR_ARG
+
+
+def _header_signatures():
+    """name -> parameter kinds ('P' pointer, 'D' double, 'F' float, 'I' int or
+    enum, 'LL' long long, 'ULL' unsigned long long) from include/*.h."""
+    sigs = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"[\w\s\*]+?\b(sa_\w+)\s*\(([^;{}]*?)\)\s*;", src):
+            name, params = m.group(1), m.group(2).strip()
+            kinds = []
+            if params and params != "void":
+                for p in params.split(","):
+                    p = " ".join(p.split())
+                    if "*" in p or "[" in p:
+                        kinds.append("P")
+                    elif "double" in p:
+                        kinds.append("D")
+                    elif "float" in p:
+                        kinds.append("F")
+                    elif "unsigned long long" in p:
+                        kinds.append("ULL")
+                    elif "long long" in p:
+                        kinds.append("LL")
+                    else:
+                        kinds.append("I")
+            sigs[name] = kinds
+    return sigs
+
+
+def _ctypes_kind(t):
+    import ctypes as C
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "P"
+    return {C.c_double: "D", C.c_float: "F", C.c_int: "I", C.c_longlong: "LL",
+            C.c_ulonglong: "ULL"}[t]
+
+
+def test_binding_argument_types_match_the_header(lib):
+    sigs = _header_signatures()
+    assert "sa_eval_flux" in sigs and len(sigs["sa_eval_flux"]) == 7
+    for name, kinds in sorted(sigs.items()):
+        f = getattr(lib.lib, name)
+        assert f.argtypes is not None, name          # every declared call is typed
+        assert [_ctypes_kind(t) for t in f.argtypes] == kinds, name
