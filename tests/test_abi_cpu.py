@@ -94,3 +94,35 @@ def test_binding_argument_types_match_the_header(lib):
         f = getattr(lib.lib, name)
         assert f.argtypes is not None, name          # every declared call is typed
         assert [_ctypes_kind(t) for t in f.argtypes] == kinds, name
+
+
+def test_struct_layouts_match_the_header(lib):
+    """sizeof and every field offset of the option, statistics and size
+    structs, from a C program compiled against include/sa.h, against the
+    binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"sa_options": lib.sa_options, "sa_step_stats": lib.sa_step_stats,
+               "sa_sizes": lib.sa_sizes}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "sa.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        src.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            src.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    src.append("return 0; }")
+    out_dir = os.path.join(ROOT, "paper_2511_20432_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    c_path = os.path.join(out_dir, "abi_layout.c")
+    exe = os.path.join(out_dir, "abi_layout")
+    with open(c_path, "w") as fh:
+        fh.write("\n".join(src) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c_path, "-o", exe],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([exe], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
