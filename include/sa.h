@@ -47,11 +47,15 @@ typedef enum sa_status {
     SA_ERR_NAN = 8             /* a non-finite value appeared in the state */
 } sa_status;
 
-/* Precision of the history sum (the only stage whose precision changes). */
+/* Arithmetic of the per-step path. */
 enum { SA_FP64 = 0,   /* every stage in FP64                                       */
-       SA_MIXED = 1   /* history sum in FP32 with ages relative to the current
-                         step, chunked Kahan-compensated accumulation and an FP64
-                         total; assembly, boundary integrals, PCG stay FP64        */ };
+       SA_MIXED = 1   /* history sums in FP32 (coefficients from ages relative to
+                         the current step; compensated accumulation on the
+                         pairwise path, per-chunk FP32 sums on the separable one)
+                         and the per-step operators' values in FP32 with FP64
+                         Krylov vectors, state and residual test (dot products
+                         from copies scaled by 1/||b||, in FP32); assembly and
+                         boundary integrals FP64                                   */ };
 
 /* Face ids: 0 xi=0, 1 xi=1, 2 eta=0, 3 eta=1, 4 zeta=0, 5 zeta=1. */
 enum { SA_FACE_NONE = 0,       /* no boundary term (top face, Section 2.1)      */
@@ -126,10 +130,13 @@ enum { SA_PRECOND_AUTO = 0, SA_PRECOND_JACOBI = 1, SA_PRECOND_FD = 2 };
 enum { SA_GUESS_PREVIOUS = 0, SA_GUESS_EXTRAPOLATE = 1 };
 enum { SA_HIST_AUTO = 0, SA_HIST_PAIRWISE = 1, SA_HIST_SEPARABLE = 2 };
 
-/* Fill o with the defaults listed above. */
+/* Fill o (caller-owned, not NULL) with the defaults listed above; host only. */
 void sa_options_default(sa_options* o);
 
-/* Create an empty context on the chosen device.  o may be NULL (defaults). */
+/* Create an empty context on the chosen device.  o may be NULL (defaults);
+ * the options are copied.  *out is owned by the caller and released with
+ * sa_destroy.  Errors: SA_ERR_ARG (out NULL, an option out of its range),
+ * SA_ERR_CUDA (device selection or query), SA_ERR_OOM. */
 sa_status sa_create(const sa_options* o, sa_ctx** out);
 
 /*
@@ -162,14 +169,19 @@ sa_status sa_create_patch(sa_ctx* ctx, const int degree[3], const int n_ctrl[3],
                           const double* ctrl_xyz, const double* weights,
                           const double* const knots[3], const int n_knots[3], int seam_dir);
 
-/* Face kinds (SA_FACE_*), face ids as above.  Default: faces 0-3 NEUMANN,
- * face 4 DIRICHLET, face 5 NONE.  Must be called before sa_create_patch to
- * take effect on set-up; SA_ERR_STATE afterwards. */
+/* Face kinds (SA_FACE_*), face ids as above (Section 2.1: Neumann data on
+ * the lateral faces, Eq. that-bc-n; Dirichlet data on the bottom face, Eq.
+ * that-bc-d; the top face's condition is built into the half-space point
+ * source).  Default: faces 0-3 NEUMANN, face 4 DIRICHLET, face 5 NONE.
+ * face_kind: 6 ints (host), copied.  Must be called before sa_create_patch
+ * to take effect on set-up.  Errors: SA_ERR_ARG (NULL, unknown kind),
+ * SA_ERR_STATE (after sa_create_patch, or a poisoned context). */
 sa_status sa_set_boundary(sa_ctx* ctx, const int face_kind[6]);
 
 /* Material (Section 2, Eq. linear-heat: alpha = k/(rho c_p)) and the
  * platform / initial temperature T_c (Section 2: T(x,0) = T_c).  All > 0
- * except T_c (any finite value). */
+ * except T_c (any finite value).  Errors: SA_ERR_ARG (a value out of range or
+ * not finite), SA_ERR_STATE (poisoned context). */
 sa_status sa_set_material(sa_ctx* ctx, double k, double rho, double cp, double T_c);
 
 /*
@@ -207,7 +219,8 @@ typedef struct sa_step_stats {
  * Advance the correction field n_steps theta-steps of size dt (Eq.
  * theta-method, theta in [0, 1]).  Per step n -> n+1: point-source history
  * sums at the boundary quadrature points, F^{n+1} and the bottom projection,
- * the theta right-hand side, PCG (Jacobi) from x0 = T^^n.  dt must stay the
+ * the theta right-hand side, PCG with the preconditioner and initial guess
+ * of sa_options (precond, initial_guess) to pcg_tol.  dt must stay the
  * same for the life of a scan (the source spacing is v*dt); a change returns
  * SA_ERR_ARG.  theta may change between calls (the operator is rebuilt).
  * stats may be NULL: the call then returns after enqueueing the work (errors
@@ -282,7 +295,8 @@ sa_status sa_eval_T_noalloc(sa_ctx* ctx, const double* pts, int n, double* T_out
  */
 sa_status sa_selftest_waits(int* barrier_flagged, int* mbarrier_flagged);
 
-/* Sizes of a context after set-up. */
+/* Sizes of a context after set-up (out: caller-owned).  Errors: SA_ERR_ARG
+ * (out NULL), SA_ERR_STATE (before sa_create_patch, or poisoned). */
 typedef struct sa_sizes {
     int n_dof, n_free, n_dir;      /* control variables; free / Dirichlet             */
     int q_lat, q_bot;              /* lateral / bottom quadrature points              */
@@ -307,16 +321,25 @@ enum { SA_FIELD_THAT = 0,      /* T^ at control variables (n_dof)               
        SA_FIELD_TT_BOT = 3,    /* T~ at bottom points, last step (q_bot)             */
        SA_FIELD_LAT_X = 4,     /* lateral points: x,y,z,nx,ny,nz,wdS (q_lat*7)       */
        SA_FIELD_BOT_X = 5      /* bottom points: x,y,z,wdS (q_bot*4)                 */ };
+/* out: count >= the field's length, host (on_device = 0) or device (1);
+ * synchronous.  Errors: SA_ERR_ARG (out NULL, unknown field, count too
+ * small), SA_ERR_STATE (before sa_create_patch), SA_ERR_CUDA. */
 sa_status sa_get_field(sa_ctx* ctx, int field, double* out, long long count, int on_device);
 
-/* Assembled matrices in natural order, CSR over ALL control variables:
- * which = 0 mass M, 1 conductivity K.  rowptr: n_dof+1, colind and vals:
- * nnz (from sa_get_matrix_nnz).  Host buffers. */
+/* Assembled matrices (Section 2.3: M_ij = int rho c_p R_i R_j dV, K_ij = int
+ * k grad R_i . grad R_j dV) in natural order, CSR over ALL control
+ * variables: which = 0 mass M, 1 conductivity K.  rowptr: n_dof+1, colind
+ * and vals: nnz (from sa_get_matrix_nnz).  Host buffers, caller-allocated;
+ * synchronous.  Errors: SA_ERR_ARG (NULL, which not 0 or 1), SA_ERR_STATE
+ * (before sa_create_patch), SA_ERR_CUDA. */
 sa_status sa_get_matrix_nnz(sa_ctx* ctx, long long* nnz);
 sa_status sa_get_matrix(sa_ctx* ctx, int which, long long* rowptr, int* colind, double* vals);
 
 /* Checkpoint: the state is (n, T^ (n_dof, natural order), F^n (n_dof)).  The
- * sources are recomputed from the scan.  Host buffers; synchronous. */
+ * sources are recomputed from the scan.  Host buffers (caller-owned; read by
+ * sa_set_state, written by sa_get_state); synchronous.  Errors: SA_ERR_ARG
+ * (NULL, n < 0), SA_ERR_STATE (before patch and material), SA_ERR_NAN (a
+ * non-finite value in the state), SA_ERR_CUDA. */
 sa_status sa_get_state(sa_ctx* ctx, long long* n, double* T_hat, double* F);
 sa_status sa_set_state(sa_ctx* ctx, long long n, const double* T_hat, const double* F);
 
@@ -331,6 +354,11 @@ sa_status sa_set_state(sa_ctx* ctx, long long n, const double* T_hat, const doub
  * in_idx, divided by |r0|_2; output: the increment of the free control
  * variables divided by |r0|_2 (the solve is linear, so the scaling is exact).
  */
+/* Every sa_mlp call: Errors SA_ERR_ARG (NULL, sizes out of range or not
+ * matching the network), SA_ERR_OOM, SA_ERR_CUDA.  *out of sa_mlp_create is
+ * owned by the caller and released with sa_mlp_destroy (NULL is a no-op);
+ * a network set as a warm start must outlive that use; the context keeps no
+ * reference after sa_set_warm_start(ctx, NULL, ...). */
 typedef struct sa_mlp sa_mlp;
 sa_status sa_mlp_create(int n_in, int hidden, int n_out, unsigned long long seed, sa_mlp** out);
 void sa_mlp_destroy(sa_mlp* m);
@@ -387,6 +415,12 @@ sa_status sa_get_stage_times(sa_ctx* ctx, double* ms, long long* steps);
  * for one context; with SA_HIST_SEPARABLE otherwise the first
  * sa_batch_step returns SA_ERR_ARG).
  */
+/* Errors of the batch calls: SA_ERR_ARG (NULL, n_inst < 1, an instance
+ * index or field out of range, options the batch does not support),
+ * SA_ERR_STATE (an instance without patch, material or scan, or instances at
+ * different steps), SA_ERR_OOM, SA_ERR_CUDA, and from sa_batch_step the
+ * sa_step statuses.  *out is owned by the caller (sa_batch_destroy; NULL is
+ * a no-op); sa_batch_last_error gives the last message. */
 typedef struct sa_batch sa_batch;
 sa_status sa_batch_create(sa_ctx* const* insts, int n_inst, const sa_options* o, sa_batch** out);
 sa_status sa_batch_step(sa_batch* b, double theta, double dt, int n_steps, sa_step_stats* stats);
@@ -403,8 +437,13 @@ sa_status sa_batch_autotune(sa_batch* b, const char* cache_path, int* P, int* NW
 const char* sa_batch_last_error(const sa_batch* b);
 void sa_batch_destroy(sa_batch* b);
 
+/* Release every device buffer, graph and stream object of the context
+ * (NULL is a no-op). */
 void sa_destroy(sa_ctx* ctx);
+/* Name of a status ("SA_ERR_ARG", ...); a static string. */
 const char* sa_status_str(sa_status s);
+/* One-line message of the context's last failure, valid until its next
+ * call; "null context" for NULL. */
 const char* sa_last_error(const sa_ctx* ctx);
 
 #ifdef __cplusplus
