@@ -19,7 +19,11 @@ sources; fast-diagonalization preconditioners, solves started from T^n),
 replayed as CUDA graphs (16 steps per graph) with the inputs resident in
 HBM.  Timed beside it: the same path with extrapolated initial guesses, with
 the Jacobi preconditioner, with the pairwise history sums, the plain FP64
-path (pairwise sums) and FP64 with the separable sums.
+path (pairwise sums) and FP64 with the separable sums.  Also in the line:
+the plate with a hole, the 256-instance batched sweep, the learned warm
+start, and the heat-loss diagnostic of Sections 3.1-3.2 (integrated |q~ +
+q^| along the top arc of the quarter-cylinder part, single source and
+contour scan, on two meshes).
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
 bounded sample of the same step.
