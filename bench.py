@@ -125,7 +125,7 @@ def clocks_start(dev):
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
     try:
         p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
-                              "-lms", "100", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
+                              "-lms", "50", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
     except OSError:
         p = None
     return p, f.name
@@ -185,90 +185,225 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle as it stands, on a bounded sample of one step
+# The oracle as it stands, on the host cores (the reference arm and the
+# cpu_baseline leg): the history sums of whole steps, split by boundary point
+# over worker processes (spawn: the parent may already hold a CUDA context),
+# and whole oracle steps (history, boundary load, projection, LU solve) of
+# the 2 x 1 x 0.5 mm cuboid.
 # ---------------------------------------------------------------------------
+_OW = {}
+
+
+def _ow_init(lat_x, lat_n, bot_x, E, mat):
+    _OW.update(lat_x=lat_x, lat_n=lat_n, bot_x=bot_x, E=E, mat=mat)
+
+
+def _ow_part(args):
+    from oracle import pointsource
+    kind, q0, q1, stride, xs, age = args
+    sl = slice(q0, q1, stride)
+    if kind == "lat":
+        return pointsource.dTdn_tilde(_OW["lat_x"][sl], _OW["lat_n"][sl], xs, age, _OW["E"],
+                                      _OW["mat"])
+    return pointsource.T_tilde(_OW["bot_x"][sl], xs, age, _OW["E"], _OW["mat"])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OracleHistory:
+    """The oracle's history sums (dT~/dn at the lateral points, T~ at the
+    bottom points) of one step of a workload, every ``stride``-th point of
+    each list, on ``procs`` worker processes."""
+
+    def __init__(self, wl, procs):
+        import multiprocessing as mp
+        from oracle import assembly, sources
+        from oracle.geometry import PatchGeom
+        from oracle.solver import FACE_DIRICHLET, FACE_NEUMANN
+        self.wl = wl
+        g = PatchGeom(wl.patch)
+        self.lat = assembly.boundary_points(g, FACE_NEUMANN)
+        self.bot = assembly.boundary_points(g, FACE_DIRICHLET)
+        self.xs = sources.discretize(wl.scan, wl.dt)
+        self.E = sources.energy(wl.scan, wl.dt)
+        self.procs = procs
+        self.q = len(self.lat["x"]) + len(self.bot["x"])
+        self.pool = mp.get_context("spawn").Pool(
+            procs, _ow_init, (self.lat["x"], self.lat["n"], self.bot["x"], self.E, wl.material))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def _tasks(self, n, stride, parts):
+        from oracle import pointsource
+        K = min(n, len(self.xs))
+        xs, age = self.xs[:K], pointsource.ages(n, K, self.wl.dt, self.wl.material,
+                                                self.wl.scan.spot_radius)
+        tasks, pts = [], 0
+        for kind, Q in (("lat", len(self.lat["x"])), ("bot", len(self.bot["x"]))):
+            cuts = [int(Q * k / parts) // stride * stride for k in range(parts)] + [Q]
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                if b > a:
+                    tasks.append((kind, a, b, stride, xs, age))
+                    pts += len(range(a, b, stride))
+        return tasks, pts, K
+
+    def step(self, n, stride=1):
+        """Evaluate step n on the pool; returns (seconds, points, pairs)."""
+        tasks, pts, K = self._tasks(n, stride, 4 * self.procs)
+        t0 = time.perf_counter()
+        self.pool.map(_ow_part, tasks)
+        return time.perf_counter() - t0, pts, pts * K
+
+    def step_single(self, n, stride):
+        """The same in this process alone (one core)."""
+        tasks, pts, K = self._tasks(n, stride, 1)
+        t0 = time.perf_counter()
+        _ow_init(self.lat["x"], self.lat["n"], self.bot["x"], self.E, self.wl.material)
+        for t in tasks:
+            _ow_part(t)
+        return time.perf_counter() - t0, pts, pts * K
+
+
+def oracle_whole_steps_cuboid():
+    """Whole oracle theta-steps (history sums, boundary load, bottom
+    projection, sparse-LU theta solve) of the 2 x 1 x 0.5 mm cuboid, all 150
+    steps of its track, one core; set-up (assembly, factorisation) apart."""
+    import workloads as W
+    from oracle.solver import Model
+    wl = W.cuboid_single_track(theta=0.5, n_steps=150)
+    t0 = time.perf_counter()
+    m = Model(wl)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m.run(wl.n_steps)
+    t_run = time.perf_counter() - t0
+    return {"workload": wl.name, "steps": wl.n_steps, "setup_s": t_setup, "run_s": t_run,
+            "steps_per_s": wl.n_steps / t_run, "cores": 1,
+            "what": "whole oracle steps: history sums, boundary load, projection, LU solve"}
+
+def block_config(wl, n0, n_first):
+    """The workload keys shared by both arms' lines (same dict in each)."""
+    n_el = [len(set(k)) - 1 for k in wl.patch.knots]
+    q_lat = 2 * 9 * (n_el[0] + n_el[1]) * n_el[2]
+    q_bot = 9 * n_el[0] * n_el[1]
+    return {"workload": wl.name + f" mid-scan from step {n0}", "n_dof": wl.patch.n_dof,
+            "q_lat": q_lat, "q_bot": q_bot, "active_sources_first": n_first,
+            "theta": wl.theta, "dt": wl.dt}
+
+
+def oracle_history_timing(wl, n_first, steps, warmup, budget_s, single_s=4.0):
+    """Time the oracle's history sums of ``steps`` consecutive steps from
+    step n_first (after ``warmup`` untimed ones) on all host cores; each step
+    evaluates every stride-th boundary point, the stride chosen so that the
+    timed and warm-up steps take about ``budget_s`` (stride 1 = whole steps).
+    Also one core on a sample of about ``single_s`` seconds."""
+    import math
+    import statistics as stt
+    procs = host_cores()
+    t0 = time.perf_counter()
+    oh = OracleHistory(wl, procs)
+    t_setup = time.perf_counter() - t0
+    try:
+        dt_c, pts_c, _ = oh.step(n_first, 64)              # calibration
+        per_step = budget_s / max(1, steps + warmup)
+        stride = max(1, math.ceil(oh.q * (dt_c / pts_c) / per_step))
+        for i in range(warmup):
+            oh.step(n_first - warmup + i, stride)
+        ts, pts, pairs = [], 0, 0
+        for i in range(steps):
+            t, p, pr = oh.step(n_first + i, stride)
+            ts.append(t)
+            pts += p
+            pairs += pr
+        n_mid = n_first + steps // 2
+        stride1 = max(stride, math.ceil(oh.q * (dt_c / pts_c) * procs / single_s))
+        t1, p1, pr1 = oh.step_single(n_mid, stride1)
+    finally:
+        oh.close()
+    frac = pts / (steps * oh.q)
+    ms = 1e3 * stt.mean(ts)
+    return {"procs": procs, "setup_s": t_setup, "stride": stride, "points_per_step": pts // steps,
+            "points_whole_step": oh.q, "ms_per_sampled_step": ms,
+            "steps_per_s": frac / (ms / 1e3), "pairs_per_s": pairs / sum(ts),
+            "single_thread": {"stride": stride1, "points": p1, "s": t1, "pairs_per_s": pr1 / t1,
+                              "steps_per_s": (p1 / oh.q) / t1}}
+
+
+def _sample_text(h, n_first):
+    whole = "whole steps" if h["stride"] == 1 else (
+        f"every {h['stride']}-th boundary point ({h['points_per_step']} of "
+        f"{h['points_whole_step']}) per step, scaled to whole steps")
+    return (f"oracle history sums (dT~/dn at every lateral point, T~ at every bottom point, all "
+            f"active sources) of consecutive steps from step {n_first}: {whole}, on "
+            f"{h['procs']} worker processes; the boundary load, the projection and the theta "
+            "solve are not in it (whole oracle steps of the 2 x 1 x 0.5 mm cuboid, solve "
+            "included, are reported beside it)")
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands on the host cores,
+    on the GPU arm's workload and steps (bounded: about 90 s of stepping)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    import numpy as np
     import workloads as W
-    from oracle import pointsource, sources
-    from oracle.geometry import PatchGeom
     wl = W.block_meander(20, theta=0.5)
-    geom = PatchGeom(wl.patch)
-    xs = sources.discretize(wl.scan, wl.dt)
-    E = sources.energy(wl.scan, wl.dt)
-    n = START_STEP
-    age = pointsource.ages(n, n, wl.dt, wl.material, wl.scan.spot_radius)
-    rng = np.random.default_rng(0)
-    lat = geom.face_points(0)
-    bot = geom.face_points(4)
-    q_lat_full = 4 * len(lat["x"])
-    q_bot_full = len(bot["x"])
-    n_pts = 128
-    il = rng.integers(0, len(lat["x"]), n_pts)
-    ib = rng.integers(0, len(bot["x"]), n_pts)
-
-    def one():
-        t0 = time.perf_counter()
-        pointsource.dTdn_tilde(lat["x"][il], lat["n"][il], xs[:n], age, E, wl.material)
-        pointsource.T_tilde(bot["x"][ib], xs[:n], age, E, wl.material)
-        return time.perf_counter() - t0
-
-    for _ in range(args.warmup):
-        one()
-    ts = [one() for _ in range(args.steps)]
-    t = float(np.mean(ts))
-    pairs_sample = 2 * n_pts * n
-    evals = pairs_sample / t
-    pairs_step = (q_lat_full + q_bot_full) * n
-    steps_per_s = evals / pairs_step
+    n0 = start_step(args)
+    n_first = n0 + args.warmup + 1
+    h = oracle_history_timing(wl, n_first, args.steps, args.warmup, 90.0)
+    whole = oracle_whole_steps_cuboid()
+    cpu = {"value": h["steps_per_s"], "unit": UNIT, "cores": h["procs"], "kind": "oracle",
+           "sample": _sample_text(h, n_first), "cpu_model": host_cpu_model(),
+           "pairs_per_s": h["pairs_per_s"], "single_thread": h["single_thread"],
+           "cuboid_whole_steps": whole}
     line = {
-        "impl": "reference", "metric": METRIC, "value": steps_per_s, "unit": UNIT,
+        "impl": "reference", "metric": METRIC, "value": h["steps_per_s"], "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 / steps_per_s, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": h["ms_per_sampled_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name + f" mid-scan step {n}", "start_step": n},
-        "point_source_evals_per_s": evals,
-        "cpu_baseline": {"value": steps_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle history sums on {n_pts} lateral + {n_pts} bottom "
-                                   f"points x {n} sources per step, scaled to the "
-                                   f"{q_lat_full + q_bot_full} points of one step; the oracle's "
-                                   "linear solve is not included"},
-        "e2e": {"value": steps_per_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+        "config": block_config(wl, n0, n_first),
+        "value_basis": "value = (evaluated points / points of a whole step) / ms_per_step",
+        "point_source_evals_per_s": h["pairs_per_s"],
+        "cpu_baseline": cpu,
+        "e2e": {"value": h["steps_per_s"], "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
-def cpu_baseline_block(wl, n, seconds_target=10.0):
-    import numpy as np
-    from oracle import pointsource, sources
-    from oracle.geometry import PatchGeom
-    geom = PatchGeom(wl.patch)
-    xs = sources.discretize(wl.scan, wl.dt)
-    E = sources.energy(wl.scan, wl.dt)
-    age = pointsource.ages(n, n, wl.dt, wl.material, wl.scan.spot_radius)
-    lat = geom.face_points(0)
-    bot = geom.face_points(4)
-    q_full = 4 * len(lat["x"]) + len(bot["x"])
-    rng = np.random.default_rng(0)
-    n_pts, spent, pairs = 256, 0.0, 0
-    while spent < seconds_target:
-        il = rng.integers(0, len(lat["x"]), n_pts)
-        ib = rng.integers(0, len(bot["x"]), n_pts)
-        t0 = time.perf_counter()
-        pointsource.dTdn_tilde(lat["x"][il], lat["n"][il], xs[:n], age, E, wl.material)
-        pointsource.T_tilde(bot["x"][ib], xs[:n], age, E, wl.material)
-        spent += time.perf_counter() - t0
-        pairs += 2 * n_pts * n
-    evals = pairs / spent
-    return {"value": evals / (q_full * n), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle history sums on {pairs // n} sampled boundary points x {n} "
-                      f"sources ({spent:.1f} s), scaled to the {q_full} points of one step; "
-                      "the oracle's linear solve is not included",
-            "point_source_evals_per_s": evals}
+def cpu_baseline_block(wl, n_first):
+    """cpu_baseline of the GPU arm's line: the same timing on a 20 s budget."""
+    h = oracle_history_timing(wl, n_first, 4, 1, 20.0)
+    return {"value": h["steps_per_s"], "unit": UNIT, "cores": h["procs"], "kind": "oracle",
+            "sample": _sample_text(h, n_first), "cpu_model": host_cpu_model(),
+            "pairs_per_s": h["pairs_per_s"], "single_thread": h["single_thread"],
+            "cuboid_whole_steps": oracle_whole_steps_cuboid()}
 
 
 # ---------------------------------------------------------------------------
@@ -517,24 +652,42 @@ def run_ours(args):
     pairs = q_pts * sum(min(n_first + i, sz.n_src) for i in range(K))
 
     # ---- timed region: K graph replays ---------------------------------------
+    # The clock sampler starts 0.4 s before the timed region and runs until
+    # at least 1 s of the same mid-scan stepping has followed it, so that it
+    # sees samples however short the K steps are.
+    clk = clocks_start(local)
+    time.sleep(0.4)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clk = clocks_start(local)
     ms = time_graph(ctx, th, dt, K, stream)
+    t_w0 = time.perf_counter()
+    K_w = 0
+    while time.perf_counter() - t_w0 < 1.0:
+        ctx.step(th, dt, 64, stats=False)
+        torch.cuda.synchronize()
+        K_w += 64
     clocks = clocks_stop(clk)
+    clocks["window"] = (f"sampled every 50 ms from 0.4 s before the timed region to "
+                        f"{K_w} steps of the same stepping after it")
     ms = max_over_ranks(ms, dist, "cuda")
+    if clocks.get("sm_mhz"):
+        clocks["ms_x_sm_mhz_per_step"] = ms / K * clocks["sm_mhz"]
     stats = ctx.step(th, dt, 0)                # counters accumulated over the timed steps
     iters_avg = stats.pcg_iters_total / K
     bot_avg = stats.bot_iters_total / K
     value = world * K / (ms / 1e3)
     evals = world * pairs / (ms / 1e3)
+    # separable sums: the pairs are not evaluated one by one (one FMA each);
+    # the exponentials are the factors, sep_factors per active source
+    exps = world * sz.sep_factors * sum(min(n_first + i, sz.n_src) for i in range(K)) / (ms / 1e3)
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
                               "precision": args.precision, "guess": args.guess, "start_step": n0,
-                              "point_source_evals_per_s": evals, "pcg_iters_per_step": iters_avg,
+                              ("point_source_equivalent_pairs_per_s" if sz.hist_separable else
+                               "point_source_evals_per_s"): evals, "pcg_iters_per_step": iters_avg,
                               "bot_iters_per_step": bot_avg, "clocks": clocks}))
         if dist:
             dist.destroy_process_group()
@@ -582,6 +735,8 @@ def run_ours(args):
     ctx_p.step(th, dt, 3)
     ms_p = time_graph(ctx_p, th, dt, K_c, stream)
     pairwise_steps = K_c / (ms_p / 1e3)
+    n_p = state[0] + 3 + 1
+    pairs_p = q_pts * sum(min(n_p + i, sz.n_src) for i in range(K_c))
     ctx_p.close()
     # plain FP64 (pairwise history sums, as the method states them) and FP64
     # with the separable sums
@@ -687,29 +842,31 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": wl.name + f" mid-scan from step {n0}", "n_dof": sz.n_dof,
-                   "q_lat": sz.q_lat, "q_bot": sz.q_bot, "nnz_a": nnz_a,
-                   "active_sources_first": n_first, "theta": th, "dt": dt,
-                   "precision": "mixed: FP32 history sum and operator values, FP64 state, "
-                                "boundary integrals and Krylov vectors",
-                   "initial_guess": args.guess,
-                   "preconditioner": "fast diagonalization (main solve and bottom projection)",
-                   "l2": "no flush: per-step inputs larger than L2 (operators in SELL-32: "
-                         "~170 MB of FP32 values and indices; 129 MB L2)",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "point_source_evals_per_s": evals,
+        "config": block_config(wl, n0, n_first),
+        "path": {"precision": "mixed: FP32 history sum and operator values, FP64 state, "
+                              "boundary integrals and Krylov vectors",
+                 "history_evaluation": "separable" if sep else "pairwise",
+                 "initial_guess": args.guess,
+                 "preconditioner": "fast diagonalization (main solve and bottom projection)",
+                 "nnz_a": nnz_a,
+                 "l2": "no flush: per-step inputs larger than L2 (operators in SELL-32: "
+                       "~170 MB of FP32 values and indices; 129 MB L2)",
+                 "parallelism": "replicas" if world > 1 else "single"},
+        # precision gain like for like (both separable), then against the
+        # plain FP64 path as the method states the sums (pairwise)
+        "precision_gain_separable": value / (world * fp64_sep_steps),
+        "mixed_over_fp64_pairwise": value / (world * fp64_steps),
+        ("point_source_equivalent_pairs_per_s" if sep else "point_source_evals_per_s"): evals,
+        "history_exponentials_per_s": exps if sep else evals,
+        "point_source_evals_per_s_pairwise_leg": world * pairs_p / (ms_p / 1e3),
         "steps_per_s_other_guess": world * cold_steps,
         "pcg_iters_per_step_other_guess": st_c.pcg_iters_total / K_c,
         "other_guess": "extrapolate" if other == sa.SA_GUESS_EXTRAPOLATE else "previous",
         "steps_per_s_jacobi": world * jacobi_steps,
         "pcg_iters_per_step_jacobi": st_j.pcg_iters_total / K_c,
         "steps_per_s_pairwise_history": world * pairwise_steps,
-        "history_evaluation": "separable" if sep else "pairwise",
-        "fp64_steps_per_s": world * fp64_steps,
-        "fp64_history": "pairwise",
-        "mixed_over_fp64": value / (world * fp64_steps),
+        "fp64_pairwise_steps_per_s": world * fp64_steps,
         "fp64_separable_steps_per_s": world * fp64_sep_steps,
-        "mixed_over_fp64_separable": value / (world * fp64_sep_steps),
         "pcg_iters_per_step": iters_avg, "bot_iters_per_step": bot_avg,
         "stage_ms": stage_avg, "stage_share": shares, "kernels": kernels,
         "roofline": roof,
@@ -724,7 +881,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline_block(wl, n0)
+        line["cpu_baseline"] = cpu_baseline_block(wl, n_first + K // 2)
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -269,10 +269,12 @@ sa_status sa_eval_flux(sa_ctx* ctx, const double* pts, const double* nrm, int n,
  * (its first call, a larger point count); this call never allocates.
  *   pts    n*3 doubles in DEVICE memory (caller-allocated)
  *   T_out  n doubles in DEVICE memory (caller-allocated); NaN outside the patch
- * Same result as sa_eval_T.  Working memory: one fixed file-scope device
- * array of 7 MiB (the current step's source coefficients and the element
- * centres), held by every device that loads the library until the process
- * exits.  Limits: at most 65,536 discretised sources and 131,072 elements;
+ * Evaluates in FP64 in every context: in an SA_FP64 context the result
+ * equals sa_eval_T's to rounding; in an SA_MIXED context (whose sa_eval_T
+ * sums the sources in FP32) the two agree within 1e-4 relative and 0.05 K.
+ * Working memory: one fixed file-scope device array of 5 MiB (the current
+ * step's FP64 source coefficients and the element centres), held by every
+ * device that loads the library until the process exits.  Limits: at most 65,536 discretised sources and 131,072 elements;
  * larger contexts get SA_ERR_ARG with a message.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  All
@@ -306,6 +308,9 @@ typedef struct sa_sizes {
     long long step_index;          /* current n                                       */
     int n_elem;                    /* volume elements                                 */
     int hist_separable;            /* 1: the history sums are evaluated separably     */
+    long long sep_factors;         /* separable sums: factor exponentials per active  */
+                                   /* source and step (sum over the face tiles of     */
+                                   /* rows + columns); 0 for the pairwise sums        */
 } sa_sizes;
 sa_status sa_get_sizes(sa_ctx* ctx, sa_sizes* out);
 

@@ -48,7 +48,7 @@ class sa_sizes(C.Structure):
                 ("q_lat", C.c_int), ("q_bot", C.c_int), ("n_src", C.c_int),
                 ("nnz_mk", C.c_longlong), ("nnz_a", C.c_longlong),
                 ("step_index", C.c_longlong), ("n_elem", C.c_int),
-                ("hist_separable", C.c_int)]
+                ("hist_separable", C.c_int), ("sep_factors", C.c_longlong)]
 
 
 class SAError(RuntimeError):

@@ -1509,6 +1509,9 @@ sa_status sa_get_sizes(sa_ctx* c, sa_sizes* out) {
     out->step_index = c->n_step;
     out->n_elem = c->n_elem;
     out->hist_separable = c->sep.ok ? 1 : 0;
+    out->sep_factors = c->sep.ok ? (long long)c->sep.n_tiles[0] * (64 + c->sep.tj[0]) +
+                                       (long long)c->sep.n_tiles[1] * (64 + c->sep.tj[1])
+                                 : 0;
     return SA_OK;
 }
 

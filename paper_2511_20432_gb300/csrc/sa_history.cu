@@ -73,7 +73,7 @@ __global__ void k_prologue(PrologueArgs a) {
         const double2 p = a.pos[i];
         if (a.s64T) {
             a.s64T[i] = make_double4(p.x, p.y, aI, cI);
-            a.s64F[i] = make_double4(p.x, p.y, aI, gI);
+            if (a.s64F) a.s64F[i] = make_double4(p.x, p.y, aI, gI);
         }
         if (a.s32T) {
             const float sx = (float)p.x, sy = (float)p.y;

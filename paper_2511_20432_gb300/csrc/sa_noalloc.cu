@@ -9,11 +9,16 @@
 // there either fails or fragments the pool).  sa_eval_T may allocate on its
 // first call and when the point count grows; this variant never does.
 //
-// Its per-call working memory (the FP64 source coefficients of the current
-// step and the element centres used for the Newton start) lives in one
-// file-scope __device__ array of fixed size, shared by every call and every
-// context in the process.  Each device that loads the library holds the
-// array until the process exits.
+// Its per-call working memory (the FP64 temperature coefficients of the
+// current step's sources and the element centres used for the Newton start)
+// lives in one file-scope __device__ array of fixed size, shared by every
+// call and every context in the process.  Each device that loads the library
+// holds the array until the process exits.
+//
+// The evaluation runs in FP64 in every context (FP64 source coefficients,
+// FP64 Newton inversion and sums).  In an FP64 context it equals sa_eval_T
+// to rounding; in an SA_MIXED context, whose sa_eval_T sums the sources in
+// FP32, the two agree within the mixed tolerance (1e-4 relative, 0.05 K).
 #include <mutex>
 
 #include "sa_internal.h"
@@ -22,7 +27,7 @@ namespace {
 
 constexpr size_t kSrcBytes = (size_t)SA_NOALLOC_MAX_SOURCES * sizeof(double4);
 constexpr size_t kElemBytes = (size_t)SA_NOALLOC_MAX_ELEMENTS * 3 * sizeof(double);
-constexpr size_t kScratchBytes = 2 * kSrcBytes + kElemBytes;   // 7 MiB
+constexpr size_t kScratchBytes = kSrcBytes + kElemBytes;   // 5 MiB
 
 // In host code this name is only a host-side stand-in; the device address is
 // obtained with cudaGetSymbolAddress below and passed to the kernels.
@@ -88,9 +93,8 @@ extern "C" sa_status sa_eval_T_noalloc(sa_ctx* c, const double* d_pts, int n, do
     e = scratch_address(c->device, &base);
     if (e != cudaSuccess)
         return sa_fail(c, SA_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    double4* evT = (double4*)base;
-    double4* evF = (double4*)(base + kSrcBytes);
-    double* ecent = (double*)(base + 2 * kSrcBytes);
+    double4* evT = (double4*)base;                  // the flux table is not needed here
+    double* ecent = (double*)(base + kSrcBytes);
     cudaStream_t s = c->stream;
     e = launch_elem_centers(c->dp, ecent, s);
     if (e != cudaSuccess) return sa_cuda_fail(c, e, "element centres (no-alloc)");
@@ -99,8 +103,8 @@ extern "C" sa_status sa_eval_T_noalloc(sa_ctx* c, const double* d_pts, int n, do
         const double alpha = c->k / (c->rho * c->cp);
         e = launch_prologue(nullptr, c->n_step, nullptr, c->n_src, c->src_pos.p, c->src_dt, alpha,
                             c->spot_radius * c->spot_radius / (8.0 * alpha),
-                            c->opt.half_space_factor * c->E / (c->rho * c->cp), SA_FP64, evT, evF,
-                            nullptr, nullptr, s);
+                            c->opt.half_space_factor * c->E / (c->rho * c->cp), SA_FP64, evT,
+                            nullptr, nullptr, nullptr, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "prologue (no-alloc)");
         n_active = (int)(c->n_step < c->n_src ? c->n_step : c->n_src);
     }

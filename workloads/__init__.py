@@ -340,6 +340,25 @@ def plate_with_hole(n_el=(48, 48, 8), theta=0.5, n_steps=None) -> Workload:
                     patch, MAT_DEFAULT, scan, dt=5e-6, theta=theta, n_steps=n_steps)
 
 
+def learned_scan(k: int, z=1.0e-3, center=(2.0e-3, 2.0e-3)) -> Scan:
+    """Scan k of the learned warm-start set (seed SEED_BASE + 4000 + k) on
+    the 4 x 4 x 1 mm block: P ~ U(150, 350) W, v ~ U(0.6, 1.6) m/s, hatch
+    spacing ~ U(0.08, 0.12) mm, 5-20 tracks of 2.4 mm centred on the top
+    face, the whole pattern rotated by an angle ~ U(0, pi).  Even k: a
+    meander (laser-off jumps between tracks); odd k: a zig-zag (the track
+    ends joined by laser-on segments, so the laser never stops)."""
+    rng = SplitMix64(SEED_BASE + 4000 + k)
+    P, v = rng.uniform(150.0, 350.0), rng.uniform(0.6, 1.6)
+    hatch, n_tr = rng.uniform(0.08e-3, 0.12e-3), rng.randint(5, 20)
+    angle = rng.uniform(0.0, np.pi)
+    y0 = center[1] - 0.5 * (n_tr - 1) * hatch
+    sc = meander(center[0] - 1.2e-3, center[0] + 1.2e-3, y0, hatch, n_tr, z, P, 0.4, v,
+                 angle=angle, center=center)
+    if k % 2 == 1:
+        sc.seg_on = np.ones_like(sc.seg_on)
+    return sc
+
+
 def _track_lengths(scan):
     """Lengths of the maximal runs of laser-on segments."""
     seg = np.linalg.norm(np.diff(scan.path, axis=0), axis=1)
