@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=2000,
                     help="training pairs of the learned warm-start leg (0: skip the leg)")
     ap.add_argument("--learned-epochs", type=int, default=20)
+    ap.add_argument("--legs", default="all",
+                    help="comma list of the legs after the main timed region to run: stages, "
+                         "variants, e2e, batched, plate, arc, learned, cpu (default all; the "
+                         "form used for profiling one leg)")
     ap.add_argument("--quick", action="store_true",
                     help="main timed region only (no stage, FP64, e2e or CPU legs): "
                          "the form used under ncu")
@@ -429,20 +433,14 @@ def learned_leg(sa, W, wl, state, stream, n_pairs, epochs, K_eval):
     probe = sa.context_from_workload(wl, precision=sa.SA_MIXED)
     n_free = probe.sizes().n_free
     probe.close()
-    n_scans = 4
+    n_scans = max(4, min(50, n_pairs // 1000))
     per = max(1, n_pairs // n_scans)
     X = torch.empty((per * n_scans, len(idx)), dtype=torch.bfloat16, device="cuda")
     Y = torch.empty((per * n_scans, n_free), dtype=torch.bfloat16, device="cuda")
     t0 = time.perf_counter()
     row = 0
     for k in range(n_scans):
-        rng = W.SplitMix64(W.SEED_BASE + 4000 + k)
-        P, v = rng.uniform(150.0, 350.0), rng.uniform(0.6, 1.6)
-        hatch, n_tr = rng.uniform(0.08e-3, 0.12e-3), rng.randint(5, 20)
-        angle = rng.uniform(0.0, np.pi)
-        y0 = 2.0e-3 - 0.5 * (n_tr - 1) * hatch
-        scan = W.meander(0.8e-3, 3.2e-3, y0, hatch, n_tr, 1.0e-3, P, 0.4, v, angle=angle,
-                         center=(2.0e-3, 2.0e-3))
+        scan = W.learned_scan(k)
         wtr = W.Workload(f"train_{k}", wl.patch, wl.material, scan, dt=dt, theta=th, n_steps=10 ** 6)
         c = sa.context_from_workload(wtr, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
         c.step(th, dt, 200)
@@ -535,6 +533,12 @@ def batched_leg(sa, W, stream, n_inst, n_steps, rank=0, world=1, dist=None):
     setup_s = time.perf_counter() - t0
     th, dt = wls[0].theta, wls[0].dt
     b.step(th, dt, 3)
+    # launch shapes from the project's tuner (history tiles, solve grid),
+    # cached by batch sizes in the build folder
+    t1 = time.perf_counter()
+    shapes = b.tune(os.path.join(ROOT, "paper_2511_20432_gb300", "_build", "batch_shapes.jsonl"),
+                    at_step=max(1, n_steps // 2))
+    tune_s = time.perf_counter() - t1
     sz = [c.sizes() for c in ctxs]
     K = n_steps - 3
     pairs = sum((z.q_lat + z.q_bot) * sum(min(n, z.n_src) for n in range(4, n_steps + 1)) for z in sz)
@@ -544,8 +548,10 @@ def batched_leg(sa, W, stream, n_inst, n_steps, rank=0, world=1, dist=None):
     pairs = sum_over_ranks(pairs, dist, "cuda")
     m_it, b_it = b.iters()
     out = {"instances": n_inst, "steps": n_steps, "timed_steps": K, "setup_s": setup_s,
+           "tuned_shapes": shapes, "tune_s": tune_s,
            "ms_per_step": ms / K, "instance_steps_per_s": n_inst * K / (ms / 1e3),
-           "point_source_evals_per_s": pairs / (ms / 1e3),
+           ("point_source_equivalent_pairs_per_s" if shapes["hist_separable"] else
+            "point_source_evals_per_s"): pairs / (ms / 1e3),
            "total_control_variables": int(sum_over_ranks(sum(z.n_dof for z in sz), dist, "cuda")),
            "total_boundary_points": int(sum_over_ranks(sum(z.q_lat + z.q_bot for z in sz), dist, "cuda")),
            "last_step_main_iters_max": int(max_over_ranks(int(m_it.max()), dist, "cuda")),
@@ -661,6 +667,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ms = time_graph(ctx, th, dt, K, stream)
+    stats = ctx.step(th, dt, 0)                # counters accumulated over the timed steps
     t_w0 = time.perf_counter()
     K_w = 0
     while time.perf_counter() - t_w0 < 1.0:
@@ -673,7 +680,6 @@ def run_ours(args):
     ms = max_over_ranks(ms, dist, "cuda")
     if clocks.get("sm_mhz"):
         clocks["ms_x_sm_mhz_per_step"] = ms / K * clocks["sm_mhz"]
-    stats = ctx.step(th, dt, 0)                # counters accumulated over the timed steps
     iters_avg = stats.pcg_iters_total / K
     bot_avg = stats.bot_iters_total / K
     value = world * K / (ms / 1e3)
@@ -712,75 +718,82 @@ def run_ours(args):
     pairs_t = q_pts * (min(state[0] + 3 + K_t // 2, sz.n_src))
     ctx_t.close()
 
-    # ---- the other initial guess, Jacobi, and the plain FP64 path
+    want = lambda leg: args.legs == "all" or leg in args.legs.split(",")
     K_c = min(K, 60)
+    cold_steps = jacobi_steps = pairwise_steps = fp64_steps = fp64_sep_steps = float("nan")
+    st_c = st_j = None
+    pairs_p, ms_p = 0, float("nan")
     other = sa.SA_GUESS_EXTRAPOLATE if guess == sa.SA_GUESS_PREVIOUS else sa.SA_GUESS_PREVIOUS
-    ctx_c = fresh(prec, other, use_graph=1)
-    ctx_c.step(th, dt, 3)
-    ctx_c.step(th, dt, 0)
-    ms_c = time_graph(ctx_c, th, dt, K_c, stream)
-    st_c = ctx_c.step(th, dt, 0)
-    cold_steps = K_c / (ms_c / 1e3)
-    ctx_c.close()
-    # the same path with the Jacobi preconditioner
-    ctx_j = fresh(prec, guess, use_graph=1, precond=sa.SA_PRECOND_JACOBI)
-    ctx_j.step(th, dt, 3)
-    ctx_j.step(th, dt, 0)
-    ms_j = time_graph(ctx_j, th, dt, K_c, stream)
-    st_j = ctx_j.step(th, dt, 0)
-    jacobi_steps = K_c / (ms_j / 1e3)
-    ctx_j.close()
-    # the same path with the pairwise history sums
-    ctx_p = fresh(prec, guess, use_graph=1, hist_mode=sa.SA_HIST_PAIRWISE)
-    ctx_p.step(th, dt, 3)
-    ms_p = time_graph(ctx_p, th, dt, K_c, stream)
-    pairwise_steps = K_c / (ms_p / 1e3)
-    n_p = state[0] + 3 + 1
-    pairs_p = q_pts * sum(min(n_p + i, sz.n_src) for i in range(K_c))
-    ctx_p.close()
-    # plain FP64 (pairwise history sums, as the method states them) and FP64
-    # with the separable sums
-    K64 = min(K, 12)
-    ctx64 = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1, hist_mode=sa.SA_HIST_PAIRWISE)
-    ctx64.step(th, dt, 2)
-    ms64 = time_graph(ctx64, th, dt, K64, stream)
-    fp64_steps = K64 / (ms64 / 1e3)
-    ctx64.close()
-    ctx64s = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1, hist_mode=sa.SA_HIST_SEPARABLE)
-    ctx64s.step(th, dt, 2)
-    ms64s = time_graph(ctx64s, th, dt, K_c, stream)
-    fp64_sep_steps = K_c / (ms64s / 1e3)
-    ctx64s.close()
+    if want("variants"):
+        # ---- the other initial guess, Jacobi, and the plain FP64 path
+        ctx_c = fresh(prec, other, use_graph=1)
+        ctx_c.step(th, dt, 3)
+        ctx_c.step(th, dt, 0)
+        ms_c = time_graph(ctx_c, th, dt, K_c, stream)
+        st_c = ctx_c.step(th, dt, 0)
+        cold_steps = K_c / (ms_c / 1e3)
+        ctx_c.close()
+        # the same path with the Jacobi preconditioner
+        ctx_j = fresh(prec, guess, use_graph=1, precond=sa.SA_PRECOND_JACOBI)
+        ctx_j.step(th, dt, 3)
+        ctx_j.step(th, dt, 0)
+        ms_j = time_graph(ctx_j, th, dt, K_c, stream)
+        st_j = ctx_j.step(th, dt, 0)
+        jacobi_steps = K_c / (ms_j / 1e3)
+        ctx_j.close()
+        # the same path with the pairwise history sums
+        ctx_p = fresh(prec, guess, use_graph=1, hist_mode=sa.SA_HIST_PAIRWISE)
+        ctx_p.step(th, dt, 3)
+        ms_p = time_graph(ctx_p, th, dt, K_c, stream)
+        pairwise_steps = K_c / (ms_p / 1e3)
+        n_p = state[0] + 3 + 1
+        pairs_p = q_pts * sum(min(n_p + i, sz.n_src) for i in range(K_c))
+        ctx_p.close()
+        # plain FP64 (pairwise history sums, as the method states them) and FP64
+        # with the separable sums
+        K64 = min(K, 12)
+        ctx64 = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1, hist_mode=sa.SA_HIST_PAIRWISE)
+        ctx64.step(th, dt, 2)
+        ms64 = time_graph(ctx64, th, dt, K64, stream)
+        fp64_steps = K64 / (ms64 / 1e3)
+        ctx64.close()
+        ctx64s = fresh(sa.SA_FP64, sa.SA_GUESS_PREVIOUS, use_graph=1, hist_mode=sa.SA_HIST_SEPARABLE)
+        ctx64s.step(th, dt, 2)
+        ms64s = time_graph(ctx64s, th, dt, K_c, stream)
+        fp64_sep_steps = K_c / (ms64s / 1e3)
+        ctx64s.close()
 
     # ---- end to end through the public API with host buffers -------------------
-    rng = np.random.default_rng(3)
-    mon = np.column_stack([rng.uniform(0.2e-3, 3.8e-3, N_MONITOR), rng.uniform(0.2e-3, 3.8e-3, N_MONITOR),
-                           rng.uniform(0.5e-3, 1.0e-3, N_MONITOR)])
-    mon = np.ascontiguousarray(mon)
-    K_e = min(K, 100)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(K_e):
-        ctx.step(th, dt, 1)                     # synchronous: status read back
-        T_mon = ctx.eval_T(mon)                 # host points in, host temperatures out
-    t_e2e = time.perf_counter() - t0
-    e2e = world * K_e / t_e2e
-    assert np.isfinite(T_mon).all()
+    e2e = None
+    if want("e2e"):
+        rng = np.random.default_rng(3)
+        mon = np.column_stack([rng.uniform(0.2e-3, 3.8e-3, N_MONITOR), rng.uniform(0.2e-3, 3.8e-3, N_MONITOR),
+                               rng.uniform(0.5e-3, 1.0e-3, N_MONITOR)])
+        mon = np.ascontiguousarray(mon)
+        K_e = min(K, 100)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K_e):
+            ctx.step(th, dt, 1)                     # synchronous: status read back
+            T_mon = ctx.eval_T(mon)                 # host points in, host temperatures out
+        t_e2e = time.perf_counter() - t0
+        e2e = world * K_e / t_e2e
+        assert np.isfinite(T_mon).all()
 
     # ---- the batched sweep (256 instances, 2000 steps) ------------------------------
     batched = (batched_leg(sa, W, stream, 256, args.batch_steps, rank, world, dist)
-               if args.batch_steps > 3 else None)
+               if args.batch_steps > 3 and want("batched") else None)
 
     # ---- the plate with a hole ---------------------------------------------------
-    plate = plate_leg(sa, W, stream, 1000, min(K, 300)) if world == 1 else None
+    plate = plate_leg(sa, W, stream, 1000, min(K, 300)) if world == 1 and want("plate") else None
 
     # ---- the quarter-cylinder part: heat-loss rates along the top arc ------------
-    qcyl = quarter_cylinder_leg(sa, W, stream) if world == 1 else None
-    qcon = quarter_cylinder_leg(sa, W, stream, "contour") if world == 1 else None
+    qcyl = quarter_cylinder_leg(sa, W, stream) if world == 1 and want("arc") else None
+    qcon = quarter_cylinder_leg(sa, W, stream, "contour") if world == 1 and want("arc") else None
 
     # ---- learned warm start (bounded: a few thousand training pairs) -------------
     learned = None
-    if args.learned_pairs > 0 and world == 1:
+    if args.learned_pairs > 0 and world == 1 and want("learned"):
         learned = learned_leg(sa, W, wl, state, stream, args.learned_pairs, args.learned_epochs,
                               min(K, 100))
 
@@ -860,18 +873,18 @@ def run_ours(args):
         "history_exponentials_per_s": exps if sep else evals,
         "point_source_evals_per_s_pairwise_leg": world * pairs_p / (ms_p / 1e3),
         "steps_per_s_other_guess": world * cold_steps,
-        "pcg_iters_per_step_other_guess": st_c.pcg_iters_total / K_c,
+        "pcg_iters_per_step_other_guess": st_c.pcg_iters_total / K_c if st_c else None,
         "other_guess": "extrapolate" if other == sa.SA_GUESS_EXTRAPOLATE else "previous",
         "steps_per_s_jacobi": world * jacobi_steps,
-        "pcg_iters_per_step_jacobi": st_j.pcg_iters_total / K_c,
+        "pcg_iters_per_step_jacobi": st_j.pcg_iters_total / K_c if st_j else None,
         "steps_per_s_pairwise_history": world * pairwise_steps,
         "fp64_pairwise_steps_per_s": world * fp64_steps,
         "fp64_separable_steps_per_s": world * fp64_sep_steps,
         "pcg_iters_per_step": iters_avg, "bot_iters_per_step": bot_avg,
         "stage_ms": stage_avg, "stage_share": shares, "kernels": kernels,
         "roofline": roof,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
-                "d2h_bytes_per_step": N_MONITOR * 8 + 96},
+        "e2e": ({"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
+                 "d2h_bytes_per_step": N_MONITOR * 8 + 96} if e2e is not None else None),
         "plate_with_hole": plate,
         "quarter_cylinder_single_source": qcyl,
         "quarter_cylinder_contour": qcon,
@@ -880,12 +893,24 @@ def run_ours(args):
         "gpu_launches": launches_per_step * K,
         "clocks": clocks,
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and want("cpu"):
         line["cpu_baseline"] = cpu_baseline_block(wl, n_first + K // 2)
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(finite(line)))
     if dist:
         dist.destroy_process_group()
+
+
+def finite(o):
+    """The line with NaN / infinite numbers (legs not run) as null."""
+    import math
+    if isinstance(o, dict):
+        return {k: finite(v) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [finite(v) for v in o]
+    if isinstance(o, float) and not math.isfinite(o):
+        return None
+    return o
 
 
 def main():

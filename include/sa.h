@@ -439,6 +439,35 @@ sa_status sa_batch_get_iters(sa_batch* b, int* main_iters, int* bottom_iters);
  * choice to the JSON-lines file cache_path (NULL: no cache), keyed by the
  * batch sizes; a cached choice is reused without timing (*best_ms = -1). */
 sa_status sa_batch_autotune(sa_batch* b, const char* cache_path, int* P, int* NW, double* best_ms);
+/* Launch shapes of a batch: the history sums (separable product: tile
+ * widths of the lateral and bottom tiles, 64 rows each, and units of sources
+ * per tile; pairwise sums: points per lane and warps) and the number of
+ * blocks of the batched solves (one 1024-thread block per SM at most). */
+typedef struct sa_batch_shapes {
+    int hist_separable;            /* 1: separable product, 0: pairwise sums          */
+    int tj_lat, tj_bot;            /* separable: tile widths (64, 48 or 32)           */
+    int units_per_tile;            /* separable: source units per tile (1, 2 or 4)    */
+    int hist_P, hist_NW;           /* pairwise: points per lane, warps per block      */
+    int pcg_grid;                  /* blocks of the batched PCG launches              */
+    double step_ms;                /* sa_batch_tune: time of one step with the chosen */
+                                   /* solve grid (ms); -1 when read from the cache    */
+} sa_batch_shapes;
+/* Tuner of the batch's launch shapes (this project's, no paper counterpart):
+ * times every separable tile shape (3 x 3 widths x 1, 2, 4 units; or the
+ * pairwise tiles when the faces are not rectangles) on the batch's data with
+ * the sources active at step at_step (0: the next step; the work grows with
+ * the step, so a mid-run step represents a run), then the solve grid (all SMs, 3/4, 1/2) over whole steps
+ * from a saved copy of the batch's state, which is restored afterwards (the
+ * simulation does not advance).  The choice is kept by the batch, written to
+ * *out and appended to the JSON-lines file cache_path (NULL: no cache),
+ * keyed by the batch's sizes and at_step; a cached choice is applied without
+ * timing (step_ms = -1).  Needs a batch that has stepped (SA_ERR_STATE);
+ * errors SA_ERR_ARG (at_step < 0), SA_ERR_OOM, SA_ERR_CUDA.  Synchronous. */
+sa_status sa_batch_tune(sa_batch* b, const char* cache_path, long long at_step,
+                        sa_batch_shapes* out);
+/* The shapes the batch runs with (out: caller-owned).  Errors: SA_ERR_ARG,
+ * SA_ERR_STATE (before the first step). */
+sa_status sa_batch_get_shapes(sa_batch* b, sa_batch_shapes* out);
 const char* sa_batch_last_error(const sa_batch* b);
 void sa_batch_destroy(sa_batch* b);
 

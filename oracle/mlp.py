@@ -34,18 +34,25 @@ def forward(params, X):
     return h, cache
 
 
-def loss_and_grads(params, X, Y):
+def loss_and_grads(params, X, Y, with_deltas=False):
+    """Loss and per-layer (dW, db); with_deltas also returns, per layer, the
+    gradient with respect to its pre-activation and its input (g_l, h_in_l),
+    the factors of dW_l = g_l^T h_in_l."""
     out, cache = forward(params, X)
     B = X.shape[0]
     diff = out - Y
     loss = 0.5 * np.sum(diff * diff) / B
     g = diff / B                                   # dL/d(out)
     grads = [None] * len(params)
+    deltas = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         h_in, z = cache[li]
         if li < len(params) - 1:
             g = g * dsilu(z)                       # through the activation
         W, _ = params[li]
         grads[li] = (g.T @ h_in, g.sum(axis=0))    # dW, db
+        deltas[li] = (g, h_in)
         g = g @ W                                  # to the previous layer
+    if with_deltas:
+        return loss, grads, deltas
     return loss, grads

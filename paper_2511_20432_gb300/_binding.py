@@ -51,6 +51,15 @@ class sa_sizes(C.Structure):
                 ("hist_separable", C.c_int), ("sep_factors", C.c_longlong)]
 
 
+class sa_batch_shapes(C.Structure):
+    _fields_ = [("hist_separable", C.c_int), ("tj_lat", C.c_int), ("tj_bot", C.c_int),
+                ("units_per_tile", C.c_int), ("hist_P", C.c_int), ("hist_NW", C.c_int),
+                ("pcg_grid", C.c_int), ("step_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class SAError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_name(status)}: {msg}")
@@ -97,6 +106,8 @@ def _load():
         "sa_batch_get_field": (I, [P, I, I, P, LL]),
         "sa_batch_get_iters": (I, [P, P, P]),
         "sa_batch_autotune": (I, [P, C.c_char_p, C.POINTER(I), C.POINTER(I), C.POINTER(D)]),
+        "sa_batch_tune": (I, [P, C.c_char_p, LL, C.POINTER(sa_batch_shapes)]),
+        "sa_batch_get_shapes": (I, [P, C.POINTER(sa_batch_shapes)]),
         "sa_batch_last_error": (C.c_char_p, [P]),
         "sa_batch_destroy": (V, [P]),
         "sa_destroy": (V, [P]),
@@ -396,6 +407,19 @@ class Batch:
         path = cache_path.encode() if cache_path else None
         self._check(lib.sa_batch_autotune(self.ptr, path, C.byref(P), C.byref(W), C.byref(ms)))
         return P.value, W.value, ms.value
+
+    def tune(self, cache_path=None, at_step=0):
+        """sa_batch_tune: history tile shapes (sources active at at_step; 0:
+        the next step) and solve grid; returns a dict."""
+        sh = sa_batch_shapes()
+        path = cache_path.encode() if cache_path else None
+        self._check(lib.sa_batch_tune(self.ptr, path, int(at_step), C.byref(sh)))
+        return sh.as_dict()
+
+    def shapes(self):
+        sh = sa_batch_shapes()
+        self._check(lib.sa_batch_get_shapes(self.ptr, C.byref(sh)))
+        return sh.as_dict()
 
 
 def selftest_waits():

@@ -1307,4 +1307,262 @@ sa_status sa_batch_autotune(sa_batch* b, const char* cache_path, int* P_out, int
     return SA_OK;
 }
 
+
+// Tuner of the launch shapes the batch runs with: the history sums (the
+// separable product's tile widths per face kind and units per tile, or the
+// pairwise tile when the faces are not rectangles) and the number of blocks
+// of the batched solves.  History shapes are timed alone on the batch's data
+// at its current step (their outputs are recomputed by every step); solve
+// grids are timed over whole steps, with the batch's state (T^, F, step
+// index) saved before and restored after, so tuning does not advance the
+// simulation.  The choice is appended to the JSON-lines file cache_path
+// (NULL: no cache) under a key of the batch's sizes and reused from there.
+}  // extern "C"
+
+namespace {
+
+bool cache_lookup(const char* path, const char* key, sa_batch_shapes* sh) {
+    if (!path) return false;
+    std::ifstream f(path);
+    std::string line;
+    auto num = [&](const std::string& ln, const char* name, size_t from) -> int {
+        const size_t k = ln.find(name, from);
+        return k == std::string::npos ? -1 : atoi(ln.c_str() + k + strlen(name));
+    };
+    while (std::getline(f, line)) {
+        const size_t k = line.find(std::string("\"") + key + "\"");
+        if (k == std::string::npos) continue;
+        sa_batch_shapes t{};
+        t.hist_separable = num(line, "\"sep\": ", k);
+        t.tj_lat = num(line, "\"tj_lat\": ", k);
+        t.tj_bot = num(line, "\"tj_bot\": ", k);
+        t.units_per_tile = num(line, "\"units\": ", k);
+        t.hist_P = num(line, "\"P\": ", k);
+        t.hist_NW = num(line, "\"NW\": ", k);
+        t.pcg_grid = num(line, "\"grid\": ", k);
+        const bool tj_ok = (t.tj_lat == 64 || t.tj_lat == 48 || t.tj_lat == 32) &&
+                           (t.tj_bot == 64 || t.tj_bot == 48 || t.tj_bot == 32);
+        const bool ok = t.pcg_grid >= 1 && (t.hist_P == 1 || t.hist_P == 2 || t.hist_P == 4) &&
+                        (t.hist_NW == 4 || t.hist_NW == 8) &&
+                        (t.hist_separable == 0 ||
+                         (t.hist_separable == 1 && tj_ok && t.units_per_tile >= 1 && t.units_per_tile <= 8));
+        if (!ok) continue;
+        *sh = t;
+        sh->step_ms = -1.0;
+        return true;
+    }
+    return false;
+}
+
+void fill_shapes(const sa_batch* b, sa_batch_shapes* out, double ms) {
+    out->hist_separable = b->sep.ok ? 1 : 0;
+    out->tj_lat = b->sep.tj[0];
+    out->tj_bot = b->sep.tj[1];
+    out->units_per_tile = b->sep.ok ? b->sep.s_max : 0;
+    out->hist_P = b->hist_P;
+    out->hist_NW = b->hist_W;
+    out->pcg_grid = b->pcg_grid;
+    out->step_ms = ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+sa_status sa_batch_get_shapes(sa_batch* b, sa_batch_shapes* out) {
+    if (!b || !out) return SA_ERR_ARG;
+    if (!b->built) return bfail(b, SA_ERR_STATE, "batch has not stepped");
+    fill_shapes(b, out, 0.0);
+    return SA_OK;
+}
+
+sa_status sa_batch_tune(sa_batch* b, const char* cache_path, long long at_step,
+                        sa_batch_shapes* out) {
+    if (!b || !out || at_step < 0) return SA_ERR_ARG;
+    if (b->poisoned) return bfail(b, SA_ERR_STATE, "batch poisoned: %s", b->err.c_str());
+    if (!b->built) return bfail(b, SA_ERR_STATE, "step the batch once before tuning");
+    char key[200];
+    const long long n_hist = at_step > 0 ? at_step : b->n_step + 1;
+    snprintf(key, sizeof(key), "batch:%d:%d:%d:%d:%d:%d:%d:%lld", b->n_inst, b->q_lat, b->q_bot,
+             b->n_src, b->n_dof, b->opt.precision, b->num_sms, n_hist);
+    cudaStream_t s = b->stream;
+    auto drop_graph = [&]() {
+        if (b->graph_exec) {
+            cudaGraphExecDestroy(b->graph_exec);
+            b->graph_exec = nullptr;
+        }
+    };
+    sa_batch_shapes c{};
+    if (cache_lookup(cache_path, key, &c) && (c.hist_separable == 1) == b->sep.ok) {
+        if (b->sep.ok && (c.tj_lat != b->sep.tj[0] || c.tj_bot != b->sep.tj[1] ||
+                          c.units_per_tile != b->sep.s_max) &&
+            !sep_batch_plan(b->inst, b->qlat_off, b->qbot_off, b->opt.precision, b->sep, c.tj_lat,
+                            c.tj_bot, c.units_per_tile))
+            return bfail(b, SA_ERR_OOM, "separable plan of the cached shapes");
+        b->hist_P = c.hist_P;
+        b->hist_W = c.hist_NW;
+        b->pcg_grid = std::min(c.pcg_grid, b->num_sms);
+        drop_graph();
+        fill_shapes(b, out, -1.0);
+        return SA_OK;
+    }
+    // the history shapes are timed with the sources active at step n_hist
+    // (the prologue reads the step index from the status block, restored
+    // below)
+    const double alpha = b->k / (b->rho * b->cp);
+    DevStatus st_keep;
+    B_CUDA(b, cudaMemcpyAsync(&st_keep, b->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    B_CUDA(b, cudaStreamSynchronize(s));
+    const long long n_pro = n_hist - 1;
+    B_CUDA(b, cudaMemcpyAsync(&b->st.p->n, &n_pro, sizeof(long long), cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_prologue_batch(b->st.p, b->n_src, b->n_inst, b->d_src_inst.p, b->d_src_off.p,
+                                          b->d_n_src.p, b->d_coefE.p, b->d_r2_8a.p, b->d_n_active.p,
+                                          b->src_pos.p, b->dt, alpha, b->opt.precision, b->s64T.p,
+                                          b->s64F.p, b->s32T.p, b->s32F.p, s);
+    if (e != cudaSuccess) return bcuda(b, e, "tuner prologue");
+    cudaEvent_t e0, e1;
+    B_CUDA(b, cudaEventCreate(&e0));
+    B_CUDA(b, cudaEventCreate(&e1));
+    // median of five timed repetitions (after one untimed) of enqueue()
+    auto time_it = [&](auto enqueue, double* ms) -> sa_status {
+        std::vector<float> t;
+        for (int rep = 0; rep < 6; ++rep) {
+            B_CUDA(b, cudaEventRecord(e0, s));
+            cudaError_t ee = enqueue();
+            if (ee != cudaSuccess) return bcuda(b, ee, "tuner launch");
+            B_CUDA(b, cudaEventRecord(e1, s));
+            B_CUDA(b, cudaEventSynchronize(e1));
+            float v = 0.f;
+            B_CUDA(b, cudaEventElapsedTime(&v, e0, e1));
+            if (rep > 0) t.push_back(v);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return SA_OK;
+    };
+    sa_status st = SA_OK;
+    // ---- history shapes
+    if (b->sep.ok) {
+        double best = 1e300;
+        int bl = b->sep.tj[0], bb = b->sep.tj[1], bu = b->sep.s_max;
+        for (int units : {1, 2, 4})
+            for (int tl : {64, 48, 32})
+                for (int tb : {64, 48, 32}) {
+                    if (st) break;
+                    if (!sep_batch_plan(b->inst, b->qlat_off, b->qbot_off, b->opt.precision, b->sep, tl,
+                                        tb, units)) {
+                        st = bfail(b, SA_ERR_OOM, "separable plan (%d, %d, %d)", tl, tb, units);
+                        break;
+                    }
+                    double ms = 0.0;
+                    st = time_it([&]() {
+                        return launch_sep_batch(b->sep, b->opt.precision, b->st.p, b->d_n_active.p,
+                                                b->d_src_off.p, b->s32F.p, b->s32T.p, b->s64F.p,
+                                                b->s64T.p, b->s_lat.p, b->tt_bot.p, s);
+                    }, &ms);
+                    if (st) break;
+                    if (ms < best) {
+                        best = ms;
+                        bl = tl;
+                        bb = tb;
+                        bu = units;
+                    }
+                    if (st) break;
+                }
+        if (!st && !sep_batch_plan(b->inst, b->qlat_off, b->qbot_off, b->opt.precision, b->sep, bl, bb, bu))
+            st = bfail(b, SA_ERR_OOM, "separable plan of the tuned shapes");
+    } else {
+        const int shapes[5][2] = {{1, 4}, {2, 4}, {2, 8}, {4, 4}, {4, 8}};
+        double best = 1e300;
+        int bp = b->hist_P, bw = b->hist_W;
+        for (auto& sh : shapes) {
+            double ms = 0.0;
+            st = time_it([&]() {
+                return launch_history_batch(b->opt.precision, sh[0], sh[1], b->st.p, b->q_lat, b->q_bot,
+                                            b->lat32.p, b->bot32.p, b->lat64.p, b->bot64.p, b->s32F.p,
+                                            b->s32T.p, b->s64F.p, b->s64T.p, b->s_lat.p, b->tt_bot.p,
+                                            b->n_inst, b->d_qlat_off.p, b->d_qbot_off.p,
+                                            b->d_src_off.p, b->d_n_active.p, s);
+            }, &ms);
+            if (st) break;
+            if (ms < best) {
+                best = ms;
+                bp = sh[0];
+                bw = sh[1];
+            }
+        }
+        b->hist_P = bp;
+        b->hist_W = bw;
+    }
+    B_CUDA(b, cudaMemcpyAsync(b->st.p, &st_keep, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+    B_CUDA(b, cudaStreamSynchronize(s));
+    drop_graph();
+    // ---- grid of the batched solves, over whole steps from a saved state
+    double best_step = 1e300;
+    if (!st) {
+        DBuf<double> T_save, F_save;
+        DevStatus st_save;
+        const long long n_save = b->n_step;
+        if (T_save.alloc(b->That.n) != cudaSuccess || F_save.alloc(b->F0.n) != cudaSuccess) {
+            cudaGetLastError();
+            st = bfail(b, SA_ERR_OOM, "tuner state copy");
+        }
+        if (!st) {
+            B_CUDA(b, cudaMemcpyAsync(T_save.p, b->That.p, sizeof(double) * b->That.n, cudaMemcpyDeviceToDevice, s));
+            B_CUDA(b, cudaMemcpyAsync(F_save.p, b->F0.p, sizeof(double) * b->F0.n, cudaMemcpyDeviceToDevice, s));
+            B_CUDA(b, cudaMemcpyAsync(&st_save, b->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+            B_CUDA(b, cudaStreamSynchronize(s));
+        }
+        auto restore = [&]() -> sa_status {
+            B_CUDA(b, cudaMemcpyAsync(b->That.p, T_save.p, sizeof(double) * b->That.n, cudaMemcpyDeviceToDevice, s));
+            B_CUDA(b, cudaMemcpyAsync(b->F0.p, F_save.p, sizeof(double) * b->F0.n, cudaMemcpyDeviceToDevice, s));
+            B_CUDA(b, cudaMemcpyAsync(b->st.p, &st_save, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+            B_CUDA(b, cudaStreamSynchronize(s));
+            b->n_step = n_save;
+            return SA_OK;
+        };
+        int best_grid = b->pcg_grid;
+        const int G = b->num_sms;
+        int grids[3] = {G, std::max(1, (3 * G) / 4), std::max(1, G / 2)};
+        for (int gi = 0; gi < 3 && !st; ++gi) {
+            if (gi > 0 && grids[gi] == grids[gi - 1]) continue;
+            b->pcg_grid = grids[gi];
+            drop_graph();
+            st = sa_batch_step(b, b->theta, b->dt, 1, nullptr);        // capture, warm
+            if (!st) {
+                B_CUDA(b, cudaEventRecord(e0, s));
+                st = sa_batch_step(b, b->theta, b->dt, 3, nullptr);
+                B_CUDA(b, cudaEventRecord(e1, s));
+                B_CUDA(b, cudaEventSynchronize(e1));
+            }
+            if (!st) {
+                float v = 0.f;
+                B_CUDA(b, cudaEventElapsedTime(&v, e0, e1));
+                DevStatus h;
+                B_CUDA(b, cudaMemcpy(&h, b->st.p, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+                // a shape whose solves gave up (device wait limit) is not chosen
+                if (!(h.err & SA_DEV_TIMEOUT) && v / 3.0 < best_step) {
+                    best_step = v / 3.0;
+                    best_grid = grids[gi];
+                }
+            }
+            if (!st) st = restore();
+        }
+        b->pcg_grid = best_grid;
+        drop_graph();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    fill_shapes(b, out, best_step);
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        f << "{\"key\": \"" << key << "\", \"sep\": " << out->hist_separable << ", \"tj_lat\": "
+          << out->tj_lat << ", \"tj_bot\": " << out->tj_bot << ", \"units\": " << out->units_per_tile
+          << ", \"P\": " << out->hist_P << ", \"NW\": " << out->hist_NW << ", \"grid\": "
+          << out->pcg_grid << ", \"step_ms\": " << best_step << "}\n";
+    }
+    return SA_OK;
+}
+
 }  // extern "C"

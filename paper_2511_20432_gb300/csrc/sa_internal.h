@@ -507,7 +507,8 @@ cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s);
 // shifted to the batch's point offsets, one unit per tile.  False when an
 // instance has no separable plan.
 bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& qlat_off,
-                    const std::vector<int>& qbot_off, int precision, SepPlan& P);
+                    const std::vector<int>& qbot_off, int precision, SepPlan& P, int tj_lat = 0,
+                    int tj_bot = 0, int s_max = 1);
 cudaError_t launch_sep_batch(const SepPlan& P, int precision, DevStatus* st, const int* n_active,
                              const int* src_off, const float4* s32F, const float4* s32T,
                              const double4* s64F, const double4* s64T, double* s_lat,

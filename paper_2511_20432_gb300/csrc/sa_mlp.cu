@@ -6,9 +6,10 @@
 //
 //   x -> silu(W1 x + b1) -> silu(W2 h + b2) -> silu(W3 h + b3) -> W4 h + b4
 //
-// Dense layers run on the tensor cores (mma.sync m16n8k16, BF16 inputs,
-// FP32 accumulators); bias, activation, loss and Adam are elementwise
-// kernels.  Training: mean squared error, Adam on FP32 master weights with
+// Dense layers of a batch run on the tensor cores (mma.sync m16n8k16, BF16
+// inputs, FP32 accumulators); one sample (the warm start inside a step) runs
+// as four memory-bound GEMVs; bias, activation, loss and Adam are
+// elementwise kernels.  Training: mean squared error, Adam on FP32 master weights with
 // BF16 copies for the GEMMs.
 #include <cuda_bf16.h>
 
@@ -142,6 +143,68 @@ __global__ void k_bias_act(long long rows, int cols, float* Z, const float* b, b
     if (H) H[i] = __float2bfloat16(act ? silu(z) : z);
 }
 
+// Batch-1 forward (the warm start inside a theta-step): each layer is a
+// matrix-vector product whose time is the read of its BF16 weights (21 M
+// parameters, ~43 MB for the block's network), so it runs as a GEMV on the
+// CUDA cores, not as a 64-row tensor-core tile of which 63 rows would be
+// padding.  ROWS output rows per warp; each lane reads 4 weights (8 bytes)
+// per load along the row, FP32 products and sums, a warp butterfly; then the
+// bias and, on hidden layers, SiLU rounded to BF16 as the batched path
+// stores it.  Z gets the pre-activation (FP32).
+template <int ROWS>
+__global__ void __launch_bounds__(256) k_gemv(int out, int in, const bf16* __restrict__ W,
+                                              const float* __restrict__ bias,
+                                              const bf16* __restrict__ x, float* __restrict__ Z,
+                                              bf16* __restrict__ H) {
+    const int lane = threadIdx.x & 31;
+    const long long r0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * ROWS;
+    if (r0 >= out) return;
+    float acc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r] = 0.f;
+    if ((in & 3) == 0) {
+        const int n4 = in >> 2;
+        const uint2* xv = reinterpret_cast<const uint2*>(x);
+        for (int k = lane; k < n4; k += 32) {
+            const uint2 xu = __ldg(xv + k);
+            const float2 x01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xu.x));
+            const float2 x23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&xu.y));
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                if (r0 + r >= out) break;
+                const uint2 wu = __ldg(reinterpret_cast<const uint2*>(W + (r0 + r) * (long long)in) + k);
+                const float2 w01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wu.x));
+                const float2 w23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wu.y));
+                acc[r] = fmaf(w01.x, x01.x, acc[r]);
+                acc[r] = fmaf(w01.y, x01.y, acc[r]);
+                acc[r] = fmaf(w23.x, x23.x, acc[r]);
+                acc[r] = fmaf(w23.y, x23.y, acc[r]);
+            }
+        }
+    } else {
+        for (int k = lane; k < in; k += 32) {
+            const float xk = __bfloat162float(x[k]);
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                if (r0 + r >= out) break;
+                acc[r] = fmaf(__bfloat162float(W[(r0 + r) * (long long)in + k]), xk, acc[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane != 0) return;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        if (r0 + r >= out) break;
+        const float z = acc[r] + bias[r0 + r];
+        Z[r0 + r] = z;
+        if (H) H[r0 + r] = __float2bfloat16(silu(z));
+    }
+}
+
 // dZ = dH * silu'(Z) (in place on the FP32 gradient), BF16 copy for the GEMMs.
 __global__ void k_act_bwd(long long n, float* G, const float* Z, bf16* Gb) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -263,6 +326,21 @@ cudaError_t gemm(int M, int N, int K, const bf16* A, long long sam, long long sa
 // forward pass of `rows` samples X (rows x n_in, BF16); output Z[3] (FP32)
 cudaError_t forward(sa_mlp* m, const bf16* X, int rows, cudaStream_t s) {
     const bf16* h = X;
+    if (rows == 1) {            // one sample: four GEMVs
+        for (int l = 0; l < 4; ++l) {
+            const int in = m->dims[l], out = m->dims[l + 1];
+            bf16* H = l < 3 ? m->H[l].p : nullptr;
+            if (l == 0) {       // a long input row: one row per warp
+                k_gemv<1><<<blocks_for(out, 8), 256, 0, s>>>(out, in, m->Wb[l].p, m->b[l].p, h,
+                                                              m->Z[l].p, H);
+            } else {            // four rows per warp: four loads in flight per lane
+                k_gemv<4><<<blocks_for(out, 32), 256, 0, s>>>(out, in, m->Wb[l].p, m->b[l].p, h,
+                                                               m->Z[l].p, H);
+            }
+            h = H;
+        }
+        return cudaGetLastError();
+    }
     for (int l = 0; l < 4; ++l) {
         const int in = m->dims[l], out = m->dims[l + 1];
         cudaError_t e = gemm(rows, out, in, h, in, 1, m->Wb[l].p, 1, in, m->Z[l].p, out, 0.f, s);

@@ -595,11 +595,12 @@ cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s) {
 
 // One plan over batched instances: every instance's faces with their output
 // offsets moved to the batch's point ranges, their coordinate lists
-// concatenated, tiles rebuilt with one tile width per kind; one unit per
-// tile (the unit runs in staging rounds), so the unit sums are the tile's
-// sums.
+// concatenated, tiles rebuilt with one tile width per kind (given, or the
+// least padded); s_max units per tile (1: the unit runs in staging rounds
+// and its sums are the tile's sums).
 bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& qlat_off,
-                    const std::vector<int>& qbot_off, int precision, SepPlan& P) {
+                    const std::vector<int>& qbot_off, int precision, SepPlan& P, int tj_lat,
+                    int tj_bot, int s_max) {
     P.ok = false;
     P.faces_h.clear();
     P.tiles_h.clear();
@@ -624,6 +625,8 @@ bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& q
                 mine.push_back((int)P.faces_h.size());
                 P.faces_h.push_back(F);
             }
+        // tile width: as given (the autotuner), else the least padded area
+        const int forced = kind == 0 ? tj_lat : tj_bot;
         long long best = -1;
         for (int tj : {64, 48, 32}) {
             long long area = 0;
@@ -631,7 +634,7 @@ bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& q
                 const SepFace& F = P.faces_h[fi];
                 area += (long long)((F.La + kTI - 1) / kTI) * kTI * ((F.Lb + tj - 1) / tj) * tj;
             }
-            if (best < 0 || area < best) {
+            if (forced == tj || (forced == 0 && (best < 0 || area < best))) {
                 best = area;
                 P.tj[kind] = tj;
             }
@@ -645,10 +648,12 @@ bool sep_batch_plan(const std::vector<sa_ctx*>& insts, const std::vector<int>& q
                 }
         }
     }
-    P.s_max = 1;
+    // units per tile: each instance's active sources split over s_max units
+    // (the kernels derive the unit length from the instance's count)
+    P.s_max = std::max(1, s_max);
     P.unit = 0;
     const std::vector<float> c32(P.coord_h.begin(), P.coord_h.end());
-    const size_t len = (size_t)std::max(1, P.n_tiles[0] + P.n_tiles[1]) * kPStride;
+    const size_t len = (size_t)std::max(1, P.n_tiles[0] + P.n_tiles[1]) * P.s_max * kPStride;
     bool ok = P.faces.alloc(P.faces_h.size()) == cudaSuccess &&
               P.tiles.alloc(P.tiles_h.size()) == cudaSuccess &&
               P.coord64.alloc(P.coord_h.size()) == cudaSuccess &&
@@ -681,7 +686,7 @@ cudaError_t launch_sep_batch(const SepPlan& P, int precision, DevStatus* st, con
         a.tile0 = kind == 0 ? 0 : P.n_tiles[0];
         a.n_tiles = P.n_tiles[kind];
         a.unit = 0;
-        a.s_max = 1;
+        a.s_max = P.s_max;
         a.st = st;
         a.coef = 0;
         a.inst_K = n_active;

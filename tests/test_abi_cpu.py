@@ -105,7 +105,7 @@ def test_struct_layouts_match_the_header(lib):
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
     structs = {"sa_options": lib.sa_options, "sa_step_stats": lib.sa_step_stats,
-               "sa_sizes": lib.sa_sizes}
+               "sa_sizes": lib.sa_sizes, "sa_batch_shapes": lib.sa_batch_shapes}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "sa.h"', "int main(void) {"]
     for name, cls in structs.items():
         src.append(f'printf("{name} %zu\\n", sizeof({name}));')

@@ -95,3 +95,45 @@ def test_batch_autotune_and_cache(sa, tmp_path):
     assert (P2, NW2) == (P, NW) and ms2 == -1.0
     batch.step(0.5, 5e-6, 10)
     assert np.isfinite(batch.field(0, sa.SA_FIELD_THAT)).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_tune_keeps_the_state_and_the_results(sa, prec, tmp_path):
+    """sa_batch_tune times the separable tile shapes and the solve grid from
+    a saved copy of the state: the batch does not advance, later steps equal
+    those of an untuned batch (other tile shapes only reorder the sums), and
+    the cached choice is applied without timing."""
+    import torch
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    tol = 1e-15 if p == sa.SA_FP64 else 1e-10
+    wls = _instances()
+    s = torch.cuda.Stream()
+    tuned = sa.Batch([gpu_context(wl, p, pcg_tol=tol) for wl in wls], precision=p, pcg_tol=tol,
+                     cuda_stream=s, use_graph=1)
+    plain = sa.Batch([gpu_context(wl, p, pcg_tol=tol) for wl in wls], precision=p, pcg_tol=tol,
+                     cuda_stream=s, use_graph=1)
+    tuned.step(0.5, 5e-6, 30)
+    plain.step(0.5, 5e-6, 30)
+    T0 = tuned.field(0, sa.SA_FIELD_THAT)
+    path = str(tmp_path / "shapes.jsonl")
+    sh = tuned.tune(path, at_step=200)
+    assert sh["hist_separable"] == 1 and sh["step_ms"] > 0
+    assert sh["tj_lat"] in (64, 48, 32) and sh["tj_bot"] in (64, 48, 32)
+    assert sh["units_per_tile"] in (1, 2, 4) and 1 <= sh["pcg_grid"]
+    assert tuned.shapes()["pcg_grid"] == sh["pcg_grid"]
+    assert np.array_equal(tuned.field(0, sa.SA_FIELD_THAT), T0)       # state restored
+    st = tuned.step(0.5, 5e-6, 30)
+    plain.step(0.5, 5e-6, 30)
+    assert st.step_index == 60
+    for i in range(len(wls)):
+        a, b = tuned.field(i, sa.SA_FIELD_THAT), plain.field(i, sa.SA_FIELD_THAT)
+        if p == sa.SA_FP64:
+            assert rel_linf(a, b) <= 1e-11, i
+        else:
+            assert rel_linf(a, b) <= TOL_MIXED_REL and np.abs(a - b).max() <= TOL_MIXED_ABS, i
+    again = sa.Batch([gpu_context(wl, p, pcg_tol=tol) for wl in wls], precision=p, pcg_tol=tol,
+                     cuda_stream=s, use_graph=1)
+    again.step(0.5, 5e-6, 30)
+    sh2 = again.tune(path, at_step=200)
+    assert sh2["step_ms"] == -1.0
+    assert {k: v for k, v in sh2.items() if k != "step_ms"} == {k: v for k, v in sh.items() if k != "step_ms"}
