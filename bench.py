@@ -71,12 +71,14 @@ def parse():
                     help="initial guess of the theta-step solves in the main region")
     ap.add_argument("--batch-steps", type=int, default=2000,
                     help="theta-steps of the 256-instance batched leg (0: skip the leg)")
+    ap.add_argument("--batch-instances", type=int, default=256,
+                    help="instances of the batched leg (256: the sweep; fewer for profiling)")
     ap.add_argument("--learned-pairs", type=int, default=2000,
                     help="training pairs of the learned warm-start leg (0: skip the leg)")
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--legs", default="all",
                     help="comma list of the legs after the main timed region to run: stages, "
-                         "variants, e2e, batched, plate, arc, learned, cpu (default all; the "
+                         "variants, cutoff, e2e, batched, plate, arc, learned, cpu (default all; the "
                          "form used for profiling one leg)")
     ap.add_argument("--quick", action="store_true",
                     help="main timed region only (no stage, FP64, e2e or CPU legs): "
@@ -415,21 +417,11 @@ def cpu_baseline_block(wl, n_first):
 # (random hatch angle and spacing, power, speed), evaluated on the benchmark
 # scan at the benchmark state
 # ---------------------------------------------------------------------------
-def boundary_inputs(patch):
-    """Free control variables on the lateral faces and in the first free
-    layer above the bottom (internal free order: natural order without the
-    bottom layer): the rows of r0 the network reads."""
-    n0, n1, n2 = patch.n_ctrl
-    idx = [(k * n1 + j) * n0 + i - n0 * n1 for k in range(1, n2) for j in range(n1) for i in range(n0)
-           if k == 1 or i in (0, n0 - 1) or j in (0, n1 - 1)]
-    return idx
-
-
 def learned_leg(sa, W, wl, state, stream, n_pairs, epochs, K_eval):
     import numpy as np
     import torch
     th, dt = wl.theta, wl.dt
-    idx = np.array(boundary_inputs(wl.patch), dtype=np.int32)
+    idx = W.warm_start_input_rows(wl.patch)
     probe = sa.context_from_workload(wl, precision=sa.SA_MIXED)
     n_free = probe.sizes().n_free
     probe.close()
@@ -763,6 +755,37 @@ def run_ours(args):
         fp64_sep_steps = K_c / (ms64s / 1e3)
         ctx64s.close()
 
+    # ---- opt-in history cutoff (not the paper's method): pairs skipped and
+    # steps/s at two budgets, on the block and on a 6 x 6 x 1 mm block with
+    # the same meander near one corner
+    cutoff = None
+    if want("cutoff"):
+        cutoff = {"block": {}, "block_6x6x1mm": {}}
+        for eta in (0.0, 1e-6, 1e-4):
+            c = fresh(prec, guess, use_graph=1, hist_cutoff=eta)
+            c.step(th, dt, 3)
+            c.step(th, dt, 0)
+            ms_x = time_graph(c, th, dt, K_c, stream)
+            st_x = c.step(th, dt, 0)
+            n_x = state[0] + 3 + 1
+            pairs_x = q_pts * sum(min(n_x + i, sz.n_src) for i in range(K_c))
+            cutoff["block"][f"{eta:g}"] = {"steps_per_s": K_c / (ms_x / 1e3),
+                                          "pairs_skipped_fraction": st_x.hist_pairs_skipped / pairs_x}
+            c.close()
+        wl6 = W.block_meander(20, theta=0.5, n_el=(96, 96, 16), size=(6e-3, 6e-3, 1e-3))
+        for eta in (0.0, 1e-6, 1e-4):
+            c = sa.context_from_workload(wl6, precision=prec, cuda_stream=stream, use_graph=1,
+                                         hist_cutoff=eta)
+            c.step(th, dt, n0)
+            z6 = c.sizes()
+            ms_x = time_graph(c, th, dt, K_c, stream)
+            st_x = c.step(th, dt, 0)
+            pairs_x = (z6.q_lat + z6.q_bot) * sum(min(n0 + 1 + i, z6.n_src) for i in range(K_c))
+            cutoff["block_6x6x1mm"][f"{eta:g}"] = {
+                "steps_per_s": K_c / (ms_x / 1e3), "n_dof": z6.n_dof,
+                "pairs_skipped_fraction": st_x.hist_pairs_skipped / pairs_x}
+            c.close()
+
     # ---- end to end through the public API with host buffers -------------------
     e2e = None
     if want("e2e"):
@@ -781,7 +804,7 @@ def run_ours(args):
         assert np.isfinite(T_mon).all()
 
     # ---- the batched sweep (256 instances, 2000 steps) ------------------------------
-    batched = (batched_leg(sa, W, stream, 256, args.batch_steps, rank, world, dist)
+    batched = (batched_leg(sa, W, stream, args.batch_instances, args.batch_steps, rank, world, dist)
                if args.batch_steps > 3 and want("batched") else None)
 
     # ---- the plate with a hole ---------------------------------------------------
@@ -885,6 +908,7 @@ def run_ours(args):
         "roofline": roof,
         "e2e": ({"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N_MONITOR * 3 * 8,
                  "d2h_bytes_per_step": N_MONITOR * 8 + 96} if e2e is not None else None),
+        "history_cutoff": cutoff,
         "plate_with_hole": plate,
         "quarter_cylinder_single_source": qcyl,
         "quarter_cylinder_contour": qcon,

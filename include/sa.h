@@ -123,6 +123,20 @@ typedef struct sa_options {
                                     sum a matrix product over the sources (one FMA a
                                     pair); SA_ERR_ARG at sa_create_patch where a face
                                     is not such a rectangle                          */
+    double hist_cutoff;        /* opt-in truncation of the separable history sums
+                                  (not the paper's method, which keeps the full
+                                  sum; 0, the default, keeps it): with eta > 0 the
+                                  product of a face tile with a unit of sources is
+                                  skipped when an upper bound of that unit's
+                                  contribution at every point of the tile (sum over
+                                  its sources of w exp(-a d_min^2), times |n . d|
+                                  on the lateral faces, d_min the distance from the
+                                  source to the tile's box) is at most eta M / U,
+                                  M the largest |sum| over the face kind's points
+                                  at the previous step and U the units per tile.
+                                  Every sum then differs from the full one by at
+                                  most eta M.  Ignored by the pairwise sums;
+                                  SA_ERR_ARG when negative or >= 1               */
 } sa_options;
 
 enum { SA_PCG_AUTO = 0, SA_PCG_SHARED = 1, SA_PCG_GLOBAL = 2 };
@@ -213,6 +227,8 @@ typedef struct sa_step_stats {
     long long step_index;      /* n after the call                                 */
     int ws_used_last;          /* 1: the last step's PCG started from the learned guess */
     double ws_ratio_last;      /* |r0 - A dx| / |r0| of the last learned guess           */
+    long long hist_pairs_skipped;  /* (point, source) pairs dropped by hist_cutoff over
+                                      the steps since the last statistics read      */
 } sa_step_stats;
 
 /*

@@ -66,3 +66,29 @@ def dTdn_tilde(x, nrm, xs, age, E, mat, s_img=2.0, chunk=256):
         g = gradT_point(x[q0:q0 + chunk], xs, age, E, mat, s_img)   # (q,K,3)
         out[q0:q0 + chunk] = np.einsum("qkc,qc->q", g, nrm[q0:q0 + chunk])
     return out
+
+
+def unit_bound(box_lo, box_hi, xs, age, E, mat, s_img=2.0, normal=None):
+    """Upper bound, over the points x of the axis-aligned box [box_lo,
+    box_hi], of sum_I |term_I(x)| for the given sources (the opt-in history
+    cutoff, not part of the paper's method, which keeps every term).
+
+    Each term decreases with the distance from its source, so it is largest
+    at the box point nearest to the source, at distance d_I:
+      T~ terms (normal None):    |T~^(I)(x)| <= c_I exp(-a_I d_I^2)
+      normal-derivative terms on a face with unit normal n along a
+      coordinate axis (box_lo = box_hi along it), where n . (x - x_I) is the
+      same at every point:       |n . grad T~^(I)(x)| <= 2 a_I c_I |n . (x - x_I)| exp(-a_I d_I^2)
+    with a_I = 1/(4 alpha age_I) and c_I the prefactor of Eq. semi-temperature.
+    Returns the bound per source (K,)."""
+    alpha = diffusivity(mat)
+    lo = np.asarray(box_lo, float)
+    hi = np.asarray(box_hi, float)
+    a = 1.0 / (4.0 * alpha * age)
+    c = s_img * E / (mat.rho * mat.cp * (4.0 * np.pi * alpha * age) ** 1.5)
+    dv = np.maximum(0.0, np.maximum(lo[None, :] - xs, xs - hi[None, :]))
+    d2 = np.einsum("kc,kc->k", dv, dv)
+    b = c * np.exp(-a * d2)
+    if normal is not None:
+        b = 2.0 * a * b * np.abs((lo[None, :] - xs) @ np.asarray(normal, float))
+    return b

@@ -32,7 +32,8 @@ class sa_options(C.Structure):
                 ("use_graph", C.c_int), ("device", C.c_int),
                 ("hist_points_per_lane", C.c_int), ("hist_warps", C.c_int),
                 ("stage_timing", C.c_int), ("pcg_variant", C.c_int),
-                ("initial_guess", C.c_int), ("precond", C.c_int), ("hist_mode", C.c_int)]
+                ("initial_guess", C.c_int), ("precond", C.c_int), ("hist_mode", C.c_int),
+                ("hist_cutoff", C.c_double)]
 
 
 class sa_step_stats(C.Structure):
@@ -40,7 +41,8 @@ class sa_step_stats(C.Structure):
                 ("pcg_iters_total", C.c_int), ("pcg_iters_max", C.c_int),
                 ("bot_iters_total", C.c_int), ("rel_res_last", C.c_double),
                 ("n_active_sources", C.c_int), ("step_index", C.c_longlong),
-                ("ws_used_last", C.c_int), ("ws_ratio_last", C.c_double)]
+                ("ws_used_last", C.c_int), ("ws_ratio_last", C.c_double),
+                ("hist_pairs_skipped", C.c_longlong)]
 
 
 class sa_sizes(C.Structure):

@@ -308,6 +308,7 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
         opt.hist_points_per_lane != 2 && opt.hist_points_per_lane != 4)
         return SA_ERR_ARG;
     if (opt.hist_warps != 0 && opt.hist_warps != 4 && opt.hist_warps != 8) return SA_ERR_ARG;
+    if (!(opt.hist_cutoff >= 0.0 && opt.hist_cutoff < 1.0)) return SA_ERR_ARG;
     sa_ctx* c = new sa_ctx();
     c->opt = opt;
     if (opt.device >= 0) {
@@ -1411,6 +1412,7 @@ sa_status sa_step(sa_ctx* c, double theta, double dt, int n_steps, sa_step_stats
         stats->pcg_iters_total = (int)h.iters_total;
         stats->pcg_iters_max = h.iters_max;
         stats->bot_iters_total = (int)h.bot_total;
+        stats->hist_pairs_skipped = h.hist_skipped;
         stats->rel_res_last = h.rel_res;
         stats->n_active_sources = h.n_active;
         stats->step_index = h.n;
@@ -1630,6 +1632,9 @@ sa_status sa_set_state(sa_ctx* c, long long n, const double* T_hat, const double
     if (c->x_prev.p)   // the first step after a restore starts from T^n
         SA_CUDA(c, cudaMemcpy(c->x_prev.p, Ti.data(), sizeof(double) * c->n_dof, cudaMemcpyHostToDevice));
     SA_CUDA(c, cudaMemcpy(&c->st.p->n, &n, sizeof(long long), cudaMemcpyHostToDevice));
+    // the cutoff's previous-step maxima belong to the old state: the first
+    // step after a restore keeps the full sums
+    if (c->sep.ref.p) SA_CUDA(c, cudaMemset(c->sep.ref.p, 0, sizeof(float) * c->sep.ref.n));
     c->n_step = n;
     return SA_OK;
 }

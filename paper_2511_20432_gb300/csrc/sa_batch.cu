@@ -1159,6 +1159,7 @@ sa_status sa_batch_step(sa_batch* b, double theta, double dt, int n_steps, sa_st
         stats->pcg_iters_total = (int)h.iters_total;
         stats->pcg_iters_max = h.iters_max;
         stats->bot_iters_total = (int)h.bot_total;
+        stats->hist_pairs_skipped = h.hist_skipped;
         stats->step_index = h.n;
         DevStatus z;
         std::memset(&z, 0, sizeof(z));

@@ -43,6 +43,7 @@ struct DevStatus {
     long long n;              // step index (device copy)
     long long iters_total;    // accumulated since the last reset by the host
     long long bot_total;
+    long long hist_skipped;   // (point, source) pairs the opt-in cutoff dropped
     int iters_max;
     int pad;
     unsigned bar_count[4];    // grid barrier counters (one pair per cooperative kernel slot)
@@ -212,6 +213,9 @@ struct SepPlan {
     DBuf<float> coord32;
     DBuf<double> part64;           // [tile][unit][64 x 64]
     DBuf<float> part32;
+    // opt-in cutoff: largest |sum| per face kind at the last two steps
+    // ([kind][step parity], FP32 bit patterns of non-negative values)
+    DBuf<float> ref;
 };
 
 // Arguments of one PCG solve.  The grid-barrier counter st->bar_count[which]

@@ -96,6 +96,12 @@ struct SepArgs {
     double* p64;
     double* s_lat;
     double* tt_bot;
+    // opt-in cutoff (ref null: off): eta, and the largest |sum| of each face
+    // kind at the last two steps ([kind][step parity], non-negative FP32
+    // bit patterns); kind of this launch's tiles (0 lateral, 1 Dirichlet)
+    float cutoff;
+    float* ref;
+    int kind;
 };
 
 template <typename T>
@@ -133,6 +139,11 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
     const int tile = a.tile0 + (int)blockIdx.x;
     const int4 td = a.tiles[tile];
     const SepFace f = a.faces[td.x];
+    // cutoff: this step's maximum starts at zero (the reduction kernel that
+    // follows this launch fills it); the previous step's sets the threshold
+    const long long n1 = a.st->n + 1;
+    if (a.ref && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        a.ref[a.kind * 2 + (int)(n1 & 1)] = 0.f;
     const int K = active_sources(a, f.inst);
     const int u = unit_len(K, a.s_max, kKC);
     const int k0 = (int)blockIdx.y * u;
@@ -150,6 +161,32 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
         }
     }
     __syncthreads();   // xs written
+    // cutoff: the tile's box along A and B, the unit's threshold
+    __shared__ T box[4];                 // A min, A max, B min, B max
+    __shared__ T bsum[NT / 32];
+    __shared__ int skip;
+    const int ni = min(kTI, f.La - td.y), nj = min(TJ, f.Lb - td.z);
+    T thr = T(0);
+    if (a.ref) {
+        thr = (T)(a.cutoff * a.ref[a.kind * 2 + (int)((n1 - 1) & 1)]) / (T)a.s_max;
+        if (threadIdx.x == 0) {
+            T lo = xs[0], hi = xs[0];
+            for (int t = 1; t < ni; ++t) {
+                lo = min(lo, xs[t]);
+                hi = max(hi, xs[t]);
+            }
+            box[0] = lo;
+            box[1] = hi;
+            lo = hi = xs[kTI];
+            for (int t = 1; t < nj; ++t) {
+                lo = min(lo, xs[kTI + t]);
+                hi = max(hi, xs[kTI + t]);
+            }
+            box[2] = lo;
+            box[3] = hi;
+        }
+        __syncthreads();
+    }
     // factors of chunk c into buffer c & 1 (log2 units; FP64: natural ones
     // with w folded into m):
     //   FA = 2^(sc (x - s_A)^2)        thread t: column t % 64, sources
@@ -199,6 +236,7 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
                                   : (const V*)(f.flux ? (const void*)a.s64F : (const void*)a.s64T);
             const T dd = (T)f.dd, nsgn = (T)f.nsgn;
             const int npad = (nr + kKC - 1) / kKC * kKC;
+            T bnd = T(0);        // cutoff: this thread's share of the unit's bound
             for (int t = threadIdx.x; t < npad; t += NT) {
                 T sa = 0, sb = 0, sc = 0, off = 0, m = 0;
                 if (t < nr) {
@@ -244,9 +282,35 @@ __global__ void __launch_bounds__(4 * TJ, (sizeof(T) == 4 ? 1024 : 512) / (4 * T
                 p4.w = off;
                 prm[t] = p4;
                 mul[t] = m;
+                if (a.ref && t < nr) {
+                    // the source's largest term over the tile: at the box
+                    // point nearest to it (|n . d| is the same over a face)
+                    const T dA = max(T(0), max(box[0] - sa, sa - box[1]));
+                    const T dB = max(T(0), max(box[2] - sb, sb - box[3]));
+                    const T e = fma(sc, fma(dA, dA, dB * dB), off);
+                    bnd += (kMixed ? (T)ex2_approx((float)e) : (T)exp((double)e)) * (m < T(0) ? -m : m);
+                }
+            }
+            if (a.ref) {
+                // the round's bound, summed in a fixed order (deterministic)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+                if ((threadIdx.x & 31) == 0) bsum[threadIdx.x >> 5] = bnd;
             }
         }
         __syncthreads();
+        if (a.ref) {
+            if (threadIdx.x == 0) {
+                T tot = T(0);
+                for (int w = 0; w < NT / 32; ++w) tot += bsum[w];
+                skip = tot <= thr * (T)nr / (T)n;
+                if (skip)
+                    atomicAdd((unsigned long long*)&a.st->hist_skipped,
+                              (unsigned long long)nr * (unsigned long long)(ni * nj));
+            }
+            __syncthreads();
+            if (skip) continue;
+        }
         const int nch = (nr + kKC - 1) / kKC;
         gen(0);
         __syncthreads();
@@ -322,6 +386,15 @@ __global__ void __launch_bounds__(256) k_sep_reduce(SepArgs a) {
     }
     tot += __shfl_xor_sync(0xffffffffu, tot, 1);
     tot += __shfl_xor_sync(0xffffffffu, tot, 2);
+    if (a.ref) {
+        // cutoff: this step's largest |sum| of the face kind (non-negative
+        // FP32 values order as their bit patterns)
+        float v = ok ? fabsf((float)tot) : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0 && v > 0.f)
+            atomicMax((int*)&a.ref[a.kind * 2 + (int)((a.st->n + 1) & 1)], __float_as_int(v));
+    }
     if (!ok || lane4 != 0) return;
     const int ea = i / f.nga, ga = i - ea * f.nga;
     const int eb = j / f.ngb, gb = j - eb * f.ngb;
@@ -547,6 +620,10 @@ sa_status sep_alloc(sa_ctx* c) {
     } else {
         SA_ALLOC(c, P.part64, len);
     }
+    if (c->opt.hist_cutoff > 0.0) {
+        SA_ALLOC(c, P.ref, 4);
+        SA_CUDA(c, cudaMemset(P.ref.p, 0, 4 * sizeof(float)));
+    }
     return SA_OK;
 }
 
@@ -586,6 +663,9 @@ cudaError_t launch_sep(sa_ctx* c, int part, double dt, cudaStream_t s) {
         a.p64 = P.part64.p;
         a.s_lat = c->s_lat.p;
         a.tt_bot = c->tt_bot.p;
+        a.cutoff = (float)c->opt.hist_cutoff;
+        a.ref = c->opt.hist_cutoff > 0.0 ? P.ref.p : nullptr;
+        a.kind = kind;
         const cudaError_t e = c->opt.precision == SA_MIXED ? launch_sep_tj<float>(P.tj[kind], a, s)
                                                            : launch_sep_tj<double>(P.tj[kind], a, s);
         if (e != cudaSuccess) return e;
@@ -701,6 +781,9 @@ cudaError_t launch_sep_batch(const SepPlan& P, int precision, DevStatus* st, con
         a.p64 = P.part64.p;
         a.s_lat = s_lat;
         a.tt_bot = tt_bot;
+        a.cutoff = 0.f;          // batches keep the full sums
+        a.ref = nullptr;
+        a.kind = kind;
         const cudaError_t e = precision == SA_MIXED ? launch_sep_tj<float>(P.tj[kind], a, s)
                                                     : launch_sep_tj<double>(P.tj[kind], a, s);
         if (e != cudaSuccess) return e;

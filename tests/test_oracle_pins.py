@@ -825,3 +825,41 @@ def test_table4_integrated_analytical_heat_loss():
                                                       m.E, wl.material, m.s_img)
         ana = float(np.sum(np.abs(qt) * ds))
         assert lo <= ana <= hi, (t_s, lo, ana, hi)
+
+
+# ---------------------------------------------------------------------------
+# C1: the bound of the opt-in history cutoff (not part of the paper's method)
+# ---------------------------------------------------------------------------
+def test_pin_C1_cutoff_bound_by_brute_force():
+    """unit_bound is an upper bound of every term over a box (brute force on
+    a 21 x 21 grid of each face box), is attained when the box is one point,
+    and the sum over any dropped subset of sources is at most the sum of
+    their bounds at every point of the box."""
+    from oracle import pointsource as ps
+    mat = W.MAT_DEFAULT
+    rng = np.random.default_rng(17)
+    E = 4e-4
+    for trial in range(6):
+        K = 40
+        xs = np.column_stack([rng.uniform(0, 1e-3, K), rng.uniform(0, 1e-3, K), np.full(K, 0.5e-3)])
+        age = rng.uniform(1e-6, 4e-4, K)
+        ax = trial % 3                                 # face normal along x, y or z
+        lo = rng.uniform(0, 0.6e-3, 3)
+        hi = lo + rng.uniform(0.05e-3, 0.4e-3, 3)
+        lo[ax] = hi[ax] = rng.uniform(0, 0.5e-3)
+        nrm = np.eye(3)[ax] * (1 if trial % 2 else -1)
+        t = [np.linspace(lo[k], hi[k], 21) if k != ax else np.array([lo[k]]) for k in range(3)]
+        pts = np.array(np.meshgrid(*t, indexing="ij")).reshape(3, -1).T
+        for normal in (None, nrm):
+            bnd = ps.unit_bound(lo, hi, xs, age, E, mat, normal=normal)
+            T = ps.T_point(pts, xs, age, E, mat)                      # (Q, K)
+            terms = T if normal is None else np.abs(
+                np.einsum("qkc,c->qk", ps.gradT_point(pts, xs, age, E, mat), normal))
+            assert np.all(terms <= bnd[None, :] * (1 + 1e-12) + 1e-300)
+            drop = rng.uniform(size=K) < 0.5
+            assert np.all(terms[:, drop].sum(1) <= bnd[drop].sum() * (1 + 1e-12) + 1e-300)
+            # one-point box: the bound is the term itself
+            p = pts[len(pts) // 3]
+            b1 = ps.unit_bound(p, p, xs, age, E, mat, normal=normal)
+            t1 = T[len(pts) // 3] if normal is None else terms[len(pts) // 3]
+            assert np.allclose(b1, t1, rtol=1e-12, atol=0)

@@ -569,3 +569,42 @@ def test_fast_diagonalization_on_the_curved_closed_plate(sa):
     c.step(wl.theta, wl.dt, 40)
     stj = c.step(wl.theta, wl.dt, 20)
     assert 2 * st.pcg_iters_total < stj.pcg_iters_total, (st.pcg_iters_total, stj.pcg_iters_total)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_history_cutoff_stays_within_its_bound(sa, prec):
+    """The opt-in history cutoff (not the paper's method, which keeps the full
+    sum): on an elongated box (2.2 x 0.4 x 0.3 mm) under a meander of several
+    hundred sources, with eta = 1e-4 the separable sums differ from the
+    oracle's full sums by at most eta times the face kind's largest |sum| at
+    the previous step (plus the path's tolerance), pairs are skipped, and with
+    the default eta = 0 none are."""
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    patch = W.cuboid_patch((2.2e-3, 0.4e-3, 0.3e-3), (22, 4, 3), 2)
+    z = float(patch.ctrl[-1, 0, 0, 2])
+    scan = W.meander(0.2e-3, 2.0e-3, 0.12e-3, 0.08e-3, 3, z, 180.0, 0.4, 1.5)
+    wl = W.Workload("cut", patch, W.MAT_DEFAULT, scan, dt=4e-6, theta=0.5, n_steps=400)
+    eta = 1e-4
+    tol = 1e-12 if p == sa.SA_FP64 else TOL_MIXED_REL
+    m = _oracle(wl)
+    ctx = gpu_context(wl, p, hist_mode=2, hist_cutoff=eta,
+                      pcg_tol=1e-15 if p == sa.SA_FP64 else 1e-10)
+    full = gpu_context(wl, p, hist_mode=2, pcg_tol=1e-15 if p == sa.SA_FP64 else 1e-10)
+    prev = None
+    skipped = skipped_full = 0
+    worst = 0.0
+    for step in range(wl.n_steps):
+        skipped += ctx.step(wl.theta, wl.dt, 1).hist_pairs_skipped
+        skipped_full += full.step(wl.theta, wl.dt, 1).hist_pairs_skipped
+        m.step()
+        ref = (m.last["s_lat"], m.last["Tt_bot"])
+        if prev is not None and (step + 1) % 25 == 0:
+            for got, r, M in ((ctx.field(sa.SA_FIELD_DTDN_LAT), ref[0], prev[0]),
+                              (ctx.field(sa.SA_FIELD_TT_BOT), ref[1], prev[1])):
+                err = np.abs(got - r).max()
+                allowed = eta * M * (1 + 1e-3) + tol * np.abs(r).max()
+                assert err <= allowed, (step, err, allowed)
+                worst = max(worst, err / (eta * M))
+        prev = (np.abs(ref[0]).max(), np.abs(ref[1]).max())
+    assert skipped > 0 and skipped_full == 0
+    print(f"\ncutoff eta {eta}: {skipped} pairs skipped, largest error {worst:.3f} eta M")

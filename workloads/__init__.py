@@ -310,17 +310,22 @@ def cuboid_single_track(theta=1.0, n_steps=150) -> Workload:
                     scan, dt=10e-6, theta=theta, n_steps=n_steps)
 
 
-def block_meander(n_tracks=20, theta=0.5, n_steps=None, n_el=(64, 64, 16)) -> Workload:
+def block_meander(n_tracks=20, theta=0.5, n_steps=None, n_el=(64, 64, 16),
+                  size=(4.0e-3, 4.0e-3, 1.0e-3)) -> Workload:
     """4 x 4 x 1 mm block, degree 2, 64x64x16 elements (78,408 control
     points); meander of ``n_tracks`` 3.5 mm tracks (hatch 0.1 mm, alternating),
-    P = 250 W, A = 0.4, v = 1.2 m/s, dt = 5 us, full history kept."""
-    patch = cuboid_patch((4.0e-3, 4.0e-3, 1.0e-3), n_el, 2)
+    P = 250 W, A = 0.4, v = 1.2 m/s, dt = 5 us, full history kept.  ``size``
+    gives a larger block with the same meander at the same place (near the
+    corner x = y = 0)."""
+    patch = cuboid_patch(size, n_el, 2)
     scan = meander(0.25e-3, 3.75e-3, 1.05e-3, 0.1e-3, n_tracks, 1.0e-3,
                    power=250.0, absorptivity=0.4, speed=1.2)
     per_track = int(np.floor(3.5e-3 / (1.2 * 5e-6) + 1e-9)) + 1
     if n_steps is None:
         n_steps = per_track * n_tracks
-    return Workload(f"block_4x4x1mm_p2_{n_el[0]}x{n_el[1]}x{n_el[2]}_meander{n_tracks}",
+    tag = "4x4x1mm" if tuple(size) == (4.0e-3, 4.0e-3, 1.0e-3) else \
+        "x".join(f"{v * 1e3:g}" for v in size) + "mm"
+    return Workload(f"block_{tag}_p2_{n_el[0]}x{n_el[1]}x{n_el[2]}_meander{n_tracks}",
                     patch, MAT_DEFAULT, scan, dt=5e-6, theta=theta, n_steps=n_steps)
 
 
@@ -357,6 +362,18 @@ def learned_scan(k: int, z=1.0e-3, center=(2.0e-3, 2.0e-3)) -> Scan:
     if k % 2 == 1:
         sc.seg_on = np.ones_like(sc.seg_on)
     return sc
+
+
+def warm_start_input_rows(patch) -> np.ndarray:
+    """Rows of the theta-step residual that the learned warm start reads: the
+    free control variables on the lateral faces and in the first free layer
+    above the bottom, as indices into the free rows (the free rows are the
+    control points in natural order without the bottom layer, which holds
+    the Dirichlet control variables)."""
+    n0, n1, n2 = patch.n_ctrl
+    idx = [(k * n1 + j) * n0 + i - n0 * n1 for k in range(1, n2) for j in range(n1)
+           for i in range(n0) if k == 1 or i in (0, n0 - 1) or j in (0, n1 - 1)]
+    return np.array(idx, dtype=np.int32)
 
 
 def _track_lengths(scan):
