@@ -164,6 +164,7 @@ struct FdView {
     double cM;
     const void* S;         // n_free diagonal scaling
     void* Z;               // n_free work vector
+    void* Z2;              // second n_free work vector (plane form, 3-D)
 };
 
 // Host and device data of one fast-diagonalization preconditioner over an
@@ -176,7 +177,7 @@ struct FdData {
     int m[3] = {1, 1, 1};
     double L[3] = {0, 0, 0}, cM = 0, c[3] = {0, 0, 0};
     std::vector<double> U[3], lam[3], md[3], kd[3];
-    DBuf<unsigned char> dU[3], dUt[3], dlamc[3], dmd[3], dkd[3], S, Z;
+    DBuf<unsigned char> dU[3], dUt[3], dlamc[3], dmd[3], dkd[3], S, Z, Z2;
 };
 
 // One face of the separable history evaluation: an axis-aligned rectangle

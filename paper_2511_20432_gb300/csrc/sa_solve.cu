@@ -748,6 +748,8 @@ struct SmemArgs {
     VT* dir_out;
     int fd_w2;             // 1: the region holds three m x m matrices (the fused
                            // pass's second one staged too), 0: two
+    int fd_rows;           // > 0: plane form of the 3-D preconditioner with slabs
+                           // of this many rows; 0: the line form
 };
 
 template <typename T>
@@ -934,6 +936,115 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
     return true;
 }
 
+// Plane form of the 3-D preconditioner: u = S (U_2 (x) U_1 (x) U_0) D^{-1}
+// (U_2 (x) U_1 (x) U_0)^T S r in three passes with two grid barriers
+// (instead of five line passes and four):
+//   A  every z-plane X (m1 x m0, x fastest) becomes U_1^T X U_0, Z -> Z2;
+//   B  z-lines of Z2: U_2^T, the diagonal D, U_2, -> Z (the line pass of the
+//      line form);
+//   C  every plane becomes U_1 X U_0^T, times S, -> out.
+// A plane is split into slabs of `rows` output rows over several blocks (the
+// block count over the plane count), so that every SM works and no block
+// transforms a whole plane alone; each block stages the plane and the two
+// m x m matrices in shared memory (wbuf: m0 m1 + m0^2 + m1^2 + rows m0
+// entries) and forms its slab as two small products.
+template <typename VT>
+__device__ void plane_slab(const VT* src, VT* dst, const VT* Sv, const VT* W1, const VT* W0,
+                           int m0, int m1, int plane, int j0, int nrow, VT* wbuf) {
+    VT* X = wbuf;                       // m1 x m0
+    VT* A1 = X + m0 * m1;               // m1 x m1: W1[a][o]
+    VT* A0 = A1 + m1 * m1;              // m0 x m0: W0[a][o]
+    VT* Tm = A0 + m0 * m0;              // nrow x m0
+    const long long base = (long long)plane * m0 * m1;
+    __syncthreads();                    // wbuf free
+    for (int t = threadIdx.x; t < m0 * m1; t += blockDim.x) X[t] = __ldcg(src + base + t);
+    for (int t = threadIdx.x; t < m1 * m1; t += blockDim.x) A1[t] = __ldg(W1 + t);
+    for (int t = threadIdx.x; t < m0 * m0; t += blockDim.x) A0[t] = __ldg(W0 + t);
+    __syncthreads();
+    // T[r][i] = sum_j W1[j][j0 + r] X[j][i]
+    for (int t = threadIdx.x; t < nrow * m0; t += blockDim.x) {
+        const int r = t / m0, i = t - r * m0;
+        VT acc = (VT)0;
+#pragma unroll 4
+        for (int j = 0; j < m1; ++j) acc = fma(A1[j * m1 + j0 + r], X[j * m0 + i], acc);
+        Tm[t] = acc;
+    }
+    __syncthreads();
+    // Y[r][o] = sum_i W0[i][o] T[r][i]
+    for (int t = threadIdx.x; t < nrow * m0; t += blockDim.x) {
+        const int r = t / m0, o = t - r * m0;
+        VT acc = (VT)0;
+#pragma unroll 4
+        for (int i = 0; i < m0; ++i) acc = fma(A0[i * m0 + o], Tm[r * m0 + i], acc);
+        const long long idx = base + (long long)(j0 + r) * m0 + o;
+        dst[idx] = Sv ? Sv[idx] * acc : acc;
+    }
+}
+
+template <typename VT>
+__device__ bool fd_apply_planes(const FdView& fd, const GridSync& sync, VT* wbuf, VT* xs, VT* out,
+                                int rows) {
+    const int lane = threadIdx.x & 31;
+    const int m0 = fd.m[0], m1 = fd.m[1], m2 = fd.m[2];
+    VT* Z = (VT*)fd.Z;
+    VT* Z2 = (VT*)fd.Z2;
+    const VT* S = (const VT*)fd.S;
+    const int nslab = (m1 + rows - 1) / rows;
+    const int items = m2 * nslab;
+    // A: planes of Z -> Z2
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int p = it / nslab, j0 = (it - p * nslab) * rows;
+        plane_slab<VT>(Z, Z2, nullptr, (const VT*)fd.U[1], (const VT*)fd.U[0], m0, m1, p, j0,
+                       min(rows, m1 - j0), wbuf);
+    }
+    // stage U_2 and U_2^T for B while waiting
+    __syncthreads();
+    VT* W2 = wbuf;
+    VT* W2t = wbuf + m2 * m2;
+    for (int t = threadIdx.x; t < m2 * m2; t += blockDim.x) {
+        W2[t] = __ldg((const VT*)fd.U[2] + t);
+        W2t[t] = __ldg((const VT*)fd.Ut[2] + t);
+    }
+    if (!sync.barrier()) return false;
+    // B: z-lines of Z2 -> Z (one warp a line, lines over all blocks' warps)
+    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const VT* l0 = (const VT*)fd.lamc[0];
+    const VT* l1 = (const VT*)fd.lamc[1];
+    const VT* l2 = (const VT*)fd.lamc[2];
+    const VT cM = (VT)fd.cM;
+    const int plane = m0 * m1;
+    for (int L = gw; L < plane; L += nw) {
+        for (int k = lane; k < m2; k += 32) xs[k] = __ldcg(Z2 + L + (long long)k * plane);
+        __syncwarp();
+        VT y[kFdPerLane];
+        fd_line_matvec(W2, xs, m2, lane, y);
+        const VT li = cM + l0[L % m0] + l1[L / m0];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kFdPerLane; ++t) {
+            const int o = lane + 32 * t;
+            if (o < m2) xs[o] = y[t] / (li + l2[o]);
+        }
+        __syncwarp();
+        fd_line_matvec(W2t, xs, m2, lane, y);
+#pragma unroll
+        for (int t = 0; t < kFdPerLane; ++t) {
+            const int o = lane + 32 * t;
+            if (o < m2) Z[L + (long long)o * plane] = y[t];
+        }
+        __syncwarp();
+    }
+    if (!sync.barrier()) return false;
+    // C: planes of Z -> S (U_1 X U_0^T) into out
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int p = it / nslab, j0 = (it - p * nslab) * rows;
+        plane_slab<VT>(Z, out, S, (const VT*)fd.Ut[1], (const VT*)fd.Ut[0], m0, m1, p, j0,
+                       min(rows, m1 - j0), wbuf);
+    }
+    return true;
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     // AT: type of the dot products (the operator precision).  The mixed
@@ -959,8 +1070,9 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     double* const P = V + 5 * a.rcap;
     double* const DI = V + 6 * a.rcap;
     __shared__ double bl64[4];
-    __shared__ AT blt[4];
-    __shared__ double res[4];
+    __shared__ AT blt[8];
+    __shared__ double res[8];
+    __shared__ int shortcut;                // 1: the first update converged (estimate)
     __shared__ double sc[4];                // alpha, beta (applied), sigma
     __shared__ AT scl[4];                   // alpha, gamma (previous) in AT
     __shared__ int state;                   // 0 run, 1 converged, 2 nan, 3 iteration cap
@@ -1069,7 +1181,11 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     // u = P^{-1} r, published (Jacobi: local; fast diagonalization: passes)
     auto precondition = [&]() -> bool {
         if (fd) {
-            if (!fd_apply<VT>(a.fd, sync, win, xs, a.ul, a.fd_w2 != 0)) return false;
+            if (a.fd_rows > 0) {
+                if (!fd_apply_planes<VT>(a.fd, sync, win, xs, a.ul, a.fd_rows)) return false;
+            } else if (!fd_apply<VT>(a.fd, sync, win, xs, a.ul, a.fd_w2 != 0)) {
+                return false;
+            }
             if (!sync.barrier()) return false;
             for (int t = threadIdx.x; t < nr; t += blockDim.x) {
                 const VT u = __ldcg(a.ul + row0 + t);
@@ -1092,17 +1208,38 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     }
     while (state == 0) {
         // ---- S: w = A u and (r, u), (w, u)
-        AT v[2] = {(AT)0, (AT)0};
+        // at the first iteration also (e, e), (e, w), (w, w) with e = r - w
+        // (scaled like r): the residual after the first update is
+        // r - al w = e + (1 - al) w, whose norm they give without
+        // cancellation when the preconditioner is nearly the inverse (al
+        // close to 1, e small), so a converged first update needs no
+        // exchange of its own
+        const bool first = it == 0;
+        AT v[5] = {(AT)0, (AT)0, (AT)0, (AT)0, (AT)0};
         spmv_block(a.plan, a.ul, win, sq, [&](int i, VT wt) {
             const int l = i - row0;
             W[l] = (double)wt;
+            const AT w32 = (AT)wt * sig;
             v[0] += R32[l] * U32[l];
-            v[1] += ((AT)wt * sig) * U32[l];
+            v[1] += w32 * U32[l];
+            if (first) {
+                const AT e32 = (AT)(R[l] - (double)wt) * sig;
+                v[2] += e32 * e32;
+                v[3] += e32 * w32;
+                v[4] += w32 * w32;
+            }
         }, &wa);
-        block_sum<2>(v, blt);
-        // partial slots: warm start 10-11, norms 8-9, then S 0-1 / 4-5 and
-        // V 2 / 6 alternating (a slot set is rewritten only two barriers later)
-        if (!grid_exchange<2>(sync, blt, 4 * (it & 1), res)) return;
+        // partial slots: warm start 10-11, norms 8-9, the first S 0-4, then
+        // V 6 / 2 and S 4-5 / 0-1 alternating (a slot set is rewritten only
+        // two barriers later)
+        if (first) {
+            block_sum<5>(v, blt);
+            if (!grid_exchange<5>(sync, blt, 0, res)) return;
+        } else {
+            AT v2[2] = {v[0], v[1]};
+            block_sum<2>(v2, blt);
+            if (!grid_exchange<2>(sync, blt, 4 * (it & 1), res)) return;
+        }
         if (threadIdx.x == 0) {
             const AT gamma = (AT)res[0], delta = (AT)res[1];
             AT be = (AT)0, al = gamma / delta;
@@ -1115,6 +1252,20 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             sc[0] = (double)al;
             sc[1] = (double)be;
             state = !(al == al) ? 2 : 0;
+            shortcut = 0;
+            if (first && state == 0) {
+                // |(sigma r1, sigma r1) - est| <= bound: sums of one rounding
+                // per product over a tree of depth ~24, with margin
+                const double om = 1.0 - (double)al;
+                const double ee = res[2], ew = res[3], ww = res[4];
+                const double est = ee + 2.0 * om * ew + om * om * ww;
+                const double bound = 64.0 * (sizeof(AT) == 4 ? 5.9604644775390625e-8 : 1.1102230246251565e-16) *
+                                     (ee + 2.0 * fabs(om) * sqrt(ee * ww) + om * om * ww);
+                if (est + bound <= stop2) {
+                    shortcut = 1;
+                    sc[3] = est > 0.0 ? est : 0.0;
+                }
+            }
         }
         __syncthreads();
         if (state != 0) break;
@@ -1142,6 +1293,11 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             }
         }
         ++it;
+        if (shortcut) {
+            if (threadIdx.x == 0) state = 1;
+            __syncthreads();
+            break;
+        }
         block_sum<1>(vr, blt);
         if (!grid_exchange<1>(sync, blt, 2 + 4 * (it & 1), res)) return;
         if (threadIdx.x == 0) {
@@ -1302,6 +1458,17 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.dir_old = L.dir_old;
             a.dir_out = (VT*)L.dir_out;
             a.fd_w2 = sh.fd_w2;
+            // 3-D: the plane form when its staging fits the shared region
+            a.fd_rows = 0;
+            if (L.fd.on && L.fd.nd == 3 && L.fd.Z2 != nullptr) {
+                const int m0 = L.fd.m[0], m1 = L.fd.m[1], m2 = L.fd.m[2];
+                const int nslab = std::max(1, sh.G / std::max(m2, 1));
+                const int rows = (m1 + nslab - 1) / nslab;
+                const long long need = (long long)m0 * m1 + (long long)m0 * m0 + (long long)m1 * m1 +
+                                       (long long)rows * m0;
+                if (need <= sh.region && 2ll * m2 * m2 <= sh.region && m2 <= 32 * kFdPerLane)
+                    a.fd_rows = rows;
+            }
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
         }
         if (L.variant == SA_PCG_SHARED) return cudaErrorInvalidConfiguration;
