@@ -1002,6 +1002,8 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         c->pcg_block = pcg_block_size();
         c->pcg_grid = c->num_sms;   // one co-resident block of 1024 threads per SM
         SA_ALLOC(c, c->partials, (size_t)12 * c->pcg_grid);
+        SA_ALLOC(c, c->npart, (size_t)2 * std::max(c->r_s.n_slices, 1));
+        SA_ALLOC(c, c->npart_bot, (size_t)2 * std::max((8 * (long long)c->n_dir + 31) / 32, 1ll));
         if (c->opt.precond != SA_PRECOND_JACOBI) {
             sa_status fst = fd_setup(c);
             if (fst) return fst;
@@ -1184,6 +1186,16 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     br.g0 = c->gnew.p;
     br.r0 = c->r0bot.p;
     br.bsq = c->bsqbot.p;
+    // the projection's Z = S r0 and norms from the gather (2-D fast
+    // diagonalization; no proposed start is tested in the projection)
+    const FdView fdb_view = fd_view(c, c->fdb);
+    const bool bot_pre = fdb_view.on && c->npart_bot.p && c->n_dir > 0;
+    if (bot_pre) {
+        br.fdS = fdb_view.S;
+        br.fdZ = fdb_view.Z;
+        br.f32 = c->opt.precision == SA_MIXED ? 1 : 0;
+        br.npart = c->npart_bot.p;
+    }
     for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
         e = launch_gather(c->wlat_rows, c->wlat_rowdof.p, c->wlat_ptr.p, c->wlat_col.p,
                           c->wlat_val.p, c->s_lat.p, c->k, c->n_dir, c->wbot_ptr.p, c->wbot_col.p,
@@ -1215,7 +1227,11 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.variant = c->opt.pcg_variant;
-        L.fd = fd_view(c, c->fdb);
+        L.fd = fdb_view;
+        if (bot_pre) {
+            L.npart = c->npart_bot.p;
+            L.npart_n = (int)((8 * (long long)c->n_dir + 31) / 32);
+        }
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
@@ -1235,6 +1251,12 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "bottom PCG");
     }
     SA_MARK(SA_STAGE_RHS);
+    // the right-hand side kernel also writes the main solve's Z = S r0 and the
+    // per-slice norms when the solve starts from T^n with the fast
+    // diagonalization (no proposed start to test first)
+    const FdView fdm_view = fd_view(c, c->fdm);
+    const bool rhs_pre = fdm_view.on && !extrap && !c->ws_net && c->npart.p &&
+                         c->npart.n >= (size_t)2 * c->r_s.n_slices;
     for (int only = overlap ? 1 : 0; only <= (overlap ? 2 : 0); ++only) {
         if (only == 2) {   // join: the projection is done
             SA_CUDA(c, cudaEventRecord(c->ev_join, sb));
@@ -1245,7 +1267,9 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                              mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
                              mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
                              c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
-                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s, only, dir_ready);
+                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s, only, dir_ready,
+                             rhs_pre ? fdm_view.S : nullptr, rhs_pre ? fdm_view.Z : nullptr,
+                             rhs_pre ? c->npart.p : nullptr);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     }
     SA_MARK(SA_STAGE_PCG);
@@ -1289,7 +1313,11 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.partials = c->partials.p;
         L.st = c->st.p;
         L.variant = c->opt.pcg_variant;
-        L.fd = fd_view(c, c->fdm);
+        L.fd = fdm_view;
+        if (rhs_pre) {
+            L.npart = c->npart.p;
+            L.npart_n = c->r_s.n_slices;
+        }
         L.which = 0;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;

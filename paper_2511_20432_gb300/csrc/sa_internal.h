@@ -255,6 +255,11 @@ struct PcgLaunch {
     // increments the theta right-hand side needs)
     const double* dir_old = nullptr;
     void* dir_out = nullptr;
+    // the right-hand side kernel's per-slice (b^2, r0^2) sums (npart_n
+    // slices) and its Z = S r0 for the fast diagonalization: the solve then
+    // needs no exchange for the norms (null: it forms them itself)
+    const float* npart = nullptr;
+    int npart_n = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -386,6 +391,9 @@ struct sa_ctx {
     DBuf<double> dev64;                  // T^n - T_c (n_dof)
     DBuf<float> dev32;
     DBuf<double> partials;    // 4 * max grid
+    DBuf<float> npart;        // per slice of the free rows: (b^2, r0^2) sums of the step's
+                              // right-hand side, for the main solve
+    DBuf<float> npart_bot;    // per gather warp of the bottom rows: the same for the projection
     DBuf<DevStatus> st;
     int pcg_grid = 0, pcg_block = 0;
     int hist_P = 0, hist_W = 0;
@@ -547,6 +555,13 @@ struct BotResid {
     const double* g0 = nullptr;   // initial guess
     double* r0 = nullptr;
     double* bsq = nullptr;
+    // for the projection solve (null: off): Z = S r0 of its 2-D fast
+    // diagonalization (FP32 when f32, else FP64) and per warp of the bottom
+    // rows the sums of b^2 and r0^2 ([warp][2])
+    const void* fdS = nullptr;
+    void* fdZ = nullptr;
+    int f32 = 0;
+    float* npart = nullptr;
 };
 cudaError_t launch_gather(int wlat_rows, const int* wlat_rowdof, const int* wlat_ptr,
                           const int* wlat_col, const double* wlat_val, const double* s_lat,
@@ -560,7 +575,8 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only = 0,
-                             bool dir_ready = false);
+                             bool dir_ready = false, const void* fdS = nullptr, void* fdZ = nullptr,
+                             float* npart = nullptr);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
                           double* gprev, double* g0, cudaStream_t s);

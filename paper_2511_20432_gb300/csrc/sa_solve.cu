@@ -119,6 +119,28 @@ __global__ void k_gather(GatherArgs a) {
             if (a.br.mptr) {
                 a.br.r0[r] = acc - mg;
                 a.br.bsq[r] = acc * acc;
+                if (a.br.fdZ) {
+                    if (a.br.f32)
+                        ((float*)a.br.fdZ)[r] = ((const float*)a.br.fdS)[r] * (float)(acc - mg);
+                    else
+                        ((double*)a.br.fdZ)[r] = ((const double*)a.br.fdS)[r] * (acc - mg);
+                }
+            }
+        }
+        if (a.br.npart) {
+            // the warp's rows (whole warps lie in the bottom range), FP32
+            // sums as for the main solve
+            float b2 = ok && sub == 0 ? (float)(acc * acc) : 0.f;
+            float r2 = ok && sub == 0 ? (float)((acc - mg) * (acc - mg)) : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+                r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                const long long w = (gt - lat_threads) >> 5;
+                a.br.npart[2 * w] = b2;
+                a.br.npart[2 * w + 1] = r2;
             }
         }
     }
@@ -162,6 +184,12 @@ struct RhsArgs {
     double* r0;
     double* bsq;           // b_i^2, for the norm of the right-hand side
     int only;              // 0: every slice; 1: slices without Dirichlet columns; 2: with
+    // for the solve that follows (null: off): Z = S r0 of its
+    // fast-diagonalization preconditioner, and per slice the sums of b_i^2
+    // and r0_i^2 over its rows ([slice][2])
+    const VT* fdS;
+    VT* fdZ;
+    float* npart;
 };
 
 // g^{n+1} - g^n and g^{n+1} in the operator precision, so that the rows
@@ -264,15 +292,34 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
         for (int hh = 1; hh < kRhsSplit; ++hh) t += part[wib + hh][v][lane];
         acc[v] = t;
     }
+    double b2 = 0.0, r2 = 0.0;
     if (i < a.n_free) {
         const double tk = a.theta * a.k;
         const double accd = a.inv_dt_rhocp * (double)acc[3] + tk * (double)acc[4];
         const double accg = a.inv_dt_rhocp * (double)acc[5] + tk * (double)acc[6];
         const double f = a.theta * a.F1[i] + (1.0 - a.theta) * a.F0[i];
-        a.r0[i] = f - a.k * (double)acc[0] - accd;
+        const double r = f - a.k * (double)acc[0] - accd;
+        a.r0[i] = r;
         const double b = a.inv_dt_rhocp * (a.Tc * (double)acc[2] + (double)acc[1]) -
                          (1.0 - a.theta) * a.k * (double)acc[0] + f - accg;
         a.bsq[i] = b * b;
+        if (a.fdZ) a.fdZ[i] = a.fdS[i] * (VT)r;
+        b2 = b * b;
+        r2 = r * r;
+    }
+    if (a.npart) {
+        // FP32 sums (a norm for the stopping test needs no more; the solve
+        // falls back to its own FP64 norms if they overflow)
+        float fb = (float)b2, fr = (float)r2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fb += __shfl_xor_sync(0xffffffffu, fb, o);
+            fr += __shfl_xor_sync(0xffffffffu, fr, o);
+        }
+        if (lane == 0) {
+            a.npart[2 * sl] = fb;
+            a.npart[2 * sl + 1] = fr;
+        }
     }
 }
 
@@ -742,6 +789,8 @@ struct SmemArgs {
     const double* dx0_scale;
     const void* dinvl;     // D^{-1} in VT
     FdView fd;             // fast-diagonalization preconditioner (fd.on), else Jacobi
+    const float* npart;    // with r0 and fd: the producer's per-slice (b^2, r0^2) sums and
+    int npart_n;           // Z = S r0 already written (slices), else null
     int fd_mmax;           // longest grid line (per-warp scratch entries)
     int plan_wcap;         // window entries reserved in shared memory
     const double* dir_old; // see PcgLaunch
@@ -1153,12 +1202,39 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
         }
         __syncthreads();
     }
-    // ---- the norms of b and r0 -> sigma; convergence at the start
-    if (fd)
-        for (int t = threadIdx.x; t < nr; t += blockDim.x) Zf[row0 + t] = Sf[row0 + t] * (VT)R[t];
+    // ---- the norms of b and r0 -> sigma; convergence at the start.  With
+    // the producer's per-slice sums (and its Z = S r0) every block adds them
+    // in the same fixed order: no exchange, no barrier before the first
+    // preconditioner pass.
+    bool pre = a.npart != nullptr && fd && a.dx0 == nullptr && a.r0 != nullptr;
     double bb;
     int it = 0;
-    {
+    __shared__ float nb2[2];
+    if (pre) {
+        // every thread adds a few slices, then an FP32 block sum in fixed
+        // order (identical in every block, so every block takes the same
+        // branch below)
+        float v2[2] = {0.f, 0.f};
+        for (int q = threadIdx.x; q < a.npart_n; q += blockDim.x) {
+            v2[0] += __ldcg(a.npart + 2 * q);
+            v2[1] += __ldcg(a.npart + 2 * q + 1);
+        }
+        block_sum<2>(v2, nb2);
+        pre = isfinite(nb2[0]) && isfinite(nb2[1]);   // else the FP64 norms below
+    }
+    if (fd && !pre)
+        for (int t = threadIdx.x; t < nr; t += blockDim.x) Zf[row0 + t] = Sf[row0 + t] * (VT)R[t];
+    if (pre) {
+        bb = (double)nb2[0];
+        const double rr = (double)nb2[1];
+        if (threadIdx.x == 0) {
+            sc[2] = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
+            const double rr0 = bb > 0.0 ? rr / bb : rr;
+            sc[3] = rr0;
+            state = !(rr0 == rr0) ? 2 : (rr0 <= a.tol * a.tol ? 1 : 0);
+        }
+        __syncthreads();
+    } else {
         double rrp = 0.0;
         for (int t = threadIdx.x; t < nr; t += blockDim.x) rrp += R[t] * R[t];
         double v2[2] = {bbp, rrp};
@@ -1458,6 +1534,8 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.dir_old = L.dir_old;
             a.dir_out = (VT*)L.dir_out;
             a.fd_w2 = sh.fd_w2;
+            a.npart = L.npart;
+            a.npart_n = L.npart_n;
             // 3-D: the plane form when its staging fits the shared region
             a.fd_rows = 0;
             if (L.fd.on && L.fd.nd == 3 && L.fd.Z2 != nullptr) {
@@ -1591,7 +1669,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only,
-                             bool dir_ready) {
+                             bool dir_ready, const void* fdS, void* fdZ, float* npart) {
     if (op.n == 0) return cudaSuccess;
     // Dirichlet increments for the flagged slices (unless the projection wrote them)
     const bool prep = only != 1 && n_dir > 0 && !dir_ready;
@@ -1602,14 +1680,16 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         float* g1 = dg + n_dir;
         if (prep) k_dir_prep<float><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, dg, g1,
-                         F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only};
+                         F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
+                         (const float*)fdS, (float*)fdZ, npart};
         k_theta_rhs<float><<<blocks, 256, 0, s>>>(a);
     } else {
         double* dg = (double*)dir_scratch;
         double* g1 = dg + n_dir;
         if (prep) k_dir_prep<double><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev, dg,
-                          g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only};
+                          g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
+                          (const double*)fdS, (double*)fdZ, npart};
         k_theta_rhs<double><<<blocks, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
