@@ -281,7 +281,7 @@ sa_status upload_fd(sa_ctx* c, FdData& f, int n_rows) {
     }
     cudaError_t e = f.S.alloc((size_t)std::max(n_rows, 1) * (f32 ? 4 : 8));
     if (e == cudaSuccess) e = f.Z.alloc((size_t)std::max(n_rows, 1) * (f32 ? 4 : 8));
-    if (e == cudaSuccess && f.nd == 3) e = f.Z2.alloc((size_t)std::max(n_rows, 1) * (f32 ? 4 : 8));
+    if (e == cudaSuccess) e = f.Z2.alloc((size_t)std::max(n_rows, 1) * (f32 ? 4 : 8));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return sa_fail(c, SA_ERR_OOM, "fast-diagonalization vectors");

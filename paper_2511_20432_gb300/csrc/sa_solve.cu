@@ -999,7 +999,8 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
 // entries) and forms its slab as two small products.
 template <typename VT>
 __device__ void plane_slab(const VT* src, VT* dst, const VT* Sv, const VT* W1, const VT* W0,
-                           int m0, int m1, int plane, int j0, int nrow, VT* wbuf) {
+                           int m0, int m1, int plane, int j0, int nrow, VT* wbuf,
+                           const FdView* dg = nullptr) {
     VT* X = wbuf;                       // m1 x m0
     VT* A1 = X + m0 * m1;               // m1 x m1: W1[a][o]
     VT* A0 = A1 + m1 * m1;              // m0 x m0: W0[a][o]
@@ -1026,6 +1027,8 @@ __device__ void plane_slab(const VT* src, VT* dst, const VT* Sv, const VT* W1, c
 #pragma unroll 4
         for (int i = 0; i < m0; ++i) acc = fma(A0[i * m0 + o], Tm[r * m0 + i], acc);
         const long long idx = base + (long long)(j0 + r) * m0 + o;
+        if (dg)   // 2-D: the diagonal D = 1 / (c_M + c_0 lambda_0 + c_1 lambda_1)
+            acc = acc / ((VT)dg->cM + ((const VT*)dg->lamc[0])[o] + ((const VT*)dg->lamc[1])[j0 + r]);
         dst[idx] = Sv ? Sv[idx] * acc : acc;
     }
 }
@@ -1040,6 +1043,21 @@ __device__ bool fd_apply_planes(const FdView& fd, const GridSync& sync, VT* wbuf
     const VT* S = (const VT*)fd.S;
     const int nslab = (m1 + rows - 1) / rows;
     const int items = m2 * nslab;
+    if (fd.nd == 2) {
+        // one plane: A with the diagonal applied, then C (one grid barrier)
+        for (int it = blockIdx.x; it < nslab; it += gridDim.x) {
+            const int j0 = it * rows;
+            plane_slab<VT>(Z, Z2, nullptr, (const VT*)fd.U[1], (const VT*)fd.U[0], m0, m1, 0, j0,
+                           min(rows, m1 - j0), wbuf, &fd);
+        }
+        if (!sync.barrier()) return false;
+        for (int it = blockIdx.x; it < nslab; it += gridDim.x) {
+            const int j0 = it * rows;
+            plane_slab<VT>(Z2, out, S, (const VT*)fd.Ut[1], (const VT*)fd.Ut[0], m0, m1, 0, j0,
+                           min(rows, m1 - j0), wbuf);
+        }
+        return true;
+    }
     // A: planes of Z -> Z2
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int p = it / nslab, j0 = (it - p * nslab) * rows;
@@ -1463,6 +1481,21 @@ struct PcgShape {
 
 constexpr size_t kSmemCap = 200 * 1024;
 
+// Plane form of the preconditioner (3-D: planes over the blocks in slabs;
+// 2-D: the one plane in slabs): rows per slab, and the shared entries it
+// stages (a plane, the two m x m matrices, a slab); 0 rows: the line form.
+inline int plane_slab_rows(const FdView& fd, int G) {
+    if (!fd.on || fd.Z2 == nullptr || (fd.nd != 2 && fd.nd != 3)) return 0;
+    const int m1 = fd.m[1], m2 = fd.nd == 3 ? fd.m[2] : 1;
+    if (m2 > 32 * kFdPerLane) return 0;
+    const int nslab = std::max(1, G / std::max(m2, 1));
+    return (m1 + nslab - 1) / nslab;
+}
+inline long long plane_slab_need(const FdView& fd, int rows) {
+    const long long m0 = fd.m[0], m1 = fd.m[1], m2 = fd.nd == 3 ? fd.m[2] : 1;
+    return std::max(m0 * m1 + m0 * m0 + m1 * m1 + rows * m0, 2 * m2 * m2);
+}
+
 template <typename VT>
 PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
     PcgShape<VT> sh;
@@ -1490,11 +1523,23 @@ PcgShape<VT> pcg_shape(const PcgLaunch& L, bool pipelined) {
         fdw = 3ll * mmax * mmax;
         sh.fd_w2 = 1;
     }
+    // the plane form's staging, when it fits
+    const int prows = pipelined ? plane_slab_rows(L.fd, sh.G) : 0;
+    if (prows > 0) {
+        const long long need = plane_slab_need(L.fd, prows);
+        if (fixed + need * sizeof(VT) <= kSmemCap) fdw = std::max(fdw, need);
+    }
     sh.window = L.op.col16 != nullptr && L.pad >= -L.op.dmin + 4 && L.pad >= L.op.dmax + 4 &&
                 fixed + std::max(sh.wl, fdw) * sizeof(VT) <= kSmemCap;
     sh.region = sh.window ? std::max(sh.wl, fdw) : fdw;
     sh.smem = fixed + (size_t)sh.region * sizeof(VT);
     return sh;
+}
+
+template <typename VT>
+int plane_rows(const PcgLaunch& L, const PcgShape<VT>& sh) {
+    const int rows = plane_slab_rows(L.fd, sh.G);
+    return rows > 0 && plane_slab_need(L.fd, rows) <= sh.region ? rows : 0;
 }
 
 cudaError_t launch_coop(const void* fn, int G, int block, size_t smem, void* args, cudaStream_t s) {
@@ -1537,16 +1582,7 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.npart = L.npart;
             a.npart_n = L.npart_n;
             // 3-D: the plane form when its staging fits the shared region
-            a.fd_rows = 0;
-            if (L.fd.on && L.fd.nd == 3 && L.fd.Z2 != nullptr) {
-                const int m0 = L.fd.m[0], m1 = L.fd.m[1], m2 = L.fd.m[2];
-                const int nslab = std::max(1, sh.G / std::max(m2, 1));
-                const int rows = (m1 + nslab - 1) / nslab;
-                const long long need = (long long)m0 * m1 + (long long)m0 * m0 + (long long)m1 * m1 +
-                                       (long long)rows * m0;
-                if (need <= sh.region && 2ll * m2 * m2 <= sh.region && m2 <= 32 * kFdPerLane)
-                    a.fd_rows = rows;
-            }
+            a.fd_rows = plane_rows(L, sh);
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
         }
         if (L.variant == SA_PCG_SHARED) return cudaErrorInvalidConfiguration;
