@@ -253,13 +253,14 @@ __device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, 
 //   b = (rho c_p/dt) M T^n - (1-theta) k K T^n + theta F^{n+1} + (1-theta) F^n
 //       - A_fd g^{n+1},   with M T^n = T_c (M 1) + M (T^n - T_c)
 // and A_fd = (rho c_p/dt) M_fd + theta k K_fd.
-constexpr int kRhsSplit = 4;   // warps sharing one slice's columns
-
-template <typename VT>
+// Warps sharing one slice's columns: 4 when every slice runs (two slices a
+// block), 8 for the slices with Dirichlet columns alone (a short launch on
+// the step's critical path: more warps in flight per SM).
+template <int kRhsSplit, typename VT>
 __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
-    // 8 warps: two slices, each split over kRhsSplit warps by columns (enough
-    // warps in flight to cover the memory latency); partial sums combined in
-    // fixed order
+    // 8 warps: 8 / kRhsSplit slices, each split over kRhsSplit warps by
+    // columns (enough warps in flight to cover the memory latency); partial
+    // sums combined in fixed order
     __shared__ VT part[8][7][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int sl = blockIdx.x * (8 / kRhsSplit) + wib / kRhsSplit;
@@ -1709,7 +1710,9 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
     if (op.n == 0) return cudaSuccess;
     // Dirichlet increments for the flagged slices (unless the projection wrote them)
     const bool prep = only != 1 && n_dir > 0 && !dir_ready;
-    const unsigned blocks = (unsigned)((op.n_slices + (8 / kRhsSplit) - 1) / (8 / kRhsSplit));
+    // the Dirichlet-column slices alone: one slice a block, eight warps on it
+    const int split = only == 2 ? 8 : 4;
+    const unsigned blocks = (unsigned)((op.n_slices + (8 / split) - 1) / (8 / split));
     const unsigned pblocks = (unsigned)((n_dir + 255) / 256);
     if (precision == SA_MIXED) {
         float* dg = (float*)dir_scratch;
@@ -1718,7 +1721,10 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, dg, g1,
                          F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
                          (const float*)fdS, (float*)fdZ, npart};
-        k_theta_rhs<float><<<blocks, 256, 0, s>>>(a);
+        if (split == 8)
+            k_theta_rhs<8, float><<<blocks, 256, 0, s>>>(a);
+        else
+            k_theta_rhs<4, float><<<blocks, 256, 0, s>>>(a);
     } else {
         double* dg = (double*)dir_scratch;
         double* g1 = dg + n_dir;
@@ -1726,7 +1732,10 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev, dg,
                           g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
                           (const double*)fdS, (double*)fdZ, npart};
-        k_theta_rhs<double><<<blocks, 256, 0, s>>>(a);
+        if (split == 8)
+            k_theta_rhs<8, double><<<blocks, 256, 0, s>>>(a);
+        else
+            k_theta_rhs<4, double><<<blocks, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
