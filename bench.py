@@ -831,11 +831,12 @@ def run_ours(args):
     warm = 1 if guess == sa.SA_GUESS_EXTRAPOLATE else 0
     # algorithmic bytes of one main-solve launch: every SpMV reads the FP32
     # values and 16-bit column offsets once and the published vector once;
-    # set-up reads r0, b^2, D^{-1} (FP64 and FP32), reads and writes x;
-    # fast diagonalization: each application (one at set-up, one per further
-    # iteration) reads and writes the FP32 vector in five line passes
-    pcg_bytes = ((iters_t + warm) * (6 * nnz_a + 4 * n_free) + (44 + 4 * warm) * n_free +
-                 max(iters_t, 1.0) * 5 * 8 * n_free)
+    # set-up reads r0 and D^{-1} (FP64), reads and writes x (FP64), reads u
+    # back (FP32); fast diagonalization: each application (one at set-up, one
+    # per further iteration) reads and writes the FP32 vector in its three
+    # plane-form passes and reads the scaling S
+    pcg_bytes = ((iters_t + warm) * (6 * nnz_a + 4 * n_free) + (36 + 4 * warm) * n_free +
+                 max(iters_t, 1.0) * (3 * 8 + 4) * n_free)
     # history: pairwise, FP32 lane-operations per pair (flux 8, T 6) on 128
     # FP32 lanes/clk/SM (MUFU ex2, 32/clk/SM, not binding); separable, one
     # FFMA per pair (the factors' exponentials are overhead)
