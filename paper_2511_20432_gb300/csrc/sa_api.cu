@@ -1293,6 +1293,7 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                                 cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "recorder input");
     }
+    bool fin_fused = false;
     {
         PcgLaunch L;
         L.dx0 = dx0;
@@ -1323,6 +1324,19 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.max_iter = c->opt.pcg_max_iter;
         L.grid = c->pcg_grid;
         L.ksplit = 0;
+        // the step's finalize in the solve's tail when the shared-memory
+        // solve runs and nothing reads the state between them (no recorder,
+        // no stage timing)
+        fin_fused = !rec && !timing && c->opt.pcg_variant != SA_PCG_GLOBAL &&
+                    pcg_shared_fits(c->opt.precision, L);
+        if (fin_fused) {
+            L.fin_F1 = c->F1.p;
+            L.fin_F0 = c->F0.p;
+            L.fin_g = c->gnew.p;
+            L.fin_That = c->That.p;
+            L.fin_n_dof = c->n_dof;
+            L.fin_n_dir = c->n_dir;
+        }
         e = launch_pcg(c->opt.precision, L, s);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "PCG");
     }
@@ -1333,9 +1347,11 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         c->rec_count += 1;
     }
     SA_MARK(SA_STAGE_FINALIZE);
-    e = launch_finalize(c->n_dir, c->n_free, c->n_dof, c->gnew.p, c->That.p, c->F1.p, c->F0.p,
-                        c->st.p, s);
-    if (e != cudaSuccess) return sa_cuda_fail(c, e, "finalize");
+    if (!fin_fused) {
+        e = launch_finalize(c->n_dir, c->n_free, c->n_dof, c->gnew.p, c->That.p, c->F1.p, c->F0.p,
+                            c->st.p, s);
+        if (e != cudaSuccess) return sa_cuda_fail(c, e, "finalize");
+    }
     SA_MARK(SA_N_STAGES);
 #undef SA_MARK
     if (timing) {

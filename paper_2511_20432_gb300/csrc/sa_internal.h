@@ -260,6 +260,13 @@ struct PcgLaunch {
     // needs no exchange for the norms (null: it forms them itself)
     const float* npart = nullptr;
     int npart_n = 0;
+    // shared-memory variant, optional: the step's finalize after the solve
+    // (That[n_free + d] = g[d], F0 = F1, the step counters); x must be That
+    const double* fin_F1 = nullptr;
+    double* fin_F0 = nullptr;
+    const double* fin_g = nullptr;
+    double* fin_That = nullptr;
+    int fin_n_dof = 0, fin_n_dir = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -792,6 +792,12 @@ struct SmemArgs {
     FdView fd;             // fast-diagonalization preconditioner (fd.on), else Jacobi
     const float* npart;    // with r0 and fd: the producer's per-slice (b^2, r0^2) sums and
     int npart_n;           // Z = S r0 already written (slices), else null
+    // non-null fin_F1: the step's finalize at the end (see PcgLaunch)
+    const double* fin_F1;
+    double* fin_F0;
+    const double* fin_g;
+    double* fin_That;      // That + ... : the Dirichlet entries start at n (= n_free)
+    int fin_n_dof, fin_n_dir;
     int fd_mmax;           // longest grid line (per-warp scratch entries)
     int plan_wcap;         // window entries reserved in shared memory
     const double* dir_old; // see PcgLaunch
@@ -1425,6 +1431,21 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             if (state != 1) atomicOr(err, SA_DEV_BOT_NOT_CONVERGED);
         }
         if (state == 2) atomicOr(err, SA_DEV_NAN);
+        if (a.fin_F1) {   // the step's counters (after this solve's own)
+            a.st->n += 1;
+            a.st->iters_total += a.st->pcg_iters;
+            a.st->bot_total += a.st->bot_iters;
+            if (a.st->pcg_iters > a.st->iters_max) a.st->iters_max = a.st->pcg_iters;
+        }
+    }
+    if (a.fin_F1) {
+        // the step's end (what k_finalize does otherwise): the Dirichlet
+        // control variables take g^{n+1}, F^n <- F^{n+1}; no kernel of its own
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.fin_n_dof;
+             i += gridDim.x * blockDim.x) {
+            a.fin_F0[i] = __ldcg(a.fin_F1 + i);
+            if (i < a.fin_n_dir) a.fin_That[n + i] = __ldcg(a.fin_g + i);
+        }
     }
 }
 
@@ -1582,6 +1603,12 @@ cudaError_t launch_pcg_t(const PcgLaunch& L, cudaStream_t s) {
             a.fd_w2 = sh.fd_w2;
             a.npart = L.npart;
             a.npart_n = L.npart_n;
+            a.fin_F1 = L.fin_F1;
+            a.fin_F0 = L.fin_F0;
+            a.fin_g = L.fin_g;
+            a.fin_That = L.fin_That;
+            a.fin_n_dof = L.fin_n_dof;
+            a.fin_n_dir = L.fin_n_dir;
             // 3-D: the plane form when its staging fits the shared region
             a.fd_rows = plane_rows(L, sh);
             return launch_coop((const void*)k_pcg_smem<VT>, sh.G, sh.block, sh.smem, &a, s);
