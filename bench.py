@@ -873,8 +873,8 @@ def run_ours(args):
     # each, and no prologue in the mixed path), gather (bottom, lateral),
     # projection (which also writes the Dirichlet increments: the block's
     # projection runs in shared memory), right-hand side (two slice sets),
-    # PCG, finalize
-    launches_per_step = 10 + warm + ((1 if prec == sa.SA_MIXED else 2) if sep else 0)
+    # PCG (which also finalizes the step)
+    launches_per_step = 9 + warm + ((1 if prec == sa.SA_MIXED else 2) if sep else 0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
