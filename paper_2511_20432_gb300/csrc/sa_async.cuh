@@ -1,5 +1,6 @@
-// Device helpers shared by the kernels: mbarrier and bulk asynchronous copy
-// (TMA engine) primitives in inline PTX, the global timer, bounded waits.
+// Device helpers shared by the kernels: mbarrier, bulk asynchronous copy
+// (TMA engine) and per-thread asynchronous copy primitives in inline PTX, the
+// global timer, bounded waits.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -57,6 +58,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     }
     return false;
 }
+
+// Per-thread asynchronous copies global -> shared (cp.async, no registers
+// held while in flight): 16-byte chunks bypassing L1 (.cg: data other blocks
+// may have written in the same launch), or 4/8/16-byte elements through L1
+// (.ca: data constant during the launch).  The issuing thread waits for all
+// of its copies with cp_async_wait_all; other threads see them after a block
+// barrier that follows that wait.
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <int kBytes>
+__device__ __forceinline__ void cp_async_ca(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(kBytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Orders this thread's earlier generic-proxy accesses (and those it has
 // acquired) before its later async-proxy (bulk copy) accesses.

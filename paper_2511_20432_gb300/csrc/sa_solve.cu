@@ -1001,42 +1001,93 @@ __device__ bool fd_apply(const FdView& fd, const GridSync& sync, VT* wbuf, VT* x
 //   C  every plane becomes U_1 X U_0^T, times S, -> out.
 // A plane is split into slabs of `rows` output rows over several blocks (the
 // block count over the plane count), so that every SM works and no block
-// transforms a whole plane alone; each block stages the plane and the two
-// m x m matrices in shared memory (wbuf: m0 m1 + m0^2 + m1^2 + rows m0
-// entries) and forms its slab as two small products.
+// transforms a whole plane alone; each block stages the plane, the m0 x m0
+// matrix and its slab's columns of the m1 x m1 one in shared memory (wbuf:
+// plane_slab_need entries) and forms its slab as two small products.
+//
+// The staging is asynchronous (cp.async): every copy of a thread is in flight
+// at once, one L2 round trip for the whole stage instead of one per element
+// that a load-then-store loop costs.  The plane is data other blocks wrote in
+// this launch, so it goes in 16-byte chunks around L1 (.cg); the constant
+// matrices go element by element through L1 (.ca).
+
+// Shared-memory entries plane_slab stages for slabs of `rows` rows (16-byte
+// alignment slack included).
+__host__ __device__ inline long long plane_stage_entries(int m0, int m1, int rows) {
+    return (long long)m0 * m1 + (long long)m0 * m0 + (long long)m1 * rows + (long long)rows * m0 +
+           m0 + rows + 4;
+}
+
 template <typename VT>
 __device__ void plane_slab(const VT* src, VT* dst, const VT* Sv, const VT* W1, const VT* W0,
                            int m0, int m1, int plane, int j0, int nrow, VT* wbuf,
                            const FdView* dg = nullptr) {
-    VT* X = wbuf;                       // m1 x m0
-    VT* A1 = X + m0 * m1;               // m1 x m1: W1[a][o]
-    VT* A0 = A1 + m1 * m1;              // m0 x m0: W0[a][o]
-    VT* Tm = A0 + m0 * m0;              // nrow x m0
+    // X (16-byte aligned) m1 x m0; A0 m0 x m0: W0[i][o]; A1 m1 x nrow:
+    // W1[j][j0 + r]; Tm nrow x m0; 2-D: lambda_0 (m0), lambda_1 of the rows
+    VT* X = (VT*)(((uintptr_t)wbuf + 15) & ~(uintptr_t)15);
+    VT* A0 = X + m0 * m1;
+    VT* A1 = A0 + m0 * m0;
+    VT* Tm = A1 + m1 * nrow;
+    VT* dl0 = Tm + nrow * m0;
+    VT* dl1 = dl0 + m0;
     const long long base = (long long)plane * m0 * m1;
+    const int nx = m0 * m1;
     __syncthreads();                    // wbuf free
-    for (int t = threadIdx.x; t < m0 * m1; t += blockDim.x) X[t] = __ldcg(src + base + t);
-    for (int t = threadIdx.x; t < m1 * m1; t += blockDim.x) A1[t] = __ldg(W1 + t);
-    for (int t = threadIdx.x; t < m0 * m0; t += blockDim.x) A0[t] = __ldg(W0 + t);
+    const VT* xsrc = src + base;
+    if ((nx * (int)sizeof(VT)) % 16 == 0 && ((uintptr_t)xsrc & 15) == 0) {
+        const int nc = nx * (int)sizeof(VT) / 16;
+        for (int t = threadIdx.x; t < nc; t += blockDim.x)
+            cp_async_cg16((char*)X + 16 * t, (const char*)xsrc + 16 * t);
+    } else {
+        for (int t = threadIdx.x; t < nx; t += blockDim.x) X[t] = __ldcg(xsrc + t);
+    }
+    for (int t = threadIdx.x; t < m0 * m0; t += blockDim.x) cp_async_ca<sizeof(VT)>(A0 + t, W0 + t);
+    for (int t = threadIdx.x; t < m1 * nrow; t += blockDim.x) {
+        const int j = t / nrow, r = t - j * nrow;
+        cp_async_ca<sizeof(VT)>(A1 + t, W1 + j * m1 + j0 + r);
+    }
+    if (dg) {
+        for (int t = threadIdx.x; t < m0 + nrow; t += blockDim.x) {
+            if (t < m0) cp_async_ca<sizeof(VT)>(dl0 + t, (const VT*)dg->lamc[0] + t);
+            else cp_async_ca<sizeof(VT)>(dl1 + (t - m0), (const VT*)dg->lamc[1] + j0 + (t - m0));
+        }
+    }
+    cp_async_wait_all();
     __syncthreads();
-    // T[r][i] = sum_j W1[j][j0 + r] X[j][i]
+    // T[r][i] = sum_j W1[j][j0 + r] X[j][i], one output a thread, the sum in
+    // three interleaved partial sums (j mod 3: a third of the dependent chain)
     for (int t = threadIdx.x; t < nrow * m0; t += blockDim.x) {
         const int r = t / m0, i = t - r * m0;
-        VT acc = (VT)0;
-#pragma unroll 4
-        for (int j = 0; j < m1; ++j) acc = fma(A1[j * m1 + j0 + r], X[j * m0 + i], acc);
-        Tm[t] = acc;
+        VT s0 = (VT)0, s1 = (VT)0, s2 = (VT)0;
+        int j = 0;
+#pragma unroll 2
+        for (; j + 3 <= m1; j += 3) {
+            s0 = fma(A1[j * nrow + r], X[j * m0 + i], s0);
+            s1 = fma(A1[(j + 1) * nrow + r], X[(j + 1) * m0 + i], s1);
+            s2 = fma(A1[(j + 2) * nrow + r], X[(j + 2) * m0 + i], s2);
+        }
+        for (; j < m1; ++j) s0 = fma(A1[j * nrow + r], X[j * m0 + i], s0);
+        Tm[t] = (s0 + s1) + s2;
     }
     __syncthreads();
-    // Y[r][o] = sum_i W0[i][o] T[r][i]
+    // Y[r][o] = sum_i W0[i][o] T[r][i], the same way
     for (int t = threadIdx.x; t < nrow * m0; t += blockDim.x) {
         const int r = t / m0, o = t - r * m0;
-        VT acc = (VT)0;
-#pragma unroll 4
-        for (int i = 0; i < m0; ++i) acc = fma(A0[i * m0 + o], Tm[r * m0 + i], acc);
+        const VT* Tr = Tm + r * m0;
+        VT s0 = (VT)0, s1 = (VT)0, s2 = (VT)0;
+        int i = 0;
+#pragma unroll 2
+        for (; i + 3 <= m0; i += 3) {
+            s0 = fma(A0[i * m0 + o], Tr[i], s0);
+            s1 = fma(A0[(i + 1) * m0 + o], Tr[i + 1], s1);
+            s2 = fma(A0[(i + 2) * m0 + o], Tr[i + 2], s2);
+        }
+        for (; i < m0; ++i) s0 = fma(A0[i * m0 + o], Tr[i], s0);
+        VT v = (s0 + s1) + s2;
         const long long idx = base + (long long)(j0 + r) * m0 + o;
         if (dg)   // 2-D: the diagonal D = 1 / (c_M + c_0 lambda_0 + c_1 lambda_1)
-            acc = acc / ((VT)dg->cM + ((const VT*)dg->lamc[0])[o] + ((const VT*)dg->lamc[1])[j0 + r]);
-        dst[idx] = Sv ? Sv[idx] * acc : acc;
+            v = v / ((VT)dg->cM + dl0[o] + dl1[r]);
+        dst[idx] = Sv ? Sv[idx] * v : v;
     }
 }
 
@@ -1071,21 +1122,28 @@ __device__ bool fd_apply_planes(const FdView& fd, const GridSync& sync, VT* wbuf
         plane_slab<VT>(Z, Z2, nullptr, (const VT*)fd.U[1], (const VT*)fd.U[0], m0, m1, p, j0,
                        min(rows, m1 - j0), wbuf);
     }
-    // stage U_2 and U_2^T for B while waiting
+    // stage U_2, U_2^T and the three lambda lists for B while waiting
     __syncthreads();
     VT* W2 = wbuf;
     VT* W2t = wbuf + m2 * m2;
+    VT* l0 = W2t + m2 * m2;
+    VT* l1 = l0 + m0;
+    VT* l2 = l1 + m1;
     for (int t = threadIdx.x; t < m2 * m2; t += blockDim.x) {
-        W2[t] = __ldg((const VT*)fd.U[2] + t);
-        W2t[t] = __ldg((const VT*)fd.Ut[2] + t);
+        cp_async_ca<sizeof(VT)>(W2 + t, (const VT*)fd.U[2] + t);
+        cp_async_ca<sizeof(VT)>(W2t + t, (const VT*)fd.Ut[2] + t);
     }
+    for (int t = threadIdx.x; t < m0 + m1 + m2; t += blockDim.x) {
+        const VT* from = t < m0 ? (const VT*)fd.lamc[0] + t
+                                : (t < m0 + m1 ? (const VT*)fd.lamc[1] + (t - m0)
+                                               : (const VT*)fd.lamc[2] + (t - m0 - m1));
+        cp_async_ca<sizeof(VT)>(l0 + t, from);
+    }
+    cp_async_wait_all();
     if (!sync.barrier()) return false;
     // B: z-lines of Z2 -> Z (one warp a line, lines over all blocks' warps)
     const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * (blockDim.x >> 5);
-    const VT* l0 = (const VT*)fd.lamc[0];
-    const VT* l1 = (const VT*)fd.lamc[1];
-    const VT* l2 = (const VT*)fd.lamc[2];
     const VT cM = (VT)fd.cM;
     const int plane = m0 * m1;
     for (int L = gw; L < plane; L += nw) {
@@ -1166,10 +1224,18 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     const int nr = row1 - row0;
     const int lane = threadIdx.x & 31;
     // ---- initial residual and the norm of b
+    // With the fast diagonalization the Jacobi scaling DI is unused: its
+    // slot takes this block's rows of x, copied asynchronously now for the
+    // update at the end (no load on the way out).
     double bbp = 0.0;
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-        DI[t] = a.dinv[row0 + t];
+        if (fd) cp_async_ca<8>(DI + t, a.x + row0 + t);
+        else DI[t] = a.dinv[row0 + t];
         D[t] = S[t] = P[t] = 0.0;
+        if (a.r0 != nullptr) {
+            R[t] = a.r0[row0 + t];
+            bbp += a.bsq[row0 + t];
+        }
     }
     if (a.r0 == nullptr) {      // mode 0: r = b - A x in FP64 (global gathers of x)
         const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
@@ -1189,11 +1255,6 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
                 R[i - row0] = bi - acc;
                 bbp += bi * bi;
             }
-        }
-    } else {
-        for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-            R[t] = a.r0[row0 + t];
-            bbp += a.bsq[row0 + t];
         }
     }
     __syncthreads();
@@ -1240,9 +1301,20 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
         // order (identical in every block, so every block takes the same
         // branch below)
         float v2[2] = {0.f, 0.f};
-        for (int q = threadIdx.x; q < a.npart_n; q += blockDim.x) {
-            v2[0] += __ldcg(a.npart + 2 * q);
-            v2[1] += __ldcg(a.npart + 2 * q + 1);
+        const float2* np2 = (const float2*)a.npart;
+        for (int q0 = 0; q0 < a.npart_n; q0 += 4 * (int)blockDim.x) {
+            // four loads in flight, then the adds in the same order
+            float2 pv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + u * blockDim.x + threadIdx.x;
+                pv[u] = q < a.npart_n ? __ldcg(np2 + q) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v2[0] += pv[u].x;
+                v2[1] += pv[u].y;
+            }
         }
         block_sum<2>(v2, nb2);
         pre = isfinite(nb2[0]) && isfinite(nb2[1]);   // else the FP64 norms below
@@ -1250,11 +1322,13 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     if (fd && !pre)
         for (int t = threadIdx.x; t < nr; t += blockDim.x) Zf[row0 + t] = Sf[row0 + t] * (VT)R[t];
     if (pre) {
+        // the sums are FP32: sigma and the relative norm in FP32 too (FP64
+        // division and square root are slow on this part)
         bb = (double)nb2[0];
-        const double rr = (double)nb2[1];
         if (threadIdx.x == 0) {
-            sc[2] = bb > 0.0 ? 1.0 / sqrt(bb) : 1.0;
-            const double rr0 = bb > 0.0 ? rr / bb : rr;
+            const float b2 = nb2[0], r2 = nb2[1];
+            sc[2] = b2 > 0.f ? (double)(1.f / sqrtf(b2)) : 1.0;
+            const double rr0 = (double)(b2 > 0.f ? r2 / b2 : r2);
             sc[3] = rr0;
             state = !(rr0 == rr0) ? 2 : (rr0 <= a.tol * a.tol ? 1 : 0);
         }
@@ -1371,6 +1445,15 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
         __syncthreads();
         if (state != 0) break;
         const double al = sc[0], be = sc[1];
+        if (shortcut) {
+            // converged by the estimate: only the step (p = u, beta = 0 at
+            // the first update) goes on to x
+            for (int t = threadIdx.x; t < nr; t += blockDim.x) D[t] = fma(al, U[t], D[t]);
+            ++it;
+            if (threadIdx.x == 0) state = 1;
+            __syncthreads();
+            break;
+        }
         // ---- V: own rows; (r, r) of the update
         AT vr[1] = {(AT)0};
         for (int t = threadIdx.x; t < nr; t += blockDim.x) {
@@ -1385,7 +1468,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             R32[t] = r32;
             vr[0] += r32 * r32;
             if (fd) {
-                Zf[row0 + t] = Sf[row0 + t] * (VT)r;
+                Zf[row0 + t] = Sf[row0 + t] * (VT)r;   // the next application's input
             } else {
                 const double u = DI[t] * r;
                 U[t] = u;
@@ -1394,11 +1477,6 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             }
         }
         ++it;
-        if (shortcut) {
-            if (threadIdx.x == 0) state = 1;
-            __syncthreads();
-            break;
-        }
         block_sum<1>(vr, blt);
         if (!grid_exchange<1>(sync, blt, 2 + 4 * (it & 1), res)) return;
         if (threadIdx.x == 0) {
@@ -1410,8 +1488,17 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
         if (state != 0) break;
         if (!precondition()) return;
     }
+    // the step's finalize inputs (one per thread when the grid covers them)
+    // in flight together with the last reads of x
+    const int fi = blockIdx.x * blockDim.x + threadIdx.x;
+    double f1v = 0.0, gv = 0.0;
+    if (a.fin_F1 && fi < a.fin_n_dof) {
+        f1v = __ldcg(a.fin_F1 + fi);
+        if (fi < a.fin_n_dir) gv = __ldcg(a.fin_g + fi);
+    }
+    if (fd) cp_async_wait_all();   // this thread's rows of x in DI
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-        const double xn = a.x[row0 + t] + D[t];
+        const double xn = (fd ? DI[t] : a.x[row0 + t]) + D[t];
         a.x[row0 + t] = xn;
         if (a.dir_out) {
             a.dir_out[row0 + t] = (VT)(xn - a.dir_old[row0 + t]);
@@ -1441,10 +1528,9 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
     if (a.fin_F1) {
         // the step's end (what k_finalize does otherwise): the Dirichlet
         // control variables take g^{n+1}, F^n <- F^{n+1}; no kernel of its own
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.fin_n_dof;
-             i += gridDim.x * blockDim.x) {
-            a.fin_F0[i] = __ldcg(a.fin_F1 + i);
-            if (i < a.fin_n_dir) a.fin_That[n + i] = __ldcg(a.fin_g + i);
+        for (int i = fi; i < a.fin_n_dof; i += gridDim.x * blockDim.x) {
+            a.fin_F0[i] = i == fi ? f1v : __ldcg(a.fin_F1 + i);
+            if (i < a.fin_n_dir) a.fin_That[n + i] = i == fi ? gv : __ldcg(a.fin_g + i);
         }
     }
 }
@@ -1515,7 +1601,8 @@ inline int plane_slab_rows(const FdView& fd, int G) {
 }
 inline long long plane_slab_need(const FdView& fd, int rows) {
     const long long m0 = fd.m[0], m1 = fd.m[1], m2 = fd.nd == 3 ? fd.m[2] : 1;
-    return std::max(m0 * m1 + m0 * m0 + m1 * m1 + rows * m0, 2 * m2 * m2);
+    // a slab's staging, or the z-line pass's (U_2, U_2^T, the three lambda lists)
+    return std::max(plane_stage_entries((int)m0, (int)m1, rows), 2 * m2 * m2 + m0 + m1 + m2);
 }
 
 template <typename VT>
