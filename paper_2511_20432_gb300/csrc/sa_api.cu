@@ -346,11 +346,13 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
     if (!opt.stage_timing &&
         (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_hist, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         if (c->ev_join) cudaEventDestroy(c->ev_join);
+        if (c->ev_hist) cudaEventDestroy(c->ev_hist);
         delete c;
         return SA_ERR_CUDA;
     }
@@ -367,6 +369,7 @@ void sa_destroy(sa_ctx* c) {
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_hist) cudaEventDestroy(c->ev_hist);
     if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
@@ -1155,9 +1158,14 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     }
     SA_MARK(SA_STAGE_HISTORY);
     for (int part = overlap ? 2 : 0; part >= (overlap ? 1 : 0); --part) {
-        if (c->sep.ok)
+        if (c->sep.ok) {
+            // the bottom chain is the longer one: its sums run first with the
+            // whole GPU, the lateral sums after them (beside the bottom
+            // gather and projection)
             e = launch_sep(c, part, dt, part == 2 ? sb : s);
-        else
+            if (e == cudaSuccess && overlap && part == 2) e = cudaEventRecord(c->ev_hist, sb);
+            if (e == cudaSuccess && overlap && part == 2) e = cudaStreamWaitEvent(s, c->ev_hist, 0);
+        } else
             e = launch_history(c->opt.precision, c->hist_P, c->hist_W, c->st.p, c->q_lat,
                                c->q_bot, c->lat32.p, c->bot32.p, c->lat64.p, c->bot64.p,
                                c->x_ref, c->y_ref, c->z_top, c->src32F.p, c->src32T.p,
@@ -1235,10 +1243,12 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
         L.which = 1;
         L.tol = c->opt.pcg_tol;
         L.max_iter = c->opt.pcg_max_iter;
-        // small system: a few blocks of ~8 slices, so that most SMs stay
-        // free for the lateral chain beside it
-        L.grid = std::max(1, std::min(c->pcg_grid, (c->mbot_s.n_slices + 7) / 8));
-        L.block = 0;
+        // small system: a few blocks of ~4 slices, so that most SMs stay
+        // free for the lateral chain beside it; 512-thread blocks (half an
+        // SM's registers), so that a block starts beside the lateral sums'
+        // CTAs instead of waiting for an SM they have left
+        L.grid = std::max(1, std::min(c->pcg_grid, 2 * ((c->mbot_s.n_slices + 7) / 8)));
+        L.block = 512;
         L.ksplit = 0;
         // the shared-memory solve also writes g^{n+1} - g^n and g^{n+1} for
         // the right-hand side (no separate kernel after it)

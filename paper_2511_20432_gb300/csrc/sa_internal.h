@@ -448,6 +448,7 @@ struct sa_ctx {
     // points, b_bot, the projection) runs beside the lateral chain
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_hist = nullptr;   // the bottom history sums done (the lateral ones wait)
     double stage_ms[SA_N_STAGES] = {};
     long long stage_steps = 0;
 };
