@@ -347,12 +347,14 @@ sa_status sa_create(const sa_options* o, sa_ctx** out) {
         (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&c->ev_hist, cudaEventDisableTiming) != cudaSuccess)) {
+         cudaEventCreateWithFlags(&c->ev_hist, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_lat, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         if (c->ev_join) cudaEventDestroy(c->ev_join);
         if (c->ev_hist) cudaEventDestroy(c->ev_hist);
+        if (c->ev_lat) cudaEventDestroy(c->ev_lat);
         delete c;
         return SA_ERR_CUDA;
     }
@@ -370,6 +372,7 @@ void sa_destroy(sa_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_hist) cudaEventDestroy(c->ev_hist);
+    if (c->ev_lat) cudaEventDestroy(c->ev_lat);
     if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
@@ -1267,20 +1270,29 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
     const FdView fdm_view = fd_view(c, c->fdm);
     const bool rhs_pre = fdm_view.on && !extrap && !c->ws_net && c->npart.p &&
                          c->npart.n >= (size_t)2 * c->r_s.n_slices;
-    for (int only = overlap ? 1 : 0; only <= (overlap ? 2 : 0); ++only) {
-        if (only == 2) {   // join: the projection is done
-            SA_CUDA(c, cudaEventRecord(c->ev_join, sb));
-            SA_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
-        }
+    // Two launches when the chains overlap: the slices without Dirichlet
+    // columns on the main stream after the lateral gather, the slices with
+    // them on the second stream once the projection and the lateral gather
+    // (F^{n+1} and the deviations T^n - T_c) are done, the two side by side;
+    // the main solve waits for both.
+    if (overlap) {
+        SA_CUDA(c, cudaEventRecord(c->ev_lat, s));
+        SA_CUDA(c, cudaStreamWaitEvent(sb, c->ev_lat, 0));
+    }
+    for (int only = overlap ? 2 : 0; only >= (overlap ? 1 : 0); --only) {
         e = launch_theta_rhs(c->opt.precision, sell_view(c->r_s),
                              mixed ? (const void*)c->r_K32.p : (const void*)c->r_K.p,
                              mixed ? (const void*)c->r_M32.p : (const void*)c->r_M.p,
                              mixed ? (const void*)c->dev32.p : (const void*)c->dev64.p, c->That.p,
                              c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
-                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, s, only, dir_ready,
+                             c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, only == 2 ? sb : s, only, dir_ready,
                              rhs_pre ? fdm_view.S : nullptr, rhs_pre ? fdm_view.Z : nullptr,
                              rhs_pre ? c->npart.p : nullptr);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
+    }
+    if (overlap) {   // join
+        SA_CUDA(c, cudaEventRecord(c->ev_join, sb));
+        SA_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     }
     SA_MARK(SA_STAGE_PCG);
     const bool rec = c->rec_X != nullptr && c->rec_count < c->rec_cap;

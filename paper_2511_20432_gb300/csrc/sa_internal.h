@@ -449,6 +449,7 @@ struct sa_ctx {
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_hist = nullptr;   // the bottom history sums done (the lateral ones wait)
+    cudaEvent_t ev_lat = nullptr;    // the lateral gather done (the Dirichlet-column right-hand side waits)
     double stage_ms[SA_N_STAGES] = {};
     long long stage_steps = 0;
 };
