@@ -945,6 +945,35 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
             if (e == cudaSuccess) e = launch_to_f32(c->r_s.n_stored, c->r_K.p, c->r_K32.p, s);
         }
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "free-row SELL");
+        if (c->opt.precision == SA_MIXED) {
+            // the slices without Dirichlet columns stream 8 bytes a nonzero
+            // instead of 12: FP32 K, bf16 M, 16-bit column offsets
+            const std::vector<unsigned char> hi = sell_hi_flags(sr_h);
+            std::vector<short> lo(sr_h.col.size(), 0);
+            bool fits = sr_h.n > 0;
+            for (int sl = 0; sl < sr_h.n_slices && fits; ++sl) {
+                if (hi[sl]) continue;
+                const long long w = (sr_h.sptr[sl + 1] - sr_h.sptr[sl]) / 32;
+                for (int l = 0; l < 32 && fits; ++l) {
+                    const int r = std::min(sl * 32 + l, sr_h.n - 1);
+                    for (long long kk = 0; kk < w; ++kk) {
+                        const long long ee = sr_h.sptr[sl] + 32 * kk + l;
+                        const long long d = sl * 32 + l < sr_h.n ? (long long)sr_h.col[ee] - r : 0;
+                        if (d < -32768 || d > 32767) {
+                            fits = false;
+                            break;
+                        }
+                        lo[ee] = (short)d;
+                    }
+                }
+            }
+            if (fits) {
+                SA_UPLOAD(c, c->r_col16lo, lo);
+                SA_ALLOC(c, c->r_M16, sr_h.col.size());
+                e = launch_to_bf16(c->r_s.n_stored, c->r_M.p, c->r_M16.p, s);
+                if (e != cudaSuccess) return sa_cuda_fail(c, e, "free-row M (bf16)");
+            }
+        }
     }
 
     // ---- state and work vectors ---------------------------------------------------
@@ -1287,7 +1316,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                              c->gnew.p, c->F0.p, c->F1.p, c->rho * c->cp / dt, c->k, theta, c->Tc,
                              c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, only == 2 ? sb : s, only, dir_ready,
                              rhs_pre ? fdm_view.S : nullptr, rhs_pre ? fdm_view.Z : nullptr,
-                             rhs_pre ? c->npart.p : nullptr);
+                             rhs_pre ? c->npart.p : nullptr, mixed ? c->r_col16lo.p : nullptr,
+                             mixed ? c->r_M16.p : nullptr);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     }
     if (overlap) {   // join

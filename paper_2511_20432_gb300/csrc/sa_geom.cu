@@ -2,6 +2,8 @@
 // points with normals and weights, element matrices and their deterministic
 // gather into CSR (Section 2.3: the map Phi, grad_x N = J^{-T} grad_xi N,
 // dV = det J dxi, and the integrals M_ij, K_ij, F_i).
+#include <cuda_bf16.h>
+
 #include "sa_internal.h"
 
 namespace {
@@ -381,6 +383,12 @@ __global__ void k_sell_fill(long long n_stored, const int* src, const double* in
 __global__ void k_to_f32(long long n, const double* in, float* out) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
+}
+
+// bf16 bit patterns (round to nearest even) of FP64 values
+__global__ void k_to_bf16(long long n, const double* in, unsigned short* out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)in[i]));
 }
 
 __global__ void k_sell_dinv(int n, const int* diag, const double* val, double* dinv) {
@@ -1120,6 +1128,12 @@ cudaError_t launch_sell_fill(long long n_stored, const int* src, const double* i
     if (n_stored == 0) return cudaSuccess;
     k_sell_fill<<<(unsigned)((n_stored + 255) / 256), 256, 0, s>>>(n_stored, src, in1, s1, in2, s2,
                                                                   out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(long long n, const double* in, unsigned short* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out);
     return cudaGetLastError();
 }
 

@@ -375,6 +375,11 @@ struct sa_ctx {
     SellDev r_s;
     DBuf<double> r_M, r_K;
     DBuf<float> r_M32, r_K32;
+    // mixed path, slices without Dirichlet columns: 16-bit column offsets
+    // from the row, and M as bf16 (M enters only b, whose norm scales the
+    // stopping test); empty when an offset does not fit
+    DBuf<short> r_col16lo;
+    DBuf<unsigned short> r_M16;
 
     // ---- device: scan and history ------------------------------------------
     DBuf<double2> src_pos;    // relative (x - x_ref, y - y_ref)
@@ -585,8 +590,10 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only = 0,
                              bool dir_ready = false, const void* fdS = nullptr, void* fdZ = nullptr,
-                             float* npart = nullptr);
+                             float* npart = nullptr, const short* col16lo = nullptr,
+                             const unsigned short* M16 = nullptr);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
+cudaError_t launch_to_bf16(long long n, const double* in, unsigned short* out, cudaStream_t s);
 cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,
                           double* gprev, double* g0, cudaStream_t s);
 sa_status fd_setup(sa_ctx* c);

@@ -190,6 +190,10 @@ struct RhsArgs {
     const VT* fdS;
     VT* fdZ;
     float* npart;
+    // FP32 path, slices without Dirichlet columns (null: off): column
+    // offsets from the row and M as bf16 bit patterns
+    const short* col16lo;
+    const unsigned short* M16;
 };
 
 // g^{n+1} - g^n and g^{n+1} in the operator precision, so that the rows
@@ -211,6 +215,30 @@ __global__ void k_dir_prep(int n_dir, int n_free, const double* That, const doub
 template <bool DIR, typename VT>
 __device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, int k0, int k1,
                                           int lane, int ir, VT (&acc)[7]) {
+    if (!DIR && sizeof(VT) == 4 && a.col16lo != nullptr) {
+        // 8 bytes a nonzero: FP32 K, bf16 M (exact widening), 16-bit offsets
+        for (int k = k0; k < k1; k += 8) {
+            int jj[8];
+            VT kv[8], mv[8], dv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {     // independent loads first
+                const bool ok = k + u < k1;
+                const long long e = base + 32ll * (ok ? k + u : 0) + lane;
+                jj[u] = ok ? ir + (int)__ldg(a.col16lo + e) : ir;
+                kv[u] = ok ? __ldg(a.K.val + e) : (VT)0;
+                mv[u] = ok ? (VT)__uint_as_float((unsigned)__ldg(a.M16 + e) << 16) : (VT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) dv[u] = a.dev[jj[u]];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                acc[0] = fma(kv[u], dv[u], acc[0]);
+                acc[1] = fma(mv[u], dv[u], acc[1]);
+                acc[2] += mv[u];
+            }
+        }
+        return;
+    }
     for (int k = k0; k < k1; k += 8) {
         int jj[8];
         VT kv[8], mv[8], dv[8];
@@ -1820,7 +1848,8 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              const double* gnew, const double* F0, const double* F1,
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only,
-                             bool dir_ready, const void* fdS, void* fdZ, float* npart) {
+                             bool dir_ready, const void* fdS, void* fdZ, float* npart,
+                             const short* col16lo, const unsigned short* M16) {
     if (op.n == 0) return cudaSuccess;
     // Dirichlet increments for the flagged slices (unless the projection wrote them)
     const bool prep = only != 1 && n_dir > 0 && !dir_ready;
@@ -1834,7 +1863,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         if (prep) k_dir_prep<float><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, dg, g1,
                          F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
-                         (const float*)fdS, (float*)fdZ, npart};
+                         (const float*)fdS, (float*)fdZ, npart, col16lo, M16};
         if (split == 8)
             k_theta_rhs<8, float><<<blocks, 256, 0, s>>>(a);
         else
@@ -1845,7 +1874,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         if (prep) k_dir_prep<double><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev, dg,
                           g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
-                          (const double*)fdS, (double*)fdZ, npart};
+                          (const double*)fdS, (double*)fdZ, npart, nullptr, nullptr};
         if (split == 8)
             k_theta_rhs<8, double><<<blocks, 256, 0, s>>>(a);
         else
