@@ -20,7 +20,7 @@
 //
 // Work layout: CTA (tile, unit) multiplies the 64 x TJ output tile over one
 // unit of consecutive sources: the active sources split evenly over a fixed
-// number of units (about four CTAs per multiprocessor), so the grid is static
+// number of units (about six CTAs per multiprocessor), so the grid is static
 // while the active count grows and every CTA has work; a unit is staged in
 // rounds of at most 512 sources (256 in FP64).  Per chunk of 32 sources the
 // CTA writes FA and FB into shared memory (double-buffered), then each thread
@@ -601,14 +601,16 @@ sa_status sep_setup(sa_ctx* c) {
 sa_status sep_alloc(sa_ctx* c) {
     SepPlan& P = c->sep;
     if (!P.ok) return SA_OK;
-    // about four CTAs a multiprocessor over both launches, and no unit
-    // longer than the shared-memory staging holds at the full scan
+    // about six CTAs a multiprocessor over the two launches (they run one
+    // after the other: ~2.6 and ~3.5 a multiprocessor each; measured against
+    // four, eight and twelve), and no unit longer than the shared-memory
+    // staging holds at the full scan
     const int n = std::max(c->n_src, 1);
     const bool f32 = c->opt.precision == SA_MIXED;
     const int kc = f32 ? chunk_of<float>() : chunk_of<double>();
     const int umax = f32 ? max_unit_of<float>() : max_unit_of<double>();
     const int tiles = std::max(1, P.n_tiles[0] + P.n_tiles[1]);
-    int s_max = std::max(1, (4 * c->num_sms + tiles - 1) / tiles);
+    int s_max = std::max(1, (6 * c->num_sms + tiles - 1) / tiles);
     s_max = std::max(s_max, (n + umax - 1) / umax);
     // with K = n: unit_len <= umax (a whole number of chunks)
     while (unit_len(n, s_max, kc) > umax) ++s_max;
