@@ -1458,12 +1458,16 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(SmemArgs<VT> a) {
             shortcut = 0;
             if (first && state == 0) {
                 // |(sigma r1, sigma r1) - est| <= bound: sums of one rounding
-                // per product over a tree of depth ~24, with margin
+                // per product over a tree of depth ~24, with margin (the
+                // Cauchy-Schwarz factor sqrt(ee) sqrt(ww) in FP32: each root
+                // stays normal down to 1e-38, far below any stopping level;
+                // FP64 square roots are slow on this part)
                 const double om = 1.0 - (double)al;
                 const double ee = res[2], ew = res[3], ww = res[4];
                 const double est = ee + 2.0 * om * ew + om * om * ww;
                 const double bound = 64.0 * (sizeof(AT) == 4 ? 5.9604644775390625e-8 : 1.1102230246251565e-16) *
-                                     (ee + 2.0 * fabs(om) * sqrt(ee * ww) + om * om * ww);
+                                     (ee + 2.0 * fabs(om) * (double)sqrtf((float)ee) *
+                                               (double)sqrtf((float)ww) + om * om * ww);
                 if (est + bound <= stop2) {
                     shortcut = 1;
                     sc[3] = est > 0.0 ? est : 0.0;
