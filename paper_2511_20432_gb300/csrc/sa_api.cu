@@ -931,6 +931,17 @@ sa_status sa_create_patch(sa_ctx* c, const int degree[3], const int n_ctrl[3],
         SA_UPLOAD_SELL(c, c->r_s, sr_h);
         c->a_h = sa_h;
         c->r_h = sr_h;
+        {
+            const std::vector<unsigned char> hi = sell_hi_flags(sr_h);
+            int lo = sr_h.n_slices, up = 0;
+            for (int sl = 0; sl < sr_h.n_slices; ++sl)
+                if (hi[sl]) {
+                    lo = std::min(lo, sl);
+                    up = sl + 1;
+                }
+            c->r_dir_sl0 = up > lo ? lo : 0;
+            c->r_dir_sl1 = up > lo ? up : 0;
+        }
         SA_ALLOC(c, c->r_M, sr_h.col.size());
         SA_ALLOC(c, c->r_K, sr_h.col.size());
         cudaError_t e = launch_sell_fill(c->r_s.n_stored, c->r_s.src.p, c->M.p, 1.0, nullptr, 0.0,
@@ -1317,7 +1328,8 @@ sa_status enqueue_step(sa_ctx* c, double theta, double dt) {
                              c->r0.p, c->bsq.p, c->n_dir, c->dirv.p, only == 2 ? sb : s, only, dir_ready,
                              rhs_pre ? fdm_view.S : nullptr, rhs_pre ? fdm_view.Z : nullptr,
                              rhs_pre ? c->npart.p : nullptr, mixed ? c->r_col16lo.p : nullptr,
-                             mixed ? c->r_M16.p : nullptr);
+                             mixed ? c->r_M16.p : nullptr, only == 2 ? c->r_dir_sl0 : 0,
+                             only == 2 ? c->r_dir_sl1 : -1);
         if (e != cudaSuccess) return sa_cuda_fail(c, e, "theta rhs");
     }
     if (overlap) {   // join

@@ -380,6 +380,7 @@ struct sa_ctx {
     // stopping test); empty when an offset does not fit
     DBuf<short> r_col16lo;
     DBuf<unsigned short> r_M16;
+    int r_dir_sl0 = 0, r_dir_sl1 = -1;   // slices with Dirichlet columns lie in [sl0, sl1)
 
     // ---- device: scan and history ------------------------------------------
     DBuf<double2> src_pos;    // relative (x - x_ref, y - y_ref)
@@ -591,7 +592,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only = 0,
                              bool dir_ready = false, const void* fdS = nullptr, void* fdZ = nullptr,
                              float* npart = nullptr, const short* col16lo = nullptr,
-                             const unsigned short* M16 = nullptr);
+                             const unsigned short* M16 = nullptr, int sl0 = 0, int sl1 = -1);
 cudaError_t launch_pcg(int precision, const PcgLaunch& L, cudaStream_t s);
 cudaError_t launch_to_bf16(long long n, const double* in, unsigned short* out, cudaStream_t s);
 cudaError_t launch_extrap(int n_free, int n_dir, const double* That, double* Tprev, float* dx0,

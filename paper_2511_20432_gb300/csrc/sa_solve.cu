@@ -194,6 +194,7 @@ struct RhsArgs {
     // offsets from the row and M as bf16 bit patterns
     const short* col16lo;
     const unsigned short* M16;
+    int sl0, sl1;          // the launch covers slices [sl0, sl1)
 };
 
 // g^{n+1} - g^n and g^{n+1} in the operator precision, so that the rows
@@ -291,10 +292,10 @@ __global__ void __launch_bounds__(256) k_theta_rhs(RhsArgs<VT> a) {
     // sums combined in fixed order
     __shared__ VT part[8][7][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sl = blockIdx.x * (8 / kRhsSplit) + wib / kRhsSplit;
+    const int sl = a.sl0 + blockIdx.x * (8 / kRhsSplit) + wib / kRhsSplit;
     const int h = wib % kRhsSplit;
     VT acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    bool live = sl < a.K.n_slices;
+    bool live = sl < a.sl1;
     if (live && a.only != 0) {
         const bool dir = a.K.hi == nullptr || a.K.hi[sl];
         live = (a.only == 2) == dir;
@@ -1853,13 +1854,16 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
                              double inv_dt_rhocp, double k, double theta, double Tc, double* r0,
                              double* bsq, int n_dir, void* dir_scratch, cudaStream_t s, int only,
                              bool dir_ready, const void* fdS, void* fdZ, float* npart,
-                             const short* col16lo, const unsigned short* M16) {
+                             const short* col16lo, const unsigned short* M16, int sl0, int sl1) {
     if (op.n == 0) return cudaSuccess;
     // Dirichlet increments for the flagged slices (unless the projection wrote them)
     const bool prep = only != 1 && n_dir > 0 && !dir_ready;
     // the Dirichlet-column slices alone: one slice a block, eight warps on it
     const int split = only == 2 ? 8 : 4;
-    const unsigned blocks = (unsigned)((op.n_slices + (8 / split) - 1) / (8 / split));
+    sl0 = std::max(0, sl0);
+    sl1 = sl1 < 0 ? op.n_slices : std::min(sl1, op.n_slices);
+    if (sl1 <= sl0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((sl1 - sl0 + (8 / split) - 1) / (8 / split));
     const unsigned pblocks = (unsigned)((n_dir + 255) / 256);
     if (precision == SA_MIXED) {
         float* dg = (float*)dir_scratch;
@@ -1867,7 +1871,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         if (prep) k_dir_prep<float><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<float> a{make_op<float>(op, Kval), (const float*)Mval, (const float*)dev, dg, g1,
                          F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
-                         (const float*)fdS, (float*)fdZ, npart, col16lo, M16};
+                         (const float*)fdS, (float*)fdZ, npart, col16lo, M16, sl0, sl1};
         if (split == 8)
             k_theta_rhs<8, float><<<blocks, 256, 0, s>>>(a);
         else
@@ -1878,7 +1882,7 @@ cudaError_t launch_theta_rhs(int precision, const SellView& op, const void* Kval
         if (prep) k_dir_prep<double><<<pblocks, 256, 0, s>>>(n_dir, op.n, That, gnew, dg, g1);
         RhsArgs<double> a{make_op<double>(op, Kval), (const double*)Mval, (const double*)dev, dg,
                           g1, F0, F1, op.n, inv_dt_rhocp, k, theta, Tc, r0, bsq, only,
-                          (const double*)fdS, (double*)fdZ, npart, nullptr, nullptr};
+                          (const double*)fdS, (double*)fdZ, npart, nullptr, nullptr, sl0, sl1};
         if (split == 8)
             k_theta_rhs<8, double><<<blocks, 256, 0, s>>>(a);
         else
