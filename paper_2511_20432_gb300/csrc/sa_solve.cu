@@ -217,25 +217,46 @@ template <bool DIR, typename VT>
 __device__ __forceinline__ void rhs_slice(const RhsArgs<VT>& a, long long base, int k0, int k1,
                                           int lane, int ir, VT (&acc)[7]) {
     if (!DIR && sizeof(VT) == 4 && a.col16lo != nullptr) {
-        // 8 bytes a nonzero: FP32 K, bf16 M (exact widening), 16-bit offsets
-        for (int k = k0; k < k1; k += 8) {
-            int jj[8];
-            VT kv[8], mv[8], dv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {     // independent loads first
-                const bool ok = k + u < k1;
-                const long long e = base + 32ll * (ok ? k + u : 0) + lane;
-                jj[u] = ok ? ir + (int)__ldg(a.col16lo + e) : ir;
-                kv[u] = ok ? __ldg(a.K.val + e) : (VT)0;
-                mv[u] = ok ? (VT)__uint_as_float((unsigned)__ldg(a.M16 + e) << 16) : (VT)0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) dv[u] = a.dev[jj[u]];
+        // 8 bytes a nonzero: FP32 K, bf16 M (exact widening), 16-bit offsets.
+        // Software-pipelined in batches of 8: the next batch's offsets and
+        // values are in flight while this batch's gathers of T^n - T_c wait
+        // (two dependent loads a batch otherwise leave HBM half idle).
+        short cj[8];
+        VT kv[8];
+        unsigned short mb[8];
+        auto load = [&](int k, short (&c)[8], VT (&kk)[8], unsigned short (&m)[8]) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
+                const bool ok = k + u < k1;
+                const long long e = base + 32ll * (ok ? k + u : 0) + lane;
+                c[u] = ok ? __ldg(a.col16lo + e) : (short)0;
+                kk[u] = ok ? __ldg(a.K.val + e) : (VT)0;
+                m[u] = ok ? __ldg(a.M16 + e) : (unsigned short)0;
+            }
+        };
+        if (k0 < k1) load(k0, cj, kv, mb);
+        for (int k = k0; k < k1; k += 8) {
+            VT dv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) dv[u] = a.dev[ir + (int)cj[u]];
+            short cn[8];
+            VT kn[8];
+            unsigned short mn[8];
+            if (k + 8 < k1) load(k + 8, cn, kn, mn);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const VT mv = (VT)__uint_as_float((unsigned)mb[u] << 16);
                 acc[0] = fma(kv[u], dv[u], acc[0]);
-                acc[1] = fma(mv[u], dv[u], acc[1]);
-                acc[2] += mv[u];
+                acc[1] = fma(mv, dv[u], acc[1]);
+                acc[2] += mv;
+            }
+            if (k + 8 < k1) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    cj[u] = cn[u];
+                    kv[u] = kn[u];
+                    mb[u] = mn[u];
+                }
             }
         }
         return;
