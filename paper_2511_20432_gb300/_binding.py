@@ -219,7 +219,12 @@ class Context:
             _check(self.ptr, lib.sa_eval_T(self.ptr, _ptr(pts), int(n), _ptr(out), 1))
             return out
         p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
-        o = np.empty(p.shape[0])
+        if out is not None:   # a caller's host buffer (e.g. pinned), n contiguous FP64
+            if out.dtype != np.float64 or out.size != p.shape[0] or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out: a contiguous float64 array of one value per point")
+            o = out
+        else:
+            o = np.empty(p.shape[0])
         _check(self.ptr, lib.sa_eval_T(self.ptr, _ptr(p), int(p.shape[0]), _ptr(o), 0))
         return o
 
