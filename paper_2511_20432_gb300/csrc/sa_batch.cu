@@ -213,6 +213,7 @@ struct BPcgArgs {
     const int* fd_loff;       // 3 x (n_inst + 1)
     const VT* fdS;            // scaling per row
     VT* fdZ;                  // work vector
+    int fd_mmax;              // largest line length (the staged matrices' size)
 };
 
 template <typename VT>
@@ -223,94 +224,124 @@ __device__ __forceinline__ int bcol(const BPcgArgs<VT>& a, long long e, int row)
 // Batched fast-diagonalization preconditioner z = S A_box^{-1} S r over
 // every instance (independent grids): on entry fdZ = S r on all rows (grid
 // barrier passed); 2 nd - 1 passes (3-D: U_0^T, U_1^T, U_2 D U_2^T, U_1, U_0;
-// 2-D: U_0^T, U_1 D U_1^T, U_0) over the lines of all instances (a line ->
-// its instance by the per-direction line offsets), one warp per line, the
-// line's matrix read through L1; the last pass writes z (FP64) and its
-// operator-precision copy.  Lines have at most 128 entries.
+// 2-D: U_0^T, U_1 D U_1^T, U_0) over the lines of all instances, one warp
+// per line; the last pass writes z (FP64) and its operator-precision copy.
+// Lines have at most 128 entries.  A block takes a contiguous range of each
+// pass's lines (instance-major), so it meets one or a few instances; for
+// each it stages the instance's line matrix (and the middle pass's second
+// one) in shared memory (Wsm: 2 m^2 entries), instead of reading it per
+// line through L1, where a pass over hundreds of instances' matrices misses
+// to L2 on every line.
 template <typename VT>
-__device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, double* z, VT* zl, unsigned* bc,
+__device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, VT* Wsm, double* z, VT* zl, unsigned* bc,
                           unsigned& bg, int* err) {
     const int lane = threadIdx.x & 31;
-    const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     const int NI = a.n_inst;
     VT* Z = a.fdZ;
     const int nd = a.fd_nd, npass = 2 * nd - 1;
     for (int pass = 0; pass < npass; ++pass) {
         const int d = pass < nd ? pass : npass - 1 - pass;
+        const bool mid = pass == nd - 1;
         const int* loff = a.fd_loff + d * (NI + 1);
         const int nlines = loff[NI];
-        for (int Lg = gw; Lg < nlines; Lg += nw) {
-            int lo = 0, hi = NI;          // loff[lo] <= Lg < loff[hi]
+        const int chunk = (nlines + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int l0 = min(nlines, (int)blockIdx.x * chunk), l1 = min(nlines, l0 + chunk);
+        int inst = 0;                  // the instance of line l0: loff[inst] <= l0 < loff[inst + 1]
+        {
+            int lo = 0, hi = NI;
             while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (loff[mid] <= Lg) lo = mid;
-                else hi = mid;
+                const int md = (lo + hi) >> 1;
+                if (loff[md] <= l0) lo = md;
+                else hi = md;
             }
-            const BFd& f = a.fd[lo];
-            const int L = Lg - loff[lo];
+            inst = lo;
+        }
+        for (int s0 = l0; s0 < l1;) {
+            while (inst + 1 < NI && loff[inst + 1] <= s0) ++inst;
+            const int s1 = min(l1, loff[inst + 1]);
+            const BFd& f = a.fd[inst];
             const int m0 = f.m[0], m1 = f.m[1];
             const int m = f.m[d];
             const int stride = d == 0 ? 1 : (d == 1 ? m0 : m0 * m1);
-            const long long base = f.row0 + (d == 0 ? (long long)L * m0
-                                            : (d == 1 ? (long long)(L / m0) * (m0 * m1) + (L % m0) : L));
-            for (int q = lane; q < m; q += 32) xs[q] = __ldcg(Z + base + (long long)q * stride);
-            __syncwarp();
-            const VT* W = (const VT*)(pass < nd ? f.U[d] : f.Ut[d]);
-            VT y[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
-#pragma unroll 4
-            for (int q = 0; q < m; ++q) {
-                const VT xq = xs[q];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int o = lane + 32 * t;
-                    if (o < m) y[t] = fma(__ldg(W + q * m + o), xq, y[t]);
-                }
+            // this instance's matrices into shared memory (all copies of a
+            // thread in flight at once); the previous segment is done with them
+            __syncthreads();
+            const VT* Wg = (const VT*)(pass < nd ? f.U[d] : f.Ut[d]);
+            const VT* W2g = (const VT*)f.Ut[nd - 1];
+            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                sa_dev::cp_async_ca<sizeof(VT)>(Wsm + t, Wg + t);
+                if (mid) sa_dev::cp_async_ca<sizeof(VT)>(Wsm + m * m + t, W2g + t);
             }
-            if (pass == nd - 1) {
-                const VT li = (VT)f.cM + ((const VT*)f.lamc[0])[L % m0] +
-                              (nd == 3 ? ((const VT*)f.lamc[1])[L / m0] : (VT)0);
-                const VT* l2 = (const VT*)f.lamc[nd - 1];
+            sa_dev::cp_async_wait_all();
+            __syncthreads();
+            const VT* W = Wsm;
+            const VT* W2 = Wsm + m * m;
+            for (int Lg = s0 + wib; Lg < s1; Lg += nwb) {
+                const int L = Lg - loff[inst];
+                const long long base = f.row0 + (d == 0 ? (long long)L * m0
+                                                : (d == 1 ? (long long)(L / m0) * (m0 * m1) + (L % m0) : L));
+                for (int q = lane; q < m; q += 32) xs[q] = __ldcg(Z + base + (long long)q * stride);
                 __syncwarp();
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int o = lane + 32 * t;
-                    if (o < m) xs[o] = y[t] / (li + l2[o]);
-                    y[t] = (VT)0;
-                }
-                __syncwarp();
-                const VT* W2 = (const VT*)f.Ut[nd - 1];
+                VT y[4] = {(VT)0, (VT)0, (VT)0, (VT)0};
 #pragma unroll 4
                 for (int q = 0; q < m; ++q) {
                     const VT xq = xs[q];
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int o = lane + 32 * t;
-                        if (o < m) y[t] = fma(__ldg(W2 + q * m + o), xq, y[t]);
+                        if (o < m) y[t] = fma(W[q * m + o], xq, y[t]);
                     }
                 }
-            }
-            __syncwarp();
+                if (mid) {
+                    const VT li = (VT)f.cM + ((const VT*)f.lamc[0])[L % m0] +
+                                  (nd == 3 ? ((const VT*)f.lamc[1])[L / m0] : (VT)0);
+                    const VT* l2 = (const VT*)f.lamc[nd - 1];
+                    __syncwarp();
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int o = lane + 32 * t;
-                if (o < m) {
-                    const long long idx = base + (long long)o * stride;
-                    if (pass == npass - 1) {
-                        const VT u = a.fdS[idx] * y[t];
-                        z[idx] = (double)u;
-                        zl[idx] = u;
-                    } else {
-                        Z[idx] = y[t];
+                    for (int t = 0; t < 4; ++t) {
+                        const int o = lane + 32 * t;
+                        if (o < m) xs[o] = y[t] / (li + l2[o]);
+                        y[t] = (VT)0;
+                    }
+                    __syncwarp();
+#pragma unroll 4
+                    for (int q = 0; q < m; ++q) {
+                        const VT xq = xs[q];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int o = lane + 32 * t;
+                            if (o < m) y[t] = fma(W2[q * m + o], xq, y[t]);
+                        }
                     }
                 }
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int o = lane + 32 * t;
+                    if (o < m) {
+                        const long long idx = base + (long long)o * stride;
+                        if (pass == npass - 1) {
+                            const VT u = a.fdS[idx] * y[t];
+                            z[idx] = (double)u;
+                            zl[idx] = u;
+                        } else {
+                            Z[idx] = y[t];
+                        }
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
+            s0 = s1;
         }
         if (!bgrid_barrier(bc, bg, err)) return false;
     }
     return true;
 }
+
+// dynamic shared memory of k_pcg_batch: two staged line matrices
+template <typename VT>
+size_t batch_pcg_smem(int mmax) { return (size_t)2 * mmax * mmax * sizeof(VT); }
 
 template <typename VT>
 __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
@@ -326,6 +357,8 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
     volatile double* is = a.is;
     __shared__ VT xsb[32][128];            // per-warp line scratch (fast diagonalization)
     VT* xs = xsb[threadIdx.x >> 5];
+    extern __shared__ __align__(16) unsigned char bsm[];   // the staged line matrices
+    VT* Wsm = (VT*)bsm;
     const bool fd = a.fd != nullptr;
     VT* const zlw = LO ? a.zl : (VT*)a.z;
     // ---- phase A: r = b - A x (FP64 values) or r = r0 (b = r0 + A x)
@@ -377,7 +410,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
     if (!bgrid_barrier(bc, bg, err)) return;
     if (fd) {
         // z = P^{-1} r, then (r, z) per slice
-        if (!bfd_apply(a, xs, a.z, zlw, bc, bg, err)) return;
+        if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err)) return;
         for (int sl = gw; sl < S; sl += nw) {
             const int i = sl * 32 + lane;
             const double t0 = warp_sum(i < a.n ? a.r[i] * a.z[i] : 0.0);
@@ -506,7 +539,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
         if (!bgrid_barrier(bc, bg, err)) return;
         if (fd) {
             // z = P^{-1} r (every row; converged instances ignore theirs), then (r, z)
-            if (!bfd_apply(a, xs, a.z, zlw, bc, bg, err)) return;
+            if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err)) return;
             for (int sl = gw; sl < S; sl += nw) {
                 const int inst = a.slice_inst[sl];
                 const int i = sl * 32 + lane;
@@ -606,6 +639,7 @@ cudaError_t launch_pcg_batch(sa_batch* b, int which, const SellDev& s, const voi
     a.fd_loff = fd ? (which == 0 ? b->fd_loff.p : b->fdb_loff.p) : nullptr;
     a.fdS = fd ? (const VT*)(which == 0 ? b->fdS.p : b->fdbS.p) : nullptr;
     a.fdZ = fd ? (VT*)(which == 0 ? b->fdZ.p : b->fdbZ.p) : nullptr;
+    a.fd_mmax = fd ? b->fd_mmax : 0;
     cudaError_t e = cudaMemsetAsync(&b->st.p->bar_count[2 + which], 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->counters.p, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -613,6 +647,10 @@ cudaError_t launch_pcg_batch(sa_batch* b, int which, const SellDev& s, const voi
     cfg.gridDim = dim3(b->pcg_grid);
     cfg.blockDim = dim3(1024);
     cfg.stream = st;
+    cfg.dynamicSmemBytes = batch_pcg_smem<VT>(a.fd_mmax);
+    e = cudaFuncSetAttribute(k_pcg_batch<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cfg.dynamicSmemBytes);
+    if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -907,6 +945,7 @@ sa_status build(sa_batch* b, double theta, double dt) {
             for (int i = 0; i < NI; ++i) {
                 const FdData& f = b->inst[i]->fdm;
                 for (int d = 0; d < 3; ++d) {
+                    b->fd_mmax = std::max(b->fd_mmax, f.m[d]);
                     desc[i].m[d] = f.m[d];
                     desc[i].U[d] = f.dU[d].p;
                     desc[i].Ut[d] = f.dUt[d].p;
@@ -943,6 +982,7 @@ sa_status build(sa_batch* b, double theta, double dt) {
                 std::memset(&desc[i], 0, sizeof(BFd));
                 for (int d = 0; d < 3; ++d) desc[i].m[d] = f.m[d];
                 for (int d = 0; d < 2; ++d) {
+                    b->fd_mmax = std::max(b->fd_mmax, f.m[d]);
                     desc[i].U[d] = f.dU[d].p;
                     desc[i].Ut[d] = f.dUt[d].p;
                     desc[i].lamc[d] = f.dlamc[d].p;
@@ -990,8 +1030,12 @@ sa_status build(sa_batch* b, double theta, double dt) {
         B_CUDA(b, cudaMemcpyAsync(&b->st.p->n, &n0, sizeof(long long), cudaMemcpyHostToDevice, s));
         b->n_step = n0;
         int occ = 0;
-        B_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                      &occ, mixed ? (const void*)k_pcg_batch<float> : (const void*)k_pcg_batch<double>, 1024, 0));
+        const size_t pcg_smem = (b->fd_on || b->fdb_on)
+                                    ? (mixed ? batch_pcg_smem<float>(b->fd_mmax) : batch_pcg_smem<double>(b->fd_mmax))
+                                    : 0;
+        const void* pcg_fn = mixed ? (const void*)k_pcg_batch<float> : (const void*)k_pcg_batch<double>;
+        B_CUDA(b, cudaFuncSetAttribute(pcg_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg_smem));
+        B_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_fn, 1024, pcg_smem));
         if (occ < 1) return bfail(b, SA_ERR_CUDA, "batched PCG kernel cannot be resident");
         b->pcg_grid = b->num_sms;
     }
