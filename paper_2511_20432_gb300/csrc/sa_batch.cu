@@ -538,41 +538,77 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
         }
         if (!bgrid_barrier(bc, bg, err)) return;
         if (fd) {
-            // z = P^{-1} r (every row; converged instances ignore theirs), then (r, z)
-            if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err)) return;
-            for (int sl = gw; sl < S; sl += nw) {
-                const int inst = a.slice_inst[sl];
-                const int i = sl * 32 + lane;
-                double rz = 0.0;
-                if (is[IS_CONV * NI + inst] == 0.0 && i < a.n) rz = a.r[i] * a.z[i];
-                rz = warp_sum(rz);
-                if (lane == 0) a.part[2 * S + sl] = rz;
+            // R2a: convergence from (r, r) before the preconditioner: an
+            // instance that has converged needs no z, and when every one has
+            // (the box preconditioner is the inverse: usually after the first
+            // update) the application and its barriers are skipped
+            for (int i = gw; i < NI; i += nw) {
+                const int s0 = a.slice_off[i], s1 = a.slice_off[i + 1];
+                const volatile double* pf = a.part + S;
+                double v = 0.0;
+                for (int s = s0 + lane; s < s1; s += 32) v += pf[s];
+                const double rr = warp_sum(v);
+                if (lane == 0 && is[IS_CONV * NI + i] == 0.0) {
+                    is[IS_RR * NI + i] = rr;
+                    a.iters[i] = it + 1;
+                    const bool conv = rr <= a.tol * a.tol * is[IS_BB * NI + i];
+                    if (!(rr == rr)) atomicOr(err, SA_DEV_NAN);
+                    if (conv) is[IS_CONV * NI + i] = 1.0;
+                    else atomicAdd(&a.active[(it + 1) & 1], 1u);
+                }
+            }
+            if (!bgrid_barrier(bc, bg, err)) return;
+            if (*((volatile unsigned*)&a.active[(it + 1) & 1]) > 0u) {
+                // z = P^{-1} r (every row; converged instances ignore theirs), then (r, z)
+                if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err)) return;
+                for (int sl = gw; sl < S; sl += nw) {
+                    const int inst = a.slice_inst[sl];
+                    const int i = sl * 32 + lane;
+                    double rz = 0.0;
+                    if (is[IS_CONV * NI + inst] == 0.0 && i < a.n) rz = a.r[i] * a.z[i];
+                    rz = warp_sum(rz);
+                    if (lane == 0) a.part[2 * S + sl] = rz;
+                }
+                if (!bgrid_barrier(bc, bg, err)) return;
+                // R2b: beta of the instances still running
+                for (int i = gw; i < NI; i += nw) {
+                    const int s0 = a.slice_off[i], s1 = a.slice_off[i + 1];
+                    const volatile double* pf = a.part + 2 * S;
+                    double v = 0.0;
+                    for (int s = s0 + lane; s < s1; s += 32) v += pf[s];
+                    const double rzn = warp_sum(v);
+                    if (lane == 0 && is[IS_CONV * NI + i] == 0.0) {
+                        is[IS_BETA * NI + i] = rzn / is[IS_RZ * NI + i];
+                        is[IS_RZ * NI + i] = rzn;
+                    }
+                }
+                if (!bgrid_barrier(bc, bg, err)) return;
+            }
+        } else {
+            // R2: convergence, beta, active count
+            for (int i = gw; i < NI; i += nw) {
+                const int s0 = a.slice_off[i], s1 = a.slice_off[i + 1];
+                double t[2];
+                for (int f = 0; f < 2; ++f) {
+                    const volatile double* pf = a.part + (long long)(1 + f) * S;
+                    double v = 0.0;
+                    for (int s = s0 + lane; s < s1; s += 32) v += pf[s];
+                    t[f] = warp_sum(v);
+                }
+                if (lane == 0 && is[IS_CONV * NI + i] == 0.0) {
+                    const double rr = t[0], rzn = t[1];
+                    is[IS_RR * NI + i] = rr;
+                    is[IS_BETA * NI + i] = rzn / is[IS_RZ * NI + i];
+                    is[IS_RZ * NI + i] = rzn;
+                    a.iters[i] = it + 1;
+                    const bool conv = rr <= a.tol * a.tol * is[IS_BB * NI + i];
+                    if (!(rr == rr)) atomicOr(err, SA_DEV_NAN);
+                    if (conv) is[IS_CONV * NI + i] = 1.0;
+                    else atomicAdd(&a.active[(it + 1) & 1], 1u);
+                }
             }
             if (!bgrid_barrier(bc, bg, err)) return;
         }
-        // R2: convergence, beta, active count
-        for (int i = gw; i < NI; i += nw) {
-            const int s0 = a.slice_off[i], s1 = a.slice_off[i + 1];
-            double t[2];
-            for (int f = 0; f < 2; ++f) {
-                const volatile double* pf = a.part + (long long)(1 + f) * S;
-                double v = 0.0;
-                for (int s = s0 + lane; s < s1; s += 32) v += pf[s];
-                t[f] = warp_sum(v);
-            }
-            if (lane == 0 && is[IS_CONV * NI + i] == 0.0) {
-                const double rr = t[0], rzn = t[1];
-                is[IS_RR * NI + i] = rr;
-                is[IS_BETA * NI + i] = rzn / is[IS_RZ * NI + i];
-                is[IS_RZ * NI + i] = rzn;
-                a.iters[i] = it + 1;
-                const bool conv = rr <= a.tol * a.tol * is[IS_BB * NI + i];
-                if (!(rr == rr)) atomicOr(err, SA_DEV_NAN);
-                if (conv) is[IS_CONV * NI + i] = 1.0;
-                else atomicAdd(&a.active[(it + 1) & 1], 1u);
-            }
-        }
-        if (!bgrid_barrier(bc, bg, err)) return;
         n_active = *((volatile unsigned*)&a.active[(it + 1) & 1]);
         ++it;
         double* t = pc;
