@@ -65,6 +65,11 @@ struct sa_batch {
     SellDev a_s, r_s, mbot_s;
     DBuf<double> a_val, r_K, r_M, mbot_val, a_dinv, mbot_dinv;
     DBuf<float> a_val32, r_K32, r_M32, mbot_val32;
+    // mixed path, slices without Dirichlet columns: 16-bit column offsets and
+    // M as bf16 (8 bytes a nonzero in the right-hand side; empty when an
+    // offset does not fit)
+    DBuf<short> r_col16lo;
+    DBuf<unsigned short> r_M16;
     DBuf<int> slice_inst_a, slice_inst_b, d_slice_off_a, d_slice_off_b;
     // state and work
     DBuf<double> That, F0, F1, gnew, bbot, r0, bsq, dirv, wr, wz, wp0, wp1, wq, dev64, partials, inst_state;
@@ -388,8 +393,9 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
                 ri = bi - acc;
             } else {
                 ri = a.r0[i];
-                // |b_i| from the right-hand-side kernel when given (no SpMV)
-                bi = a.bsq ? sqrt(a.bsq[i]) : ri + acc;
+                // b_i^2 from the right-hand-side kernel when given (no SpMV;
+                // only the square is used)
+                bi = a.bsq ? 0.0 : ri + acc;
             }
             a.r[i] = ri;
             if (fd) {
@@ -400,7 +406,8 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
                 if (LO) a.zl[i] = (VT)zi;
             }
         }
-        const double t0 = warp_sum(ri * zi), t1 = warp_sum(ri * ri), t2 = warp_sum(bi * bi);
+        const double b2 = a.bsq ? (i < a.n ? a.bsq[i] : 0.0) : bi * bi;
+        const double t0 = warp_sum(ri * zi), t1 = warp_sum(ri * ri), t2 = warp_sum(b2);
         if (lane == 0) {
             a.part[sl] = t0;
             a.part[S + sl] = t1;
@@ -938,6 +945,32 @@ sa_status build(sa_batch* b, double theta, double dt) {
             if (e == cudaSuccess) e = launch_to_f32(b->r_s.n_stored, b->r_M.p, b->r_M32.p, s);
             if (e == cudaSuccess) e = launch_to_f32(b->mbot_s.n_stored, b->mbot_val.p, b->mbot_val32.p, s);
             if (e != cudaSuccess) return bcuda(b, e, "FP32 operators");
+            const std::vector<unsigned char> hi = sell_hi_flags(R);
+            std::vector<short> lo(R.col.size(), 0);
+            bool fits = R.n > 0;
+            for (int sl = 0; sl < R.n_slices && fits; ++sl) {
+                if (hi[sl]) continue;
+                const long long w = (R.sptr[sl + 1] - R.sptr[sl]) / 32;
+                for (int l = 0; l < 32 && fits; ++l) {
+                    const int r = std::min(sl * 32 + l, R.n - 1);
+                    for (long long kk = 0; kk < w; ++kk) {
+                        const long long ee = R.sptr[sl] + 32 * kk + l;
+                        const long long d = sl * 32 + l < R.n ? (long long)R.col[ee] - r : 0;
+                        if (d < -32768 || d > 32767) {
+                            fits = false;
+                            break;
+                        }
+                        lo[ee] = (short)d;
+                    }
+                }
+            }
+            if (fits) {
+                sa_status st3;
+                if ((st3 = bupload(b, b->r_col16lo, lo, "r_col16lo"))) return st3;
+                B_ALLOC(b, b->r_M16, R.col.size());
+                e = launch_to_bf16(b->r_s.n_stored, b->r_M.p, b->r_M16.p, s);
+                if (e != cudaSuccess) return bcuda(b, e, "free-row M (bf16)");
+            }
         }
     }
 
@@ -1126,7 +1159,8 @@ sa_status enqueue_batch_step(sa_batch* b) {
                          mixed ? (const void*)b->r_M32.p : (const void*)b->r_M.p,
                          mixed ? (const void*)b->dev32.p : (const void*)b->dev64.p, b->That.p,
                          b->gnew.p, b->F0.p, b->F1.p, b->rho * b->cp / b->dt, b->k, b->theta,
-                         b->Tc, b->r0.p, b->bsq.p, b->n_dir, b->dirv.p, s);
+                         b->Tc, b->r0.p, b->bsq.p, b->n_dir, b->dirv.p, s, 0, false, nullptr, nullptr,
+                         nullptr, mixed ? b->r_col16lo.p : nullptr, mixed ? b->r_M16.p : nullptr);
     if (e != cudaSuccess) return bcuda(b, e, "batched rhs");
     if (mixed)
         e = launch_pcg_batch<float>(b, 0, b->a_s, b->a_val32.p, b->a_val.p, b->slice_inst_a.p,
