@@ -231,7 +231,9 @@ __device__ __forceinline__ int bcol(const BPcgArgs<VT>& a, long long e, int row)
 // barrier passed); 2 nd - 1 passes (3-D: U_0^T, U_1^T, U_2 D U_2^T, U_1, U_0;
 // 2-D: U_0^T, U_1 D U_1^T, U_0) over the lines of all instances, one warp
 // per line; the last pass writes z (FP64) and its operator-precision copy.
-// Lines have at most 128 entries.  A block takes a contiguous range of each
+// Lines have at most 128 entries.  Inside the iteration loop the lines of
+// instances that have converged are skipped (skip_converged): one straggler
+// then costs its own lines, not every instance's.  A block takes a contiguous range of each
 // pass's lines (instance-major), so it meets one or a few instances; for
 // each it stages the instance's line matrix (and the middle pass's second
 // one) in shared memory (Wsm: 2 m^2 entries), instead of reading it per
@@ -239,7 +241,7 @@ __device__ __forceinline__ int bcol(const BPcgArgs<VT>& a, long long e, int row)
 // to L2 on every line.
 template <typename VT>
 __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, VT* Wsm, double* z, VT* zl, unsigned* bc,
-                          unsigned& bg, int* err) {
+                          unsigned& bg, int* err, bool skip_converged) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     const int NI = a.n_inst;
@@ -265,6 +267,10 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, VT* Wsm, double* z, VT*
         for (int s0 = l0; s0 < l1;) {
             while (inst + 1 < NI && loff[inst + 1] <= s0) ++inst;
             const int s1 = min(l1, loff[inst + 1]);
+            if (skip_converged && ((volatile double*)a.is)[IS_CONV * NI + inst] != 0.0) {
+                s0 = s1;               // a converged instance's z is not used again
+                continue;
+            }
             const BFd& f = a.fd[inst];
             const int m0 = f.m[0], m1 = f.m[1];
             const int m = f.m[d];
@@ -417,7 +423,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
     if (!bgrid_barrier(bc, bg, err)) return;
     if (fd) {
         // z = P^{-1} r, then (r, z) per slice
-        if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err)) return;
+        if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err, false)) return;
         for (int sl = gw; sl < S; sl += nw) {
             const int i = sl * 32 + lane;
             const double t0 = warp_sum(i < a.n ? a.r[i] * a.z[i] : 0.0);
@@ -567,7 +573,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
             if (!bgrid_barrier(bc, bg, err)) return;
             if (*((volatile unsigned*)&a.active[(it + 1) & 1]) > 0u) {
                 // z = P^{-1} r (every row; converged instances ignore theirs), then (r, z)
-                if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err)) return;
+                if (!bfd_apply(a, xs, Wsm, a.z, zlw, bc, bg, err, true)) return;
                 for (int sl = gw; sl < S; sl += nw) {
                     const int inst = a.slice_inst[sl];
                     const int i = sl * 32 + lane;
