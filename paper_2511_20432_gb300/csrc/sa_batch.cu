@@ -218,7 +218,7 @@ struct BPcgArgs {
     const int* fd_loff;       // 3 x (n_inst + 1)
     const VT* fdS;            // scaling per row
     VT* fdZ;                  // work vector
-    int fd_mmax;              // largest line length (the staged matrices' size)
+    int fd_mmax;              // line length the staged matrices hold (0: read through L1)
 };
 
 template <typename VT>
@@ -280,14 +280,17 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, VT* Wsm, double* z, VT*
             __syncthreads();
             const VT* Wg = (const VT*)(pass < nd ? f.U[d] : f.Ut[d]);
             const VT* W2g = (const VT*)f.Ut[nd - 1];
-            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-                sa_dev::cp_async_ca<sizeof(VT)>(Wsm + t, Wg + t);
-                if (mid) sa_dev::cp_async_ca<sizeof(VT)>(Wsm + m * m + t, W2g + t);
+            const bool staged = a.fd_mmax > 0;   // else (too large to stage) through L1
+            if (staged) {
+                for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                    sa_dev::cp_async_ca<sizeof(VT)>(Wsm + t, Wg + t);
+                    if (mid) sa_dev::cp_async_ca<sizeof(VT)>(Wsm + m * m + t, W2g + t);
+                }
+                sa_dev::cp_async_wait_all();
+                __syncthreads();
             }
-            sa_dev::cp_async_wait_all();
-            __syncthreads();
-            const VT* W = Wsm;
-            const VT* W2 = Wsm + m * m;
+            const VT* W = staged ? Wsm : Wg;
+            const VT* W2 = staged ? Wsm + m * m : W2g;
             for (int Lg = s0 + wib; Lg < s1; Lg += nwb) {
                 const int L = Lg - loff[inst];
                 const long long base = f.row0 + (d == 0 ? (long long)L * m0
@@ -353,6 +356,15 @@ __device__ bool bfd_apply(const BPcgArgs<VT>& a, VT* xs, VT* Wsm, double* z, VT*
 // dynamic shared memory of k_pcg_batch: two staged line matrices
 template <typename VT>
 size_t batch_pcg_smem(int mmax) { return (size_t)2 * mmax * mmax * sizeof(VT); }
+
+// The line length to stage for: 0 (no staging, matrices read through L1)
+// when two matrices would not fit beside the kernel's static scratch
+// (32 x 128 entries) in a block's 227 KB.
+template <typename VT>
+int batch_pcg_stage_m(int mmax) {
+    const size_t limit = (size_t)227 * 1024 - (size_t)32 * 128 * sizeof(VT) - 1024;
+    return batch_pcg_smem<VT>(mmax) <= limit ? mmax : 0;
+}
 
 template <typename VT>
 __global__ void __launch_bounds__(1024, 1) k_pcg_batch(BPcgArgs<VT> a) {
@@ -688,7 +700,7 @@ cudaError_t launch_pcg_batch(sa_batch* b, int which, const SellDev& s, const voi
     a.fd_loff = fd ? (which == 0 ? b->fd_loff.p : b->fdb_loff.p) : nullptr;
     a.fdS = fd ? (const VT*)(which == 0 ? b->fdS.p : b->fdbS.p) : nullptr;
     a.fdZ = fd ? (VT*)(which == 0 ? b->fdZ.p : b->fdbZ.p) : nullptr;
-    a.fd_mmax = fd ? b->fd_mmax : 0;
+    a.fd_mmax = fd ? batch_pcg_stage_m<VT>(b->fd_mmax) : 0;
     cudaError_t e = cudaMemsetAsync(&b->st.p->bar_count[2 + which], 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->counters.p, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -1106,7 +1118,8 @@ sa_status build(sa_batch* b, double theta, double dt) {
         b->n_step = n0;
         int occ = 0;
         const size_t pcg_smem = (b->fd_on || b->fdb_on)
-                                    ? (mixed ? batch_pcg_smem<float>(b->fd_mmax) : batch_pcg_smem<double>(b->fd_mmax))
+                                    ? (mixed ? batch_pcg_smem<float>(batch_pcg_stage_m<float>(b->fd_mmax))
+                                             : batch_pcg_smem<double>(batch_pcg_stage_m<double>(b->fd_mmax)))
                                     : 0;
         const void* pcg_fn = mixed ? (const void*)k_pcg_batch<float> : (const void*)k_pcg_batch<double>;
         B_CUDA(b, cudaFuncSetAttribute(pcg_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg_smem));
