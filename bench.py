@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--legs", default="all",
                     help="comma list of the legs after the main timed region to run: stages, "
-                         "variants, cutoff, e2e, batched, plate, arc, learned, cpu (default all; the "
+                         "variants, cutoff, e2e, batched, plate, lasers, arc, learned, cpu (default all; the "
                          "form used for profiling one leg)")
     ap.add_argument("--quick", action="store_true",
                     help="main timed region only (no stage, FP64, e2e or CPU legs): "
@@ -510,6 +510,52 @@ def plate_leg(sa, W, stream, n_ff, K):
     return out
 
 
+def two_lasers_leg(sa, W, stream, n_ff, K):
+    """Two lasers on the benchmark's block (reading R22): the 20-track
+    meander and the same meander mirrored across the block's mid-plane
+    y = 2 mm, switched on together.  By superposition each laser runs in a
+    context of its own (the same part); a two-laser theta-step is one step of
+    each, and T at the monitor points is sa_eval_T_superposed of the two.
+    Times K steps of both after n_ff untimed ones."""
+    import numpy as np
+    import torch
+    wl = W.block_meander(20, theta=0.5)
+    sc = wl.scan
+    mirrored = W.Scan(path=np.column_stack([sc.path[:, 0], 4.0e-3 - sc.path[:, 1], sc.path[:, 2]]),
+                      seg_on=sc.seg_on, power=sc.power, absorptivity=sc.absorptivity,
+                      speed=sc.speed, spot_radius=sc.spot_radius)
+    wls = [wl, W.Workload(wl.name + "_mirrored", wl.patch, wl.material, mirrored, dt=wl.dt,
+                          theta=wl.theta, n_steps=wl.n_steps)]
+    ctxs = [sa.context_from_workload(w, precision=sa.SA_MIXED, cuda_stream=stream, use_graph=1)
+            for w in wls]
+    th, dt = wl.theta, wl.dt
+    for c in ctxs:
+        c.step(th, dt, n_ff + 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for c in ctxs:
+        c.step(th, dt, K, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rng = np.random.default_rng(5)
+    mon = np.column_stack([rng.uniform(0.2e-3, 3.8e-3, 64), rng.uniform(0.2e-3, 3.8e-3, 64),
+                           rng.uniform(0.5e-3, 1.0e-3, 64)])
+    t0 = time.perf_counter()
+    T = sa.eval_T_superposed(ctxs, mon)
+    t_eval = time.perf_counter() - t0
+    st = [c.step(th, dt, 0) for c in ctxs]
+    out = {"workload": wl.name + " + mirrored meander", "first_step": n_ff + 4, "steps": K,
+           "two_laser_steps_per_s": K / (ms / 1e3),
+           "pcg_iters_per_step": sum(x.pcg_iters_total for x in st) / (2 * K),
+           "superposed_eval_ms_64_points": 1e3 * t_eval,
+           "monitor_T_max_K": float(np.nanmax(T))}
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def batched_leg(sa, W, stream, n_inst, n_steps, rank=0, world=1, dist=None):
     """The batched sweep: n_inst seeded instances (uneven boxes, powers,
     speeds, track counts) stepped together for n_steps theta-steps (the
@@ -815,6 +861,14 @@ def run_ours(args):
     # ---- the plate with a hole ---------------------------------------------------
     plate = plate_leg(sa, W, stream, 1000, min(K, 300)) if world == 1 and want("plate") else None
 
+    # ---- two lasers by superposition (a leg of its own; an error is reported, not raised)
+    lasers = None
+    if world == 1 and want("lasers"):
+        try:
+            lasers = two_lasers_leg(sa, W, stream, n0, min(K, 300))
+        except Exception as exc:   # the main line stands without this leg
+            lasers = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- the quarter-cylinder part: heat-loss rates along the top arc ------------
     qcyl = quarter_cylinder_leg(sa, W, stream) if world == 1 and want("arc") else None
     qcon = quarter_cylinder_leg(sa, W, stream, "contour") if world == 1 and want("arc") else None
@@ -920,6 +974,7 @@ def run_ours(args):
                 if e2e is not None else None),
         "history_cutoff": cutoff,
         "plate_with_hole": plate,
+        "two_lasers": lasers,
         "quarter_cylinder_single_source": qcyl,
         "quarter_cylinder_contour": qcon,
         "batched_256": batched,

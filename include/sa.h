@@ -262,6 +262,28 @@ sa_status sa_step(sa_ctx* ctx, double theta, double dt, int n_steps, sa_step_sta
 sa_status sa_eval_T(sa_ctx* ctx, const double* pts, int n, double* T_out, int on_device);
 
 /*
+ * T = T~ + T^ at n physical points for SEVERAL LASERS on one part, by
+ * superposition (the setting of Section 2 allows several lasers; its outlook
+ * names them): the problem is linear (constant material, Eq. that-heat with
+ * linear boundary data in T~, and T~ a plain sum over sources, Eq.
+ * sum-of-point-temp), so the temperature of lasers 1..L switched on together
+ * is sum_l T_l - (L - 1) T_c, where T_l is the temperature with laser l
+ * alone.  ctxs[l] is a context that carries laser l alone (sa_set_scan with
+ * its path, power and speed), stepped with the same theta and dt as the
+ * others (separately, or together in an sa_batch).
+ *   ctxs     n_ctx >= 1 contexts on the current device: same patch (the
+ *            same control-variable count), material and T_c, and the same
+ *            step index (SA_ERR_ARG otherwise)
+ *   pts      n*3 doubles, host (on_device = 0) or device (on_device = 1)
+ *   T_out    n doubles, same memory space; NaN outside the patch
+ * Each context evaluates like sa_eval_T (its own precision); the sum runs
+ * on the device.  Working buffers belong to ctxs[0] (grown on demand, kept).
+ * Synchronous.  Errors: SA_ERR_ARG, SA_ERR_STATE, SA_ERR_CUDA.
+ */
+sa_status sa_eval_T_superposed(sa_ctx* const* ctxs, int n_ctx, const double* pts, int n, double* T_out,
+                               int on_device);
+
+/*
  * Heat-loss rates at n physical points with unit normals (Section 3.1, the
  * diagnostic q~ + q^ = -k dT/dn of the adiabatic boundary): q~ = -k n . grad T~
  * (the history sum's gradient at t_n) and q^ = -k n . grad T^ (grad T^ =

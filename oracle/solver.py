@@ -187,3 +187,49 @@ class Model:
             qt = -self.mat.k * pointsource.dTdn_tilde(x, nrm, self.xs[:K], self.source_ages(self.n),
                                                        self.E, self.mat, self.s_img)
         return x, qt, np.array(qh)
+
+
+class MultiLaserModel(Model):
+    """Several lasers on one patch, all switched on at t = 0 with the same
+    time step (reading R22): every laser's discretised sources (its own path,
+    speed and power; source j of laser l active from step j on) enter the
+    same history sums, i.e. T~ and dT~/dn are Eq. sum-of-point-temp summed
+    over the lasers, and ONE correction field T^ takes the combined boundary
+    data through the theta-scheme.  ``workload`` gives the patch, material,
+    dt and theta (its own scan is not used)."""
+
+    def __init__(self, workload, scans, s_img=2.0, direct=True):
+        super().__init__(workload, s_img, direct)
+        self.lasers = [(sources.discretize(sc, self.dt), sources.energy(sc, self.dt), sc.spot_radius)
+                       for sc in scans]
+
+    def _laser_terms(self, n):
+        """(positions, ages, E) of the sources of each laser active at step n."""
+        out = []
+        for xs, E, r in self.lasers:
+            K = min(n, len(xs))
+            if K > 0:
+                out.append((xs[:K], pointsource.ages(n, K, self.dt, self.mat, r), E))
+        return out
+
+    def flux_normal_derivative(self, n):
+        if self.lat is None:
+            return np.zeros(0)
+        s = np.zeros(len(self.lat["x"]))
+        for xs, age, E in self._laser_terms(n):
+            s += pointsource.dTdn_tilde(self.lat["x"], self.lat["n"], xs, age, E, self.mat, self.s_img)
+        return s
+
+    def T_tilde_at(self, x, n):
+        t = np.zeros(len(x))
+        for xs, age, E in self._laser_terms(n):
+            t += pointsource.T_tilde(x, xs, age, E, self.mat, self.s_img)
+        return t
+
+    def eval_flux(self, xi_pts, nrm):
+        """As Model.eval_flux, q~ summed over the lasers."""
+        x, _, qh = Model.eval_flux(self, xi_pts, nrm)
+        qt = np.zeros(len(x))
+        for xs, age, E in self._laser_terms(self.n):
+            qt += -self.mat.k * pointsource.dTdn_tilde(x, np.atleast_2d(nrm), xs, age, E, self.mat, self.s_img)
+        return x, qt, qh

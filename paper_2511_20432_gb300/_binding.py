@@ -84,6 +84,7 @@ def _load():
         "sa_step": (I, [P, D, D, I, C.POINTER(sa_step_stats)]),
         "sa_eval_T": (I, [P, P, I, P, I]),
         "sa_eval_T_noalloc": (I, [P, P, I, P]),
+        "sa_eval_T_superposed": (I, [P, I, P, I, P, I]),
         "sa_eval_flux": (I, [P, P, P, I, P, P, I]),
         "sa_get_sizes": (I, [P, C.POINTER(sa_sizes)]),
         "sa_get_field": (I, [P, I, P, LL, I]),
@@ -427,6 +428,21 @@ class Batch:
         sh = sa_batch_shapes()
         self._check(lib.sa_batch_get_shapes(self.ptr, C.byref(sh)))
         return sh.as_dict()
+
+
+def eval_T_superposed(ctxs, pts, out=None, on_device=False):
+    """T at points for several lasers on one part: ctxs[l] carries laser l
+    alone (same patch, material and step); sa_eval_T_superposed forms
+    sum_l T_l - (L - 1) T_c on the device (see include/sa.h)."""
+    arr = (C.c_void_p * len(ctxs))(*[c.ptr.value for c in ctxs])
+    c0 = ctxs[0].ptr if ctxs else None
+    if on_device:
+        _check(c0, lib.sa_eval_T_superposed(arr, len(ctxs), _ptr(pts), int(pts.shape[0]), _ptr(out), 1))
+        return out
+    p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    o = np.empty(p.shape[0]) if out is None else out
+    _check(c0, lib.sa_eval_T_superposed(arr, len(ctxs), _ptr(p), int(p.shape[0]), _ptr(o), 0))
+    return o
 
 
 def selftest_waits():

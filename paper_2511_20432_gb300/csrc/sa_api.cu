@@ -1824,6 +1824,67 @@ sa_status sa_eval_T(sa_ctx* c, const double* pts, int n, double* T_out, int on_d
     return eval_points(c, pts, nullptr, n, T_out, nullptr, on_device);
 }
 
+}  // extern "C"
+
+namespace {
+// acc += t - T_c: one more laser's temperature onto the superposed sum
+__global__ void k_superpose(int n, const double* t, double* acc, double Tc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) acc[i] += t[i] - Tc;
+}
+}  // namespace
+
+extern "C" {
+
+sa_status sa_eval_T_superposed(sa_ctx* const* ctxs, int n_ctx, const double* pts, int n, double* T_out,
+                               int on_device) {
+    if (!ctxs || n_ctx < 1 || !ctxs[0]) return SA_ERR_ARG;
+    sa_ctx* c0 = ctxs[0];
+    sa_status st = check_usable(c0);
+    if (st) return st;
+    for (int l = 0; l < n_ctx; ++l) {
+        sa_ctx* c = ctxs[l];
+        if (!c) return sa_fail(c0, SA_ERR_ARG, "context %d is null", l);
+        if ((st = check_usable(c))) return sa_fail(c0, st, "context %d is not usable", l);
+        if (!c->has_patch || !c->has_material)
+            return sa_fail(c0, SA_ERR_STATE, "context %d needs patch and material", l);
+        if (c->n_dof != c0->n_dof || c->k != c0->k || c->rho != c0->rho || c->cp != c0->cp ||
+            c->Tc != c0->Tc)
+            return sa_fail(c0, SA_ERR_ARG, "context %d: another part or material than context 0", l);
+        if (c->n_step != c0->n_step)
+            return sa_fail(c0, SA_ERR_ARG, "context %d is at step %lld, context 0 at %lld", l,
+                           c->n_step, c0->n_step);
+    }
+    if (n < 0 || (n > 0 && (!pts || !T_out))) return sa_fail(c0, SA_ERR_ARG, "bad argument");
+    if (n == 0) return SA_OK;
+    cudaStream_t s = c0->stream;
+    if (c0->sup_acc.n < (size_t)n) {
+        SA_ALLOC(c0, c0->sup_acc, (size_t)n);
+        SA_ALLOC(c0, c0->sup_tmp, (size_t)n);
+    }
+    const double* dpts = pts;
+    if (!on_device) {
+        if (c0->sup_pts.n < (size_t)3 * n) SA_ALLOC(c0, c0->sup_pts, (size_t)3 * n);
+        SA_CUDA(c0, cudaMemcpyAsync(c0->sup_pts.p, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        SA_CUDA(c0, cudaStreamSynchronize(s));   // the other contexts read the points on their streams
+        dpts = c0->sup_pts.p;
+    }
+    // laser 0 into the sum, then each further laser's T - T_c onto it (each
+    // evaluation is synchronous on its context's stream)
+    if ((st = eval_points(c0, dpts, nullptr, n, c0->sup_acc.p, nullptr, 1))) return st;
+    for (int l = 1; l < n_ctx; ++l) {
+        if ((st = eval_points(ctxs[l], dpts, nullptr, n, c0->sup_tmp.p, nullptr, 1)))
+            return sa_fail(c0, st, "context %d: %s", l, sa_last_error(ctxs[l]));
+        k_superpose<<<(n + 255) / 256, 256, 0, s>>>(n, c0->sup_tmp.p, c0->sup_acc.p, c0->Tc);
+        SA_CUDA(c0, cudaGetLastError());
+        SA_CUDA(c0, cudaStreamSynchronize(s));   // sup_tmp is rewritten by the next laser
+    }
+    SA_CUDA(c0, cudaMemcpyAsync(T_out, c0->sup_acc.p, sizeof(double) * n,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    SA_CUDA(c0, cudaStreamSynchronize(s));
+    return SA_OK;
+}
+
 sa_status sa_eval_flux(sa_ctx* c, const double* pts, const double* nrm, int n, double* q_tilde,
                        double* q_hat, int on_device) {
     if (!nrm && n > 0) return c ? sa_fail(c, SA_ERR_ARG, "nrm is NULL") : SA_ERR_ARG;

@@ -381,6 +381,9 @@ struct sa_ctx {
     DBuf<short> r_col16lo;
     DBuf<unsigned short> r_M16;
     int r_dir_sl0 = 0, r_dir_sl1 = -1;   // slices with Dirichlet columns lie in [sl0, sl1)
+    // sa_eval_T_superposed (this context first in the list): points, the sum
+    // and one context's values, n entries each (3 n for the points)
+    DBuf<double> sup_pts, sup_acc, sup_tmp;
 
     // ---- device: scan and history ------------------------------------------
     DBuf<double2> src_pos;    // relative (x - x_ref, y - y_ref)

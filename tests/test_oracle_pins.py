@@ -863,3 +863,65 @@ def test_pin_C1_cutoff_bound_by_brute_force():
             b1 = ps.unit_bound(p, p, xs, age, E, mat, normal=normal)
             t1 = T[len(pts) // 3] if normal is None else terms[len(pts) // 3]
             assert np.allclose(b1, t1, rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# R22: several lasers.  The multi-laser model sums every laser's sources in
+#      the history sums and runs ONE theta-scheme; the pins check it against
+#      routes that do not share that sum: single-laser models (the problem
+#      is linear, so one solve of the combined data must equal the sum of
+#      single-laser solves, sum_l T_l - (L - 1) T_c), a one-laser list
+#      (the plain model), and mirror symmetry of two mirrored lasers.
+# ---------------------------------------------------------------------------
+def _single(wl, scan):
+    m = Model(W.Workload("laser", wl.patch, wl.material, scan, dt=wl.dt, theta=wl.theta,
+                         n_steps=wl.n_steps))
+    m.run(wl.n_steps)
+    return m
+
+
+def test_R22_multi_laser_one_laser_is_the_plain_model():
+    from oracle.solver import MultiLaserModel
+    wl, scans = W.two_lasers_cuboid(n_steps=12)
+    m = MultiLaserModel(wl, scans[:1])
+    m.run(12)
+    ref = _single(wl, scans[0])
+    assert np.abs(m.T_hat - ref.T_hat).max() <= 1e-12 * np.abs(ref.T_hat).max()
+    assert np.abs(m.F - ref.F).max() <= 1e-12 * max(np.abs(ref.F).max(), 1e-300)
+
+
+def test_R22_multi_laser_superposition_of_single_laser_solves():
+    from oracle.solver import MultiLaserModel
+    wl, scans = W.two_lasers_cuboid(n_steps=30)
+    m = MultiLaserModel(wl, scans)
+    m.run(30)
+    singles = [_single(wl, sc) for sc in scans]
+    Tc = wl.material.T_c
+    sup = sum(s.T_hat for s in singles) - (len(singles) - 1) * Tc
+    assert np.abs(m.T_hat - sup).max() <= 1e-9 * np.abs(sup).max()
+    # F (linear in the sources, no T_c offset) and T at points on and under the tracks
+    assert np.abs(m.F - sum(s.F for s in singles)).max() <= 1e-10 * np.abs(m.F).max()
+    xi = np.array([[0.30, 0.30, 1.0], [0.50, 0.50, 0.9], [0.60, 0.70, 1.0], [0.10, 0.90, 0.5],
+                   [0.80, 0.20, 0.2]])
+    _, T = m.eval_T(xi)
+    Ts = sum(s.eval_T(xi)[1] for s in singles) - (len(singles) - 1) * Tc
+    assert np.abs(T - Ts).max() <= 1e-9 * np.abs(Ts).max()
+    # both lasers matter: each single-laser field differs from the combined one
+    for s in singles:
+        assert np.abs(s.T_hat - m.T_hat).max() > 1e-3
+
+
+def test_R22_mirrored_lasers_give_a_mirror_symmetric_field():
+    from oracle.solver import MultiLaserModel
+    wl, scans = W.two_lasers_cuboid(powers=(180.0, 180.0), ys=(0.3e-3, 0.7e-3), n_steps=20)
+    m = MultiLaserModel(wl, scans)
+    m.run(20)
+    # near the tracks (laser front at x ~ 0.45 mm after 20 steps) and away from them
+    xi = np.array([[0.20, 0.30, 1.0], [0.18, 0.25, 0.95], [0.45, 0.35, 0.8], [0.70, 0.10, 0.4],
+                   [0.55, 0.45, 1.0]])
+    mirror = xi.copy()
+    mirror[:, 1] = 1.0 - mirror[:, 1]
+    _, T = m.eval_T(xi)
+    _, Tm = m.eval_T(mirror)
+    assert np.abs(T - Tm).max() <= 1e-9 * np.abs(T).max()
+    assert np.abs(T - wl.material.T_c).max() > 1e-3

@@ -608,3 +608,50 @@ def test_history_cutoff_stays_within_its_bound(sa, prec):
         prev = (np.abs(ref[0]).max(), np.abs(ref[1]).max())
     assert skipped > 0 and skipped_full == 0
     print(f"\ncutoff eta {eta}: {skipped} pairs skipped, largest error {worst:.3f} eta M")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_two_lasers_superposed_match_the_multi_laser_oracle(sa, prec):
+    """Two lasers on the cuboid (reading R22): one context per laser, each
+    stepped on its own, evaluated together by sa_eval_T_superposed, against
+    the oracle that sums both lasers' sources and runs one theta-scheme.
+    Host and device points give the same values; contexts at different steps
+    are refused."""
+    import torch
+    from oracle.solver import MultiLaserModel
+    n_steps = 40
+    wl, scans = W.two_lasers_cuboid(n_steps=n_steps)
+    m = MultiLaserModel(wl, scans)
+    m.run(n_steps)
+    p = sa.SA_FP64 if prec == "fp64" else sa.SA_MIXED
+    tol = 1e-15 if prec == "fp64" else 1e-10
+    wls = [W.Workload(f"laser{l}", wl.patch, wl.material, sc, dt=wl.dt, theta=wl.theta,
+                      n_steps=n_steps) for l, sc in enumerate(scans)]
+    ctxs = [gpu_context(w, p, pcg_tol=tol) for w in wls]
+    for c in ctxs:
+        c.step(wl.theta, wl.dt, n_steps)
+    rng = np.random.default_rng(11)
+    xi = rng.uniform(0, 1, (30, 3))
+    xi[:10, 2] = 1.0
+    xi[:5, 0] = rng.uniform(0.15, 0.30, 5)      # near the two laser fronts
+    xi[:5, 1] = np.where(np.arange(5) % 2 == 0, 0.3, 0.7)
+    x, T_ref = m.eval_T(xi)
+    T = sa.eval_T_superposed(ctxs, x)
+    assert np.abs(T_ref - wl.material.T_c).max() > 1.0      # the lasers heat the part
+    if prec == "fp64":
+        assert rel_linf(T, T_ref) <= TOL_FP64
+    else:
+        assert rel_linf(T, T_ref) <= TOL_MIXED_REL
+        assert np.abs(T - T_ref).max() <= TOL_MIXED_ABS
+    # device points and output: the same values
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    Td = torch.empty(len(x), dtype=torch.float64, device="cuda")
+    sa.eval_T_superposed(ctxs, xd, out=Td, on_device=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(Td.cpu().numpy(), T)
+    # contexts at different steps are refused
+    ctxs[1].step(wl.theta, wl.dt, 1)
+    with pytest.raises(sa.SAError):
+        sa.eval_T_superposed(ctxs, x)
+    for c in ctxs:
+        c.close()

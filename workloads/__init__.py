@@ -310,6 +310,20 @@ def cuboid_single_track(theta=1.0, n_steps=150) -> Workload:
                     scan, dt=10e-6, theta=theta, n_steps=n_steps)
 
 
+def two_lasers_cuboid(powers=(200.0, 150.0), ys=(0.3e-3, 0.7e-3), theta=0.5, n_steps=60):
+    """The 2.0 x 1.0 x 0.5 mm cuboid (degree 2, 16x8x4 elements) with two
+    lasers switched on together: straight 1.5 mm tracks along x at y = ys[0]
+    and ys[1], powers ``powers``, A = 0.4, v = 1 m/s, dt = 10 us.  Returns the
+    workload (patch, material, dt, theta; its scan is laser 0) and the list of
+    the two scans."""
+    patch = cuboid_patch((2.0e-3, 1.0e-3, 0.5e-3), (16, 8, 4), 2)
+    scans = [straight_track((0.25e-3, y, 0.5e-3), (1.75e-3, y, 0.5e-3), power=p,
+                            absorptivity=0.4, speed=1.0) for p, y in zip(powers, ys)]
+    wl = Workload("cuboid_2x1x0.5mm_p2_16x8x4_two_lasers", patch, MAT_DEFAULT, scans[0],
+                  dt=10e-6, theta=theta, n_steps=n_steps)
+    return wl, scans
+
+
 def block_meander(n_tracks=20, theta=0.5, n_steps=None, n_el=(64, 64, 16),
                   size=(4.0e-3, 4.0e-3, 1.0e-3)) -> Workload:
     """4 x 4 x 1 mm block, degree 2, 64x64x16 elements (78,408 control
