@@ -170,6 +170,25 @@ def _boundary_normals_inward(geom, kind):
     return pts
 
 
+def _laser_terms_last_laser_dropped(self, n):
+    out = []
+    for xs, E, r in self.lasers[:-1]:
+        K = min(n, len(xs))
+        if K > 0:
+            out.append((xs[:K], pointsource.ages(n, K, self.dt, self.mat, r), E))
+    return out
+
+
+def _laser_terms_first_laser_energy(self, n):
+    out = []
+    E0 = self.lasers[0][1]
+    for xs, E, r in self.lasers:
+        K = min(n, len(xs))
+        if K > 0:
+            out.append((xs[:K], pointsource.ages(n, K, self.dt, self.mat, r), E0))
+    return out
+
+
 MUTATIONS = {
     "ages one step too old": (
         (pointsource, "ages", _ages_one_step_old),
@@ -222,6 +241,12 @@ MUTATIONS = {
     "q~ with the wrong sign": (
         (solver.Model, "eval_flux", _eval_flux_wrong_q_tilde_sign),
         [(pins.test_heat_loss_rate_is_minus_k_times_the_normal_derivative, ())]),
+    "several lasers: the last laser dropped": (
+        (solver.MultiLaserModel, "_laser_terms", _laser_terms_last_laser_dropped),
+        [(pins.test_R22_multi_laser_superposition_of_single_laser_solves, ())]),
+    "several lasers: every laser with the first one's power": (
+        (solver.MultiLaserModel, "_laser_terms", _laser_terms_first_laser_energy),
+        [(pins.test_R22_multi_laser_superposition_of_single_laser_solves, ())]),
     "full-space kernel (s_img = 1) in the model": (
         (solver.Model, "__init__", _model_full_space),
         [(pins.test_table3_integrated_analytical_heat_loss, ())]),
